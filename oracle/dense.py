@@ -1,0 +1,131 @@
+"""Dense Galerkin system of Section 2.3 (def:linsys, eq_linsysEntry), solved by LU.
+
+TEST INFRASTRUCTURE (see the package header). Pins, in tests/test_oracle_*.py:
+  * pair integrals -- Sauter-Schwab sub-maps integrate polynomials on tau x tau exactly;
+    coplanar identical pairs give exactly zero K2/K3 integrals; the G0 part of identical and
+    adjacent pairs matches a closed-form inner integral (uniformly charged flat triangle)
+    with high-order outer Gauss quadrature; K1/K4 blocks are symmetric.
+  * solve + energy -- Kirkwood closed form (centred charge) and Kirkwood series (off-centre
+    charges) within the discretisation error the paper prints in Table 1; the null case
+    eps = 1, kappa = 0 gives A = mass matrix and E = 0.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import lib
+
+KCAL = 4.0 * np.pi * 332.0716  # e_c/(4 pi A) -> kcal/mol/e_c (Section 3)
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Phys:
+    """eps1 (inside), eps2 (outside), kappa (1/Angstrom), qs (Gauss points per cube axis of
+    the singular quadrature)."""
+
+    def __init__(self, eps1=1.0, eps2=80.0, kappa=0.1257, qs=3):
+        self.eps1, self.eps2, self.kappa, self.qs = float(eps1), float(eps2), float(kappa), int(qs)
+
+    @property
+    def eps(self):
+        return self.eps2 / self.eps1
+
+
+def gauss_legendre01(n):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    if lib().orc_gauss_legendre01(n, _dp(x), _dp(w)) != 0:
+        raise ValueError("order out of range")
+    return x, w
+
+
+def kernel_point(x, nx, y, ny, eps, kappa):
+    out = np.zeros(4)
+    lib().orc_kernel_point(_dp(_f64(x)), _dp(_f64(nx)), _dp(_f64(y)), _dp(_f64(ny)), eps, kappa, _dp(out))
+    return out
+
+
+def geometry(verts, tris):
+    V, T = _f64(verts), _i32(tris)
+    nt = T.shape[0]
+    c = np.zeros((nt, 3))
+    a = np.zeros(nt)
+    n = np.zeros((nt, 3))
+    lib().orc_geometry(_dp(V), _ip(T), nt, _dp(c), _dp(a), _dp(n))
+    return c, a, n
+
+
+def ss_points(case, xi, h1, h2, h3):
+    xh = np.zeros(12)
+    yh = np.zeros(12)
+    jac = np.zeros(6)
+    k = lib().orc_ss_points(case, xi, h1, h2, h3, _dp(xh), _dp(yh), _dp(jac))
+    return xh[: 2 * k].reshape(k, 2), yh[: 2 * k].reshape(k, 2), jac[:k]
+
+
+def pair_integrals(verts, tris, i, j, ph: Phys):
+    V, T = _f64(verts), _i32(tris)
+    out = np.zeros(4)
+    lib().orc_pair_integrals(_dp(V), _ip(T), int(i), int(j), ph.eps, ph.kappa, ph.qs, _dp(out))
+    return out
+
+
+def assemble(verts, tris, ph: Phys):
+    """Dense 2N x 2N matrix, unknowns ordered [phi; dphi/dn]."""
+    V, T = _f64(verts), _i32(tris)
+    nt = T.shape[0]
+    A = np.zeros((2 * nt, 2 * nt))
+    lib().orc_assemble(_dp(V), _ip(T), nt, ph.eps, ph.kappa, ph.qs, _dp(A))
+    return A
+
+
+def rows_matvec(verts, tris, ph: Phys, elems, x):
+    """(A x) restricted to the phi and dphi/dn rows of the given elements: returns (y1, y2)."""
+    V, T = _f64(verts), _i32(tris)
+    e = _i32(elems)
+    xx = _f64(x)
+    y = np.zeros(2 * e.shape[0])
+    lib().orc_rows_matvec(_dp(V), _ip(T), T.shape[0], ph.eps, ph.kappa, ph.qs, e.shape[0], _ip(e), _dp(xx), _dp(y))
+    return y[0::2].copy(), y[1::2].copy()
+
+
+def rhs(mesh, ph: Phys):
+    V, T = _f64(mesh.verts), _i32(mesh.tris)
+    b = np.zeros(2 * T.shape[0])
+    lib().orc_rhs(_dp(V), _ip(T), T.shape[0], _dp(_f64(mesh.qpos)), _dp(_f64(mesh.q)), mesh.nc, ph.eps1, _dp(b))
+    return b
+
+
+def energy(mesh, ph: Phys, x):
+    """Solvation energy (eqsolengdis) in kcal/mol."""
+    V, T = _f64(mesh.verts), _i32(mesh.tris)
+    xx = _f64(x)
+    return float(
+        lib().orc_energy(_dp(V), _ip(T), T.shape[0], _dp(_f64(mesh.qpos)), _dp(_f64(mesh.q)), mesh.nc, ph.eps, ph.kappa, _dp(xx))
+    )
+
+
+def solve(mesh, ph: Phys, A=None):
+    """Dense LU solve of A x = b (partial pivoting, LAPACK via numpy)."""
+    if A is None:
+        A = assemble(mesh.verts, mesh.tris, ph)
+    b = rhs(mesh, ph)
+    x = np.linalg.solve(A, b)
+    return x, A, b
