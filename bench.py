@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the FMM-accelerated Galerkin PB solve on GB300.
+
+Workload (default): the Kirkwood sphere with off-centre charges -- radius 20 A, icosphere
+level 6 (81920 flat triangles, 163840 unknowns), 50 charges uniform in the ball of radius
+16 A with values uniform in [-1, 1] e (seed 2000), eps_in = 1, eps_out = 80,
+kappa = 0.1257 / A; FMM order p = 8, eta0 = 0.8, leaf size 64, FP32 bulk arithmetic with
+FP64 singular integrals, Arnoldi and energy (mixed precision), block-diagonal
+preconditioner, GMRES(50) to 1e-6 relative residual.
+
+One step = the whole hot path on the resident mesh: pb_build_tree (geometry, octree,
+lists, singular integrals, preconditioner), pb_gmres_solve (right-hand side + GMRES with
+FMM products) and pb_solvation_energy. value = element-matvecs per second of the step:
+N x (matrix-vector products the solver performed) / step time, in Melem/s -- setup
+included. The L2 cache is flushed between steps (outside the timed events).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM matvec Melem/s (whole solve: setup + GMRES to 1e-6 + energy)"
+UNIT = "Melem/s"
+FLOPS_PER_NEAR_PAIR = 75  # formula count of the near-field pair evaluation (exp, rsqrt as 1 each)
+
+
+def workload(level=6, seed=2000):
+    from paper_2110_13778_gb300 import inputs
+
+    return inputs.kirkwood_ball(level, 20.0, 50, 16.0, seed)
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--level", type=int, default=6)
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--eta0", type=float, default=0.8)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        reasons = set()
+        for s in self.samples:
+            for k, name in enumerate(self.NAMES):
+                if s[3 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------- distributed plumbing (replicas)
+def dist_setup(ngpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if os.environ.get("PB_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return rank, world, local
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+def cpu_oracle_rate(mesh, budget_s=12.0, max_rows=None):
+    """Dense-Galerkin rows of A x per second on the host cores (oracle, as it stands).
+    A full product is N rows, so rows/s / 1e6 is the oracle's element-matvec rate."""
+    from oracle import dense
+
+    ph = dense.Phys(1.0, 80.0, 0.1257, qs=3)
+    x = np.random.default_rng(0).uniform(-1, 1, 2 * mesh.nt)
+    rows = 8
+    t0 = time.perf_counter()
+    dense.rows_matvec(mesh.verts, mesh.tris, ph, np.arange(rows), x)
+    t1 = time.perf_counter() - t0
+    nrows = int(min(mesh.nt if max_rows is None else max_rows, max(rows, budget_s / max(t1, 1e-9) * rows)))
+    sel = np.linspace(0, mesh.nt - 1, nrows).astype(np.int32)
+    t0 = time.perf_counter()
+    dense.rows_matvec(mesh.verts, mesh.tris, ph, sel, x)
+    dt = time.perf_counter() - t0
+    return nrows / dt / 1e6, nrows, dt
+
+
+def run_reference(a):
+    rank, world, local = dist_setup(a.gpus)
+    if rank != 0:
+        return 0
+    mesh = workload(a.level)
+    cores = os.cpu_count()
+    for _ in range(a.warmup):
+        cpu_oracle_rate(mesh, budget_s=1.0, max_rows=64)
+    vals, times = [], []
+    for _ in range(a.steps):
+        v, nrows, dt = cpu_oracle_rate(mesh, budget_s=8.0)
+        vals.append(v)
+        times.append(dt)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(a, mesh),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"dense Galerkin rows of A x (one-point + Sauter-Schwab qs=3), {nrows} sampled rows "
+                                   f"of the {mesh.nt}-triangle workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(a, mesh):
+    return {
+        "workload": f"Kirkwood sphere r=20 A, icosphere level {a.level} ({mesh.nt} triangles), 50 charges in r<=16 A, "
+                    f"eps 1/80, kappa 0.1257",
+        "N": mesh.nt, "p": a.p, "eta0": a.eta0, "leaf_size": a.leaf, "precision": a.precision,
+        "precond": "block-diagonal (leaf level)", "gmres": f"GMRES(50) tol {a.tol}",
+        "step": "build_tree + gmres_solve + solvation_energy on the resident mesh",
+        "l2": "flushed between steps (256 MiB write, outside the timed events)",
+    }
+
+
+def peaks(sm_max_mhz):
+    """Roofline denominators: measured HBM copy bandwidth, and ALU peaks derived from unit
+    counts (152 SMs x 128 FP32 lanes x 2 flops per FMA x clock; FP64 at the nominal
+    1.25 TFLOP/s of the part)."""
+    mhz = sm_max_mhz or 2070.0
+    hbm = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm = json.load(f).get("hbm_gbs")
+    except OSError:
+        pass
+    return {"fp32_tflops": 152 * 128 * 2 * mhz * 1e6 / 1e12, "fp64_tflops": 1.25, "hbm_gbs": hbm or 6800.0,
+            "hbm_source": "measured" if hbm else "fallback"}
+
+
+def run_ours(a):
+    rank, world, local = dist_setup(a.gpus)
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_2110_13778_gb300 import build, pb
+
+    build.build()
+    mesh = workload(a.level)
+    N = mesh.nt
+    prec = pb.PB_MIXED if a.precision == "mixed" else pb.PB_FP64
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def make_ctx(precision):
+        prm = pb.params(eps_in=1.0, eps_out=80.0, kappa=0.1257, eta0=a.eta0, leaf_size=a.leaf, p=a.p, qs=3,
+                        precision=precision, precond=pb.PB_PRECOND_BLOCK)
+        return pb.pb_create(prm, stream)
+
+    ctx = make_ctx(prec)
+    pb.pb_mesh_upload(ctx, mesh.verts, mesh.tris, mesh.qpos, mesh.q)
+    x = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def step(c):
+        pb.pb_build_tree(c)
+        info = pb.pb_gmres_solve(c, x, tol=a.tol, max_iter=500, restart=50)
+        E = pb.pb_solvation_energy(c, x)
+        return info, E
+
+    for _ in range(a.warmup):
+        step(ctx)
+    torch.cuda.synchronize()
+    pb.pb_set_timing(ctx, 1)
+    n0 = pb.pb_get_launch_count(ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    times, matvecs, iters, energies = [], 0, [], []
+    barrier(world)
+    with ClockSampler(local) as clk:
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0.record()
+            info, E = step(ctx)
+            ev1.record()
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+            matvecs += info.matvecs
+            iters.append(info.iterations)
+            energies.append(E)
+    barrier(world)
+    launches = pb.pb_get_launch_count(ctx) - n0
+    phases = pb.pb_get_timing(ctx)
+    pb.pb_set_timing(ctx, 0)
+    stats = pb.pb_get_tree_stats(ctx)
+    t_total = sum(times) / 1e3
+    t_max = dist_max(t_total, world)
+    value = world * N * matvecs / t_max / 1e6
+
+    # matrix-vector product alone, resident, L2 warm (reported beside the step metric)
+    xv = torch.rand(2 * N, dtype=torch.float64, device="cuda")
+    yv = torch.empty_like(xv)
+    for _ in range(3):
+        pb.pb_matvec(ctx, xv, yv)
+    torch.cuda.synchronize()
+    ev0.record()
+    nmv = 20
+    for _ in range(nmv):
+        pb.pb_matvec(ctx, xv, yv)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_mv = ev0.elapsed_time(ev1) / nmv
+
+    # end to end through the public API with host buffers
+    pin = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).pin_memory().numpy()
+    hv, ht, hqp, hq = pin(mesh.verts), pin(mesh.tris), pin(mesh.qpos), pin(mesh.q)
+    xh = torch.empty(2 * N, dtype=torch.float64).pin_memory()
+    e2e_t, e2e_mv = [], 0
+    for k in range(a.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pb.pb_mesh_upload(ctx, hv, ht, hqp, hq)
+        info, E = step(ctx)
+        xh.copy_(x)
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e_t.append(time.perf_counter() - t0)
+            e2e_mv += info.matvecs
+    e2e_value = world * N * e2e_mv / dist_max(sum(e2e_t), world) / 1e6
+    h2d = hv.nbytes + ht.nbytes + hqp.nbytes + hq.nbytes
+    d2h = 2 * N * 8 + 8
+
+    # plain FP64 method on the same box, for the precision comparison
+    fp64 = None
+    if not a.no_fp64_compare and prec == pb.PB_MIXED:
+        c64 = make_ctx(pb.PB_FP64)
+        pb.pb_mesh_upload(c64, mesh.verts, mesh.tris, mesh.qpos, mesh.q)
+        step(c64)
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev0.record()
+        info64, E64 = step(c64)
+        ev1.record()
+        torch.cuda.synchronize()
+        fp64 = {"solve_ms": ev0.elapsed_time(ev1), "iterations": info64.iterations, "matvecs": info64.matvecs,
+                "energy_kcal": E64, "rel_energy_diff_mixed_vs_fp64": abs(energies[-1] - E64) / abs(E64)}
+        pb.pb_destroy(c64)
+    pb.pb_destroy(ctx)
+
+    clocks = clk.summary()
+    pk = peaks(clocks.get("sm_max_mhz"))
+    per_step = {k: v[0] / a.steps for k, v in phases.items()}
+    # roofline of the dominant kernel
+    kernels = {k: v for k, v in phases.items() if v[1] > 0}
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    avg_ms = kernels[dom][0] / kernels[dom][1]
+    near_pairs = stats["near_pairs"] - N
+    roof = {"kernel": dom, "avg_launch_ms": avg_ms}
+    if dom == "near":
+        flops = near_pairs * FLOPS_PER_NEAR_PAIR
+        peak = pk["fp32_tflops"] if prec == pb.PB_MIXED else pk["fp64_tflops"]
+        ach = flops / (avg_ms * 1e-3) / 1e12
+        roof.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "traffic": None, "work_per_launch": f"{near_pairs} element pairs x {FLOPS_PER_NEAR_PAIR} flops"})
+    else:
+        roof.update({"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                     "traffic": None})
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        v, nrows, dt = cpu_oracle_rate(mesh, budget_s=12.0)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{nrows} dense Galerkin rows of A x of the {N}-triangle workload ({dt:.1f} s)"}
+    if rank == 0:
+        try:
+            from oracle import kirkwood
+
+            Ek = kirkwood.series(mesh.qpos, mesh.q, 20.0, 1.0, 80.0, 0.1257)
+        except Exception:  # noqa: BLE001
+            Ek = None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * t_max / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == pb.PB_MIXED else "f64", "data": "synthetic",
+            "config": config_dict(a, mesh), "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+            "gmres_iterations": iters, "matvecs_per_step": matvecs / a.steps,
+            "phases_ms_per_step": per_step, "matvec_ms": t_mv, "matvec_only_melem_s": N / t_mv / 1e3,
+            "energy_kcal": energies[-1], "kirkwood_series_kcal": Ek, "tree": stats, "fp64_method": fp64,
+            "peaks": pk,
+        }
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * libpb -- C ABI of the GB300 Galerkin boundary-integral Poisson-Boltzmann solver.
+ *
+ * The library solves Juffer's derivative boundary integral system (eqbim_3/eqbim_4,
+ * Section 2.2) for the surface potential phi and its normal derivative dphi/dn on a
+ * triangulated molecular surface, discretised by piecewise-constant Galerkin (Section 2.3),
+ * with the matrix-vector product accelerated by the Cartesian FMM of Section 2.4 and solved
+ * by right-preconditioned GMRES with the block-diagonal preconditioner of Section 2.6.
+ *
+ * Conventions for every call:
+ *   - Return value: PB_OK (0) or one of the PB_ERR_* codes below; pb_last_error() gives a
+ *     one-line reason. A failed call leaves the context usable unless it returns
+ *     PB_ERR_CUDA, after which only pb_destroy is allowed.
+ *   - Unknowns are ordered x = [phi_1 .. phi_N, dphi_1 .. dphi_N] (def:linsys), element
+ *     order as uploaded, FP64.
+ *   - "device pointer" arguments point to GPU memory of the current device, allocated and
+ *     owned by the caller (for example a torch tensor's data_ptr). "host pointer" arguments
+ *     point to CPU memory owned by the caller. The library never frees caller memory and
+ *     keeps no caller pointer after a call returns.
+ *   - All GPU work is queued on the stream given to pb_create (NULL = legacy default
+ *     stream). Calls that return a value on the host synchronise that stream; the others
+ *     return with the work queued unless stated otherwise.
+ *   - Units: lengths in Angstrom, charges in e, potentials in e/(4 pi Angstrom) (Section 3),
+ *     energies in kcal/mol.
+ */
+#ifndef PB_H
+#define PB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PB_OK 0
+#define PB_ERR_ARG 1            /* bad argument or parameter */
+#define PB_ERR_MESH 2           /* malformed mesh (degenerate triangle, bad index, ...) */
+#define PB_ERR_CUDA 3           /* a CUDA call failed; the context is no longer usable */
+#define PB_ERR_NOT_CONVERGED 4  /* GMRES hit max_iter before the tolerance */
+#define PB_ERR_NONFINITE 5      /* a NaN or Inf appeared in a residual */
+#define PB_ERR_STATE 6          /* call out of order (e.g. matvec before pb_build_tree) */
+#define PB_ERR_NOMEM 7          /* device allocation failed */
+
+#define PB_FP64 0  /* every step in double precision */
+#define PB_MIXED 1 /* near and far field in FP32 with FP64 leaf-sum accumulation; FP64
+                      singular integrals, preconditioner, Arnoldi, Givens and energy sum */
+
+#define PB_PRECOND_NONE 0
+#define PB_PRECOND_DIAG 1  /* 2x2 blocks of A for each element ("d" in Table 4) */
+#define PB_PRECOND_BLOCK 2 /* blocks of A for all element pairs of one leaf ("bd", Sec. 2.6) */
+
+/* Physical and numerical parameters. */
+typedef struct pb_params {
+    double eps_in;   /* eps_1, dielectric constant inside the surface (Section 2.1) */
+    double eps_out;  /* eps_2, dielectric constant outside */
+    double kappa;    /* inverse Debye length, 1/Angstrom (eqNPBE, Eq_K1) */
+    double eta0;     /* clusters c, c' are neighbours when eta(c,c') > eta0 (def:eta); 0 < eta0 < 1 */
+    int leaf_size;   /* s: the tree depth L is the deepest level with mean cluster size >= s */
+    int levels;      /* > 0: use this depth L instead (1..10) */
+    int p;           /* Taylor order p_L of the finest level (1..10) */
+    int adaptive;    /* 1: p_l = p_L + L - l (variable:order), capped at 12; 0: p_l = p_L */
+    int qs;          /* Gauss-Legendre points per axis of the 4-cube in the singular
+                        (Sauter-Schwab) quadrature, 1..8 */
+    int precision;   /* PB_FP64 or PB_MIXED */
+    int precond;     /* PB_PRECOND_NONE, PB_PRECOND_DIAG or PB_PRECOND_BLOCK */
+} pb_params;
+
+typedef struct pb_ctx pb_ctx;
+
+typedef struct pb_solve_info {
+    int iterations;      /* Arnoldi steps taken (= matrix-vector products after the first) */
+    int matvecs;         /* matrix-vector products, including residual evaluations */
+    double rel_residual; /* final ||b - A x|| / ||b||, recomputed with a true product */
+    int status;          /* PB_OK, PB_ERR_NOT_CONVERGED or PB_ERR_NONFINITE */
+} pb_solve_info;
+
+/* Tree statistics (for tests and reports). */
+typedef struct pb_tree_stats {
+    int levels;           /* L */
+    int nclusters[11];    /* clusters per level 0..L */
+    long long nnear[11];  /* neighbour-list entries per level */
+    long long ninter[11]; /* interaction-list entries per level */
+    int order[11];        /* p_l per level */
+    long long near_pairs; /* element pairs in the near field */
+    long long touching;   /* ordered element pairs sharing a vertex (incl. i == j) */
+    int max_leaf;         /* largest leaf */
+} pb_tree_stats;
+
+/* Create a context. params is copied. stream is a cudaStream_t (may be NULL). */
+int pb_create(const pb_params* params, void* stream, pb_ctx** out);
+
+/* Destroy a context and free all library-owned device memory. Accepts NULL. */
+int pb_destroy(pb_ctx* ctx);
+
+/* One-line description of the last error on this context (never NULL). */
+const char* pb_last_error(const pb_ctx* ctx);
+
+/* Upload a closed surface and its charges (Section 2.3, eqbemesh; source_terms).
+ * verts: host pointer, nv x 3 doubles. tris: host pointer, nt x 3 int32 vertex indices,
+ * counter-clockwise seen from outside (so the normal (v-u)x(w-u) points out of the solute).
+ * qpos: host pointer, nc x 3 doubles; q: host pointer, nc doubles (charge states beyond one
+ * are uploaded with pb_set_charges). Replaces any earlier mesh; copies host -> device and
+ * synchronises. Rejects nt < 1, indices out of range and zero-area triangles (PB_ERR_MESH). */
+int pb_mesh_upload(pb_ctx* ctx, const double* verts, int nv, const int32_t* tris, int nt,
+                   const double* qpos, const double* q, int nc);
+
+/* Replace the charge values (same positions). q: host pointer, nc doubles. */
+int pb_set_charges(pb_ctx* ctx, const double* q, int nc);
+
+/* Build everything that depends only on the geometry (Sections 2.3-2.6): element geometry,
+ * Morton-ordered octree with shrink boxes, neighbour and interaction lists (def:eta),
+ * singular Sauter-Schwab integrals of identical and adjacent triangle pairs, and the
+ * preconditioner factors. Synchronises (list sizes are read back to size allocations). */
+int pb_build_tree(pb_ctx* ctx);
+
+/* y = A x with A of def:linsys/eq_linsysEntry evaluated by the FMM (near field + Taylor
+ * far field). x, y: device pointers, 2N doubles each, must not overlap. Queued, no sync. */
+int pb_matvec(pb_ctx* ctx, const double* x, double* y);
+
+/* b = [b1; b2] of the Galerkin right-hand side (source_terms) by the one-point rule.
+ * b: device pointer, 2N doubles. Queued, no sync. */
+int pb_rhs(pb_ctx* ctx, double* b);
+
+/* z = M^-1 r for the configured preconditioner (identity for PB_PRECOND_NONE).
+ * r, z: device pointers, 2N doubles. Queued, no sync. */
+int pb_precond_apply(pb_ctx* ctx, const double* r, double* z);
+
+/* Solve A x = b for the uploaded charges with right-preconditioned restarted GMRES to
+ * ||b - A x|| <= tol ||b|| (Section 2.3, last paragraph; Section 3). x: device pointer,
+ * 2N doubles; read as the initial guess when use_x0 != 0 (e.g. a learned warm start),
+ * otherwise zero-initialised; overwritten with the solution. restart: Krylov dimension
+ * m (1..200). The Arnoldi process, Givens rotations and updates run on the device in FP64;
+ * the host reads one residual estimate per iteration. info may be NULL. */
+int pb_gmres_solve(pb_ctx* ctx, double* x, double tol, int max_iter, int restart, int use_x0,
+                   pb_solve_info* info);
+
+/* Electrostatic solvation energy (eqsolengdis) for x = [phi; dphi/dn] in kcal/mol, using
+ * the factor 4 pi 332.0716 of Section 3. x: device pointer. E_kcal: host pointer.
+ * Synchronises. */
+int pb_solvation_energy(pb_ctx* ctx, const double* x, double* E_kcal);
+
+/* Tree statistics after pb_build_tree. out: host pointer. Synchronises. */
+int pb_get_tree_stats(pb_ctx* ctx, pb_tree_stats* out);
+
+/* Copy tree data to the host (for parity tests). order: host int32[N], sorted position ->
+ * element index; level_begin: host int32[sum_l nclusters[l]] with each level's cluster
+ * start offsets, concatenated level by level; near_idx / inter_idx: host int32 arrays
+ * sized by pb_tree_stats (sum of nnear / ninter), each level's lists concatenated cluster
+ * by cluster in cluster order; near_cnt / inter_cnt: host int32[sum_l nclusters[l]] list
+ * lengths. Any pointer may be NULL to skip it. Synchronises. */
+int pb_get_tree(pb_ctx* ctx, int32_t* order, int32_t* level_begin, int32_t* near_cnt,
+                int32_t* near_idx, int32_t* inter_cnt, int32_t* inter_idx);
+
+/* Split products for parity tests: y = (mass + near field) x, or y = far-field x, with the
+ * same conventions as pb_matvec. which: 0 = full, 1 = near field incl. mass and singular
+ * corrections, 2 = far field only. */
+int pb_matvec_part(pb_ctx* ctx, const double* x, double* y, int which);
+
+/* Per-phase device times measured with CUDA events recorded around each launch (no extra
+ * synchronisation) while timing is enabled. pb_get_timing synchronises, writes for each slot
+ * s the pair out[2s] = total milliseconds, out[2s+1] = number of timed launches, and resets
+ * the counts. out: host double[2 * PB_TIMING_SLOTS]. At most 256 launches per slot are
+ * remembered between two reads. */
+#define PB_TIMING_SLOTS 12
+#define PB_T_NEAR 0       /* near-field kernel (one-point rule + mass terms) */
+#define PB_T_CORR 1       /* Sauter-Schwab corrections of touching pairs */
+#define PB_T_UP 2         /* leaf moments and MtM */
+#define PB_T_M2L 3        /* MtL on all levels */
+#define PB_T_DOWN 4       /* LtL and LtP */
+#define PB_T_PRECOND 5    /* preconditioner apply */
+#define PB_T_ARNOLDI 6    /* orthogonalisation, Givens, update */
+#define PB_T_SINGULAR 7   /* singular integrals (setup) */
+#define PB_T_TREE 8       /* geometry, octree and lists (setup) */
+#define PB_T_PCBUILD 9    /* preconditioner assembly and inversion (setup) */
+#define PB_T_ENERGY 10    /* solvation energy */
+#define PB_T_RHS 11       /* right-hand side */
+int pb_set_timing(pb_ctx* ctx, int enable);
+int pb_get_timing(pb_ctx* ctx, double* out);
+
+/* Number of this library's kernel launches queued on ctx since it was created. */
+int pb_get_launch_count(pb_ctx* ctx, long long* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PB_H */

@@ -1,0 +1,440 @@
+// Far field of the FMM matrix-vector product (Section 2.4, steps 2-6): leaf moments,
+// upward MtM pass (eqMtM), interaction phase MtL (eqcoeff) with kernel derivatives by
+// recurrence, downward LtL pass and LtP evaluation (LtP).
+//
+// The four kernels regroup into two expansions. With densities f0 = dphi m - phi m_nu (for
+// G0) and fk = -dphi m + eps phi m_nu (for Gk), where m^b(psi_i) = A_i (c_i - x_c)^b and
+// m_nu^b(psi_i) = A_i n_i . grad (y - x_c)^b at y = c_i (one-point rule, eqmoment), the
+// far-field rows are
+//   y1_i -= A_i sum_a (lam0 + lamk)^a (c_i - x_c)^a
+//   y2_i -= A_i sum_a (lam0 + lamk / eps)^a n_i . grad (x - x_c)^a
+// since K1 + K2 pair G0 and Gk single and double layers, and K3 + K4 are their normal
+// derivatives at the target (Eq_K1/Eq_K2).
+//
+// Kernel derivatives (MtL). With phi = exp(-kappa r)/(4 pi r), psi = exp(-kappa r)/(4 pi)
+// and Taylor coefficients F_k = D^k phi(d)/k!, Psi_k = D^k psi(d)/k!, the identities
+// r^2 grad phi = -(phi + kappa psi) x and grad psi = -kappa phi x, applied to the Euler
+// operator h . grad of the expansion in h, give for n = |k| >= 1
+//   |d|^2 n F_k = -(2n - 1) sum_i d_i F_{k-e_i} - (n - 1) sum_i F_{k-2e_i}
+//                 - kappa sum_i d_i Psi_{k-e_i} - kappa sum_i Psi_{k-2e_i}
+//   n Psi_k     = -kappa (sum_i d_i F_{k-e_i} + sum_i F_{k-2e_i})
+// (terms with a negative index vanish). kappa = 0 gives the Coulomb recurrence.
+// The MtL sum is evaluated as  a! lam^a = sum_b D^{a+b} G(d) * [(-1)^|b| m^b / b!].
+#include <math.h>
+
+#include "pb_internal.cuh"
+
+#define FAR_T 128
+#define NT_MAX 455  // nterms(12)
+
+__constant__ int c_mi[NT_MAX];          // multi-index exponents a | b << 8 | c << 16
+__constant__ double c_fact[25];         // n!
+__constant__ double c_binom[13][13];    // C(n, k)
+
+__device__ __forceinline__ void mi_unpack(int v, int& a, int& b, int& c)
+{
+    a = v & 0xff;
+    b = (v >> 8) & 0xff;
+    c = v >> 16;
+}
+
+// ---------- step 2: leaf moments ----------
+template <class R>
+__global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restrict__ begin,
+                                               const double* __restrict__ xc, const double4_32a* __restrict__ ep,
+                                               const double4_32a* __restrict__ en, const double* __restrict__ xs,
+                                               double eps, R* __restrict__ sig0, R* __restrict__ sigk)
+{
+    __shared__ R pw[FAR_T][3][PB_PMAX + 1];
+    __shared__ R sn[FAR_T][3];
+    __shared__ R sw[FAR_T][2];
+    const int c = blockIdx.x;
+    const int T = pb_nterms(p);
+    const int b = begin[c], e = begin[c + 1];
+    const double cx = xc[3 * c], cy = xc[3 * c + 1], cz = xc[3 * c + 2];
+    R acc0[4] = {0, 0, 0, 0}, acck[4] = {0, 0, 0, 0};  // up to 4 multi-indices per thread
+    for (int s0 = b; s0 < e; s0 += FAR_T) {
+        int ns = min(FAR_T, e - s0);
+        __syncthreads();
+        if (threadIdx.x < ns) {
+            int j = s0 + threadIdx.x;
+            double4_32a P = ep[j], Nn = en[j];
+            R d[3] = {(R)(P.x - cx), (R)(P.y - cy), (R)(P.z - cz)};
+            for (int a = 0; a < 3; ++a) {
+                R v = 1;
+                for (int k = 0; k <= p; ++k) {
+                    pw[threadIdx.x][a][k] = v;
+                    v *= d[a];
+                }
+            }
+            sn[threadIdx.x][0] = (R)Nn.x;
+            sn[threadIdx.x][1] = (R)Nn.y;
+            sn[threadIdx.x][2] = (R)Nn.z;
+            sw[threadIdx.x][0] = (R)(P.w * xs[j]);       // A phi
+            sw[threadIdx.x][1] = (R)(P.w * xs[nt + j]);  // A dphi
+        }
+        __syncthreads();
+        for (int r = 0; r < 4; ++r) {
+            int al = threadIdx.x + r * FAR_T;
+            if (al >= T) break;
+            int a, bb, cc;
+            mi_unpack(c_mi[al], a, bb, cc);
+            R s0v = 0, skv = 0;
+            for (int q = 0; q < ns; ++q) {
+                R mx = pw[q][0][a], my = pw[q][1][bb], mz = pw[q][2][cc];
+                R mono = mx * my * mz;
+                R dm = 0;
+                if (a) dm += sn[q][0] * (R)a * pw[q][0][a - 1] * my * mz;
+                if (bb) dm += sn[q][1] * (R)bb * mx * pw[q][1][bb - 1] * mz;
+                if (cc) dm += sn[q][2] * (R)cc * mx * my * pw[q][2][cc - 1];
+                R wphi = sw[q][0], wdphi = sw[q][1];
+                s0v += wdphi * mono - wphi * dm;
+                skv += -wdphi * mono + (R)eps * wphi * dm;
+            }
+            acc0[r] += s0v;
+            acck[r] += skv;
+        }
+    }
+    for (int r = 0; r < 4; ++r) {
+        int al = threadIdx.x + r * FAR_T;
+        if (al >= T) break;
+        sig0[(size_t)c * T + al] = acc0[r];
+        sigk[(size_t)c * T + al] = acck[r];
+    }
+}
+
+// ---------- step 3: MtM, children (order pc) into parent (order pp) ----------
+template <class R>
+__global__ void __launch_bounds__(FAR_T) k_m2m(int pp, int pc, const int* __restrict__ cbeg,
+                                               const double* __restrict__ xp, const double* __restrict__ xch,
+                                               const R* __restrict__ c0, const R* __restrict__ ck,
+                                               R* __restrict__ s0, R* __restrict__ sk)
+{
+    __shared__ R tp[3][PB_PMAX + 1];
+    const int c = blockIdx.x;
+    const int Tp = pb_nterms(pp), Tc = pb_nterms(pc);
+    R a0[4] = {0, 0, 0, 0}, ak[4] = {0, 0, 0, 0};
+    for (int ch = cbeg[c]; ch < cbeg[c + 1]; ++ch) {
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            R t = (R)(xch[3 * ch + threadIdx.x] - xp[3 * c + threadIdx.x]);
+            R v = 1;
+            for (int k = 0; k <= pp; ++k) {
+                tp[threadIdx.x][k] = v;
+                v *= t;
+            }
+        }
+        __syncthreads();
+        const R* m0 = c0 + (size_t)ch * Tc;
+        const R* mk = ck + (size_t)ch * Tc;
+        for (int r = 0; r < 4; ++r) {
+            int al = threadIdx.x + r * FAR_T;
+            if (al >= Tp) break;
+            int a1, a2, a3;
+            mi_unpack(c_mi[al], a1, a2, a3);
+            R v0 = 0, vk = 0;
+            for (int b1 = 0; b1 <= a1; ++b1)
+                for (int b2 = 0; b2 <= a2; ++b2)
+                    for (int b3 = 0; b3 <= a3; ++b3) {
+                        if (b1 + b2 + b3 > pc) continue;
+                        R w = (R)(c_binom[a1][b1] * c_binom[a2][b2] * c_binom[a3][b3]) * tp[0][a1 - b1] *
+                              tp[1][a2 - b2] * tp[2][a3 - b3];
+                        int pos = pb_midx(b1, b2, b3);
+                        v0 += w * m0[pos];
+                        vk += w * mk[pos];
+                    }
+            a0[r] += v0;
+            ak[r] += vk;
+        }
+    }
+    for (int r = 0; r < 4; ++r) {
+        int al = threadIdx.x + r * FAR_T;
+        if (al >= Tp) break;
+        s0[(size_t)c * Tp + al] = a0[r];
+        sk[(size_t)c * Tp + al] = ak[r];
+    }
+}
+
+// ---------- step 4: MtL over the interaction lists of one level ----------
+template <class R>
+__global__ void __launch_bounds__(FAR_T) k_m2l(int p, double kappa, const int* __restrict__ ioff,
+                                               const int* __restrict__ iidx, const double* __restrict__ xc,
+                                               const R* __restrict__ s0, const R* __restrict__ sk,
+                                               R* __restrict__ l0, R* __restrict__ lk)
+{
+    __shared__ R F0[NT_MAX], Fk[NT_MAX], Pk[NT_MAX];
+    __shared__ R M0[NT_MAX], Mk[NT_MAX];
+    const int c = blockIdx.x;
+    const int T = pb_nterms(p);
+    R L0[4] = {0, 0, 0, 0}, Lk[4] = {0, 0, 0, 0};
+    const double i4pi = 0.07957747154594767;
+    for (int t = ioff[c]; t < ioff[c + 1]; ++t) {
+        const int c2 = iidx[t];
+        const R dx = (R)(xc[3 * c] - xc[3 * c2]), dy = (R)(xc[3 * c + 1] - xc[3 * c2 + 1]),
+                dz = (R)(xc[3 * c + 2] - xc[3 * c2 + 2]);
+        const R d2 = dx * dx + dy * dy + dz * dz;
+        const R kap = (R)kappa;
+        __syncthreads();
+        // source moments, scaled by (-1)^|b| / b!
+        for (int b = threadIdx.x; b < T; b += FAR_T) {
+            int b1, b2, b3;
+            mi_unpack(c_mi[b], b1, b2, b3);
+            R sc = (R)(((b1 + b2 + b3) & 1 ? -1.0 : 1.0) / (c_fact[b1] * c_fact[b2] * c_fact[b3]));
+            M0[b] = s0[(size_t)c2 * T + b] * sc;
+            Mk[b] = sk[(size_t)c2 * T + b] * sc;
+        }
+        if (threadIdx.x == 0) {
+            R r = sqrt(d2);
+            R ex = exp(-kap * r);
+            F0[0] = (R)i4pi / r;
+            Fk[0] = (R)i4pi * ex / r;
+            Pk[0] = (R)i4pi * ex;
+        }
+        __syncthreads();
+        // Taylor coefficients degree by degree
+        for (int n = 1; n <= p; ++n) {
+            const int lo = pb_nterms(n - 1), hi = pb_nterms(n);
+            for (int k = lo + threadIdx.x; k < hi; k += FAR_T) {
+                int k1, k2, k3;
+                mi_unpack(c_mi[k], k1, k2, k3);
+                R d[3] = {dx, dy, dz};
+                int kk[3] = {k1, k2, k3};
+                R a0 = 0, a1 = 0, ak0 = 0, ak1 = 0, ap0 = 0, ap1 = 0;
+                for (int i = 0; i < 3; ++i) {
+                    if (kk[i] >= 1) {
+                        int q = pb_midx(k1 - (i == 0), k2 - (i == 1), k3 - (i == 2));
+                        a0 += d[i] * F0[q];
+                        ak0 += d[i] * Fk[q];
+                        ap0 += d[i] * Pk[q];
+                    }
+                    if (kk[i] >= 2) {
+                        int q = pb_midx(k1 - 2 * (i == 0), k2 - 2 * (i == 1), k3 - 2 * (i == 2));
+                        a1 += F0[q];
+                        ak1 += Fk[q];
+                        ap1 += Pk[q];
+                    }
+                }
+                R nn = (R)n;
+                F0[k] = (-(R)(2 * n - 1) * a0 - (nn - 1) * a1) / (d2 * nn);
+                Fk[k] = (-(R)(2 * n - 1) * ak0 - (nn - 1) * ak1 - kap * ap0 - kap * ap1) / (d2 * nn);
+                Pk[k] = -kap * (ak0 + ak1) / nn;
+            }
+            __syncthreads();
+        }
+        // raw derivatives D^k = k! F_k
+        for (int k = threadIdx.x; k < T; k += FAR_T) {
+            int k1, k2, k3;
+            mi_unpack(c_mi[k], k1, k2, k3);
+            R f = (R)(c_fact[k1] * c_fact[k2] * c_fact[k3]);
+            F0[k] *= f;
+            Fk[k] *= f;
+        }
+        __syncthreads();
+        for (int r = 0; r < 4; ++r) {
+            int al = threadIdx.x + r * FAR_T;
+            if (al >= T) break;
+            int a1, a2, a3;
+            mi_unpack(c_mi[al], a1, a2, a3);
+            int nb = pb_nterms(p - (a1 + a2 + a3));
+            R v0 = 0, vk = 0;
+            for (int b = 0; b < nb; ++b) {
+                int b1, b2, b3;
+                mi_unpack(c_mi[b], b1, b2, b3);
+                int g = pb_midx(a1 + b1, a2 + b2, a3 + b3);
+                v0 += F0[g] * M0[b];
+                vk += Fk[g] * Mk[b];
+            }
+            L0[r] += v0;
+            Lk[r] += vk;
+        }
+    }
+    for (int r = 0; r < 4; ++r) {
+        int al = threadIdx.x + r * FAR_T;
+        if (al >= T) break;
+        int a1, a2, a3;
+        mi_unpack(c_mi[al], a1, a2, a3);
+        R f = (R)(1.0 / (c_fact[a1] * c_fact[a2] * c_fact[a3]));
+        l0[(size_t)c * T + al] = L0[r] * f;
+        lk[(size_t)c * T + al] = Lk[r] * f;
+    }
+}
+
+// ---------- step 5: LtL, parent (order pp) into child (order pc) ----------
+template <class R>
+__global__ void __launch_bounds__(FAR_T) k_l2l(int pp, int pc, const int* __restrict__ parent,
+                                               const double* __restrict__ xp, const double* __restrict__ xch,
+                                               const R* __restrict__ lp0, const R* __restrict__ lpk,
+                                               R* __restrict__ lc0, R* __restrict__ lck)
+{
+    __shared__ R tp[3][PB_PMAX + 1];
+    const int c = blockIdx.x;
+    const int P = parent[c];
+    const int Tp = pb_nterms(pp), Tc = pb_nterms(pc);
+    if (threadIdx.x < 3) {
+        R t = (R)(xch[3 * c + threadIdx.x] - xp[3 * P + threadIdx.x]);
+        R v = 1;
+        for (int k = 0; k <= pp; ++k) {
+            tp[threadIdx.x][k] = v;
+            v *= t;
+        }
+    }
+    __syncthreads();
+    const R* m0 = lp0 + (size_t)P * Tp;
+    const R* mk = lpk + (size_t)P * Tp;
+    for (int be = threadIdx.x; be < Tc; be += FAR_T) {
+        int b1, b2, b3;
+        mi_unpack(c_mi[be], b1, b2, b3);
+        int ng = pb_nterms(pp - (b1 + b2 + b3));
+        R v0 = 0, vk = 0;
+        for (int g = 0; g < ng; ++g) {
+            int g1, g2, g3;
+            mi_unpack(c_mi[g], g1, g2, g3);
+            R w = (R)(c_binom[b1 + g1][b1] * c_binom[b2 + g2][b2] * c_binom[b3 + g3][b3]) * tp[0][g1] * tp[1][g2] *
+                  tp[2][g3];
+            int pos = pb_midx(b1 + g1, b2 + g2, b3 + g3);
+            v0 += w * m0[pos];
+            vk += w * mk[pos];
+        }
+        lc0[(size_t)c * Tc + be] += v0;
+        lck[(size_t)c * Tc + be] += vk;
+    }
+}
+
+// ---------- step 6: LtP ----------
+template <class R>
+__global__ void __launch_bounds__(FAR_T) k_l2p(int nt, int p, double eps, const int* __restrict__ begin,
+                                               const double* __restrict__ xc, const double4_32a* __restrict__ ep,
+                                               const double4_32a* __restrict__ en, const R* __restrict__ l0,
+                                               const R* __restrict__ lk, double* __restrict__ ys)
+{
+    __shared__ R A1[NT_MAX], A2[NT_MAX];
+    __shared__ R pw[FAR_T][3][PB_PMAX + 1];
+    const int c = blockIdx.x;
+    const int T = pb_nterms(p);
+    for (int a = threadIdx.x; a < T; a += FAR_T) {
+        R u = l0[(size_t)c * T + a], v = lk[(size_t)c * T + a];
+        A1[a] = u + v;
+        A2[a] = u + v * (R)(1.0 / eps);
+    }
+    const double cx = xc[3 * c], cy = xc[3 * c + 1], cz = xc[3 * c + 2];
+    __syncthreads();
+    for (int k = begin[c] + threadIdx.x; k < begin[c + 1]; k += FAR_T) {
+        double4_32a P = ep[k], Nn = en[k];
+        R d[3] = {(R)(P.x - cx), (R)(P.y - cy), (R)(P.z - cz)};
+        R nx = (R)Nn.x, ny = (R)Nn.y, nz = (R)Nn.z;
+        for (int a = 0; a < 3; ++a) {
+            R v = 1;
+            for (int q = 0; q <= p; ++q) {
+                pw[threadIdx.x][a][q] = v;
+                v *= d[a];
+            }
+        }
+        R s1 = 0, s2 = 0;
+        for (int al = 0; al < T; ++al) {
+            int a, b, cc;
+            mi_unpack(c_mi[al], a, b, cc);
+            R mx = pw[threadIdx.x][0][a], my = pw[threadIdx.x][1][b], mz = pw[threadIdx.x][2][cc];
+            R dm = 0;
+            if (a) dm += nx * (R)a * pw[threadIdx.x][0][a - 1] * my * mz;
+            if (b) dm += ny * (R)b * mx * pw[threadIdx.x][1][b - 1] * mz;
+            if (cc) dm += nz * (R)cc * mx * my * pw[threadIdx.x][2][cc - 1];
+            s1 += A1[al] * mx * my * mz;
+            s2 += A2[al] * dm;
+        }
+        ys[k] -= P.w * (double)s1;
+        ys[nt + k] -= P.w * (double)s2;
+    }
+}
+
+static bool g_tables = false;
+
+static int upload_tables(pb_ctx* c)
+{
+    int mi[NT_MAX];
+    for (int n = 0, pos = 0; n <= PB_PMAX; ++n)
+        for (int a = n; a >= 0; --a)
+            for (int b = n - a; b >= 0; --b) mi[pos++] = a | (b << 8) | ((n - a - b) << 16);
+    double f[25];
+    f[0] = 1;
+    for (int i = 1; i < 25; ++i) f[i] = f[i - 1] * i;
+    double bn[13][13] = {};
+    for (int n = 0; n <= 12; ++n) {
+        bn[n][0] = 1;
+        for (int k = 1; k <= n; ++k) bn[n][k] = bn[n - 1][k - 1] + (k <= n - 1 ? bn[n - 1][k] : 0);
+    }
+    PB_CUDA(c, cudaMemcpyToSymbol(c_mi, mi, sizeof(mi)));
+    PB_CUDA(c, cudaMemcpyToSymbol(c_fact, f, sizeof(f)));
+    PB_CUDA(c, cudaMemcpyToSymbol(c_binom, bn, sizeof(bn)));
+    return PB_OK;
+}
+
+int pb_far_setup(pb_ctx* c)
+{
+    int rc = upload_tables(c);
+    if (rc) return rc;
+    g_tables = true;
+    size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
+    for (int l = 1; l <= c->L; ++l) {
+        PbLevel& lv = c->lev[l];
+        size_t n = (size_t)lv.ncl * pb_nterms(lv.p);
+        lv.sig0 = pb_alloc(c, rs * n);
+        lv.sigk = pb_alloc(c, rs * n);
+        lv.lam0 = pb_alloc(c, rs * n);
+        lv.lamk = pb_alloc(c, rs * n);
+        if (!lv.sig0 || !lv.sigk || !lv.lam0 || !lv.lamk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");
+    }
+    return PB_OK;
+}
+
+template <class R>
+static int far_apply(pb_ctx* c, const double* xs, double* ys)
+{
+    const int L = c->L;
+    if (L < 1) return PB_OK;
+    double eps = c->prm.eps_out / c->prm.eps_in;
+    pb_tic(c, PB_T_UP);
+    {
+        PbLevel& lv = c->lev[L];
+        k_p2m<R><<<lv.ncl, FAR_T, 0, c->st>>>(c->nt, lv.p, lv.begin, lv.xc, c->e64p, c->e64n, xs, eps, (R*)lv.sig0,
+                                              (R*)lv.sigk);
+        PB_LAUNCH(c);
+    }
+    for (int l = L - 1; l >= 1; --l) {
+        PbLevel& lv = c->lev[l];
+        PbLevel& ch = c->lev[l + 1];
+        k_m2m<R><<<lv.ncl, FAR_T, 0, c->st>>>(lv.p, ch.p, lv.cbeg, lv.xc, ch.xc, (R*)ch.sig0, (R*)ch.sigk,
+                                              (R*)lv.sig0, (R*)lv.sigk);
+        PB_LAUNCH(c);
+    }
+    pb_toc(c, PB_T_UP);
+    pb_tic(c, PB_T_M2L);
+    for (int l = 1; l <= L; ++l) {
+        PbLevel& lv = c->lev[l];
+        k_m2l<R><<<lv.ncl, FAR_T, 0, c->st>>>(lv.p, c->prm.kappa, lv.int_off, lv.int_idx, lv.xc, (R*)lv.sig0,
+                                              (R*)lv.sigk, (R*)lv.lam0, (R*)lv.lamk);
+        PB_LAUNCH(c);
+    }
+    pb_toc(c, PB_T_M2L);
+    pb_tic(c, PB_T_DOWN);
+    for (int l = 1; l < L; ++l) {
+        PbLevel& lv = c->lev[l];
+        PbLevel& ch = c->lev[l + 1];
+        k_l2l<R><<<ch.ncl, FAR_T, 0, c->st>>>(lv.p, ch.p, ch.parent, lv.xc, ch.xc, (R*)lv.lam0, (R*)lv.lamk,
+                                              (R*)ch.lam0, (R*)ch.lamk);
+        PB_LAUNCH(c);
+    }
+    {
+        PbLevel& lv = c->lev[L];
+        k_l2p<R><<<lv.ncl, FAR_T, 0, c->st>>>(c->nt, lv.p, eps, lv.begin, lv.xc, c->e64p, c->e64n, (R*)lv.lam0,
+                                              (R*)lv.lamk, ys);
+        PB_LAUNCH(c);
+    }
+    pb_toc(c, PB_T_DOWN);
+    return PB_OK;
+}
+
+int pb_far_apply(pb_ctx* c, const double* xs, double* ys)
+{
+    if (c->prm.precision == PB_MIXED) return far_apply<float>(c, xs, ys);
+    return far_apply<double>(c, xs, ys);
+}

@@ -1,0 +1,80 @@
+// Point evaluation of the four kernels K1..K4 of Eq_K1/Eq_K2 (Section 2.2).
+//
+// With d = x - y, r = |d|, t = kappa r and E = exp(-t) - 1:
+//   K1 = (G0 - Gk)                   = -E / (4 pi r)
+//   K2 = eps dGk/dn_y - dG0/dn_y     = (n_y.d) / (4 pi r^3) [eps (1 - c1) - 1]
+//   K3 = dG0/dn_x - dGk/dn_x / eps   = -(n_x.d) / (4 pi r^3) [1 - (1 - c1) / eps]
+//   K4 = d2(Gk - G0)/dn_x dn_y       = [c3 (n_x.d)(n_y.d) / r^2 - c1 (n_x.n_y)] / (4 pi r^3)
+// where c1 = 1 - e^-t (1 + t) and c3 = 3 - e^-t (3 + 3t + t^2) are the screened-minus-
+// Coulomb radial factors. Both vanish like t^2/2 as t -> 0; writing them through
+// g = E + t = t^2/2 - t^3/6 + ... (a Taylor series for small t, exact arithmetic otherwise)
+// keeps the relative error of the differences bounded instead of growing like 1/t^2.
+#pragma once
+
+#include <cuda_runtime.h>
+
+template <class R>
+struct PbKer;
+
+template <>
+struct PbKer<double> {
+    static __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+};
+template <>
+struct PbKer<float> {
+    static __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+};
+
+// g(t) = exp(-t) - 1 + t, and E = exp(-t) - 1
+template <class R>
+__device__ __forceinline__ void pb_screen(R t, R& E, R& g)
+{
+    E = PbKer<R>::expm1_(-t);
+    if (t < R(0.125)) {
+        // t^2/2 - t^3/6 + t^4/24 - ... (terms to t^13; below 1e-17 relative at t = 0.125)
+        R s = R(-1.0 / 6227020800.0);               // -1/13!
+        s = s * t + R(1.0 / 479001600.0);           // 1/12!
+        s = s * t + R(-1.0 / 39916800.0);
+        s = s * t + R(1.0 / 3628800.0);
+        s = s * t + R(-1.0 / 362880.0);
+        s = s * t + R(1.0 / 40320.0);
+        s = s * t + R(-1.0 / 5040.0);
+        s = s * t + R(1.0 / 720.0);
+        s = s * t + R(-1.0 / 120.0);
+        s = s * t + R(1.0 / 24.0);
+        s = s * t + R(-1.0 / 6.0);
+        s = s * t + R(0.5);
+        g = s * t * t;
+    } else {
+        g = E + t;
+    }
+}
+
+// K[0..3] = K1..K4 for d = x - y, target normal n_x, source normal n_y.
+template <class R>
+__device__ __forceinline__ void pb_kernels(R dx, R dy, R dz, R nxx, R nxy, R nxz, R nyx, R nyy, R nyz,
+                                           R eps, R inv_eps, R kappa, R* K)
+{
+    const R i4pi = R(0.07957747154594767);  // 1 / (4 pi)
+    R r2 = dx * dx + dy * dy + dz * dz;
+    R rinv = PbKer<R>::rsqrt_(r2);
+    R r = r2 * rinv;
+    R t = kappa * r;
+    R E, g;
+    pb_screen<R>(t, E, g);
+    R tE = t * E;
+    R c1 = -g - tE;
+    R c3 = R(-3) * g - t * t - tE * (R(3) + t);
+    R ri = rinv * i4pi;
+    R ri3 = ri * rinv * rinv;
+    R nxd = nxx * dx + nxy * dy + nxz * dz;
+    R nyd = nyx * dx + nyy * dy + nyz * dz;
+    R nxny = nxx * nyx + nxy * nyy + nxz * nyz;
+    R e1 = R(1) - c1;  // e^-t (1 + t)
+    K[0] = -E * ri;
+    K[1] = nyd * ri3 * (eps * e1 - R(1));
+    K[2] = -nxd * ri3 * (R(1) - e1 * inv_eps);
+    K[3] = ri3 * (c3 * nxd * nyd * rinv * rinv - c1 * nxny);
+}

@@ -1,0 +1,432 @@
+// Right-hand side (source_terms), solvation energy (eqsolengdis) and restarted GMRES with
+// right preconditioning (Section 2.3 last paragraph; Section 2.6). All vectors are in tree
+// order. Arnoldi orthogonalisation (classical Gram-Schmidt applied twice), Givens rotations,
+// the triangular solve and the update run in FP64 kernels; the host only reads one residual
+// estimate per iteration to decide whether to continue.
+#include <math.h>
+
+#include <vector>
+
+#include "kernels.cuh"
+#include "pb_internal.cuh"
+
+#define KB 256
+
+// ---------- right-hand side: b1 = A S1(c), b2 = A S2(c) ----------
+__global__ void k_rhs(int nt, int nc, const double4_32a* __restrict__ ep, const double4_32a* __restrict__ en,
+                      const double* __restrict__ qpos, const double* __restrict__ q, double eps1,
+                      double* __restrict__ b)
+{
+    __shared__ double sq[KB][4];
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double4_32a p = make_double4_32a(0, 0, 0, 0), n = p;
+    if (k < nt) {
+        p = ep[k];
+        n = en[k];
+    }
+    double s1 = 0.0, s2 = 0.0;
+    const double i4pi = 0.07957747154594767;
+    for (int t0 = 0; t0 < nc; t0 += KB) {
+        __syncthreads();
+        if (t0 + threadIdx.x < nc) {
+            int t = t0 + threadIdx.x;
+            sq[threadIdx.x][0] = qpos[3 * t];
+            sq[threadIdx.x][1] = qpos[3 * t + 1];
+            sq[threadIdx.x][2] = qpos[3 * t + 2];
+            sq[threadIdx.x][3] = q[t];
+        }
+        __syncthreads();
+        int m = min(KB, nc - t0);
+        if (k < nt)
+            for (int t = 0; t < m; ++t) {
+                double dx = p.x - sq[t][0], dy = p.y - sq[t][1], dz = p.z - sq[t][2];
+                double r2 = dx * dx + dy * dy + dz * dz;
+                double ri = rsqrt(r2);
+                double nd = n.x * dx + n.y * dy + n.z * dz;
+                s1 += sq[t][3] * ri;
+                s2 -= sq[t][3] * nd * ri * ri * ri;  // dG0/dn_x = -(n.d)/(4 pi r^3)
+            }
+    }
+    if (k < nt) {
+        b[k] = p.w * s1 * i4pi / eps1;
+        b[nt + k] = p.w * s2 * i4pi / eps1;
+    }
+}
+
+int pb_rhs_sorted(pb_ctx* c, double* bs)
+{
+    int nt = c->nt;
+    pb_tic(c, PB_T_RHS);
+    k_rhs<<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q, c->prm.eps_in, bs);
+    PB_LAUNCH(c);
+    pb_toc(c, PB_T_RHS);
+    return PB_OK;
+}
+
+// ---------- energy: 1/2 sum_n q_n sum_i A_i [K1(x_n, c_i) dphi_i + K2(x_n, c_i) phi_i] ----------
+template <class R>
+__global__ void k_energy(int nt, int nc, const double4_32a* __restrict__ ep, const double4_32a* __restrict__ en,
+                         const double* __restrict__ qpos, const double* __restrict__ q, double eps, double kappa,
+                         const double* __restrict__ xs, double* __restrict__ part)
+{
+    __shared__ double sq[KB][4];
+    __shared__ double red[KB];
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double4_32a p = make_double4_32a(0, 0, 0, 0), n = p;
+    double ph = 0, dph = 0;
+    if (k < nt) {
+        p = ep[k];
+        n = en[k];
+        ph = xs[k];
+        dph = xs[nt + k];
+    }
+    double acc = 0.0;
+    const R e = (R)eps, ie = (R)(1.0 / eps), kp = (R)kappa;
+    for (int t0 = 0; t0 < nc; t0 += KB) {
+        __syncthreads();
+        if (t0 + threadIdx.x < nc) {
+            int t = t0 + threadIdx.x;
+            sq[threadIdx.x][0] = qpos[3 * t];
+            sq[threadIdx.x][1] = qpos[3 * t + 1];
+            sq[threadIdx.x][2] = qpos[3 * t + 2];
+            sq[threadIdx.x][3] = q[t];
+        }
+        __syncthreads();
+        int m = min(KB, nc - t0);
+        if (k < nt) {
+            R s = 0;
+            for (int t = 0; t < m; ++t) {
+                R K[4];
+                pb_kernels<R>((R)(sq[t][0] - p.x), (R)(sq[t][1] - p.y), (R)(sq[t][2] - p.z), R(0), R(0), R(0),
+                              (R)n.x, (R)n.y, (R)n.z, e, ie, kp, K);
+                s += (R)sq[t][3] * (K[0] * (R)dph + K[1] * (R)ph);
+            }
+            acc += (double)s;
+        }
+    }
+    red[threadIdx.x] = acc * p.w;
+    __syncthreads();
+    for (int h = KB / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum(int n, const double* __restrict__ part, double* __restrict__ out, double scale)
+{
+    __shared__ double red[KB];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += KB) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = KB / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] * scale;
+}
+
+int pb_energy_sorted(pb_ctx* c, const double* xs, double* E)
+{
+    int nt = c->nt, nb = (nt + KB - 1) / KB;
+    if (!c->scratch) {
+        c->scratch = (double*)pb_alloc(c, sizeof(double) * ((size_t)nb + 8));
+        if (!c->scratch) return pb_fail(c, PB_ERR_NOMEM, "energy: out of memory");
+    }
+    double eps = c->prm.eps_out / c->prm.eps_in;
+    pb_tic(c, PB_T_ENERGY);
+    if (c->prm.precision == PB_MIXED)
+        k_energy<float><<<nb, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q, eps, c->prm.kappa, xs,
+                                              c->scratch);
+    else
+        k_energy<double><<<nb, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q, eps, c->prm.kappa, xs,
+                                               c->scratch);
+    PB_LAUNCH(c);
+    k_sum<<<1, KB, 0, c->st>>>(nb, c->scratch, c->scratch + nb, 0.5 * 4.0 * PB_PI * 332.0716);
+    PB_LAUNCH(c);
+    pb_toc(c, PB_T_ENERGY);
+    PB_CUDA(c, cudaMemcpyAsync(c->hscal, c->scratch + nb, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    *E = c->hscal[0];
+    return PB_OK;
+}
+
+// ---------- GMRES building blocks ----------
+#define DOT_BLOCKS 304  // 2 x 152 SMs
+
+// part[col * DOT_BLOCKS + blk] = partial of <V[col], w> (or of <w, w> when V == nullptr)
+__global__ void k_multidot(long long n, const double* __restrict__ V, const double* __restrict__ w,
+                           double* __restrict__ part)
+{
+    __shared__ double red[KB];
+    const int col = blockIdx.y;
+    const double* v = V ? V + (size_t)col * n : w;
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) s += v[i] * w[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = KB / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(size_t)col * gridDim.x + blockIdx.x] = red[0];
+}
+
+// out[col] (+)= sum of partials of column col
+__global__ void k_finish(int nparts, const double* __restrict__ part, double* __restrict__ out, int accumulate)
+{
+    __shared__ double red[KB];
+    const int col = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += KB) s += part[(size_t)col * nparts + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = KB / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[col] = accumulate ? out[col] + red[0] : red[0];
+}
+
+// w -= V[:, 0..ncol) h
+__global__ void k_orth_update(long long n, int ncol, const double* __restrict__ V, const double* __restrict__ h,
+                              double* __restrict__ w)
+{
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        double s = 0.0;
+        for (int c = 0; c < ncol; ++c) s += V[(size_t)c * n + i] * h[c];
+        w[i] -= s;
+    }
+}
+
+// dst = src * (1 / *nrm) (nrm read from device)
+__global__ void k_scale(long long n, const double* __restrict__ src, const double* __restrict__ nrm, double* __restrict__ dst)
+{
+    double f = 1.0 / sqrt(*nrm);
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) dst[i] = src[i] * f;
+}
+
+// r = b - r  (r holds A x on input)
+__global__ void k_residual(long long n, const double* __restrict__ b, double* __restrict__ r)
+{
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) r[i] = b[i] - r[i];
+}
+
+// x += u
+__global__ void k_axpy1(long long n, const double* __restrict__ u, double* __restrict__ x)
+{
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) x[i] += u[i];
+}
+
+// u = V[:, 0..k) y
+__global__ void k_combine(long long n, int k, const double* __restrict__ V, const double* __restrict__ y,
+                          double* __restrict__ u)
+{
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        double s = 0.0;
+        for (int c = 0; c < k; ++c) s += V[(size_t)c * n + i] * y[c];
+        u[i] = s;
+    }
+}
+
+// Small dense state of GMRES(m) on the device: H (column-major (m+1) x m), Givens cs/sn, g.
+struct GmState {
+    double* H;
+    double* cs;
+    double* sn;
+    double* g;
+    double* y;
+    double* hcol;  // h[0..j] and ||w||^2 of the current step
+    double* res;   // |g_{j+1}|
+};
+
+// start of a cycle: g = (beta, 0, ...), beta = sqrt(hcol[0])
+__global__ void k_gm_start(int m, GmState s)
+{
+    for (int i = 0; i <= m; ++i) s.g[i] = 0.0;
+    s.g[0] = sqrt(s.hcol[0]);
+    s.res[0] = s.g[0];
+}
+
+// step j: H[:, j] = (hcol[0..j], sqrt(hcol[j+1])); apply rotations; new rotation; residual
+__global__ void k_gm_givens(int m, int j, GmState s)
+{
+    double* Hj = s.H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) Hj[i] = s.hcol[i];
+    Hj[j + 1] = sqrt(s.hcol[j + 1]);
+    for (int i = 0; i < j; ++i) {
+        double a = Hj[i], b = Hj[i + 1];
+        Hj[i] = s.cs[i] * a + s.sn[i] * b;
+        Hj[i + 1] = -s.sn[i] * a + s.cs[i] * b;
+    }
+    double a = Hj[j], b = Hj[j + 1];
+    double r = hypot(a, b);
+    double c = r > 0 ? a / r : 1.0, sn = r > 0 ? b / r : 0.0;
+    s.cs[j] = c;
+    s.sn[j] = sn;
+    Hj[j] = r;
+    Hj[j + 1] = 0.0;
+    s.g[j + 1] = -sn * s.g[j];
+    s.g[j] = c * s.g[j];
+    s.res[0] = fabs(s.g[j + 1]);
+}
+
+// back substitution: H[0..k, 0..k) y = g
+__global__ void k_gm_solve(int m, int k, GmState s)
+{
+    for (int i = k - 1; i >= 0; --i) {
+        double v = s.g[i];
+        for (int q = i + 1; q < k; ++q) v -= s.H[(size_t)q * (m + 1) + i] * s.y[q];
+        double d = s.H[(size_t)i * (m + 1) + i];
+        s.y[i] = d != 0.0 ? v / d : 0.0;
+    }
+}
+
+static int grid_for(long long n) { return (int)std::min<long long>((n + KB - 1) / KB, 4 * 152 * 4); }
+
+int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max_iter, int restart,
+                    pb_solve_info* info)
+{
+    const long long n = 2LL * c->nt;
+    const int m = restart;
+    const int G = grid_for(n);
+    int rc;
+    // workspace, kept with the mesh and regrown when the restart length grows
+    if (m > c->gm_m) {
+        c->gmV = (double*)pb_alloc(c, sizeof(double) * n * (m + 1));
+        c->gmw = (double*)pb_alloc(c, sizeof(double) * n);
+        c->gmz = (double*)pb_alloc(c, sizeof(double) * n);
+        c->gmpart = (double*)pb_alloc(c, sizeof(double) * DOT_BLOCKS * (m + 2));
+        c->gmsmall = (double*)pb_alloc(c, sizeof(double) * ((m + 1) * m + 6 * (m + 2)));
+        if (!c->gmV || !c->gmw || !c->gmz || !c->gmpart || !c->gmsmall) {
+            c->gm_m = 0;
+            return pb_fail(c, PB_ERR_NOMEM, "gmres: out of memory");
+        }
+        c->gm_m = m;
+    }
+    double *V = c->gmV, *w = c->gmw, *z = c->gmz, *part = c->gmpart, *small = c->gmsmall;
+    GmState s;
+    s.H = small;
+    s.cs = s.H + (size_t)(m + 1) * m;
+    s.sn = s.cs + (m + 2);
+    s.g = s.sn + (m + 2);
+    s.y = s.g + (m + 2);
+    s.hcol = s.y + (m + 2);
+    s.res = s.hcol + (m + 2);
+    pb_solve_info inf = {0, 0, 0.0, PB_OK};
+    // ||b||
+    k_multidot<<<dim3(DOT_BLOCKS, 1), KB, 0, c->st>>>(n, nullptr, bs, part);
+    PB_LAUNCH(c);
+    k_finish<<<1, KB, 0, c->st>>>(DOT_BLOCKS, part, s.hcol, 0);
+    PB_LAUNCH(c);
+    PB_CUDA(c, cudaMemcpyAsync(c->hscal, s.hcol, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    const double bnorm = sqrt(c->hscal[0]);
+    if (!(bnorm > 0)) {
+        PB_CUDA(c, cudaMemsetAsync(xs, 0, sizeof(double) * n, c->st));
+        if (info) *info = inf;
+        return PB_OK;
+    }
+    int it = 0;
+    double rel = 1.0;
+    bool done = false, converged = false;
+    while (!done) {
+        // r0 = b - A x ; V0 = r0 / ||r0||
+        if ((rc = pb_matvec_sorted(c, xs, w, 0))) return rc;
+        inf.matvecs++;
+        k_residual<<<G, KB, 0, c->st>>>(n, bs, w);
+        PB_LAUNCH(c);
+        k_multidot<<<dim3(DOT_BLOCKS, 1), KB, 0, c->st>>>(n, nullptr, w, part);
+        PB_LAUNCH(c);
+        k_finish<<<1, KB, 0, c->st>>>(DOT_BLOCKS, part, s.hcol, 0);
+        PB_LAUNCH(c);
+        k_scale<<<G, KB, 0, c->st>>>(n, w, s.hcol, V);
+        PB_LAUNCH(c);
+        k_gm_start<<<1, 1, 0, c->st>>>(m, s);
+        PB_LAUNCH(c);
+        PB_CUDA(c, cudaMemcpyAsync(c->hscal, s.res, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        PB_CUDA(c, cudaStreamSynchronize(c->st));
+        rel = c->hscal[0] / bnorm;
+        if (!isfinite(rel)) {
+            inf.status = PB_ERR_NONFINITE;
+            break;
+        }
+        if (rel <= tol) {
+            converged = true;
+            break;
+        }
+        int k = 0;
+        for (int j = 0; j < m && it < max_iter; ++j) {
+            double* vj = V + (size_t)j * n;
+            if ((rc = pb_precond_apply_sorted(c, vj, z))) return rc;
+            if ((rc = pb_matvec_sorted(c, z, w, 0))) return rc;
+            inf.matvecs++;
+            pb_tic(c, PB_T_ARNOLDI);
+            // CGS2
+            for (int pass = 0; pass < 2; ++pass) {
+                k_multidot<<<dim3(DOT_BLOCKS, j + 1), KB, 0, c->st>>>(n, V, w, part);
+                PB_LAUNCH(c);
+                k_finish<<<j + 1, KB, 0, c->st>>>(DOT_BLOCKS, part, pass ? s.y : s.hcol, 0);
+                PB_LAUNCH(c);
+                k_orth_update<<<G, KB, 0, c->st>>>(n, j + 1, V, pass ? s.y : s.hcol, w);
+                PB_LAUNCH(c);
+            }
+            // merge the two passes: hcol[i] += y[i]
+            k_axpy1<<<1, KB, 0, c->st>>>(j + 1, s.y, s.hcol);
+            PB_LAUNCH(c);
+            k_multidot<<<dim3(DOT_BLOCKS, 1), KB, 0, c->st>>>(n, nullptr, w, part);
+            PB_LAUNCH(c);
+            k_finish<<<1, KB, 0, c->st>>>(DOT_BLOCKS, part, s.hcol + j + 1, 0);
+            PB_LAUNCH(c);
+            k_scale<<<G, KB, 0, c->st>>>(n, w, s.hcol + j + 1, V + (size_t)(j + 1) * n);
+            PB_LAUNCH(c);
+            k_gm_givens<<<1, 1, 0, c->st>>>(m, j, s);
+            PB_LAUNCH(c);
+            pb_toc(c, PB_T_ARNOLDI);
+            PB_CUDA(c, cudaMemcpyAsync(c->hscal, s.res, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+            PB_CUDA(c, cudaStreamSynchronize(c->st));
+            ++it;
+            k = j + 1;
+            rel = c->hscal[0] / bnorm;
+            if (!isfinite(rel)) {
+                inf.status = PB_ERR_NONFINITE;
+                done = true;
+                break;
+            }
+            if (rel <= tol) {
+                converged = done = true;
+                break;
+            }
+        }
+        if (k > 0 && inf.status == PB_OK) {
+            // x += M^-1 V y
+            k_gm_solve<<<1, 1, 0, c->st>>>(m, k, s);
+            PB_LAUNCH(c);
+            k_combine<<<G, KB, 0, c->st>>>(n, k, V, s.y, w);
+            PB_LAUNCH(c);
+            if ((rc = pb_precond_apply_sorted(c, w, z))) return rc;
+            k_axpy1<<<G, KB, 0, c->st>>>(n, z, xs);
+            PB_LAUNCH(c);
+        }
+        if (it >= max_iter) done = true;
+        if (inf.status != PB_OK) break;
+    }
+    // true residual
+    if ((rc = pb_matvec_sorted(c, xs, w, 0))) return rc;
+    inf.matvecs++;
+    k_residual<<<G, KB, 0, c->st>>>(n, bs, w);
+    PB_LAUNCH(c);
+    k_multidot<<<dim3(DOT_BLOCKS, 1), KB, 0, c->st>>>(n, nullptr, w, part);
+    PB_LAUNCH(c);
+    k_finish<<<1, KB, 0, c->st>>>(DOT_BLOCKS, part, s.hcol, 0);
+    PB_LAUNCH(c);
+    PB_CUDA(c, cudaMemcpyAsync(c->hscal, s.hcol, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    inf.iterations = it;
+    inf.rel_residual = sqrt(c->hscal[0]) / bnorm;
+    if (inf.status == PB_OK && !converged) inf.status = PB_ERR_NOT_CONVERGED;
+    if (inf.status == PB_OK && !isfinite(inf.rel_residual)) inf.status = PB_ERR_NONFINITE;
+    if (info) *info = inf;
+    return inf.status;
+}

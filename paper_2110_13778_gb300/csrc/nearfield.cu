@@ -1,0 +1,150 @@
+// Near field of the FMM matrix-vector product (Section 2.4, step 1 "Nearfield Calculation"):
+// for every leaf c and every neighbour leaf c' in N(c), the Galerkin block of A between their
+// elements is applied directly. Regular pairs use the one-point (centroid) rule
+// A_i A_j K_m(c_i, c_j); identical and adjacent pairs receive their Sauter-Schwab
+// correction afterwards (k_corrections). The mass terms 1/2 (1 + eps) A_i and
+// 1/2 (1 + 1/eps) A_i of eq_linsysEntry are added here.
+//
+// Row signs follow eqbim_5/eqbim_6:
+//   y1_i = 1/2 (1 + eps) A_i phi_i     - sum_j (I1_ij dphi_j + I2_ij phi_j)
+//   y2_i = 1/2 (1 + 1/eps) A_i dphi_i  - sum_j (I3_ij dphi_j + I4_ij phi_j)
+//
+// Layout: one CTA per target leaf, one thread per target element. Source leaves are staged
+// tile by tile in shared memory (centroid, area, normal, A_j phi_j, A_j dphi_j) and read as
+// warp-wide broadcasts. In mixed precision each source leaf's partial sums are kept in FP32
+// and added into FP64 accumulators per leaf (compensated leaf sums), and coordinates are
+// carried as FP32 hi + lo pairs so that d = (x_hi - y_hi) + (x_lo - y_lo) keeps the
+// separation of close elements to FP32 relative accuracy instead of losing digits to the
+// size of the coordinates.
+#include "kernels.cuh"
+#include "pb_internal.cuh"
+
+#define NEAR_T 128
+
+template <class R, class PV, bool HILO>
+__global__ void __launch_bounds__(NEAR_T) k_near(int nt, const int* __restrict__ begin,
+                                                 const int* __restrict__ noff, const int* __restrict__ nidx,
+                                                 const PV* __restrict__ ep, const PV* __restrict__ en,
+                                                 const float4* __restrict__ elo, const double* __restrict__ xs,
+                                                 double eps_d, double kappa_d, double* __restrict__ ys)
+{
+    __shared__ R sx[NEAR_T], sy[NEAR_T], sz[NEAR_T], snx[NEAR_T], sny[NEAR_T], snz[NEAR_T];
+    __shared__ R sphi[NEAR_T], sdphi[NEAR_T];
+    __shared__ R slx[HILO ? NEAR_T : 1], sly[HILO ? NEAR_T : 1], slz[HILO ? NEAR_T : 1];
+    const int c = blockIdx.x;
+    const int tb = begin[c], te = begin[c + 1];
+    const R eps = (R)eps_d, inv_eps = (R)(1.0 / eps_d), kappa = (R)kappa_d;
+    for (int t0 = tb; t0 < te; t0 += NEAR_T) {
+        const int k = t0 + threadIdx.x;
+        const bool act = k < te;
+        R px = 0, py = 0, pz = 0, qx = 0, qy = 0, qz = 0, lx = 0, ly = 0, lz = 0;
+        if (act) {
+            PV p = ep[k], n = en[k];
+            if (HILO) {
+                float4 l = elo[k];
+                lx = l.x;
+                ly = l.y;
+                lz = l.z;
+            }
+            px = (R)p.x;
+            py = (R)p.y;
+            pz = (R)p.z;
+            qx = (R)n.x;
+            qy = (R)n.y;
+            qz = (R)n.z;
+        }
+        double acc1 = 0.0, acc2 = 0.0;
+        for (int t = noff[c]; t < noff[c + 1]; ++t) {
+            const int c2 = nidx[t];
+            const int sb = begin[c2], se = begin[c2 + 1];
+            R s1 = 0, s2 = 0;
+            for (int s0 = sb; s0 < se; s0 += NEAR_T) {
+                const int ns = min(NEAR_T, se - s0);
+                __syncthreads();
+                if (threadIdx.x < ns) {
+                    const int j = s0 + threadIdx.x;
+                    PV p = ep[j], n = en[j];
+                    sx[threadIdx.x] = (R)p.x;
+                    sy[threadIdx.x] = (R)p.y;
+                    sz[threadIdx.x] = (R)p.z;
+                    snx[threadIdx.x] = (R)n.x;
+                    sny[threadIdx.x] = (R)n.y;
+                    snz[threadIdx.x] = (R)n.z;
+                    sphi[threadIdx.x] = (R)(p.w * xs[j]);
+                    sdphi[threadIdx.x] = (R)(p.w * xs[nt + j]);
+                    if (HILO) {
+                        float4 l = elo[j];
+                        slx[threadIdx.x] = l.x;
+                        sly[threadIdx.x] = l.y;
+                        slz[threadIdx.x] = l.z;
+                    }
+                }
+                __syncthreads();
+                if (act) {
+#pragma unroll 4
+                    for (int q = 0; q < ns; ++q) {
+                        if (s0 + q == k) continue;
+                        R K[4];
+                        R dx = px - sx[q], dy = py - sy[q], dz = pz - sz[q];
+                        if (HILO) {
+                            dx += lx - slx[q];
+                            dy += ly - sly[q];
+                            dz += lz - slz[q];
+                        }
+                        pb_kernels<R>(dx, dy, dz, qx, qy, qz, snx[q], sny[q], snz[q], eps, inv_eps, kappa, K);
+                        s1 += K[0] * sdphi[q] + K[1] * sphi[q];
+                        s2 += K[2] * sdphi[q] + K[3] * sphi[q];
+                    }
+                }
+            }
+            acc1 += (double)s1;
+            acc2 += (double)s2;
+        }
+        if (act) {
+            double A = (double)ep[k].w;
+            ys[k] = 0.5 * (1.0 + eps_d) * A * xs[k] - A * acc1;
+            ys[nt + k] = 0.5 * (1.0 + 1.0 / eps_d) * A * xs[nt + k] - A * acc2;
+        }
+    }
+}
+
+// Sauter-Schwab corrections of identical and adjacent pairs (FP64)
+__global__ void k_corrections(int nt, const int* __restrict__ toff, const int* __restrict__ tj,
+                              const double* __restrict__ corr, const double* __restrict__ xs,
+                              double* __restrict__ ys)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    double y1 = 0.0, y2 = 0.0;
+    for (int t = toff[k]; t < toff[k + 1]; ++t) {
+        int j = tj[t];
+        double ph = xs[j], dph = xs[nt + j];
+        y1 += corr[4 * t] * dph + corr[4 * t + 1] * ph;
+        y2 += corr[4 * t + 2] * dph + corr[4 * t + 3] * ph;
+    }
+    ys[k] -= y1;
+    ys[nt + k] -= y2;
+}
+
+int pb_near_apply(pb_ctx* c, const double* xs, double* ys)
+{
+    const PbLevel& lv = c->lev[c->L];
+    double eps = c->prm.eps_out / c->prm.eps_in;
+    if (c->prm.precision == PB_MIXED)
+        k_near<float, float4, true><<<lv.ncl, NEAR_T, 0, c->st>>>(c->nt, lv.begin, lv.near_off, lv.near_idx,
+                                                                  c->e32p, c->e32n, c->e32l, xs, eps, c->prm.kappa,
+                                                                  ys);
+    else
+        k_near<double, double4_32a, false><<<lv.ncl, NEAR_T, 0, c->st>>>(c->nt, lv.begin, lv.near_off,
+                                                                         lv.near_idx, c->e64p, c->e64n, nullptr, xs,
+                                                                         eps, c->prm.kappa, ys);
+    PB_LAUNCH(c);
+    return PB_OK;
+}
+
+int pb_corr_apply(pb_ctx* c, const double* xs, double* ys)
+{
+    k_corrections<<<(c->nt + 255) / 256, 256, 0, c->st>>>(c->nt, c->touch_off, c->touch_j, c->corr, xs, ys);
+    PB_LAUNCH(c);
+    return PB_OK;
+}

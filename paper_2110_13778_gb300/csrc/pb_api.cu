@@ -1,0 +1,405 @@
+// C ABI entry points of libpb: context, mesh upload, orchestration of the solve.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "pb_internal.cuh"
+
+int pb_fail(pb_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+void* pb_alloc(pb_ctx* c, size_t bytes, bool build_lifetime)
+{
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaMemsetAsync(p, 0, bytes, c->st) != cudaSuccess) {
+        cudaFree(p);
+        return nullptr;
+    }
+    (build_lifetime ? c->build_allocs : c->mesh_allocs).push_back(p);
+    return p;
+}
+
+// drop everything pb_build_tree made (tree, lists, integrals, factors, work vectors)
+static void pb_free_build(pb_ctx* c)
+{
+    cudaStreamSynchronize(c->st);
+    for (void* p : c->build_allocs) cudaFree(p);
+    c->build_allocs.clear();
+    c->built = false;
+    c->gm_m = 0;
+    c->scratch = nullptr;
+    c->L = 0;
+    for (auto& l : c->lev) l = PbLevel();
+    c->cent = c->area = c->nrm = nullptr;
+}
+
+static void pb_free_mesh(pb_ctx* c)
+{
+    pb_free_build(c);
+    for (void* p : c->mesh_allocs) cudaFree(p);
+    c->mesh_allocs.clear();
+    c->verts = c->qpos = c->q = nullptr;
+    c->tris = nullptr;
+    c->nt = c->nv = c->nc = 0;
+}
+
+extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
+{
+    if (!prm || !out) return PB_ERR_ARG;
+    *out = nullptr;
+    if (!(prm->eps_in > 0) || !(prm->eps_out > 0) || !(prm->kappa >= 0)) return PB_ERR_ARG;
+    if (!(prm->eta0 > 0 && prm->eta0 < 1)) return PB_ERR_ARG;
+    if (prm->p < 0 || prm->p > 10 || prm->qs < 1 || prm->qs > 8) return PB_ERR_ARG;
+    if (prm->levels < 0 || prm->levels > PB_MAXL || (prm->levels == 0 && prm->leaf_size < 1))
+        return PB_ERR_ARG;
+    if (prm->precision != PB_FP64 && prm->precision != PB_MIXED) return PB_ERR_ARG;
+    if (prm->precond < PB_PRECOND_NONE || prm->precond > PB_PRECOND_BLOCK) return PB_ERR_ARG;
+    pb_ctx* c = new pb_ctx();
+    c->prm = *prm;
+    c->st = (cudaStream_t)stream;
+    void* h = nullptr;
+    if (cudaMallocHost(&h, 64 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return PB_ERR_NOMEM;
+    }
+    c->hscal = (double*)h;
+    for (int i = 0; i < 10; ++i) cudaEventCreate(&c->ev[i]);
+    *out = c;
+    return PB_OK;
+}
+
+extern "C" int pb_destroy(pb_ctx* c)
+{
+    if (!c) return PB_OK;
+    cudaStreamSynchronize(c->st);
+    for (void* p : c->mesh_allocs) cudaFree(p);
+    for (void* p : c->build_allocs) cudaFree(p);
+    for (int i = 0; i < 10; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->tev_ready)
+        for (int a = 0; a < 2; ++a)
+            for (int s = 0; s < PB_TIMING_SLOTS; ++s)
+                for (int k = 0; k < PB_TMAX; ++k) cudaEventDestroy(c->tev[a][s][k]);
+    if (c->hscal) cudaFreeHost(c->hscal);
+    delete c;
+    return PB_OK;
+}
+
+extern "C" const char* pb_last_error(const pb_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+#define PB_ALIVE(c)                                                          \
+    do {                                                                     \
+        if (!(c)) return PB_ERR_ARG;                                         \
+        if ((c)->dead) return pb_fail((c), PB_ERR_CUDA, "context is dead after a CUDA error"); \
+    } while (0)
+
+extern "C" int pb_mesh_upload(pb_ctx* c, const double* verts, int nv, const int32_t* tris, int nt,
+                              const double* qpos, const double* q, int nc)
+{
+    PB_ALIVE(c);
+    if (!verts || !tris || nv < 3 || nt < 1 || nc < 0 || (nc > 0 && (!qpos || !q)))
+        return pb_fail(c, PB_ERR_ARG, "mesh_upload: need nv >= 3, nt >= 1 and non-null arrays");
+    // host-side validation (indices, zero-area or non-finite triangles)
+    for (int i = 0; i < nt; ++i) {
+        int a = tris[3 * i], b = tris[3 * i + 1], d = tris[3 * i + 2];
+        if (a < 0 || b < 0 || d < 0 || a >= nv || b >= nv || d >= nv || a == b || b == d || a == d)
+            return pb_fail(c, PB_ERR_MESH, "triangle %d has a bad vertex index", i);
+        const double *u = verts + 3 * a, *v = verts + 3 * b, *w = verts + 3 * d;
+        double e1[3] = {v[0] - u[0], v[1] - u[1], v[2] - u[2]};
+        double e2[3] = {w[0] - u[0], w[1] - u[1], w[2] - u[2]};
+        double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                        e1[0] * e2[1] - e1[1] * e2[0]};
+        double A2 = cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2];
+        if (!(A2 > 0) || !isfinite(A2)) return pb_fail(c, PB_ERR_MESH, "triangle %d has zero area", i);
+    }
+    for (int k = 0; k < 3 * nc; ++k)
+        if (!isfinite(qpos[k])) return pb_fail(c, PB_ERR_MESH, "charge position %d not finite", k / 3);
+    for (int k = 0; k < nc; ++k)
+        if (!isfinite(q[k])) return pb_fail(c, PB_ERR_MESH, "charge %d not finite", k);
+    pb_free_mesh(c);
+    c->verts = (double*)pb_alloc(c, sizeof(double) * 3 * nv, false);
+    c->tris = (int*)pb_alloc(c, sizeof(int) * 3 * nt, false);
+    c->qpos = (double*)pb_alloc(c, sizeof(double) * 3 * (nc > 0 ? nc : 1), false);
+    c->q = (double*)pb_alloc(c, sizeof(double) * (nc > 0 ? nc : 1), false);
+    if (!c->verts || !c->tris || !c->qpos || !c->q) return pb_fail(c, PB_ERR_NOMEM, "mesh_upload: out of memory");
+    PB_CUDA(c, cudaMemcpyAsync(c->verts, verts, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(c->tris, tris, sizeof(int) * 3 * nt, cudaMemcpyHostToDevice, c->st));
+    if (nc > 0) {
+        PB_CUDA(c, cudaMemcpyAsync(c->qpos, qpos, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->st));
+        PB_CUDA(c, cudaMemcpyAsync(c->q, q, sizeof(double) * nc, cudaMemcpyHostToDevice, c->st));
+    }
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    c->nv = nv;
+    c->nt = nt;
+    c->nc = nc;
+    return PB_OK;
+}
+
+extern "C" int pb_set_charges(pb_ctx* c, const double* q, int nc)
+{
+    PB_ALIVE(c);
+    if (!c->verts) return pb_fail(c, PB_ERR_STATE, "set_charges before mesh_upload");
+    if (nc != c->nc || (nc > 0 && !q)) return pb_fail(c, PB_ERR_ARG, "set_charges: nc must match the upload");
+    for (int k = 0; k < nc; ++k)
+        if (!isfinite(q[k])) return pb_fail(c, PB_ERR_MESH, "charge %d not finite", k);
+    if (nc > 0) PB_CUDA(c, cudaMemcpyAsync(c->q, q, sizeof(double) * nc, cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    return PB_OK;
+}
+
+extern "C" int pb_build_tree(pb_ctx* c)
+{
+    PB_ALIVE(c);
+    if (!c->verts) return pb_fail(c, PB_ERR_STATE, "build_tree before mesh_upload");
+    pb_free_build(c);
+    int rc;
+    pb_tic(c, PB_T_TREE);
+    if ((rc = pb_geometry_and_tree(c))) return rc;
+    pb_toc(c, PB_T_TREE);
+    pb_tic(c, PB_T_SINGULAR);
+    if ((rc = pb_touching_and_singular(c))) return rc;
+    pb_toc(c, PB_T_SINGULAR);
+    if ((rc = pb_far_setup(c))) return rc;
+    pb_tic(c, PB_T_PCBUILD);
+    if ((rc = pb_precond_build(c))) return rc;
+    pb_toc(c, PB_T_PCBUILD);
+    size_t n2 = 2 * (size_t)c->nt;
+    c->xs = (double*)pb_alloc(c, sizeof(double) * n2);
+    c->ys = (double*)pb_alloc(c, sizeof(double) * n2);
+    c->ws = (double*)pb_alloc(c, sizeof(double) * n2);
+    if (!c->xs || !c->ys || !c->ws) return pb_fail(c, PB_ERR_NOMEM, "build_tree: out of memory");
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    c->built = true;
+    return PB_OK;
+}
+
+// ---------- permutation between element order and tree order ----------
+__global__ void k_gather(int n, const int* __restrict__ order, const double* __restrict__ x,
+                         double* __restrict__ xs)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        int e = order[k];
+        xs[k] = x[e];
+        xs[n + k] = x[n + e];
+    }
+}
+
+__global__ void k_scatter(int n, const int* __restrict__ order, const double* __restrict__ xs,
+                          double* __restrict__ x)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        int e = order[k];
+        x[e] = xs[k];
+        x[n + e] = xs[n + k];
+    }
+}
+
+int pb_gather(pb_ctx* c, const double* x, double* xs)
+{
+    int n = c->nt;
+    k_gather<<<(n + 255) / 256, 256, 0, c->st>>>(n, c->order, x, xs);
+    PB_LAUNCH(c);
+    return PB_OK;
+}
+
+int pb_scatter(pb_ctx* c, const double* xs, double* x)
+{
+    int n = c->nt;
+    k_scatter<<<(n + 255) / 256, 256, 0, c->st>>>(n, c->order, xs, x);
+    PB_LAUNCH(c);
+    return PB_OK;
+}
+
+int pb_matvec_sorted(pb_ctx* c, const double* xs, double* ys, int which)
+{
+    int rc;
+    if (which == 2) {
+        PB_CUDA(c, cudaMemsetAsync(ys, 0, sizeof(double) * 2 * c->nt, c->st));
+    } else {
+        pb_tic(c, PB_T_NEAR);
+        if ((rc = pb_near_apply(c, xs, ys))) return rc;
+        pb_toc(c, PB_T_NEAR);
+        pb_tic(c, PB_T_CORR);
+        if ((rc = pb_corr_apply(c, xs, ys))) return rc;
+        pb_toc(c, PB_T_CORR);
+    }
+    if (which != 1)
+        if ((rc = pb_far_apply(c, xs, ys))) return rc;
+    return PB_OK;
+}
+
+extern "C" int pb_matvec_part(pb_ctx* c, const double* x, double* y, int which)
+{
+    PB_ALIVE(c);
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "matvec before build_tree");
+    if (!x || !y || x == y || which < 0 || which > 2) return pb_fail(c, PB_ERR_ARG, "matvec: bad arguments");
+    int rc;
+    if ((rc = pb_gather(c, x, c->xs))) return rc;
+    if ((rc = pb_matvec_sorted(c, c->xs, c->ys, which))) return rc;
+    return pb_scatter(c, c->ys, y);
+}
+
+extern "C" int pb_matvec(pb_ctx* c, const double* x, double* y) { return pb_matvec_part(c, x, y, 0); }
+
+extern "C" int pb_rhs(pb_ctx* c, double* b)
+{
+    PB_ALIVE(c);
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "rhs before build_tree");
+    if (!b) return pb_fail(c, PB_ERR_ARG, "rhs: null output");
+    int rc;
+    if ((rc = pb_rhs_sorted(c, c->ws))) return rc;
+    return pb_scatter(c, c->ws, b);
+}
+
+extern "C" int pb_precond_apply(pb_ctx* c, const double* r, double* z)
+{
+    PB_ALIVE(c);
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "precond before build_tree");
+    if (!r || !z || r == z) return pb_fail(c, PB_ERR_ARG, "precond: bad arguments");
+    int rc;
+    if ((rc = pb_gather(c, r, c->xs))) return rc;
+    if ((rc = pb_precond_apply_sorted(c, c->xs, c->ys))) return rc;
+    return pb_scatter(c, c->ys, z);
+}
+
+extern "C" int pb_gmres_solve(pb_ctx* c, double* x, double tol, int max_iter, int restart,
+                              int use_x0, pb_solve_info* info)
+{
+    PB_ALIVE(c);
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "solve before build_tree");
+    if (!x || !(tol > 0) || max_iter < 1 || restart < 1 || restart > 200)
+        return pb_fail(c, PB_ERR_ARG, "gmres: bad arguments");
+    int rc;
+    // b in ws, x0 in xs (both sorted)
+    if ((rc = pb_rhs_sorted(c, c->ws))) return rc;
+    if (use_x0) {
+        if ((rc = pb_gather(c, x, c->xs))) return rc;
+    } else {
+        PB_CUDA(c, cudaMemsetAsync(c->xs, 0, sizeof(double) * 2 * c->nt, c->st));
+    }
+    pb_solve_info loc;
+    if ((rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc)) &&
+        rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE)
+        return rc;
+    int rc2 = pb_scatter(c, c->xs, x);
+    if (info) *info = loc;
+    if (rc2) return rc2;
+    return rc;
+}
+
+extern "C" int pb_solvation_energy(pb_ctx* c, const double* x, double* E)
+{
+    PB_ALIVE(c);
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "energy before build_tree");
+    if (!x || !E) return pb_fail(c, PB_ERR_ARG, "energy: null argument");
+    int rc;
+    if ((rc = pb_gather(c, x, c->xs))) return rc;
+    return pb_energy_sorted(c, c->xs, E);
+}
+
+extern "C" int pb_get_tree_stats(pb_ctx* c, pb_tree_stats* s)
+{
+    PB_ALIVE(c);
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "tree stats before build_tree");
+    if (!s) return pb_fail(c, PB_ERR_ARG, "null output");
+    memset(s, 0, sizeof(*s));
+    s->levels = c->L;
+    for (int l = 0; l <= c->L; ++l) {
+        s->nclusters[l] = c->lev[l].ncl;
+        s->nnear[l] = c->lev[l].nnear;
+        s->ninter[l] = c->lev[l].ninter;
+        s->order[l] = c->lev[l].p;
+    }
+    s->near_pairs = c->near_pairs;
+    s->touching = c->ntouch;
+    s->max_leaf = c->max_leaf;
+    return PB_OK;
+}
+
+extern "C" int pb_get_tree(pb_ctx* c, int32_t* order, int32_t* level_begin, int32_t* near_cnt,
+                           int32_t* near_idx, int32_t* inter_cnt, int32_t* inter_idx)
+{
+    PB_ALIVE(c);
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "get_tree before build_tree");
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    if (order) PB_CUDA(c, cudaMemcpy(order, c->order, sizeof(int) * c->nt, cudaMemcpyDeviceToHost));
+    size_t cl = 0, nn = 0, ni = 0;
+    for (int l = 0; l <= c->L; ++l) {
+        const PbLevel& lv = c->lev[l];
+        std::vector<int> off(lv.ncl + 1);
+        if (level_begin)
+            PB_CUDA(c, cudaMemcpy(level_begin + cl, lv.begin, sizeof(int) * lv.ncl, cudaMemcpyDeviceToHost));
+        PB_CUDA(c, cudaMemcpy(off.data(), lv.near_off, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost));
+        if (near_cnt)
+            for (int k = 0; k < lv.ncl; ++k) near_cnt[cl + k] = off[k + 1] - off[k];
+        if (near_idx && lv.nnear)
+            PB_CUDA(c, cudaMemcpy(near_idx + nn, lv.near_idx, sizeof(int) * lv.nnear, cudaMemcpyDeviceToHost));
+        PB_CUDA(c, cudaMemcpy(off.data(), lv.int_off, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost));
+        if (inter_cnt)
+            for (int k = 0; k < lv.ncl; ++k) inter_cnt[cl + k] = off[k + 1] - off[k];
+        if (inter_idx && lv.ninter)
+            PB_CUDA(c, cudaMemcpy(inter_idx + ni, lv.int_idx, sizeof(int) * lv.ninter, cudaMemcpyDeviceToHost));
+        cl += lv.ncl;
+        nn += lv.nnear;
+        ni += lv.ninter;
+    }
+    return PB_OK;
+}
+
+extern "C" int pb_set_timing(pb_ctx* c, int enable)
+{
+    PB_ALIVE(c);
+    if (enable && !c->tev_ready) {
+        for (int a = 0; a < 2; ++a)
+            for (int s = 0; s < PB_TIMING_SLOTS; ++s)
+                for (int k = 0; k < PB_TMAX; ++k) PB_CUDA(c, cudaEventCreate(&c->tev[a][s][k]));
+        c->tev_ready = true;
+    }
+    c->timing = enable != 0;
+    for (int s = 0; s < PB_TIMING_SLOTS; ++s) c->tcount[s] = 0;
+    return PB_OK;
+}
+
+extern "C" int pb_get_timing(pb_ctx* c, double* out)
+{
+    PB_ALIVE(c);
+    if (!out) return pb_fail(c, PB_ERR_ARG, "null output");
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    for (int s = 0; s < PB_TIMING_SLOTS; ++s) {
+        double tot = 0.0;
+        for (int k = 0; k < c->tcount[s]; ++k) {
+            float ms = 0.f;
+            PB_CUDA(c, cudaEventElapsedTime(&ms, c->tev[0][s][k], c->tev[1][s][k]));
+            tot += ms;
+        }
+        out[2 * s] = tot;
+        out[2 * s + 1] = c->tcount[s];
+        c->tcount[s] = 0;
+    }
+    return PB_OK;
+}
+
+extern "C" int pb_get_launch_count(pb_ctx* c, long long* out)
+{
+    PB_ALIVE(c);
+    if (!out) return pb_fail(c, PB_ERR_ARG, "null output");
+    *out = c->nlaunch;
+    return PB_OK;
+}

@@ -1,0 +1,154 @@
+// Internal declarations shared by the libpb translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pb.h"
+
+#define PB_MAXL 10          // deepest tree level (Morton keys of 3 * 10 bits)
+#define PB_PMAX 12          // largest Taylor order
+#define PB_PI 3.14159265358979323846
+#define PB_TMAX 256         // timed launches remembered per slot
+
+// number of multi-indices with |a| <= p
+__host__ __device__ inline int pb_nterms(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// position of multi-index (a, b, c) in the layout: total degree n ascending, then a
+// descending, then b descending.
+__host__ __device__ inline int pb_midx(int a, int b, int c)
+{
+    int n = a + b + c;
+    int m = n - a;
+    return n * (n + 1) * (n + 2) / 6 + m * (m + 1) / 2 + (m - b);
+}
+
+struct PbLevel {
+    int ncl = 0;             // clusters on this level
+    int* begin = nullptr;    // [ncl + 1] first sorted element of each cluster, then N
+    int* parent = nullptr;   // [ncl] index of the parent cluster on level - 1
+    int* cbeg = nullptr;     // [ncl + 1] first child on level + 1 (children are contiguous)
+    double* xc = nullptr;    // [3 * ncl] shrink-box centres
+    double* rho = nullptr;   // [ncl] half diagonals
+    int* near_off = nullptr; // [ncl + 1] CSR neighbour lists
+    int* near_idx = nullptr;
+    int* int_off = nullptr;  // [ncl + 1] CSR interaction lists
+    int* int_idx = nullptr;
+    long long nnear = 0, ninter = 0;
+    int p = 0;               // Taylor order on this level
+    // far-field expansions, [ncl * nterms(p)] each, of the working precision
+    void* sig0 = nullptr;    // moments for G0
+    void* sigk = nullptr;    // moments for Gk
+    void* lam0 = nullptr;    // local coefficients for G0
+    void* lamk = nullptr;    // local coefficients for Gk
+};
+
+struct pb_ctx {
+    pb_params prm;
+    cudaStream_t st = nullptr;
+    std::string err = "no error";
+    bool dead = false;
+    std::vector<void*> build_allocs; // freed on a new build or upload
+    std::vector<void*> mesh_allocs;  // freed on a new upload
+    // mesh
+    int nv = 0, nt = 0, nc = 0;
+    double* verts = nullptr;  // [3 nv]
+    int* tris = nullptr;      // [3 nt]
+    double* qpos = nullptr;   // [3 nc]
+    double* q = nullptr;      // [nc]
+    // per-element geometry, element order
+    double* cent = nullptr;   // [3 nt]
+    double* area = nullptr;   // [nt]
+    double* nrm = nullptr;    // [3 nt]
+    // tree
+    bool built = false;
+    int L = 0;
+    PbLevel lev[PB_MAXL + 1];
+    int* order = nullptr;     // [nt] sorted position -> element
+    int* rank = nullptr;      // [nt] element -> sorted position
+    int max_leaf = 0;
+    // sorted element data: position (x, y, z, area) and (nx, ny, nz, 0)
+    double4_32a* e64p = nullptr;
+    double4_32a* e64n = nullptr;
+    float4* e32p = nullptr;
+    float4* e32n = nullptr;
+    float4* e32l = nullptr;   // low parts: centroid - (double)hi, so hi + lo carries ~48 bits
+    int* stris = nullptr;     // [3 nt] vertex indices in sorted order
+    // touching pairs (share >= 1 vertex, incl. i == j), CSR by sorted target position
+    int* touch_off = nullptr; // [nt + 1]
+    int* touch_j = nullptr;   // sorted source position
+    double* corr = nullptr;   // [4 * ntouch] exact integral minus one-point rule (I1..I4)
+    long long ntouch = 0;
+    long long near_pairs = 0;
+    // preconditioner: per leaf a dense (2n x 2n) inverse, unknowns [phi of leaf; dphi of leaf]
+    long long* blk_off = nullptr; // [ncl_L + 1] offsets into minv
+    double* minv = nullptr;
+    double* dinv = nullptr;       // [4 nt] inverse 2x2 blocks for PB_PRECOND_DIAG
+    // work vectors in sorted order
+    double* xs = nullptr;
+    double* ys = nullptr;
+    double* ws = nullptr;
+    double* scratch = nullptr;    // reduction partials
+    double* hscal = nullptr;      // pinned host scalars
+    // GMRES workspace (Krylov basis, work vectors, reduction partials, small dense state)
+    int gm_m = 0;
+    double *gmV = nullptr, *gmw = nullptr, *gmz = nullptr, *gmpart = nullptr, *gmsmall = nullptr;
+    // timing: per slot a ring of (start, stop) event pairs, read back by pb_get_timing
+    bool timing = false;
+    cudaEvent_t ev[10] = {};
+    cudaEvent_t tev[2][PB_TIMING_SLOTS][PB_TMAX] = {};
+    int tcount[PB_TIMING_SLOTS] = {};
+    bool tev_ready = false;
+    long long nlaunch = 0;  // kernels of this library launched on this context
+};
+
+inline void pb_tic(pb_ctx* c, int slot)
+{
+    if (c->timing && c->tcount[slot] < PB_TMAX) cudaEventRecord(c->tev[0][slot][c->tcount[slot]], c->st);
+}
+inline void pb_toc(pb_ctx* c, int slot)
+{
+    if (c->timing && c->tcount[slot] < PB_TMAX) cudaEventRecord(c->tev[1][slot][c->tcount[slot]++], c->st);
+}
+
+// error helpers (pb_api.cu)
+int pb_fail(pb_ctx* c, int code, const char* fmt, ...);
+#define PB_CUDA(c, call)                                                                   \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            (c)->dead = true;                                                              \
+            return pb_fail((c), PB_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                           __FILE__, __LINE__);                                            \
+        }                                                                                  \
+    } while (0)
+#define PB_LAUNCH(c)                          \
+    do {                                      \
+        ++(c)->nlaunch;                       \
+        PB_CUDA(c, cudaGetLastError());       \
+    } while (0)
+
+// device allocation owned by the context (zero-filled); nullptr on failure. Build-lifetime
+// buffers are freed by the next pb_build_tree or pb_mesh_upload, mesh-lifetime buffers by
+// the next pb_mesh_upload.
+void* pb_alloc(pb_ctx* c, size_t bytes, bool build_lifetime = true);
+
+// translation-unit entry points
+int pb_geometry_and_tree(pb_ctx* c);          // tree.cu
+int pb_touching_and_singular(pb_ctx* c);      // singular.cu
+int pb_near_apply(pb_ctx* c, const double* xs, double* ys);        // nearfield.cu (writes ys)
+int pb_corr_apply(pb_ctx* c, const double* xs, double* ys);        // nearfield.cu (adds)
+int pb_far_setup(pb_ctx* c);                                       // farfield.cu
+int pb_far_apply(pb_ctx* c, const double* xs, double* ys);         // farfield.cu (adds)
+int pb_precond_build(pb_ctx* c);                                   // precond.cu
+int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z);
+int pb_rhs_sorted(pb_ctx* c, double* bs);                          // krylov.cu
+int pb_energy_sorted(pb_ctx* c, const double* xs, double* E);      // krylov.cu
+int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max_iter,
+                    int restart, pb_solve_info* info);              // krylov.cu
+int pb_matvec_sorted(pb_ctx* c, const double* xs, double* ys, int which);  // pb_api.cu
+int pb_gather(pb_ctx* c, const double* x, double* xs);   // element -> sorted order
+int pb_scatter(pb_ctx* c, const double* xs, double* x);  // sorted -> element order

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libpb (include/pb.h): argument marshalling only.
+
+Every function keeps the C name. Device arrays are passed as torch CUDA tensors (float64,
+contiguous) or raw integer device addresses; host arrays as numpy arrays. Errors raise
+``PBError`` with the library's one-line reason. There is no fallback: if libpb.so is not
+built, importing this module's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpb.so")
+
+PB_OK, PB_ERR_ARG, PB_ERR_MESH, PB_ERR_CUDA, PB_ERR_NOT_CONVERGED, PB_ERR_NONFINITE, PB_ERR_STATE, PB_ERR_NOMEM = range(8)
+PB_FP64, PB_MIXED = 0, 1
+PB_PRECOND_NONE, PB_PRECOND_DIAG, PB_PRECOND_BLOCK = 0, 1, 2
+
+EXPORTS = [
+    "pb_create", "pb_destroy", "pb_last_error", "pb_mesh_upload", "pb_set_charges", "pb_build_tree",
+    "pb_matvec", "pb_rhs", "pb_precond_apply", "pb_gmres_solve", "pb_solvation_energy",
+    "pb_get_tree_stats", "pb_get_tree", "pb_matvec_part", "pb_set_timing", "pb_get_timing",
+    "pb_get_launch_count",
+]
+
+
+class PBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libpb error {code}: {msg}")
+        self.code = code
+
+
+class pb_params(ctypes.Structure):
+    _fields_ = [
+        ("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double), ("kappa", ctypes.c_double),
+        ("eta0", ctypes.c_double), ("leaf_size", ctypes.c_int), ("levels", ctypes.c_int),
+        ("p", ctypes.c_int), ("adaptive", ctypes.c_int), ("qs", ctypes.c_int),
+        ("precision", ctypes.c_int), ("precond", ctypes.c_int),
+    ]
+
+
+class pb_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("matvecs", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+class pb_tree_stats(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int), ("nclusters", ctypes.c_int * 11), ("nnear", ctypes.c_longlong * 11),
+        ("ninter", ctypes.c_longlong * 11), ("order", ctypes.c_int * 11), ("near_pairs", ctypes.c_longlong),
+        ("touching", ctypes.c_longlong), ("max_leaf", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libpb.so (built by ``paper_2110_13778_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is not built: run paper_2110_13778_gb300.build.build() (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
+        c_int, c_double = ctypes.c_int, ctypes.c_double
+        L.pb_create.argtypes = [ctypes.POINTER(pb_params), vp, ctypes.POINTER(vp)]
+        L.pb_destroy.argtypes = [vp]
+        L.pb_last_error.argtypes = [vp]
+        L.pb_last_error.restype = ctypes.c_char_p
+        L.pb_mesh_upload.argtypes = [vp, dp, c_int, ip, c_int, dp, dp, c_int]
+        L.pb_set_charges.argtypes = [vp, dp, c_int]
+        L.pb_build_tree.argtypes = [vp]
+        L.pb_matvec.argtypes = [vp, vp, vp]
+        L.pb_matvec_part.argtypes = [vp, vp, vp, c_int]
+        L.pb_rhs.argtypes = [vp, vp]
+        L.pb_precond_apply.argtypes = [vp, vp, vp]
+        L.pb_gmres_solve.argtypes = [vp, vp, c_double, c_int, c_int, c_int, ctypes.POINTER(pb_solve_info)]
+        L.pb_solvation_energy.argtypes = [vp, vp, dp]
+        L.pb_get_tree_stats.argtypes = [vp, ctypes.POINTER(pb_tree_stats)]
+        L.pb_get_tree.argtypes = [vp, ip, ip, ip, ip, ip, ip]
+        L.pb_set_timing.argtypes = [vp, c_int]
+        L.pb_get_timing.argtypes = [vp, dp]
+        L.pb_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    """Device address of a torch tensor (float64, contiguous, CUDA) or an int address."""
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(ctx, rc):
+    if rc != PB_OK:
+        raise PBError(rc, lib().pb_last_error(ctx).decode())
+
+
+def params(eps_in=1.0, eps_out=80.0, kappa=0.1257, eta0=0.8, leaf_size=64, levels=0, p=8, adaptive=0, qs=3,
+           precision=PB_FP64, precond=PB_PRECOND_BLOCK):
+    return pb_params(eps_in, eps_out, kappa, eta0, leaf_size, levels, p, adaptive, qs, precision, precond)
+
+
+def pb_create(prm: pb_params, stream=0):
+    h = ctypes.c_void_p()
+    rc = lib().pb_create(ctypes.byref(prm), ctypes.c_void_p(stream), ctypes.byref(h))
+    if rc != PB_OK:
+        raise PBError(rc, "pb_create rejected the parameters")
+    return h
+
+
+def pb_destroy(ctx):
+    lib().pb_destroy(ctx)
+
+
+def pb_mesh_upload(ctx, verts, tris, qpos, q):
+    V = np.ascontiguousarray(verts, dtype=np.float64)
+    T = np.ascontiguousarray(tris, dtype=np.int32)
+    QP = np.ascontiguousarray(np.reshape(qpos, (-1, 3)), dtype=np.float64)
+    Q = np.ascontiguousarray(np.reshape(q, (-1,)), dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(ctx, lib().pb_mesh_upload(ctx, V.ctypes.data_as(dp), V.shape[0], T.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     T.shape[0], QP.ctypes.data_as(dp), Q.ctypes.data_as(dp), Q.shape[0]))
+
+
+def pb_set_charges(ctx, q):
+    Q = np.ascontiguousarray(np.reshape(q, (-1,)), dtype=np.float64)
+    _check(ctx, lib().pb_set_charges(ctx, Q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), Q.shape[0]))
+
+
+def pb_build_tree(ctx):
+    _check(ctx, lib().pb_build_tree(ctx))
+
+
+def pb_matvec(ctx, x, y):
+    _check(ctx, lib().pb_matvec(ctx, _ptr(x), _ptr(y)))
+
+
+def pb_matvec_part(ctx, x, y, which):
+    _check(ctx, lib().pb_matvec_part(ctx, _ptr(x), _ptr(y), which))
+
+
+def pb_rhs(ctx, b):
+    _check(ctx, lib().pb_rhs(ctx, _ptr(b)))
+
+
+def pb_precond_apply(ctx, r, z):
+    _check(ctx, lib().pb_precond_apply(ctx, _ptr(r), _ptr(z)))
+
+
+def pb_gmres_solve(ctx, x, tol=1e-6, max_iter=200, restart=50, use_x0=False, raise_on_fail=True):
+    info = pb_solve_info()
+    rc = lib().pb_gmres_solve(ctx, _ptr(x), tol, max_iter, restart, int(bool(use_x0)), ctypes.byref(info))
+    if rc != PB_OK and (raise_on_fail or rc not in (PB_ERR_NOT_CONVERGED, PB_ERR_NONFINITE)):
+        _check(ctx, rc)
+    return info
+
+
+def pb_solvation_energy(ctx, x):
+    E = ctypes.c_double()
+    _check(ctx, lib().pb_solvation_energy(ctx, _ptr(x), ctypes.byref(E)))
+    return E.value
+
+
+def pb_get_tree_stats(ctx):
+    s = pb_tree_stats()
+    _check(ctx, lib().pb_get_tree_stats(ctx, ctypes.byref(s)))
+    L = s.levels
+    return {
+        "levels": L,
+        "nclusters": list(s.nclusters[: L + 1]),
+        "nnear": list(s.nnear[: L + 1]),
+        "ninter": list(s.ninter[: L + 1]),
+        "order": list(s.order[: L + 1]),
+        "near_pairs": s.near_pairs,
+        "touching": s.touching,
+        "max_leaf": s.max_leaf,
+    }
+
+
+def pb_get_tree(ctx, nt):
+    st = pb_get_tree_stats(ctx)
+    ncl = sum(st["nclusters"])
+    order = np.zeros(nt, dtype=np.int32)
+    lb = np.zeros(ncl, dtype=np.int32)
+    nc = np.zeros(ncl, dtype=np.int32)
+    ni = np.zeros(max(1, sum(st["nnear"])), dtype=np.int32)
+    ic = np.zeros(ncl, dtype=np.int32)
+    ii = np.zeros(max(1, sum(st["ninter"])), dtype=np.int32)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    _check(ctx, lib().pb_get_tree(ctx, order.ctypes.data_as(ip), lb.ctypes.data_as(ip), nc.ctypes.data_as(ip),
+                                  ni.ctypes.data_as(ip), ic.ctypes.data_as(ip), ii.ctypes.data_as(ip)))
+    return st, order, lb, nc, ni, ic, ii
+
+
+def pb_set_timing(ctx, enable):
+    _check(ctx, lib().pb_set_timing(ctx, int(enable)))
+
+
+TIMING_SLOTS = ["near", "corr", "up", "m2l", "down", "precond", "arnoldi", "singular", "tree", "pcbuild",
+                "energy", "rhs"]
+
+
+def pb_get_timing(ctx):
+    """{slot: (total_ms, launches)} since the last read."""
+    out = (ctypes.c_double * (2 * len(TIMING_SLOTS)))()
+    _check(ctx, lib().pb_get_timing(ctx, out))
+    return {s: (out[2 * i], int(out[2 * i + 1])) for i, s in enumerate(TIMING_SLOTS)}
+
+
+def pb_get_launch_count(ctx):
+    n = ctypes.c_longlong()
+    _check(ctx, lib().pb_get_launch_count(ctx, ctypes.byref(n)))
+    return n.value
