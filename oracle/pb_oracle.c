@@ -76,6 +76,37 @@ typedef struct {
     double kappa; /* inverse Debye length */
 } orc_phys;
 
+/* The six terms the kernels are made of, at x (normal nx) and y (normal ny):
+ * Q[0] = G0 - Gk, Q[1] = d2Gk/dnx dny - d2G0/dnx dny, Q[2] = dG0/dny, Q[3] = dGk/dny,
+ * Q[4] = dG0/dnx, Q[5] = dGk/dnx. */
+static void orc_kernel_terms(const double* x, const double* nx, const double* y, const double* ny,
+                             const orc_phys* ph, double* Q)
+{
+    double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double r = sqrt(r2);
+    double kr = ph->kappa * r;
+    double e = exp(-kr);
+    double fpi = 4.0 * ORC_PI;
+    double G0 = 1.0 / (fpi * r);
+    double Gk = e / (fpi * r);
+    double g0p = -1.0 / (fpi * r2);
+    double gkp = -(1.0 + kr) * e / (fpi * r2);
+    double g0pp = 2.0 / (fpi * r2 * r);
+    double gkpp = (2.0 + 2.0 * kr + kr * kr) * e / (fpi * r2 * r);
+    double nxd = nx[0] * d[0] + nx[1] * d[1] + nx[2] * d[2];
+    double nyd = ny[0] * d[0] + ny[1] * d[1] + ny[2] * d[2];
+    double nxny = nx[0] * ny[0] + nx[1] * ny[1] + nx[2] * ny[2];
+    double d2G0 = -((g0pp - g0p / r) * nxd * nyd / r2 + (g0p / r) * nxny);
+    double d2Gk = -((gkpp - gkp / r) * nxd * nyd / r2 + (gkp / r) * nxny);
+    Q[0] = G0 - Gk;
+    Q[1] = d2Gk - d2G0;
+    Q[2] = -g0p * nyd / r;
+    Q[3] = -gkp * nyd / r;
+    Q[4] = g0p * nxd / r;
+    Q[5] = gkp * nxd / r;
+}
+
 /* Kout[0..3] = K1..K4 at target x (normal nx) and source y (normal ny). */
 static void orc_kernels(const double* x, const double* nx, const double* y, const double* ny,
                         const orc_phys* ph, double* Kout)
@@ -281,8 +312,18 @@ static void orc_pair(const double* V, const int32_t* T, int i, int j, const orc_
         for (int m = 0; m < 4; ++m) I[m] = Ai * Aj * K[m];
         return;
     }
+    /* One quadrature serves both orderings of a touching pair: the rule is always laid out
+     * from the triangle with the smaller index (its shared vertices first, in its order),
+     * and the integrals of (j, i) follow from those of (i, j) by exchanging the roles of the
+     * two normals. */
+    int first = i < j ? i : j, second = i < j ? j : i;
+    double na[3], nb[3];
+    for (int k = 0; k < 3; ++k) {
+        na[k] = (first == i) ? ni[k] : nj[k];
+        nb[k] = (first == i) ? nj[k] : ni[k];
+    }
     int32_t ti[3], tj[3];
-    orc_reorder(T, i, j, shared, ti, tj);
+    orc_reorder(T, first, second, shared, ti, tj);
     double P[3][3], Q[3][3];
     for (int a = 0; a < 3; ++a)
         for (int k = 0; k < 3; ++k) {
@@ -292,7 +333,7 @@ static void orc_pair(const double* V, const int32_t* T, int i, int j, const orc_
     /* The reference triangle {0 <= e2 <= e1 <= 1} has corners (0,0), (1,0), (1,1); the affine
      * map sending them to P0, P1, P2 is P0 + e1 (P1 - P0) + e2 (P2 - P1). (eqparameter prints
      * P2 - P0 in the last term, which sends (1,1) to P1 + P2 - P0, outside the element.) */
-    double acc[4] = {0, 0, 0, 0};
+    double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int a = 0; a < qs; ++a)
         for (int b = 0; b < qs; ++b)
             for (int c = 0; c < qs; ++c)
@@ -301,19 +342,31 @@ static void orc_pair(const double* V, const int32_t* T, int i, int j, const orc_
                     double xh[12], yh[12], jac[6];
                     int ns = orc_ss_points(shared, gx[a], gx[b], gx[c], gx[d], xh, yh, jac);
                     for (int s = 0; s < ns; ++s) {
-                        double x[3], y[3], K[4];
+                        double x[3], y[3], Qt[6];
                         for (int k = 0; k < 3; ++k) {
                             x[k] = P[0][k] + xh[2 * s] * (P[1][k] - P[0][k]) +
                                    xh[2 * s + 1] * (P[2][k] - P[1][k]);
                             y[k] = Q[0][k] + yh[2 * s] * (Q[1][k] - Q[0][k]) +
                                    yh[2 * s + 1] * (Q[2][k] - Q[1][k]);
                         }
-                        orc_kernels(x, ni, y, nj, ph, K);
-                        for (int m = 0; m < 4; ++m) acc[m] += wq * jac[s] * K[m];
+                        orc_kernel_terms(x, na, y, nb, ph, Qt);
+                        for (int m = 0; m < 6; ++m) acc[m] += wq * jac[s] * Qt[m];
                     }
                 }
     /* Jacobian of each affine element map is 2 A */
-    for (int m = 0; m < 4; ++m) I[m] = (2.0 * Ai) * (2.0 * Aj) * acc[m];
+    for (int m = 0; m < 6; ++m) acc[m] *= (2.0 * Ai) * (2.0 * Aj);
+    double eps = ph->eps;
+    I[0] = acc[0];
+    I[3] = acc[1];
+    if (first == i) {
+        /* target = first triangle: K2 = eps dGk/dny - dG0/dny, K3 = dG0/dnx - dGk/dnx / eps */
+        I[1] = eps * acc[3] - acc[2];
+        I[2] = acc[4] - acc[5] / eps;
+    } else {
+        /* target = second triangle: its source normal derivative is the first's dn_x */
+        I[1] = eps * acc[5] - acc[4];
+        I[2] = acc[2] - acc[3] / eps;
+    }
 }
 
 /* exported: the four integrals for one ordered pair (target i, source j) */
