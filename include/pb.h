@@ -180,6 +180,7 @@ int pb_get_timing(pb_ctx* ctx, double* out);
 /* Number of this library's kernel launches queued on ctx since it was created. */
 int pb_get_launch_count(pb_ctx* ctx, long long* out);
 
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,13 @@
 // The MtL sum is evaluated as  a! lam^a = sum_b D^{a+b} G(d) * [(-1)^|b| m^b / b!].
 #include <math.h>
 
+#include <vector>
+
 #include "pb_internal.cuh"
+
+template <int P>
+struct M2LPassCount;
+#include "m2l_unrolled.cuh"
 
 #define FAR_T 128
 #define NT_MAX 455  // nterms(12)
@@ -111,6 +117,9 @@ __global__ void __launch_bounds__(FAR_T) k_m2m(int pp, int pc, const int* __rest
                                                R* __restrict__ s0, R* __restrict__ sk)
 {
     __shared__ R tp[3][PB_PMAX + 1];
+    __shared__ R sbin[PB_PMAX + 1][PB_PMAX + 1];  // binomials, read with thread-dependent indices
+    for (int t = threadIdx.x; t < (PB_PMAX + 1) * (PB_PMAX + 1); t += blockDim.x)
+        sbin[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)] = (R)c_binom[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)];
     const int c = blockIdx.x;
     const int Tp = pb_nterms(pp), Tc = pb_nterms(pc);
     R a0[4] = {0, 0, 0, 0}, ak[4] = {0, 0, 0, 0};
@@ -137,7 +146,7 @@ __global__ void __launch_bounds__(FAR_T) k_m2m(int pp, int pc, const int* __rest
                 for (int b2 = 0; b2 <= a2; ++b2)
                     for (int b3 = 0; b3 <= a3; ++b3) {
                         if (b1 + b2 + b3 > pc) continue;
-                        R w = (R)(c_binom[a1][b1] * c_binom[a2][b2] * c_binom[a3][b3]) * tp[0][a1 - b1] *
+                        R w = sbin[a1][b1] * sbin[a2][b2] * sbin[a3][b3] * tp[0][a1 - b1] *
                               tp[1][a2 - b2] * tp[2][a3 - b3];
                         int pos = pb_midx(b1, b2, b3);
                         v0 += w * m0[pos];
@@ -259,6 +268,146 @@ __global__ void __launch_bounds__(FAR_T) k_m2l(int p, double kappa, const int* _
     }
 }
 
+// ---------- step 4, precomputed form ----------
+// Setup: the kernel derivatives D^g G0 and D^g Gk of every interaction slot depend only on
+// the geometry, so they are evaluated once (FP64 recurrence, stored in the working
+// precision) in the interleaved slot layout the contraction reads.
+template <class R>
+__global__ void __launch_bounds__(FAR_T) k_m2l_setup(int p, double kappa, const int* __restrict__ soff,
+                                                     const int* __restrict__ ssrc, const double* __restrict__ xc,
+                                                     R* __restrict__ D0, R* __restrict__ Dk)
+{
+    __shared__ double F0[NT_MAX], Fk[NT_MAX], Pk[NT_MAX];
+    const int c = blockIdx.x;
+    const int T = pb_nterms(p);
+    const double i4pi = 0.07957747154594767;
+    for (int s = soff[c]; s < soff[c + 1]; ++s) {
+        const int c2 = ssrc[s];
+        const size_t base = ((size_t)(s >> 5) * T) * 32 + (s & 31);
+        if (c2 < 0) {
+            for (int k = threadIdx.x; k < T; k += FAR_T) {
+                D0[base + (size_t)k * 32] = R(0);
+                Dk[base + (size_t)k * 32] = R(0);
+            }
+            continue;
+        }
+        const double d[3] = {xc[3 * c] - xc[3 * c2], xc[3 * c + 1] - xc[3 * c2 + 1], xc[3 * c + 2] - xc[3 * c2 + 2]};
+        const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double r = sqrt(d2), ex = exp(-kappa * r);
+            F0[0] = i4pi / r;
+            Fk[0] = i4pi * ex / r;
+            Pk[0] = i4pi * ex;
+        }
+        __syncthreads();
+        for (int n = 1; n <= p; ++n) {
+            for (int k = pb_nterms(n - 1) + threadIdx.x; k < pb_nterms(n); k += FAR_T) {
+                int kk[3];
+                mi_unpack(c_mi[k], kk[0], kk[1], kk[2]);
+                double a0 = 0, a1 = 0, ak0 = 0, ak1 = 0, ap0 = 0, ap1 = 0;
+                for (int i = 0; i < 3; ++i) {
+                    if (kk[i] >= 1) {
+                        int q = pb_midx(kk[0] - (i == 0), kk[1] - (i == 1), kk[2] - (i == 2));
+                        a0 += d[i] * F0[q];
+                        ak0 += d[i] * Fk[q];
+                        ap0 += d[i] * Pk[q];
+                    }
+                    if (kk[i] >= 2) {
+                        int q = pb_midx(kk[0] - 2 * (i == 0), kk[1] - 2 * (i == 1), kk[2] - 2 * (i == 2));
+                        a1 += F0[q];
+                        ak1 += Fk[q];
+                        ap1 += Pk[q];
+                    }
+                }
+                F0[k] = (-(2.0 * n - 1.0) * a0 - (n - 1.0) * a1) / (d2 * n);
+                Fk[k] = (-(2.0 * n - 1.0) * ak0 - (n - 1.0) * ak1 - kappa * ap0 - kappa * ap1) / (d2 * n);
+                Pk[k] = -kappa * (ak0 + ak1) / n;
+            }
+            __syncthreads();
+        }
+        for (int k = threadIdx.x; k < T; k += FAR_T) {
+            int k1, k2, k3;
+            mi_unpack(c_mi[k], k1, k2, k3);
+            double f = c_fact[k1] * c_fact[k2] * c_fact[k3];
+            D0[base + (size_t)k * 32] = (R)(F0[k] * f);
+            Dk[base + (size_t)k * 32] = (R)(Fk[k] * f);
+        }
+    }
+}
+
+// Contraction: one warp per target cluster, one lane per interaction slot; the local
+// coefficients of the pass live in registers (straight-line bodies of m2l_unrolled.cuh), the
+// 32 sources' scaled moments in shared memory ([b][33] per warp), the derivatives stream from
+// the slot layout. The per-lane partial sums are added across the warp at the end.
+#define M2LF_WARPS 4
+template <int P, class R>
+__global__ void __launch_bounds__(32 * M2LF_WARPS) k_m2l_fast(int ncl, const int* __restrict__ soff,
+                                                              const int* __restrict__ ssrc, const R* __restrict__ D0,
+                                                              const R* __restrict__ Dk, const R* __restrict__ s0,
+                                                              const R* __restrict__ sk, R* __restrict__ l0,
+                                                              R* __restrict__ lk)
+{
+    constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ R sc[T];      // (-1)^|b| / b!
+    __shared__ R ifac[T];    // 1 / a!
+    const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    R* Ms = (R*)dsm + (size_t)warp * T * 33;
+    for (int b = threadIdx.x; b < T; b += blockDim.x) {
+        int b1, b2, b3;
+        mi_unpack(c_mi[b], b1, b2, b3);
+        double f = c_fact[b1] * c_fact[b2] * c_fact[b3];
+        sc[b] = (R)(((b1 + b2 + b3) & 1 ? -1.0 : 1.0) / f);
+        ifac[b] = (R)(1.0 / f);
+    }
+    __syncthreads();
+    const int c = blockIdx.x * M2LF_WARPS + warp;
+    if (c >= ncl) return;  // no block-wide barrier below this point
+    const int sb = soff[c], se = soff[c + 1];
+#pragma unroll 1
+    for (int kern = 0; kern < 2; ++kern) {
+        const R* D = kern ? Dk : D0;
+        const R* sg = kern ? sk : s0;
+        R* out = kern ? lk : l0;
+#pragma unroll 1
+        for (int pass = 0; pass < M2LPassCount<P>::n; ++pass) {
+            R L[84];
+#pragma unroll
+            for (int i = 0; i < 84; ++i) L[i] = R(0);
+#pragma unroll 1
+            for (int s0i = sb; s0i < se; s0i += 32) {
+                const int my = ssrc[s0i + lane];
+                __syncwarp();
+                for (int q = 0; q < 32; ++q) {
+                    const int src = __shfl_sync(0xffffffffu, my, q);
+                    for (int b = lane; b < T; b += 32) Ms[b * 33 + q] = src >= 0 ? sg[(size_t)src * T + b] * sc[b] : R(0);
+                }
+                __syncwarp();
+                const R* Dl = D + ((size_t)(s0i >> 5) * T) * 32 + lane;
+                const R* Ml = Ms + lane;
+                if (pass == 0) M2LBody<P, 0>::run(Dl, Ml, L);
+                if constexpr (M2LPassCount<P>::n > 1) {
+                    if (pass == 1) M2LBody<P, (M2LPassCount<P>::n > 1 ? 1 : 0)>::run(Dl, Ml, L);
+                }
+            }
+            // sum the lanes' partial coefficients through shared memory
+            const int a0 = pass * 84, a1 = min(T, a0 + 84);
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 84; ++i)
+                if (a0 + i < a1) Ms[i * 33 + lane] = L[i];
+            __syncwarp();
+            for (int i = lane; i < a1 - a0; i += 32) {
+                R s = 0;
+                for (int l = 0; l < 32; ++l) s += Ms[i * 33 + l];
+                out[(size_t)c * T + a0 + i] = s * ifac[a0 + i];
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // ---------- step 5: LtL, parent (order pp) into child (order pc) ----------
 template <class R>
 __global__ void __launch_bounds__(FAR_T) k_l2l(int pp, int pc, const int* __restrict__ parent,
@@ -267,6 +416,9 @@ __global__ void __launch_bounds__(FAR_T) k_l2l(int pp, int pc, const int* __rest
                                                R* __restrict__ lc0, R* __restrict__ lck)
 {
     __shared__ R tp[3][PB_PMAX + 1];
+    __shared__ R sbin[PB_PMAX + 1][PB_PMAX + 1];  // binomials, read with thread-dependent indices
+    for (int t = threadIdx.x; t < (PB_PMAX + 1) * (PB_PMAX + 1); t += blockDim.x)
+        sbin[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)] = (R)c_binom[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)];
     const int c = blockIdx.x;
     const int P = parent[c];
     const int Tp = pb_nterms(pp), Tc = pb_nterms(pc);
@@ -289,7 +441,7 @@ __global__ void __launch_bounds__(FAR_T) k_l2l(int pp, int pc, const int* __rest
         for (int g = 0; g < ng; ++g) {
             int g1, g2, g3;
             mi_unpack(c_mi[g], g1, g2, g3);
-            R w = (R)(c_binom[b1 + g1][b1] * c_binom[b2 + g2][b2] * c_binom[b3 + g3][b3]) * tp[0][g1] * tp[1][g2] *
+            R w = sbin[b1 + g1][b1] * sbin[b2 + g2][b2] * sbin[b3 + g3][b3] * tp[0][g1] * tp[1][g2] *
                   tp[2][g3];
             int pos = pb_midx(b1 + g1, b2 + g2, b3 + g3);
             v0 += w * m0[pos];
@@ -368,6 +520,57 @@ static int upload_tables(pb_ctx* c)
     return PB_OK;
 }
 
+static bool m2l_fast_order(int p) { return p == 4 || p == 6 || p == 8; }
+
+// interaction lists padded to multiples of 32 slots, then the derivative tensors per slot
+static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
+{
+    std::vector<int> off(lv.ncl + 1), idx(lv.ninter);
+    PB_CUDA(c, cudaMemcpyAsync(off.data(), lv.int_off, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(idx.data(), lv.int_idx, sizeof(int) * lv.ninter, cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    std::vector<int> soff(lv.ncl + 1);
+    soff[0] = 0;
+    for (int k = 0; k < lv.ncl; ++k) soff[k + 1] = soff[k] + ((off[k + 1] - off[k] + 31) / 32) * 32;
+    std::vector<int> ssrc(soff[lv.ncl], -1);
+    for (int k = 0; k < lv.ncl; ++k)
+        for (int t = off[k]; t < off[k + 1]; ++t) ssrc[soff[k] + (t - off[k])] = idx[t];
+    lv.nslots = soff[lv.ncl];
+    const int T = pb_nterms(lv.p);
+    size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
+    lv.slot_off = (int*)pb_alloc(c, sizeof(int) * (lv.ncl + 1));
+    lv.slot_src = (int*)pb_alloc(c, sizeof(int) * (lv.nslots + 1));
+    lv.D0 = pb_alloc(c, rs * (size_t)lv.nslots * T);
+    lv.Dk = pb_alloc(c, rs * (size_t)lv.nslots * T);
+    if (!lv.slot_off || !lv.slot_src || !lv.D0 || !lv.Dk) return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
+    PB_CUDA(c, cudaMemcpyAsync(lv.slot_off, soff.data(), sizeof(int) * (lv.ncl + 1), cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(lv.slot_src, ssrc.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, c->st));
+    if (c->prm.precision == PB_MIXED)
+        k_m2l_setup<float><<<lv.ncl, FAR_T, 0, c->st>>>(lv.p, c->prm.kappa, lv.slot_off, lv.slot_src, lv.xc,
+                                                        (float*)lv.D0, (float*)lv.Dk);
+    else
+        k_m2l_setup<double><<<lv.ncl, FAR_T, 0, c->st>>>(lv.p, c->prm.kappa, lv.slot_off, lv.slot_src, lv.xc,
+                                                         (double*)lv.D0, (double*)lv.Dk);
+    PB_LAUNCH(c);
+    // host vectors above are read by the queued copies: wait before they go out of scope
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    return PB_OK;
+}
+
+template <int P, class R>
+static int m2l_fast_launch(pb_ctx* c, PbLevel& lv)
+{
+    constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
+    size_t smem = sizeof(R) * (size_t)M2LF_WARPS * T * 33;
+    PB_CUDA(c, cudaFuncSetAttribute(k_m2l_fast<P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = (lv.ncl + M2LF_WARPS - 1) / M2LF_WARPS;
+    k_m2l_fast<P, R><<<grid, 32 * M2LF_WARPS, smem, c->st>>>(lv.ncl, lv.slot_off, lv.slot_src, (const R*)lv.D0,
+                                                             (const R*)lv.Dk, (const R*)lv.sig0, (const R*)lv.sigk,
+                                                             (R*)lv.lam0, (R*)lv.lamk);
+    PB_LAUNCH(c);
+    return PB_OK;
+}
+
 int pb_far_setup(pb_ctx* c)
 {
     int rc = upload_tables(c);
@@ -382,6 +585,10 @@ int pb_far_setup(pb_ctx* c)
         lv.lam0 = pb_alloc(c, rs * n);
         lv.lamk = pb_alloc(c, rs * n);
         if (!lv.sig0 || !lv.sigk || !lv.lam0 || !lv.lamk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");
+        if (lv.ninter > 0 && m2l_fast_order(lv.p)) {
+            int rc2 = m2l_fast_setup(c, lv);
+            if (rc2) return rc2;
+        }
     }
     return PB_OK;
 }
@@ -410,6 +617,14 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys)
     pb_tic(c, PB_T_M2L);
     for (int l = 1; l <= L; ++l) {
         PbLevel& lv = c->lev[l];
+        int rc = -1;
+        if (lv.D0) {
+            if (lv.p == 4) rc = m2l_fast_launch<4, R>(c, lv);
+            else if (lv.p == 6) rc = m2l_fast_launch<6, R>(c, lv);
+            else if (lv.p == 8) rc = m2l_fast_launch<8, R>(c, lv);
+        }
+        if (rc > 0) return rc;
+        if (rc == 0) continue;
         k_m2l<R><<<lv.ncl, FAR_T, 0, c->st>>>(lv.p, c->prm.kappa, lv.int_off, lv.int_idx, lv.xc, (R*)lv.sig0,
                                               (R*)lv.sigk, (R*)lv.lam0, (R*)lv.lamk);
         PB_LAUNCH(c);

@@ -78,3 +78,37 @@ __device__ __forceinline__ void pb_kernels(R dx, R dy, R dz, R nxx, R nxy, R nxz
     K[2] = -nxd * ri3 * (R(1) - e1 * inv_eps);
     K[3] = ri3 * (c3 * nxd * nyd * rinv * rinv - c1 * nxny);
 }
+
+// The parts from which K1..K4 of both orderings of a pair are assembled:
+//   P[0] = K1, P[1] = K4 (both symmetric in x <-> y),
+//   P[2] = dG0/dn_y = (n_y.d)/(4 pi r^3),   P[3] = dGk/dn_y = P[2] e^-t (1 + t),
+//   P[4] = -dG0/dn_x = (n_x.d)/(4 pi r^3),  P[5] = -dGk/dn_x = P[4] e^-t (1 + t).
+// For (x, y): K2 = eps P[3] - P[2], K3 = -P[4] + P[5] / eps; for (y, x): K2 = P[4] - eps P[5],
+// K3 = P[2] - P[3] / eps.
+template <class R>
+__device__ __forceinline__ void pb_kernel_parts(R dx, R dy, R dz, R nxx, R nxy, R nxz, R nyx, R nyy, R nyz, R kappa,
+                                                R* P)
+{
+    const R i4pi = R(0.07957747154594767);
+    R r2 = dx * dx + dy * dy + dz * dz;
+    R rinv = PbKer<R>::rsqrt_(r2);
+    R r = r2 * rinv;
+    R t = kappa * r;
+    R E, g;
+    pb_screen<R>(t, E, g);
+    R tE = t * E;
+    R c1 = -g - tE;
+    R c3 = R(-3) * g - t * t - tE * (R(3) + t);
+    R ri = rinv * i4pi;
+    R ri3 = ri * rinv * rinv;
+    R nxd = nxx * dx + nxy * dy + nxz * dz;
+    R nyd = nyx * dx + nyy * dy + nyz * dz;
+    R nxny = nxx * nyx + nxy * nyy + nxz * nyz;
+    R e1 = R(1) - c1;
+    P[0] = -E * ri;
+    P[1] = ri3 * (c3 * nxd * nyd * rinv * rinv - c1 * nxny);
+    P[2] = nyd * ri3;
+    P[3] = P[2] * e1;
+    P[4] = nxd * ri3;
+    P[5] = P[4] * e1;
+}

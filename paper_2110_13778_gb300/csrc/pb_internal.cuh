@@ -44,6 +44,13 @@ struct PbLevel {
     void* sigk = nullptr;    // moments for Gk
     void* lam0 = nullptr;    // local coefficients for G0
     void* lamk = nullptr;    // local coefficients for Gk
+    // MtL with precomputed kernel derivatives: each cluster's interaction list padded to a
+    // multiple of 32 slots; D^gamma G of slot s stored at ((s / 32) * T + gamma) * 32 + s % 32
+    int* slot_off = nullptr; // [ncl + 1]
+    int* slot_src = nullptr; // [nslots], -1 for padding
+    long long nslots = 0;
+    void* D0 = nullptr;      // derivatives of G0, working precision
+    void* Dk = nullptr;      // derivatives of Gk
 };
 
 struct pb_ctx {
@@ -85,7 +92,7 @@ struct pb_ctx {
     long long near_pairs = 0;
     // preconditioner: per leaf a dense (2n x 2n) inverse, unknowns [phi of leaf; dphi of leaf]
     long long* blk_off = nullptr; // [ncl_L + 1] offsets into minv
-    double* minv = nullptr;
+    void* minv = nullptr;         // inverse blocks, working precision (float in mixed mode)
     double* dinv = nullptr;       // [4 nt] inverse 2x2 blocks for PB_PRECOND_DIAG
     // work vectors in sorted order
     double* xs = nullptr;

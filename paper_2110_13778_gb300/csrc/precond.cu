@@ -3,81 +3,92 @@
 // Block-diagonal ("bd"): M keeps the entries of A whose two elements lie in the same cube of
 // the designated level -- here the leaf level -- and is zero elsewhere. Permuting the unknowns
 // leaf by leaf makes M = diag(M_1, ..., M_nL); each M_c (order [phi of the leaf; dphi of the
-// leaf], size 2 n_c) is assembled in FP64 from the same one-point entries and Sauter-Schwab
-// corrections as the near field, and inverted once by Gauss-Jordan elimination with partial
-// pivoting. Applying M^-1 is then one dense matrix-vector product per leaf, a bandwidth-bound
-// pass instead of two latency-bound triangular solves.
+// leaf], size m = 2 n_c) is assembled from the same one-point entries and Sauter-Schwab
+// corrections as the near field (evaluated in FP64) and inverted once, in place, by
+// Gauss-Jordan elimination with partial pivoting. Applying M^-1 is then one dense
+// matrix-vector product per leaf, a bandwidth-bound pass instead of two latency-bound
+// triangular solves. The inverse is stored and applied in the working precision (FP32 in
+// mixed mode): a preconditioner only has to be a fixed linear operator close to A^-1, and
+// right-preconditioned GMRES measures convergence on the true residual of A.
 //
 // Diagonal ("d"): the 2x2 blocks [[A11_ii, A12_ii], [A21_ii, A22_ii]] of every element.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "kernels.cuh"
 #include "pb_internal.cuh"
 
-// Assemble the block of leaf c into W (2n rows, 4n columns: [M | I]).
-__global__ void k_blk_fill(const int* __restrict__ begin, const long long* __restrict__ woff,
+#define GJ_T 256
+#define GJ_SMEM_BYTES (200 * 1024)
+
+// Assemble the block of leaf c, row-major m x m, into minv + moff[c].
+template <class R>
+__global__ void k_blk_fill(const int* __restrict__ begin, const long long* __restrict__ moff,
                            const double4_32a* __restrict__ ep, const double4_32a* __restrict__ en,
                            const int* __restrict__ toff, const int* __restrict__ tj,
-                           const double* __restrict__ corr, double eps, double kappa, double* __restrict__ W)
+                           const double* __restrict__ corr, double eps, double kappa, R* __restrict__ minv)
 {
     const int c = blockIdx.x;
-    const int b = begin[c], n = begin[c + 1] - begin[c], m = 2 * n, ld = 4 * n;
-    double* Wc = W + woff[c];
+    const int b = begin[c], n = begin[c + 1] - begin[c], m = 2 * n;
+    R* Mc = minv + moff[c];
     const double inv_eps = 1.0 / eps;
-    for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
-        int i = (int)(t / n), j = (int)(t % n);
-        double4_32a pi = ep[b + i], pj = ep[b + j], ni = en[b + i], nj = en[b + j];
-        double I[4] = {0, 0, 0, 0};
-        if (i != j) {
-            double K[4];
-            pb_kernels<double>(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, ni.x, ni.y, ni.z, nj.x, nj.y, nj.z, eps,
-                               inv_eps, kappa, K);
-            for (int q = 0; q < 4; ++q) I[q] = pi.w * pj.w * K[q];
-        }
-        Wc[(size_t)i * ld + j] = -I[1];
-        Wc[(size_t)i * ld + n + j] = -I[0];
-        Wc[(size_t)(n + i) * ld + j] = -I[3];
-        Wc[(size_t)(n + i) * ld + n + j] = -I[2];
-        Wc[(size_t)i * ld + m + j] = (i == j);
-        Wc[(size_t)i * ld + m + n + j] = 0.0;
-        Wc[(size_t)(n + i) * ld + m + j] = 0.0;
-        Wc[(size_t)(n + i) * ld + m + n + j] = (i == j);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double A = ep[b + i].w;
-        Wc[(size_t)i * ld + i] += 0.5 * (1.0 + eps) * A;
-        Wc[(size_t)(n + i) * ld + n + i] += 0.5 * (1.0 + inv_eps) * A;
-        for (int t = toff[b + i]; t < toff[b + i + 1]; ++t) {
-            int j = tj[t] - b;
-            if (j < 0 || j >= n) continue;
-            Wc[(size_t)i * ld + j] -= corr[4 * t + 1];
-            Wc[(size_t)i * ld + n + j] -= corr[4 * t];
-            Wc[(size_t)(n + i) * ld + j] -= corr[4 * t + 3];
-            Wc[(size_t)(n + i) * ld + n + j] -= corr[4 * t + 2];
+    for (int i = threadIdx.x / 32; i < n; i += blockDim.x / 32) {
+        double4_32a pi = ep[b + i], ni = en[b + i];
+        for (int j = threadIdx.x & 31; j < n; j += 32) {
+            double4_32a pj = ep[b + j], nj = en[b + j];
+            double I[4] = {0, 0, 0, 0};
+            if (i != j) {
+                double K[4];
+                pb_kernels<double>(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, ni.x, ni.y, ni.z, nj.x, nj.y, nj.z, eps,
+                                   inv_eps, kappa, K);
+                for (int q = 0; q < 4; ++q) I[q] = pi.w * pj.w * K[q];
+            }
+            // Sauter-Schwab correction if (i, j) touch (lists are short and sorted)
+            for (int t = toff[b + i]; t < toff[b + i + 1]; ++t)
+                if (tj[t] == b + j)
+                    for (int q = 0; q < 4; ++q) I[q] += corr[4 * t + q];
+            double m11 = -I[1], m12 = -I[0], m21 = -I[3], m22 = -I[2];
+            if (i == j) {
+                m11 += 0.5 * (1.0 + eps) * pi.w;
+                m22 += 0.5 * (1.0 + inv_eps) * pi.w;
+            }
+            Mc[(size_t)i * m + j] = (R)m11;
+            Mc[(size_t)i * m + n + j] = (R)m12;
+            Mc[(size_t)(n + i) * m + j] = (R)m21;
+            Mc[(size_t)(n + i) * m + n + j] = (R)m22;
         }
     }
 }
 
-// Gauss-Jordan with partial pivoting on [M | I] -> [I | M^-1]; copies M^-1 to minv.
-__global__ void __launch_bounds__(256) k_blk_invert(const int* __restrict__ begin, const long long* __restrict__ woff,
-                                                    const long long* __restrict__ moff, double* __restrict__ W,
-                                                    double* __restrict__ minv, int* __restrict__ singular)
+// In-place Gauss-Jordan inversion with partial pivoting. Blocks with m <= mfit are worked
+// on in shared memory; larger ones in place in global memory (L2 resident).
+template <class R>
+__global__ void __launch_bounds__(GJ_T) k_blk_gj(const int* __restrict__ begin, const long long* __restrict__ moff,
+                                                 R* __restrict__ minv, int mcap, int mfit, int* __restrict__ singular)
 {
-    __shared__ double sv[256];
-    __shared__ int si[256];
-    __shared__ double prow_scale;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ R sv[GJ_T];
+    __shared__ int si[GJ_T];
+    R* colk = (R*)dsm;
+    R* rowk = colk + mcap;
+    int* perm = (int*)(rowk + mcap);
+    R* smat = (R*)(perm + mcap + (mcap & 1)) ;
     const int c = blockIdx.x;
-    const int n = begin[c + 1] - begin[c], m = 2 * n, ld = 4 * n;
-    double* Wc = W + woff[c];
+    const int m = 2 * (begin[c + 1] - begin[c]);
+    R* g = minv + moff[c];
+    const bool in_smem = m <= mfit;
+    R* a = in_smem ? smat : g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x / 32, nw = GJ_T / 32;
+    if (in_smem)
+        for (int t = threadIdx.x; t < m * m; t += GJ_T) a[t] = g[t];
+    __syncthreads();
     for (int k = 0; k < m; ++k) {
-        // pivot search in column k, rows k..m-1
-        double best = -1.0;
+        R best = R(-1);
         int bi = k;
-        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
-            double v = fabs(Wc[(size_t)i * ld + k]);
+        for (int i = k + threadIdx.x; i < m; i += GJ_T) {
+            R v = fabs(a[(size_t)i * m + k]);
             if (v > best) {
                 best = v;
                 bi = i;
@@ -86,9 +97,9 @@ __global__ void __launch_bounds__(256) k_blk_invert(const int* __restrict__ begi
         sv[threadIdx.x] = best;
         si[threadIdx.x] = bi;
         __syncthreads();
-        for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        for (int h = GJ_T / 2; h > 0; h >>= 1) {
             if (threadIdx.x < h) {
-                double o = sv[threadIdx.x + h];
+                R o = sv[threadIdx.x + h];
                 int oi = si[threadIdx.x + h];
                 if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
                     sv[threadIdx.x] = o;
@@ -97,61 +108,72 @@ __global__ void __launch_bounds__(256) k_blk_invert(const int* __restrict__ begi
             }
             __syncthreads();
         }
-        const int piv = si[0];
-        if (threadIdx.x == 0) {
-            double pv = Wc[(size_t)piv * ld + k];
-            if (!(fabs(pv) > 0.0)) {
-                atomicExch(singular, 1);
-                pv = 1.0;
+        const int p = si[0];
+        if (threadIdx.x == 0) perm[k] = p;
+        if (p != k)
+            for (int j = threadIdx.x; j < m; j += GJ_T) {
+                R t = a[(size_t)k * m + j];
+                a[(size_t)k * m + j] = a[(size_t)p * m + j];
+                a[(size_t)p * m + j] = t;
             }
-            prow_scale = 1.0 / pv;
+        __syncthreads();
+        R piv = a[(size_t)k * m + k];
+        if (!(fabs(piv) > R(0))) {
+            if (threadIdx.x == 0) atomicExch(singular, 1);
+            piv = R(1);
+        }
+        const R ip = R(1) / piv;
+        for (int j = threadIdx.x; j < m; j += GJ_T) {
+            R v = (j == k) ? ip : a[(size_t)k * m + j] * ip;
+            rowk[j] = v;
+            colk[j] = a[(size_t)j * m + k];
         }
         __syncthreads();
-        // swap rows k and piv, scale row k
-        for (int j = threadIdx.x; j < ld; j += blockDim.x) {
-            double a = Wc[(size_t)k * ld + j], b2 = Wc[(size_t)piv * ld + j];
-            if (piv != k) Wc[(size_t)piv * ld + j] = a;
-            Wc[(size_t)k * ld + j] = b2 * prow_scale;
+        for (int j = threadIdx.x; j < m; j += GJ_T) a[(size_t)k * m + j] = rowk[j];
+        for (int i = warp; i < m; i += nw) {
+            if (i == k) continue;
+            const R f = colk[i];
+            R* ai = a + (size_t)i * m;
+            for (int j = lane; j < m; j += 32) ai[j] = (j == k ? R(0) : ai[j]) - f * rowk[j];
         }
-        __syncthreads();
-        // eliminate column k from every other row
-        for (long long t = threadIdx.x; t < (long long)m * ld; t += blockDim.x) {
-            int i = (int)(t / ld), j = (int)(t % ld);
-            if (i == k || j < k) continue;
-            double f = Wc[(size_t)i * ld + k];
-            if (j == k) continue;
-            Wc[(size_t)i * ld + j] -= f * Wc[(size_t)k * ld + j];
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < m; i += blockDim.x)
-            if (i != k) Wc[(size_t)i * ld + k] = 0.0;
         __syncthreads();
     }
-    double* Mc = minv + moff[c];
-    for (long long t = threadIdx.x; t < (long long)m * m; t += blockDim.x) {
-        int i = (int)(t / m), j = (int)(t % m);
-        Mc[t] = Wc[(size_t)i * ld + m + j];
+    // undo the row interchanges as column interchanges, in reverse order
+    for (int i = threadIdx.x; i < m; i += GJ_T) {
+        R* ai = a + (size_t)i * m;
+        for (int k = m - 1; k >= 0; --k) {
+            int p = perm[k];
+            if (p != k) {
+                R t = ai[k];
+                ai[k] = ai[p];
+                ai[p] = t;
+            }
+        }
     }
+    __syncthreads();
+    if (in_smem)
+        for (int t = threadIdx.x; t < m * m; t += GJ_T) g[t] = a[t];
 }
 
 // z = M^-1 r per leaf: one warp per row, lanes stride the columns
+template <class R>
 __global__ void k_blk_apply(int nt, const int* __restrict__ begin, const long long* __restrict__ moff,
-                            const double* __restrict__ minv, const double* __restrict__ r, double* __restrict__ z)
+                            const R* __restrict__ minv, const double* __restrict__ r, double* __restrict__ z)
 {
     const int c = blockIdx.x;
     const int b = begin[c], n = begin[c + 1] - begin[c], m = 2 * n;
-    const double* Mc = minv + moff[c];
+    const R* Mc = minv + moff[c];
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31, nw = blockDim.x / 32;
     for (int i = warp; i < m; i += nw) {
-        double s = 0.0;
+        R s = 0;
         for (int j = lane; j < m; j += 32) {
             double rv = j < n ? r[b + j] : r[nt + b + j - n];
-            s += Mc[(size_t)i * m + j] * rv;
+            s += Mc[(size_t)i * m + j] * (R)rv;
         }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
-            if (i < n) z[b + i] = s;
-            else z[nt + b + i - n] = s;
+            if (i < n) z[b + i] = (double)s;
+            else z[nt + b + i - n] = (double)s;
         }
     }
 }
@@ -186,6 +208,33 @@ __global__ void k_diag_apply(int nt, const double* __restrict__ dinv, const doub
     z[nt + k] = dinv[4 * k + 2] * a + dinv[4 * k + 3] * b;
 }
 
+template <class R>
+static int blk_build(pb_ctx* c, const long long* dmoff, long long ntot, int mcap, int ncl)
+{
+    double eps = c->prm.eps_out / c->prm.eps_in;
+    const PbLevel& lv = c->lev[c->L];
+    R* M = (R*)pb_alloc(c, sizeof(R) * (size_t)ntot);
+    int* sing = (int*)pb_alloc(c, sizeof(int));
+    if (!M || !sing) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
+    c->minv = M;
+    k_blk_fill<R><<<ncl, 256, 0, c->st>>>(lv.begin, dmoff, c->e64p, c->e64n, c->touch_off, c->touch_j, c->corr, eps,
+                                           c->prm.kappa, M);
+    PB_LAUNCH(c);
+    // shared memory: col, row, perm (mcap each) + the block itself when it fits
+    size_t fixed = sizeof(R) * 2 * (size_t)mcap + sizeof(int) * ((size_t)mcap + 1) + 16;
+    int mfit = 0;
+    while ((size_t)(mfit + 1) * (mfit + 1) * sizeof(R) + fixed <= GJ_SMEM_BYTES) ++mfit;
+    size_t smem = fixed + (size_t)std::min(mfit, mcap) * std::min(mfit, mcap) * sizeof(R);
+    PB_CUDA(c, cudaFuncSetAttribute(k_blk_gj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_blk_gj<R><<<ncl, GJ_T, smem, c->st>>>(lv.begin, dmoff, M, mcap, std::min(mfit, mcap), sing);
+    PB_LAUNCH(c);
+    int hs = 0;
+    PB_CUDA(c, cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    if (hs) return pb_fail(c, PB_ERR_MESH, "a preconditioner block is singular");
+    return PB_OK;
+}
+
 int pb_precond_build(pb_ctx* c)
 {
     const int nt = c->nt;
@@ -202,36 +251,19 @@ int pb_precond_build(pb_ctx* c)
     std::vector<int> hb(lv.ncl + 1);
     PB_CUDA(c, cudaMemcpyAsync(hb.data(), lv.begin, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost, c->st));
     PB_CUDA(c, cudaStreamSynchronize(c->st));
-    std::vector<long long> woff(lv.ncl + 1), moff(lv.ncl + 1);
-    woff[0] = moff[0] = 0;
+    std::vector<long long> moff(lv.ncl + 1);
+    moff[0] = 0;
+    int mcap = 0;
     for (int k = 0; k < lv.ncl; ++k) {
-        long long n = hb[k + 1] - hb[k];
-        woff[k + 1] = woff[k] + (2 * n) * (4 * n);
-        moff[k + 1] = moff[k] + (2 * n) * (2 * n);
+        long long m = 2LL * (hb[k + 1] - hb[k]);
+        moff[k + 1] = moff[k] + m * m;
+        mcap = std::max(mcap, (int)m);
     }
-    long long* dwoff = (long long*)pb_alloc(c, sizeof(long long) * (lv.ncl + 1));
     c->blk_off = (long long*)pb_alloc(c, sizeof(long long) * (lv.ncl + 1));
-    c->minv = (double*)pb_alloc(c, sizeof(double) * moff[lv.ncl]);
-    int* sing = (int*)pb_alloc(c, sizeof(int));
-    double* W = nullptr;
-    if (!dwoff || !c->blk_off || !c->minv || !sing) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
-    if (cudaMallocAsync((void**)&W, sizeof(double) * woff[lv.ncl], c->st) != cudaSuccess) {
-        cudaGetLastError();
-        return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory (work)");
-    }
-    PB_CUDA(c, cudaMemcpyAsync(dwoff, woff.data(), sizeof(long long) * (lv.ncl + 1), cudaMemcpyHostToDevice, c->st));
+    if (!c->blk_off) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
     PB_CUDA(c, cudaMemcpyAsync(c->blk_off, moff.data(), sizeof(long long) * (lv.ncl + 1), cudaMemcpyHostToDevice, c->st));
-    k_blk_fill<<<lv.ncl, 256, 0, c->st>>>(lv.begin, dwoff, c->e64p, c->e64n, c->touch_off, c->touch_j, c->corr, eps,
-                                          c->prm.kappa, W);
-    PB_LAUNCH(c);
-    k_blk_invert<<<lv.ncl, 256, 0, c->st>>>(lv.begin, dwoff, c->blk_off, W, c->minv, sing);
-    PB_LAUNCH(c);
-    PB_CUDA(c, cudaFreeAsync(W, c->st));
-    int hs = 0;
-    PB_CUDA(c, cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    PB_CUDA(c, cudaStreamSynchronize(c->st));
-    if (hs) return pb_fail(c, PB_ERR_MESH, "a preconditioner block is singular");
-    return PB_OK;
+    if (c->prm.precision == PB_MIXED) return blk_build<float>(c, c->blk_off, moff[lv.ncl], mcap, lv.ncl);
+    return blk_build<double>(c, c->blk_off, moff[lv.ncl], mcap, lv.ncl);
 }
 
 int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z)
@@ -240,7 +272,10 @@ int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z)
     pb_tic(c, PB_T_PRECOND);
     if (c->prm.precond == PB_PRECOND_BLOCK) {
         const PbLevel& lv = c->lev[c->L];
-        k_blk_apply<<<lv.ncl, 256, 0, c->st>>>(nt, lv.begin, c->blk_off, c->minv, r, z);
+        if (c->prm.precision == PB_MIXED)
+            k_blk_apply<float><<<lv.ncl, 256, 0, c->st>>>(nt, lv.begin, c->blk_off, (const float*)c->minv, r, z);
+        else
+            k_blk_apply<double><<<lv.ncl, 256, 0, c->st>>>(nt, lv.begin, c->blk_off, (const double*)c->minv, r, z);
     } else if (c->prm.precond == PB_PRECOND_DIAG) {
         k_diag_apply<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->dinv, r, z);
     } else {

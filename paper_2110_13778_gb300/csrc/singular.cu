@@ -169,7 +169,7 @@ __device__ __forceinline__ double ss_weight(int shared, int s, double xi, double
 // One warp per touching pair (target k, source j). Lanes split the qs^4 cube points.
 __global__ void __launch_bounds__(256) k_singular(long long npairs, int nt, const int* __restrict__ toff,
                                                   const int* __restrict__ tj, const int* __restrict__ stris,
-                                                  const double* __restrict__ V,
+                                                  const int* __restrict__ order, const double* __restrict__ V,
                                                   const double4_32a* __restrict__ ep,
                                                   const double4_32a* __restrict__ en, int qs, double eps,
                                                   double kappa, double* __restrict__ corr)
@@ -185,6 +185,10 @@ __global__ void __launch_bounds__(256) k_singular(long long npairs, int nt, cons
         else hi = m;
     }
     int k = lo, j = tj[pair];
+    // One quadrature serves both orderings: it is laid out from the triangle with the smaller
+    // element index (shared vertices first, in that triangle's order); that warp writes the
+    // corrections of (k, j) and (j, k).
+    if (order[k] > order[j]) return;
     int ti[3] = {stris[3 * k], stris[3 * k + 1], stris[3 * k + 2]};
     int tjv[3] = {stris[3 * j], stris[3 * j + 1], stris[3 * j + 2]};
     // shared vertices first, in the same order for both triangles
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(256) k_singular(long long npairs, int nt, cons
         }
     double4_32a pi = ep[k], pj = ep[j], ni = en[k], nj = en[j];
     int nsub = ns == 3 ? 6 : (ns == 2 ? 5 : 2);
-    double acc[4] = {0, 0, 0, 0};
+    double acc[6] = {0, 0, 0, 0, 0, 0};
     int npts = qs * qs * qs * qs;
     double inv_eps = 1.0 / eps;
     for (int t = lane; t < npts; t += 32) {
@@ -233,20 +237,33 @@ __global__ void __launch_bounds__(256) k_singular(long long npairs, int nt, cons
                 double y = Q[0][e] + yh[0] * (Q[1][e] - Q[0][e]) + yh[1] * (Q[2][e] - Q[1][e]);
                 dv[e] = x - y;
             }
-            double K[4];
-            pb_kernels<double>(dv[0], dv[1], dv[2], ni.x, ni.y, ni.z, nj.x, nj.y, nj.z, eps, inv_eps, kappa, K);
-            for (int m = 0; m < 4; ++m) acc[m] += w * K[m];
+            double Pt[6];
+            pb_kernel_parts<double>(dv[0], dv[1], dv[2], ni.x, ni.y, ni.z, nj.x, nj.y, nj.z, kappa, Pt);
+            for (int m = 0; m < 6; ++m) acc[m] += w * Pt[m];
         }
     }
-    for (int m = 0; m < 4; ++m)
+    for (int m = 0; m < 6; ++m)
         for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
     if (lane == 0) {
         double jac = (2.0 * pi.w) * (2.0 * pj.w);
+        for (int m = 0; m < 6; ++m) acc[m] *= jac;
+        // (k, j): target k, source j
+        double Ikj[4] = {acc[0], eps * acc[3] - acc[2], -acc[4] + acc[5] * inv_eps, acc[1]};
         double reg[4] = {0, 0, 0, 0};
         if (k != j)
             pb_kernels<double>(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, ni.x, ni.y, ni.z, nj.x, nj.y, nj.z, eps,
                                inv_eps, kappa, reg);
-        for (int m = 0; m < 4; ++m) corr[4 * pair + m] = jac * acc[m] - pi.w * pj.w * reg[m];
+        for (int m = 0; m < 4; ++m) corr[4 * pair + m] = Ikj[m] - pi.w * pj.w * reg[m];
+        if (k != j) {
+            // (j, k): the same integrals with the roles of the normals exchanged
+            double Ijk[4] = {acc[0], acc[4] - eps * acc[5], acc[2] - acc[3] * inv_eps, acc[1]};
+            pb_kernels<double>(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z, nj.x, nj.y, nj.z, ni.x, ni.y, ni.z, eps,
+                               inv_eps, kappa, reg);
+            int q = toff[j];
+            while (q < toff[j + 1] && tj[q] != k) ++q;
+            if (q < toff[j + 1])
+                for (int m = 0; m < 4; ++m) corr[4 * (long long)q + m] = Ijk[m] - pi.w * pj.w * reg[m];
+        }
     }
 }
 
@@ -303,7 +320,7 @@ int pb_touching_and_singular(pb_ctx* c)
     PB_CUDA(c, cudaMemcpyToSymbolAsync(c_gx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, c->st));
     PB_CUDA(c, cudaMemcpyToSymbolAsync(c_gw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, c->st));
     double eps = c->prm.eps_out / c->prm.eps_in;
-    k_singular<<<nblk(htot, 8), 256, 0, c->st>>>(htot, nt, c->touch_off, c->touch_j, c->stris, c->verts, c->e64p,
+    k_singular<<<nblk(htot, 8), 256, 0, c->st>>>(htot, nt, c->touch_off, c->touch_j, c->stris, c->order, c->verts, c->e64p,
                                                  c->e64n, c->prm.qs, eps, c->prm.kappa, c->corr);
     PB_LAUNCH(c);
     return PB_OK;

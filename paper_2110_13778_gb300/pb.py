@@ -219,3 +219,4 @@ def pb_get_launch_count(ctx):
     n = ctypes.c_longlong()
     _check(ctx, lib().pb_get_launch_count(ctx, ctypes.byref(n)))
     return n.value
+

@@ -91,7 +91,7 @@ def test_all_near_fp64_equals_dense(sphere3):
         pb.pb_destroy(ctx)
 
 
-@pytest.mark.parametrize("p,adaptive", [(4, 0), (6, 0), (3, 1)])
+@pytest.mark.parametrize("p,adaptive", [(4, 0), (6, 0), (8, 0), (3, 1), (5, 0)])
 def test_fmm_fp64_matches_oracle_fmm(sphere3, p, adaptive):
     m, ph, A = sphere3
     ctx = _ctx(m, leaf_size=16, eta0=0.8, p=p, adaptive=adaptive, precision=pb.PB_FP64)
