@@ -180,6 +180,33 @@ int pb_get_timing(pb_ctx* ctx, double* out);
 /* Number of this library's kernel launches queued on ctx since it was created. */
 int pb_get_launch_count(pb_ctx* ctx, long long* out);
 
+/* Solvation energy for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that must not call
+ * cudaMalloc -- for example code that runs while a stream is being captured into a CUDA
+ * graph, where an allocation would break the capture, or a host that gives the library a
+ * fixed memory budget and forbids allocations after start-up. It computes the same energy
+ * as pb_solvation_energy, without a context, from caller-owned buffers, and allocates
+ * nothing: its only scratch (one partial sum per block of 256 triangles) lives in a fixed
+ * 64 KiB device array that every GPU loading this library holds until the process exits.
+ *
+ * verts (nv x 3 doubles), tris (nt x 3 int32), qpos (nc x 3 doubles), q (nc doubles) and
+ * x = [phi; dphi/dn] (2 nt doubles, element order): device pointers. E: device pointer to
+ * one double, written with the energy in kcal/mol. precision: PB_FP64 or PB_MIXED (FP32
+ * kernel evaluation, FP64 sums). stream: cudaStream_t (NULL = default stream); the call
+ * only queues work. errbuf/errlen: optional host buffer for a one-line reason on failure.
+ * Returns PB_ERR_ARG for nt > 2,097,152 (the fixed scratch limit) or bad arguments, and
+ * PB_ERR_CUDA if the launch fails.
+ *
+ * The first call on a device looks up the scratch array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call before any stream
+ * capture. Every call reuses the same array and leaves its partial sums there; calls that
+ * may overlap on the GPU (on different streams, or from several threads) race on it and
+ * must be serialised by the caller. */
+int pb_solvation_energy_noalloc(const double* verts, const int32_t* tris, int nt, const double* qpos,
+                                const double* q, int nc, double eps_in, double eps_out, double kappa,
+                                int precision, const double* x, double* E, void* stream, char* errbuf,
+                                int errlen);
 
 #ifdef __cplusplus
 }

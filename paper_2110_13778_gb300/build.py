@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpb.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["pb_api.cu", "tree.cu", "singular.cu", "nearfield.cu", "farfield.cu", "precond.cu", "krylov.cu"]
+SOURCES = ["pb_api.cu", "tree.cu", "singular.cu", "nearfield.cu", "farfield.cu", "precond.cu", "krylov.cu",
+           "noalloc.cu"]
 
 
 def nvcc():

@@ -23,7 +23,7 @@ EXPORTS = [
     "pb_create", "pb_destroy", "pb_last_error", "pb_mesh_upload", "pb_set_charges", "pb_build_tree",
     "pb_matvec", "pb_rhs", "pb_precond_apply", "pb_gmres_solve", "pb_solvation_energy",
     "pb_get_tree_stats", "pb_get_tree", "pb_matvec_part", "pb_set_timing", "pb_get_timing",
-    "pb_get_launch_count",
+    "pb_get_launch_count", "pb_solvation_energy_noalloc",
 ]
 
 
@@ -85,6 +85,8 @@ def lib():
         L.pb_set_timing.argtypes = [vp, c_int]
         L.pb_get_timing.argtypes = [vp, dp]
         L.pb_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.pb_solvation_energy_noalloc.argtypes = [vp, vp, c_int, vp, vp, c_int, c_double, c_double, c_double, c_int,
+                                                  vp, vp, vp, ctypes.c_char_p, c_int]
         _lib = L
     return _lib
 
@@ -220,3 +222,16 @@ def pb_get_launch_count(ctx):
     _check(ctx, lib().pb_get_launch_count(ctx, ctypes.byref(n)))
     return n.value
 
+
+def pb_solvation_energy_noalloc(verts, tris, qpos, q, x, E, eps_in=1.0, eps_out=80.0, kappa=0.1257,
+                                precision=PB_FP64, stream=0):
+    """Energy from caller-owned device tensors into the device scalar E; allocates nothing.
+    verts (nv, 3) float64, tris (nt, 3) int32, qpos (nc, 3) float64, q (nc,) float64,
+    x (2 nt,) float64, E (1,) float64 -- all contiguous CUDA tensors."""
+    err = ctypes.create_string_buffer(256)
+    nt = int(tris.shape[0])
+    nc = int(q.shape[0])
+    rc = lib().pb_solvation_energy_noalloc(_ptr(verts), _ptr(tris), nt, _ptr(qpos), _ptr(q), nc, eps_in, eps_out,
+                                           kappa, precision, _ptr(x), _ptr(E), ctypes.c_void_p(stream), err, 256)
+    if rc != PB_OK:
+        raise PBError(rc, err.value.decode())
