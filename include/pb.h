@@ -40,6 +40,7 @@ extern "C" {
 #define PB_ERR_NONFINITE 5      /* a NaN or Inf appeared in a residual */
 #define PB_ERR_STATE 6          /* call out of order (e.g. matvec before pb_build_tree) */
 #define PB_ERR_NOMEM 7          /* device allocation failed */
+#define PB_ERR_TIMEOUT 8        /* a bounded wait inside a kernel gave up (copy never landed) */
 
 #define PB_FP64 0  /* every step in double precision */
 #define PB_MIXED 1 /* near and far field in FP32 with FP64 leaf-sum accumulation; FP64
@@ -84,6 +85,7 @@ typedef struct pb_tree_stats {
     long long near_pairs; /* element pairs in the near field */
     long long touching;   /* ordered element pairs sharing a vertex (incl. i == j) */
     int max_leaf;         /* largest leaf */
+    long long touch_class[4]; /* ordered touching pairs sharing 1, 2, 3 vertices (index 0 unused) */
 } pb_tree_stats;
 
 /* Create a context. params is copied. stream is a cudaStream_t (may be NULL). */

@@ -22,12 +22,11 @@
 // The MtL sum is evaluated as  a! lam^a = sum_b D^{a+b} G(d) * [(-1)^|b| m^b / b!].
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "pb_internal.cuh"
 
-template <int P>
-struct M2LPassCount;
 #include "m2l_unrolled.cuh"
 
 #define FAR_T 128
@@ -80,9 +79,10 @@ __global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restr
             sw[threadIdx.x][1] = (R)(P.w * xs[nt + j]);  // A dphi
         }
         __syncthreads();
+#pragma unroll
         for (int r = 0; r < 4; ++r) {
             int al = threadIdx.x + r * FAR_T;
-            if (al >= T) break;
+            if (al >= T) continue;
             int a, bb, cc;
             mi_unpack(c_mi[al], a, bb, cc);
             R s0v = 0, skv = 0;
@@ -101,66 +101,75 @@ __global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restr
             acck[r] += skv;
         }
     }
+#pragma unroll
     for (int r = 0; r < 4; ++r) {
         int al = threadIdx.x + r * FAR_T;
-        if (al >= T) break;
+        if (al >= T) continue;
         sig0[(size_t)c * T + al] = acc0[r];
         sigk[(size_t)c * T + al] = acck[r];
     }
 }
 
 // ---------- step 3: MtM, children (order pc) into parent (order pp) ----------
+// One block per parent; work items (child, parent multi-index) are spread over the threads,
+// each child's contribution lands in its own shared-memory row and the rows are added in
+// child order, so the result does not depend on thread scheduling.
+#define M2M_T 256
 template <class R>
-__global__ void __launch_bounds__(FAR_T) k_m2m(int pp, int pc, const int* __restrict__ cbeg,
+__global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __restrict__ cbeg,
                                                const double* __restrict__ xp, const double* __restrict__ xch,
                                                const R* __restrict__ c0, const R* __restrict__ ck,
                                                R* __restrict__ s0, R* __restrict__ sk)
 {
-    __shared__ R tp[3][PB_PMAX + 1];
+    __shared__ R tp[8][3][PB_PMAX + 1];
     __shared__ R sbin[PB_PMAX + 1][PB_PMAX + 1];  // binomials, read with thread-dependent indices
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const int Tp = pb_nterms(pp), Tc = pb_nterms(pc);
+    R* part0 = (R*)dsm;       // [8][Tp]
+    R* partk = part0 + 8 * Tp;
     for (int t = threadIdx.x; t < (PB_PMAX + 1) * (PB_PMAX + 1); t += blockDim.x)
         sbin[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)] = (R)c_binom[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)];
     const int c = blockIdx.x;
-    const int Tp = pb_nterms(pp), Tc = pb_nterms(pc);
-    R a0[4] = {0, 0, 0, 0}, ak[4] = {0, 0, 0, 0};
-    for (int ch = cbeg[c]; ch < cbeg[c + 1]; ++ch) {
-        __syncthreads();
-        if (threadIdx.x < 3) {
-            R t = (R)(xch[3 * ch + threadIdx.x] - xp[3 * c + threadIdx.x]);
-            R v = 1;
-            for (int k = 0; k <= pp; ++k) {
-                tp[threadIdx.x][k] = v;
-                v *= t;
-            }
-        }
-        __syncthreads();
-        const R* m0 = c0 + (size_t)ch * Tc;
-        const R* mk = ck + (size_t)ch * Tc;
-        for (int r = 0; r < 4; ++r) {
-            int al = threadIdx.x + r * FAR_T;
-            if (al >= Tp) break;
-            int a1, a2, a3;
-            mi_unpack(c_mi[al], a1, a2, a3);
-            R v0 = 0, vk = 0;
-            for (int b1 = 0; b1 <= a1; ++b1)
-                for (int b2 = 0; b2 <= a2; ++b2)
-                    for (int b3 = 0; b3 <= a3; ++b3) {
-                        if (b1 + b2 + b3 > pc) continue;
-                        R w = sbin[a1][b1] * sbin[a2][b2] * sbin[a3][b3] * tp[0][a1 - b1] *
-                              tp[1][a2 - b2] * tp[2][a3 - b3];
-                        int pos = pb_midx(b1, b2, b3);
-                        v0 += w * m0[pos];
-                        vk += w * mk[pos];
-                    }
-            a0[r] += v0;
-            ak[r] += vk;
+    const int cb = cbeg[c], nch = min(cbeg[c + 1] - cb, 8);
+    for (int t = threadIdx.x; t < 3 * nch; t += blockDim.x) {
+        const int ch = t / 3, a = t % 3;
+        R v = 1, d = (R)(xch[3 * (cb + ch) + a] - xp[3 * c + a]);
+        for (int k = 0; k <= pp; ++k) {
+            tp[ch][a][k] = v;
+            v *= d;
         }
     }
-    for (int r = 0; r < 4; ++r) {
-        int al = threadIdx.x + r * FAR_T;
-        if (al >= Tp) break;
-        s0[(size_t)c * Tp + al] = a0[r];
-        sk[(size_t)c * Tp + al] = ak[r];
+    __syncthreads();
+    for (int w = threadIdx.x; w < nch * Tp; w += M2M_T) {
+        const int ch = w / Tp, al = w - ch * Tp;
+        int a1, a2, a3;
+        mi_unpack(c_mi[al], a1, a2, a3);
+        const R* m0 = c0 + (size_t)(cb + ch) * Tc;
+        const R* mk = ck + (size_t)(cb + ch) * Tc;
+        R v0 = 0, vk = 0;
+        for (int b1 = 0; b1 <= a1; ++b1)
+            for (int b2 = 0; b2 <= a2; ++b2) {
+                const R w12 = sbin[a1][b1] * sbin[a2][b2] * tp[ch][0][a1 - b1] * tp[ch][1][a2 - b2];
+                const int b3max = min(a3, pc - b1 - b2);
+                for (int b3 = 0; b3 <= b3max; ++b3) {
+                    const R wgt = w12 * sbin[a3][b3] * tp[ch][2][a3 - b3];
+                    const int pos = pb_midx(b1, b2, b3);
+                    v0 += wgt * m0[pos];
+                    vk += wgt * mk[pos];
+                }
+            }
+        part0[ch * Tp + al] = v0;
+        partk[ch * Tp + al] = vk;
+    }
+    __syncthreads();
+    for (int al = threadIdx.x; al < Tp; al += M2M_T) {
+        R v0 = 0, vk = 0;
+        for (int ch = 0; ch < nch; ++ch) {
+            v0 += part0[ch * Tp + al];
+            vk += partk[ch * Tp + al];
+        }
+        s0[(size_t)c * Tp + al] = v0;
+        sk[(size_t)c * Tp + al] = vk;
     }
 }
 
@@ -336,75 +345,190 @@ __global__ void __launch_bounds__(FAR_T) k_m2l_setup(int p, double kappa, const 
     }
 }
 
-// Contraction: one warp per target cluster, one lane per interaction slot; the local
-// coefficients of the pass live in registers (straight-line bodies of m2l_unrolled.cuh), the
-// 32 sources' scaled moments in shared memory ([b][33] per warp), the derivatives stream from
-// the slot layout. The per-lane partial sums are added across the warp at the end.
-#define M2LF_WARPS 4
-template <int P, class R>
-__global__ void __launch_bounds__(32 * M2LF_WARPS) k_m2l_fast(int ncl, const int* __restrict__ soff,
-                                                              const int* __restrict__ ssrc, const R* __restrict__ D0,
-                                                              const R* __restrict__ Dk, const R* __restrict__ s0,
-                                                              const R* __restrict__ sk, R* __restrict__ l0,
-                                                              R* __restrict__ lk)
+// Contraction, precomputed form: one warp per target cluster, one lane per interaction slot,
+// the order-P local coefficients of the lane in registers (straight-line bodies of
+// m2l_unrolled.cuh). Per chunk of 32 slots the derivative block D and the gathered scaled
+// moments M (both T x 32, contiguous) are read from shared memory; the per-lane partial sums
+// are added across the warp at the end.
+//
+// Scaled moments gathered into the chunk layout: M[((s / 32) * T + b) * 32 + s % 32] =
+// (-1)^|b| sigma^b(src(s)) / b!, zero for padding slots.
+template <class R>
+__global__ void k_m2l_gather(int T, const int* __restrict__ ssrc, const R* __restrict__ s0, const R* __restrict__ sk,
+                             R* __restrict__ M0, R* __restrict__ Mk)
 {
-    constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
-    extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ R sc[T];      // (-1)^|b| / b!
-    __shared__ R ifac[T];    // 1 / a!
-    const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-    R* Ms = (R*)dsm + (size_t)warp * T * 33;
-    for (int b = threadIdx.x; b < T; b += blockDim.x) {
+    // one block per chunk of 32 slots; thread (b, lane) pairs walk the T x 32 block
+    const long long chunk = blockIdx.x;
+    const size_t base = (size_t)chunk * T * 32;
+    for (int t = threadIdx.x; t < T * 32; t += blockDim.x) {
+        const int b = t >> 5, lane = t & 31;
+        const int src = ssrc[chunk * 32 + lane];
         int b1, b2, b3;
         mi_unpack(c_mi[b], b1, b2, b3);
-        double f = c_fact[b1] * c_fact[b2] * c_fact[b3];
-        sc[b] = (R)(((b1 + b2 + b3) & 1 ? -1.0 : 1.0) / f);
-        ifac[b] = (R)(1.0 / f);
+        const R sc = (R)(((b1 + b2 + b3) & 1 ? -1.0 : 1.0) / (c_fact[b1] * c_fact[b2] * c_fact[b3]));
+        M0[base + t] = src >= 0 ? s0[(size_t)src * T + b] * sc : R(0);
+        Mk[base + t] = src >= 0 ? sk[(size_t)src * T + b] * sc : R(0);
     }
-    __syncthreads();
-    const int c = blockIdx.x * M2LF_WARPS + warp;
-    if (c >= ncl) return;  // no block-wide barrier below this point
+}
+
+// warp-level sum of the lanes' coefficients, scaled by 1/a!, written to out[c * T + a]
+template <int P, class R>
+__device__ __forceinline__ void m2l_flush(R* L, R* scratch, R* __restrict__ out, int c, int lane)
+{
+    constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < T; ++i) scratch[i * 33 + lane] = L[i];
+    __syncwarp();
+    for (int i = lane; i < T; i += 32) {
+        R s = 0;
+        for (int l = 0; l < 32; ++l) s += scratch[i * 33 + l];
+        int a1, a2, a3;
+        mi_unpack(c_mi[i], a1, a2, a3);
+        out[(size_t)c * T + i] = s * (R)(1.0 / (c_fact[a1] * c_fact[a2] * c_fact[a3]));
+    }
+    __syncwarp();
+}
+
+// ---- TMA bulk copies and mbarriers (FP32 path) ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long* bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: gives up after PB_WAIT_LIMIT polls (each poll may itself block briefly)
+#define PB_WAIT_LIMIT (1u << 24)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase)
+{
+    for (unsigned it = 0; it < PB_WAIT_LIMIT; ++it)
+        if (mbar_try(bar, phase)) return true;
+    return false;
+}
+
+// FP32: one warp per block; D and M chunks arrive by TMA bulk copy into a double buffer,
+// the next chunk's copies in flight while the current chunk is contracted.
+template <int P>
+__global__ void __launch_bounds__(32, 1) k_m2l_tma(int ncl, const int* __restrict__ soff, const float* __restrict__ D0,
+                                                   const float* __restrict__ Dk, const float* __restrict__ M0,
+                                                   const float* __restrict__ Mk, float* __restrict__ l0,
+                                                   float* __restrict__ lk, int* __restrict__ err)
+{
+    constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
+    constexpr unsigned CH = T * 32 * sizeof(float);  // bytes of one chunk block (multiple of 16)
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) unsigned long long bar[2];
+    float* Ds = (float*)dsm;            // [2][T * 32]
+    float* Ms = Ds + 2 * T * 32;        // [2][T * 32]
+    const int lane = threadIdx.x;
+    const int c = blockIdx.x;
+    if (c >= ncl) return;
+    const int sb = soff[c], nch = (soff[c + 1] - sb) >> 5;
+    if (lane == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    unsigned ph0 = 0u, ph1 = 0u;  // parity of the next completion of each buffer's barrier
+    bool ok = true;
+#pragma unroll 1
+    for (int kern = 0; kern < 2; ++kern) {
+        const float* D = kern ? Dk : D0;
+        const float* M = kern ? Mk : M0;
+        float* out = kern ? lk : l0;
+        float L[T];
+#pragma unroll
+        for (int i = 0; i < T; ++i) L[i] = 0.f;
+        const size_t cb = (size_t)(sb >> 5);  // first chunk of this cluster
+        if (nch > 0 && lane == 0) {
+            // order the earlier shared-memory reads and writes (generic proxy) before the copies
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect(&bar[0], 2 * CH);
+            bulk_g2s(Ds, D + cb * T * 32, CH, &bar[0]);
+            bulk_g2s(Ms, M + cb * T * 32, CH, &bar[0]);
+        }
+#pragma unroll 1
+        for (int k = 0; k < nch; ++k) {
+            const int buf = k & 1;
+            if (k + 1 < nch && lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const int nb = buf ^ 1;
+                mbar_expect(&bar[nb], 2 * CH);
+                bulk_g2s(Ds + nb * T * 32, D + (cb + k + 1) * T * 32, CH, &bar[nb]);
+                bulk_g2s(Ms + nb * T * 32, M + (cb + k + 1) * T * 32, CH, &bar[nb]);
+            }
+            if (!mbar_wait(&bar[buf], buf ? ph1 : ph0)) {
+                ok = false;
+                break;
+            }
+            if (buf) ph1 ^= 1u;
+            else ph0 ^= 1u;
+            M2LBody<P, 0>::run(Ds + buf * T * 32 + lane, Ms + buf * T * 32 + lane, L);
+            __syncwarp();
+        }
+        if (!ok) break;
+        // the buffers are free again: reuse the first one as the reduction scratch
+        m2l_flush<P, float>(L, Ds, out, c, lane);
+    }
+    if (!ok) {
+        // a copy never completed: record it, give any copies in flight a bounded time to land
+        if (lane == 0) atomicExch(err, 1);
+        mbar_wait(&bar[0], ph0);
+        mbar_wait(&bar[1], ph1);
+    }
+}
+
+// FP64 (and fallback): D read from global memory, the moment chunk copied to shared memory.
+template <int P, class R>
+__global__ void __launch_bounds__(32) k_m2l_chunks(int ncl, const int* __restrict__ soff, const R* __restrict__ D0,
+                                                   const R* __restrict__ Dk, const R* __restrict__ M0,
+                                                   const R* __restrict__ Mk, R* __restrict__ l0, R* __restrict__ lk)
+{
+    constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    R* Ms = (R*)dsm;  // [T * 33] (also the reduction scratch)
+    const int lane = threadIdx.x;
+    const int c = blockIdx.x;
+    if (c >= ncl) return;
     const int sb = soff[c], se = soff[c + 1];
 #pragma unroll 1
     for (int kern = 0; kern < 2; ++kern) {
         const R* D = kern ? Dk : D0;
-        const R* sg = kern ? sk : s0;
+        const R* M = kern ? Mk : M0;
         R* out = kern ? lk : l0;
-#pragma unroll 1
-        for (int pass = 0; pass < M2LPassCount<P>::n; ++pass) {
-            R L[84];
+        R L[T];
 #pragma unroll
-            for (int i = 0; i < 84; ++i) L[i] = R(0);
+        for (int i = 0; i < T; ++i) L[i] = R(0);
 #pragma unroll 1
-            for (int s0i = sb; s0i < se; s0i += 32) {
-                const int my = ssrc[s0i + lane];
-                __syncwarp();
-                for (int q = 0; q < 32; ++q) {
-                    const int src = __shfl_sync(0xffffffffu, my, q);
-                    for (int b = lane; b < T; b += 32) Ms[b * 33 + q] = src >= 0 ? sg[(size_t)src * T + b] * sc[b] : R(0);
-                }
-                __syncwarp();
-                const R* Dl = D + ((size_t)(s0i >> 5) * T) * 32 + lane;
-                const R* Ml = Ms + lane;
-                if (pass == 0) M2LBody<P, 0>::run(Dl, Ml, L);
-                if constexpr (M2LPassCount<P>::n > 1) {
-                    if (pass == 1) M2LBody<P, (M2LPassCount<P>::n > 1 ? 1 : 0)>::run(Dl, Ml, L);
-                }
-            }
-            // sum the lanes' partial coefficients through shared memory
-            const int a0 = pass * 84, a1 = min(T, a0 + 84);
+        for (int s = sb; s < se; s += 32) {
+            const R* Mc = M + (size_t)(s >> 5) * T * 32;
             __syncwarp();
-#pragma unroll
-            for (int i = 0; i < 84; ++i)
-                if (a0 + i < a1) Ms[i * 33 + lane] = L[i];
+            for (int t = lane; t < T * 32; t += 32) Ms[t] = Mc[t];
             __syncwarp();
-            for (int i = lane; i < a1 - a0; i += 32) {
-                R s = 0;
-                for (int l = 0; l < 32; ++l) s += Ms[i * 33 + l];
-                out[(size_t)c * T + a0 + i] = s * ifac[a0 + i];
-            }
-            __syncwarp();
+            M2LBody<P, 0>::run(D + (size_t)(s >> 5) * T * 32 + lane, Ms + lane, L);
         }
+        m2l_flush<P, R>(L, Ms, out, c, lane);
     }
 }
 
@@ -498,7 +622,6 @@ __global__ void __launch_bounds__(FAR_T) k_l2p(int nt, int p, double eps, const 
     }
 }
 
-static bool g_tables = false;
 
 static int upload_tables(pb_ctx* c)
 {
@@ -542,7 +665,10 @@ static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
     lv.slot_src = (int*)pb_alloc(c, sizeof(int) * (lv.nslots + 1));
     lv.D0 = pb_alloc(c, rs * (size_t)lv.nslots * T);
     lv.Dk = pb_alloc(c, rs * (size_t)lv.nslots * T);
-    if (!lv.slot_off || !lv.slot_src || !lv.D0 || !lv.Dk) return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
+    lv.Mg0 = pb_alloc(c, rs * (size_t)lv.nslots * T);
+    lv.Mgk = pb_alloc(c, rs * (size_t)lv.nslots * T);
+    if (!lv.slot_off || !lv.slot_src || !lv.D0 || !lv.Dk || !lv.Mg0 || !lv.Mgk)
+        return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
     PB_CUDA(c, cudaMemcpyAsync(lv.slot_off, soff.data(), sizeof(int) * (lv.ncl + 1), cudaMemcpyHostToDevice, c->st));
     PB_CUDA(c, cudaMemcpyAsync(lv.slot_src, ssrc.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, c->st));
     if (c->prm.precision == PB_MIXED)
@@ -561,12 +687,22 @@ template <int P, class R>
 static int m2l_fast_launch(pb_ctx* c, PbLevel& lv)
 {
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
-    size_t smem = sizeof(R) * (size_t)M2LF_WARPS * T * 33;
-    PB_CUDA(c, cudaFuncSetAttribute(k_m2l_fast<P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int grid = (lv.ncl + M2LF_WARPS - 1) / M2LF_WARPS;
-    k_m2l_fast<P, R><<<grid, 32 * M2LF_WARPS, smem, c->st>>>(lv.ncl, lv.slot_off, lv.slot_src, (const R*)lv.D0,
-                                                             (const R*)lv.Dk, (const R*)lv.sig0, (const R*)lv.sigk,
-                                                             (R*)lv.lam0, (R*)lv.lamk);
+    k_m2l_gather<R><<<(unsigned)(lv.nslots / 32), 256, 0, c->st>>>(T, lv.slot_src, (const R*)lv.sig0,
+                                                                   (const R*)lv.sigk, (R*)lv.Mg0, (R*)lv.Mgk);
+    PB_LAUNCH(c);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        size_t smem = 4 * (size_t)T * 32 * sizeof(float);
+        PB_CUDA(c, cudaFuncSetAttribute(k_m2l_tma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_m2l_tma<P><<<lv.ncl, 32, smem, c->st>>>(lv.ncl, lv.slot_off, (const float*)lv.D0, (const float*)lv.Dk,
+                                                   (const float*)lv.Mg0, (const float*)lv.Mgk, (float*)lv.lam0,
+                                                   (float*)lv.lamk, c->dev_err);
+    } else {
+        size_t smem = (size_t)T * 33 * sizeof(R);
+        PB_CUDA(c, cudaFuncSetAttribute(k_m2l_chunks<P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_m2l_chunks<P, R><<<lv.ncl, 32, smem, c->st>>>(lv.ncl, lv.slot_off, (const R*)lv.D0, (const R*)lv.Dk,
+                                                        (const R*)lv.Mg0, (const R*)lv.Mgk, (R*)lv.lam0,
+                                                        (R*)lv.lamk);
+    }
     PB_LAUNCH(c);
     return PB_OK;
 }
@@ -575,7 +711,6 @@ int pb_far_setup(pb_ctx* c)
 {
     int rc = upload_tables(c);
     if (rc) return rc;
-    g_tables = true;
     size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
     for (int l = 1; l <= c->L; ++l) {
         PbLevel& lv = c->lev[l];
@@ -609,7 +744,9 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys)
     for (int l = L - 1; l >= 1; --l) {
         PbLevel& lv = c->lev[l];
         PbLevel& ch = c->lev[l + 1];
-        k_m2m<R><<<lv.ncl, FAR_T, 0, c->st>>>(lv.p, ch.p, lv.cbeg, lv.xc, ch.xc, (R*)ch.sig0, (R*)ch.sigk,
+        const size_t msm = 2 * 8 * (size_t)pb_nterms(lv.p) * sizeof(R);
+        PB_CUDA(c, cudaFuncSetAttribute(k_m2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm));
+        k_m2m<R><<<lv.ncl, M2M_T, msm, c->st>>>(lv.p, ch.p, lv.cbeg, lv.xc, ch.xc, (R*)ch.sig0, (R*)ch.sigk,
                                               (R*)lv.sig0, (R*)lv.sigk);
         PB_LAUNCH(c);
     }

@@ -27,29 +27,38 @@ struct PbKer<float> {
     static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 };
 
-// g(t) = exp(-t) - 1 + t, and E = exp(-t) - 1
+// g(t) = exp(-t) - 1 + t, and E = exp(-t) - 1.
+// FP32: below t = 0.125 both come from the Taylor series of g (terms to t^8, truncation
+// below 1e-9 relative), E = g - t; above it from exp directly. The two are evaluated
+// branch-free and selected, so a warp never diverges on t.
+// FP64: exp(-t) - 1 and E + t lose at most ~1e-16/t and ~1e-16/t^2 relative, which stays far
+// below the quadrature error at the separations the singular rules sample.
 template <class R>
-__device__ __forceinline__ void pb_screen(R t, R& E, R& g)
+__device__ __forceinline__ void pb_screen(R t, R& E, R& g);
+
+template <>
+__device__ __forceinline__ void pb_screen<float>(float t, float& E, float& g)
 {
-    E = PbKer<R>::expm1_(-t);
-    if (t < R(0.125)) {
-        // t^2/2 - t^3/6 + t^4/24 - ... (terms to t^13; below 1e-17 relative at t = 0.125)
-        R s = R(-1.0 / 6227020800.0);               // -1/13!
-        s = s * t + R(1.0 / 479001600.0);           // 1/12!
-        s = s * t + R(-1.0 / 39916800.0);
-        s = s * t + R(1.0 / 3628800.0);
-        s = s * t + R(-1.0 / 362880.0);
-        s = s * t + R(1.0 / 40320.0);
-        s = s * t + R(-1.0 / 5040.0);
-        s = s * t + R(1.0 / 720.0);
-        s = s * t + R(-1.0 / 120.0);
-        s = s * t + R(1.0 / 24.0);
-        s = s * t + R(-1.0 / 6.0);
-        s = s * t + R(0.5);
-        g = s * t * t;
-    } else {
-        g = E + t;
-    }
+    float s = -1.0f / 40320.0f;        // -1/8! ... the series of g / t^2
+    s = fmaf(s, t, 1.0f / 5040.0f);
+    s = fmaf(s, t, -1.0f / 720.0f);
+    s = fmaf(s, t, 1.0f / 120.0f);
+    s = fmaf(s, t, -1.0f / 24.0f);
+    s = fmaf(s, t, 1.0f / 6.0f);
+    s = fmaf(s, t, -0.5f);
+    // s now holds -(g / t^2) up to the sign convention of the alternating series
+    float gs = -s * t * t;
+    float ed = __expf(-t) - 1.0f;
+    bool small = t < 0.125f;
+    g = small ? gs : ed + t;
+    E = small ? gs - t : ed;
+}
+
+template <>
+__device__ __forceinline__ void pb_screen<double>(double t, double& E, double& g)
+{
+    E = exp(-t) - 1.0;
+    g = E + t;
 }
 
 // K[0..3] = K1..K4 for d = x - y, target normal n_x, source normal n_y.

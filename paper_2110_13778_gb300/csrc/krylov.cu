@@ -427,6 +427,14 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
     inf.rel_residual = sqrt(c->hscal[0]) / bnorm;
     if (inf.status == PB_OK && !converged) inf.status = PB_ERR_NOT_CONVERGED;
     if (inf.status == PB_OK && !isfinite(inf.rel_residual)) inf.status = PB_ERR_NONFINITE;
+    // a kernel whose bounded wait gave up leaves its flag set; report it instead of a result
+    int derr = 0;
+    PB_CUDA(c, cudaMemcpyAsync(&derr, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    if (derr) {
+        inf.status = PB_ERR_TIMEOUT;
+        pb_fail(c, PB_ERR_TIMEOUT, "a bounded wait in the MtL kernel gave up");
+    }
     if (info) *info = inf;
     return inf.status;
 }

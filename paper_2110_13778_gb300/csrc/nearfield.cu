@@ -16,6 +16,8 @@
 // carried as FP32 hi + lo pairs so that d = (x_hi - y_hi) + (x_lo - y_lo) keeps the
 // separation of close elements to FP32 relative accuracy instead of losing digits to the
 // size of the coordinates.
+#include <vector>
+
 #include "kernels.cuh"
 #include "pb_internal.cuh"
 
@@ -108,6 +110,80 @@ __global__ void __launch_bounds__(NEAR_T) k_near(int nt, const int* __restrict__
     }
 }
 
+// ---------- mixed precision near field ----------
+// Per matrix-vector product the sources are packed once as FP32 records
+// (x_hi, y_hi, z_hi, A phi), (n_x, n_y, n_z, A dphi) beside the fixed (x_lo, y_lo, z_lo).
+__global__ void k_near_pack(int nt, const float4* __restrict__ e32p, const float4* __restrict__ e32n,
+                            const double* __restrict__ xs, float4* __restrict__ sp, float4* __restrict__ sn)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    float4 p = e32p[k], n = e32n[k];
+    double A = (double)p.w;
+    sp[k] = make_float4(p.x, p.y, p.z, (float)(A * xs[k]));
+    sn[k] = make_float4(n.x, n.y, n.z, (float)(A * xs[nt + k]));
+}
+
+// One warp per chunk of up to 32 targets of a leaf; every lane walks the same sources of the
+// leaf's neighbour list, so source records are warp-uniform loads (one L1 transaction each)
+// and no block-wide synchronisation is needed.
+__global__ void __launch_bounds__(256, 3) k_near32(int nt, int nchunks, const int* __restrict__ chunk_leaf,
+                                                const int* __restrict__ chunk_first,
+                                                const int* __restrict__ begin, const int* __restrict__ noff,
+                                                const int* __restrict__ nidx, const float4* __restrict__ sp,
+                                                const float4* __restrict__ sn, const float4* __restrict__ sl,
+                                                const double* __restrict__ xs, double eps_d, double kappa_d,
+                                                double* __restrict__ ys)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nchunks) return;
+    const int c = chunk_leaf[w];
+    const int k = chunk_first[w] + lane;
+    const bool act = k < begin[c + 1];
+    const int kk = act ? k : chunk_first[w];
+    const float4 tp = sp[kk], tn = sn[kk], tl = sl[kk];
+    const float eps = (float)eps_d, inv_eps = (float)(1.0 / eps_d), kappa = (float)kappa_d;
+    double acc1 = 0.0, acc2 = 0.0;
+    for (int t = noff[c]; t < noff[c + 1]; ++t) {
+        const int c2 = nidx[t];
+        const int sb = begin[c2], se = begin[c2 + 1];
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
+        for (int j = sb; j < se; ++j) {
+            const float4 a = sp[j], b = sn[j], l = sl[j];
+            float K[4];
+            float dx = (tp.x - a.x) + (tl.x - l.x);
+            float dy = (tp.y - a.y) + (tl.y - l.y);
+            float dz = (tp.z - a.z) + (tl.z - l.z);
+            if (j == k) dx = 1.0f;  // the identical pair is the correction's; keep r finite
+            pb_kernels<float>(dx, dy, dz, tn.x, tn.y, tn.z, b.x, b.y, b.z, eps, inv_eps, kappa, K);
+            float u1 = K[0] * b.w + K[1] * a.w;
+            float u2 = K[2] * b.w + K[3] * a.w;
+            s1 += (j == k) ? 0.f : u1;
+            s2 += (j == k) ? 0.f : u2;
+        }
+        acc1 += (double)s1;
+        acc2 += (double)s2;
+    }
+    if (act) {
+        // raw sums; k_near_finish applies A_k and the mass terms in FP64
+        ys[k] = acc1;
+        ys[nt + k] = acc2;
+    }
+}
+
+// y1 = 1/2 (1 + eps) A phi - A acc1, y2 = 1/2 (1 + 1/eps) A dphi - A acc2 (FP64)
+__global__ void k_near_finish(int nt, const double4_32a* __restrict__ ep, const double* __restrict__ xs,
+                              double eps, double* __restrict__ ys)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    double A = ep[k].w;
+    ys[k] = 0.5 * (1.0 + eps) * A * xs[k] - A * ys[k];
+    ys[nt + k] = 0.5 * (1.0 + 1.0 / eps) * A * xs[nt + k] - A * ys[nt + k];
+}
+
 // Sauter-Schwab corrections of identical and adjacent pairs (FP64)
 __global__ void k_corrections(int nt, const int* __restrict__ toff, const int* __restrict__ tj,
                               const double* __restrict__ corr, const double* __restrict__ xs,
@@ -126,15 +202,47 @@ __global__ void k_corrections(int nt, const int* __restrict__ toff, const int* _
     ys[nt + k] -= y2;
 }
 
+// chunks of at most 32 targets per leaf and the packed source buffers (mixed precision)
+int pb_near_setup(pb_ctx* c)
+{
+    if (c->prm.precision != PB_MIXED) return PB_OK;
+    const PbLevel& lv = c->lev[c->L];
+    std::vector<int> b(lv.ncl + 1);
+    PB_CUDA(c, cudaMemcpyAsync(b.data(), lv.begin, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    std::vector<int> cl, cf;
+    for (int k = 0; k < lv.ncl; ++k)
+        for (int s = b[k]; s < b[k + 1]; s += 32) {
+            cl.push_back(k);
+            cf.push_back(s);
+        }
+    c->nchunks = (int)cl.size();
+    c->chunk_leaf = (int*)pb_alloc(c, sizeof(int) * cl.size());
+    c->chunk_first = (int*)pb_alloc(c, sizeof(int) * cf.size());
+    c->near_sp = (float4*)pb_alloc(c, sizeof(float4) * c->nt);
+    c->near_sn = (float4*)pb_alloc(c, sizeof(float4) * c->nt);
+    if (!c->chunk_leaf || !c->chunk_first || !c->near_sp || !c->near_sn)
+        return pb_fail(c, PB_ERR_NOMEM, "near setup: out of memory");
+    PB_CUDA(c, cudaMemcpyAsync(c->chunk_leaf, cl.data(), sizeof(int) * cl.size(), cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(c->chunk_first, cf.data(), sizeof(int) * cf.size(), cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    return PB_OK;
+}
+
 int pb_near_apply(pb_ctx* c, const double* xs, double* ys)
 {
     const PbLevel& lv = c->lev[c->L];
     double eps = c->prm.eps_out / c->prm.eps_in;
-    if (c->prm.precision == PB_MIXED)
-        k_near<float, float4, true><<<lv.ncl, NEAR_T, 0, c->st>>>(c->nt, lv.begin, lv.near_off, lv.near_idx,
-                                                                  c->e32p, c->e32n, c->e32l, xs, eps, c->prm.kappa,
-                                                                  ys);
-    else
+    if (c->prm.precision == PB_MIXED) {
+        const int nt = c->nt;
+        k_near_pack<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->e32p, c->e32n, xs, c->near_sp, c->near_sn);
+        PB_LAUNCH(c);
+        k_near32<<<(c->nchunks * 32 + 255) / 256, 256, 0, c->st>>>(nt, c->nchunks, c->chunk_leaf, c->chunk_first,
+                                                                    lv.begin, lv.near_off, lv.near_idx, c->near_sp,
+                                                                    c->near_sn, c->e32l, xs, eps, c->prm.kappa, ys);
+        PB_LAUNCH(c);
+        k_near_finish<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->e64p, xs, eps, ys);
+    } else
         k_near<double, double4_32a, false><<<lv.ncl, NEAR_T, 0, c->st>>>(c->nt, lv.begin, lv.near_off,
                                                                          lv.near_idx, c->e64p, c->e64n, nullptr, xs,
                                                                          eps, c->prm.kappa, ys);

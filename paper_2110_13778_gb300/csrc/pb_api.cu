@@ -21,12 +21,13 @@ void* pb_alloc(pb_ctx* c, size_t bytes, bool build_lifetime)
 {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    // stream-ordered allocation from the context's pool, which keeps released memory for reuse
+    if (cudaMallocFromPoolAsync(&p, bytes, c->pool, c->st) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
     if (cudaMemsetAsync(p, 0, bytes, c->st) != cudaSuccess) {
-        cudaFree(p);
+        cudaFreeAsync(p, c->st);
         return nullptr;
     }
     (build_lifetime ? c->build_allocs : c->mesh_allocs).push_back(p);
@@ -36,8 +37,7 @@ void* pb_alloc(pb_ctx* c, size_t bytes, bool build_lifetime)
 // drop everything pb_build_tree made (tree, lists, integrals, factors, work vectors)
 static void pb_free_build(pb_ctx* c)
 {
-    cudaStreamSynchronize(c->st);
-    for (void* p : c->build_allocs) cudaFree(p);
+    for (void* p : c->build_allocs) cudaFreeAsync(p, c->st);
     c->build_allocs.clear();
     c->built = false;
     c->gm_m = 0;
@@ -50,7 +50,7 @@ static void pb_free_build(pb_ctx* c)
 static void pb_free_mesh(pb_ctx* c)
 {
     pb_free_build(c);
-    for (void* p : c->mesh_allocs) cudaFree(p);
+    for (void* p : c->mesh_allocs) cudaFreeAsync(p, c->st);
     c->mesh_allocs.clear();
     c->verts = c->qpos = c->q = nullptr;
     c->tris = nullptr;
@@ -78,6 +78,20 @@ extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
         return PB_ERR_NOMEM;
     }
     c->hscal = (double*)h;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    if (cudaMemPoolCreate(&c->pool, &pp) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(h);
+        delete c;
+        return PB_ERR_NOMEM;
+    }
+    unsigned long long keep = ~0ULL;  // never hand released blocks back to the driver early
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     for (int i = 0; i < 10; ++i) cudaEventCreate(&c->ev[i]);
     *out = c;
     return PB_OK;
@@ -86,9 +100,10 @@ extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
 extern "C" int pb_destroy(pb_ctx* c)
 {
     if (!c) return PB_OK;
+    for (void* p : c->mesh_allocs) cudaFreeAsync(p, c->st);
+    for (void* p : c->build_allocs) cudaFreeAsync(p, c->st);
     cudaStreamSynchronize(c->st);
-    for (void* p : c->mesh_allocs) cudaFree(p);
-    for (void* p : c->build_allocs) cudaFree(p);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
     for (int i = 0; i < 10; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->tev_ready)
@@ -168,6 +183,8 @@ extern "C" int pb_build_tree(pb_ctx* c)
     if (!c->verts) return pb_fail(c, PB_ERR_STATE, "build_tree before mesh_upload");
     pb_free_build(c);
     int rc;
+    c->dev_err = (int*)pb_alloc(c, sizeof(int));
+    if (!c->dev_err) return pb_fail(c, PB_ERR_NOMEM, "build_tree: out of memory");
     pb_tic(c, PB_T_TREE);
     if ((rc = pb_geometry_and_tree(c))) return rc;
     pb_toc(c, PB_T_TREE);
@@ -175,6 +192,7 @@ extern "C" int pb_build_tree(pb_ctx* c)
     if ((rc = pb_touching_and_singular(c))) return rc;
     pb_toc(c, PB_T_SINGULAR);
     if ((rc = pb_far_setup(c))) return rc;
+    if ((rc = pb_near_setup(c))) return rc;
     pb_tic(c, PB_T_PCBUILD);
     if ((rc = pb_precond_build(c))) return rc;
     pb_toc(c, PB_T_PCBUILD);
@@ -296,7 +314,7 @@ extern "C" int pb_gmres_solve(pb_ctx* c, double* x, double tol, int max_iter, in
     }
     pb_solve_info loc;
     if ((rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc)) &&
-        rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE)
+        rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE && rc != PB_ERR_TIMEOUT)
         return rc;
     int rc2 = pb_scatter(c, c->xs, x);
     if (info) *info = loc;
@@ -329,6 +347,7 @@ extern "C" int pb_get_tree_stats(pb_ctx* c, pb_tree_stats* s)
     }
     s->near_pairs = c->near_pairs;
     s->touching = c->ntouch;
+    for (int q = 0; q < 4; ++q) s->touch_class[q] = c->touch_class[q];
     s->max_leaf = c->max_leaf;
     return PB_OK;
 }

@@ -51,6 +51,8 @@ struct PbLevel {
     long long nslots = 0;
     void* D0 = nullptr;      // derivatives of G0, working precision
     void* Dk = nullptr;      // derivatives of Gk
+    void* Mg0 = nullptr;     // scaled source moments gathered into the slot layout (per product)
+    void* Mgk = nullptr;
 };
 
 struct pb_ctx {
@@ -58,6 +60,7 @@ struct pb_ctx {
     cudaStream_t st = nullptr;
     std::string err = "no error";
     bool dead = false;
+    cudaMemPool_t pool = nullptr;    // device memory pool of this context
     std::vector<void*> build_allocs; // freed on a new build or upload
     std::vector<void*> mesh_allocs;  // freed on a new upload
     // mesh
@@ -84,14 +87,23 @@ struct pb_ctx {
     float4* e32n = nullptr;
     float4* e32l = nullptr;   // low parts: centroid - (double)hi, so hi + lo carries ~48 bits
     int* stris = nullptr;     // [3 nt] vertex indices in sorted order
+    // mixed-precision near field: target chunks (<= 32 per leaf) and packed source records
+    int nchunks = 0;
+    int* chunk_leaf = nullptr;
+    int* chunk_first = nullptr;
+    float4* near_sp = nullptr;  // (x_hi, y_hi, z_hi, A phi)
+    float4* near_sn = nullptr;  // (n_x, n_y, n_z, A dphi)
     // touching pairs (share >= 1 vertex, incl. i == j), CSR by sorted target position
     int* touch_off = nullptr; // [nt + 1]
     int* touch_j = nullptr;   // sorted source position
     double* corr = nullptr;   // [4 * ntouch] exact integral minus one-point rule (I1..I4)
     long long ntouch = 0;
+    long long touch_class[4] = {0, 0, 0, 0};  // ordered pairs sharing 0..3 vertices
     long long near_pairs = 0;
     // preconditioner: per leaf a dense (2n x 2n) inverse, unknowns [phi of leaf; dphi of leaf]
-    long long* blk_off = nullptr; // [ncl_L + 1] offsets into minv
+    int npcblk = 0;               // preconditioner blocks
+    int* pc_begin = nullptr;      // [npcblk + 1] first sorted element of each block
+    long long* blk_off = nullptr; // [npcblk + 1] offsets into minv
     void* minv = nullptr;         // inverse blocks, working precision (float in mixed mode)
     double* dinv = nullptr;       // [4 nt] inverse 2x2 blocks for PB_PRECOND_DIAG
     // work vectors in sorted order
@@ -110,6 +122,7 @@ struct pb_ctx {
     int tcount[PB_TIMING_SLOTS] = {};
     bool tev_ready = false;
     long long nlaunch = 0;  // kernels of this library launched on this context
+    int* dev_err = nullptr; // set by a kernel whose bounded wait gave up (device, build lifetime)
 };
 
 inline void pb_tic(pb_ctx* c, int slot)
@@ -146,6 +159,7 @@ void* pb_alloc(pb_ctx* c, size_t bytes, bool build_lifetime = true);
 // translation-unit entry points
 int pb_geometry_and_tree(pb_ctx* c);          // tree.cu
 int pb_touching_and_singular(pb_ctx* c);      // singular.cu
+int pb_near_setup(pb_ctx* c);                                      // nearfield.cu
 int pb_near_apply(pb_ctx* c, const double* xs, double* ys);        // nearfield.cu (writes ys)
 int pb_corr_apply(pb_ctx* c, const double* xs, double* ys);        // nearfield.cu (adds)
 int pb_far_setup(pb_ctx* c);                                       // farfield.cu

@@ -22,6 +22,7 @@
 
 #define GJ_T 256
 #define GJ_SMEM_BYTES (200 * 1024)
+#define PB_PC_BMAX 96  // largest preconditioner block, in elements
 
 // Assemble the block of leaf c, row-major m x m, into minv + moff[c].
 template <class R>
@@ -94,20 +95,27 @@ __global__ void __launch_bounds__(GJ_T) k_blk_gj(const int* __restrict__ begin, 
                 bi = i;
             }
         }
-        sv[threadIdx.x] = best;
-        si[threadIdx.x] = bi;
-        __syncthreads();
-        for (int h = GJ_T / 2; h > 0; h >>= 1) {
-            if (threadIdx.x < h) {
-                R o = sv[threadIdx.x + h];
-                int oi = si[threadIdx.x + h];
-                if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
-                    sv[threadIdx.x] = o;
-                    si[threadIdx.x] = oi;
-                }
+        for (int o = 16; o > 0; o >>= 1) {
+            R ov = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
             }
-            __syncthreads();
         }
+        if (lane == 0) {
+            sv[warp] = best;
+            si[warp] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < nw; ++q)
+                if (sv[q] > sv[0] || (sv[q] == sv[0] && si[q] < si[0])) {
+                    sv[0] = sv[q];
+                    si[0] = si[q];
+                }
+        }
+        __syncthreads();
         const int p = si[0];
         if (threadIdx.x == 0) perm[k] = p;
         if (p != k)
@@ -212,12 +220,11 @@ template <class R>
 static int blk_build(pb_ctx* c, const long long* dmoff, long long ntot, int mcap, int ncl)
 {
     double eps = c->prm.eps_out / c->prm.eps_in;
-    const PbLevel& lv = c->lev[c->L];
     R* M = (R*)pb_alloc(c, sizeof(R) * (size_t)ntot);
     int* sing = (int*)pb_alloc(c, sizeof(int));
     if (!M || !sing) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
     c->minv = M;
-    k_blk_fill<R><<<ncl, 256, 0, c->st>>>(lv.begin, dmoff, c->e64p, c->e64n, c->touch_off, c->touch_j, c->corr, eps,
+    k_blk_fill<R><<<ncl, 256, 0, c->st>>>(c->pc_begin, dmoff, c->e64p, c->e64n, c->touch_off, c->touch_j, c->corr, eps,
                                            c->prm.kappa, M);
     PB_LAUNCH(c);
     // shared memory: col, row, perm (mcap each) + the block itself when it fits
@@ -226,7 +233,7 @@ static int blk_build(pb_ctx* c, const long long* dmoff, long long ntot, int mcap
     while ((size_t)(mfit + 1) * (mfit + 1) * sizeof(R) + fixed <= GJ_SMEM_BYTES) ++mfit;
     size_t smem = fixed + (size_t)std::min(mfit, mcap) * std::min(mfit, mcap) * sizeof(R);
     PB_CUDA(c, cudaFuncSetAttribute(k_blk_gj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_blk_gj<R><<<ncl, GJ_T, smem, c->st>>>(lv.begin, dmoff, M, mcap, std::min(mfit, mcap), sing);
+    k_blk_gj<R><<<ncl, GJ_T, smem, c->st>>>(c->pc_begin, dmoff, M, mcap, std::min(mfit, mcap), sing);
     PB_LAUNCH(c);
     int hs = 0;
     PB_CUDA(c, cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -247,23 +254,41 @@ int pb_precond_build(pb_ctx* c)
         return PB_OK;
     }
     if (c->prm.precond != PB_PRECOND_BLOCK) return PB_OK;
+    // blocks: the leaves of the tree; a leaf with more than PB_PC_BMAX elements is split into
+    // nearly equal consecutive (Morton-ordered) parts of at most PB_PC_BMAX elements
     const PbLevel& lv = c->lev[c->L];
     std::vector<int> hb(lv.ncl + 1);
     PB_CUDA(c, cudaMemcpyAsync(hb.data(), lv.begin, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost, c->st));
     PB_CUDA(c, cudaStreamSynchronize(c->st));
-    std::vector<long long> moff(lv.ncl + 1);
+    std::vector<int> pb_;
+    for (int k = 0; k < lv.ncl; ++k) {
+        int n = hb[k + 1] - hb[k];
+        int parts = (n + PB_PC_BMAX - 1) / PB_PC_BMAX;
+        int base = n / parts, extra = n % parts, s = hb[k];
+        for (int q = 0; q < parts; ++q) {
+            pb_.push_back(s);
+            s += base + (q < extra ? 1 : 0);
+        }
+    }
+    pb_.push_back(nt);
+    const int nb = (int)pb_.size() - 1;
+    std::vector<long long> moff(nb + 1);
     moff[0] = 0;
     int mcap = 0;
-    for (int k = 0; k < lv.ncl; ++k) {
-        long long m = 2LL * (hb[k + 1] - hb[k]);
+    for (int k = 0; k < nb; ++k) {
+        long long m = 2LL * (pb_[k + 1] - pb_[k]);
         moff[k + 1] = moff[k] + m * m;
         mcap = std::max(mcap, (int)m);
     }
-    c->blk_off = (long long*)pb_alloc(c, sizeof(long long) * (lv.ncl + 1));
-    if (!c->blk_off) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
-    PB_CUDA(c, cudaMemcpyAsync(c->blk_off, moff.data(), sizeof(long long) * (lv.ncl + 1), cudaMemcpyHostToDevice, c->st));
-    if (c->prm.precision == PB_MIXED) return blk_build<float>(c, c->blk_off, moff[lv.ncl], mcap, lv.ncl);
-    return blk_build<double>(c, c->blk_off, moff[lv.ncl], mcap, lv.ncl);
+    c->npcblk = nb;
+    c->pc_begin = (int*)pb_alloc(c, sizeof(int) * (nb + 1));
+    c->blk_off = (long long*)pb_alloc(c, sizeof(long long) * (nb + 1));
+    if (!c->blk_off || !c->pc_begin) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
+    PB_CUDA(c, cudaMemcpyAsync(c->pc_begin, pb_.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(c->blk_off, moff.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice, c->st));
+    int rc = c->prm.precision == PB_MIXED ? blk_build<float>(c, c->blk_off, moff[nb], mcap, nb)
+                                          : blk_build<double>(c, c->blk_off, moff[nb], mcap, nb);
+    return rc;  // blk_build synchronises before the host vectors go out of scope
 }
 
 int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z)
@@ -271,11 +296,11 @@ int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z)
     const int nt = c->nt;
     pb_tic(c, PB_T_PRECOND);
     if (c->prm.precond == PB_PRECOND_BLOCK) {
-        const PbLevel& lv = c->lev[c->L];
         if (c->prm.precision == PB_MIXED)
-            k_blk_apply<float><<<lv.ncl, 256, 0, c->st>>>(nt, lv.begin, c->blk_off, (const float*)c->minv, r, z);
+            k_blk_apply<float><<<c->npcblk, 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off, (const float*)c->minv, r, z);
         else
-            k_blk_apply<double><<<lv.ncl, 256, 0, c->st>>>(nt, lv.begin, c->blk_off, (const double*)c->minv, r, z);
+            k_blk_apply<double><<<c->npcblk, 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off, (const double*)c->minv, r,
+                                                              z);
     } else if (c->prm.precond == PB_PRECOND_DIAG) {
         k_diag_apply<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->dinv, r, z);
     } else {

@@ -117,6 +117,22 @@ __global__ void k_touch(int nt, const int* __restrict__ stris, const int* __rest
     for (int q = 0; q < n; ++q) tj[off[k] + q] = cand[q];
 }
 
+__global__ void k_touch_classes(int nt, const int* __restrict__ toff, const int* __restrict__ tj,
+                                const int* __restrict__ stris, unsigned long long* __restrict__ cls)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    unsigned long long n[4] = {0, 0, 0, 0};
+    for (int t = toff[k]; t < toff[k + 1]; ++t) {
+        int j = tj[t], s = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) s += stris[3 * k + a] == stris[3 * j + b];
+        n[s > 3 ? 3 : s]++;
+    }
+    for (int q = 1; q < 4; ++q)
+        if (n[q]) atomicAdd(&cls[q], n[q]);
+}
+
 // ---------- Sauter-Schwab sub-maps (reference triangle {0 <= e2 <= e1 <= 1}) ----------
 // Each writes xhat, yhat and the Jacobian weight of sub-map s at cube point (xi, h1, h2, h3).
 __device__ __forceinline__ int ss_map(int shared, int s, double xi, double h1, double h2, double h3,
@@ -219,27 +235,42 @@ __global__ void __launch_bounds__(256) k_singular(long long npairs, int nt, cons
             Q[a][d] = V[3 * oj[a] + d];
         }
     double4_32a pi = ep[k], pj = ep[j], ni = en[k], nj = en[j];
-    int nsub = ns == 3 ? 6 : (ns == 2 ? 5 : 2);
+    // Identical flat triangle: (x - y) is tangent, so the normal-derivative parts vanish and
+    // K1, K4 depend on |x - y| only; the six sub-maps pair up under xhat <-> yhat (1-2, 3-4,
+    // 5-6), so sub-maps 1, 3, 5 are evaluated with weight 2.
+    const bool ident = ns == 3;
+    const int nsub = ident ? 3 : (ns == 2 ? 5 : 2);
     double acc[6] = {0, 0, 0, 0, 0, 0};
     int npts = qs * qs * qs * qs;
     double inv_eps = 1.0 / eps;
+    double eP[2][3], eQ[2][3], d0[3];
+    for (int e = 0; e < 3; ++e) {
+        eP[0][e] = P[1][e] - P[0][e];
+        eP[1][e] = P[2][e] - P[1][e];
+        eQ[0][e] = Q[1][e] - Q[0][e];
+        eQ[1][e] = Q[2][e] - Q[1][e];
+        d0[e] = P[0][e] - Q[0][e];
+    }
     for (int t = lane; t < npts; t += 32) {
         int a = t % qs, b = (t / qs) % qs, cc = (t / (qs * qs)) % qs, d = t / (qs * qs * qs);
         double xi = c_gx[a], h1 = c_gx[b], h2 = c_gx[cc], h3 = c_gx[d];
         double wq = c_gw[a] * c_gw[b] * c_gw[cc] * c_gw[d];
         for (int s = 0; s < nsub; ++s) {
+            const int sm = ident ? 2 * s : s;
             double xh[2], yh[2];
-            ss_map(ns, s, xi, h1, h2, h3, xh, yh);
-            double w = wq * ss_weight(ns, s, xi, h1, h2);
+            ss_map(ns, sm, xi, h1, h2, h3, xh, yh);
+            double w = wq * ss_weight(ns, sm, xi, h1, h2) * (ident ? 2.0 : 1.0);
             double dv[3];
-            for (int e = 0; e < 3; ++e) {
-                double x = P[0][e] + xh[0] * (P[1][e] - P[0][e]) + xh[1] * (P[2][e] - P[1][e]);
-                double y = Q[0][e] + yh[0] * (Q[1][e] - Q[0][e]) + yh[1] * (Q[2][e] - Q[1][e]);
-                dv[e] = x - y;
-            }
+            for (int e = 0; e < 3; ++e)
+                dv[e] = d0[e] + xh[0] * eP[0][e] + xh[1] * eP[1][e] - yh[0] * eQ[0][e] - yh[1] * eQ[1][e];
             double Pt[6];
             pb_kernel_parts<double>(dv[0], dv[1], dv[2], ni.x, ni.y, ni.z, nj.x, nj.y, nj.z, kappa, Pt);
-            for (int m = 0; m < 6; ++m) acc[m] += w * Pt[m];
+            if (ident) {
+                acc[0] += w * Pt[0];
+                acc[1] += w * Pt[1];
+            } else {
+                for (int m = 0; m < 6; ++m) acc[m] += w * Pt[m];
+            }
         }
     }
     for (int m = 0; m < 6; ++m)
@@ -314,6 +345,17 @@ int pb_touching_and_singular(pb_ctx* c)
     if (!c->touch_j || !c->corr) return pb_fail(c, PB_ERR_NOMEM, "touching: out of memory");
     k_touch<1><<<nblk(nt, 128), 128, 0, c->st>>>(nt, c->stris, voff, vlist, nullptr, c->touch_off, c->touch_j, bad);
     PB_LAUNCH(c);
+    {
+        // ordered touching pairs by number of shared vertices (for the work counts of reports)
+        unsigned long long* cls = (unsigned long long*)pb_alloc(c, sizeof(unsigned long long) * 4);
+        if (!cls) return pb_fail(c, PB_ERR_NOMEM, "touching: out of memory");
+        k_touch_classes<<<nblk(nt, 128), 128, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->stris, cls);
+        PB_LAUNCH(c);
+        unsigned long long h[4];
+        PB_CUDA(c, cudaMemcpyAsync(h, cls, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+        PB_CUDA(c, cudaStreamSynchronize(c->st));
+        for (int q = 0; q < 4; ++q) c->touch_class[q] = (long long)h[q];
+    }
     // Gauss-Legendre rule of the 4-cube
     double gx[8] = {0}, gw[8] = {0};
     gauss01(c->prm.qs, gx, gw);

@@ -15,7 +15,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpb.so")
 
-PB_OK, PB_ERR_ARG, PB_ERR_MESH, PB_ERR_CUDA, PB_ERR_NOT_CONVERGED, PB_ERR_NONFINITE, PB_ERR_STATE, PB_ERR_NOMEM = range(8)
+(PB_OK, PB_ERR_ARG, PB_ERR_MESH, PB_ERR_CUDA, PB_ERR_NOT_CONVERGED, PB_ERR_NONFINITE, PB_ERR_STATE, PB_ERR_NOMEM,
+ PB_ERR_TIMEOUT) = range(9)
 PB_FP64, PB_MIXED = 0, 1
 PB_PRECOND_NONE, PB_PRECOND_DIAG, PB_PRECOND_BLOCK = 0, 1, 2
 
@@ -51,7 +52,7 @@ class pb_tree_stats(ctypes.Structure):
     _fields_ = [
         ("levels", ctypes.c_int), ("nclusters", ctypes.c_int * 11), ("nnear", ctypes.c_longlong * 11),
         ("ninter", ctypes.c_longlong * 11), ("order", ctypes.c_int * 11), ("near_pairs", ctypes.c_longlong),
-        ("touching", ctypes.c_longlong), ("max_leaf", ctypes.c_int),
+        ("touching", ctypes.c_longlong), ("max_leaf", ctypes.c_int), ("touch_class", ctypes.c_longlong * 4),
     ]
 
 
@@ -183,6 +184,7 @@ def pb_get_tree_stats(ctx):
         "order": list(s.order[: L + 1]),
         "near_pairs": s.near_pairs,
         "touching": s.touching,
+        "touch_class": list(s.touch_class),
         "max_leaf": s.max_leaf,
     }
 
