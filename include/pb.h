@@ -136,6 +136,17 @@ int pb_precond_apply(pb_ctx* ctx, const double* r, double* z);
 int pb_gmres_solve(pb_ctx* ctx, double* x, double tol, int max_iter, int restart, int use_x0,
                    pb_solve_info* info);
 
+/* Solve for several charge states of the uploaded charge positions on one built mesh: the
+ * geometry (tree, singular integrals, preconditioner, MtL tables) is built once and shared
+ * by all states. q: host pointer, nrhs x nc doubles (state s at q + s nc). X: device
+ * pointer, nrhs x 2N doubles (state s at X + 2 N s), written with the solutions. E: host
+ * pointer, nrhs doubles, written with the solvation energies in kcal/mol (may be NULL).
+ * warm != 0 starts each state's GMRES from the previous state's solution (state 0 from
+ * zero). infos: host pointer to nrhs records (may be NULL). On return the uploaded charges
+ * are those of the last state. Synchronises. */
+int pb_solve_states(pb_ctx* ctx, const double* q, int nrhs, double* X, double* E, double tol, int max_iter,
+                    int restart, int warm, pb_solve_info* infos);
+
 /* Electrostatic solvation energy (eqsolengdis) for x = [phi; dphi/dn] in kcal/mol, using
  * the factor 4 pi 332.0716 of Section 3. x: device pointer. E_kcal: host pointer.
  * Synchronises. */

@@ -13,39 +13,55 @@
 #define KB 256
 
 // ---------- right-hand side: b1 = A S1(c), b2 = A S2(c) ----------
+// FP64: every pair in double precision. Mixed: pair terms in FP32 with hi + lo coordinates
+// (separations keep FP32 relative accuracy), each tile of charges summed in FP32 and added
+// into FP64 accumulators.
+template <class R>
 __global__ void k_rhs(int nt, int nc, const double4_32a* __restrict__ ep, const double4_32a* __restrict__ en,
                       const double* __restrict__ qpos, const double* __restrict__ q, double eps1,
                       double* __restrict__ b)
 {
-    __shared__ double sq[KB][4];
+    __shared__ R sh[KB][3], sl[KB][3], sq[KB];
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     double4_32a p = make_double4_32a(0, 0, 0, 0), n = p;
     if (k < nt) {
         p = ep[k];
         n = en[k];
     }
+    const R ph[3] = {(R)p.x, (R)p.y, (R)p.z};
+    const R pl[3] = {(R)(p.x - (double)ph[0]), (R)(p.y - (double)ph[1]), (R)(p.z - (double)ph[2])};
+    const R nx = (R)n.x, ny = (R)n.y, nz = (R)n.z;
     double s1 = 0.0, s2 = 0.0;
     const double i4pi = 0.07957747154594767;
     for (int t0 = 0; t0 < nc; t0 += KB) {
         __syncthreads();
         if (t0 + threadIdx.x < nc) {
             int t = t0 + threadIdx.x;
-            sq[threadIdx.x][0] = qpos[3 * t];
-            sq[threadIdx.x][1] = qpos[3 * t + 1];
-            sq[threadIdx.x][2] = qpos[3 * t + 2];
-            sq[threadIdx.x][3] = q[t];
+            for (int a = 0; a < 3; ++a) {
+                double v = qpos[3 * t + a];
+                R hv = (R)v;
+                sh[threadIdx.x][a] = hv;
+                sl[threadIdx.x][a] = (R)(v - (double)hv);
+            }
+            sq[threadIdx.x] = (R)q[t];
         }
         __syncthreads();
         int m = min(KB, nc - t0);
-        if (k < nt)
+        if (k < nt) {
+            R a1 = 0, a2 = 0;
             for (int t = 0; t < m; ++t) {
-                double dx = p.x - sq[t][0], dy = p.y - sq[t][1], dz = p.z - sq[t][2];
-                double r2 = dx * dx + dy * dy + dz * dz;
-                double ri = rsqrt(r2);
-                double nd = n.x * dx + n.y * dy + n.z * dz;
-                s1 += sq[t][3] * ri;
-                s2 -= sq[t][3] * nd * ri * ri * ri;  // dG0/dn_x = -(n.d)/(4 pi r^3)
+                R dx = (ph[0] - sh[t][0]) + (pl[0] - sl[t][0]);
+                R dy = (ph[1] - sh[t][1]) + (pl[1] - sl[t][1]);
+                R dz = (ph[2] - sh[t][2]) + (pl[2] - sl[t][2]);
+                R r2 = dx * dx + dy * dy + dz * dz;
+                R ri = PbKer<R>::rsqrt_(r2);
+                R nd = nx * dx + ny * dy + nz * dz;
+                a1 += sq[t] * ri;
+                a2 -= sq[t] * nd * ri * ri * ri;  // dG0/dn_x = -(n.d)/(4 pi r^3)
             }
+            s1 += (double)a1;
+            s2 += (double)a2;
+        }
     }
     if (k < nt) {
         b[k] = p.w * s1 * i4pi / eps1;
@@ -57,7 +73,12 @@ int pb_rhs_sorted(pb_ctx* c, double* bs)
 {
     int nt = c->nt;
     pb_tic(c, PB_T_RHS);
-    k_rhs<<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q, c->prm.eps_in, bs);
+    if (c->prm.precision == PB_MIXED)
+        k_rhs<float><<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q, c->prm.eps_in,
+                                                           bs);
+    else
+        k_rhs<double><<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q,
+                                                            c->prm.eps_in, bs);
     PB_LAUNCH(c);
     pb_toc(c, PB_T_RHS);
     return PB_OK;

@@ -322,6 +322,40 @@ extern "C" int pb_gmres_solve(pb_ctx* c, double* x, double tol, int max_iter, in
     return rc;
 }
 
+extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, double* E, double tol,
+                               int max_iter, int restart, int warm, pb_solve_info* infos)
+{
+    PB_ALIVE(c);
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "solve_states before build_tree");
+    if (!q || !X || nrhs < 1 || !(tol > 0) || max_iter < 1 || restart < 1 || restart > 200)
+        return pb_fail(c, PB_ERR_ARG, "solve_states: bad arguments");
+    for (long long k = 0; k < (long long)nrhs * c->nc; ++k)
+        if (!isfinite(q[k])) return pb_fail(c, PB_ERR_MESH, "charge state value %lld not finite", k);
+    const size_t n2 = 2 * (size_t)c->nt;
+    int worst = PB_OK;
+    for (int s = 0; s < nrhs; ++s) {
+        if (c->nc > 0)
+            PB_CUDA(c, cudaMemcpyAsync(c->q, q + (size_t)s * c->nc, sizeof(double) * c->nc, cudaMemcpyHostToDevice,
+                                       c->st));
+        int rc;
+        if ((rc = pb_rhs_sorted(c, c->ws))) return rc;
+        if (!(warm && s > 0)) PB_CUDA(c, cudaMemsetAsync(c->xs, 0, sizeof(double) * n2, c->st));
+        pb_solve_info loc;
+        rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc);
+        if (rc && rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE && rc != PB_ERR_TIMEOUT) return rc;
+        if (rc && worst == PB_OK) worst = rc;
+        if (infos) infos[s] = loc;
+        if ((rc = pb_scatter(c, c->xs, X + (size_t)s * n2))) return rc;
+        if (E) {
+            double e = 0.0;
+            if ((rc = pb_energy_sorted(c, c->xs, &e))) return rc;
+            E[s] = e;
+        }
+    }
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    return worst;
+}
+
 extern "C" int pb_solvation_energy(pb_ctx* c, const double* x, double* E)
 {
     PB_ALIVE(c);

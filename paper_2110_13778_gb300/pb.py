@@ -24,7 +24,7 @@ EXPORTS = [
     "pb_create", "pb_destroy", "pb_last_error", "pb_mesh_upload", "pb_set_charges", "pb_build_tree",
     "pb_matvec", "pb_rhs", "pb_precond_apply", "pb_gmres_solve", "pb_solvation_energy",
     "pb_get_tree_stats", "pb_get_tree", "pb_matvec_part", "pb_set_timing", "pb_get_timing",
-    "pb_get_launch_count", "pb_solvation_energy_noalloc",
+    "pb_get_launch_count", "pb_solvation_energy_noalloc", "pb_solve_states",
 ]
 
 
@@ -81,6 +81,8 @@ def lib():
         L.pb_precond_apply.argtypes = [vp, vp, vp]
         L.pb_gmres_solve.argtypes = [vp, vp, c_double, c_int, c_int, c_int, ctypes.POINTER(pb_solve_info)]
         L.pb_solvation_energy.argtypes = [vp, vp, dp]
+        L.pb_solve_states.argtypes = [vp, dp, c_int, vp, dp, c_double, c_int, c_int, c_int,
+                                      ctypes.POINTER(pb_solve_info)]
         L.pb_get_tree_stats.argtypes = [vp, ctypes.POINTER(pb_tree_stats)]
         L.pb_get_tree.argtypes = [vp, ip, ip, ip, ip, ip, ip]
         L.pb_set_timing.argtypes = [vp, c_int]
@@ -164,6 +166,21 @@ def pb_gmres_solve(ctx, x, tol=1e-6, max_iter=200, restart=50, use_x0=False, rai
     if rc != PB_OK and (raise_on_fail or rc not in (PB_ERR_NOT_CONVERGED, PB_ERR_NONFINITE)):
         _check(ctx, rc)
     return info
+
+
+def pb_solve_states(ctx, q_states, X, tol=1e-6, max_iter=200, restart=50, warm=True, raise_on_fail=True):
+    """Solve nrhs charge states on one built mesh. q_states: (nrhs, nc) host array;
+    X: (nrhs, 2N) float64 CUDA tensor (overwritten). Returns (energies, infos)."""
+    Q = np.ascontiguousarray(q_states, dtype=np.float64)
+    nrhs = Q.shape[0]
+    E = np.zeros(nrhs)
+    infos = (pb_solve_info * nrhs)()
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib().pb_solve_states(ctx, Q.ctypes.data_as(dp), nrhs, _ptr(X), E.ctypes.data_as(dp), tol, max_iter,
+                               restart, int(bool(warm)), infos)
+    if rc != PB_OK and (raise_on_fail or rc not in (PB_ERR_NOT_CONVERGED, PB_ERR_NONFINITE)):
+        _check(ctx, rc)
+    return E, list(infos)
 
 
 def pb_solvation_energy(ctx, x):

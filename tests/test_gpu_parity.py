@@ -147,7 +147,7 @@ def test_rhs_and_energy_match_oracle(sphere3):
             b = torch.empty(2 * m.nt, device="cuda", dtype=torch.float64)
             pb.pb_rhs(ctx, b)
             bo = dense.rhs(m, ph)
-            assert _rel(b.cpu().numpy(), bo) < 1e-12
+            assert _rel(b.cpu().numpy(), bo) < tol
             x = np.linalg.solve(A, bo)
             E = pb.pb_solvation_energy(ctx, _dev(x))
             Eo = dense.energy(m, ph, x)
