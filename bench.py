@@ -63,7 +63,9 @@ def args_parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "molecule", "batch"])
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "molecule", "batch", "learned"])
+    ap.add_argument("--train-molecules", type=int, default=48)
+    ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--atoms", type=int, default=2000)
     ap.add_argument("--grid", type=float, default=0.9)
     ap.add_argument("--molecules", type=int, default=8)
@@ -479,12 +481,103 @@ def run_batch(a):
     return 0
 
 
+def run_learned(a):
+    """Learned warm start against a zero start, and both against plain FP64 from zero.
+
+    Training (untimed): `train-molecules` protein-like molecules of 50-500 atoms (log-uniform),
+    each solved from zero by the mixed-precision solver; the network (18 -> 128 -> 128 -> 128
+    -> 2, BF16 tensor-core kernels) is fitted to their scaled solutions by Adam. Evaluation:
+    the `atoms`-atom molecule, three arms per step, each pb_build_tree + solve to `tol` +
+    energy: mixed precision from the learned start (network inference included), mixed from
+    zero, FP64 from zero. value = the learned arm's time per solve."""
+    rank, world, local = dist_setup(a.gpus)
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_2110_13778_gb300 import build, molecules, pb, warmstart
+
+    build.build()
+    stream = torch.cuda.current_stream().cuda_stream
+    rng = np.random.default_rng(6000 + rank)
+    counts = np.exp(rng.uniform(np.log(50), np.log(500), a.train_molecules)).astype(int)
+    t0 = time.perf_counter()
+    F, T = warmstart.make_dataset(counts, seed=6100 + rank, grid=a.grid)
+    t_data = time.perf_counter() - t0
+    net = pb.pb_mlp_create(pb.NFEAT, warmstart.WIDTH, warmstart.DEPTH, 2, seed=17, stream=stream)
+    first, last, t_train = warmstart.train(net, F, T, steps=a.train_steps, batch=8192, lr=1e-3, lr_final=1e-4)
+    mesh = workload(kind="molecule", atoms=a.atoms, h=a.grid)
+    N = mesh.nt
+
+    def prm(precision):
+        return pb.params(eps_in=1.0, eps_out=80.0, kappa=0.1257, eta0=a.eta0, leaf_size=a.leaf, p=a.p, qs=3,
+                         precision=precision, precond=pb.PB_PRECOND_BLOCK)
+
+    arms = {"learned_mixed": (pb.PB_MIXED, True), "zero_mixed": (pb.PB_MIXED, False), "zero_fp64": (pb.PB_FP64, False)}
+    ctxs = {}
+    for k, (precision, _) in arms.items():
+        ctxs[k] = pb.pb_create(prm(precision), stream)
+        pb.pb_mesh_upload(ctxs[k], mesh.verts, mesh.tris, mesh.qpos, mesh.q)
+    x = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {k: {"ms": [], "info": None, "E": None} for k in arms}
+
+    def run(k):
+        precision, learned = arms[k]
+        c = ctxs[k]
+        pb.pb_build_tree(c)
+        if learned:
+            pb.pb_learned_guess(c, net, x)
+        else:
+            x.zero_()
+        info = pb.pb_gmres_solve(c, x, tol=a.tol, max_iter=500, restart=50, use_x0=learned)
+        return info, pb.pb_solvation_energy(c, x)
+
+    for it in range(a.warmup + a.steps):
+        for k in arms:
+            flush.fill_(it & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            info, E = run(k)
+            e1.record()
+            torch.cuda.synchronize()
+            if it >= a.warmup:
+                res[k]["ms"].append(e0.elapsed_time(e1))
+                res[k]["info"], res[k]["E"] = info, E
+    for c in ctxs.values():
+        pb.pb_destroy(c)
+    pb.pb_mlp_destroy(net)
+    if rank != 0:
+        return 0
+    ms = {k: statistics.median(v["ms"]) for k, v in res.items()}
+    Eref = res["zero_fp64"]["E"]
+    arms_out = {k: {"ms": ms[k], "iterations": v["info"].iterations, "matvecs": v["info"].matvecs,
+                    "initial_residual": v["info"].initial_residual, "rel_residual": v["info"].rel_residual,
+                    "energy_kcal": v["E"], "energy_rel_err_vs_fp64": abs(v["E"] - Eref) / abs(Eref)}
+                for k, v in res.items()}
+    print(json.dumps({
+        "metric": "PB solve time to 1e-6 residual (build + solve + energy), learned+mixed", "value": ms["learned_mixed"],
+        "unit": "ms", "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": sum(ms.values()),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64+bf16",
+        "data": "synthetic", "arms": arms_out,
+        "speedup_vs_fp64_zero": ms["zero_fp64"] / ms["learned_mixed"],
+        "speedup_vs_mixed_zero": ms["zero_mixed"] / ms["learned_mixed"],
+        "training": {"molecules": int(a.train_molecules), "atoms": [int(c) for c in counts], "rows": int(F.shape[0]),
+                     "data_seconds": t_data, "steps": a.train_steps, "train_seconds": t_train,
+                     "loss_first": first, "loss_last": last},
+        "config": {"workload": f"protein-like molecule, {a.atoms} atoms, grid {a.grid} A, {N} triangles",
+                   "p": a.p, "eta0": a.eta0, "leaf_size": a.leaf, "l2": "flushed (256 MiB write) before each arm"}}))
+    return 0
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batch":
         return run_batch(a)
+    if a.workload == "learned":
+        return run_learned(a)
     return run_ours(a)
 
 

@@ -73,6 +73,7 @@ typedef struct pb_solve_info {
     int matvecs;         /* matrix-vector products, including residual evaluations */
     double rel_residual; /* final ||b - A x|| / ||b||, recomputed with a true product */
     int status;          /* PB_OK, PB_ERR_NOT_CONVERGED or PB_ERR_NONFINITE */
+    double initial_residual; /* ||b - A x0|| / ||b|| of the start (1 for a zero start) */
 } pb_solve_info;
 
 /* Tree statistics (for tests and reports). */
@@ -192,6 +193,64 @@ int pb_get_timing(pb_ctx* ctx, double* out);
 
 /* Number of this library's kernel launches queued on ctx since it was created. */
 int pb_get_launch_count(pb_ctx* ctx, long long* out);
+
+/* ---------------- learned warm start for GMRES ----------------
+ * The paper starts GMRES from zero (Section 2.6). These calls add a per-element multilayer
+ * perceptron that predicts x = [phi; dphi/dn] from local features, so that GMRES can start
+ * from the prediction; the converged solution does not depend on the start, only the number
+ * of iterations does. The network has nin inputs, depth hidden layers of width units with
+ * ReLU, and nout linear outputs; layer l computes z = W_l a + b_l with W_l (out x in,
+ * row-major). Forward and backward passes run on the tensor cores with BF16 weights and
+ * activations and FP32 accumulation; master weights, gradients and Adam moments are FP32.
+ * The loss is the mean squared error over all rows and outputs.
+ *
+ * Parameter layout (pb_mlp_get_params / set_params / the gradient): every layer's weight
+ * matrix in order, then every layer's bias, each in the layer's PADDED shape: inputs rounded
+ * up to a multiple of 16 (layer 0 only), outputs of the last layer rounded up to a multiple
+ * of 16; padded rows and columns stay zero as long as the caller keeps them zero. */
+typedef struct pb_mlp pb_mlp;
+
+/* Create a network with weights drawn uniformly from +-sqrt(6 / (fan_in + fan_out)) by a
+ * SplitMix64 sequence of seed, zero biases and zero Adam moments. width: multiple of 16;
+ * 1 <= depth <= 7; 1 <= nout <= 64. stream: cudaStream_t for all the network's work.
+ * Synchronises. */
+int pb_mlp_create(int nin, int width, int depth, int nout, unsigned long long seed, void* stream, pb_mlp** out);
+int pb_mlp_destroy(pb_mlp* net);
+const char* pb_mlp_last_error(const pb_mlp* net);
+/* Number of FP32 parameters in the padded layout above. */
+int pb_mlp_param_count(pb_mlp* net, long long* n);
+/* Copy all parameters to / from a host array of pb_mlp_param_count floats. Synchronises. */
+int pb_mlp_get_params(pb_mlp* net, float* host);
+int pb_mlp_set_params(pb_mlp* net, const float* host);
+/* Y (device, n x nout FP32, row-major) = network(X) for X (device, n x nin FP32, row-major).
+ * Queues the work. */
+int pb_mlp_forward(pb_mlp* net, const float* X, int n, float* Y);
+/* Loss and gradient of the loss for inputs X and targets T (device, n x nout FP32); loss and
+ * grad (pb_mlp_param_count floats) are host pointers and may be NULL. Synchronises. */
+int pb_mlp_gradient(pb_mlp* net, const float* X, const float* T, int n, float* loss, float* grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the gradient of the
+ * batch (X, T). loss: host pointer or NULL (NULL leaves the step queued, no sync). */
+int pb_mlp_train_step(pb_mlp* net, const float* X, const float* T, int n, float lr, float* loss);
+
+/* Per-element features of the learned warm start after pb_build_tree, element order,
+ * F (device, nt x 18 FP32). With r the distance from the centroid to charge k: centroid minus
+ * the mean charge position over the centroids' radius of gyration (3), unit normal (3),
+ * log(area / mean area), 1 - mean normal product with the triangles sharing a vertex,
+ * S1 and S2 of eqbim_3/eqbim_4 at the centroid, sum_k |q_k| / (4 pi r), nearest-charge
+ * distance / 3 A, sum_k q_k exp(-kappa r) / (4 pi eps_in r), sum_k q_k / (4 pi eps_in
+ * sqrt(r^2 + a^2)) for a = 4 and 8 A, sum_k exp(-r^2 / 50) / 10, and -sum_k q_k n . (c - x_k)
+ * / (4 pi eps_in (r^2 + a^2)^(3/2)) for a = 4 and 8 A; the eight source columns are divided by
+ * their root mean square over the molecule.
+ * If x (device, 2 nt FP64, a solution) is given, T (device, nt x 2 FP32) receives the
+ * training targets phi_i / s_phi and dphi_i / s_dphi with s_phi = rms S1 * 2 eps_in /
+ * (eps_in + eps_out) and s_dphi = rms S2 * 2 eps_out / (eps_in + eps_out) (the flat-interface
+ * image-charge values); x and T are both NULL or both set. scales: host double[20] or NULL:
+ * [c] the divisor of column c ([0] for columns 0-2, [6] the mean area), [18] s_phi,
+ * [19] s_dphi; synchronises when given. */
+int pb_features(pb_ctx* ctx, float* F, const double* x, float* T, double* scales);
+/* x (device, 2 nt FP64) = the network's prediction for the uploaded molecule, unscaled by
+ * s_phi and s_dphi; net must map 18 inputs to 2 outputs. Use as the start of pb_gmres_solve. */
+int pb_learned_guess(pb_ctx* ctx, pb_mlp* net, double* x);
 
 /* Solvation energy for callers that cannot allocate device memory.
  *

@@ -335,7 +335,7 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
     s.y = s.g + (m + 2);
     s.hcol = s.y + (m + 2);
     s.res = s.hcol + (m + 2);
-    pb_solve_info inf = {0, 0, 0.0, PB_OK};
+    pb_solve_info inf = {0, 0, 0.0, PB_OK, 1.0};
     // ||b||
     k_multidot<<<dim3(DOT_BLOCKS, 1), KB, 0, c->st>>>(n, nullptr, bs, part);
     PB_LAUNCH(c);
@@ -369,6 +369,7 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
         PB_CUDA(c, cudaMemcpyAsync(c->hscal, s.res, sizeof(double), cudaMemcpyDeviceToHost, c->st));
         PB_CUDA(c, cudaStreamSynchronize(c->st));
         rel = c->hscal[0] / bnorm;
+        if (inf.matvecs == 1) inf.initial_residual = rel;
         if (!isfinite(rel)) {
             inf.status = PB_ERR_NONFINITE;
             break;

@@ -1,0 +1,714 @@
+// Learned warm start for GMRES: a per-element multilayer perceptron that maps local
+// geometry and source-term features to the element's (phi, dphi/dn), trained on solutions
+// the solver itself produces. GMRES started from its prediction still converges to the same
+// residual, so the network only changes the number of iterations, never the answer.
+//
+// Arithmetic: BF16 weights and activations, FP32 accumulation, on the tensor cores through
+// mma.sync m16n8k16 (BF16 inputs, FP32 accumulators); FP32 master weights and Adam moments.
+// Hidden layers use ReLU, the output layer is linear, the loss is the mean squared error.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "pb_internal.cuh"
+
+#define MLP_MAXL 8
+
+struct pb_mlp {
+    int nin = 0, width = 0, depth = 0, nout = 0;  // depth = number of hidden layers
+    int nl = 0;                                   // weight layers = depth + 1
+    int din[MLP_MAXL] = {}, dout[MLP_MAXL] = {};  // padded dimensions (multiples of 16)
+    long long woff[MLP_MAXL + 1] = {}, boff[MLP_MAXL + 1] = {};
+    cudaStream_t st = nullptr;
+    float *W = nullptr, *Wm = nullptr, *Wv = nullptr, *G = nullptr;  // all weights then biases
+    __nv_bfloat16* Wb = nullptr;                                      // BF16 copy of the weights
+    // training buffers (grown on demand): per layer pre-activations and BF16 activations
+    int cap = 0;
+    float* Z[MLP_MAXL] = {};
+    __nv_bfloat16* Ab[MLP_MAXL + 1] = {};
+    float* dA = nullptr;
+    __nv_bfloat16* dZb = nullptr;
+    float* lossbuf = nullptr;
+    long long nparam = 0;
+    int adam_t = 0;
+    std::string err;
+};
+
+static int mlp_fail(pb_mlp* m, int code, const char* msg)
+{
+    if (m) m->err = msg;
+    return code;
+}
+
+// ---------- generic BF16 GEMM on the tensor cores ----------
+// C[M x N] (FP32, ldc) = sum_k A(i, k) B(k, j) with A(i, k) = A[i * sAi + k * sAk] and
+// B(k, j) = B[k * sBk + j * sBj] (BF16, any strides); one warp per 16 x 64 tile, K split over
+// gridDim.z slices that accumulate with atomicAdd when ksplit > 1.
+__device__ __forceinline__ unsigned pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+__global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
+                                                   long long sAi, long long sAk, const __nv_bfloat16* __restrict__ B,
+                                                   long long sBk, long long sBj, float* __restrict__ C, long long ldc,
+                                                   int accumulate)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int i0 = (blockIdx.x * 4 + warp) * 16;
+    const int j0 = blockIdx.y * 64;
+    if (i0 >= M) return;
+    const int kslice = (K + gridDim.z - 1) / gridDim.z;
+    const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
+    const __nv_bfloat16 z = __float2bfloat16(0.f);
+    float acc[8][4];
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[n][q] = 0.f;
+    auto ld_a = [&](int i, int k) -> __nv_bfloat16 {
+        return (i < M && k < ke) ? A[(long long)i * sAi + (long long)k * sAk] : z;
+    };
+    auto ld_b = [&](int k, int j) -> __nv_bfloat16 {
+        return (j < N && k < ke) ? B[(long long)k * sBk + (long long)j * sBj] : z;
+    };
+    for (int k0 = kb; k0 < ke; k0 += 16) {
+        unsigned a[4];
+        a[0] = pack2(ld_a(i0 + g, k0 + 2 * t), ld_a(i0 + g, k0 + 2 * t + 1));
+        a[1] = pack2(ld_a(i0 + g + 8, k0 + 2 * t), ld_a(i0 + g + 8, k0 + 2 * t + 1));
+        a[2] = pack2(ld_a(i0 + g, k0 + 2 * t + 8), ld_a(i0 + g, k0 + 2 * t + 9));
+        a[3] = pack2(ld_a(i0 + g + 8, k0 + 2 * t + 8), ld_a(i0 + g + 8, k0 + 2 * t + 9));
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const int j = j0 + n * 8 + g;
+            unsigned b0 = pack2(ld_b(k0 + 2 * t, j), ld_b(k0 + 2 * t + 1, j));
+            unsigned b1 = pack2(ld_b(k0 + 2 * t + 8, j), ld_b(k0 + 2 * t + 9, j));
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};\n"
+                : "+f"(acc[n][0]), "+f"(acc[n][1]), "+f"(acc[n][2]), "+f"(acc[n][3])
+                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + g + (q >= 2 ? 8 : 0);
+            const int j = j0 + n * 8 + 2 * t + (q & 1);
+            if (i < M && j < N) {
+                float* c = C + (long long)i * ldc + j;
+                if (accumulate) atomicAdd(c, acc[n][q]);
+                else *c = acc[n][q];
+            }
+        }
+}
+
+static void gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, long long sAi, long long sAk,
+                 const __nv_bfloat16* B, long long sBk, long long sBj, float* C, long long ldc, int ksplit)
+{
+    dim3 grid((M + 63) / 64, (N + 63) / 64, ksplit);
+    k_gemm_bf16<<<grid, 128, 0, st>>>(M, N, K, A, sAi, sAk, B, sBk, sBj, C, ldc, ksplit > 1);
+}
+
+// ---------- elementwise pieces ----------
+__global__ void k_to_bf16(long long n, const float* __restrict__ x, __nv_bfloat16* __restrict__ y)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16(x[i]);
+}
+
+// input rows (n x nin, FP32) into a zero-padded BF16 matrix (n x dpad)
+__global__ void k_pack_input(int n, int nin, int dpad, const float* __restrict__ X, __nv_bfloat16* __restrict__ Y)
+{
+    long long tot = (long long)n * dpad;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(i / dpad), c = (int)(i % dpad);
+        Y[i] = __float2bfloat16(c < nin ? X[(long long)r * nin + c] : 0.f);
+    }
+}
+
+// Z += bias; A = relu(Z) (hidden) or Z (output), as BF16 for the next layer
+__global__ void k_bias_act(int n, int d, const float* __restrict__ b, float* __restrict__ Z,
+                           __nv_bfloat16* __restrict__ Ab, int relu)
+{
+    long long tot = (long long)n * d;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        float v = Z[i] + b[i % d];
+        Z[i] = v;
+        if (Ab) Ab[i] = __float2bfloat16(relu ? fmaxf(v, 0.f) : v);
+    }
+}
+
+// output layer: dZ = 2 (Y - T) / (n nout) on the real outputs, loss partial sums
+__global__ void k_mse(int n, int nout, int dpad, const float* __restrict__ Y, const float* __restrict__ T,
+                      float* __restrict__ dZ, float* __restrict__ loss)
+{
+    __shared__ float red[256];
+    float s = 0.f;
+    long long tot = (long long)n * dpad;
+    const float sc = 2.f / ((float)n * (float)nout);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(i / dpad), c = (int)(i % dpad);
+        float g = 0.f;
+        if (c < nout) {
+            float e = Y[i] - T[(long long)r * nout + c];
+            s += e * e;
+            g = sc * e;
+        }
+        dZ[i] = g;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0] / ((float)n * (float)nout));
+}
+
+// dZ = dA * relu'(Z)
+__global__ void k_relu_back(long long n, const float* __restrict__ Z, const float* __restrict__ dA,
+                            __nv_bfloat16* __restrict__ dZb)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dZb[i] = __float2bfloat16(Z[i] > 0.f ? dA[i] : 0.f);
+}
+
+// bias gradient: column sums of dZ (n x d)
+__global__ void k_colsum(int n, int d, const __nv_bfloat16* __restrict__ dZ, float* __restrict__ gb)
+{
+    int c = blockIdx.x;
+    float s = 0.f;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) s += __bfloat162float(dZ[(long long)r * d + c]);
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gb[c] = red[0];
+}
+
+__global__ void k_adam(long long n, float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, float lr, float b1, float b2, float c1, float c2, float eps)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.f - b1) * gi;
+        float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// deterministic initialisation: uniform(-s, s) with s = sqrt(6 / (fan_in + fan_out)) (SplitMix64)
+__global__ void k_init(long long n, float* __restrict__ w, float s, unsigned long long seed)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z = z ^ (z >> 31);
+        double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+        w[i] = (float)((2.0 * u - 1.0) * s);
+    }
+}
+
+static int grid1(long long n) { return (int)std::min<long long>((n + 255) / 256, 152 * 8); }
+
+static int ensure_cap(pb_mlp* m, int n)
+{
+    if (n <= m->cap) return PB_OK;
+    cudaStreamSynchronize(m->st);
+    for (int l = 0; l < m->nl; ++l) {
+        cudaFree(m->Z[l]);
+        m->Z[l] = nullptr;
+    }
+    for (int l = 0; l <= m->nl; ++l) {
+        cudaFree(m->Ab[l]);
+        m->Ab[l] = nullptr;
+    }
+    cudaFree(m->dA);
+    cudaFree(m->dZb);
+    int dmax = 16;
+    for (int l = 0; l < m->nl; ++l) dmax = std::max(dmax, std::max(m->din[l], m->dout[l]));
+    bool ok = true;
+    for (int l = 0; l < m->nl; ++l) ok &= cudaMalloc(&m->Z[l], sizeof(float) * (size_t)n * m->dout[l]) == cudaSuccess;
+    ok &= cudaMalloc(&m->Ab[0], sizeof(__nv_bfloat16) * (size_t)n * m->din[0]) == cudaSuccess;
+    for (int l = 0; l < m->nl; ++l)
+        ok &= cudaMalloc(&m->Ab[l + 1], sizeof(__nv_bfloat16) * (size_t)n * m->dout[l]) == cudaSuccess;
+    ok &= cudaMalloc(&m->dA, sizeof(float) * (size_t)n * dmax) == cudaSuccess;
+    ok &= cudaMalloc(&m->dZb, sizeof(__nv_bfloat16) * (size_t)n * dmax) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        m->cap = 0;
+        return mlp_fail(m, PB_ERR_NOMEM, "mlp: out of memory");
+    }
+    m->cap = n;
+    return PB_OK;
+}
+
+// forward pass over n rows; keeps Z and BF16 activations for a backward pass
+static int mlp_forward(pb_mlp* m, const float* X, int n)
+{
+    int rc = ensure_cap(m, n);
+    if (rc) return rc;
+    k_to_bf16<<<grid1(m->nparam), 256, 0, m->st>>>(m->nparam, m->W, m->Wb);
+    k_pack_input<<<grid1((long long)n * m->din[0]), 256, 0, m->st>>>(n, m->nin, m->din[0], X, m->Ab[0]);
+    for (int l = 0; l < m->nl; ++l) {
+        const int k = m->din[l], d = m->dout[l];
+        // Z = A W^T: B(kk, j) = W[j][kk]
+        gemm(m->st, n, d, k, m->Ab[l], k, 1, m->Wb + m->woff[l], 1, k, m->Z[l], d, 1);
+        k_bias_act<<<grid1((long long)n * d), 256, 0, m->st>>>(n, d, m->W + m->boff[l], m->Z[l], m->Ab[l + 1],
+                                                               l + 1 < m->nl);
+    }
+    return cudaGetLastError() == cudaSuccess ? PB_OK : mlp_fail(m, PB_ERR_CUDA, "mlp forward launch failed");
+}
+
+// backward pass after mlp_forward: gradients into m->G, loss into m->lossbuf
+static int mlp_backward(pb_mlp* m, const float* T, int n)
+{
+    const int L = m->nl;
+    cudaMemsetAsync(m->G, 0, sizeof(float) * m->nparam, m->st);
+    cudaMemsetAsync(m->lossbuf, 0, sizeof(float), m->st);
+    const int dl = m->dout[L - 1];
+    k_mse<<<grid1((long long)n * dl), 256, 0, m->st>>>(n, m->nout, dl, m->Z[L - 1], T, m->dA, m->lossbuf);
+    k_to_bf16<<<grid1((long long)n * dl), 256, 0, m->st>>>((long long)n * dl, m->dA, m->dZb);
+    for (int l = L - 1; l >= 0; --l) {
+        const int k = m->din[l], d = m->dout[l];
+        // dW = dZ^T A: A-operand (i = out unit, kk = row) = dZ[kk][i]; B(kk = row, j = in) = A[kk][j]
+        const int ks = std::max(1, std::min(64, n / 2048));
+        gemm(m->st, d, k, n, m->dZb, 1, d, m->Ab[l], k, 1, m->G + m->woff[l], k, ks);
+        k_colsum<<<d, 256, 0, m->st>>>(n, d, m->dZb, m->G + m->boff[l]);
+        if (l > 0) {
+            // dA_prev = dZ W: A(i = row, kk = out) = dZ[i][kk]; B(kk = out, j = in) = W[kk][j]
+            gemm(m->st, n, k, d, m->dZb, d, 1, m->Wb + m->woff[l], k, 1, m->dA, k, 1);
+            k_relu_back<<<grid1((long long)n * k), 256, 0, m->st>>>((long long)n * k, m->Z[l - 1], m->dA, m->dZb);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? PB_OK : mlp_fail(m, PB_ERR_CUDA, "mlp backward launch failed");
+}
+
+extern "C" int pb_mlp_create(int nin, int width, int depth, int nout, unsigned long long seed, void* stream,
+                             pb_mlp** out)
+{
+    if (!out || nin < 1 || width < 16 || width % 16 || depth < 1 || depth + 1 > MLP_MAXL || nout < 1 || nout > 64)
+        return PB_ERR_ARG;
+    pb_mlp* m = new pb_mlp();
+    m->nin = nin;
+    m->width = width;
+    m->depth = depth;
+    m->nout = nout;
+    m->nl = depth + 1;
+    m->st = (cudaStream_t)stream;
+    auto pad = [](int x) { return (x + 15) / 16 * 16; };
+    long long o = 0;
+    for (int l = 0; l < m->nl; ++l) {
+        m->din[l] = l == 0 ? pad(nin) : width;
+        m->dout[l] = l + 1 < m->nl ? width : pad(nout);
+        m->woff[l] = o;
+        o += (long long)m->din[l] * m->dout[l];
+    }
+    m->woff[m->nl] = o;
+    for (int l = 0; l < m->nl; ++l) {
+        m->boff[l] = o;
+        o += m->dout[l];
+    }
+    m->boff[m->nl] = o;
+    m->nparam = o;
+    bool ok = cudaMalloc(&m->W, sizeof(float) * o) == cudaSuccess;
+    ok &= cudaMalloc(&m->Wm, sizeof(float) * o) == cudaSuccess;
+    ok &= cudaMalloc(&m->Wv, sizeof(float) * o) == cudaSuccess;
+    ok &= cudaMalloc(&m->G, sizeof(float) * o) == cudaSuccess;
+    ok &= cudaMalloc(&m->Wb, sizeof(__nv_bfloat16) * o) == cudaSuccess;
+    ok &= cudaMalloc(&m->lossbuf, sizeof(float)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        delete m;
+        return PB_ERR_NOMEM;
+    }
+    cudaMemsetAsync(m->W, 0, sizeof(float) * o, m->st);
+    cudaMemsetAsync(m->Wm, 0, sizeof(float) * o, m->st);
+    cudaMemsetAsync(m->Wv, 0, sizeof(float) * o, m->st);
+    for (int l = 0; l < m->nl; ++l) {
+        long long n = (long long)m->din[l] * m->dout[l];
+        float s = sqrtf(6.f / (float)((l == 0 ? nin : width) + (l + 1 < m->nl ? width : nout)));
+        k_init<<<grid1(n), 256, 0, m->st>>>(n, m->W + m->woff[l], s, seed + 7919ULL * l);
+    }
+    // padded input columns and output rows carry zero weights
+    std::vector<float> h(o);
+    cudaMemcpyAsync(h.data(), m->W, sizeof(float) * o, cudaMemcpyDeviceToHost, m->st);
+    cudaStreamSynchronize(m->st);
+    for (int l = 0; l < m->nl; ++l) {
+        int realin = l == 0 ? nin : width, realout = l + 1 < m->nl ? width : nout;
+        for (int j = 0; j < m->dout[l]; ++j)
+            for (int kk = 0; kk < m->din[l]; ++kk)
+                if (j >= realout || kk >= realin) h[m->woff[l] + (long long)j * m->din[l] + kk] = 0.f;
+    }
+    cudaMemcpyAsync(m->W, h.data(), sizeof(float) * o, cudaMemcpyHostToDevice, m->st);
+    if (cudaStreamSynchronize(m->st) != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return PB_ERR_CUDA;
+    }
+    *out = m;
+    return PB_OK;
+}
+
+extern "C" int pb_mlp_destroy(pb_mlp* m)
+{
+    if (!m) return PB_OK;
+    cudaStreamSynchronize(m->st);
+    cudaFree(m->W);
+    cudaFree(m->Wm);
+    cudaFree(m->Wv);
+    cudaFree(m->G);
+    cudaFree(m->Wb);
+    cudaFree(m->lossbuf);
+    for (int l = 0; l < MLP_MAXL; ++l) cudaFree(m->Z[l]);
+    for (int l = 0; l <= MLP_MAXL; ++l) cudaFree(m->Ab[l]);
+    cudaFree(m->dA);
+    cudaFree(m->dZb);
+    delete m;
+    return PB_OK;
+}
+
+extern "C" const char* pb_mlp_last_error(const pb_mlp* m) { return m ? m->err.c_str() : "null network"; }
+
+extern "C" int pb_mlp_param_count(pb_mlp* m, long long* n)
+{
+    if (!m || !n) return PB_ERR_ARG;
+    *n = m->nparam;
+    return PB_OK;
+}
+
+extern "C" int pb_mlp_get_params(pb_mlp* m, float* host)
+{
+    if (!m || !host) return PB_ERR_ARG;
+    if (cudaMemcpyAsync(host, m->W, sizeof(float) * m->nparam, cudaMemcpyDeviceToHost, m->st) != cudaSuccess ||
+        cudaStreamSynchronize(m->st) != cudaSuccess)
+        return mlp_fail(m, PB_ERR_CUDA, "mlp: copy failed");
+    return PB_OK;
+}
+
+extern "C" int pb_mlp_set_params(pb_mlp* m, const float* host)
+{
+    if (!m || !host) return PB_ERR_ARG;
+    if (cudaMemcpyAsync(m->W, host, sizeof(float) * m->nparam, cudaMemcpyHostToDevice, m->st) != cudaSuccess ||
+        cudaStreamSynchronize(m->st) != cudaSuccess)
+        return mlp_fail(m, PB_ERR_CUDA, "mlp: copy failed");
+    return PB_OK;
+}
+
+extern "C" int pb_mlp_forward(pb_mlp* m, const float* X, int n, float* Y)
+{
+    if (!m || !X || !Y || n < 1) return PB_ERR_ARG;
+    int rc = mlp_forward(m, X, n);
+    if (rc) return rc;
+    // real outputs of the last layer, row-major n x nout
+    const int L = m->nl, dl = m->dout[L - 1];
+    if (cudaMemcpy2DAsync(Y, sizeof(float) * m->nout, m->Z[L - 1], sizeof(float) * dl, sizeof(float) * m->nout, n,
+                          cudaMemcpyDeviceToDevice, m->st) != cudaSuccess)
+        return mlp_fail(m, PB_ERR_CUDA, "mlp: output copy failed");
+    return PB_OK;
+}
+
+extern "C" int pb_mlp_gradient(pb_mlp* m, const float* X, const float* T, int n, float* loss, float* grad_host)
+{
+    if (!m || !X || !T || n < 1) return PB_ERR_ARG;
+    int rc = mlp_forward(m, X, n);
+    if (!rc) rc = mlp_backward(m, T, n);
+    if (rc) return rc;
+    if (loss && cudaMemcpyAsync(loss, m->lossbuf, sizeof(float), cudaMemcpyDeviceToHost, m->st) != cudaSuccess)
+        return mlp_fail(m, PB_ERR_CUDA, "mlp: copy failed");
+    if (grad_host &&
+        cudaMemcpyAsync(grad_host, m->G, sizeof(float) * m->nparam, cudaMemcpyDeviceToHost, m->st) != cudaSuccess)
+        return mlp_fail(m, PB_ERR_CUDA, "mlp: copy failed");
+    if (cudaStreamSynchronize(m->st) != cudaSuccess) return mlp_fail(m, PB_ERR_CUDA, "mlp: sync failed");
+    return PB_OK;
+}
+
+extern "C" int pb_mlp_train_step(pb_mlp* m, const float* X, const float* T, int n, float lr, float* loss)
+{
+    if (!m || !X || !T || n < 1 || !(lr > 0)) return PB_ERR_ARG;
+    int rc = mlp_forward(m, X, n);
+    if (!rc) rc = mlp_backward(m, T, n);
+    if (rc) return rc;
+    m->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    float c1 = 1.f - powf(b1, (float)m->adam_t), c2 = 1.f - powf(b2, (float)m->adam_t);
+    k_adam<<<grid1(m->nparam), 256, 0, m->st>>>(m->nparam, m->W, m->Wm, m->Wv, m->G, lr, b1, b2, c1, c2, 1e-8f);
+    if (loss && cudaMemcpyAsync(loss, m->lossbuf, sizeof(float), cudaMemcpyDeviceToHost, m->st) != cudaSuccess)
+        return mlp_fail(m, PB_ERR_CUDA, "mlp: copy failed");
+    if (loss && cudaStreamSynchronize(m->st) != cudaSuccess) return mlp_fail(m, PB_ERR_CUDA, "mlp: sync failed");
+    return cudaGetLastError() == cudaSuccess ? PB_OK : mlp_fail(m, PB_ERR_CUDA, "mlp: launch failed");
+}
+
+// ---------- features of the learned warm start ----------
+// Per element, in element order (16 columns; r = distance from the centroid c to charge k):
+//   0-2   c minus the mean charge position, over the radius of gyration of the centroids
+//   3-5   unit normal
+//   6     log(A / mean A)
+//   7     curvature: 1 - mean n_i . n_j over the other triangles sharing a vertex with i
+//   8, 9  S1 and S2 at the centroid (the source terms of eqbim_3/eqbim_4)
+//   10    U = sum_k |q_k| / (4 pi r)
+//   11    distance to the nearest charge / 3 Angstrom
+//   12    screened source sum_k q_k exp(-kappa r) / (4 pi eps_in r)
+//   13,14 smoothed sources sum_k q_k / (4 pi eps_in sqrt(r^2 + a^2)), a = 4 and 8 Angstrom
+//   15    charge density around c: sum_k exp(-r^2 / 50) / 10
+//   16,17 smoothed normal fields -sum_k q_k n.(c - x_k) / (4 pi eps_in (r^2 + a^2)^(3/2)),
+//         a = 4 and 8 Angstrom
+// Columns 8, 9, 10, 12, 13, 14, 16 and 17 are divided by their root mean square over the
+// molecule.
+// Targets: phi / (rms S1 * 2 eps_in / (eps_in + eps_out)) and
+// dphi / (rms S2 * 2 eps_out / (eps_in + eps_out)) -- the image-charge values at a flat
+// dielectric interface, so that targets are O(1) for molecules of any size and charge.
+#define NFEAT 18
+#define NSTAT 20  // column normalisers [0, 18) and the two target scales [18], [19]
+
+struct PoolTmp {
+    pb_ctx* c;
+    void* p = nullptr;
+    PoolTmp(pb_ctx* cc, size_t bytes) : c(cc)
+    {
+        if (cudaMallocFromPoolAsync(&p, bytes, c->pool, c->st) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    ~PoolTmp()
+    {
+        if (p) cudaFreeAsync(p, c->st);
+    }
+};
+
+// raw columns in sorted order. The charge sums run in FP32 (coordinates relative to the charge
+// centre, charges staged through shared memory 256 at a time), each tile's partial sums added
+// into FP64: the features only feed the network, and FP32 keeps this pass to a few ms even for
+// 200k elements x 2000 charges.
+#define FT 256
+__global__ void __launch_bounds__(FT) k_feat_pass(int nt, int nc, const double4_32a* __restrict__ ep,
+                                                  const double4_32a* __restrict__ en,
+                                                  const double* __restrict__ qpos, const double* __restrict__ q,
+                                                  const int* __restrict__ toff, const int* __restrict__ tj, double cx,
+                                                  double cy, double cz, double eps_in, double kappa,
+                                                  float* __restrict__ raw)
+{
+    __shared__ float4 sq[FT];
+    const int k = blockIdx.x * FT + threadIdx.x;
+    const bool act = k < nt;
+    double4_32a p = {0, 0, 0, 0}, n = {0, 0, 0, 0};
+    if (act) {
+        p = ep[k];
+        n = en[k];
+    }
+    const float px = (float)(p.x - cx), py = (float)(p.y - cy), pz = (float)(p.z - cz);
+    const float nx = (float)n.x, ny = (float)n.y, nz = (float)n.z, kap = (float)kappa;
+    double s1 = 0, s2 = 0, u = 0, sk = 0, sa4 = 0, sa8 = 0, dens = 0, e4 = 0, e8 = 0;
+    float dmin2 = 3.0e38f;
+    for (int t0 = 0; t0 < nc; t0 += FT) {
+        __syncthreads();
+        if (t0 + threadIdx.x < nc) {
+            const int t = t0 + threadIdx.x;
+            sq[threadIdx.x] = make_float4((float)(qpos[3 * t] - cx), (float)(qpos[3 * t + 1] - cy),
+                                          (float)(qpos[3 * t + 2] - cz), (float)q[t]);
+        }
+        __syncthreads();
+        const int m = min(FT, nc - t0);
+        float f1 = 0, f2 = 0, fu = 0, fk = 0, f4 = 0, f8 = 0, fd = 0, g4 = 0, g8 = 0;
+        for (int j = 0; j < m; ++j) {
+            const float4 c = sq[j];
+            const float dx = px - c.x, dy = py - c.y, dz = pz - c.z;
+            const float r2 = dx * dx + dy * dy + dz * dz, ri = rsqrtf(r2);
+            const float nd = nx * dx + ny * dy + nz * dz;
+            const float w4 = rsqrtf(r2 + 16.f), w8 = rsqrtf(r2 + 64.f);
+            f1 += c.w * ri;
+            f2 -= c.w * nd * ri * ri * ri;
+            fu += fabsf(c.w) * ri;
+            fk += c.w * __expf(-kap * r2 * ri) * ri;
+            f4 += c.w * w4;
+            f8 += c.w * w8;
+            g4 -= c.w * nd * w4 * w4 * w4;
+            g8 -= c.w * nd * w8 * w8 * w8;
+            fd += __expf(-r2 * 0.02f);
+            dmin2 = fminf(dmin2, r2);
+        }
+        s1 += f1;
+        s2 += f2;
+        u += fu;
+        sk += fk;
+        sa4 += f4;
+        sa8 += f8;
+        e4 += g4;
+        e8 += g8;
+        dens += fd;
+    }
+    if (!act) return;
+    double curv = 0;
+    int cnt = 0;
+    for (int t = toff[k]; t < toff[k + 1]; ++t) {
+        int j = tj[t];
+        if (j == k) continue;
+        double4_32a m2 = en[j];
+        curv += n.x * m2.x + n.y * m2.y + n.z * m2.z;
+        ++cnt;
+    }
+    curv = cnt ? 1.0 - curv / cnt : 0.0;
+    const double i4pi = 0.07957747154594767;
+    float* r = raw + (size_t)k * NFEAT;
+    r[0] = (float)(p.x - cx);
+    r[1] = (float)(p.y - cy);
+    r[2] = (float)(p.z - cz);
+    r[3] = (float)n.x;
+    r[4] = (float)n.y;
+    r[5] = (float)n.z;
+    r[6] = (float)p.w;
+    r[7] = (float)curv;
+    r[8] = (float)(s1 * i4pi / eps_in);
+    r[9] = (float)(s2 * i4pi / eps_in);
+    r[10] = (float)(u * i4pi);
+    r[11] = sqrtf(dmin2) / 3.f;
+    r[12] = (float)(sk * i4pi / eps_in);
+    r[13] = (float)(sa4 * i4pi / eps_in);
+    r[14] = (float)(sa8 * i4pi / eps_in);
+    r[15] = (float)(dens / 10.0);
+    r[16] = (float)(e4 * i4pi / eps_in);
+    r[17] = (float)(e8 * i4pi / eps_in);
+}
+
+// the normalisers, one block: sums of squares (means for column 6) over the molecule
+#define NRED 10
+__global__ void k_feat_stats(int nt, const float* __restrict__ raw, double eps_in, double eps_out,
+                             double* __restrict__ stats)
+{
+    const int cols[NRED] = {0, 6, 8, 9, 10, 12, 13, 14, 16, 17};
+    __shared__ double red[NRED][256];
+    double s[NRED];
+    for (int c = 0; c < NRED; ++c) s[c] = 0;
+    for (int k = threadIdx.x; k < nt; k += 256) {
+        const float* r = raw + (size_t)k * NFEAT;
+        s[0] += (double)r[0] * r[0] + (double)r[1] * r[1] + (double)r[2] * r[2];
+        s[1] += r[6];
+        for (int c = 2; c < NRED; ++c) s[c] += (double)r[cols[c]] * r[cols[c]];
+    }
+    for (int c = 0; c < NRED; ++c) red[c][threadIdx.x] = s[c];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int c = 0; c < NRED; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < NSTAT; ++c) stats[c] = 1.0;
+        stats[0] = sqrt(red[0][0] / nt) + 1e-30;
+        stats[6] = red[1][0] / nt;
+        for (int c = 2; c < NRED; ++c) stats[cols[c]] = sqrt(red[c][0] / nt) + 1e-30;
+        stats[18] = stats[8] * 2.0 * eps_in / (eps_in + eps_out);
+        stats[19] = stats[9] * 2.0 * eps_out / (eps_in + eps_out);
+    }
+}
+
+// normalise and scatter from sorted to element order; optionally the scaled targets
+__global__ void k_feat_finish(int nt, const int* __restrict__ order, const float* __restrict__ raw,
+                              const double* __restrict__ stats, float* __restrict__ F, const double* __restrict__ x,
+                              float* __restrict__ T)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    const float* r = raw + (size_t)k * NFEAT;
+    const int e = order[k];
+    float* f = F + (size_t)e * NFEAT;
+#pragma unroll
+    for (int c = 0; c < NFEAT; ++c) {
+        const float s = (float)stats[c < 3 ? 0 : c];
+        f[c] = c == 6 ? logf(r[6] / s) : r[c] / s;
+    }
+    if (T) {
+        T[2 * (size_t)e] = (float)(x[e] / stats[18]);
+        T[2 * (size_t)e + 1] = (float)(x[nt + e] / stats[19]);
+    }
+}
+
+static int features(pb_ctx* c, float* F, const double* x, float* T, double* stats)
+{
+    const int nt = c->nt;
+    std::vector<double> qp(3 * (size_t)std::max(c->nc, 1));
+    double cx = 0, cy = 0, cz = 0;
+    if (c->nc > 0) {
+        PB_CUDA(c, cudaMemcpyAsync(qp.data(), c->qpos, sizeof(double) * 3 * c->nc, cudaMemcpyDeviceToHost, c->st));
+        PB_CUDA(c, cudaStreamSynchronize(c->st));
+        for (int k = 0; k < c->nc; ++k) {
+            cx += qp[3 * k];
+            cy += qp[3 * k + 1];
+            cz += qp[3 * k + 2];
+        }
+        cx /= c->nc;
+        cy /= c->nc;
+        cz /= c->nc;
+    }
+    PoolTmp raw(c, sizeof(float) * (size_t)nt * NFEAT);
+    if (!raw.p) return pb_fail(c, PB_ERR_NOMEM, "features: out of memory");
+    k_feat_pass<<<(nt + FT - 1) / FT, FT, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q, c->touch_off,
+                                                     c->touch_j, cx, cy, cz, c->prm.eps_in, c->prm.kappa,
+                                                     (float*)raw.p);
+    PB_LAUNCH(c);
+    k_feat_stats<<<1, 256, 0, c->st>>>(nt, (const float*)raw.p, c->prm.eps_in, c->prm.eps_out, stats);
+    PB_LAUNCH(c);
+    k_feat_finish<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->order, (const float*)raw.p, stats, F, x, T);
+    PB_LAUNCH(c);
+    return PB_OK;
+}
+
+extern "C" int pb_features(pb_ctx* c, float* F, const double* x, float* T, double* scales)
+{
+    if (!c) return PB_ERR_ARG;
+    if (c->dead) return PB_ERR_CUDA;
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "features before build_tree");
+    if (!F || (!x) != (!T)) return pb_fail(c, PB_ERR_ARG, "features: F is required, x and T go together");
+    PoolTmp stats(c, sizeof(double) * NSTAT);
+    if (!stats.p) return pb_fail(c, PB_ERR_NOMEM, "features: out of memory");
+    int rc = features(c, F, x, T, (double*)stats.p);
+    if (rc) return rc;
+    if (scales) {
+        PB_CUDA(c, cudaMemcpyAsync(scales, stats.p, sizeof(double) * NSTAT, cudaMemcpyDeviceToHost, c->st));
+        PB_CUDA(c, cudaStreamSynchronize(c->st));
+    }
+    return PB_OK;
+}
+
+// x0 from the network output Y (element order, nt x 2) times the two target scales
+__global__ void k_unscale(int nt, const float* __restrict__ Y, const double* __restrict__ stats,
+                          double* __restrict__ x)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    x[k] = (double)Y[2 * (size_t)k] * stats[18];
+    x[nt + k] = (double)Y[2 * (size_t)k + 1] * stats[19];
+}
+
+extern "C" int pb_learned_guess(pb_ctx* c, pb_mlp* m, double* x)
+{
+    if (!c || !m || !x) return PB_ERR_ARG;
+    if (c->dead) return PB_ERR_CUDA;
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "learned guess before build_tree");
+    if (m->nin != NFEAT || m->nout != 2) return pb_fail(c, PB_ERR_ARG, "learned guess: network must map 18 -> 2");
+    const int nt = c->nt;
+    PoolTmp F(c, sizeof(float) * (size_t)nt * NFEAT), Y(c, sizeof(float) * (size_t)nt * 2),
+        stats(c, sizeof(double) * NSTAT);
+    if (!F.p || !Y.p || !stats.p) return pb_fail(c, PB_ERR_NOMEM, "learned guess: out of memory");
+    int rc = features(c, (float*)F.p, nullptr, nullptr, (double*)stats.p);
+    if (rc) return rc;
+    if (m->st != c->st) PB_CUDA(c, cudaStreamSynchronize(c->st));
+    rc = pb_mlp_forward(m, (const float*)F.p, nt, (float*)Y.p);
+    if (rc) return pb_fail(c, rc, "%s", m->err.c_str());
+    if (m->st != c->st) PB_CUDA(c, cudaStreamSynchronize(m->st));
+    k_unscale<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, (const float*)Y.p, (const double*)stats.p, x);
+    PB_LAUNCH(c);
+    return PB_OK;
+}

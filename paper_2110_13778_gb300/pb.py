@@ -25,7 +25,12 @@ EXPORTS = [
     "pb_matvec", "pb_rhs", "pb_precond_apply", "pb_gmres_solve", "pb_solvation_energy",
     "pb_get_tree_stats", "pb_get_tree", "pb_matvec_part", "pb_set_timing", "pb_get_timing",
     "pb_get_launch_count", "pb_solvation_energy_noalloc", "pb_solve_states",
+    "pb_mlp_create", "pb_mlp_destroy", "pb_mlp_last_error", "pb_mlp_param_count", "pb_mlp_get_params",
+    "pb_mlp_set_params", "pb_mlp_forward", "pb_mlp_gradient", "pb_mlp_train_step", "pb_features",
+    "pb_learned_guess",
 ]
+NFEAT = 18
+NSTAT = 20
 
 
 class PBError(RuntimeError):
@@ -45,7 +50,7 @@ class pb_params(ctypes.Structure):
 
 class pb_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("matvecs", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("initial_residual", ctypes.c_double)]
 
 
 class pb_tree_stats(ctypes.Structure):
@@ -90,12 +95,27 @@ def lib():
         L.pb_get_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.pb_solvation_energy_noalloc.argtypes = [vp, vp, c_int, vp, vp, c_int, c_double, c_double, c_double, c_int,
                                                   vp, vp, vp, ctypes.c_char_p, c_int]
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.pb_mlp_create.argtypes = [c_int, c_int, c_int, c_int, ctypes.c_ulonglong, vp, ctypes.POINTER(vp)]
+        L.pb_mlp_destroy.argtypes = [vp]
+        L.pb_mlp_last_error.argtypes = [vp]
+        L.pb_mlp_last_error.restype = ctypes.c_char_p
+        L.pb_mlp_param_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.pb_mlp_get_params.argtypes = [vp, fp]
+        L.pb_mlp_set_params.argtypes = [vp, fp]
+        L.pb_mlp_forward.argtypes = [vp, vp, c_int, vp]
+        L.pb_mlp_gradient.argtypes = [vp, vp, vp, c_int, fp, fp]
+        L.pb_mlp_train_step.argtypes = [vp, vp, vp, c_int, ctypes.c_float, fp]
+        L.pb_features.argtypes = [vp, vp, vp, vp, dp]
+        L.pb_learned_guess.argtypes = [vp, vp, vp]
         _lib = L
     return _lib
 
 
 def _ptr(t):
-    """Device address of a torch tensor (float64, contiguous, CUDA) or an int address."""
+    """Device address of a contiguous CUDA torch tensor, an int address, or NULL for None."""
+    if t is None:
+        return ctypes.c_void_p(None)
     if isinstance(t, int):
         return ctypes.c_void_p(t)
     if not (t.is_cuda and t.is_contiguous()):
@@ -254,3 +274,75 @@ def pb_solvation_energy_noalloc(verts, tris, qpos, q, x, E, eps_in=1.0, eps_out=
                                            kappa, precision, _ptr(x), _ptr(E), ctypes.c_void_p(stream), err, 256)
     if rc != PB_OK:
         raise PBError(rc, err.value.decode())
+
+
+# ---------------- learned warm start ----------------
+
+
+def _mcheck(net, rc):
+    if rc != PB_OK:
+        raise PBError(rc, lib().pb_mlp_last_error(net).decode())
+
+
+def pb_mlp_create(nin=NFEAT, width=128, depth=3, nout=2, seed=0, stream=0):
+    h = ctypes.c_void_p()
+    rc = lib().pb_mlp_create(nin, width, depth, nout, seed, ctypes.c_void_p(stream), ctypes.byref(h))
+    if rc != PB_OK:
+        raise PBError(rc, "pb_mlp_create rejected the shape or could not allocate")
+    return h
+
+
+def pb_mlp_destroy(net):
+    lib().pb_mlp_destroy(net)
+
+
+def pb_mlp_param_count(net):
+    n = ctypes.c_longlong()
+    _mcheck(net, lib().pb_mlp_param_count(net, ctypes.byref(n)))
+    return n.value
+
+
+def pb_mlp_get_params(net):
+    w = np.zeros(pb_mlp_param_count(net), dtype=np.float32)
+    _mcheck(net, lib().pb_mlp_get_params(net, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return w
+
+
+def pb_mlp_set_params(net, w):
+    W = np.ascontiguousarray(w, dtype=np.float32)
+    if W.size != pb_mlp_param_count(net):
+        raise ValueError("parameter vector has the wrong length")
+    _mcheck(net, lib().pb_mlp_set_params(net, W.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+
+def pb_mlp_forward(net, X, Y):
+    """Y (n, nout) float32 CUDA = network(X (n, nin) float32 CUDA)."""
+    _mcheck(net, lib().pb_mlp_forward(net, _ptr(X), int(X.shape[0]), _ptr(Y)))
+
+
+def pb_mlp_gradient(net, X, T):
+    """(loss, gradient as a float32 numpy array) for the batch (X, T)."""
+    loss = ctypes.c_float()
+    g = np.zeros(pb_mlp_param_count(net), dtype=np.float32)
+    _mcheck(net, lib().pb_mlp_gradient(net, _ptr(X), _ptr(T), int(X.shape[0]), ctypes.byref(loss),
+                                       g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return loss.value, g
+
+
+def pb_mlp_train_step(net, X, T, lr=1e-3, want_loss=True):
+    loss = ctypes.c_float()
+    _mcheck(net, lib().pb_mlp_train_step(net, _ptr(X), _ptr(T), int(X.shape[0]), lr,
+                                         ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def pb_features(ctx, F, x=None, T=None):
+    """F (nt, 18) float32 CUDA; optional training targets T (nt, 2) float32 CUDA from a
+    solution x (2 nt) float64 CUDA. Returns the 20 normalisers."""
+    sc = np.zeros(NSTAT)
+    _check(ctx, lib().pb_features(ctx, _ptr(F), _ptr(x), _ptr(T), sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return sc
+
+
+def pb_learned_guess(ctx, net, x):
+    _check(ctx, lib().pb_learned_guess(ctx, net, _ptr(x)))
