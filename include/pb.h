@@ -64,7 +64,15 @@ typedef struct pb_params {
                         (Sauter-Schwab) quadrature, 1..8 */
     int precision;   /* PB_FP64 or PB_MIXED */
     int precond;     /* PB_PRECOND_NONE, PB_PRECOND_DIAG or PB_PRECOND_BLOCK */
+    int singular;    /* arithmetic of the Sauter-Schwab integrals: PB_SINGULAR_AUTO (0: float-float
+                        under PB_MIXED, FP64 under PB_FP64), PB_SINGULAR_FP64 or PB_SINGULAR_FF */
 } pb_params;
+
+/* Float-float ("double-single", ~1e-13 relative) evaluates every step of the singular
+ * quadrature on the FP32 pipe, whose rate on this GPU is 64 times the FP64 rate. */
+#define PB_SINGULAR_AUTO 0
+#define PB_SINGULAR_FP64 1
+#define PB_SINGULAR_FF 2
 
 typedef struct pb_ctx pb_ctx;
 

@@ -67,6 +67,7 @@ extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
     if (prm->levels < 0 || prm->levels > PB_MAXL || (prm->levels == 0 && prm->leaf_size < 1))
         return PB_ERR_ARG;
     if (prm->precision != PB_FP64 && prm->precision != PB_MIXED) return PB_ERR_ARG;
+    if (prm->singular < PB_SINGULAR_AUTO || prm->singular > PB_SINGULAR_FF) return PB_ERR_ARG;
     if (prm->precond < PB_PRECOND_NONE || prm->precond > PB_PRECOND_BLOCK) return PB_ERR_ARG;
     pb_ctx* c = new pb_ctx();
     c->prm = *prm;

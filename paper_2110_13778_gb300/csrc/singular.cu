@@ -13,6 +13,7 @@
 
 #include <vector>
 
+#include "ff.cuh"
 #include "kernels.cuh"
 #include "pb_internal.cuh"
 
@@ -135,7 +136,7 @@ __global__ void k_touch_classes(int nt, const int* __restrict__ toff, const int*
 
 // ---------- Sauter-Schwab sub-maps (reference triangle {0 <= e2 <= e1 <= 1}) ----------
 // Each writes xhat, yhat and the Jacobian weight of sub-map s at cube point (xi, h1, h2, h3).
-__device__ __forceinline__ int ss_map(int shared, int s, double xi, double h1, double h2, double h3,
+__host__ __device__ __forceinline__ int ss_map(int shared, int s, double xi, double h1, double h2, double h3,
                                       double* xh, double* yh)
 {
     double x0, x1, y0, y1, w;
@@ -174,7 +175,7 @@ __device__ __forceinline__ int ss_map(int shared, int s, double xi, double h1, d
     return 0 * (int)w;  // unused
 }
 
-__device__ __forceinline__ double ss_weight(int shared, int s, double xi, double h1, double h2)
+__host__ __device__ __forceinline__ double ss_weight(int shared, int s, double xi, double h1, double h2)
 {
     double xi3 = xi * xi * xi;
     if (shared == 3) return xi3 * h1 * h1 * h2;
@@ -298,6 +299,331 @@ __global__ void __launch_bounds__(256) k_singular(long long npairs, int nt, cons
     }
 }
 
+// ---------- the same integrals in float-float arithmetic (mixed precision) ----------
+// Every step of k_singular, carried out in float-float (ff.cuh) on the FP32 pipe: ~1e-13
+// relative instead of FP64's ~1e-16, at a fraction of the FP64 pipe's time. The cube points
+// of each Sauter-Schwab class come from a table built on the host in FP64, holding for each
+// point the coefficients of x - y in the pair's edge vectors (so that x - y never forms as the
+// difference of two absolute positions) and the quadrature weight. Per element, the three edge
+// vectors, the unit normal, the centroid and the area are held as float-float records.
+
+// g = e^-t - 1 + t and E = g - t in float-float. Below t = 0.5 from the Taylor series of
+// g / t^2 = sum_k (-t)^k / (k + 2)!, the terms k >= 5 (at most 6.2e-6 of the sum) in FP32;
+// above it from the FP64 exponential (touching pairs reach t = 0.5 only at kappa r = 0.5).
+__device__ __forceinline__ void ff_screen(ff t, ff& E, ff& g)
+{
+    if (t.h < 0.5f) {
+        const float mt = -t.h;
+        float tail = (float)(1.0 / 1307674368000.0);  // 1/15!
+        tail = fmaf(tail, mt, (float)(1.0 / 87178291200.0));
+        tail = fmaf(tail, mt, (float)(1.0 / 6227020800.0));
+        tail = fmaf(tail, mt, (float)(1.0 / 479001600.0));
+        tail = fmaf(tail, mt, (float)(1.0 / 39916800.0));
+        tail = fmaf(tail, mt, (float)(1.0 / 3628800.0));
+        tail = fmaf(tail, mt, (float)(1.0 / 362880.0));
+        tail = fmaf(tail, mt, (float)(1.0 / 40320.0));
+        tail = fmaf(tail, mt, (float)(1.0 / 5040.0));  // k = 5: 1/7!
+        const ff nt = ff_neg(t);
+        constexpr double c4 = 1.0 / 720.0, c3 = 1.0 / 120.0, c2 = 1.0 / 24.0, c1 = 1.0 / 6.0;
+        ff u = ff_add(ff_mul_f(nt, tail), ff{(float)c4, (float)(c4 - (double)(float)c4)});
+        u = ff_add(ff_mul(nt, u), ff{(float)c3, (float)(c3 - (double)(float)c3)});
+        u = ff_add(ff_mul(nt, u), ff{(float)c2, (float)(c2 - (double)(float)c2)});
+        u = ff_add(ff_mul(nt, u), ff{(float)c1, (float)(c1 - (double)(float)c1)});
+        u = ff_add_f(ff_mul(nt, u), 0.5f);
+        g = ff_mul(u, ff_sqr(t));
+        E = ff_sub(g, t);
+    } else {
+        const double td = ff_to(t);
+        const double Ed = expm1(-td);
+        E = ff_from(Ed);
+        g = ff_from(Ed + td);
+    }
+}
+
+// The six parts of pb_kernel_parts from r^2 and the normal projections n_x.d and n_y.d.
+// PARTS = 2 computes P[0], P[1] only (identical triangles, where both projections vanish).
+template <int PARTS>
+__device__ __forceinline__ void ff_parts(ff r2, ff nxd, ff nyd, ff nxny, ff kap, ff* P)
+{
+    constexpr double i4pi = 0.07957747154594767;
+    const ff I4PI = {(float)i4pi, (float)(i4pi - (double)(float)i4pi)};
+    ff rinv = ff_rsqrt(r2);
+    ff r = ff_mul(r2, rinv);
+    ff t = ff_mul(kap, r);
+    ff E, g;
+    ff_screen(t, E, g);
+    ff tE = ff_mul(t, E);
+    ff c1 = ff_neg(ff_add(g, tE));
+    ff rinv2 = ff_sqr(rinv);
+    ff ri3 = ff_mul(ff_mul(rinv, I4PI), rinv2);
+    P[0] = ff_neg(ff_mul(ff_mul(E, rinv), I4PI));
+    if (PARTS == 2) {
+        P[1] = ff_neg(ff_mul(ri3, ff_mul(c1, nxny)));
+        return;
+    }
+    // c3 = -3 g - t^2 - t E (3 + t)
+    ff c3 = ff_neg(ff_add(ff_add(ff_mul_f(g, 3.0f), ff_sqr(t)), ff_mul(tE, ff_add_f(t, 3.0f))));
+    P[1] = ff_mul(ri3, ff_sub(ff_mul(ff_mul(c3, ff_mul(nxd, nyd)), rinv2), ff_mul(c1, nxny)));
+    ff e1 = ff_add_f(ff_neg(c1), 1.0f);
+    P[2] = ff_mul(nyd, ri3);
+    P[3] = ff_mul(P[2], e1);
+    P[4] = ff_mul(nxd, ri3);
+    P[5] = ff_mul(P[4], e1);
+}
+
+__device__ __forceinline__ ff ff_dot3(const ff* a, const ff* b)
+{
+    return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
+}
+
+// Per sorted element: slots 0-8 the edge vectors e_a = v_{a+1} - v_a (a = 0, 1, 2, vertices in
+// stris order), 9-11 the unit normal, 12-14 the centroid, 15 the area.
+#define FF_ESLOTS 16
+__global__ void k_elem_ff(int nt, const int* __restrict__ stris, const double* __restrict__ V,
+                          const double4_32a* __restrict__ ep, const double4_32a* __restrict__ en,
+                          float2* __restrict__ out)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    float2* o = out + (size_t)k * FF_ESLOTS;
+    for (int a = 0; a < 3; ++a) {
+        const int u = stris[3 * k + a], w = stris[3 * k + (a + 1) % 3];
+        for (int c = 0; c < 3; ++c) {
+            ff e = ff_from(V[3 * w + c] - V[3 * u + c]);
+            o[3 * a + c] = make_float2(e.h, e.l);
+        }
+    }
+    const double4_32a p = ep[k], n = en[k];
+    const double nv[3] = {n.x, n.y, n.z}, pv[4] = {p.x, p.y, p.z, p.w};
+    for (int c = 0; c < 3; ++c) {
+        ff a = ff_from(nv[c]);
+        o[9 + c] = make_float2(a.h, a.l);
+    }
+    for (int c = 0; c < 4; ++c) {
+        ff a = ff_from(pv[c]);
+        o[12 + c] = make_float2(a.h, a.l);
+    }
+}
+
+__device__ __forceinline__ ff ld_ff(const float2* p)
+{
+    float2 v = __ldg(p);
+    return {v.x, v.y};
+}
+
+// edge vector from local vertex a to local vertex b of an element (b = a + 1 or a - 1 mod 3)
+__device__ __forceinline__ void ff_edge(const float2* rec, int a, int b, ff* e)
+{
+    const bool fwd = b == (a + 1) % 3;
+    const int slot = 3 * (fwd ? a : b);
+    for (int c = 0; c < 3; ++c) {
+        ff v = ld_ff(rec + slot + c);
+        e[c] = fwd ? v : ff_neg(v);
+    }
+}
+
+// Table of cube points per class (0: one shared vertex, 1: shared edge, 2: identical), each
+// record the float-float coefficients (a0, a1, b0, b1) of x - y = a0 eP0 + a1 eP1 - b0 eQ0 -
+// b1 eQ1 and the weight w (Gauss weights x Jacobian x symmetry factor). For a shared edge
+// eQ0 = eP0 is merged into a0; for identical triangles eQ = eP is merged into a0, a1.
+struct SsTable {
+    std::vector<float2> rec;  // [5][n]: a0, a1, b0, b1, w
+    int off[3], cnt[3], n;
+};
+
+static void ss_table(int qs, SsTable& T)
+{
+    double gx[8], gw[8];
+    gauss01(qs, gx, gw);
+    const int q4 = qs * qs * qs * qs;
+    const int nsub[3] = {2, 5, 3};
+    std::vector<double> f[5];
+    int n = 0;
+    for (int cls = 0; cls < 3; ++cls) {
+        const int ns = cls + 1;
+        T.off[cls] = n;
+        T.cnt[cls] = nsub[cls] * q4;
+        for (int s = 0; s < nsub[cls]; ++s) {
+            const int sm = ns == 3 ? 2 * s : s;
+            for (int t = 0; t < q4; ++t) {
+                int a = t % qs, b = (t / qs) % qs, c = (t / (qs * qs)) % qs, d = t / (qs * qs * qs);
+                double xh[2], yh[2];
+                ss_map(ns, sm, gx[a], gx[b], gx[c], gx[d], xh, yh);
+                double w = gw[a] * gw[b] * gw[c] * gw[d] * ss_weight(ns, sm, gx[a], gx[b], gx[c]) *
+                           (ns == 3 ? 2.0 : 1.0);
+                double co[4];
+                if (ns == 3) {
+                    co[0] = xh[0] - yh[0];
+                    co[1] = xh[1] - yh[1];
+                    co[2] = co[3] = 0.0;
+                } else if (ns == 2) {
+                    co[0] = xh[0] - yh[0];
+                    co[1] = xh[1];
+                    co[2] = 0.0;
+                    co[3] = yh[1];
+                } else {
+                    co[0] = xh[0];
+                    co[1] = xh[1];
+                    co[2] = yh[0];
+                    co[3] = yh[1];
+                }
+                for (int m = 0; m < 4; ++m) f[m].push_back(co[m]);
+                f[4].push_back(w);
+                ++n;
+            }
+        }
+    }
+    T.n = n;
+    T.rec.resize(5 * (size_t)n);
+    for (int m = 0; m < 5; ++m)
+        for (int i = 0; i < n; ++i) {
+            ff v = ff_from(f[m][i]);
+            T.rec[(size_t)m * n + i] = make_float2(v.h, v.l);
+        }
+}
+
+// One warp per touching pair, as k_singular; lanes split the class's cube points.
+template <int NS>
+__device__ __forceinline__ void ss_points_ff(int lane, const float2* __restrict__ tab, int tn, int off, int cnt,
+                                             const ff (*eP)[3], const ff (*eQ)[3], const ff* proj, ff nxny, ff kap,
+                                             ff* acc)
+{
+    for (int i = off + lane; i < off + cnt; i += 32) {
+        const ff a0 = ld_ff(tab + i), a1 = ld_ff(tab + tn + i), w = ld_ff(tab + 4 * tn + i);
+        ff b0 = {0.f, 0.f}, b1 = {0.f, 0.f};
+        if (NS <= 2) b1 = ld_ff(tab + 3 * tn + i);
+        if (NS == 1) b0 = ld_ff(tab + 2 * tn + i);
+        ff d[3];
+        for (int c = 0; c < 3; ++c) {
+            d[c] = ff_add(ff_mul(a0, eP[0][c]), ff_mul(a1, eP[1][c]));
+            if (NS <= 2) d[c] = ff_sub(d[c], ff_mul(b1, eQ[1][c]));
+            if (NS == 1) d[c] = ff_sub(d[c], ff_mul(b0, eQ[0][c]));
+        }
+        const ff r2 = ff_add(ff_add(ff_sqr(d[0]), ff_sqr(d[1])), ff_sqr(d[2]));
+        ff P[6];
+        if (NS == 3) {
+            ff_parts<2>(r2, ff{0.f, 0.f}, ff{0.f, 0.f}, nxny, kap, P);
+            acc[0] = ff_add(acc[0], ff_mul(w, P[0]));
+            acc[1] = ff_add(acc[1], ff_mul(w, P[1]));
+        } else {
+            // n_x.(x - y) and n_y.(x - y): a triangle's own edges are orthogonal to its normal
+            // proj = {n_x.eQ0, n_x.eQ1, n_y.eP0, n_y.eP1}
+            ff nxd = ff_neg(ff_mul(b1, proj[1]));
+            if (NS == 1) nxd = ff_sub(nxd, ff_mul(b0, proj[0]));
+            const ff nyd = ff_add(ff_mul(a0, proj[2]), ff_mul(a1, proj[3]));
+            ff_parts<6>(r2, nxd, nyd, nxny, kap, P);
+            for (int m = 0; m < 6; ++m) acc[m] = ff_add(acc[m], ff_mul(w, P[m]));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_singular_ff(long long npairs, int nt, const int* __restrict__ toff,
+                                                     const int* __restrict__ tj, const int* __restrict__ stris,
+                                                     const int* __restrict__ order, const float2* __restrict__ erec,
+                                                     const float2* __restrict__ tab, int tn, int3 toffs, int3 tcnts,
+                                                     double eps, double kappa, double* __restrict__ corr)
+{
+    long long pair = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (pair >= npairs) return;
+    int lo = 0, hi = nt;
+    while (hi - lo > 1) {
+        int m = (lo + hi) / 2;
+        if (toff[m] <= pair) lo = m;
+        else hi = m;
+    }
+    const int k = lo, j = tj[pair];
+    if (order[k] > order[j]) return;
+    // local vertex indices (0..2) of both triangles, shared vertices first in k's order
+    int oi[3], oj[3], ns = 0;
+    if (k == j) {
+        ns = 3;
+        for (int a = 0; a < 3; ++a) oi[a] = oj[a] = a;
+    } else {
+        int usedi[3] = {0, 0, 0}, usedj[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (stris[3 * k + a] == stris[3 * j + b]) {
+                    oi[ns] = a;
+                    oj[ns] = b;
+                    usedi[a] = usedj[b] = 1;
+                    ++ns;
+                }
+        int p = ns, q = ns;
+        for (int a = 0; a < 3; ++a)
+            if (!usedi[a]) oi[p++] = a;
+        for (int b = 0; b < 3; ++b)
+            if (!usedj[b]) oj[q++] = b;
+    }
+    const float2* rk = erec + (size_t)k * FF_ESLOTS;
+    const float2* rj = erec + (size_t)j * FF_ESLOTS;
+    ff eP[2][3], eQ[2][3], ni[3], nj[3];
+    ff_edge(rk, oi[0], oi[1], eP[0]);
+    ff_edge(rk, oi[1], oi[2], eP[1]);
+    ff_edge(rj, oj[0], oj[1], eQ[0]);
+    ff_edge(rj, oj[1], oj[2], eQ[1]);
+    for (int c = 0; c < 3; ++c) {
+        ni[c] = ld_ff(rk + 9 + c);
+        nj[c] = ld_ff(rj + 9 + c);
+    }
+    const ff kap = ff_from(kappa);
+    const ff nxny = ff_dot3(ni, nj);
+    ff acc[6];
+    for (int m = 0; m < 6; ++m) acc[m] = ff{0.f, 0.f};
+    if (ns == 3) {
+        ss_points_ff<3>(lane, tab, tn, toffs.z, tcnts.z, eP, eQ, nullptr, nxny, kap, acc);
+    } else {
+        const ff proj[4] = {ff_dot3(ni, eQ[0]), ff_dot3(ni, eQ[1]), ff_dot3(nj, eP[0]), ff_dot3(nj, eP[1])};
+        if (ns == 2) ss_points_ff<2>(lane, tab, tn, toffs.y, tcnts.y, eP, eQ, proj, nxny, kap, acc);
+        else ss_points_ff<1>(lane, tab, tn, toffs.x, tcnts.x, eP, eQ, proj, nxny, kap, acc);
+    }
+    for (int m = 0; m < 6; ++m)
+        for (int o = 16; o > 0; o >>= 1) {
+            ff v = {__shfl_xor_sync(0xffffffffu, acc[m].h, o), __shfl_xor_sync(0xffffffffu, acc[m].l, o)};
+            acc[m] = ff_add(acc[m], v);
+        }
+    if (lane > 1 || (lane == 1 && k == j)) return;
+    // lane 0 writes (k, j), lane 1 writes (j, k): target t, source s
+    const float2* rt = lane ? rj : rk;
+    const float2* rs = lane ? rk : rj;
+    const ff At = ld_ff(rt + 15), As = ld_ff(rs + 15);
+    const ff jac = ff_mul_f(ff_mul(At, As), 4.0f);
+    for (int m = 0; m < 6; ++m) acc[m] = ff_mul(acc[m], jac);
+    const ff EPS = ff_from(eps), IEPS = ff_from(1.0 / eps);
+    // exact integrals; for (j, k) the normals exchange roles (k_singular's assembly)
+    ff I[4];
+    I[0] = acc[0];
+    I[3] = acc[1];
+    if (!lane) {
+        I[1] = ff_sub(ff_mul(EPS, acc[3]), acc[2]);
+        I[2] = ff_sub(ff_mul(acc[5], IEPS), acc[4]);
+    } else {
+        I[1] = ff_sub(acc[4], ff_mul(EPS, acc[5]));
+        I[2] = ff_sub(acc[2], ff_mul(acc[3], IEPS));
+    }
+    long long q = pair;
+    if (k != j) {
+        // one-point rule at the centroids: d = c_t - c_s, n_x = n_t, n_y = n_s
+        ff d[3], nt_[3], ns_[3];
+        for (int c = 0; c < 3; ++c) {
+            d[c] = ff_sub(ld_ff(rt + 12 + c), ld_ff(rs + 12 + c));
+            nt_[c] = ld_ff(rt + 9 + c);
+            ns_[c] = ld_ff(rs + 9 + c);
+        }
+        ff P[6];
+        ff_parts<6>(ff_dot3(d, d), ff_dot3(nt_, d), ff_dot3(ns_, d), ff_dot3(nt_, ns_), kap, P);
+        const ff AA = ff_mul(At, As);
+        const ff reg[4] = {P[0], ff_sub(ff_mul(EPS, P[3]), P[2]), ff_sub(ff_mul(P[5], IEPS), P[4]), P[1]};
+        for (int m = 0; m < 4; ++m) I[m] = ff_sub(I[m], ff_mul(AA, reg[m]));
+        if (lane) {
+            q = toff[j];
+            while (q < toff[j + 1] && tj[q] != k) ++q;
+            if (q >= toff[j + 1]) return;
+        }
+    }
+    for (int m = 0; m < 4; ++m) corr[4 * q + m] = ff_to(I[m]);
+}
+
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
 int pb_touching_and_singular(pb_ctx* c)
@@ -362,8 +688,27 @@ int pb_touching_and_singular(pb_ctx* c)
     PB_CUDA(c, cudaMemcpyToSymbolAsync(c_gx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, c->st));
     PB_CUDA(c, cudaMemcpyToSymbolAsync(c_gw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, c->st));
     double eps = c->prm.eps_out / c->prm.eps_in;
-    k_singular<<<nblk(htot, 8), 256, 0, c->st>>>(htot, nt, c->touch_off, c->touch_j, c->stris, c->order, c->verts, c->e64p,
-                                                 c->e64n, c->prm.qs, eps, c->prm.kappa, c->corr);
+    const int mode = c->prm.singular ? c->prm.singular : (c->prm.precision == PB_MIXED ? PB_SINGULAR_FF : PB_SINGULAR_FP64);
+    if (mode == PB_SINGULAR_FP64) {
+        k_singular<<<nblk(htot, 8), 256, 0, c->st>>>(htot, nt, c->touch_off, c->touch_j, c->stris, c->order, c->verts,
+                                                     c->e64p, c->e64n, c->prm.qs, eps, c->prm.kappa, c->corr);
+        PB_LAUNCH(c);
+        return PB_OK;
+    }
+    SsTable T;
+    ss_table(c->prm.qs, T);
+    float2* tab = (float2*)pb_alloc(c, sizeof(float2) * T.rec.size());
+    float2* erec = (float2*)pb_alloc(c, sizeof(float2) * FF_ESLOTS * (size_t)nt);
+    if (!tab || !erec) return pb_fail(c, PB_ERR_NOMEM, "singular: out of memory");
+    PB_CUDA(c, cudaMemcpyAsync(tab, T.rec.data(), sizeof(float2) * T.rec.size(), cudaMemcpyHostToDevice, c->st));
+    k_elem_ff<<<nblk(nt, B), B, 0, c->st>>>(nt, c->stris, c->verts, c->e64p, c->e64n, erec);
     PB_LAUNCH(c);
+    k_singular_ff<<<nblk(htot, 8), 256, 0, c->st>>>(htot, nt, c->touch_off, c->touch_j, c->stris, c->order, erec, tab,
+                                                    T.n, make_int3(T.off[0], T.off[1], T.off[2]),
+                                                    make_int3(T.cnt[0], T.cnt[1], T.cnt[2]), eps, c->prm.kappa,
+                                                    c->corr);
+    PB_LAUNCH(c);
+    // the table's host copy must outlive the queued upload
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
     return PB_OK;
 }

@@ -91,6 +91,38 @@ def test_all_near_fp64_equals_dense(sphere3):
         pb.pb_destroy(ctx)
 
 
+def test_float_float_singular_equals_dense(sphere3):
+    # the Sauter-Schwab integrals in float-float reproduce the FP64 oracle's Galerkin matrix
+    m, ph, A = sphere3
+    ctx = _ctx(m, leaf_size=16, eta0=1e-6, p=2, precision=pb.PB_FP64, singular=pb.PB_SINGULAR_FF)
+    try:
+        x = inputs.random_density(m.nt, 5)
+        y = torch.empty(2 * m.nt, device="cuda", dtype=torch.float64)
+        pb.pb_matvec(ctx, _dev(x), y)
+        assert _rel(y.cpu().numpy(), A @ x) < 1e-11
+    finally:
+        pb.pb_destroy(ctx)
+
+
+@pytest.mark.parametrize("kappa", [KAP, 2.5])
+def test_float_float_singular_matches_fp64_on_molecule(kappa):
+    # irregular marching-tetrahedra triangles; kappa = 2.5 takes kappa r past 0.5 (FP64 exp branch)
+    from paper_2110_13778_gb300 import molecules
+
+    m = molecules.molecule(40, 4040, 1.0)[0]
+    x = _dev(inputs.random_density(m.nt, 6))
+    ys = []
+    for mode in (pb.PB_SINGULAR_FP64, pb.PB_SINGULAR_FF):
+        ctx = _ctx(m, leaf_size=32, eta0=0.7, p=4, kappa=kappa, precision=pb.PB_FP64, singular=mode)
+        try:
+            y = torch.empty(2 * m.nt, device="cuda", dtype=torch.float64)
+            pb.pb_matvec_part(ctx, x, y, 1)
+            ys.append(y.cpu().numpy())
+        finally:
+            pb.pb_destroy(ctx)
+    assert _rel(ys[1], ys[0]) < 1e-11
+
+
 @pytest.mark.parametrize("p,adaptive", [(4, 0), (6, 0), (8, 0), (3, 1), (5, 0)])
 def test_fmm_fp64_matches_oracle_fmm(sphere3, p, adaptive):
     m, ph, A = sphere3
