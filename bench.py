@@ -218,10 +218,11 @@ def config_dict(a, mesh):
     }
 
 
-def peaks(sm_max_mhz):
-    """Roofline denominators: measured HBM copy bandwidth, and ALU peaks derived from unit
-    counts (152 SMs x 128 FP32 lanes x 2 flops per FMA x clock; FP64 at the nominal
-    1.25 TFLOP/s of the part)."""
+def peaks(sm_max_mhz, measured=None):
+    """Roofline denominators: the measured HBM copy bandwidth (MEASURED_PEAKS.json) and the
+    FP32 / FP64 FMA rates measured by pb_measure_alu_peaks in this run; if the probe did not
+    run, FP32 from unit counts (152 SMs x 128 lanes x 2 flops x clock) and FP64 at the part's
+    nominal 1.25 TFLOP/s."""
     mhz = sm_max_mhz or 2070.0
     hbm = None
     try:
@@ -229,11 +230,21 @@ def peaks(sm_max_mhz):
             hbm = json.load(f).get("hbm_gbs")
     except OSError:
         pass
-    return {"fp32_tflops": 152 * 128 * 2 * mhz * 1e6 / 1e12, "fp64_tflops": 1.25, "hbm_gbs": hbm or 6800.0,
-            "hbm_source": "measured" if hbm else "fallback"}
+    pk = {"fp32_tflops": 152 * 128 * 2 * mhz * 1e6 / 1e12, "fp64_tflops": 1.25, "hbm_gbs": hbm or 6800.0,
+          "hbm_source": "measured" if hbm else "fallback", "alu_source": "derived / nominal"}
+    if measured:
+        pk["fp32_tflops_derived"], pk["fp64_tflops_nominal"] = pk["fp32_tflops"], pk["fp64_tflops"]
+        pk["fp32_tflops"], pk["fp64_tflops"] = measured
+        pk["alu_source"] = "measured: FMA-chain probe (pb_measure_alu_peaks) in this run"
+    return pk
 
 
 FLOPS_PER_SS_POINT = 100  # FP64 formula count of one Sauter-Schwab point (maps, kernel parts, sums)
+# FP32 instructions of one float-float Sauter-Schwab point by class (one shared vertex, a shared
+# edge, identical), counted from csrc/singular.cu and csrc/ff.cuh: the primitives cost two-sum 6,
+# ff_add 11, ff_mul 7, ff_sqr 7, ff_rsqrt 25, the screening series 122, the six kernel parts 350
+# (228 for the two of identical triangles), plus the point's x - y, r^2, projections and sums.
+FF_INST_PER_SS_POINT = {1: 734, 2: 662, 3: 382}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the same kernel build, or None
 TRAFFIC_BYTES = {"near": None, "m2l": None, "singular": None}
 
@@ -258,10 +269,29 @@ def phase_roofline(name, tv, stats, N, a, prec, pk):
         flops = sum(2 * 2 * comb(orders[l] + 6, 6) * pairs[l] for l in range(len(pairs)))
         peak = pk["fp32_tflops"] if fp32 else pk["fp64_tflops"]
         work = f"{sum(pairs)} cluster pairs x 2 kernels x 2 C(p+6,6) flops"
+    elif name == "pcbuild":
+        # Gauss-Jordan inversion of every block: m^3 FMAs (2 m^3 flops), in the working precision;
+        # the assembly (n^2 kernel evaluations per block) is not counted
+        flops = 2.0 * stats["pc_sum_m3"]
+        if not flops:
+            return None
+        peak = pk["fp32_tflops"] if fp32 else pk["fp64_tflops"]
+        work = f"{stats['pc_blocks']} blocks (m <= {stats['pc_max']}), sum 2 m^3 flops"
     elif name == "singular":
         q4 = 3 ** 4
         cls = stats["touch_class"]
-        points = q4 * (3 * cls[3] + 5 * cls[2] // 2 + 2 * cls[1] // 2)
+        pts = {3: q4 * 3 * cls[3], 2: q4 * 5 * cls[2] // 2, 1: q4 * 2 * cls[1] // 2}
+        points = sum(pts.values())
+        if fp32:
+            # float-float on the FP32 pipe: FP32 instructions against the FMA issue rate
+            inst = sum(FF_INST_PER_SS_POINT[c] * pts[c] for c in pts)
+            ach = inst / (avg_ms * 1e-3) / 1e12
+            peak = pk["fp32_tflops"] / 2
+            return {"kernel": name, "avg_launch_ms": avg_ms, "bound": "alu", "achieved": ach, "peak": peak,
+                    "unit": "Tinst/s", "frac": ach / peak, "traffic": TRAFFIC_BYTES.get(name),
+                    "work_per_launch": f"{points} quadrature points x float-float FP32 instructions "
+                                       f"{FF_INST_PER_SS_POINT} by class = {inst} instructions",
+                    "peak_source": "FP32 FMA instructions per second = FP32 FLOP rate / 2 (" + pk["alu_source"] + ")"}
         flops = points * FLOPS_PER_SS_POINT
         peak = pk["fp64_tflops"]
         work = f"{points} quadrature points x {FLOPS_PER_SS_POINT} FP64 flops"
@@ -270,8 +300,7 @@ def phase_roofline(name, tv, stats, N, a, prec, pk):
     ach = flops / (avg_ms * 1e-3) / 1e12
     return {"kernel": name, "avg_launch_ms": avg_ms, "bound": "alu", "achieved": ach, "peak": peak,
             "unit": "TFLOP/s", "frac": ach / peak, "traffic": TRAFFIC_BYTES.get(name), "work_per_launch": work,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max clock" if peak == pk["fp32_tflops"]
-            else "nominal FP64 rate of the part (1.25 TFLOP/s)"}
+            "peak_source": ("FP32 " if peak == pk["fp32_tflops"] else "FP64 ") + pk["alu_source"]}
 
 
 def run_ours(a):
@@ -385,13 +414,17 @@ def run_ours(a):
     pb.pb_destroy(ctx)
 
     clocks = clk.summary()
-    pk = peaks(clocks.get("sm_max_mhz"))
+    try:
+        measured = pb.pb_measure_alu_peaks(torch.cuda.current_stream().cuda_stream)
+    except pb.PBError:
+        measured = None
+    pk = peaks(clocks.get("sm_max_mhz"), measured)
     per_step = {k: v[0] / a.steps for k, v in phases.items()}
     # roofline of the dominant kernel (and of the other hot kernels, for the report)
     kernels = {k: v for k, v in phases.items() if v[1] > 0}
     dom = max(kernels, key=lambda k: kernels[k][0])
-    rooflines = {k: phase_roofline(k, kernels[k], stats, N, a, prec, pk) for k in ("near", "m2l", "singular")
-                 if k in kernels}
+    rooflines = {k: phase_roofline(k, kernels[k], stats, N, a, prec, pk)
+                 for k in ("near", "m2l", "singular", "pcbuild") if k in kernels}
     roof = rooflines.get(dom) or {"kernel": dom, "avg_launch_ms": kernels[dom][0] / kernels[dom][1], "bound": "alu",
                                   "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None}
 

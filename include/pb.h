@@ -95,6 +95,9 @@ typedef struct pb_tree_stats {
     long long touching;   /* ordered element pairs sharing a vertex (incl. i == j) */
     int max_leaf;         /* largest leaf */
     long long touch_class[4]; /* ordered touching pairs sharing 1, 2, 3 vertices (index 0 unused) */
+    int pc_blocks;        /* block-diagonal preconditioner blocks (0 for the other preconditioners) */
+    int pc_max;           /* largest block order m = 2 n_c */
+    double pc_sum_m3;     /* sum over blocks of m^3 (the Gauss-Jordan inversion takes m^3 FMAs) */
 } pb_tree_stats;
 
 /* Create a context. params is copied. stream is a cudaStream_t (may be NULL). */
@@ -183,7 +186,7 @@ int pb_matvec_part(pb_ctx* ctx, const double* x, double* y, int which);
  * s the pair out[2s] = total milliseconds, out[2s+1] = number of timed launches, and resets
  * the counts. out: host double[2 * PB_TIMING_SLOTS]. At most 256 launches per slot are
  * remembered between two reads. */
-#define PB_TIMING_SLOTS 12
+#define PB_TIMING_SLOTS 13
 #define PB_T_NEAR 0       /* near-field kernel (one-point rule + mass terms) */
 #define PB_T_CORR 1       /* Sauter-Schwab corrections of touching pairs */
 #define PB_T_UP 2         /* leaf moments and MtM */
@@ -196,11 +199,18 @@ int pb_matvec_part(pb_ctx* ctx, const double* x, double* y, int which);
 #define PB_T_PCBUILD 9    /* preconditioner assembly and inversion (setup) */
 #define PB_T_ENERGY 10    /* solvation energy */
 #define PB_T_RHS 11       /* right-hand side */
+#define PB_T_FARSETUP 12  /* MtL derivative tables and near-field chunks (setup) */
 int pb_set_timing(pb_ctx* ctx, int enable);
 int pb_get_timing(pb_ctx* ctx, double* out);
 
 /* Number of this library's kernel launches queued on ctx since it was created. */
 int pb_get_launch_count(pb_ctx* ctx, long long* out);
+
+/* Measured FMA throughput of the current device in TFLOP/s (2 flops per FMA): eight
+ * independent FMA chains per thread on 8 x (SM count) blocks of 256 threads, timed with CUDA
+ * events on stream (cudaStream_t, NULL = default). The roofline denominators of the
+ * ALU-bound kernels. Host pointers; synchronises; takes ~15 ms. No counterpart in the paper. */
+int pb_measure_alu_peaks(void* stream, double* fp32_tflops, double* fp64_tflops);
 
 /* ---------------- learned warm start for GMRES ----------------
  * The paper starts GMRES from zero (Section 2.6). These calls add a per-element multilayer

@@ -406,9 +406,167 @@ extern "C" int pb_mlp_set_params(pb_mlp* m, const float* host)
     return PB_OK;
 }
 
+// ---------- fused inference: every layer in one kernel ----------
+// For width 128, a first layer of at most 32 padded inputs and at most 16 padded outputs. A CTA
+// of four warps converts all weights to BF16 into shared memory once (rows padded to 136 / 40
+// elements so that the eight rows a B fragment touches fall in distinct banks), then loops over
+// tiles of 64 rows: each warp runs its 16 rows through all layers with the activations held in
+// registers -- the FP32 accumulator fragment of one layer, rounded to BF16 pairs, is exactly the
+// A fragment of the next -- so the features are read once and two outputs written per row.
+// Rounding points are those of the layer-by-layer path.
+#define FUSED_W 128
+#define FUSED_WP 136
+#define FUSED_D0P 40
+struct MlpDesc {
+    long long woff[MLP_MAXL], boff[MLP_MAXL];
+    int nin, din0, nl, nout;  // inputs, padded inputs (row length of W_0), layers, outputs
+};
+
+__device__ __forceinline__ void mma_bf16(float* c, const unsigned* a, unsigned b0, unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned pack_f2(float lo, float hi)
+{
+    return pack2(__float2bfloat16(lo), __float2bfloat16(hi));
+}
+
+static size_t fused_smem(int nl)
+{
+    return sizeof(__nv_bfloat16) * ((size_t)FUSED_W * FUSED_D0P + (size_t)(nl - 2) * FUSED_W * FUSED_WP +
+                                     16 * FUSED_WP) +
+           sizeof(float) * ((size_t)(nl - 1) * FUSED_W + 16);
+}
+
+__global__ void __launch_bounds__(128) k_mlp_fused(int n, const float* __restrict__ X, const float* __restrict__ W,
+                                                   MlpDesc md, float* __restrict__ Y)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int nl = md.nl, din0 = md.din0;
+    __nv_bfloat16* w0 = (__nv_bfloat16*)fsm;                 // [128][40]
+    __nv_bfloat16* wh = w0 + FUSED_W * FUSED_D0P;            // [nl-2][128][136]
+    __nv_bfloat16* wl = wh + (size_t)(nl - 2) * FUSED_W * FUSED_WP;  // [16][136]
+    float* bs = (float*)(wl + 16 * FUSED_WP);                // [nl-1][128] then [16]
+    for (int i = threadIdx.x; i < FUSED_W * din0; i += blockDim.x)
+        w0[(i / din0) * FUSED_D0P + i % din0] = __float2bfloat16(W[md.woff[0] + i]);
+    for (int l = 1; l < nl - 1; ++l)
+        for (int i = threadIdx.x; i < FUSED_W * FUSED_W; i += blockDim.x)
+            wh[(size_t)(l - 1) * FUSED_W * FUSED_WP + (i / FUSED_W) * FUSED_WP + i % FUSED_W] =
+                __float2bfloat16(W[md.woff[l] + i]);
+    for (int i = threadIdx.x; i < 16 * FUSED_W; i += blockDim.x)
+        wl[(i / FUSED_W) * FUSED_WP + i % FUSED_W] = __float2bfloat16(W[md.woff[nl - 1] + i]);
+    for (int l = 0; l < nl - 1; ++l)
+        for (int i = threadIdx.x; i < FUSED_W; i += blockDim.x) bs[l * FUSED_W + i] = W[md.boff[l] + i];
+    for (int i = threadIdx.x; i < 16; i += blockDim.x) bs[(nl - 1) * FUSED_W + i] = W[md.boff[nl - 1] + i];
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int ntiles = (n + 63) / 64;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * 64 + warp * 16;
+        if (r0 >= n) continue;
+        const int ra = r0 + g, rb = r0 + g + 8;
+        float acc[16][4];
+        unsigned a[8][4];
+        // layer 0: A fragments straight from the FP32 features (columns >= nin and rows >= n are 0)
+        auto xin = [&](int r, int c) -> float { return (r < n && c < md.nin) ? X[(size_t)r * md.nin + c] : 0.f; };
+#pragma unroll
+        for (int kc = 0; kc < 8; ++kc) {
+            const int c0 = 16 * kc + 2 * t;
+            if (kc >= 2) {
+                a[kc][0] = a[kc][1] = a[kc][2] = a[kc][3] = 0u;
+                continue;
+            }
+            a[kc][0] = pack_f2(xin(ra, c0), xin(ra, c0 + 1));
+            a[kc][1] = pack_f2(xin(rb, c0), xin(rb, c0 + 1));
+            a[kc][2] = pack_f2(xin(ra, c0 + 8), xin(ra, c0 + 9));
+            a[kc][3] = pack_f2(xin(rb, c0 + 8), xin(rb, c0 + 9));
+        }
+        int kchunks = din0 / 16;
+        for (int l = 0; l < nl; ++l) {
+            const bool last = l == nl - 1;
+            const int ntile = last ? 2 : 16;
+            const __nv_bfloat16* wsm = l == 0 ? w0 : last ? wl : wh + (size_t)(l - 1) * FUSED_W * FUSED_WP;
+            const int stride = l == 0 ? FUSED_D0P : FUSED_WP;
+            const float* bias = bs + l * FUSED_W;
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) {
+                if (kc >= kchunks) break;
+#pragma unroll
+                for (int nt = 0; nt < 16; ++nt) {
+                    if (nt < ntile) {
+                        const __nv_bfloat16* wr = wsm + (nt * 8 + g) * stride + 16 * kc + 2 * t;
+                        mma_bf16(acc[nt], a[kc], *(const unsigned*)wr, *(const unsigned*)(wr + 8));
+                    }
+                }
+            }
+            if (last) {
+                // bias and output: row g holds columns 2t, 2t+1 of tile 0 (and of tile 1 above 8)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int col = nt * 8 + 2 * t + (q & 1), row = q < 2 ? ra : rb;
+                        if (col < md.nout && row < n) Y[(size_t)row * md.nout + col] = acc[nt][q] + bias[col];
+                    }
+                break;
+            }
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) {
+                const int c0 = 16 * kc + 2 * t;
+                a[kc][0] = pack_f2(fmaxf(acc[2 * kc][0] + bias[c0], 0.f), fmaxf(acc[2 * kc][1] + bias[c0 + 1], 0.f));
+                a[kc][1] = pack_f2(fmaxf(acc[2 * kc][2] + bias[c0], 0.f), fmaxf(acc[2 * kc][3] + bias[c0 + 1], 0.f));
+                a[kc][2] = pack_f2(fmaxf(acc[2 * kc + 1][0] + bias[c0 + 8], 0.f),
+                                   fmaxf(acc[2 * kc + 1][1] + bias[c0 + 9], 0.f));
+                a[kc][3] = pack_f2(fmaxf(acc[2 * kc + 1][2] + bias[c0 + 8], 0.f),
+                                   fmaxf(acc[2 * kc + 1][3] + bias[c0 + 9], 0.f));
+            }
+            kchunks = 8;
+        }
+    }
+}
+
+static bool fused_ok(const pb_mlp* m)
+{
+    return m->width == FUSED_W && m->din[0] <= 32 && m->dout[m->nl - 1] == 16 && m->nl >= 2 &&
+           fused_smem(m->nl) <= 200 * 1024;
+}
+
+static int mlp_forward_fused(pb_mlp* m, const float* X, int n, float* Y)
+{
+    MlpDesc md;
+    for (int l = 0; l < MLP_MAXL; ++l) {
+        md.woff[l] = l < m->nl ? m->woff[l] : 0;
+        md.boff[l] = l < m->nl ? m->boff[l] : 0;
+    }
+    md.nin = m->nin;
+    md.din0 = m->din[0];
+    md.nl = m->nl;
+    md.nout = m->nout;
+    const size_t smem = fused_smem(m->nl);
+    if (cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return mlp_fail(m, PB_ERR_CUDA, "mlp: shared memory attribute failed");
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = (n + 63) / 64;
+    const int grid = std::max(1, std::min(tiles, 2 * nsm));
+    k_mlp_fused<<<grid, 128, smem, m->st>>>(n, X, m->W, md, Y);
+    return cudaGetLastError() == cudaSuccess ? PB_OK : mlp_fail(m, PB_ERR_CUDA, "mlp fused forward launch failed");
+}
+
 extern "C" int pb_mlp_forward(pb_mlp* m, const float* X, int n, float* Y)
 {
     if (!m || !X || !Y || n < 1) return PB_ERR_ARG;
+    if (fused_ok(m)) return mlp_forward_fused(m, X, n, Y);
     int rc = mlp_forward(m, X, n);
     if (rc) return rc;
     // real outputs of the last layer, row-major n x nout

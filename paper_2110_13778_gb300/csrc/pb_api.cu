@@ -192,8 +192,10 @@ extern "C" int pb_build_tree(pb_ctx* c)
     pb_tic(c, PB_T_SINGULAR);
     if ((rc = pb_touching_and_singular(c))) return rc;
     pb_toc(c, PB_T_SINGULAR);
+    pb_tic(c, PB_T_FARSETUP);
     if ((rc = pb_far_setup(c))) return rc;
     if ((rc = pb_near_setup(c))) return rc;
+    pb_toc(c, PB_T_FARSETUP);
     pb_tic(c, PB_T_PCBUILD);
     if ((rc = pb_precond_build(c))) return rc;
     pb_toc(c, PB_T_PCBUILD);
@@ -384,6 +386,11 @@ extern "C" int pb_get_tree_stats(pb_ctx* c, pb_tree_stats* s)
     s->touching = c->ntouch;
     for (int q = 0; q < 4; ++q) s->touch_class[q] = c->touch_class[q];
     s->max_leaf = c->max_leaf;
+    if (c->prm.precond == PB_PRECOND_BLOCK) {
+        s->pc_blocks = c->npcblk;
+        s->pc_max = c->pc_max;
+        s->pc_sum_m3 = c->pc_sum_m3;
+    }
     return PB_OK;
 }
 

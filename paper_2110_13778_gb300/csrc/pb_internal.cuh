@@ -102,6 +102,8 @@ struct pb_ctx {
     long long near_pairs = 0;
     // preconditioner: per leaf a dense (2n x 2n) inverse, unknowns [phi of leaf; dphi of leaf]
     int npcblk = 0;               // preconditioner blocks
+    int pc_max = 0;               // largest block order
+    double pc_sum_m3 = 0;         // sum of m^3 over blocks
     int* pc_begin = nullptr;      // [npcblk + 1] first sorted element of each block
     long long* blk_off = nullptr; // [npcblk + 1] offsets into minv
     void* minv = nullptr;         // inverse blocks, working precision (float in mixed mode)

@@ -24,7 +24,9 @@
 #define GJ_SMEM_BYTES (200 * 1024)
 #define PB_PC_BMAX 96  // largest preconditioner block, in elements
 
-// Assemble the block of leaf c, row-major m x m, into minv + moff[c].
+// Assemble the block of leaf c, row-major m x m, into minv + moff[c]: the one-point entries
+// of every pair (evaluated in the working precision R from FP64 separations) and the mass
+// terms, then the Sauter-Schwab corrections of the touching pairs inside the block.
 template <class R>
 __global__ void k_blk_fill(const int* __restrict__ begin, const long long* __restrict__ moff,
                            const double4_32a* __restrict__ ep, const double4_32a* __restrict__ en,
@@ -36,31 +38,39 @@ __global__ void k_blk_fill(const int* __restrict__ begin, const long long* __res
     R* Mc = minv + moff[c];
     const double inv_eps = 1.0 / eps;
     for (int i = threadIdx.x / 32; i < n; i += blockDim.x / 32) {
-        double4_32a pi = ep[b + i], ni = en[b + i];
+        const double4_32a pi = ep[b + i], ni = en[b + i];
         for (int j = threadIdx.x & 31; j < n; j += 32) {
-            double4_32a pj = ep[b + j], nj = en[b + j];
-            double I[4] = {0, 0, 0, 0};
+            const double4_32a pj = ep[b + j], nj = en[b + j];
+            R K[4] = {0, 0, 0, 0};
             if (i != j) {
-                double K[4];
-                pb_kernels<double>(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, ni.x, ni.y, ni.z, nj.x, nj.y, nj.z, eps,
-                                   inv_eps, kappa, K);
-                for (int q = 0; q < 4; ++q) I[q] = pi.w * pj.w * K[q];
+                pb_kernels<R>((R)(pi.x - pj.x), (R)(pi.y - pj.y), (R)(pi.z - pj.z), (R)ni.x, (R)ni.y, (R)ni.z,
+                              (R)nj.x, (R)nj.y, (R)nj.z, (R)eps, (R)inv_eps, (R)kappa, K);
+                const R aa = (R)(pi.w * pj.w);
+                for (int q = 0; q < 4; ++q) K[q] *= aa;
             }
-            // Sauter-Schwab correction if (i, j) touch (lists are short and sorted)
-            for (int t = toff[b + i]; t < toff[b + i + 1]; ++t)
-                if (tj[t] == b + j)
-                    for (int q = 0; q < 4; ++q) I[q] += corr[4 * t + q];
-            double m11 = -I[1], m12 = -I[0], m21 = -I[3], m22 = -I[2];
+            R m11 = -K[1], m12 = -K[0], m21 = -K[3], m22 = -K[2];
             if (i == j) {
-                m11 += 0.5 * (1.0 + eps) * pi.w;
-                m22 += 0.5 * (1.0 + inv_eps) * pi.w;
+                m11 += (R)(0.5 * (1.0 + eps) * pi.w);
+                m22 += (R)(0.5 * (1.0 + inv_eps) * pi.w);
             }
-            Mc[(size_t)i * m + j] = (R)m11;
-            Mc[(size_t)i * m + n + j] = (R)m12;
-            Mc[(size_t)(n + i) * m + j] = (R)m21;
-            Mc[(size_t)(n + i) * m + n + j] = (R)m22;
+            Mc[(size_t)i * m + j] = m11;
+            Mc[(size_t)i * m + n + j] = m12;
+            Mc[(size_t)(n + i) * m + j] = m21;
+            Mc[(size_t)(n + i) * m + n + j] = m22;
         }
     }
+    __syncthreads();
+    // corrections: each touching pair of the block once, from the target's list
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int t = toff[b + i]; t < toff[b + i + 1]; ++t) {
+            const int j = tj[t] - b;
+            if (j < 0 || j >= n) continue;
+            const double* cr = corr + 4 * (size_t)t;
+            Mc[(size_t)i * m + j] -= (R)cr[1];
+            Mc[(size_t)i * m + n + j] -= (R)cr[0];
+            Mc[(size_t)(n + i) * m + j] -= (R)cr[3];
+            Mc[(size_t)(n + i) * m + n + j] -= (R)cr[2];
+        }
 }
 
 // In-place Gauss-Jordan inversion with partial pivoting. Blocks with m <= mfit are worked
@@ -163,6 +173,131 @@ __global__ void __launch_bounds__(GJ_T) k_blk_gj(const int* __restrict__ begin, 
         for (int t = threadIdx.x; t < m * m; t += GJ_T) g[t] = a[t];
 }
 
+// Register-tiled Gauss-Jordan inversion (FP32, m <= 16 MT) by pivot exchanges without row
+// interchanges: a 16 x 16 thread grid, thread (ty, tx) holding rows ty + 16 a and columns
+// tx + 16 b (a, b < MT) of the block in registers. Step k exchanges the roles of unknown k and
+// equation p (the unused row with the largest |entry| in column k): with a = T[p][k],
+//   T[p][k] <- 1/a,  T[p][j] <- -T[p][j]/a,  T[i][k] <- T[i][k]/a,
+//   T[i][j] <- T[i][j] - T[i][k] T[p][j]/a   (i != p, j != k).
+// After all m exchanges, T[p_k][k'] = (A^-1)[k][p_k'], which the final store applies. The
+// column loop is unrolled by blocks of 16 so that the column a step works on is a
+// compile-time register index; per step, the owners of column k publish it with their
+// partial maxima, the owners of row p publish that row, and every thread updates its
+// MT x MT tile -- two barriers per step (buffers alternate by step parity).
+template <int MT>
+__global__ void __launch_bounds__(256, 1) k_blk_gj_reg(const int* __restrict__ begin, const long long* __restrict__ moff,
+                                                      float* __restrict__ minv, int* __restrict__ singular)
+{
+    constexpr int MC = 16 * MT;
+    __shared__ float colb[2][MC], rowb[2][MC], redv[2][16];
+    __shared__ int redi[2][16], perm[MC], inv[MC];
+    const int c = blockIdx.x;
+    const int m = 2 * (begin[c + 1] - begin[c]);
+    float* g = minv + moff[c];
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    float v[MT][MT];
+#pragma unroll
+    for (int a = 0; a < MT; ++a)
+#pragma unroll
+        for (int b = 0; b < MT; ++b) {
+            const int i = ty + 16 * a, j = tx + 16 * b;
+            v[a][b] = (i < m && j < m) ? g[(size_t)i * m + j] : 0.f;
+        }
+    unsigned used = 0;  // bit a: row ty + 16 a has been a pivot row
+#pragma unroll
+    for (int kb = 0; kb < MT; ++kb) {
+        for (int kk = 0; kk < 16; ++kk) {
+            const int k = 16 * kb + kk;
+            if (k >= m) break;
+            const int s = k & 1;
+            // 1. owners of column k publish it and their largest |entry| among unused rows
+            if (tx == kk) {
+                float best = -1.f;
+                int bi = m;
+#pragma unroll
+                for (int a = 0; a < MT; ++a) {
+                    const int i = ty + 16 * a;
+                    const float x = v[a][kb];
+                    if (i < m) {
+                        colb[s][i] = x;
+                        if (!((used >> a) & 1u) && fabsf(x) > best) {
+                            best = fabsf(x);
+                            bi = i;
+                        }
+                    }
+                }
+                redv[s][ty] = best;
+                redi[s][ty] = bi;
+            }
+            __syncthreads();
+            float best = redv[s][0];
+            int p = redi[s][0];
+            for (int q = 1; q < 16; ++q) {
+                const float o = redv[s][q];
+                const int oi = redi[s][q];
+                if (o > best || (o == best && oi < p)) {
+                    best = o;
+                    p = oi;
+                }
+            }
+            // 2. owners of row p publish it
+            if (ty == (p & 15)) {
+#pragma unroll
+                for (int a = 0; a < MT; ++a)
+                    if (ty + 16 * a == p) {
+                        used |= 1u << a;
+#pragma unroll
+                        for (int b = 0; b < MT; ++b) {
+                            const int j = tx + 16 * b;
+                            if (j < m) rowb[s][j] = v[a][b];
+                        }
+                    }
+            }
+            if (threadIdx.x == 0) {
+                perm[k] = p;
+                inv[p] = k;
+            }
+            __syncthreads();
+            float piv = rowb[s][k];
+            if (!(fabsf(piv) > 0.f)) {
+                if (threadIdx.x == 0) atomicExch(singular, 1);
+                piv = 1.f;
+            }
+            const float ia = 1.f / piv;
+            // 3. the exchange
+            float rk[MT];
+#pragma unroll
+            for (int b = 0; b < MT; ++b) {
+                const int j = tx + 16 * b;
+                rk[b] = j < m ? rowb[s][j] * ia : 0.f;
+            }
+            const bool ownk = tx == kk;
+#pragma unroll
+            for (int a = 0; a < MT; ++a) {
+                const int i = ty + 16 * a;
+                if (i == p) {
+#pragma unroll
+                    for (int b = 0; b < MT; ++b) v[a][b] = (b == kb && ownk) ? ia : -v[a][b] * ia;
+                } else {
+                    const float ck = i < m ? colb[s][i] : 0.f;
+#pragma unroll
+                    for (int b = 0; b < MT; ++b)
+                        v[a][b] = (b == kb && ownk) ? ck * ia : fmaf(-ck, rk[b], v[a][b]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // (A^-1)[inv[i]][perm[j]] = T[i][j]
+#pragma unroll
+    for (int a = 0; a < MT; ++a)
+#pragma unroll
+        for (int b = 0; b < MT; ++b) {
+            const int i = ty + 16 * a, j = tx + 16 * b;
+            if (i < m && j < m) g[(size_t)inv[i] * m + perm[j]] = v[a][b];
+        }
+}
+
 // z = M^-1 r per leaf: one warp per row, lanes stride the columns
 template <class R>
 __global__ void k_blk_apply(int nt, const int* __restrict__ begin, const long long* __restrict__ moff,
@@ -227,6 +362,18 @@ static int blk_build(pb_ctx* c, const long long* dmoff, long long ntot, int mcap
     k_blk_fill<R><<<ncl, 256, 0, c->st>>>(c->pc_begin, dmoff, c->e64p, c->e64n, c->touch_off, c->touch_j, c->corr, eps,
                                            c->prm.kappa, M);
     PB_LAUNCH(c);
+    if (sizeof(R) == 4 && mcap <= 192) {
+        if (mcap <= 128)
+            k_blk_gj_reg<8><<<ncl, 256, 0, c->st>>>(c->pc_begin, dmoff, (float*)M, sing);
+        else
+            k_blk_gj_reg<12><<<ncl, 256, 0, c->st>>>(c->pc_begin, dmoff, (float*)M, sing);
+        PB_LAUNCH(c);
+        int hs = 0;
+        PB_CUDA(c, cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        PB_CUDA(c, cudaStreamSynchronize(c->st));
+        if (hs) return pb_fail(c, PB_ERR_MESH, "a preconditioner block is singular");
+        return PB_OK;
+    }
     // shared memory: col, row, perm (mcap each) + the block itself when it fits
     size_t fixed = sizeof(R) * 2 * (size_t)mcap + sizeof(int) * ((size_t)mcap + 1) + 16;
     int mfit = 0;
@@ -281,6 +428,12 @@ int pb_precond_build(pb_ctx* c)
         mcap = std::max(mcap, (int)m);
     }
     c->npcblk = nb;
+    c->pc_max = mcap;
+    c->pc_sum_m3 = 0;
+    for (int k = 0; k < nb; ++k) {
+        const double m = 2.0 * (pb_[k + 1] - pb_[k]);
+        c->pc_sum_m3 += m * m * m;
+    }
     c->pc_begin = (int*)pb_alloc(c, sizeof(int) * (nb + 1));
     c->blk_off = (long long*)pb_alloc(c, sizeof(long long) * (nb + 1));
     if (!c->blk_off || !c->pc_begin) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");

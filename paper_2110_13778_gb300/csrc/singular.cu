@@ -482,58 +482,67 @@ static void ss_table(int qs, SsTable& T)
         }
 }
 
-// One warp per touching pair, as k_singular; lanes split the class's cube points.
-template <int NS>
+// One warp per unordered touching pair; lanes split the class's cube points. One body serves
+// all three classes (the table's zero coefficients drop the merged edge vectors, and identical
+// triangles pass zero normal projections), so the hot loop is a single copy of the code: three
+// specialised copies overflowed the instruction cache.
 __device__ __forceinline__ void ss_points_ff(int lane, const float2* __restrict__ tab, int tn, int off, int cnt,
                                              const ff (*eP)[3], const ff (*eQ)[3], const ff* proj, ff nxny, ff kap,
                                              ff* acc)
 {
     for (int i = off + lane; i < off + cnt; i += 32) {
-        const ff a0 = ld_ff(tab + i), a1 = ld_ff(tab + tn + i), w = ld_ff(tab + 4 * tn + i);
-        ff b0 = {0.f, 0.f}, b1 = {0.f, 0.f};
-        if (NS <= 2) b1 = ld_ff(tab + 3 * tn + i);
-        if (NS == 1) b0 = ld_ff(tab + 2 * tn + i);
+        const ff a0 = ld_ff(tab + i), a1 = ld_ff(tab + tn + i), b0 = ld_ff(tab + 2 * tn + i),
+                 b1 = ld_ff(tab + 3 * tn + i), w = ld_ff(tab + 4 * tn + i);
         ff d[3];
         for (int c = 0; c < 3; ++c) {
             d[c] = ff_add(ff_mul(a0, eP[0][c]), ff_mul(a1, eP[1][c]));
-            if (NS <= 2) d[c] = ff_sub(d[c], ff_mul(b1, eQ[1][c]));
-            if (NS == 1) d[c] = ff_sub(d[c], ff_mul(b0, eQ[0][c]));
+            d[c] = ff_sub(d[c], ff_add(ff_mul(b0, eQ[0][c]), ff_mul(b1, eQ[1][c])));
         }
         const ff r2 = ff_add(ff_add(ff_sqr(d[0]), ff_sqr(d[1])), ff_sqr(d[2]));
+        // n_x.(x - y) and n_y.(x - y): a triangle's own edges are orthogonal to its normal;
+        // proj = {n_x.eQ0, n_x.eQ1, n_y.eP0, n_y.eP1}
+        const ff nxd = ff_neg(ff_add(ff_mul(b0, proj[0]), ff_mul(b1, proj[1])));
+        const ff nyd = ff_add(ff_mul(a0, proj[2]), ff_mul(a1, proj[3]));
         ff P[6];
-        if (NS == 3) {
-            ff_parts<2>(r2, ff{0.f, 0.f}, ff{0.f, 0.f}, nxny, kap, P);
-            acc[0] = ff_add(acc[0], ff_mul(w, P[0]));
-            acc[1] = ff_add(acc[1], ff_mul(w, P[1]));
-        } else {
-            // n_x.(x - y) and n_y.(x - y): a triangle's own edges are orthogonal to its normal
-            // proj = {n_x.eQ0, n_x.eQ1, n_y.eP0, n_y.eP1}
-            ff nxd = ff_neg(ff_mul(b1, proj[1]));
-            if (NS == 1) nxd = ff_sub(nxd, ff_mul(b0, proj[0]));
-            const ff nyd = ff_add(ff_mul(a0, proj[2]), ff_mul(a1, proj[3]));
-            ff_parts<6>(r2, nxd, nyd, nxny, kap, P);
-            for (int m = 0; m < 6; ++m) acc[m] = ff_add(acc[m], ff_mul(w, P[m]));
-        }
+        ff_parts<6>(r2, nxd, nyd, nxny, kap, P);
+        for (int m = 0; m < 6; ++m) acc[m] = ff_add(acc[m], ff_mul(w, P[m]));
     }
 }
 
-__global__ void __launch_bounds__(256) k_singular_ff(long long npairs, int nt, const int* __restrict__ toff,
-                                                     const int* __restrict__ tj, const int* __restrict__ stris,
-                                                     const int* __restrict__ order, const float2* __restrict__ erec,
-                                                     const float2* __restrict__ tab, int tn, int3 toffs, int3 tcnts,
-                                                     double eps, double kappa, double* __restrict__ corr)
+// Unordered touching pairs: the ordered pairs (k, j) with order[k] <= order[j] (the quadrature is
+// laid out from the triangle of smaller element index), as (k, ordered-pair index).
+template <int PASS>
+__global__ void k_canon(int nt, const int* __restrict__ toff, const int* __restrict__ tj,
+                        const int* __restrict__ order, int* __restrict__ cnt, const int* __restrict__ coff,
+                        int* __restrict__ ck, int* __restrict__ cp)
 {
-    long long pair = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    int n = PASS ? coff[k] : 0;
+    for (int t = toff[k]; t < toff[k + 1]; ++t)
+        if (order[k] <= order[tj[t]]) {
+            if (PASS) {
+                ck[n] = k;
+                cp[n] = t;
+            }
+            ++n;
+        }
+    if (!PASS) cnt[k] = n;
+}
+
+__global__ void __launch_bounds__(256) k_singular_ff(int ncanon, const int* __restrict__ ck,
+                                                     const int* __restrict__ cp, const int* __restrict__ toff,
+                                                     const int* __restrict__ tj, const int* __restrict__ stris,
+                                                     const float2* __restrict__ erec, const float2* __restrict__ tab,
+                                                     int tn, int3 toffs, int3 tcnts, ff kap, ff epsf, ff iepsf,
+                                                     double* __restrict__ corr)
+{
+    const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
-    if (pair >= npairs) return;
-    int lo = 0, hi = nt;
-    while (hi - lo > 1) {
-        int m = (lo + hi) / 2;
-        if (toff[m] <= pair) lo = m;
-        else hi = m;
-    }
-    const int k = lo, j = tj[pair];
-    if (order[k] > order[j]) return;
+    if (w >= ncanon) return;
+    const int k = ck[w];
+    const long long pair = cp[w];
+    const int j = tj[pair];
     // local vertex indices (0..2) of both triangles, shared vertices first in k's order
     int oi[3], oj[3], ns = 0;
     if (k == j) {
@@ -566,40 +575,43 @@ __global__ void __launch_bounds__(256) k_singular_ff(long long npairs, int nt, c
         ni[c] = ld_ff(rk + 9 + c);
         nj[c] = ld_ff(rj + 9 + c);
     }
-    const ff kap = ff_from(kappa);
     const ff nxny = ff_dot3(ni, nj);
     ff acc[6];
     for (int m = 0; m < 6; ++m) acc[m] = ff{0.f, 0.f};
-    if (ns == 3) {
-        ss_points_ff<3>(lane, tab, tn, toffs.z, tcnts.z, eP, eQ, nullptr, nxny, kap, acc);
-    } else {
-        const ff proj[4] = {ff_dot3(ni, eQ[0]), ff_dot3(ni, eQ[1]), ff_dot3(nj, eP[0]), ff_dot3(nj, eP[1])};
-        if (ns == 2) ss_points_ff<2>(lane, tab, tn, toffs.y, tcnts.y, eP, eQ, proj, nxny, kap, acc);
-        else ss_points_ff<1>(lane, tab, tn, toffs.x, tcnts.x, eP, eQ, proj, nxny, kap, acc);
+    const ff z = {0.f, 0.f};
+    ff proj[4] = {z, z, z, z};
+    if (ns < 3) {
+        proj[0] = ff_dot3(ni, eQ[0]);
+        proj[1] = ff_dot3(ni, eQ[1]);
+        proj[2] = ff_dot3(nj, eP[0]);
+        proj[3] = ff_dot3(nj, eP[1]);
     }
+    const int off = ns == 3 ? toffs.z : ns == 2 ? toffs.y : toffs.x;
+    const int cnt = ns == 3 ? tcnts.z : ns == 2 ? tcnts.y : tcnts.x;
+    ss_points_ff(lane, tab, tn, off, cnt, eP, eQ, proj, nxny, kap, acc);
     for (int m = 0; m < 6; ++m)
         for (int o = 16; o > 0; o >>= 1) {
             ff v = {__shfl_xor_sync(0xffffffffu, acc[m].h, o), __shfl_xor_sync(0xffffffffu, acc[m].l, o)};
             acc[m] = ff_add(acc[m], v);
         }
-    if (lane > 1 || (lane == 1 && k == j)) return;
-    // lane 0 writes (k, j), lane 1 writes (j, k): target t, source s
-    const float2* rt = lane ? rj : rk;
-    const float2* rs = lane ? rk : rj;
+    // Every lane now holds the sums. Even lanes assemble (k, j), odd lanes (j, k) (target t,
+    // source s); lanes 0-7 then store one entry each, so the FP64 conversions issue once.
+    const int o = lane & 1;
+    const float2* rt = o ? rj : rk;
+    const float2* rs = o ? rk : rj;
     const ff At = ld_ff(rt + 15), As = ld_ff(rs + 15);
     const ff jac = ff_mul_f(ff_mul(At, As), 4.0f);
     for (int m = 0; m < 6; ++m) acc[m] = ff_mul(acc[m], jac);
-    const ff EPS = ff_from(eps), IEPS = ff_from(1.0 / eps);
     // exact integrals; for (j, k) the normals exchange roles (k_singular's assembly)
     ff I[4];
     I[0] = acc[0];
     I[3] = acc[1];
-    if (!lane) {
-        I[1] = ff_sub(ff_mul(EPS, acc[3]), acc[2]);
-        I[2] = ff_sub(ff_mul(acc[5], IEPS), acc[4]);
+    if (!o) {
+        I[1] = ff_sub(ff_mul(epsf, acc[3]), acc[2]);
+        I[2] = ff_sub(ff_mul(acc[5], iepsf), acc[4]);
     } else {
-        I[1] = ff_sub(acc[4], ff_mul(EPS, acc[5]));
-        I[2] = ff_sub(acc[2], ff_mul(acc[3], IEPS));
+        I[1] = ff_sub(acc[4], ff_mul(epsf, acc[5]));
+        I[2] = ff_sub(acc[2], ff_mul(acc[3], iepsf));
     }
     long long q = pair;
     if (k != j) {
@@ -613,15 +625,17 @@ __global__ void __launch_bounds__(256) k_singular_ff(long long npairs, int nt, c
         ff P[6];
         ff_parts<6>(ff_dot3(d, d), ff_dot3(nt_, d), ff_dot3(ns_, d), ff_dot3(nt_, ns_), kap, P);
         const ff AA = ff_mul(At, As);
-        const ff reg[4] = {P[0], ff_sub(ff_mul(EPS, P[3]), P[2]), ff_sub(ff_mul(P[5], IEPS), P[4]), P[1]};
+        const ff reg[4] = {P[0], ff_sub(ff_mul(epsf, P[3]), P[2]), ff_sub(ff_mul(P[5], iepsf), P[4]), P[1]};
         for (int m = 0; m < 4; ++m) I[m] = ff_sub(I[m], ff_mul(AA, reg[m]));
-        if (lane) {
+        if (o) {
             q = toff[j];
             while (q < toff[j + 1] && tj[q] != k) ++q;
-            if (q >= toff[j + 1]) return;
         }
     }
-    for (int m = 0; m < 4; ++m) corr[4 * q + m] = ff_to(I[m]);
+    const int m = (lane >> 1) & 3;
+    const ff v = m == 0 ? I[0] : m == 1 ? I[1] : m == 2 ? I[2] : I[3];
+    const bool store = lane < 8 && !(o && (k == j || q >= toff[j + 1]));
+    if (store) corr[4 * q + m] = ff_to(v);
 }
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
@@ -703,10 +717,34 @@ int pb_touching_and_singular(pb_ctx* c)
     PB_CUDA(c, cudaMemcpyAsync(tab, T.rec.data(), sizeof(float2) * T.rec.size(), cudaMemcpyHostToDevice, c->st));
     k_elem_ff<<<nblk(nt, B), B, 0, c->st>>>(nt, c->stris, c->verts, c->e64p, c->e64n, erec);
     PB_LAUNCH(c);
-    k_singular_ff<<<nblk(htot, 8), 256, 0, c->st>>>(htot, nt, c->touch_off, c->touch_j, c->stris, c->order, erec, tab,
+    // unordered pairs
+    int* ccnt = (int*)pb_alloc(c, sizeof(int) * (nt + 1));
+    int* coff = (int*)pb_alloc(c, sizeof(int) * (nt + 1));
+    if (!ccnt || !coff) return pb_fail(c, PB_ERR_NOMEM, "singular: out of memory");
+    PB_CUDA(c, cudaMemsetAsync(ccnt + nt, 0, sizeof(int), c->st));
+    k_canon<0><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, ccnt, nullptr, nullptr, nullptr);
+    PB_LAUNCH(c);
+    {
+        size_t ctmp = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, ctmp, ccnt, coff, nt + 1, c->st);
+        void* cbuf = nullptr;
+        PB_CUDA(c, cudaMallocAsync(&cbuf, ctmp, c->st));
+        cub::DeviceScan::ExclusiveSum(cbuf, ctmp, ccnt, coff, nt + 1, c->st);
+        PB_LAUNCH(c);
+        PB_CUDA(c, cudaFreeAsync(cbuf, c->st));
+    }
+    int ncanon = 0;
+    PB_CUDA(c, cudaMemcpyAsync(&ncanon, coff + nt, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    int* ck = (int*)pb_alloc(c, sizeof(int) * (ncanon + 1));
+    int* cp = (int*)pb_alloc(c, sizeof(int) * (ncanon + 1));
+    if (!ck || !cp) return pb_fail(c, PB_ERR_NOMEM, "singular: out of memory");
+    k_canon<1><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, nullptr, coff, ck, cp);
+    PB_LAUNCH(c);
+    k_singular_ff<<<nblk(ncanon, 8), 256, 0, c->st>>>(ncanon, ck, cp, c->touch_off, c->touch_j, c->stris, erec, tab,
                                                     T.n, make_int3(T.off[0], T.off[1], T.off[2]),
-                                                    make_int3(T.cnt[0], T.cnt[1], T.cnt[2]), eps, c->prm.kappa,
-                                                    c->corr);
+                                                    make_int3(T.cnt[0], T.cnt[1], T.cnt[2]), ff_from(c->prm.kappa),
+                                                    ff_from(eps), ff_from(1.0 / eps), c->corr);
     PB_LAUNCH(c);
     // the table's host copy must outlive the queued upload
     PB_CUDA(c, cudaStreamSynchronize(c->st));

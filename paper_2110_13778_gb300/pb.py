@@ -28,7 +28,7 @@ EXPORTS = [
     "pb_get_launch_count", "pb_solvation_energy_noalloc", "pb_solve_states",
     "pb_mlp_create", "pb_mlp_destroy", "pb_mlp_last_error", "pb_mlp_param_count", "pb_mlp_get_params",
     "pb_mlp_set_params", "pb_mlp_forward", "pb_mlp_gradient", "pb_mlp_train_step", "pb_features",
-    "pb_learned_guess",
+    "pb_learned_guess", "pb_measure_alu_peaks",
 ]
 NFEAT = 18
 NSTAT = 20
@@ -59,6 +59,7 @@ class pb_tree_stats(ctypes.Structure):
         ("levels", ctypes.c_int), ("nclusters", ctypes.c_int * 11), ("nnear", ctypes.c_longlong * 11),
         ("ninter", ctypes.c_longlong * 11), ("order", ctypes.c_int * 11), ("near_pairs", ctypes.c_longlong),
         ("touching", ctypes.c_longlong), ("max_leaf", ctypes.c_int), ("touch_class", ctypes.c_longlong * 4),
+        ("pc_blocks", ctypes.c_int), ("pc_max", ctypes.c_int), ("pc_sum_m3", ctypes.c_double),
     ]
 
 
@@ -109,6 +110,7 @@ def lib():
         L.pb_mlp_train_step.argtypes = [vp, vp, vp, c_int, ctypes.c_float, fp]
         L.pb_features.argtypes = [vp, vp, vp, vp, dp]
         L.pb_learned_guess.argtypes = [vp, vp, vp]
+        L.pb_measure_alu_peaks.argtypes = [vp, dp, dp]
         _lib = L
     return _lib
 
@@ -224,6 +226,9 @@ def pb_get_tree_stats(ctx):
         "touching": s.touching,
         "touch_class": list(s.touch_class),
         "max_leaf": s.max_leaf,
+        "pc_blocks": s.pc_blocks,
+        "pc_max": s.pc_max,
+        "pc_sum_m3": s.pc_sum_m3,
     }
 
 
@@ -247,7 +252,7 @@ def pb_set_timing(ctx, enable):
 
 
 TIMING_SLOTS = ["near", "corr", "up", "m2l", "down", "precond", "arnoldi", "singular", "tree", "pcbuild",
-                "energy", "rhs"]
+                "energy", "rhs", "farsetup"]
 
 
 def pb_get_timing(ctx):
@@ -347,3 +352,12 @@ def pb_features(ctx, F, x=None, T=None):
 
 def pb_learned_guess(ctx, net, x):
     _check(ctx, lib().pb_learned_guess(ctx, net, _ptr(x)))
+
+
+def pb_measure_alu_peaks(stream=0):
+    """(FP32, FP64) FMA throughput of the current device in TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = lib().pb_measure_alu_peaks(ctypes.c_void_p(stream), ctypes.byref(a), ctypes.byref(b))
+    if rc != PB_OK:
+        raise PBError(rc, "pb_measure_alu_peaks failed")
+    return a.value, b.value

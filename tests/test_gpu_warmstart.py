@@ -72,6 +72,23 @@ def test_forward_matches_oracle(net, n):
     assert _rel(y, yf) < 3e-2
 
 
+@pytest.mark.parametrize("shape", [(5, 64, 2, 3), (16, 128, 1, 17), (40, 128, 2, 2)])
+def test_forward_layered_path_matches_oracle(shape):
+    # shapes outside the fused kernel (width != 128, > 16 outputs, > 32 inputs) take the
+    # layer-by-layer tensor-core GEMMs
+    h = pb.pb_mlp_create(*shape, seed=3)
+    try:
+        w = omlp.init_params(shape, 4).astype(np.float32)
+        pb.pb_mlp_set_params(h, w)
+        X = np.random.default_rng(9).standard_normal((300, shape[0])).astype(np.float32)
+        Y = torch.empty((300, shape[3]), device="cuda", dtype=torch.float32)
+        pb.pb_mlp_forward(h, torch.from_numpy(X).cuda(), Y)
+        ye, _ = omlp.forward(w.astype(np.float64), shape, X.astype(np.float64), emulate=True)
+        assert _rel(Y.cpu().numpy(), ye) < 2e-3
+    finally:
+        pb.pb_mlp_destroy(h)
+
+
 @pytest.mark.parametrize("n", [19, 20000 + 5])
 def test_gradient_matches_oracle(net, n):
     w = omlp.init_params(SHAPE, 2).astype(np.float32)
