@@ -281,67 +281,72 @@ __global__ void __launch_bounds__(FAR_T) k_m2l(int p, double kappa, const int* _
 // Setup: the kernel derivatives D^g G0 and D^g Gk of every interaction slot depend only on
 // the geometry, so they are evaluated once (FP64 recurrence, stored in the working
 // precision) in the interleaved slot layout the contraction reads.
+// One warp per slot (target cluster, source cluster): the lanes share the terms of each order
+// of the recurrence, so orders are separated by warp barriers only and eight slots of a block
+// proceed independently. Per-warp scratch: three FP64 term arrays in dynamic shared memory.
 template <class R>
-__global__ void __launch_bounds__(FAR_T) k_m2l_setup(int p, double kappa, const int* __restrict__ soff,
-                                                     const int* __restrict__ ssrc, const double* __restrict__ xc,
-                                                     R* __restrict__ D0, R* __restrict__ Dk)
+__global__ void __launch_bounds__(256) k_m2l_setup(int nslots, int p, double kappa, const int* __restrict__ stgt,
+                                                   const int* __restrict__ ssrc, const double* __restrict__ xc,
+                                                   R* __restrict__ D0, R* __restrict__ Dk)
 {
-    __shared__ double F0[NT_MAX], Fk[NT_MAX], Pk[NT_MAX];
-    const int c = blockIdx.x;
+    extern __shared__ double m2ls[];
     const int T = pb_nterms(p);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * 8 + warp;
+    if (s >= nslots) return;
+    double* F0 = m2ls + (size_t)warp * 3 * T;
+    double* Fk = F0 + T;
+    double* Pk = Fk + T;
     const double i4pi = 0.07957747154594767;
-    for (int s = soff[c]; s < soff[c + 1]; ++s) {
-        const int c2 = ssrc[s];
-        const size_t base = ((size_t)(s >> 5) * T) * 32 + (s & 31);
-        if (c2 < 0) {
-            for (int k = threadIdx.x; k < T; k += FAR_T) {
-                D0[base + (size_t)k * 32] = R(0);
-                Dk[base + (size_t)k * 32] = R(0);
-            }
-            continue;
+    const int c = stgt[s], c2 = ssrc[s];
+    const size_t base = ((size_t)(s >> 5) * T) * 32 + (s & 31);
+    if (c2 < 0) {
+        for (int k = lane; k < T; k += 32) {
+            D0[base + (size_t)k * 32] = R(0);
+            Dk[base + (size_t)k * 32] = R(0);
         }
-        const double d[3] = {xc[3 * c] - xc[3 * c2], xc[3 * c + 1] - xc[3 * c2 + 1], xc[3 * c + 2] - xc[3 * c2 + 2]};
-        const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double r = sqrt(d2), ex = exp(-kappa * r);
-            F0[0] = i4pi / r;
-            Fk[0] = i4pi * ex / r;
-            Pk[0] = i4pi * ex;
-        }
-        __syncthreads();
-        for (int n = 1; n <= p; ++n) {
-            for (int k = pb_nterms(n - 1) + threadIdx.x; k < pb_nterms(n); k += FAR_T) {
-                int kk[3];
-                mi_unpack(c_mi[k], kk[0], kk[1], kk[2]);
-                double a0 = 0, a1 = 0, ak0 = 0, ak1 = 0, ap0 = 0, ap1 = 0;
-                for (int i = 0; i < 3; ++i) {
-                    if (kk[i] >= 1) {
-                        int q = pb_midx(kk[0] - (i == 0), kk[1] - (i == 1), kk[2] - (i == 2));
-                        a0 += d[i] * F0[q];
-                        ak0 += d[i] * Fk[q];
-                        ap0 += d[i] * Pk[q];
-                    }
-                    if (kk[i] >= 2) {
-                        int q = pb_midx(kk[0] - 2 * (i == 0), kk[1] - 2 * (i == 1), kk[2] - 2 * (i == 2));
-                        a1 += F0[q];
-                        ak1 += Fk[q];
-                        ap1 += Pk[q];
-                    }
+        return;
+    }
+    const double d[3] = {xc[3 * c] - xc[3 * c2], xc[3 * c + 1] - xc[3 * c2 + 1], xc[3 * c + 2] - xc[3 * c2 + 2]};
+    const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (lane == 0) {
+        double r = sqrt(d2), ex = exp(-kappa * r);
+        F0[0] = i4pi / r;
+        Fk[0] = i4pi * ex / r;
+        Pk[0] = i4pi * ex;
+    }
+    __syncwarp();
+    for (int n = 1; n <= p; ++n) {
+        for (int k = pb_nterms(n - 1) + lane; k < pb_nterms(n); k += 32) {
+            int kk[3];
+            mi_unpack(c_mi[k], kk[0], kk[1], kk[2]);
+            double a0 = 0, a1 = 0, ak0 = 0, ak1 = 0, ap0 = 0, ap1 = 0;
+            for (int i = 0; i < 3; ++i) {
+                if (kk[i] >= 1) {
+                    int q = pb_midx(kk[0] - (i == 0), kk[1] - (i == 1), kk[2] - (i == 2));
+                    a0 += d[i] * F0[q];
+                    ak0 += d[i] * Fk[q];
+                    ap0 += d[i] * Pk[q];
                 }
-                F0[k] = (-(2.0 * n - 1.0) * a0 - (n - 1.0) * a1) / (d2 * n);
-                Fk[k] = (-(2.0 * n - 1.0) * ak0 - (n - 1.0) * ak1 - kappa * ap0 - kappa * ap1) / (d2 * n);
-                Pk[k] = -kappa * (ak0 + ak1) / n;
+                if (kk[i] >= 2) {
+                    int q = pb_midx(kk[0] - 2 * (i == 0), kk[1] - 2 * (i == 1), kk[2] - 2 * (i == 2));
+                    a1 += F0[q];
+                    ak1 += Fk[q];
+                    ap1 += Pk[q];
+                }
             }
-            __syncthreads();
+            F0[k] = (-(2.0 * n - 1.0) * a0 - (n - 1.0) * a1) / (d2 * n);
+            Fk[k] = (-(2.0 * n - 1.0) * ak0 - (n - 1.0) * ak1 - kappa * ap0 - kappa * ap1) / (d2 * n);
+            Pk[k] = -kappa * (ak0 + ak1) / n;
         }
-        for (int k = threadIdx.x; k < T; k += FAR_T) {
-            int k1, k2, k3;
-            mi_unpack(c_mi[k], k1, k2, k3);
-            double f = c_fact[k1] * c_fact[k2] * c_fact[k3];
-            D0[base + (size_t)k * 32] = (R)(F0[k] * f);
-            Dk[base + (size_t)k * 32] = (R)(Fk[k] * f);
-        }
+        __syncwarp();
+    }
+    for (int k = lane; k < T; k += 32) {
+        int k1, k2, k3;
+        mi_unpack(c_mi[k], k1, k2, k3);
+        double f = c_fact[k1] * c_fact[k2] * c_fact[k3];
+        D0[base + (size_t)k * 32] = (R)(F0[k] * f);
+        Dk[base + (size_t)k * 32] = (R)(Fk[k] * f);
     }
 }
 
@@ -357,15 +362,21 @@ template <class R>
 __global__ void k_m2l_gather(int T, const int* __restrict__ ssrc, const R* __restrict__ s0, const R* __restrict__ sk,
                              R* __restrict__ M0, R* __restrict__ Mk)
 {
-    // one block per chunk of 32 slots; thread (b, lane) pairs walk the T x 32 block
-    const long long chunk = blockIdx.x;
-    const size_t base = (size_t)chunk * T * 32;
-    for (int t = threadIdx.x; t < T * 32; t += blockDim.x) {
-        const int b = t >> 5, lane = t & 31;
-        const int src = ssrc[chunk * 32 + lane];
+    // one block per chunk of 32 slots; thread (b, lane) pairs walk the T x 32 block. The
+    // factors (-1)^|b| / b! are formed once per block.
+    __shared__ R scs[NT_MAX];
+    for (int b = threadIdx.x; b < T; b += blockDim.x) {
         int b1, b2, b3;
         mi_unpack(c_mi[b], b1, b2, b3);
-        const R sc = (R)(((b1 + b2 + b3) & 1 ? -1.0 : 1.0) / (c_fact[b1] * c_fact[b2] * c_fact[b3]));
+        scs[b] = (R)(((b1 + b2 + b3) & 1 ? -1.0 : 1.0) / (c_fact[b1] * c_fact[b2] * c_fact[b3]));
+    }
+    __syncthreads();
+    const long long chunk = blockIdx.x;
+    const size_t base = (size_t)chunk * T * 32;
+    const int src = ssrc[chunk * 32 + (threadIdx.x & 31)];
+    for (int t = threadIdx.x; t < T * 32; t += blockDim.x) {
+        const int b = t >> 5;
+        const R sc = scs[b];
         M0[base + t] = src >= 0 ? s0[(size_t)src * T + b] * sc : R(0);
         Mk[base + t] = src >= 0 ? sk[(size_t)src * T + b] * sc : R(0);
     }
@@ -655,9 +666,11 @@ static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
     std::vector<int> soff(lv.ncl + 1);
     soff[0] = 0;
     for (int k = 0; k < lv.ncl; ++k) soff[k + 1] = soff[k] + ((off[k + 1] - off[k] + 31) / 32) * 32;
-    std::vector<int> ssrc(soff[lv.ncl], -1);
-    for (int k = 0; k < lv.ncl; ++k)
+    std::vector<int> ssrc(soff[lv.ncl], -1), stgt(soff[lv.ncl]);
+    for (int k = 0; k < lv.ncl; ++k) {
         for (int t = off[k]; t < off[k + 1]; ++t) ssrc[soff[k] + (t - off[k])] = idx[t];
+        for (int t = soff[k]; t < soff[k + 1]; ++t) stgt[t] = k;
+    }
     lv.nslots = soff[lv.ncl];
     const int T = pb_nterms(lv.p);
     size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
@@ -671,12 +684,21 @@ static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
         return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
     PB_CUDA(c, cudaMemcpyAsync(lv.slot_off, soff.data(), sizeof(int) * (lv.ncl + 1), cudaMemcpyHostToDevice, c->st));
     PB_CUDA(c, cudaMemcpyAsync(lv.slot_src, ssrc.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, c->st));
-    if (c->prm.precision == PB_MIXED)
-        k_m2l_setup<float><<<lv.ncl, FAR_T, 0, c->st>>>(lv.p, c->prm.kappa, lv.slot_off, lv.slot_src, lv.xc,
-                                                        (float*)lv.D0, (float*)lv.Dk);
-    else
-        k_m2l_setup<double><<<lv.ncl, FAR_T, 0, c->st>>>(lv.p, c->prm.kappa, lv.slot_off, lv.slot_src, lv.xc,
-                                                         (double*)lv.D0, (double*)lv.Dk);
+    int* stg = (int*)pb_alloc(c, sizeof(int) * (lv.nslots + 1));
+    if (!stg) return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
+    PB_CUDA(c, cudaMemcpyAsync(stg, stgt.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, c->st));
+    const size_t smem = sizeof(double) * 3 * (size_t)T * 8;
+    const unsigned nb = (unsigned)((lv.nslots + 7) / 8);
+    if (nb == 0) {
+    } else if (c->prm.precision == PB_MIXED) {
+        PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_m2l_setup<float><<<nb, 256, smem, c->st>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
+                                                     (float*)lv.D0, (float*)lv.Dk);
+    } else {
+        PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_m2l_setup<double><<<nb, 256, smem, c->st>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
+                                                      (double*)lv.D0, (double*)lv.Dk);
+    }
     PB_LAUNCH(c);
     // host vectors above are read by the queued copies: wait before they go out of scope
     PB_CUDA(c, cudaStreamSynchronize(c->st));
