@@ -206,6 +206,26 @@ int pb_get_timing(pb_ctx* ctx, double* out);
 /* Number of this library's kernel launches queued on ctx since it was created. */
 int pb_get_launch_count(pb_ctx* ctx, long long* out);
 
+/* Autotuner (no counterpart in the paper, which sets the leaf size and order by hand): on the
+ * uploaded molecule, tries leaf sizes {32, 48, 64, 96, 128} x orders {4, 6, 8} (uniform order,
+ * the context's eta0 and precision), timing pb_build_tree and pb_matvec with CUDA events and
+ * measuring the product's relative L2 error against an order-10 product on a fixed
+ * pseudo-random density. At each leaf size the orders are tried upwards until one meets tol.
+ * Chooses the candidate with the least build_ms + matvecs_per_solve x matvec_ms among those
+ * within tol (else the most accurate), stores its leaf size and order in the context's
+ * parameters and leaves the context built with them. out: host pointer. Synchronises; takes
+ * about 16 builds. */
+typedef struct pb_tune_result {
+    int leaf_size;      /* chosen leaf size s */
+    int p;              /* chosen order (all levels) */
+    double matvec_ms;   /* median product time of the choice */
+    double build_ms;    /* its pb_build_tree time */
+    double rel_err;     /* its product error against the order-10 reference */
+    int tried;          /* candidates built */
+    int met_tolerance;  /* 1 if rel_err <= tol */
+} pb_tune_result;
+int pb_autotune(pb_ctx* ctx, double tol, int matvecs_per_solve, pb_tune_result* out);
+
 /* Measured FMA throughput of the current device in TFLOP/s (2 flops per FMA): eight
  * independent FMA chains per thread on 8 x (SM count) blocks of 256 threads, timed with CUDA
  * events on stream (cudaStream_t, NULL = default). The roofline denominators of the

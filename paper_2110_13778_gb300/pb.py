@@ -28,7 +28,7 @@ EXPORTS = [
     "pb_get_launch_count", "pb_solvation_energy_noalloc", "pb_solve_states",
     "pb_mlp_create", "pb_mlp_destroy", "pb_mlp_last_error", "pb_mlp_param_count", "pb_mlp_get_params",
     "pb_mlp_set_params", "pb_mlp_forward", "pb_mlp_gradient", "pb_mlp_train_step", "pb_features",
-    "pb_learned_guess", "pb_measure_alu_peaks",
+    "pb_learned_guess", "pb_measure_alu_peaks", "pb_autotune",
 ]
 NFEAT = 18
 NSTAT = 20
@@ -52,6 +52,12 @@ class pb_params(ctypes.Structure):
 class pb_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("matvecs", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("status", ctypes.c_int), ("initial_residual", ctypes.c_double)]
+
+
+class pb_tune_result(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("p", ctypes.c_int), ("matvec_ms", ctypes.c_double),
+                ("build_ms", ctypes.c_double), ("rel_err", ctypes.c_double), ("tried", ctypes.c_int),
+                ("met_tolerance", ctypes.c_int)]
 
 
 class pb_tree_stats(ctypes.Structure):
@@ -111,6 +117,7 @@ def lib():
         L.pb_features.argtypes = [vp, vp, vp, vp, dp]
         L.pb_learned_guess.argtypes = [vp, vp, vp]
         L.pb_measure_alu_peaks.argtypes = [vp, dp, dp]
+        L.pb_autotune.argtypes = [vp, c_double, c_int, ctypes.POINTER(pb_tune_result)]
         _lib = L
     return _lib
 
@@ -361,3 +368,10 @@ def pb_measure_alu_peaks(stream=0):
     if rc != PB_OK:
         raise PBError(rc, "pb_measure_alu_peaks failed")
     return a.value, b.value
+
+
+def pb_autotune(ctx, tol=1e-4, matvecs_per_solve=10):
+    """Choose leaf size and order for the uploaded molecule; leaves ctx built with them."""
+    r = pb_tune_result()
+    _check(ctx, lib().pb_autotune(ctx, tol, matvecs_per_solve, ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in pb_tune_result._fields_}

@@ -86,3 +86,27 @@ def dense_mesh(m, q):
     from paper_2110_13778_gb300.inputs import Mesh
 
     return Mesh(m.verts, m.tris, m.qpos, q)
+
+
+@pytest.mark.parametrize("prec", [pb.PB_FP64, pb.PB_MIXED])
+def test_autotune_picks_an_accurate_configuration(mol, prec):
+    m, ph, A = mol
+    xo = np.linalg.solve(A, dense.rhs(m, ph))
+    Eo = dense.energy(m, ph, xo)
+    ctx = pb.pb_create(pb.params(eta0=0.7, leaf_size=64, p=8, precision=prec))
+    try:
+        pb.pb_mesh_upload(ctx, m.verts, m.tris, m.qpos, m.q)
+        r = pb.pb_autotune(ctx, tol=1e-4, matvecs_per_solve=10)
+        assert r["met_tolerance"] == 1 and r["rel_err"] <= 1e-4
+        assert r["leaf_size"] in (32, 48, 64, 96, 128) and r["p"] in (4, 6, 8)
+        assert r["tried"] >= 5 and r["matvec_ms"] > 0
+        st = pb.pb_get_tree_stats(ctx)
+        assert all(o == r["p"] for o in st["order"][1:])
+        # the context is left built with the choice and solves to the oracle's energy
+        x = torch.zeros(2 * m.nt, device="cuda", dtype=torch.float64)
+        info = pb.pb_gmres_solve(ctx, x, tol=1e-6, max_iter=300, restart=50)
+        assert info.status == pb.PB_OK
+        E = pb.pb_solvation_energy(ctx, x)
+        assert abs(E - Eo) < 1e-3 * abs(Eo), (E, Eo)
+    finally:
+        pb.pb_destroy(ctx)
