@@ -71,6 +71,7 @@ def args_parse():
     ap.add_argument("--molecules", type=int, default=8)
     ap.add_argument("--states", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--states-mode", default="batched", choices=["batched", "sequential"])
     return ap.parse_args()
 
 
@@ -498,7 +499,8 @@ def run_batch(a):
         mv = 0
         for cx, m, Q, X in zip(ctxs, mols, states, Xs):
             pb.pb_build_tree(cx)
-            E, infos = pb.pb_solve_states(cx, Q, X, tol=a.tol, max_iter=500, restart=50, warm=True)
+            E, infos = pb.pb_solve_states(cx, Q, X, tol=a.tol, max_iter=500, restart=50,
+                                          warm=2 if a.states_mode == "batched" else True)
             mv += sum(i.matvecs * m.nt for i in infos)
         return mv
 
@@ -522,7 +524,7 @@ def run_batch(a):
             "dtype": "f32+f64" if a.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": f"{a.molecules} protein-like molecules ({[int(n) for n in sizes]} atoms, "
                                    f"{[m.nt for m in mols]} triangles) x {a.states} charge states",
-                       "eta0": a.eta0,
+                       "eta0": a.eta0, "states": a.states_mode,
                        "autotune": ({"leaf_size": [t["leaf_size"] for t in tuned], "p": [t["p"] for t in tuned],
                                      "rel_err": [t["rel_err"] for t in tuned], "seconds": t_tune}
                                     if tuned else {"leaf_size": a.leaf, "p": a.p})}}))

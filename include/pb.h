@@ -131,6 +131,13 @@ int pb_build_tree(pb_ctx* ctx);
  * far field). x, y: device pointers, 2N doubles each, must not overlap. Queued, no sync. */
 int pb_matvec(pb_ctx* ctx, const double* x, double* y);
 
+/* nr products at once, Y_q = A X_q for q < nr (1 <= nr <= PB_MAX_RHS): X and Y are device
+ * pointers to nr x 2N doubles (vector q at + 2 N q), element order. The geometry-only work
+ * is shared: in mixed precision each near-field pair is evaluated once for up to 16 vectors
+ * and every far-field launch covers all nr vectors; FP64 applies the near field per vector.
+ * Queues the work. No counterpart in the paper. */
+int pb_matvec_multi(pb_ctx* ctx, const double* X, double* Y, int nr);
+
 /* b = [b1; b2] of the Galerkin right-hand side (source_terms) by the one-point rule.
  * b: device pointer, 2N doubles. Queued, no sync. */
 int pb_rhs(pb_ctx* ctx, double* b);
@@ -153,8 +160,12 @@ int pb_gmres_solve(pb_ctx* ctx, double* x, double tol, int max_iter, int restart
  * by all states. q: host pointer, nrhs x nc doubles (state s at q + s nc). X: device
  * pointer, nrhs x 2N doubles (state s at X + 2 N s), written with the solutions. E: host
  * pointer, nrhs doubles, written with the solvation energies in kcal/mol (may be NULL).
- * warm != 0 starts each state's GMRES from the previous state's solution (state 0 from
- * zero). infos: host pointer to nrhs records (may be NULL). On return the uploaded charges
+ * warm = 0: each state from zero, one after the other; 1: each state from the previous
+ * state's solution (state 0 from zero); 2: state 0 from zero, then the other states together,
+ * in batches of up to PB_MAX_RHS, from state 0's solution: their GMRES iterations run in
+ * lockstep, each Arnoldi step applying one batched product (pb_matvec_multi's kernels) to all
+ * of them; every state keeps its own Krylov basis, so each result is what its own GMRES would
+ * give. infos: host pointer to nrhs records (may be NULL). On return the uploaded charges
  * are those of the last state. Synchronises. */
 int pb_solve_states(pb_ctx* ctx, const double* q, int nrhs, double* X, double* E, double tol, int max_iter,
                     int restart, int warm, pb_solve_info* infos);
@@ -186,6 +197,9 @@ int pb_matvec_part(pb_ctx* ctx, const double* x, double* y, int which);
  * s the pair out[2s] = total milliseconds, out[2s+1] = number of timed launches, and resets
  * the counts. out: host double[2 * PB_TIMING_SLOTS]. At most 256 launches per slot are
  * remembered between two reads. */
+/* Largest number of right-hand sides of one batched call (pb_matvec_multi, batched solve). */
+#define PB_MAX_RHS 64
+
 #define PB_TIMING_SLOTS 13
 #define PB_T_NEAR 0       /* near-field kernel (one-point rule + mass terms) */
 #define PB_T_CORR 1       /* Sauter-Schwab corrections of touching pairs */

@@ -48,8 +48,13 @@ template <class R>
 __global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restrict__ begin,
                                                const double* __restrict__ xc, const double4_32a* __restrict__ ep,
                                                const double4_32a* __restrict__ en, const double* __restrict__ xs,
-                                               double eps, R* __restrict__ sig0, R* __restrict__ sigk)
+                                               double eps, R* __restrict__ sig0, R* __restrict__ sigk,
+                                               long long xstr, long long sstr)
 {
+    // right-hand side blockIdx.y: its density at xs + y xstr, its moments at sig + y sstr
+    xs += blockIdx.y * xstr;
+    sig0 += blockIdx.y * sstr;
+    sigk += blockIdx.y * sstr;
     __shared__ R pw[FAR_T][3][PB_PMAX + 1];
     __shared__ R sn[FAR_T][3];
     __shared__ R sw[FAR_T][2];
@@ -119,8 +124,12 @@ template <class R>
 __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __restrict__ cbeg,
                                                const double* __restrict__ xp, const double* __restrict__ xch,
                                                const R* __restrict__ c0, const R* __restrict__ ck,
-                                               R* __restrict__ s0, R* __restrict__ sk)
+                                               R* __restrict__ s0, R* __restrict__ sk, long long cstr, long long pstr)
 {
+    c0 += blockIdx.y * cstr;
+    ck += blockIdx.y * cstr;
+    s0 += blockIdx.y * pstr;
+    sk += blockIdx.y * pstr;
     __shared__ R tp[8][3][PB_PMAX + 1];
     __shared__ R sbin[PB_PMAX + 1][PB_PMAX + 1];  // binomials, read with thread-dependent indices
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -178,8 +187,12 @@ template <class R>
 __global__ void __launch_bounds__(FAR_T) k_m2l(int p, double kappa, const int* __restrict__ ioff,
                                                const int* __restrict__ iidx, const double* __restrict__ xc,
                                                const R* __restrict__ s0, const R* __restrict__ sk,
-                                               R* __restrict__ l0, R* __restrict__ lk)
+                                               R* __restrict__ l0, R* __restrict__ lk, long long str)
 {
+    s0 += blockIdx.y * str;
+    sk += blockIdx.y * str;
+    l0 += blockIdx.y * str;
+    lk += blockIdx.y * str;
     __shared__ R F0[NT_MAX], Fk[NT_MAX], Pk[NT_MAX];
     __shared__ R M0[NT_MAX], Mk[NT_MAX];
     const int c = blockIdx.x;
@@ -360,8 +373,12 @@ __global__ void __launch_bounds__(256) k_m2l_setup(int nslots, int p, double kap
 // (-1)^|b| sigma^b(src(s)) / b!, zero for padding slots.
 template <class R>
 __global__ void k_m2l_gather(int T, const int* __restrict__ ssrc, const R* __restrict__ s0, const R* __restrict__ sk,
-                             R* __restrict__ M0, R* __restrict__ Mk)
+                             R* __restrict__ M0, R* __restrict__ Mk, long long sstr, long long mstr)
 {
+    s0 += blockIdx.y * sstr;
+    sk += blockIdx.y * sstr;
+    M0 += blockIdx.y * mstr;
+    Mk += blockIdx.y * mstr;
     // one block per chunk of 32 slots; thread (b, lane) pairs walk the T x 32 block. The
     // factors (-1)^|b| / b! are formed once per block.
     __shared__ R scs[NT_MAX];
@@ -443,8 +460,14 @@ template <int P>
 __global__ void __launch_bounds__(32, 1) k_m2l_tma(int ncl, const int* __restrict__ soff, const float* __restrict__ D0,
                                                    const float* __restrict__ Dk, const float* __restrict__ M0,
                                                    const float* __restrict__ Mk, float* __restrict__ l0,
-                                                   float* __restrict__ lk, int* __restrict__ err)
+                                                   float* __restrict__ lk, int* __restrict__ err, long long mstr,
+                                                   long long lstr)
 {
+    // right-hand side blockIdx.y: the same derivative tables, its own gathered moments
+    M0 += blockIdx.y * mstr;
+    Mk += blockIdx.y * mstr;
+    l0 += blockIdx.y * lstr;
+    lk += blockIdx.y * lstr;
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr unsigned CH = T * 32 * sizeof(float);  // bytes of one chunk block (multiple of 16)
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -514,8 +537,13 @@ __global__ void __launch_bounds__(32, 1) k_m2l_tma(int ncl, const int* __restric
 template <int P, class R>
 __global__ void __launch_bounds__(32) k_m2l_chunks(int ncl, const int* __restrict__ soff, const R* __restrict__ D0,
                                                    const R* __restrict__ Dk, const R* __restrict__ M0,
-                                                   const R* __restrict__ Mk, R* __restrict__ l0, R* __restrict__ lk)
+                                                   const R* __restrict__ Mk, R* __restrict__ l0, R* __restrict__ lk,
+                                                   long long mstr, long long lstr)
 {
+    M0 += blockIdx.y * mstr;
+    Mk += blockIdx.y * mstr;
+    l0 += blockIdx.y * lstr;
+    lk += blockIdx.y * lstr;
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
     extern __shared__ __align__(128) unsigned char dsm[];
     R* Ms = (R*)dsm;  // [T * 33] (also the reduction scratch)
@@ -548,8 +576,12 @@ template <class R>
 __global__ void __launch_bounds__(FAR_T) k_l2l(int pp, int pc, const int* __restrict__ parent,
                                                const double* __restrict__ xp, const double* __restrict__ xch,
                                                const R* __restrict__ lp0, const R* __restrict__ lpk,
-                                               R* __restrict__ lc0, R* __restrict__ lck)
+                                               R* __restrict__ lc0, R* __restrict__ lck, long long pstr, long long cstr)
 {
+    lp0 += blockIdx.y * pstr;
+    lpk += blockIdx.y * pstr;
+    lc0 += blockIdx.y * cstr;
+    lck += blockIdx.y * cstr;
     __shared__ R tp[3][PB_PMAX + 1];
     __shared__ R sbin[PB_PMAX + 1][PB_PMAX + 1];  // binomials, read with thread-dependent indices
     for (int t = threadIdx.x; t < (PB_PMAX + 1) * (PB_PMAX + 1); t += blockDim.x)
@@ -592,8 +624,12 @@ template <class R>
 __global__ void __launch_bounds__(FAR_T) k_l2p(int nt, int p, double eps, const int* __restrict__ begin,
                                                const double* __restrict__ xc, const double4_32a* __restrict__ ep,
                                                const double4_32a* __restrict__ en, const R* __restrict__ l0,
-                                               const R* __restrict__ lk, double* __restrict__ ys)
+                                               const R* __restrict__ lk, double* __restrict__ ys, long long lstr,
+                                               long long ystr)
 {
+    l0 += blockIdx.y * lstr;
+    lk += blockIdx.y * lstr;
+    ys += blockIdx.y * ystr;
     __shared__ R A1[NT_MAX], A2[NT_MAX];
     __shared__ R pw[FAR_T][3][PB_PMAX + 1];
     const int c = blockIdx.x;
@@ -706,31 +742,57 @@ static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
 }
 
 template <int P, class R>
-static int m2l_fast_launch(pb_ctx* c, PbLevel& lv)
+static int m2l_fast_launch(pb_ctx* c, PbLevel& lv, int nr)
 {
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
-    k_m2l_gather<R><<<(unsigned)(lv.nslots / 32), 256, 0, c->st>>>(T, lv.slot_src, (const R*)lv.sig0,
-                                                                   (const R*)lv.sigk, (R*)lv.Mg0, (R*)lv.Mgk);
+    const long long sstr = (long long)lv.ncl * T, mstr = (long long)lv.nslots * T;
+    k_m2l_gather<R><<<dim3((unsigned)(lv.nslots / 32), nr), 256, 0, c->st>>>(
+        T, lv.slot_src, (const R*)lv.sig0, (const R*)lv.sigk, (R*)lv.Mg0, (R*)lv.Mgk, sstr, mstr);
     PB_LAUNCH(c);
     if constexpr (sizeof(R) == sizeof(float)) {
         size_t smem = 4 * (size_t)T * 32 * sizeof(float);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_tma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_tma<P><<<lv.ncl, 32, smem, c->st>>>(lv.ncl, lv.slot_off, (const float*)lv.D0, (const float*)lv.Dk,
-                                                   (const float*)lv.Mg0, (const float*)lv.Mgk, (float*)lv.lam0,
-                                                   (float*)lv.lamk, c->dev_err);
+        k_m2l_tma<P><<<dim3(lv.ncl, nr), 32, smem, c->st>>>(lv.ncl, lv.slot_off, (const float*)lv.D0,
+                                                             (const float*)lv.Dk, (const float*)lv.Mg0,
+                                                             (const float*)lv.Mgk, (float*)lv.lam0, (float*)lv.lamk,
+                                                             c->dev_err, mstr, sstr);
     } else {
         size_t smem = (size_t)T * 33 * sizeof(R);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_chunks<P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_chunks<P, R><<<lv.ncl, 32, smem, c->st>>>(lv.ncl, lv.slot_off, (const R*)lv.D0, (const R*)lv.Dk,
-                                                        (const R*)lv.Mg0, (const R*)lv.Mgk, (R*)lv.lam0,
-                                                        (R*)lv.lamk);
+        k_m2l_chunks<P, R><<<dim3(lv.ncl, nr), 32, smem, c->st>>>(lv.ncl, lv.slot_off, (const R*)lv.D0,
+                                                                  (const R*)lv.Dk, (const R*)lv.Mg0, (const R*)lv.Mgk,
+                                                                  (R*)lv.lam0, (R*)lv.lamk, mstr, sstr);
     }
     PB_LAUNCH(c);
     return PB_OK;
 }
 
+// moments, local coefficients and gathered moments for nr right-hand sides at once
+int pb_far_reserve(pb_ctx* c, int nr)
+{
+    if (nr <= c->far_nr) return PB_OK;
+    size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
+    for (int l = 1; l <= c->L; ++l) {
+        PbLevel& lv = c->lev[l];
+        const size_t T = pb_nterms(lv.p), n = (size_t)lv.ncl * T * nr;
+        lv.sig0 = pb_alloc(c, rs * n);
+        lv.sigk = pb_alloc(c, rs * n);
+        lv.lam0 = pb_alloc(c, rs * n);
+        lv.lamk = pb_alloc(c, rs * n);
+        if (!lv.sig0 || !lv.sigk || !lv.lam0 || !lv.lamk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");
+        if (lv.D0) {
+            lv.Mg0 = pb_alloc(c, rs * (size_t)lv.nslots * T * nr);
+            lv.Mgk = pb_alloc(c, rs * (size_t)lv.nslots * T * nr);
+            if (!lv.Mg0 || !lv.Mgk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");
+        }
+    }
+    c->far_nr = nr;
+    return PB_OK;
+}
+
 int pb_far_setup(pb_ctx* c)
 {
+    c->far_nr = 1;
     int rc = upload_tables(c);
     if (rc) return rc;
     size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
@@ -750,17 +812,22 @@ int pb_far_setup(pb_ctx* c)
     return PB_OK;
 }
 
+// nr right-hand sides: xs and ys hold nr vectors of 2 nt, one after the other
 template <class R>
-static int far_apply(pb_ctx* c, const double* xs, double* ys)
+static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
 {
     const int L = c->L;
     if (L < 1) return PB_OK;
+    int rc0 = pb_far_reserve(c, nr);
+    if (rc0) return rc0;
     double eps = c->prm.eps_out / c->prm.eps_in;
+    const long long vstr = 2LL * c->nt;
+    auto sstr = [](const PbLevel& lv) { return (long long)lv.ncl * pb_nterms(lv.p); };
     pb_tic(c, PB_T_UP);
     {
         PbLevel& lv = c->lev[L];
-        k_p2m<R><<<lv.ncl, FAR_T, 0, c->st>>>(c->nt, lv.p, lv.begin, lv.xc, c->e64p, c->e64n, xs, eps, (R*)lv.sig0,
-                                              (R*)lv.sigk);
+        k_p2m<R><<<dim3(lv.ncl, nr), FAR_T, 0, c->st>>>(c->nt, lv.p, lv.begin, lv.xc, c->e64p, c->e64n, xs, eps,
+                                                        (R*)lv.sig0, (R*)lv.sigk, vstr, sstr(lv));
         PB_LAUNCH(c);
     }
     for (int l = L - 1; l >= 1; --l) {
@@ -768,8 +835,8 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys)
         PbLevel& ch = c->lev[l + 1];
         const size_t msm = 2 * 8 * (size_t)pb_nterms(lv.p) * sizeof(R);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm));
-        k_m2m<R><<<lv.ncl, M2M_T, msm, c->st>>>(lv.p, ch.p, lv.cbeg, lv.xc, ch.xc, (R*)ch.sig0, (R*)ch.sigk,
-                                              (R*)lv.sig0, (R*)lv.sigk);
+        k_m2m<R><<<dim3(lv.ncl, nr), M2M_T, msm, c->st>>>(lv.p, ch.p, lv.cbeg, lv.xc, ch.xc, (R*)ch.sig0,
+                                                        (R*)ch.sigk, (R*)lv.sig0, (R*)lv.sigk, sstr(ch), sstr(lv));
         PB_LAUNCH(c);
     }
     pb_toc(c, PB_T_UP);
@@ -778,14 +845,14 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys)
         PbLevel& lv = c->lev[l];
         int rc = -1;
         if (lv.D0) {
-            if (lv.p == 4) rc = m2l_fast_launch<4, R>(c, lv);
-            else if (lv.p == 6) rc = m2l_fast_launch<6, R>(c, lv);
-            else if (lv.p == 8) rc = m2l_fast_launch<8, R>(c, lv);
+            if (lv.p == 4) rc = m2l_fast_launch<4, R>(c, lv, nr);
+            else if (lv.p == 6) rc = m2l_fast_launch<6, R>(c, lv, nr);
+            else if (lv.p == 8) rc = m2l_fast_launch<8, R>(c, lv, nr);
         }
         if (rc > 0) return rc;
         if (rc == 0) continue;
-        k_m2l<R><<<lv.ncl, FAR_T, 0, c->st>>>(lv.p, c->prm.kappa, lv.int_off, lv.int_idx, lv.xc, (R*)lv.sig0,
-                                              (R*)lv.sigk, (R*)lv.lam0, (R*)lv.lamk);
+        k_m2l<R><<<dim3(lv.ncl, nr), FAR_T, 0, c->st>>>(lv.p, c->prm.kappa, lv.int_off, lv.int_idx, lv.xc,
+                                                        (R*)lv.sig0, (R*)lv.sigk, (R*)lv.lam0, (R*)lv.lamk, sstr(lv));
         PB_LAUNCH(c);
     }
     pb_toc(c, PB_T_M2L);
@@ -793,22 +860,22 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys)
     for (int l = 1; l < L; ++l) {
         PbLevel& lv = c->lev[l];
         PbLevel& ch = c->lev[l + 1];
-        k_l2l<R><<<ch.ncl, FAR_T, 0, c->st>>>(lv.p, ch.p, ch.parent, lv.xc, ch.xc, (R*)lv.lam0, (R*)lv.lamk,
-                                              (R*)ch.lam0, (R*)ch.lamk);
+        k_l2l<R><<<dim3(ch.ncl, nr), FAR_T, 0, c->st>>>(lv.p, ch.p, ch.parent, lv.xc, ch.xc, (R*)lv.lam0,
+                                                        (R*)lv.lamk, (R*)ch.lam0, (R*)ch.lamk, sstr(lv), sstr(ch));
         PB_LAUNCH(c);
     }
     {
         PbLevel& lv = c->lev[L];
-        k_l2p<R><<<lv.ncl, FAR_T, 0, c->st>>>(c->nt, lv.p, eps, lv.begin, lv.xc, c->e64p, c->e64n, (R*)lv.lam0,
-                                              (R*)lv.lamk, ys);
+        k_l2p<R><<<dim3(lv.ncl, nr), FAR_T, 0, c->st>>>(c->nt, lv.p, eps, lv.begin, lv.xc, c->e64p, c->e64n,
+                                                        (R*)lv.lam0, (R*)lv.lamk, ys, sstr(lv), vstr);
         PB_LAUNCH(c);
     }
     pb_toc(c, PB_T_DOWN);
     return PB_OK;
 }
 
-int pb_far_apply(pb_ctx* c, const double* xs, double* ys)
+int pb_far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
 {
-    if (c->prm.precision == PB_MIXED) return far_apply<float>(c, xs, ys);
-    return far_apply<double>(c, xs, ys);
+    if (c->prm.precision == PB_MIXED) return far_apply<float>(c, xs, ys, nr);
+    return far_apply<double>(c, xs, ys, nr);
 }

@@ -460,3 +460,321 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
     if (info) *info = inf;
     return inf.status;
 }
+
+// ---------- several right-hand sides in lockstep ----------
+// nr independent right-preconditioned GMRES(m) iterations advance together: each Arnoldi step
+// applies one batched product (pb_matvec_sorted_multi) to the nr current basis vectors, and the
+// orthogonalisation, Givens rotations and updates run batched over the right-hand sides
+// (grid dimension y or z = right-hand side). Every right-hand side keeps its own Krylov basis,
+// Hessenberg matrix and residual, so each one computes exactly what its own GMRES would; one
+// that has converged stops at its own step count and its later steps are discarded.
+
+// part[r][col][blk] = partial of <V_r[col], w_r> (or <w_r, w_r> when V == nullptr)
+__global__ void k_bdot(long long n, const double* __restrict__ V, long long vstr, const double* __restrict__ w,
+                       double* __restrict__ part, long long pstr)
+{
+    __shared__ double red[KB];
+    const int col = blockIdx.y, r = blockIdx.z;
+    w += r * n;
+    const double* v = V ? V + r * vstr + (size_t)col * n : w;
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) s += v[i] * w[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = KB / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[r * pstr + (size_t)col * gridDim.x + blockIdx.x] = red[0];
+}
+
+// out_r[col] = sum of the partials of column col of right-hand side r
+__global__ void k_bfinish(int nparts, const double* __restrict__ part, long long pstr, double* __restrict__ out,
+                          long long ostr)
+{
+    __shared__ double red[KB];
+    const int col = blockIdx.x, r = blockIdx.y;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += KB) s += part[r * pstr + (size_t)col * nparts + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = KB / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r * ostr + col] = red[0];
+}
+
+// w_r -= V_r[:, 0..ncol) h_r
+__global__ void k_borth(long long n, int ncol, const double* __restrict__ V, long long vstr,
+                        const double* __restrict__ h, long long hstr, double* __restrict__ w)
+{
+    const int r = blockIdx.y;
+    V += r * vstr;
+    h += r * hstr;
+    w += r * n;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        double s = 0.0;
+        for (int c = 0; c < ncol; ++c) s += V[(size_t)c * n + i] * h[c];
+        w[i] -= s;
+    }
+}
+
+// dst_r = src_r / sqrt(*nrm_r)
+__global__ void k_bscale(long long n, const double* __restrict__ src, long long sstr, const double* __restrict__ nrm,
+                         long long nstr, double* __restrict__ dst, long long dstr)
+{
+    const int r = blockIdx.y;
+    src += r * sstr;
+    dst += r * dstr;
+    const double f = 1.0 / sqrt(nrm[r * nstr]);
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) dst[i] = src[i] * f;
+}
+
+// r_q = b_q - r_q for all q
+__global__ void k_bresidual(long long n, const double* __restrict__ b, double* __restrict__ w)
+{
+    b += blockIdx.y * n;
+    w += blockIdx.y * n;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) w[i] = b[i] - w[i];
+}
+
+// hcol_r[i] += y_r[i], i <= j
+__global__ void k_bmerge(int k, double* __restrict__ small, long long sstr, long long yoff, long long hoff)
+{
+    double* s = small + blockIdx.x * sstr;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) s[hoff + i] += s[yoff + i];
+}
+
+static GmState gm_state(double* small, int m)
+{
+    GmState s;
+    s.H = small;
+    s.cs = s.H + (size_t)(m + 1) * m;
+    s.sn = s.cs + (m + 2);
+    s.g = s.sn + (m + 2);
+    s.y = s.g + (m + 2);
+    s.hcol = s.y + (m + 2);
+    s.res = s.hcol + (m + 2);
+    return s;
+}
+
+// right-hand side r = blockIdx.x: the single-vector kernels on its own small state
+__global__ void k_bgm_start(int m, GmState s, long long sstr)
+{
+    const long long o = blockIdx.x * sstr;
+    GmState t = {s.H + o, s.cs + o, s.sn + o, s.g + o, s.y + o, s.hcol + o, s.res + o};
+    for (int i = 0; i <= m; ++i) t.g[i] = 0.0;
+    t.g[0] = sqrt(t.hcol[0]);
+    t.res[0] = t.g[0];
+}
+
+__global__ void k_bgm_givens(int m, int j, GmState s, long long sstr)
+{
+    const long long o = blockIdx.x * sstr;
+    GmState t = {s.H + o, s.cs + o, s.sn + o, s.g + o, s.y + o, s.hcol + o, s.res + o};
+    double* Hj = t.H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) Hj[i] = t.hcol[i];
+    Hj[j + 1] = sqrt(t.hcol[j + 1]);
+    for (int i = 0; i < j; ++i) {
+        double a = Hj[i], b = Hj[i + 1];
+        Hj[i] = t.cs[i] * a + t.sn[i] * b;
+        Hj[i + 1] = -t.sn[i] * a + t.cs[i] * b;
+    }
+    double a = Hj[j], b = Hj[j + 1];
+    double rr = hypot(a, b);
+    double c = rr > 0 ? a / rr : 1.0, sn = rr > 0 ? b / rr : 0.0;
+    t.cs[j] = c;
+    t.sn[j] = sn;
+    Hj[j] = rr;
+    Hj[j + 1] = 0.0;
+    t.g[j + 1] = -sn * t.g[j];
+    t.g[j] = c * t.g[j];
+    t.res[0] = fabs(t.g[j + 1]);
+}
+
+int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double tol, int max_iter, int restart,
+                          pb_solve_info* infos)
+{
+    const long long n = 2LL * c->nt;
+    const int m = restart;
+    const int G = grid_for(n);
+    const long long S = (long long)(m + 1) * m + 6 * (m + 2);  // small state per right-hand side
+    const long long vstr = (long long)(m + 1) * n;               // Krylov basis per right-hand side
+    const long long pstr = (long long)DOT_BLOCKS * (m + 2);      // dot partials per right-hand side
+    if (nr > c->gb_nr || m > c->gb_m) {
+        c->gbV = (double*)pb_alloc(c, sizeof(double) * (size_t)(vstr * nr));
+        c->gbW = (double*)pb_alloc(c, sizeof(double) * (size_t)(n * nr));
+        c->gbZ = (double*)pb_alloc(c, sizeof(double) * (size_t)(n * nr));
+        c->gbpart = (double*)pb_alloc(c, sizeof(double) * (size_t)(pstr * nr));
+        c->gbsmall = (double*)pb_alloc(c, sizeof(double) * (size_t)(S * nr));
+        if (!c->gbV || !c->gbW || !c->gbZ || !c->gbpart || !c->gbsmall) {
+            c->gb_nr = c->gb_m = 0;
+            return pb_fail(c, PB_ERR_NOMEM, "batched gmres: out of memory");
+        }
+        c->gb_nr = nr;
+        c->gb_m = m;
+    }
+    double *V = c->gbV, *W = c->gbW, *Z = c->gbZ, *part = c->gbpart, *small = c->gbsmall;
+    const GmState st = gm_state(small, m);
+    const long long hoff = st.hcol - small, yoff = st.y - small, roff = st.res - small;
+    std::vector<double> hv(nr), bnorm(nr), rel(nr, 1.0);
+    std::vector<int> active(nr, 1), steps(nr, 0), its(nr, 0), mvs(nr, 0), status(nr, PB_OK), conv(nr, 0);
+    std::vector<double> init(nr, 1.0);
+    auto read = [&](long long off) -> int {
+        PB_CUDA(c, cudaMemcpy2DAsync(hv.data(), sizeof(double), small + off, sizeof(double) * S, sizeof(double), nr,
+                                     cudaMemcpyDeviceToHost, c->st));
+        PB_CUDA(c, cudaStreamSynchronize(c->st));
+        return PB_OK;
+    };
+    int rc;
+    // ||b_r||
+    k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, B, part, pstr);
+    PB_LAUNCH(c);
+    k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff, S);
+    PB_LAUNCH(c);
+    if ((rc = read(hoff))) return rc;
+    for (int r = 0; r < nr; ++r) {
+        bnorm[r] = sqrt(hv[r]);
+        if (!(bnorm[r] > 0)) {
+            active[r] = 0;
+            conv[r] = 1;
+            PB_CUDA(c, cudaMemsetAsync(X + r * n, 0, sizeof(double) * n, c->st));
+        }
+    }
+    int it = 0, first = 1;
+    auto any_active = [&]() {
+        for (int r = 0; r < nr; ++r)
+            if (active[r]) return true;
+        return false;
+    };
+    while (any_active() && it < max_iter) {
+        // r = b - A x, V_0 = r / ||r||
+        if ((rc = pb_matvec_sorted_multi(c, X, W, nr))) return rc;
+        for (int r = 0; r < nr; ++r) mvs[r] += active[r];
+        k_bresidual<<<dim3(G, nr), KB, 0, c->st>>>(n, B, W);
+        PB_LAUNCH(c);
+        k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
+        PB_LAUNCH(c);
+        k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff, S);
+        PB_LAUNCH(c);
+        k_bscale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, n, small + hoff, S, V, vstr);
+        PB_LAUNCH(c);
+        k_bgm_start<<<nr, 1, 0, c->st>>>(m, st, S);
+        PB_LAUNCH(c);
+        if ((rc = read(roff))) return rc;
+        if (first == 1) {
+            // a start worse than zero (||b - A x0|| > ||b||) is replaced by zero, once
+            bool redo = false;
+            for (int r = 0; r < nr; ++r)
+                if (active[r] && hv[r] > bnorm[r]) {
+                    PB_CUDA(c, cudaMemsetAsync(X + r * n, 0, sizeof(double) * n, c->st));
+                    redo = true;
+                }
+            first = 2;
+            if (redo) continue;
+        }
+        for (int r = 0; r < nr; ++r) {
+            if (!active[r]) continue;
+            rel[r] = hv[r] / bnorm[r];
+            if (first) init[r] = rel[r];
+            if (!isfinite(rel[r])) {
+                status[r] = PB_ERR_NONFINITE;
+                active[r] = 0;
+            } else if (rel[r] <= tol) {
+                conv[r] = 1;
+                active[r] = 0;
+            }
+            steps[r] = 0;
+        }
+        first = 0;
+        std::vector<int> cyc(nr, 0);  // right-hand sides iterating in this cycle
+        for (int r = 0; r < nr; ++r) cyc[r] = active[r];
+        int j = 0;
+        for (; j < m && it < max_iter && any_active(); ++j) {
+            // z = M^-1 v_j, w = A z (all right-hand sides; finished ones are discarded)
+            if ((rc = pb_precond_apply_multi(c, V + (size_t)j * n, vstr, Z, n, nr))) return rc;
+            if ((rc = pb_matvec_sorted_multi(c, Z, W, nr))) return rc;
+            pb_tic(c, PB_T_ARNOLDI);
+            for (int pass = 0; pass < 2; ++pass) {
+                k_bdot<<<dim3(DOT_BLOCKS, j + 1, nr), KB, 0, c->st>>>(n, V, vstr, W, part, pstr);
+                PB_LAUNCH(c);
+                k_bfinish<<<dim3(j + 1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + (pass ? yoff : hoff), S);
+                PB_LAUNCH(c);
+                k_borth<<<dim3(G, nr), KB, 0, c->st>>>(n, j + 1, V, vstr, small + (pass ? yoff : hoff), S, W);
+                PB_LAUNCH(c);
+            }
+            k_bmerge<<<nr, 64, 0, c->st>>>(j + 1, small, S, yoff, hoff);
+            PB_LAUNCH(c);
+            k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
+            PB_LAUNCH(c);
+            k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff + j + 1, S);
+            PB_LAUNCH(c);
+            k_bscale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, n, small + hoff + j + 1, S, V + (size_t)(j + 1) * n, vstr);
+            PB_LAUNCH(c);
+            k_bgm_givens<<<nr, 1, 0, c->st>>>(m, j, st, S);
+            PB_LAUNCH(c);
+            pb_toc(c, PB_T_ARNOLDI);
+            if ((rc = read(roff))) return rc;
+            ++it;
+            for (int r = 0; r < nr; ++r) {
+                if (!active[r]) continue;
+                ++its[r];
+                ++mvs[r];
+                steps[r] = j + 1;
+                rel[r] = hv[r] / bnorm[r];
+                if (!isfinite(rel[r])) {
+                    status[r] = PB_ERR_NONFINITE;
+                    active[r] = 0;
+                    steps[r] = 0;  // no update from a broken cycle
+                } else if (rel[r] <= tol) {
+                    conv[r] = 1;
+                    active[r] = 0;
+                }
+            }
+        }
+        // x_r += M^-1 V_r y_r over the steps r took in this cycle
+        for (int r = 0; r < nr; ++r) {
+            if (!cyc[r] || steps[r] == 0) continue;
+            GmState t = st;
+            const long long o = r * S;
+            t.H += o;
+            t.cs += o;
+            t.sn += o;
+            t.g += o;
+            t.y += o;
+            t.hcol += o;
+            t.res += o;
+            k_gm_solve<<<1, 1, 0, c->st>>>(m, steps[r], t);
+            PB_LAUNCH(c);
+            k_combine<<<G, KB, 0, c->st>>>(n, steps[r], V + r * vstr, t.y, W + r * n);
+            PB_LAUNCH(c);
+            if ((rc = pb_precond_apply_multi(c, W + r * n, 0, Z + r * n, 0, 1))) return rc;
+            k_axpy1<<<G, KB, 0, c->st>>>(n, Z + r * n, X + r * n);
+            PB_LAUNCH(c);
+        }
+    }
+    // true residuals
+    if ((rc = pb_matvec_sorted_multi(c, X, W, nr))) return rc;
+    k_bresidual<<<dim3(G, nr), KB, 0, c->st>>>(n, B, W);
+    PB_LAUNCH(c);
+    k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
+    PB_LAUNCH(c);
+    k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff, S);
+    PB_LAUNCH(c);
+    if ((rc = read(hoff))) return rc;
+    int derr = 0;
+    PB_CUDA(c, cudaMemcpyAsync(&derr, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    int worst = PB_OK;
+    for (int r = 0; r < nr; ++r) {
+        pb_solve_info inf = {its[r], mvs[r] + 1, bnorm[r] > 0 ? sqrt(hv[r]) / bnorm[r] : 0.0, status[r], init[r]};
+        if (inf.status == PB_OK && !conv[r]) inf.status = PB_ERR_NOT_CONVERGED;
+        if (inf.status == PB_OK && !isfinite(inf.rel_residual)) inf.status = PB_ERR_NONFINITE;
+        if (derr) inf.status = PB_ERR_TIMEOUT;
+        if (infos) infos[r] = inf;
+        if (inf.status != PB_OK && worst == PB_OK) worst = inf.status;
+    }
+    if (derr) pb_fail(c, PB_ERR_TIMEOUT, "a bounded wait in the MtL kernel gave up");
+    return worst;
+}

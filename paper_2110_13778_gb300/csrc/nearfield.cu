@@ -173,12 +173,90 @@ __global__ void __launch_bounds__(256, 3) k_near32(int nt, int nchunks, const in
     }
 }
 
+// ---------- several right-hand sides at once (mixed precision) ----------
+// The pair kernels depend on the geometry only, so one evaluation serves NR densities: the
+// source's geometry records are loaded once per pair and each right-hand side adds four FMAs.
+// dens[r nt + j] = (A_j phi_j, A_j dphi_j) of right-hand side r.
+__global__ void k_near_dens(int nt, const float4* __restrict__ e32p, const double* __restrict__ xs,
+                            float2* __restrict__ dens)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    const double A = (double)e32p[k].w;
+    const double* x = xs + 2LL * nt * blockIdx.y;
+    dens[(size_t)nt * blockIdx.y + k] = make_float2((float)(A * x[k]), (float)(A * x[nt + k]));
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nchunks, const int* __restrict__ chunk_leaf,
+                                                    const int* __restrict__ chunk_first,
+                                                    const int* __restrict__ begin, const int* __restrict__ noff,
+                                                    const int* __restrict__ nidx, const float4* __restrict__ sp,
+                                                    const float4* __restrict__ sn, const float4* __restrict__ sl,
+                                                    const float2* __restrict__ dens, double eps_d, double kappa_d,
+                                                    double* __restrict__ ys)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nchunks) return;
+    const int c = chunk_leaf[w];
+    const int k = chunk_first[w] + lane;
+    const bool act = k < begin[c + 1];
+    const int kk = act ? k : chunk_first[w];
+    const float4 tp = sp[kk], tn = sn[kk], tl = sl[kk];
+    const float eps = (float)eps_d, inv_eps = (float)(1.0 / eps_d), kappa = (float)kappa_d;
+    double acc1[NR], acc2[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc1[r] = acc2[r] = 0.0;
+    for (int t = noff[c]; t < noff[c + 1]; ++t) {
+        const int c2 = nidx[t];
+        const int sb = begin[c2], se = begin[c2 + 1];
+        float s1[NR], s2[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) s1[r] = s2[r] = 0.f;
+#pragma unroll 2
+        for (int j = sb; j < se; ++j) {
+            const float4 a = sp[j], b = sn[j], l = sl[j];
+            float K[4];
+            float dx = (tp.x - a.x) + (tl.x - l.x);
+            float dy = (tp.y - a.y) + (tl.y - l.y);
+            float dz = (tp.z - a.z) + (tl.z - l.z);
+            if (j == k) dx = 1.0f;  // the identical pair is the correction's; keep r finite
+            pb_kernels<float>(dx, dy, dz, tn.x, tn.y, tn.z, b.x, b.y, b.z, eps, inv_eps, kappa, K);
+            const float z = (j == k) ? 0.f : 1.f;
+            K[0] *= z;
+            K[1] *= z;
+            K[2] *= z;
+            K[3] *= z;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float2 d = dens[(size_t)nt * r + j];
+                s1[r] = fmaf(K[0], d.y, fmaf(K[1], d.x, s1[r]));
+                s2[r] = fmaf(K[2], d.y, fmaf(K[3], d.x, s2[r]));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            acc1[r] += (double)s1[r];
+            acc2[r] += (double)s2[r];
+        }
+    }
+    if (act)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            ys[2LL * nt * r + k] = acc1[r];
+            ys[2LL * nt * r + nt + k] = acc2[r];
+        }
+}
+
 // y1 = 1/2 (1 + eps) A phi - A acc1, y2 = 1/2 (1 + 1/eps) A dphi - A acc2 (FP64)
 __global__ void k_near_finish(int nt, const double4_32a* __restrict__ ep, const double* __restrict__ xs,
                               double eps, double* __restrict__ ys)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nt) return;
+    xs += 2LL * nt * blockIdx.y;
+    ys += 2LL * nt * blockIdx.y;
     double A = ep[k].w;
     ys[k] = 0.5 * (1.0 + eps) * A * xs[k] - A * ys[k];
     ys[nt + k] = 0.5 * (1.0 + 1.0 / eps) * A * xs[nt + k] - A * ys[nt + k];
@@ -191,6 +269,8 @@ __global__ void k_corrections(int nt, const int* __restrict__ toff, const int* _
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nt) return;
+    xs += 2LL * nt * blockIdx.y;
+    ys += 2LL * nt * blockIdx.y;
     double y1 = 0.0, y2 = 0.0;
     for (int t = toff[k]; t < toff[k + 1]; ++t) {
         int j = tj[t];
@@ -250,9 +330,58 @@ int pb_near_apply(pb_ctx* c, const double* xs, double* ys)
     return PB_OK;
 }
 
-int pb_corr_apply(pb_ctx* c, const double* xs, double* ys)
+int pb_corr_apply(pb_ctx* c, const double* xs, double* ys, int nr)
 {
-    k_corrections<<<(c->nt + 255) / 256, 256, 0, c->st>>>(c->nt, c->touch_off, c->touch_j, c->corr, xs, ys);
+    k_corrections<<<dim3((c->nt + 255) / 256, nr), 256, 0, c->st>>>(c->nt, c->touch_off, c->touch_j, c->corr, xs,
+                                                                     ys);
+    PB_LAUNCH(c);
+    return PB_OK;
+}
+
+template <int NR>
+static void near_multi_launch(pb_ctx* c, const float2* dens, double* ys, double eps)
+{
+    const PbLevel& lv = c->lev[c->L];
+    k_near32m<NR><<<(c->nchunks * 32 + 255) / 256, 256, 0, c->st>>>(c->nt, c->nchunks, c->chunk_leaf,
+                                                                     c->chunk_first, lv.begin, lv.near_off,
+                                                                     lv.near_idx, c->e32p, c->e32n, c->e32l, dens, eps,
+                                                                     c->prm.kappa, ys);
+}
+
+// nr right-hand sides: xs and ys hold nr vectors of 2 nt; mixed precision evaluates each pair
+// once for up to 16 of them, FP64 applies the single-vector kernel per right-hand side
+int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr)
+{
+    const int nt = c->nt;
+    const double eps = c->prm.eps_out / c->prm.eps_in;
+    if (c->prm.precision != PB_MIXED) {
+        for (int r = 0; r < nr; ++r) {
+            int rc = pb_near_apply(c, xs + 2LL * nt * r, ys + 2LL * nt * r);
+            if (rc) return rc;
+        }
+        return PB_OK;
+    }
+    if (nr > c->dens_nr) {
+        c->near_dens = (float2*)pb_alloc(c, sizeof(float2) * (size_t)nt * nr);
+        if (!c->near_dens) return pb_fail(c, PB_ERR_NOMEM, "near field: out of memory");
+        c->dens_nr = nr;
+    }
+    k_near_dens<<<dim3((nt + 255) / 256, nr), 256, 0, c->st>>>(nt, c->e32p, xs, c->near_dens);
+    PB_LAUNCH(c);
+    for (int r0 = 0; r0 < nr;) {
+        const int left = nr - r0;
+        const int g = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        const float2* d = c->near_dens + (size_t)nt * r0;
+        double* y = ys + 2LL * nt * r0;
+        if (g == 16) near_multi_launch<16>(c, d, y, eps);
+        else if (g == 8) near_multi_launch<8>(c, d, y, eps);
+        else if (g == 4) near_multi_launch<4>(c, d, y, eps);
+        else if (g == 2) near_multi_launch<2>(c, d, y, eps);
+        else near_multi_launch<1>(c, d, y, eps);
+        PB_LAUNCH(c);
+        r0 += g;
+    }
+    k_near_finish<<<dim3((nt + 255) / 256, nr), 256, 0, c->st>>>(nt, c->e64p, xs, eps, ys);
     PB_LAUNCH(c);
     return PB_OK;
 }

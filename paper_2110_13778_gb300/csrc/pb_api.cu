@@ -4,6 +4,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "pb_internal.cuh"
 
 int pb_fail(pb_ctx* c, int code, const char* fmt, ...)
@@ -42,6 +45,10 @@ static void pb_free_build(pb_ctx* c)
     c->built = false;
     c->gm_m = 0;
     c->scratch = nullptr;
+    c->mv_nr = c->gb_nr = c->gb_m = c->dens_nr = 0;
+    c->far_nr = 1;
+    c->mxs = c->mys = c->gbV = c->gbW = c->gbZ = c->gbB = c->gbpart = c->gbsmall = nullptr;
+    c->near_dens = nullptr;
     c->L = 0;
     for (auto& l : c->lev) l = PbLevel();
     c->cent = c->area = c->nrm = nullptr;
@@ -214,6 +221,8 @@ __global__ void k_gather(int n, const int* __restrict__ order, const double* __r
                          double* __restrict__ xs)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
+    x += 2LL * n * blockIdx.y;  // vector blockIdx.y of a batch
+    xs += 2LL * n * blockIdx.y;
     if (k < n) {
         int e = order[k];
         xs[k] = x[e];
@@ -225,6 +234,8 @@ __global__ void k_scatter(int n, const int* __restrict__ order, const double* __
                           double* __restrict__ x)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
+    x += 2LL * n * blockIdx.y;
+    xs += 2LL * n * blockIdx.y;
     if (k < n) {
         int e = order[k];
         x[e] = xs[k];
@@ -258,11 +269,52 @@ int pb_matvec_sorted(pb_ctx* c, const double* xs, double* ys, int which)
         if ((rc = pb_near_apply(c, xs, ys))) return rc;
         pb_toc(c, PB_T_NEAR);
         pb_tic(c, PB_T_CORR);
-        if ((rc = pb_corr_apply(c, xs, ys))) return rc;
+        if ((rc = pb_corr_apply(c, xs, ys, 1))) return rc;
         pb_toc(c, PB_T_CORR);
     }
     if (which != 1)
-        if ((rc = pb_far_apply(c, xs, ys))) return rc;
+        if ((rc = pb_far_apply(c, xs, ys, 1))) return rc;
+    return PB_OK;
+}
+
+// nr products at once: xs and ys hold nr vectors of 2 nt in tree order
+int pb_matvec_sorted_multi(pb_ctx* c, const double* xs, double* ys, int nr)
+{
+    int rc;
+    pb_tic(c, PB_T_NEAR);
+    if ((rc = pb_near_apply_multi(c, xs, ys, nr))) return rc;
+    pb_toc(c, PB_T_NEAR);
+    pb_tic(c, PB_T_CORR);
+    if ((rc = pb_corr_apply(c, xs, ys, nr))) return rc;
+    pb_toc(c, PB_T_CORR);
+    return pb_far_apply(c, xs, ys, nr);
+}
+
+// tree-ordered work vectors for nr right-hand sides (build lifetime, grown on demand)
+static int reserve_multi(pb_ctx* c, int nr)
+{
+    if (nr <= c->mv_nr) return PB_OK;
+    const size_t n = (size_t)nr * 2 * c->nt;
+    c->mxs = (double*)pb_alloc(c, sizeof(double) * n);
+    c->mys = (double*)pb_alloc(c, sizeof(double) * n);
+    if (!c->mxs || !c->mys) return pb_fail(c, PB_ERR_NOMEM, "matvec_multi: out of memory");
+    c->mv_nr = nr;
+    return PB_OK;
+}
+
+extern "C" int pb_matvec_multi(pb_ctx* c, const double* X, double* Y, int nr)
+{
+    PB_ALIVE(c);
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "matvec before build_tree");
+    if (!X || !Y || X == Y || nr < 1 || nr > PB_MAX_RHS) return pb_fail(c, PB_ERR_ARG, "matvec_multi: bad arguments");
+    int rc;
+    if ((rc = reserve_multi(c, nr))) return rc;
+    const int n = c->nt;
+    k_gather<<<dim3((n + 255) / 256, nr), 256, 0, c->st>>>(n, c->order, X, c->mxs);
+    PB_LAUNCH(c);
+    if ((rc = pb_matvec_sorted_multi(c, c->mxs, c->mys, nr))) return rc;
+    k_scatter<<<dim3((n + 255) / 256, nr), 256, 0, c->st>>>(n, c->order, c->mys, Y);
+    PB_LAUNCH(c);
     return PB_OK;
 }
 
@@ -330,13 +382,15 @@ extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, 
 {
     PB_ALIVE(c);
     if (!c->built) return pb_fail(c, PB_ERR_STATE, "solve_states before build_tree");
-    if (!q || !X || nrhs < 1 || !(tol > 0) || max_iter < 1 || restart < 1 || restart > 200)
+    if (!q || !X || nrhs < 1 || !(tol > 0) || max_iter < 1 || restart < 1 || restart > 200 || warm < 0 || warm > 2)
         return pb_fail(c, PB_ERR_ARG, "solve_states: bad arguments");
     for (long long k = 0; k < (long long)nrhs * c->nc; ++k)
         if (!isfinite(q[k])) return pb_fail(c, PB_ERR_MESH, "charge state value %lld not finite", k);
     const size_t n2 = 2 * (size_t)c->nt;
     int worst = PB_OK;
-    for (int s = 0; s < nrhs; ++s) {
+    // batched: state 0 alone from zero, then the others in lockstep from its solution
+    const int nseq = warm == 2 ? 1 : nrhs;
+    for (int s = 0; s < nseq; ++s) {
         if (c->nc > 0)
             PB_CUDA(c, cudaMemcpyAsync(c->q, q + (size_t)s * c->nc, sizeof(double) * c->nc, cudaMemcpyHostToDevice,
                                        c->st));
@@ -353,6 +407,35 @@ extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, 
             double e = 0.0;
             if ((rc = pb_energy_sorted(c, c->xs, &e))) return rc;
             E[s] = e;
+        }
+    }
+    for (int s0 = nseq; s0 < nrhs; s0 += PB_MAX_RHS) {
+        const int nr = std::min(PB_MAX_RHS, nrhs - s0);
+        int rc;
+        if ((rc = reserve_multi(c, nr))) return rc;
+        double *Xs = c->mxs, *Bs = c->mys;
+        for (int r = 0; r < nr; ++r) {
+            if (c->nc > 0)
+                PB_CUDA(c, cudaMemcpyAsync(c->q, q + (size_t)(s0 + r) * c->nc, sizeof(double) * c->nc,
+                                           cudaMemcpyHostToDevice, c->st));
+            if ((rc = pb_rhs_sorted(c, Bs + r * n2))) return rc;
+            PB_CUDA(c, cudaMemcpyAsync(Xs + r * n2, c->xs, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->st));
+        }
+        std::vector<pb_solve_info> loc(nr);
+        rc = pb_gmres_batch_sorted(c, Xs, Bs, nr, tol, max_iter, restart, loc.data());
+        if (rc && rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE && rc != PB_ERR_TIMEOUT) return rc;
+        if (rc && worst == PB_OK) worst = rc;
+        for (int r = 0; r < nr; ++r) {
+            if (infos) infos[s0 + r] = loc[r];
+            if ((rc = pb_scatter(c, Xs + r * n2, X + (size_t)(s0 + r) * n2))) return rc;
+            if (E) {
+                if (c->nc > 0)
+                    PB_CUDA(c, cudaMemcpyAsync(c->q, q + (size_t)(s0 + r) * c->nc, sizeof(double) * c->nc,
+                                               cudaMemcpyHostToDevice, c->st));
+                double e = 0.0;
+                if ((rc = pb_energy_sorted(c, Xs + r * n2, &e))) return rc;
+                E[s0 + r] = e;
+            }
         }
     }
     PB_CUDA(c, cudaStreamSynchronize(c->st));

@@ -93,6 +93,8 @@ struct pb_ctx {
     int* chunk_first = nullptr;
     float4* near_sp = nullptr;  // (x_hi, y_hi, z_hi, A phi)
     float4* near_sn = nullptr;  // (n_x, n_y, n_z, A dphi)
+    float2* near_dens = nullptr; // [dens_nr][nt] (A phi, A dphi) for several right-hand sides
+    int dens_nr = 0;
     // touching pairs (share >= 1 vertex, incl. i == j), CSR by sorted target position
     int* touch_off = nullptr; // [nt + 1]
     int* touch_j = nullptr;   // sorted source position
@@ -101,6 +103,7 @@ struct pb_ctx {
     long long touch_class[4] = {0, 0, 0, 0};  // ordered pairs sharing 0..3 vertices
     long long near_pairs = 0;
     // preconditioner: per leaf a dense (2n x 2n) inverse, unknowns [phi of leaf; dphi of leaf]
+    int far_nr = 1;               // right-hand sides the far-field work arrays hold
     int npcblk = 0;               // preconditioner blocks
     int pc_max = 0;               // largest block order
     double pc_sum_m3 = 0;         // sum of m^3 over blocks
@@ -113,6 +116,11 @@ struct pb_ctx {
     double* ys = nullptr;
     double* ws = nullptr;
     double* scratch = nullptr;    // reduction partials
+    // several right-hand sides: tree-ordered work vectors and the batched GMRES workspace
+    double *mxs = nullptr, *mys = nullptr;
+    int mv_nr = 0;
+    double *gbV = nullptr, *gbW = nullptr, *gbZ = nullptr, *gbB = nullptr, *gbpart = nullptr, *gbsmall = nullptr;
+    int gb_nr = 0, gb_m = 0;
     double* hscal = nullptr;      // pinned host scalars
     // GMRES workspace (Krylov basis, work vectors, reduction partials, small dense state)
     int gm_m = 0;
@@ -163,11 +171,17 @@ int pb_geometry_and_tree(pb_ctx* c);          // tree.cu
 int pb_touching_and_singular(pb_ctx* c);      // singular.cu
 int pb_near_setup(pb_ctx* c);                                      // nearfield.cu
 int pb_near_apply(pb_ctx* c, const double* xs, double* ys);        // nearfield.cu (writes ys)
-int pb_corr_apply(pb_ctx* c, const double* xs, double* ys);        // nearfield.cu (adds)
+int pb_corr_apply(pb_ctx* c, const double* xs, double* ys, int nr);  // nearfield.cu (adds)
+int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr);  // nearfield.cu (writes)
 int pb_far_setup(pb_ctx* c);                                       // farfield.cu
-int pb_far_apply(pb_ctx* c, const double* xs, double* ys);         // farfield.cu (adds)
+int pb_far_apply(pb_ctx* c, const double* xs, double* ys, int nr);  // farfield.cu (adds; nr vectors)
+int pb_far_reserve(pb_ctx* c, int nr);
 int pb_precond_build(pb_ctx* c);                                   // precond.cu
 int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z);
+int pb_precond_apply_multi(pb_ctx* c, const double* r, long long rstr, double* z, long long zstr, int nr);
+int pb_matvec_sorted_multi(pb_ctx* c, const double* xs, double* ys, int nr);  // pb_api.cu
+int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double tol, int max_iter, int restart,
+                          pb_solve_info* infos);  // krylov.cu
 int pb_rhs_sorted(pb_ctx* c, double* bs);                          // krylov.cu
 int pb_energy_sorted(pb_ctx* c, const double* xs, double* E);      // krylov.cu
 int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max_iter,

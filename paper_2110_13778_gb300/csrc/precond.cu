@@ -301,8 +301,11 @@ __global__ void __launch_bounds__(256, 1) k_blk_gj_reg(const int* __restrict__ b
 // z = M^-1 r per leaf: one warp per row, lanes stride the columns
 template <class R>
 __global__ void k_blk_apply(int nt, const int* __restrict__ begin, const long long* __restrict__ moff,
-                            const R* __restrict__ minv, const double* __restrict__ r, double* __restrict__ z)
+                            const R* __restrict__ minv, const double* __restrict__ r, double* __restrict__ z,
+                            long long rstr, long long zstr)
 {
+    r += blockIdx.y * rstr;  // right-hand side blockIdx.y
+    z += blockIdx.y * zstr;
     const int c = blockIdx.x;
     const int b = begin[c], n = begin[c + 1] - begin[c], m = 2 * n;
     const R* Mc = minv + moff[c];
@@ -342,10 +345,12 @@ __global__ void k_diag_build(int nt, const double4_32a* __restrict__ ep, const i
 }
 
 __global__ void k_diag_apply(int nt, const double* __restrict__ dinv, const double* __restrict__ r,
-                             double* __restrict__ z)
+                             double* __restrict__ z, long long rstr, long long zstr)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nt) return;
+    r += blockIdx.y * rstr;
+    z += blockIdx.y * zstr;
     double a = r[k], b = r[nt + k];
     z[k] = dinv[4 * k] * a + dinv[4 * k + 1] * b;
     z[nt + k] = dinv[4 * k + 2] * a + dinv[4 * k + 3] * b;
@@ -444,20 +449,24 @@ int pb_precond_build(pb_ctx* c)
     return rc;  // blk_build synchronises before the host vectors go out of scope
 }
 
-int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z)
+// z_q = M^-1 r_q for nr vectors r_q = r + q rstr, z_q = z + q zstr
+int pb_precond_apply_multi(pb_ctx* c, const double* r, long long rstr, double* z, long long zstr, int nr)
 {
     const int nt = c->nt;
     pb_tic(c, PB_T_PRECOND);
     if (c->prm.precond == PB_PRECOND_BLOCK) {
         if (c->prm.precision == PB_MIXED)
-            k_blk_apply<float><<<c->npcblk, 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off, (const float*)c->minv, r, z);
+            k_blk_apply<float><<<dim3(c->npcblk, nr), 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off,
+                                                                       (const float*)c->minv, r, z, rstr, zstr);
         else
-            k_blk_apply<double><<<c->npcblk, 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off, (const double*)c->minv, r,
-                                                              z);
+            k_blk_apply<double><<<dim3(c->npcblk, nr), 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off,
+                                                                        (const double*)c->minv, r, z, rstr, zstr);
     } else if (c->prm.precond == PB_PRECOND_DIAG) {
-        k_diag_apply<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->dinv, r, z);
+        k_diag_apply<<<dim3((nt + 255) / 256, nr), 256, 0, c->st>>>(nt, c->dinv, r, z, rstr, zstr);
     } else {
-        PB_CUDA(c, cudaMemcpyAsync(z, r, sizeof(double) * 2 * nt, cudaMemcpyDeviceToDevice, c->st));
+        for (int q = 0; q < nr; ++q)
+            PB_CUDA(c, cudaMemcpyAsync(z + q * zstr, r + q * rstr, sizeof(double) * 2 * nt, cudaMemcpyDeviceToDevice,
+                                       c->st));
         pb_toc(c, PB_T_PRECOND);
         return PB_OK;
     }
@@ -465,3 +474,5 @@ int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z)
     pb_toc(c, PB_T_PRECOND);
     return PB_OK;
 }
+
+int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z) { return pb_precond_apply_multi(c, r, 0, z, 0, 1); }

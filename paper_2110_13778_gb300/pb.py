@@ -28,8 +28,9 @@ EXPORTS = [
     "pb_get_launch_count", "pb_solvation_energy_noalloc", "pb_solve_states",
     "pb_mlp_create", "pb_mlp_destroy", "pb_mlp_last_error", "pb_mlp_param_count", "pb_mlp_get_params",
     "pb_mlp_set_params", "pb_mlp_forward", "pb_mlp_gradient", "pb_mlp_train_step", "pb_features",
-    "pb_learned_guess", "pb_measure_alu_peaks", "pb_autotune",
+    "pb_learned_guess", "pb_measure_alu_peaks", "pb_autotune", "pb_matvec_multi",
 ]
+PB_MAX_RHS = 64
 NFEAT = 18
 NSTAT = 20
 
@@ -117,6 +118,7 @@ def lib():
         L.pb_features.argtypes = [vp, vp, vp, vp, dp]
         L.pb_learned_guess.argtypes = [vp, vp, vp]
         L.pb_measure_alu_peaks.argtypes = [vp, dp, dp]
+        L.pb_matvec_multi.argtypes = [vp, vp, vp, c_int]
         L.pb_autotune.argtypes = [vp, c_double, c_int, ctypes.POINTER(pb_tune_result)]
         _lib = L
     return _lib
@@ -178,6 +180,11 @@ def pb_matvec(ctx, x, y):
     _check(ctx, lib().pb_matvec(ctx, _ptr(x), _ptr(y)))
 
 
+def pb_matvec_multi(ctx, X, Y):
+    """Y[q] = A X[q] for the rows of X (nr, 2N) float64 CUDA; Y the same shape."""
+    _check(ctx, lib().pb_matvec_multi(ctx, _ptr(X), _ptr(Y), int(X.shape[0])))
+
+
 def pb_matvec_part(ctx, x, y, which):
     _check(ctx, lib().pb_matvec_part(ctx, _ptr(x), _ptr(y), which))
 
@@ -200,14 +207,15 @@ def pb_gmres_solve(ctx, x, tol=1e-6, max_iter=200, restart=50, use_x0=False, rai
 
 def pb_solve_states(ctx, q_states, X, tol=1e-6, max_iter=200, restart=50, warm=True, raise_on_fail=True):
     """Solve nrhs charge states on one built mesh. q_states: (nrhs, nc) host array;
-    X: (nrhs, 2N) float64 CUDA tensor (overwritten). Returns (energies, infos)."""
+    X: (nrhs, 2N) float64 CUDA tensor (overwritten). warm: False / True (sequential, each from
+    the previous solution) or 2 (batched lockstep after state 0). Returns (energies, infos)."""
     Q = np.ascontiguousarray(q_states, dtype=np.float64)
     nrhs = Q.shape[0]
     E = np.zeros(nrhs)
     infos = (pb_solve_info * nrhs)()
     dp = ctypes.POINTER(ctypes.c_double)
     rc = lib().pb_solve_states(ctx, Q.ctypes.data_as(dp), nrhs, _ptr(X), E.ctypes.data_as(dp), tol, max_iter,
-                               restart, int(bool(warm)), infos)
+                               restart, 2 if (warm == 2 and not isinstance(warm, bool)) else int(bool(warm)), infos)
     if rc != PB_OK and (raise_on_fail or rc not in (PB_ERR_NOT_CONVERGED, PB_ERR_NONFINITE)):
         _check(ctx, rc)
     return E, list(infos)

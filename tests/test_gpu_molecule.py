@@ -110,3 +110,56 @@ def test_autotune_picks_an_accurate_configuration(mol, prec):
         assert abs(E - Eo) < 1e-3 * abs(Eo), (E, Eo)
     finally:
         pb.pb_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,nr", [(pb.PB_FP64, 3), (pb.PB_MIXED, 5), (pb.PB_MIXED, 19)])
+def test_matvec_multi_matches_single_products(mol, prec, nr):
+    # 19 right-hand sides take the 16-, 2- and 1-wide near-field kernels
+    m, ph, A = mol
+    ctx = _ctx(m, leaf_size=32, eta0=0.7, p=6, precision=prec)
+    try:
+        rng = np.random.default_rng(nr)
+        X = torch.tensor(rng.standard_normal((nr, 2 * m.nt)), device="cuda", dtype=torch.float64)
+        Y = torch.empty_like(X)
+        pb.pb_matvec_multi(ctx, X, Y)
+        y1 = torch.empty(2 * m.nt, device="cuda", dtype=torch.float64)
+        for q in range(nr):
+            pb.pb_matvec(ctx, X[q].contiguous(), y1)
+            d = float((Y[q] - y1).norm() / y1.norm())
+            # FP64 runs the same arithmetic per vector; mixed regroups the FP32 near-field sums
+            assert d < (1e-14 if prec == pb.PB_FP64 else 1e-6), (q, d)
+    finally:
+        pb.pb_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [pb.PB_FP64, pb.PB_MIXED])
+def test_batched_charge_states_match_sequential(mol, prec):
+    m, ph, A = mol
+    rng = np.random.default_rng(11)
+    states = []
+    for s in range(6):
+        q = m.q.copy()
+        flip = rng.random(q.size) < 0.05
+        q[flip] = -q[flip]
+        states.append(q)
+    Q = np.array(states)
+    res = {}
+    for mode in (1, 2):
+        ctx = _ctx(m, leaf_size=32, eta0=0.7, p=8, precision=prec)
+        try:
+            X = torch.zeros((len(states), 2 * m.nt), device="cuda", dtype=torch.float64)
+            E, infos = pb.pb_solve_states(ctx, Q, X, tol=1e-6, max_iter=300, restart=50, warm=mode)
+            assert all(i.status == pb.PB_OK for i in infos)
+            assert all(i.rel_residual <= 1.5e-6 for i in infos)
+            res[mode] = (E, X.cpu().numpy(), infos)
+        finally:
+            pb.pb_destroy(ctx)
+    Es, Xs, _ = res[1]
+    Eb, Xb, ib = res[2]
+    for s in range(len(states)):
+        assert abs(Eb[s] - Es[s]) < 1e-5 * abs(Es[s]), (s, Eb[s], Es[s])
+        assert np.linalg.norm(Xb[s] - Xs[s]) / np.linalg.norm(Xs[s]) < 1e-4
+    # the batched states start from state 0's solution where that beats a zero start
+    assert all(i.initial_residual <= 1.0 for i in ib[1:])
+    Eo = dense.energy(dense_mesh(m, states[3]), ph, np.linalg.solve(A, dense.rhs(dense_mesh(m, states[3]), ph)))
+    assert abs(Eb[3] - Eo) < 1e-3 * abs(Eo)
