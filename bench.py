@@ -144,7 +144,8 @@ def dist_max(x, world):
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -459,6 +460,13 @@ def run_ours(a):
     return 0
 
 
+def batch_sizes(rank, molecules):
+    """Each rank's own molecules (weak scaling: the ranks share no data): atom counts
+    log-uniform in [200, 2000] from a rank-seeded generator, which also draws the states."""
+    rng = np.random.default_rng(4000 + rank)
+    return rng, np.exp(rng.uniform(np.log(200), np.log(2000), size=molecules)).astype(int)
+
+
 def run_batch(a):
     """Several protein-like molecules of different sizes, each with `states` charge states
     (5 % of the charges flipped per state): one build per molecule, all states solved on it
@@ -470,8 +478,7 @@ def run_batch(a):
     from paper_2110_13778_gb300 import build, molecules, pb
 
     build.build()
-    rng = np.random.default_rng(4000 + rank)
-    sizes = np.exp(rng.uniform(np.log(200), np.log(2000), size=a.molecules)).astype(int)
+    rng, sizes = batch_sizes(rank, a.molecules)
     mols = [molecules.molecule(int(n), 5000 + 97 * rank + k, a.grid)[0] for k, n in enumerate(sizes)]
     states = []
     for m in mols:
