@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "ff.cuh"
 #include "pb_internal.cuh"
 
 #include "m2l_unrolled.cuh"
@@ -371,6 +372,96 @@ __global__ void __launch_bounds__(256) k_m2l_setup(int nslots, int p, double kap
 //
 // Scaled moments gathered into the chunk layout: M[((s / 32) * T + b) * 32 + s % 32] =
 // (-1)^|b| sigma^b(src(s)) / b!, zero for padding slots.
+// The same recurrence in float-float on the FP32 pipe, for the FP32 tables of mixed
+// precision: ~1e-13 relative before the final rounding to FP32, at a fraction of the FP64
+// pipe's time. The starting values come from FP64 once per slot.
+__device__ __forceinline__ ff ld_ffs(const float2* p)
+{
+    const float2 v = *p;
+    return {v.x, v.y};
+}
+
+__global__ void __launch_bounds__(256) k_m2l_setup_ff(int nslots, int p, double kappa, const int* __restrict__ stgt,
+                                                      const int* __restrict__ ssrc, const double* __restrict__ xc,
+                                                      float* __restrict__ D0, float* __restrict__ Dk)
+{
+    extern __shared__ float2 m2lf[];
+    const int T = pb_nterms(p);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * 8 + warp;
+    if (s >= nslots) return;
+    float2* F0 = m2lf + (size_t)warp * 3 * T;
+    float2* Fk = F0 + T;
+    float2* Pk = Fk + T;
+    const int c = stgt[s], c2 = ssrc[s];
+    const size_t base = ((size_t)(s >> 5) * T) * 32 + (s & 31);
+    if (c2 < 0) {
+        for (int k = lane; k < T; k += 32) {
+            D0[base + (size_t)k * 32] = 0.f;
+            Dk[base + (size_t)k * 32] = 0.f;
+        }
+        return;
+    }
+    const ff d[3] = {ff_from(xc[3 * c] - xc[3 * c2]), ff_from(xc[3 * c + 1] - xc[3 * c2 + 1]),
+                     ff_from(xc[3 * c + 2] - xc[3 * c2 + 2])};
+    const ff d2 = ff_add(ff_add(ff_sqr(d[0]), ff_sqr(d[1])), ff_sqr(d[2]));
+    const ff kap = ff_from(kappa);
+    if (lane == 0) {
+        const double dd[3] = {xc[3 * c] - xc[3 * c2], xc[3 * c + 1] - xc[3 * c2 + 1], xc[3 * c + 2] - xc[3 * c2 + 2]};
+        const double r = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]), ex = exp(-kappa * r);
+        const double i4pi = 0.07957747154594767;
+        const ff a = ff_from(i4pi / r), b = ff_from(i4pi * ex / r), e = ff_from(i4pi * ex);
+        F0[0] = make_float2(a.h, a.l);
+        Fk[0] = make_float2(b.h, b.l);
+        Pk[0] = make_float2(e.h, e.l);
+    }
+    // 1 / d2 to float-float accuracy: FP32 estimate and one Newton step
+    const float y0 = 1.0f / d2.h;
+    const ff id2 = ff_add_f(ff_mul_f(ff_neg(ff_add_f(ff_mul_f(d2, y0), -1.0f)), y0), y0);
+    __syncwarp();
+    for (int n = 1; n <= p; ++n) {
+        const float fn = (float)n, in = 1.0f / fn;
+        const ff inv_n = ff_add_f(ff_mul_f(ff_neg(ff{fn * in - 1.0f, fmaf(fn, in, -(fn * in))}), in), in);
+        const ff scale = ff_mul(id2, inv_n);
+        for (int k = pb_nterms(n - 1) + lane; k < pb_nterms(n); k += 32) {
+            int kk[3];
+            mi_unpack(c_mi[k], kk[0], kk[1], kk[2]);
+            ff a0 = {0.f, 0.f}, a1 = a0, ak0 = a0, ak1 = a0, ap0 = a0, ap1 = a0;
+            for (int i = 0; i < 3; ++i) {
+                if (kk[i] >= 1) {
+                    const int q = pb_midx(kk[0] - (i == 0), kk[1] - (i == 1), kk[2] - (i == 2));
+                    a0 = ff_add(a0, ff_mul(d[i], ld_ffs(F0 + q)));
+                    ak0 = ff_add(ak0, ff_mul(d[i], ld_ffs(Fk + q)));
+                    ap0 = ff_add(ap0, ff_mul(d[i], ld_ffs(Pk + q)));
+                }
+                if (kk[i] >= 2) {
+                    const int q = pb_midx(kk[0] - 2 * (i == 0), kk[1] - 2 * (i == 1), kk[2] - 2 * (i == 2));
+                    a1 = ff_add(a1, ld_ffs(F0 + q));
+                    ak1 = ff_add(ak1, ld_ffs(Fk + q));
+                    ap1 = ff_add(ap1, ld_ffs(Pk + q));
+                }
+            }
+            const float c1 = -(2.0f * fn - 1.0f), c2 = -(fn - 1.0f);
+            const ff f0 = ff_mul(ff_add(ff_mul_f(a0, c1), ff_mul_f(a1, c2)), scale);
+            const ff fk = ff_mul(ff_sub(ff_add(ff_mul_f(ak0, c1), ff_mul_f(ak1, c2)), ff_mul(kap, ff_add(ap0, ap1))),
+                                 scale);
+            const ff pk = ff_neg(ff_mul(ff_mul(kap, ff_add(ak0, ak1)), inv_n));
+            F0[k] = make_float2(f0.h, f0.l);
+            Fk[k] = make_float2(fk.h, fk.l);
+            Pk[k] = make_float2(pk.h, pk.l);
+        }
+        __syncwarp();
+    }
+    for (int k = lane; k < T; k += 32) {
+        int k1, k2, k3;
+        mi_unpack(c_mi[k], k1, k2, k3);
+        const float f = (float)(c_fact[k1] * c_fact[k2] * c_fact[k3]);  // at most 12!, exact in FP32 up to 8!
+        const ff a = ff_mul_f(ld_ffs(F0 + k), f), b = ff_mul_f(ld_ffs(Fk + k), f);
+        D0[base + (size_t)k * 32] = a.h + a.l;
+        Dk[base + (size_t)k * 32] = b.h + b.l;
+    }
+}
+
 template <class R>
 __global__ void k_m2l_gather(int T, const int* __restrict__ ssrc, const R* __restrict__ s0, const R* __restrict__ sk,
                              R* __restrict__ M0, R* __restrict__ Mk, long long sstr, long long mstr)
@@ -727,9 +818,9 @@ static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
     const unsigned nb = (unsigned)((lv.nslots + 7) / 8);
     if (nb == 0) {
     } else if (c->prm.precision == PB_MIXED) {
-        PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_setup<float><<<nb, 256, smem, c->st>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
-                                                     (float*)lv.D0, (float*)lv.Dk);
+        PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_m2l_setup_ff<<<nb, 256, smem, c->st>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
+                                                 (float*)lv.D0, (float*)lv.Dk);
     } else {
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_m2l_setup<double><<<nb, 256, smem, c->st>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
