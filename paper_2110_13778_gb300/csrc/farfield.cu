@@ -914,6 +914,11 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
     double eps = c->prm.eps_out / c->prm.eps_in;
     const long long vstr = 2LL * c->nt;
     auto sstr = [](const PbLevel& lv) { return (long long)lv.ncl * pb_nterms(lv.p); };
+    // coarsest level with an interaction list: moments above it and local expansions there
+    // would only ever be zero or unused
+    int lmin = 1;
+    while (lmin <= L && c->lev[lmin].ninter == 0) ++lmin;
+    if (lmin > L) return PB_OK;  // every pair is near
     pb_tic(c, PB_T_UP);
     {
         PbLevel& lv = c->lev[L];
@@ -921,7 +926,7 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
                                                         (R*)lv.sig0, (R*)lv.sigk, vstr, sstr(lv));
         PB_LAUNCH(c);
     }
-    for (int l = L - 1; l >= 1; --l) {
+    for (int l = L - 1; l >= lmin; --l) {
         PbLevel& lv = c->lev[l];
         PbLevel& ch = c->lev[l + 1];
         const size_t msm = 2 * 8 * (size_t)pb_nterms(lv.p) * sizeof(R);
@@ -932,7 +937,7 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
     }
     pb_toc(c, PB_T_UP);
     pb_tic(c, PB_T_M2L);
-    for (int l = 1; l <= L; ++l) {
+    for (int l = lmin; l <= L; ++l) {
         PbLevel& lv = c->lev[l];
         int rc = -1;
         if (lv.D0) {
@@ -948,7 +953,7 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
     }
     pb_toc(c, PB_T_M2L);
     pb_tic(c, PB_T_DOWN);
-    for (int l = 1; l < L; ++l) {
+    for (int l = lmin; l < L; ++l) {
         PbLevel& lv = c->lev[l];
         PbLevel& ch = c->lev[l + 1];
         k_l2l<R><<<dim3(ch.ncl, nr), FAR_T, 0, c->st>>>(lv.p, ch.p, ch.parent, lv.xc, ch.xc, (R*)lv.lam0,

@@ -657,7 +657,7 @@ int pb_touching_and_singular(pb_ctx* c)
     size_t tmp = 0;
     cub::DeviceScan::ExclusiveSum(nullptr, tmp, vcnt, voff, nv + 1, c->st);
     void* t = nullptr;
-    PB_CUDA(c, cudaMallocAsync(&t, tmp, c->st));
+    PB_CUDA(c, cudaMallocFromPoolAsync(&t, tmp, c->pool, c->st));
     cub::DeviceScan::ExclusiveSum(t, tmp, vcnt, voff, nv + 1, c->st);
     PB_LAUNCH(c);
     k_vfill<<<nblk(nt, B), B, 0, c->st>>>(nt, c->stris, voff, vfill, vlist);
@@ -668,7 +668,7 @@ int pb_touching_and_singular(pb_ctx* c)
     cub::DeviceScan::ExclusiveSum(nullptr, tmp2, tcnt, c->touch_off, nt + 1, c->st);
     if (tmp2 > tmp) {
         PB_CUDA(c, cudaFreeAsync(t, c->st));
-        PB_CUDA(c, cudaMallocAsync(&t, tmp2, c->st));
+        PB_CUDA(c, cudaMallocFromPoolAsync(&t, tmp2, c->pool, c->st));
         tmp = tmp2;
     }
     cub::DeviceScan::ExclusiveSum(t, tmp, tcnt, c->touch_off, nt + 1, c->st);
@@ -728,7 +728,7 @@ int pb_touching_and_singular(pb_ctx* c)
         size_t ctmp = 0;
         cub::DeviceScan::ExclusiveSum(nullptr, ctmp, ccnt, coff, nt + 1, c->st);
         void* cbuf = nullptr;
-        PB_CUDA(c, cudaMallocAsync(&cbuf, ctmp, c->st));
+        PB_CUDA(c, cudaMallocFromPoolAsync(&cbuf, ctmp, c->pool, c->st));
         cub::DeviceScan::ExclusiveSum(cbuf, ctmp, ccnt, coff, nt + 1, c->st);
         PB_LAUNCH(c);
         PB_CUDA(c, cudaFreeAsync(cbuf, c->st));

@@ -278,7 +278,7 @@ static int scan_counts(pb_ctx* c, const int* cnt, int* off, int n, long long* to
     size_t tmp = 0;
     cub::DeviceScan::ExclusiveSum(nullptr, tmp, cnt, off, n + 1, c->st);
     void* t = nullptr;
-    PB_CUDA(c, cudaMallocAsync(&t, tmp, c->st));
+    PB_CUDA(c, cudaMallocFromPoolAsync(&t, tmp, c->pool, c->st));
     cub::DeviceScan::ExclusiveSum(t, tmp, cnt, off, n + 1, c->st);
     PB_LAUNCH(c);
     PB_CUDA(c, cudaFreeAsync(t, c->st));
@@ -341,7 +341,7 @@ int pb_geometry_and_tree(pb_ctx* c)
         size_t tmp = 0;
         cub::DeviceRadixSort::SortPairs(nullptr, tmp, keys, skeys, idx, c->order, nt, 0, 3 * PB_MAXL, c->st);
         void* t = nullptr;
-        PB_CUDA(c, cudaMallocAsync(&t, tmp, c->st));
+        PB_CUDA(c, cudaMallocFromPoolAsync(&t, tmp, c->pool, c->st));
         cub::DeviceRadixSort::SortPairs(t, tmp, keys, skeys, idx, c->order, nt, 0, 3 * PB_MAXL, c->st);
         PB_LAUNCH(c);
         PB_CUDA(c, cudaFreeAsync(t, c->st));
