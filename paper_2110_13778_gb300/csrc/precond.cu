@@ -173,127 +173,119 @@ __global__ void __launch_bounds__(GJ_T) k_blk_gj(const int* __restrict__ begin, 
         for (int t = threadIdx.x; t < m * m; t += GJ_T) g[t] = a[t];
 }
 
-// Register-tiled Gauss-Jordan inversion (FP32, m <= 16 MT) by pivot exchanges without row
-// interchanges: a 16 x 16 thread grid, thread (ty, tx) holding rows ty + 16 a and columns
-// tx + 16 b (a, b < MT) of the block in registers. Step k exchanges the roles of unknown k and
-// equation p (the unused row with the largest |entry| in column k): with a = T[p][k],
-//   T[p][k] <- 1/a,  T[p][j] <- -T[p][j]/a,  T[i][k] <- T[i][k]/a,
-//   T[i][j] <- T[i][j] - T[i][k] T[p][j]/a   (i != p, j != k).
-// After all m exchanges, T[p_k][k'] = (A^-1)[k][p_k'], which the final store applies. The
-// column loop is unrolled by blocks of 16 so that the column a step works on is a
-// compile-time register index; per step, the owners of column k publish it with their
-// partial maxima, the owners of row p publish that row, and every thread updates its
-// MT x MT tile -- two barriers per step (buffers alternate by step parity).
-template <int MT>
-__global__ void __launch_bounds__(256, 1) k_blk_gj_reg(const int* __restrict__ begin, const long long* __restrict__ moff,
-                                                      float* __restrict__ minv, int* __restrict__ singular)
+// Register-resident Gauss-Jordan inversion by pivot exchanges (FP32, m <= 32 MA and m <= 8 MB),
+// laid out so that a column belongs to one warp: lane l of warp w holds rows l + 32 a (a < MA)
+// of columns w + 8 b (b < MB). Step k: the warp owning column k finds the pivot row p (the
+// unused row of largest |entry|) with warp shuffles and publishes the column, p and the pivot
+// to shared memory -- the step's only barrier follows -- and every warp takes row p of its own
+// columns from the lane holding it by a shuffle, then applies the exchange
+//   T[p][k] <- 1/a, T[p][j] <- -T[p][j]/a, T[i][k] <- T[i][k]/a, T[i][j] -= T[i][k] T[p][j]/a.
+// After m exchanges T[p_k][k'] = (A^-1)[k][p_k'], which the final store applies.
+template <int MA, int MB>
+__global__ void __launch_bounds__(256, 1) k_blk_gj_w(const int* __restrict__ begin, const long long* __restrict__ moff,
+                                                    float* __restrict__ minv, int* __restrict__ singular)
 {
-    constexpr int MC = 16 * MT;
-    __shared__ float colb[2][MC], rowb[2][MC], redv[2][16];
-    __shared__ int redi[2][16], perm[MC], inv[MC];
+    __shared__ float colb[2][32 * MA], pivv[2];
+    __shared__ int pivs[2], perm[32 * MA], inv[32 * MA];
     const int c = blockIdx.x;
     const int m = 2 * (begin[c + 1] - begin[c]);
     float* g = minv + moff[c];
-    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-    float v[MT][MT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float v[MA][MB];
 #pragma unroll
-    for (int a = 0; a < MT; ++a)
+    for (int a = 0; a < MA; ++a)
 #pragma unroll
-        for (int b = 0; b < MT; ++b) {
-            const int i = ty + 16 * a, j = tx + 16 * b;
+        for (int b = 0; b < MB; ++b) {
+            const int i = lane + 32 * a, j = warp + 8 * b;
             v[a][b] = (i < m && j < m) ? g[(size_t)i * m + j] : 0.f;
         }
-    unsigned used = 0;  // bit a: row ty + 16 a has been a pivot row
+    unsigned used = 0;  // bit a: row lane + 32 a has been a pivot row
 #pragma unroll
-    for (int kb = 0; kb < MT; ++kb) {
-        for (int kk = 0; kk < 16; ++kk) {
-            const int k = 16 * kb + kk;
+    for (int kb = 0; kb < MB; ++kb) {
+        for (int kw = 0; kw < 8; ++kw) {
+            const int k = 8 * kb + kw;
             if (k >= m) break;
             const int s = k & 1;
-            // 1. owners of column k publish it and their largest |entry| among unused rows
-            if (tx == kk) {
+            if (warp == kw) {
                 float best = -1.f;
-                int bi = m;
+                int bi = 0x7fffffff;
 #pragma unroll
-                for (int a = 0; a < MT; ++a) {
-                    const int i = ty + 16 * a;
+                for (int a = 0; a < MA; ++a) {
+                    const int i = lane + 32 * a;
                     const float x = v[a][kb];
                     if (i < m) {
                         colb[s][i] = x;
-                        if (!((used >> a) & 1u) && fabsf(x) > best) {
-                            best = fabsf(x);
+                        float ax = fabsf(x);
+                        if (!(ax >= 0.f)) ax = 0.f;  // a NaN still yields a valid (singular) pivot row
+                        if (!((used >> a) & 1u) && ax > best) {
+                            best = ax;
                             bi = i;
                         }
                     }
                 }
-                redv[s][ty] = best;
-                redi[s][ty] = bi;
-            }
-            __syncthreads();
-            float best = redv[s][0];
-            int p = redi[s][0];
-            for (int q = 1; q < 16; ++q) {
-                const float o = redv[s][q];
-                const int oi = redi[s][q];
-                if (o > best || (o == best && oi < p)) {
-                    best = o;
-                    p = oi;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ob > best || (ob == best && oi < bi)) {
+                        best = ob;
+                        bi = oi;
+                    }
+                }
+                if (lane == (bi & 31)) {
+                    // the lane holding the pivot row publishes it and its entry in column k
+                    float pv = 0.f;
+#pragma unroll
+                    for (int a = 0; a < MA; ++a)
+                        if (lane + 32 * a == bi) pv = v[a][kb];
+                    pivs[s] = bi;
+                    pivv[s] = pv;
                 }
             }
-            // 2. owners of row p publish it
-            if (ty == (p & 15)) {
-#pragma unroll
-                for (int a = 0; a < MT; ++a)
-                    if (ty + 16 * a == p) {
-                        used |= 1u << a;
-#pragma unroll
-                        for (int b = 0; b < MT; ++b) {
-                            const int j = tx + 16 * b;
-                            if (j < m) rowb[s][j] = v[a][b];
-                        }
-                    }
-            }
+            __syncthreads();
+            const int p = pivs[s];
+            float piv = pivv[s];
             if (threadIdx.x == 0) {
                 perm[k] = p;
                 inv[p] = k;
+                if (!(fabsf(piv) > 0.f)) atomicExch(singular, 1);
             }
-            __syncthreads();
-            float piv = rowb[s][k];
-            if (!(fabsf(piv) > 0.f)) {
-                if (threadIdx.x == 0) atomicExch(singular, 1);
-                piv = 1.f;
-            }
+            if (!(fabsf(piv) > 0.f)) piv = 1.f;
             const float ia = 1.f / piv;
-            // 3. the exchange
-            float rk[MT];
+            const int pa = p >> 5, pl = p & 31;
+            if (lane == pl) used |= 1u << pa;
+            // row p of this warp's columns, from the lane that holds it
+            float rk[MB];
 #pragma unroll
-            for (int b = 0; b < MT; ++b) {
-                const int j = tx + 16 * b;
-                rk[b] = j < m ? rowb[s][j] * ia : 0.f;
+            for (int b = 0; b < MB; ++b) {
+                float x = v[0][b];
+#pragma unroll
+                for (int a = 1; a < MA; ++a)
+                    if (a == pa) x = v[a][b];
+                rk[b] = __shfl_sync(0xffffffffu, x, pl) * ia;
             }
-            const bool ownk = tx == kk;
+            const bool ownk = warp == kw;
 #pragma unroll
-            for (int a = 0; a < MT; ++a) {
-                const int i = ty + 16 * a;
+            for (int a = 0; a < MA; ++a) {
+                const int i = lane + 32 * a;
                 if (i == p) {
 #pragma unroll
-                    for (int b = 0; b < MT; ++b) v[a][b] = (b == kb && ownk) ? ia : -v[a][b] * ia;
+                    for (int b = 0; b < MB; ++b) v[a][b] = (b == kb && ownk) ? ia : -v[a][b] * ia;
                 } else {
                     const float ck = i < m ? colb[s][i] : 0.f;
 #pragma unroll
-                    for (int b = 0; b < MT; ++b)
+                    for (int b = 0; b < MB; ++b)
                         v[a][b] = (b == kb && ownk) ? ck * ia : fmaf(-ck, rk[b], v[a][b]);
                 }
             }
         }
     }
     __syncthreads();
-    // (A^-1)[inv[i]][perm[j]] = T[i][j]
 #pragma unroll
-    for (int a = 0; a < MT; ++a)
+    for (int a = 0; a < MA; ++a)
 #pragma unroll
-        for (int b = 0; b < MT; ++b) {
-            const int i = ty + 16 * a, j = tx + 16 * b;
+        for (int b = 0; b < MB; ++b) {
+            const int i = lane + 32 * a, j = warp + 8 * b;
             if (i < m && j < m) g[(size_t)inv[i] * m + perm[j]] = v[a][b];
         }
 }
@@ -369,9 +361,9 @@ static int blk_build(pb_ctx* c, const long long* dmoff, long long ntot, int mcap
     PB_LAUNCH(c);
     if (sizeof(R) == 4 && mcap <= 192) {
         if (mcap <= 128)
-            k_blk_gj_reg<8><<<ncl, 256, 0, c->st>>>(c->pc_begin, dmoff, (float*)M, sing);
+            k_blk_gj_w<4, 16><<<ncl, 256, 0, c->st>>>(c->pc_begin, dmoff, (float*)M, sing);
         else
-            k_blk_gj_reg<12><<<ncl, 256, 0, c->st>>>(c->pc_begin, dmoff, (float*)M, sing);
+            k_blk_gj_w<6, 24><<<ncl, 256, 0, c->st>>>(c->pc_begin, dmoff, (float*)M, sing);
         PB_LAUNCH(c);
         int hs = 0;
         PB_CUDA(c, cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, c->st));
