@@ -137,6 +137,8 @@ __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __rest
     const int Tp = pb_nterms(pp), Tc = pb_nterms(pc);
     R* part0 = (R*)dsm;       // [8][Tp]
     R* partk = part0 + 8 * Tp;
+    R* cm0 = partk + 8 * Tp;  // [8][Tc] the children's moments, staged once
+    R* cmk = cm0 + 8 * Tc;
     for (int t = threadIdx.x; t < (PB_PMAX + 1) * (PB_PMAX + 1); t += blockDim.x)
         sbin[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)] = (R)c_binom[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)];
     const int c = blockIdx.x;
@@ -149,13 +151,17 @@ __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __rest
             v *= d;
         }
     }
+    for (int t = threadIdx.x; t < nch * Tc; t += blockDim.x) {
+        cm0[t] = c0[(size_t)cb * Tc + t];
+        cmk[t] = ck[(size_t)cb * Tc + t];
+    }
     __syncthreads();
     for (int w = threadIdx.x; w < nch * Tp; w += M2M_T) {
         const int ch = w / Tp, al = w - ch * Tp;
         int a1, a2, a3;
         mi_unpack(c_mi[al], a1, a2, a3);
-        const R* m0 = c0 + (size_t)(cb + ch) * Tc;
-        const R* mk = ck + (size_t)(cb + ch) * Tc;
+        const R* m0 = cm0 + ch * Tc;
+        const R* mk = cmk + ch * Tc;
         R v0 = 0, vk = 0;
         for (int b1 = 0; b1 <= a1; ++b1)
             for (int b2 = 0; b2 <= a2; ++b2) {
@@ -689,8 +695,14 @@ __global__ void __launch_bounds__(FAR_T) k_l2l(int pp, int pc, const int* __rest
         }
     }
     __syncthreads();
-    const R* m0 = lp0 + (size_t)P * Tp;
-    const R* mk = lpk + (size_t)P * Tp;
+    __shared__ R pm0[NT_MAX], pmk[NT_MAX];
+    for (int t = threadIdx.x; t < Tp; t += FAR_T) {
+        pm0[t] = lp0[(size_t)P * Tp + t];
+        pmk[t] = lpk[(size_t)P * Tp + t];
+    }
+    __syncthreads();
+    const R* m0 = pm0;
+    const R* mk = pmk;
     for (int be = threadIdx.x; be < Tc; be += FAR_T) {
         int b1, b2, b3;
         mi_unpack(c_mi[be], b1, b2, b3);
@@ -929,7 +941,7 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
     for (int l = L - 1; l >= lmin; --l) {
         PbLevel& lv = c->lev[l];
         PbLevel& ch = c->lev[l + 1];
-        const size_t msm = 2 * 8 * (size_t)pb_nterms(lv.p) * sizeof(R);
+        const size_t msm = 2 * 8 * ((size_t)pb_nterms(lv.p) + pb_nterms(ch.p)) * sizeof(R);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm));
         k_m2m<R><<<dim3(lv.ncl, nr), M2M_T, msm, c->st>>>(lv.p, ch.p, lv.cbeg, lv.xc, ch.xc, (R*)ch.sig0,
                                                         (R*)ch.sigk, (R*)lv.sig0, (R*)lv.sigk, sstr(ch), sstr(lv));

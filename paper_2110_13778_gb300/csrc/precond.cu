@@ -290,24 +290,25 @@ __global__ void __launch_bounds__(256, 1) k_blk_gj_w(const int* __restrict__ beg
         }
 }
 
-// z = M^-1 r per leaf: one warp per row, lanes stride the columns
+// z = M^-1 r per leaf: the block's slice of r staged once in shared memory (in the working
+// precision), then one warp per row with lanes striding the columns
 template <class R>
 __global__ void k_blk_apply(int nt, const int* __restrict__ begin, const long long* __restrict__ moff,
                             const R* __restrict__ minv, const double* __restrict__ r, double* __restrict__ z,
                             long long rstr, long long zstr)
 {
+    __shared__ R rv[2 * PB_PC_BMAX];
     r += blockIdx.y * rstr;  // right-hand side blockIdx.y
     z += blockIdx.y * zstr;
     const int c = blockIdx.x;
     const int b = begin[c], n = begin[c + 1] - begin[c], m = 2 * n;
     const R* Mc = minv + moff[c];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) rv[j] = (R)(j < n ? r[b + j] : r[nt + b + j - n]);
+    __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31, nw = blockDim.x / 32;
     for (int i = warp; i < m; i += nw) {
         R s = 0;
-        for (int j = lane; j < m; j += 32) {
-            double rv = j < n ? r[b + j] : r[nt + b + j - n];
-            s += Mc[(size_t)i * m + j] * (R)rv;
-        }
+        for (int j = lane; j < m; j += 32) s += Mc[(size_t)i * m + j] * rv[j];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
             if (i < n) z[b + i] = (double)s;
