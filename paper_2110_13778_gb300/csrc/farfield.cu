@@ -767,8 +767,8 @@ __global__ void __launch_bounds__(FAR_T) k_l2p(int nt, int p, double eps, const 
             s1 += A1[al] * mx * my * mz;
             s2 += A2[al] * dm;
         }
-        ys[k] -= P.w * (double)s1;
-        ys[nt + k] -= P.w * (double)s2;
+        ys[k] = -(P.w * (double)s1);  // every element lies in one leaf: the far-field part is set here
+        ys[nt + k] = -(P.w * (double)s2);
     }
 }
 
@@ -845,24 +845,24 @@ static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
 }
 
 template <int P, class R>
-static int m2l_fast_launch(pb_ctx* c, PbLevel& lv, int nr)
+static int m2l_fast_launch(pb_ctx* c, PbLevel& lv, int nr, cudaStream_t st)
 {
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
     const long long sstr = (long long)lv.ncl * T, mstr = (long long)lv.nslots * T;
-    k_m2l_gather<R><<<dim3((unsigned)(lv.nslots / 32), nr), 256, 0, c->st>>>(
+    k_m2l_gather<R><<<dim3((unsigned)(lv.nslots / 32), nr), 256, 0, st>>>(
         T, lv.slot_src, (const R*)lv.sig0, (const R*)lv.sigk, (R*)lv.Mg0, (R*)lv.Mgk, sstr, mstr);
     PB_LAUNCH(c);
     if constexpr (sizeof(R) == sizeof(float)) {
         size_t smem = 4 * (size_t)T * 32 * sizeof(float);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_tma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_tma<P><<<dim3(lv.ncl, nr), 32, smem, c->st>>>(lv.ncl, lv.slot_off, (const float*)lv.D0,
+        k_m2l_tma<P><<<dim3(lv.ncl, nr), 32, smem, st>>>(lv.ncl, lv.slot_off, (const float*)lv.D0,
                                                              (const float*)lv.Dk, (const float*)lv.Mg0,
                                                              (const float*)lv.Mgk, (float*)lv.lam0, (float*)lv.lamk,
                                                              c->dev_err, mstr, sstr);
     } else {
         size_t smem = (size_t)T * 33 * sizeof(R);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_chunks<P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_chunks<P, R><<<dim3(lv.ncl, nr), 32, smem, c->st>>>(lv.ncl, lv.slot_off, (const R*)lv.D0,
+        k_m2l_chunks<P, R><<<dim3(lv.ncl, nr), 32, smem, st>>>(lv.ncl, lv.slot_off, (const R*)lv.D0,
                                                                   (const R*)lv.Dk, (const R*)lv.Mg0, (const R*)lv.Mgk,
                                                                   (R*)lv.lam0, (R*)lv.lamk, mstr, sstr);
     }
@@ -915,12 +915,16 @@ int pb_far_setup(pb_ctx* c)
     return PB_OK;
 }
 
-// nr right-hand sides: xs and ys hold nr vectors of 2 nt, one after the other
+// nr right-hand sides: xs and ys hold nr vectors of 2 nt, one after the other; ys receives the
+// far-field part of the product (overwritten). All work is queued on stream st.
 template <class R>
-static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
+static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream_t st)
 {
     const int L = c->L;
-    if (L < 1) return PB_OK;
+    if (L < 1) {
+        PB_CUDA(c, cudaMemsetAsync(ys, 0, sizeof(double) * 2 * c->nt * nr, st));
+        return PB_OK;
+    }
     int rc0 = pb_far_reserve(c, nr);
     if (rc0) return rc0;
     double eps = c->prm.eps_out / c->prm.eps_in;
@@ -930,11 +934,14 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
     // would only ever be zero or unused
     int lmin = 1;
     while (lmin <= L && c->lev[lmin].ninter == 0) ++lmin;
-    if (lmin > L) return PB_OK;  // every pair is near
-    pb_tic(c, PB_T_UP);
+    if (lmin > L) {  // every pair is near
+        PB_CUDA(c, cudaMemsetAsync(ys, 0, sizeof(double) * 2 * c->nt * nr, st));
+        return PB_OK;
+    }
+    pb_tic_on(c, PB_T_UP, st);
     {
         PbLevel& lv = c->lev[L];
-        k_p2m<R><<<dim3(lv.ncl, nr), FAR_T, 0, c->st>>>(c->nt, lv.p, lv.begin, lv.xc, c->e64p, c->e64n, xs, eps,
+        k_p2m<R><<<dim3(lv.ncl, nr), FAR_T, 0, st>>>(c->nt, lv.p, lv.begin, lv.xc, c->e64p, c->e64n, xs, eps,
                                                         (R*)lv.sig0, (R*)lv.sigk, vstr, sstr(lv));
         PB_LAUNCH(c);
     }
@@ -943,47 +950,47 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
         PbLevel& ch = c->lev[l + 1];
         const size_t msm = 2 * 8 * ((size_t)pb_nterms(lv.p) + pb_nterms(ch.p)) * sizeof(R);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm));
-        k_m2m<R><<<dim3(lv.ncl, nr), M2M_T, msm, c->st>>>(lv.p, ch.p, lv.cbeg, lv.xc, ch.xc, (R*)ch.sig0,
+        k_m2m<R><<<dim3(lv.ncl, nr), M2M_T, msm, st>>>(lv.p, ch.p, lv.cbeg, lv.xc, ch.xc, (R*)ch.sig0,
                                                         (R*)ch.sigk, (R*)lv.sig0, (R*)lv.sigk, sstr(ch), sstr(lv));
         PB_LAUNCH(c);
     }
-    pb_toc(c, PB_T_UP);
-    pb_tic(c, PB_T_M2L);
+    pb_toc_on(c, PB_T_UP, st);
+    pb_tic_on(c, PB_T_M2L, st);
     for (int l = lmin; l <= L; ++l) {
         PbLevel& lv = c->lev[l];
         int rc = -1;
         if (lv.D0) {
-            if (lv.p == 4) rc = m2l_fast_launch<4, R>(c, lv, nr);
-            else if (lv.p == 6) rc = m2l_fast_launch<6, R>(c, lv, nr);
-            else if (lv.p == 8) rc = m2l_fast_launch<8, R>(c, lv, nr);
+            if (lv.p == 4) rc = m2l_fast_launch<4, R>(c, lv, nr, st);
+            else if (lv.p == 6) rc = m2l_fast_launch<6, R>(c, lv, nr, st);
+            else if (lv.p == 8) rc = m2l_fast_launch<8, R>(c, lv, nr, st);
         }
         if (rc > 0) return rc;
         if (rc == 0) continue;
-        k_m2l<R><<<dim3(lv.ncl, nr), FAR_T, 0, c->st>>>(lv.p, c->prm.kappa, lv.int_off, lv.int_idx, lv.xc,
+        k_m2l<R><<<dim3(lv.ncl, nr), FAR_T, 0, st>>>(lv.p, c->prm.kappa, lv.int_off, lv.int_idx, lv.xc,
                                                         (R*)lv.sig0, (R*)lv.sigk, (R*)lv.lam0, (R*)lv.lamk, sstr(lv));
         PB_LAUNCH(c);
     }
-    pb_toc(c, PB_T_M2L);
-    pb_tic(c, PB_T_DOWN);
+    pb_toc_on(c, PB_T_M2L, st);
+    pb_tic_on(c, PB_T_DOWN, st);
     for (int l = lmin; l < L; ++l) {
         PbLevel& lv = c->lev[l];
         PbLevel& ch = c->lev[l + 1];
-        k_l2l<R><<<dim3(ch.ncl, nr), FAR_T, 0, c->st>>>(lv.p, ch.p, ch.parent, lv.xc, ch.xc, (R*)lv.lam0,
+        k_l2l<R><<<dim3(ch.ncl, nr), FAR_T, 0, st>>>(lv.p, ch.p, ch.parent, lv.xc, ch.xc, (R*)lv.lam0,
                                                         (R*)lv.lamk, (R*)ch.lam0, (R*)ch.lamk, sstr(lv), sstr(ch));
         PB_LAUNCH(c);
     }
     {
         PbLevel& lv = c->lev[L];
-        k_l2p<R><<<dim3(lv.ncl, nr), FAR_T, 0, c->st>>>(c->nt, lv.p, eps, lv.begin, lv.xc, c->e64p, c->e64n,
+        k_l2p<R><<<dim3(lv.ncl, nr), FAR_T, 0, st>>>(c->nt, lv.p, eps, lv.begin, lv.xc, c->e64p, c->e64n,
                                                         (R*)lv.lam0, (R*)lv.lamk, ys, sstr(lv), vstr);
         PB_LAUNCH(c);
     }
-    pb_toc(c, PB_T_DOWN);
+    pb_toc_on(c, PB_T_DOWN, st);
     return PB_OK;
 }
 
-int pb_far_apply(pb_ctx* c, const double* xs, double* ys, int nr)
+int pb_far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream_t st)
 {
-    if (c->prm.precision == PB_MIXED) return far_apply<float>(c, xs, ys, nr);
-    return far_apply<double>(c, xs, ys, nr);
+    if (c->prm.precision == PB_MIXED) return far_apply<float>(c, xs, ys, nr, st);
+    return far_apply<double>(c, xs, ys, nr, st);
 }

@@ -262,21 +262,29 @@ __global__ void k_near_finish(int nt, const double4_32a* __restrict__ ep, const 
     ys[nt + k] = 0.5 * (1.0 + 1.0 / eps) * A * xs[nt + k] - A * ys[nt + k];
 }
 
-// Sauter-Schwab corrections of identical and adjacent pairs (FP64)
+// Sauter-Schwab corrections of identical and adjacent pairs (FP64), and the far-field part of
+// the product when yf is given (xs == nullptr: the far field alone)
 __global__ void k_corrections(int nt, const int* __restrict__ toff, const int* __restrict__ tj,
                               const double* __restrict__ corr, const double* __restrict__ xs,
-                              double* __restrict__ ys)
+                              double* __restrict__ ys, const double* __restrict__ yf)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nt) return;
-    xs += 2LL * nt * blockIdx.y;
-    ys += 2LL * nt * blockIdx.y;
+    const long long o = 2LL * nt * blockIdx.y;
+    ys += o;
     double y1 = 0.0, y2 = 0.0;
-    for (int t = toff[k]; t < toff[k + 1]; ++t) {
-        int j = tj[t];
-        double ph = xs[j], dph = xs[nt + j];
-        y1 += corr[4 * t] * dph + corr[4 * t + 1] * ph;
-        y2 += corr[4 * t + 2] * dph + corr[4 * t + 3] * ph;
+    if (xs) {
+        xs += o;
+        for (int t = toff[k]; t < toff[k + 1]; ++t) {
+            int j = tj[t];
+            double ph = xs[j], dph = xs[nt + j];
+            y1 += corr[4 * t] * dph + corr[4 * t + 1] * ph;
+            y2 += corr[4 * t + 2] * dph + corr[4 * t + 3] * ph;
+        }
+    }
+    if (yf) {
+        y1 -= yf[o + k];
+        y2 -= yf[o + nt + k];
     }
     ys[k] -= y1;
     ys[nt + k] -= y2;
@@ -330,10 +338,10 @@ int pb_near_apply(pb_ctx* c, const double* xs, double* ys)
     return PB_OK;
 }
 
-int pb_corr_apply(pb_ctx* c, const double* xs, double* ys, int nr)
+int pb_corr_apply(pb_ctx* c, const double* xs, double* ys, int nr, const double* yfar)
 {
     k_corrections<<<dim3((c->nt + 255) / 256, nr), 256, 0, c->st>>>(c->nt, c->touch_off, c->touch_j, c->corr, xs,
-                                                                     ys);
+                                                                     ys, yfar);
     PB_LAUNCH(c);
     return PB_OK;
 }

@@ -49,6 +49,8 @@ static void pb_free_build(pb_ctx* c)
     c->far_nr = 1;
     c->mxs = c->mys = c->gbV = c->gbW = c->gbZ = c->gbB = c->gbpart = c->gbsmall = nullptr;
     c->near_dens = nullptr;
+    c->yfar = nullptr;
+    c->yfar_nr = 0;
     c->L = 0;
     for (auto& l : c->lev) l = PbLevel();
     c->cent = c->area = c->nrm = nullptr;
@@ -101,6 +103,16 @@ extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
     unsigned long long keep = ~0ULL;  // never hand released blocks back to the driver early
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     for (int i = 0; i < 10; ++i) cudaEventCreate(&c->ev[i]);
+    // the far field runs on a second stream of the highest priority, overlapping the near field
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        pb_destroy(c);
+        return PB_ERR_CUDA;
+    }
     *out = c;
     return PB_OK;
 }
@@ -111,6 +123,12 @@ extern "C" int pb_destroy(pb_ctx* c)
     for (void* p : c->mesh_allocs) cudaFreeAsync(p, c->st);
     for (void* p : c->build_allocs) cudaFreeAsync(p, c->st);
     cudaStreamSynchronize(c->st);
+    if (c->st2) {
+        cudaStreamSynchronize(c->st2);
+        cudaStreamDestroy(c->st2);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     for (int i = 0; i < 10; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -259,36 +277,45 @@ int pb_scatter(pb_ctx* c, const double* xs, double* x)
     return PB_OK;
 }
 
-int pb_matvec_sorted(pb_ctx* c, const double* xs, double* ys, int which)
+// y = A x in tree order for nr vectors (which: 0 = all, 1 = near field incl. mass and
+// corrections, 2 = far field). The far field runs on the context's second stream into its own
+// buffer, overlapping the near field; the corrections kernel waits for it and adds it in.
+static int matvec_parts(pb_ctx* c, const double* xs, double* ys, int nr, int which)
 {
     int rc;
-    if (which == 2) {
-        PB_CUDA(c, cudaMemsetAsync(ys, 0, sizeof(double) * 2 * c->nt, c->st));
-    } else {
-        pb_tic(c, PB_T_NEAR);
-        if ((rc = pb_near_apply(c, xs, ys))) return rc;
-        pb_toc(c, PB_T_NEAR);
-        pb_tic(c, PB_T_CORR);
-        if ((rc = pb_corr_apply(c, xs, ys, 1))) return rc;
-        pb_toc(c, PB_T_CORR);
+    const bool far = which != 1;
+    if (far) {
+        // every buffer the far field touches exists before the fork
+        if ((rc = pb_far_reserve(c, nr))) return rc;
+        if (nr > c->yfar_nr) {
+            c->yfar = (double*)pb_alloc(c, sizeof(double) * 2 * (size_t)c->nt * nr);
+            if (!c->yfar) return pb_fail(c, PB_ERR_NOMEM, "matvec: out of memory");
+            c->yfar_nr = nr;
+        }
+        PB_CUDA(c, cudaEventRecord(c->ev_fork, c->st));
+        PB_CUDA(c, cudaStreamWaitEvent(c->st2, c->ev_fork, 0));
+        if ((rc = pb_far_apply(c, xs, c->yfar, nr, c->st2))) return rc;
+        PB_CUDA(c, cudaEventRecord(c->ev_join, c->st2));
     }
-    if (which != 1)
-        if ((rc = pb_far_apply(c, xs, ys, 1))) return rc;
+    if (which == 2) {
+        PB_CUDA(c, cudaMemsetAsync(ys, 0, sizeof(double) * 2 * c->nt * nr, c->st));
+        PB_CUDA(c, cudaStreamWaitEvent(c->st, c->ev_join, 0));
+        return pb_corr_apply(c, nullptr, ys, nr, c->yfar);
+    }
+    pb_tic(c, PB_T_NEAR);
+    if ((rc = nr == 1 ? pb_near_apply(c, xs, ys) : pb_near_apply_multi(c, xs, ys, nr))) return rc;
+    pb_toc(c, PB_T_NEAR);
+    if (far) PB_CUDA(c, cudaStreamWaitEvent(c->st, c->ev_join, 0));
+    pb_tic(c, PB_T_CORR);
+    if ((rc = pb_corr_apply(c, xs, ys, nr, far ? c->yfar : nullptr))) return rc;
+    pb_toc(c, PB_T_CORR);
     return PB_OK;
 }
 
+int pb_matvec_sorted(pb_ctx* c, const double* xs, double* ys, int which) { return matvec_parts(c, xs, ys, 1, which); }
+
 // nr products at once: xs and ys hold nr vectors of 2 nt in tree order
-int pb_matvec_sorted_multi(pb_ctx* c, const double* xs, double* ys, int nr)
-{
-    int rc;
-    pb_tic(c, PB_T_NEAR);
-    if ((rc = pb_near_apply_multi(c, xs, ys, nr))) return rc;
-    pb_toc(c, PB_T_NEAR);
-    pb_tic(c, PB_T_CORR);
-    if ((rc = pb_corr_apply(c, xs, ys, nr))) return rc;
-    pb_toc(c, PB_T_CORR);
-    return pb_far_apply(c, xs, ys, nr);
-}
+int pb_matvec_sorted_multi(pb_ctx* c, const double* xs, double* ys, int nr) { return matvec_parts(c, xs, ys, nr, 0); }
 
 // tree-ordered work vectors for nr right-hand sides (build lifetime, grown on demand)
 static int reserve_multi(pb_ctx* c, int nr)

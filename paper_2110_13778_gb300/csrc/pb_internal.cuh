@@ -58,6 +58,8 @@ struct PbLevel {
 struct pb_ctx {
     pb_params prm;
     cudaStream_t st = nullptr;
+    cudaStream_t st2 = nullptr;      // far field, concurrent with the near field on st
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err = "no error";
     bool dead = false;
     cudaMemPool_t pool = nullptr;    // device memory pool of this context
@@ -94,6 +96,8 @@ struct pb_ctx {
     float4* near_sp = nullptr;  // (x_hi, y_hi, z_hi, A phi)
     float4* near_sn = nullptr;  // (n_x, n_y, n_z, A dphi)
     float2* near_dens = nullptr; // [dens_nr][nt] (A phi, A dphi) for several right-hand sides
+    double* yfar = nullptr;      // [yfar_nr][2 nt] far-field part of the product (tree order)
+    int yfar_nr = 0;
     int dens_nr = 0;
     // touching pairs (share >= 1 vertex, incl. i == j), CSR by sorted target position
     int* touch_off = nullptr; // [nt + 1]
@@ -143,6 +147,15 @@ inline void pb_toc(pb_ctx* c, int slot)
 {
     if (c->timing && c->tcount[slot] < PB_TMAX) cudaEventRecord(c->tev[1][slot][c->tcount[slot]++], c->st);
 }
+// the same on another stream of the context
+inline void pb_tic_on(pb_ctx* c, int slot, cudaStream_t s)
+{
+    if (c->timing && c->tcount[slot] < PB_TMAX) cudaEventRecord(c->tev[0][slot][c->tcount[slot]], s);
+}
+inline void pb_toc_on(pb_ctx* c, int slot, cudaStream_t s)
+{
+    if (c->timing && c->tcount[slot] < PB_TMAX) cudaEventRecord(c->tev[1][slot][c->tcount[slot]++], s);
+}
 
 // error helpers (pb_api.cu)
 int pb_fail(pb_ctx* c, int code, const char* fmt, ...);
@@ -171,10 +184,10 @@ int pb_geometry_and_tree(pb_ctx* c);          // tree.cu
 int pb_touching_and_singular(pb_ctx* c);      // singular.cu
 int pb_near_setup(pb_ctx* c);                                      // nearfield.cu
 int pb_near_apply(pb_ctx* c, const double* xs, double* ys);        // nearfield.cu (writes ys)
-int pb_corr_apply(pb_ctx* c, const double* xs, double* ys, int nr);  // nearfield.cu (adds)
+int pb_corr_apply(pb_ctx* c, const double* xs, double* ys, int nr, const double* yfar);  // nearfield.cu (adds)
 int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr);  // nearfield.cu (writes)
 int pb_far_setup(pb_ctx* c);                                       // farfield.cu
-int pb_far_apply(pb_ctx* c, const double* xs, double* ys, int nr);  // farfield.cu (adds; nr vectors)
+int pb_far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream_t st);  // farfield.cu (sets ys)
 int pb_far_reserve(pb_ctx* c, int nr);
 int pb_precond_build(pb_ctx* c);                                   // precond.cu
 int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z);
