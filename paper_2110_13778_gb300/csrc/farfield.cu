@@ -790,6 +790,7 @@ static int upload_tables(pb_ctx* c)
     PB_CUDA(c, cudaMemcpyToSymbol(c_mi, mi, sizeof(mi)));
     PB_CUDA(c, cudaMemcpyToSymbol(c_fact, f, sizeof(f)));
     PB_CUDA(c, cudaMemcpyToSymbol(c_binom, bn, sizeof(bn)));
+    c->tables_ready = true;
     return PB_OK;
 }
 
@@ -798,10 +799,11 @@ static bool m2l_fast_order(int p) { return p == 4 || p == 6 || p == 8; }
 // interaction lists padded to multiples of 32 slots, then the derivative tensors per slot
 static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
 {
+    cudaStream_t fs = c->st2;  // the whole far-field setup runs on the second stream
     std::vector<int> off(lv.ncl + 1), idx(lv.ninter);
-    PB_CUDA(c, cudaMemcpyAsync(off.data(), lv.int_off, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost, c->st));
-    PB_CUDA(c, cudaMemcpyAsync(idx.data(), lv.int_idx, sizeof(int) * lv.ninter, cudaMemcpyDeviceToHost, c->st));
-    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    PB_CUDA(c, cudaMemcpyAsync(off.data(), lv.int_off, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost, fs));
+    PB_CUDA(c, cudaMemcpyAsync(idx.data(), lv.int_idx, sizeof(int) * lv.ninter, cudaMemcpyDeviceToHost, fs));
+    PB_CUDA(c, cudaStreamSynchronize(fs));
     std::vector<int> soff(lv.ncl + 1);
     soff[0] = 0;
     for (int k = 0; k < lv.ncl; ++k) soff[k + 1] = soff[k] + ((off[k + 1] - off[k] + 31) / 32) * 32;
@@ -813,34 +815,34 @@ static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
     lv.nslots = soff[lv.ncl];
     const int T = pb_nterms(lv.p);
     size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
-    lv.slot_off = (int*)pb_alloc(c, sizeof(int) * (lv.ncl + 1));
-    lv.slot_src = (int*)pb_alloc(c, sizeof(int) * (lv.nslots + 1));
-    lv.D0 = pb_alloc(c, rs * (size_t)lv.nslots * T);
-    lv.Dk = pb_alloc(c, rs * (size_t)lv.nslots * T);
-    lv.Mg0 = pb_alloc(c, rs * (size_t)lv.nslots * T);
-    lv.Mgk = pb_alloc(c, rs * (size_t)lv.nslots * T);
+    lv.slot_off = (int*)pb_alloc_on(c, sizeof(int) * (lv.ncl + 1), fs);
+    lv.slot_src = (int*)pb_alloc_on(c, sizeof(int) * (lv.nslots + 1), fs);
+    lv.D0 = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
+    lv.Dk = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
+    lv.Mg0 = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
+    lv.Mgk = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
     if (!lv.slot_off || !lv.slot_src || !lv.D0 || !lv.Dk || !lv.Mg0 || !lv.Mgk)
         return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
-    PB_CUDA(c, cudaMemcpyAsync(lv.slot_off, soff.data(), sizeof(int) * (lv.ncl + 1), cudaMemcpyHostToDevice, c->st));
-    PB_CUDA(c, cudaMemcpyAsync(lv.slot_src, ssrc.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, c->st));
-    int* stg = (int*)pb_alloc(c, sizeof(int) * (lv.nslots + 1));
+    PB_CUDA(c, cudaMemcpyAsync(lv.slot_off, soff.data(), sizeof(int) * (lv.ncl + 1), cudaMemcpyHostToDevice, fs));
+    PB_CUDA(c, cudaMemcpyAsync(lv.slot_src, ssrc.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, fs));
+    int* stg = (int*)pb_alloc_on(c, sizeof(int) * (lv.nslots + 1), fs);
     if (!stg) return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
-    PB_CUDA(c, cudaMemcpyAsync(stg, stgt.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(stg, stgt.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, fs));
+    // host vectors above are read by the queued copies: wait before they go out of scope
+    PB_CUDA(c, cudaStreamSynchronize(fs));
     const size_t smem = sizeof(double) * 3 * (size_t)T * 8;
     const unsigned nb = (unsigned)((lv.nslots + 7) / 8);
     if (nb == 0) {
     } else if (c->prm.precision == PB_MIXED) {
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_setup_ff<<<nb, 256, smem, c->st>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
-                                                 (float*)lv.D0, (float*)lv.Dk);
+        k_m2l_setup_ff<<<nb, 256, smem, fs>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
+                                                  (float*)lv.D0, (float*)lv.Dk);
     } else {
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_setup<double><<<nb, 256, smem, c->st>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
-                                                      (double*)lv.D0, (double*)lv.Dk);
+        k_m2l_setup<double><<<nb, 256, smem, fs>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
+                                                       (double*)lv.D0, (double*)lv.Dk);
     }
     PB_LAUNCH(c);
-    // host vectors above are read by the queued copies: wait before they go out of scope
-    PB_CUDA(c, cudaStreamSynchronize(c->st));
     return PB_OK;
 }
 
@@ -896,22 +898,29 @@ int pb_far_reserve(pb_ctx* c, int nr)
 int pb_far_setup(pb_ctx* c)
 {
     c->far_nr = 1;
-    int rc = upload_tables(c);
+    // on the second stream, after the tree (ev_tree) and concurrently with the singular pass
+    cudaStream_t fs = c->st2;
+    PB_CUDA(c, cudaStreamWaitEvent(fs, c->ev_tree, 0));
+    // the constant tables never change: uploaded by the first build of a context (a blocking
+    // copy, done before any of its streams has work in flight)
+    int rc = c->tables_ready ? PB_OK : upload_tables(c);
     if (rc) return rc;
     size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
     for (int l = 1; l <= c->L; ++l) {
         PbLevel& lv = c->lev[l];
         size_t n = (size_t)lv.ncl * pb_nterms(lv.p);
-        lv.sig0 = pb_alloc(c, rs * n);
-        lv.sigk = pb_alloc(c, rs * n);
-        lv.lam0 = pb_alloc(c, rs * n);
-        lv.lamk = pb_alloc(c, rs * n);
+        lv.sig0 = pb_alloc_on(c, rs * n, fs);
+        lv.sigk = pb_alloc_on(c, rs * n, fs);
+        lv.lam0 = pb_alloc_on(c, rs * n, fs);
+        lv.lamk = pb_alloc_on(c, rs * n, fs);
         if (!lv.sig0 || !lv.sigk || !lv.lam0 || !lv.lamk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");
         if (lv.ninter > 0 && m2l_fast_order(lv.p)) {
             int rc2 = m2l_fast_setup(c, lv);
             if (rc2) return rc2;
         }
     }
+    // the MtL table kernels of all levels ran on the second stream
+    PB_CUDA(c, cudaEventRecord(c->ev_join, c->st2));
     return PB_OK;
 }
 

@@ -20,17 +20,19 @@ int pb_fail(pb_ctx* c, int code, const char* fmt, ...)
     return code;
 }
 
-void* pb_alloc(pb_ctx* c, size_t bytes, bool build_lifetime)
+void* pb_alloc(pb_ctx* c, size_t bytes, bool build_lifetime) { return pb_alloc_on(c, bytes, c->st, build_lifetime); }
+
+void* pb_alloc_on(pb_ctx* c, size_t bytes, cudaStream_t s, bool build_lifetime)
 {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
     // stream-ordered allocation from the context's pool, which keeps released memory for reuse
-    if (cudaMallocFromPoolAsync(&p, bytes, c->pool, c->st) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&p, bytes, c->pool, s) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
-    if (cudaMemsetAsync(p, 0, bytes, c->st) != cudaSuccess) {
-        cudaFreeAsync(p, c->st);
+    if (cudaMemsetAsync(p, 0, bytes, s) != cudaSuccess) {
+        cudaFreeAsync(p, s);
         return nullptr;
     }
     (build_lifetime ? c->build_allocs : c->mesh_allocs).push_back(p);
@@ -108,7 +110,8 @@ extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_tree, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         pb_destroy(c);
         return PB_ERR_CUDA;
@@ -129,6 +132,7 @@ extern "C" int pb_destroy(pb_ctx* c)
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_tree) cudaEventDestroy(c->ev_tree);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     for (int i = 0; i < 10; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -214,16 +218,23 @@ extern "C" int pb_build_tree(pb_ctx* c)
     pb_tic(c, PB_T_TREE);
     if ((rc = pb_geometry_and_tree(c))) return rc;
     pb_toc(c, PB_T_TREE);
+    // Everything that reads tree data back to the host is planned first; then the singular
+    // integrals run on the first stream while the far-field setup (host work and table
+    // kernels) proceeds on the second; the preconditioner, which needs the singular entries,
+    // is factored last and the streams are joined.
+    if ((rc = pb_near_setup(c))) return rc;
+    if ((rc = pb_precond_plan(c))) return rc;
+    PB_CUDA(c, cudaEventRecord(c->ev_tree, c->st));
     pb_tic(c, PB_T_SINGULAR);
     if ((rc = pb_touching_and_singular(c))) return rc;
     pb_toc(c, PB_T_SINGULAR);
-    pb_tic(c, PB_T_FARSETUP);
+    pb_tic_on(c, PB_T_FARSETUP, c->st2);
     if ((rc = pb_far_setup(c))) return rc;
-    if ((rc = pb_near_setup(c))) return rc;
-    pb_toc(c, PB_T_FARSETUP);
+    pb_toc_on(c, PB_T_FARSETUP, c->st2);
     pb_tic(c, PB_T_PCBUILD);
-    if ((rc = pb_precond_build(c))) return rc;
+    if ((rc = pb_precond_factor(c))) return rc;
     pb_toc(c, PB_T_PCBUILD);
+    PB_CUDA(c, cudaStreamWaitEvent(c->st, c->ev_join, 0));
     size_t n2 = 2 * (size_t)c->nt;
     c->xs = (double*)pb_alloc(c, sizeof(double) * n2);
     c->ys = (double*)pb_alloc(c, sizeof(double) * n2);

@@ -59,7 +59,8 @@ struct pb_ctx {
     pb_params prm;
     cudaStream_t st = nullptr;
     cudaStream_t st2 = nullptr;      // far field, concurrent with the near field on st
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tree = nullptr;
+    bool tables_ready = false;       // far-field constant tables uploaded
     std::string err = "no error";
     bool dead = false;
     cudaMemPool_t pool = nullptr;    // device memory pool of this context
@@ -110,6 +111,7 @@ struct pb_ctx {
     int far_nr = 1;               // right-hand sides the far-field work arrays hold
     int npcblk = 0;               // preconditioner blocks
     int pc_max = 0;               // largest block order
+    long long pc_total = 0;       // entries of all blocks
     double pc_sum_m3 = 0;         // sum of m^3 over blocks
     int* pc_begin = nullptr;      // [npcblk + 1] first sorted element of each block
     long long* blk_off = nullptr; // [npcblk + 1] offsets into minv
@@ -178,6 +180,7 @@ int pb_fail(pb_ctx* c, int code, const char* fmt, ...);
 // buffers are freed by the next pb_build_tree or pb_mesh_upload, mesh-lifetime buffers by
 // the next pb_mesh_upload.
 void* pb_alloc(pb_ctx* c, size_t bytes, bool build_lifetime = true);
+void* pb_alloc_on(pb_ctx* c, size_t bytes, cudaStream_t s, bool build_lifetime = true);
 
 // translation-unit entry points
 int pb_geometry_and_tree(pb_ctx* c);          // tree.cu
@@ -189,7 +192,8 @@ int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr);  // ne
 int pb_far_setup(pb_ctx* c);                                       // farfield.cu
 int pb_far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream_t st);  // farfield.cu (sets ys)
 int pb_far_reserve(pb_ctx* c, int nr);
-int pb_precond_build(pb_ctx* c);                                   // precond.cu
+int pb_precond_plan(pb_ctx* c);    // precond.cu: block partition (host, synchronises)
+int pb_precond_factor(pb_ctx* c);                                   // precond.cu
 int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z);
 int pb_precond_apply_multi(pb_ctx* c, const double* r, long long rstr, double* z, long long zstr, int nr);
 int pb_matvec_sorted_multi(pb_ctx* c, const double* xs, double* ys, int nr);  // pb_api.cu

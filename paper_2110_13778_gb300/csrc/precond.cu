@@ -387,17 +387,11 @@ static int blk_build(pb_ctx* c, const long long* dmoff, long long ntot, int mcap
     return PB_OK;
 }
 
-int pb_precond_build(pb_ctx* c)
+// The block partition, from the leaf ranges read back to the host (synchronises; before the
+// singular integrals are queued, so that this read-back does not wait for them).
+int pb_precond_plan(pb_ctx* c)
 {
     const int nt = c->nt;
-    double eps = c->prm.eps_out / c->prm.eps_in;
-    if (c->prm.precond == PB_PRECOND_DIAG) {
-        c->dinv = (double*)pb_alloc(c, sizeof(double) * 4 * nt);
-        if (!c->dinv) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
-        k_diag_build<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->e64p, c->touch_off, c->touch_j, c->corr, eps, c->dinv);
-        PB_LAUNCH(c);
-        return PB_OK;
-    }
     if (c->prm.precond != PB_PRECOND_BLOCK) return PB_OK;
     // blocks: the leaves of the tree; a leaf with more than PB_PC_BMAX elements is split into
     // nearly equal consecutive (Morton-ordered) parts of at most PB_PC_BMAX elements
@@ -437,9 +431,26 @@ int pb_precond_build(pb_ctx* c)
     if (!c->blk_off || !c->pc_begin) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
     PB_CUDA(c, cudaMemcpyAsync(c->pc_begin, pb_.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, c->st));
     PB_CUDA(c, cudaMemcpyAsync(c->blk_off, moff.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice, c->st));
-    int rc = c->prm.precision == PB_MIXED ? blk_build<float>(c, c->blk_off, moff[nb], mcap, nb)
-                                          : blk_build<double>(c, c->blk_off, moff[nb], mcap, nb);
-    return rc;  // blk_build synchronises before the host vectors go out of scope
+    c->pc_total = moff[nb];
+    PB_CUDA(c, cudaStreamSynchronize(c->st));  // the host vectors go out of scope
+    return PB_OK;
+}
+
+// Assemble and invert the blocks (or the 2x2 diagonal blocks): needs the singular entries.
+int pb_precond_factor(pb_ctx* c)
+{
+    const int nt = c->nt;
+    double eps = c->prm.eps_out / c->prm.eps_in;
+    if (c->prm.precond == PB_PRECOND_DIAG) {
+        c->dinv = (double*)pb_alloc(c, sizeof(double) * 4 * nt);
+        if (!c->dinv) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
+        k_diag_build<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->e64p, c->touch_off, c->touch_j, c->corr, eps, c->dinv);
+        PB_LAUNCH(c);
+        return PB_OK;
+    }
+    if (c->prm.precond != PB_PRECOND_BLOCK) return PB_OK;
+    return c->prm.precision == PB_MIXED ? blk_build<float>(c, c->blk_off, c->pc_total, c->pc_max, c->npcblk)
+                                        : blk_build<double>(c, c->blk_off, c->pc_total, c->pc_max, c->npcblk);
 }
 
 // z_q = M^-1 r_q for nr vectors r_q = r + q rstr, z_q = z + q zstr

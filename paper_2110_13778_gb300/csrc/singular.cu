@@ -746,7 +746,7 @@ int pb_touching_and_singular(pb_ctx* c)
                                                     make_int3(T.cnt[0], T.cnt[1], T.cnt[2]), ff_from(c->prm.kappa),
                                                     ff_from(eps), ff_from(1.0 / eps), c->corr);
     PB_LAUNCH(c);
-    // the table's host copy must outlive the queued upload
-    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    // (the table's upload was queued before the synchronisation that read ncanon, so the host
+    // copy may go out of scope now; the singular pass itself is left running)
     return PB_OK;
 }
