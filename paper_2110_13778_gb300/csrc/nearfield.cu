@@ -173,6 +173,106 @@ __global__ void __launch_bounds__(256, 3) k_near32(int nt, int nchunks, const in
     }
 }
 
+// Both directions of a pair at once, by 32 x 32 tiles. K1 and K4 are symmetric in (x, y), and
+// with d = x_i - x_j the double-layer kernels of the reversed pair follow from the same radial
+// factors: K2(j, i) = -(n_i.d) ri3 (eps e1 - 1), K3(j, i) = (n_j.d) ri3 (1 - e1/eps). The warp of
+// target chunk A (lane l holds target A_l) visits every source chunk B of the neighbour leaves
+// c2 >= c that follows A (B after A within A's own leaf); B's records are staged in shared
+// memory and, at step s, lane l pairs A_l with B_(l+s mod 32), keeps the forward terms and
+// hands the reverse terms by one shuffle to lane l+s, which accumulates them for its source.
+// Forward sums of a chunk of B and reverse sums of a tile are FP32, added into FP64 (atomics
+// for the reverse terms and the final forward sums; ys starts at zero). The tile of A with
+// itself keeps only the forward terms and drops the identical pair.
+__global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nchunks, const int* __restrict__ chunk_leaf,
+                                                    const int* __restrict__ chunk_first,
+                                                    const int* __restrict__ begin, const int* __restrict__ noff,
+                                                    const int* __restrict__ nidx, const float4* __restrict__ sp,
+                                                    const float4* __restrict__ sn, const float4* __restrict__ sl,
+                                                    double eps_d, double kappa_d, double* __restrict__ ys)
+{
+    __shared__ float4 sbp[8][32], sbn[8][32], sbl[8][32];
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    if (w >= nchunks) return;
+    const int c = chunk_leaf[w], a0 = chunk_first[w];
+    const int k = a0 + lane;
+    const bool act = k < begin[c + 1];
+    const int kk = act ? k : a0;
+    const float4 tp = sp[kk], tn = sn[kk], tl = sl[kk];
+    const float tphi = act ? tp.w : 0.f, tdphi = act ? tn.w : 0.f;  // A phi_i, A dphi_i of the target
+    const float eps = (float)eps_d, inv_eps = (float)(1.0 / eps_d), kappa = (float)kappa_d;
+    const float i4pi = 0.07957747154594767f;
+    double acc1 = 0.0, acc2 = 0.0;
+    for (int t = noff[c]; t < noff[c + 1]; ++t) {
+        const int c2 = nidx[t];
+        if (c2 < c) continue;
+        const int sb = begin[c2], se = begin[c2 + 1];
+        for (int b0 = (c2 == c ? a0 : sb); b0 < se; b0 += 32) {
+            const bool diag = b0 == a0;
+            const int j = b0 + lane;
+            const bool bact = j < se;
+            const int jj = bact ? j : b0;
+            float4 p = sp[jj], n = sn[jj];
+            if (!bact) p.w = n.w = 0.f;
+            __syncwarp();
+            sbp[wi][lane] = p;
+            sbn[wi][lane] = n;
+            float4 lo = sl[jj];
+            lo.w = bact ? 1.f : 0.f;  // marks a real source (padding lanes repeat the chunk's first)
+            sbl[wi][lane] = lo;
+            __syncwarp();
+            float s1 = 0.f, s2 = 0.f, r1 = 0.f, r2 = 0.f;
+#pragma unroll 2
+            for (int s = 0; s < 32; ++s) {
+                const int m = (lane + s) & 31;
+                const float4 a = sbp[wi][m], b = sbn[wi][m], l = sbl[wi][m];
+                float dx = (tp.x - a.x) + (tl.x - l.x);
+                const float dy = (tp.y - a.y) + (tl.y - l.y);
+                const float dz = (tp.z - a.z) + (tl.z - l.z);
+                // drop the identical pair (the correction's) and padding lanes on either side,
+                // keeping r finite for them
+                const bool ok = !(diag && s == 0) && act && l.w != 0.f;
+                if (!ok) dx = 1.0f;
+                const float r2d = dx * dx + dy * dy + dz * dz;
+                const float rinv = rsqrtf(r2d);
+                const float r = r2d * rinv, tt = kappa * r;
+                float E, g;
+                pb_screen<float>(tt, E, g);
+                const float tE = tt * E;
+                const float c1 = -g - tE;
+                const float c3 = -3.f * g - tt * tt - tE * (3.f + tt);
+                const float ri = rinv * i4pi, ri3 = ri * rinv * rinv;
+                const float nxd = tn.x * dx + tn.y * dy + tn.z * dz;
+                const float nyd = b.x * dx + b.y * dy + b.z * dz;
+                const float nxny = tn.x * b.x + tn.y * b.y + tn.z * b.z;
+                const float e1 = 1.f - c1;
+                const float f2 = ri3 * (eps * e1 - 1.f), f3 = ri3 * (1.f - e1 * inv_eps);
+                const float z = ok ? 1.f : 0.f;
+                const float K1 = -E * ri * z;
+                const float K4 = ri3 * (c3 * nxd * nyd * rinv * rinv - c1 * nxny) * z;
+                s1 += K1 * b.w + (nyd * f2 * z) * a.w;
+                s2 += (-nxd * f3 * z) * b.w + K4 * a.w;
+                // reverse terms for source m, handed to lane m
+                const float zr = diag ? 0.f : z;
+                const float q1 = (K1 * tdphi + (-nxd * f2) * tphi) * zr;
+                const float q2 = ((nyd * f3) * tdphi + K4 * tphi) * zr;
+                r1 += __shfl_sync(0xffffffffu, q1, (lane - s) & 31);
+                r2 += __shfl_sync(0xffffffffu, q2, (lane - s) & 31);
+            }
+            acc1 += (double)s1;
+            acc2 += (double)s2;
+            if (!diag && bact) {
+                atomicAdd(&ys[j], (double)r1);
+                atomicAdd(&ys[nt + j], (double)r2);
+            }
+        }
+    }
+    if (act) {
+        atomicAdd(&ys[k], acc1);
+        atomicAdd(&ys[nt + k], acc2);
+    }
+}
+
 // ---------- several right-hand sides at once (mixed precision) ----------
 // The pair kernels depend on the geometry only, so one evaluation serves NR densities: the
 // source's geometry records are loaded once per pair and each right-hand side adds four FMAs.
@@ -325,9 +425,11 @@ int pb_near_apply(pb_ctx* c, const double* xs, double* ys)
         const int nt = c->nt;
         k_near_pack<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->e32p, c->e32n, xs, c->near_sp, c->near_sn);
         PB_LAUNCH(c);
-        k_near32<<<(c->nchunks * 32 + 255) / 256, 256, 0, c->st>>>(nt, c->nchunks, c->chunk_leaf, c->chunk_first,
-                                                                    lv.begin, lv.near_off, lv.near_idx, c->near_sp,
-                                                                    c->near_sn, c->e32l, xs, eps, c->prm.kappa, ys);
+        PB_CUDA(c, cudaMemsetAsync(ys, 0, sizeof(double) * 2 * nt, c->st));
+        k_near_tile<<<(c->nchunks * 32 + 255) / 256, 256, 0, c->st>>>(nt, c->nchunks, c->chunk_leaf,
+                                                                       c->chunk_first, lv.begin, lv.near_off,
+                                                                       lv.near_idx, c->near_sp, c->near_sn, c->e32l,
+                                                                       eps, c->prm.kappa, ys);
         PB_LAUNCH(c);
         k_near_finish<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->e64p, xs, eps, ys);
     } else
