@@ -173,16 +173,17 @@ __global__ void __launch_bounds__(256, 3) k_near32(int nt, int nchunks, const in
     }
 }
 
-// Both directions of a pair at once, by 32 x 32 tiles. K1 and K4 are symmetric in (x, y), and
-// with d = x_i - x_j the double-layer kernels of the reversed pair follow from the same radial
-// factors: K2(j, i) = -(n_i.d) ri3 (eps e1 - 1), K3(j, i) = (n_j.d) ri3 (1 - e1/eps). The warp of
-// target chunk A (lane l holds target A_l) visits every source chunk B of the neighbour leaves
-// c2 >= c that follows A (B after A within A's own leaf); B's records are staged in shared
-// memory and, at step s, lane l pairs A_l with B_(l+s mod 32), keeps the forward terms and
-// hands the reverse terms by one shuffle to lane l+s, which accumulates them for its source.
-// Forward sums of a chunk of B and reverse sums of a tile are FP32, added into FP64 (atomics
-// for the reverse terms and the final forward sums; ys starts at zero). The tile of A with
-// itself keeps only the forward terms and drops the identical pair.
+// Both directions of a pair at once, by tiles of one target chunk A (up to 32 targets, lane l
+// holds A_l) and one source chunk B of nb <= 32 sources. K1 and K4 are symmetric in (x, y),
+// and with d = x_i - x_j the double-layer kernels of the reversed pair follow from the same
+// radial factors: K2(j, i) = -(n_i.d) ri3 (eps e1 - 1), K3(j, i) = (n_j.d) ri3 (1 - e1/eps).
+// The warp of chunk A visits every source chunk B of the neighbour leaves c2 >= c that
+// follows A (B after A within A's own leaf). B's records are staged in shared memory; at step
+// s (s < nb) lane l pairs A_l with B_((l + s) mod nb), keeps the forward terms and adds the
+// reverse terms to B's shared-memory accumulators (FP32 shared atomics; lanes l and l + nb
+// meet at the same source). Forward sums of a chunk and reverse sums of a tile are FP32,
+// added into FP64 (atomics for the reverse terms and the final forward sums; ys starts at
+// zero). The tile of A with itself keeps only the forward terms and drops the identical pair.
 __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nchunks, const int* __restrict__ chunk_leaf,
                                                     const int* __restrict__ chunk_first,
                                                     const int* __restrict__ begin, const int* __restrict__ noff,
@@ -191,6 +192,7 @@ __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nchunks, const
                                                     double eps_d, double kappa_d, double* __restrict__ ys)
 {
     __shared__ float4 sbp[8][32], sbn[8][32], sbl[8][32];
+    __shared__ float rv1[8][32], rv2[8][32];
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     if (w >= nchunks) return;
@@ -209,29 +211,27 @@ __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nchunks, const
         const int sb = begin[c2], se = begin[c2 + 1];
         for (int b0 = (c2 == c ? a0 : sb); b0 < se; b0 += 32) {
             const bool diag = b0 == a0;
+            const int nb = min(32, se - b0);
             const int j = b0 + lane;
-            const bool bact = j < se;
-            const int jj = bact ? j : b0;
-            float4 p = sp[jj], n = sn[jj];
-            if (!bact) p.w = n.w = 0.f;
             __syncwarp();
-            sbp[wi][lane] = p;
-            sbn[wi][lane] = n;
-            float4 lo = sl[jj];
-            lo.w = bact ? 1.f : 0.f;  // marks a real source (padding lanes repeat the chunk's first)
-            sbl[wi][lane] = lo;
+            if (lane < nb) {
+                sbp[wi][lane] = sp[j];
+                sbn[wi][lane] = sn[j];
+                sbl[wi][lane] = sl[j];
+            }
+            rv1[wi][lane] = 0.f;
+            rv2[wi][lane] = 0.f;
             __syncwarp();
-            float s1 = 0.f, s2 = 0.f, r1 = 0.f, r2 = 0.f;
+            float s1 = 0.f, s2 = 0.f;
+            int m = lane % nb;
 #pragma unroll 2
-            for (int s = 0; s < 32; ++s) {
-                const int m = (lane + s) & 31;
+            for (int s = 0; s < nb; ++s) {
                 const float4 a = sbp[wi][m], b = sbn[wi][m], l = sbl[wi][m];
                 float dx = (tp.x - a.x) + (tl.x - l.x);
                 const float dy = (tp.y - a.y) + (tl.y - l.y);
                 const float dz = (tp.z - a.z) + (tl.z - l.z);
-                // drop the identical pair (the correction's) and padding lanes on either side,
-                // keeping r finite for them
-                const bool ok = !(diag && s == 0) && act && l.w != 0.f;
+                // drop the identical pair (the correction's) and padding targets, keeping r finite
+                const bool ok = act && !(diag && m == lane);
                 if (!ok) dx = 1.0f;
                 const float r2d = dx * dx + dy * dy + dz * dz;
                 const float rinv = rsqrtf(r2d);
@@ -246,24 +246,24 @@ __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nchunks, const
                 const float nyd = b.x * dx + b.y * dy + b.z * dz;
                 const float nxny = tn.x * b.x + tn.y * b.y + tn.z * b.z;
                 const float e1 = 1.f - c1;
-                const float f2 = ri3 * (eps * e1 - 1.f), f3 = ri3 * (1.f - e1 * inv_eps);
                 const float z = ok ? 1.f : 0.f;
+                const float f2 = ri3 * (eps * e1 - 1.f) * z, f3 = ri3 * (1.f - e1 * inv_eps) * z;
                 const float K1 = -E * ri * z;
                 const float K4 = ri3 * (c3 * nxd * nyd * rinv * rinv - c1 * nxny) * z;
-                s1 += K1 * b.w + (nyd * f2 * z) * a.w;
-                s2 += (-nxd * f3 * z) * b.w + K4 * a.w;
-                // reverse terms for source m, handed to lane m
-                const float zr = diag ? 0.f : z;
-                const float q1 = (K1 * tdphi + (-nxd * f2) * tphi) * zr;
-                const float q2 = ((nyd * f3) * tdphi + K4 * tphi) * zr;
-                r1 += __shfl_sync(0xffffffffu, q1, (lane - s) & 31);
-                r2 += __shfl_sync(0xffffffffu, q2, (lane - s) & 31);
+                s1 += K1 * b.w + (nyd * f2) * a.w;
+                s2 += (-nxd * f3) * b.w + K4 * a.w;
+                if (!diag) {
+                    atomicAdd(&rv1[wi][m], K1 * tdphi + (-nxd * f2) * tphi);
+                    atomicAdd(&rv2[wi][m], (nyd * f3) * tdphi + K4 * tphi);
+                }
+                m = m + 1 == nb ? 0 : m + 1;
             }
             acc1 += (double)s1;
             acc2 += (double)s2;
-            if (!diag && bact) {
-                atomicAdd(&ys[j], (double)r1);
-                atomicAdd(&ys[nt + j], (double)r2);
+            __syncwarp();
+            if (!diag && lane < nb) {
+                atomicAdd(&ys[j], (double)rv1[wi][lane]);
+                atomicAdd(&ys[nt + j], (double)rv2[wi][lane]);
             }
         }
     }
