@@ -9,9 +9,12 @@
 //   y1_i = 1/2 (1 + eps) A_i phi_i     - sum_j (I1_ij dphi_j + I2_ij phi_j)
 //   y2_i = 1/2 (1 + 1/eps) A_i dphi_i  - sum_j (I3_ij dphi_j + I4_ij phi_j)
 //
-// Layout: one CTA per target leaf, one thread per target element. Source leaves are staged
-// tile by tile in shared memory (centroid, area, normal, A_j phi_j, A_j dphi_j) and read as
-// warp-wide broadcasts. In mixed precision each source leaf's partial sums are kept in FP32
+// Layout (FP64): one CTA per target leaf, one thread per target element. Source leaves are
+// staged tile by tile in shared memory (centroid, area, normal, A_j phi_j, A_j dphi_j) and read
+// as warp-wide broadcasts. Mixed precision: one warp per chunk of up to 32 targets, which
+// evaluates each pair of distinct chunks once for both directions (k_near_tile; several
+// right-hand sides: k_near32m, one direction, up to 16 densities per pair evaluation). In
+// mixed precision each source leaf's partial sums are kept in FP32
 // and added into FP64 accumulators per leaf (compensated leaf sums), and coordinates are
 // carried as FP32 hi + lo pairs so that d = (x_hi - y_hi) + (x_lo - y_lo) keeps the
 // separation of close elements to FP32 relative accuracy instead of losing digits to the
@@ -124,54 +127,6 @@ __global__ void k_near_pack(int nt, const float4* __restrict__ e32p, const float
     sn[k] = make_float4(n.x, n.y, n.z, (float)(A * xs[nt + k]));
 }
 
-// One warp per chunk of up to 32 targets of a leaf; every lane walks the same sources of the
-// leaf's neighbour list, so source records are warp-uniform loads (one L1 transaction each)
-// and no block-wide synchronisation is needed.
-__global__ void __launch_bounds__(256, 3) k_near32(int nt, int nchunks, const int* __restrict__ chunk_leaf,
-                                                const int* __restrict__ chunk_first,
-                                                const int* __restrict__ begin, const int* __restrict__ noff,
-                                                const int* __restrict__ nidx, const float4* __restrict__ sp,
-                                                const float4* __restrict__ sn, const float4* __restrict__ sl,
-                                                const double* __restrict__ xs, double eps_d, double kappa_d,
-                                                double* __restrict__ ys)
-{
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= nchunks) return;
-    const int c = chunk_leaf[w];
-    const int k = chunk_first[w] + lane;
-    const bool act = k < begin[c + 1];
-    const int kk = act ? k : chunk_first[w];
-    const float4 tp = sp[kk], tn = sn[kk], tl = sl[kk];
-    const float eps = (float)eps_d, inv_eps = (float)(1.0 / eps_d), kappa = (float)kappa_d;
-    double acc1 = 0.0, acc2 = 0.0;
-    for (int t = noff[c]; t < noff[c + 1]; ++t) {
-        const int c2 = nidx[t];
-        const int sb = begin[c2], se = begin[c2 + 1];
-        float s1 = 0.f, s2 = 0.f;
-#pragma unroll 4
-        for (int j = sb; j < se; ++j) {
-            const float4 a = sp[j], b = sn[j], l = sl[j];
-            float K[4];
-            float dx = (tp.x - a.x) + (tl.x - l.x);
-            float dy = (tp.y - a.y) + (tl.y - l.y);
-            float dz = (tp.z - a.z) + (tl.z - l.z);
-            if (j == k) dx = 1.0f;  // the identical pair is the correction's; keep r finite
-            pb_kernels<float>(dx, dy, dz, tn.x, tn.y, tn.z, b.x, b.y, b.z, eps, inv_eps, kappa, K);
-            float u1 = K[0] * b.w + K[1] * a.w;
-            float u2 = K[2] * b.w + K[3] * a.w;
-            s1 += (j == k) ? 0.f : u1;
-            s2 += (j == k) ? 0.f : u2;
-        }
-        acc1 += (double)s1;
-        acc2 += (double)s2;
-    }
-    if (act) {
-        // raw sums; k_near_finish applies A_k and the mass terms in FP64
-        ys[k] = acc1;
-        ys[nt + k] = acc2;
-    }
-}
 
 // Both directions of a pair at once, by tiles of one target chunk A (up to 32 targets, lane l
 // holds A_l) and one source chunk B of nb <= 32 sources. K1 and K4 are symmetric in (x, y),
