@@ -249,9 +249,9 @@ FLOPS_PER_SS_POINT = 100  # FP64 formula count of one Sauter-Schwab point (maps,
 # (228 for the two of identical triangles), plus the point's x - y, r^2, projections and sums.
 FF_INST_PER_SS_POINT = {1: 734, 2: 662, 3: 382}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the same kernel build, or None
-# k_near32: 4.0 MB read at 81920 triangles (captured on this workload); k_singular_ff: 5.25 MB
+# k_near_tile: 5.35 MB read at 81920 triangles (captured on this workload); k_singular_ff: 5.25 MB
 # read at 20480 triangles, scaled by the quadrature points (x 4) to the 81920-triangle launch
-TRAFFIC_BYTES = {"near": 4.0e6, "m2l": None, "singular": 2.1e7, "pcbuild": None}
+TRAFFIC_BYTES = {"near": 5.35e6, "m2l": None, "singular": 2.1e7, "pcbuild": None}
 
 
 def phase_roofline(name, tv, stats, N, a, prec, pk):
