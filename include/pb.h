@@ -220,6 +220,12 @@ int pb_get_timing(pb_ctx* ctx, double* out);
 /* Number of this library's kernel launches queued on ctx since it was created. */
 int pb_get_launch_count(pb_ctx* ctx, long long* out);
 
+/* Number of CUDA-graph replays on ctx: the batched charge-state solve (pb_solve_states mode 2)
+ * captures each Arnoldi step of its lockstep GMRES (about 40 launches over the context's two
+ * streams) into one graph per step index and replays it; with timing enabled it launches the
+ * kernels directly instead. */
+int pb_get_graph_launches(pb_ctx* ctx, long long* out);
+
 /* Autotuner (no counterpart in the paper, which sets the leaf size and order by hand): on the
  * uploaded molecule, tries leaf sizes {32, 48, 64, 96, 128} x orders {4, 6, 8} (uniform order,
  * the context's eta0 and precision), timing pb_build_tree and pb_matvec with CUDA events and

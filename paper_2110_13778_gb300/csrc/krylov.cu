@@ -642,6 +642,80 @@ int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double 
             PB_CUDA(c, cudaMemsetAsync(X + r * n, 0, sizeof(double) * n, c->st));
         }
     }
+    // One Arnoldi step of all right-hand sides: z = M^-1 v_j, w = A z, CGS2, normalisation,
+    // Givens rotation (finished right-hand sides are carried along and discarded).
+    auto step_launches = [&](int j) -> int {
+        int rc2;
+        if ((rc2 = pb_precond_apply_multi(c, V + (size_t)j * n, vstr, Z, n, nr))) return rc2;
+        if ((rc2 = pb_matvec_sorted_multi(c, Z, W, nr))) return rc2;
+        pb_tic(c, PB_T_ARNOLDI);
+        for (int pass = 0; pass < 2; ++pass) {
+            k_bdot<<<dim3(DOT_BLOCKS, j + 1, nr), KB, 0, c->st>>>(n, V, vstr, W, part, pstr);
+            PB_LAUNCH(c);
+            k_bfinish<<<dim3(j + 1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + (pass ? yoff : hoff), S);
+            PB_LAUNCH(c);
+            k_borth<<<dim3(G, nr), KB, 0, c->st>>>(n, j + 1, V, vstr, small + (pass ? yoff : hoff), S, W);
+            PB_LAUNCH(c);
+        }
+        k_bmerge<<<nr, 64, 0, c->st>>>(j + 1, small, S, yoff, hoff);
+        PB_LAUNCH(c);
+        k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
+        PB_LAUNCH(c);
+        k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff + j + 1, S);
+        PB_LAUNCH(c);
+        k_bscale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, n, small + hoff + j + 1, S, V + (size_t)(j + 1) * n, vstr);
+        PB_LAUNCH(c);
+        k_bgm_givens<<<nr, 1, 0, c->st>>>(m, j, st, S);
+        PB_LAUNCH(c);
+        pb_toc(c, PB_T_ARNOLDI);
+        return PB_OK;
+    };
+    // Each step's launches (about 40, over both streams) are captured once into a CUDA graph
+    // per step index and replayed; the graphs stay valid while the build and this workspace do.
+    // With timing enabled (events per phase) the launches are issued directly.
+    if ((rc = pb_matvec_reserve(c, nr))) return rc;
+    const bool use_graphs = !c->timing;
+    if (c->gb_graph_key != (void*)V || (int)c->gb_graphs.size() != m || c->gb_graph_nr != nr) {
+        pb_drop_graphs(c);
+        c->gb_graphs.assign(m, nullptr);
+        c->gb_graph_n.assign(m, 0);
+        c->gb_graph_key = V;
+        c->gb_graph_nr = nr;
+    }
+    auto arnoldi_step = [&](int j) -> int {
+        if (!use_graphs || c->gb_graph_failed) return step_launches(j);
+        if (!c->gb_graphs[j]) {
+            cudaStream_t keep = c->st;
+            c->st = c->cap_st;  // capture on the context's private stream
+            long long n0 = c->nlaunch;
+            cudaGraph_t g = nullptr;
+            int rc2 = PB_OK;
+            if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                rc2 = -1;
+            } else {
+                rc2 = step_launches(j);
+                if (cudaStreamEndCapture(c->st, &g) != cudaSuccess) rc2 = -1;
+            }
+            c->st = keep;
+            c->gb_graph_n[j] = c->nlaunch - n0;
+            c->nlaunch = n0;
+            cudaGraphExec_t ex = nullptr;
+            if (rc2 == PB_OK && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+                c->gb_graphs[j] = ex;
+            } else {
+                // capture not possible here: issue the launches directly from now on
+                cudaGetLastError();
+                c->gb_graph_failed = true;
+                c->err = "no error";
+            }
+            if (g) cudaGraphDestroy(g);
+            if (!c->gb_graphs[j]) return step_launches(j);
+        }
+        PB_CUDA(c, cudaGraphLaunch(c->gb_graphs[j], c->st));
+        c->nlaunch += c->gb_graph_n[j];
+        ++c->graph_launches;
+        return PB_OK;
+    };
     int it = 0, first = 1;
     auto any_active = [&]() {
         for (int r = 0; r < nr; ++r)
@@ -692,29 +766,7 @@ int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double 
         for (int r = 0; r < nr; ++r) cyc[r] = active[r];
         int j = 0;
         for (; j < m && it < max_iter && any_active(); ++j) {
-            // z = M^-1 v_j, w = A z (all right-hand sides; finished ones are discarded)
-            if ((rc = pb_precond_apply_multi(c, V + (size_t)j * n, vstr, Z, n, nr))) return rc;
-            if ((rc = pb_matvec_sorted_multi(c, Z, W, nr))) return rc;
-            pb_tic(c, PB_T_ARNOLDI);
-            for (int pass = 0; pass < 2; ++pass) {
-                k_bdot<<<dim3(DOT_BLOCKS, j + 1, nr), KB, 0, c->st>>>(n, V, vstr, W, part, pstr);
-                PB_LAUNCH(c);
-                k_bfinish<<<dim3(j + 1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + (pass ? yoff : hoff), S);
-                PB_LAUNCH(c);
-                k_borth<<<dim3(G, nr), KB, 0, c->st>>>(n, j + 1, V, vstr, small + (pass ? yoff : hoff), S, W);
-                PB_LAUNCH(c);
-            }
-            k_bmerge<<<nr, 64, 0, c->st>>>(j + 1, small, S, yoff, hoff);
-            PB_LAUNCH(c);
-            k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
-            PB_LAUNCH(c);
-            k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff + j + 1, S);
-            PB_LAUNCH(c);
-            k_bscale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, n, small + hoff + j + 1, S, V + (size_t)(j + 1) * n, vstr);
-            PB_LAUNCH(c);
-            k_bgm_givens<<<nr, 1, 0, c->st>>>(m, j, st, S);
-            PB_LAUNCH(c);
-            pb_toc(c, PB_T_ARNOLDI);
+            if ((rc = arnoldi_step(j))) return rc;
             if ((rc = read(roff))) return rc;
             ++it;
             for (int r = 0; r < nr; ++r) {

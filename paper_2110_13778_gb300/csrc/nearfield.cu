@@ -413,6 +413,16 @@ static void near_multi_launch(pb_ctx* c, const float2* dens, double* ys, double 
                                                                      c->prm.kappa, ys);
 }
 
+// density buffer of the multi-vector near field (build lifetime, grown on demand)
+int pb_near_reserve(pb_ctx* c, int nr)
+{
+    if (c->prm.precision != PB_MIXED || nr < 2 || nr <= c->dens_nr) return PB_OK;
+    c->near_dens = (float2*)pb_alloc(c, sizeof(float2) * (size_t)c->nt * nr);
+    if (!c->near_dens) return pb_fail(c, PB_ERR_NOMEM, "near field: out of memory");
+    c->dens_nr = nr;
+    return PB_OK;
+}
+
 // nr right-hand sides: xs and ys hold nr vectors of 2 nt; mixed precision evaluates each pair
 // once for up to 16 of them, FP64 applies the single-vector kernel per right-hand side
 int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr)
@@ -426,11 +436,8 @@ int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr)
         }
         return PB_OK;
     }
-    if (nr > c->dens_nr) {
-        c->near_dens = (float2*)pb_alloc(c, sizeof(float2) * (size_t)nt * nr);
-        if (!c->near_dens) return pb_fail(c, PB_ERR_NOMEM, "near field: out of memory");
-        c->dens_nr = nr;
-    }
+    int rc0 = pb_near_reserve(c, nr);
+    if (rc0) return rc0;
     k_near_dens<<<dim3((nt + 255) / 256, nr), 256, 0, c->st>>>(nt, c->e32p, xs, c->near_dens);
     PB_LAUNCH(c);
     for (int r0 = 0; r0 < nr;) {

@@ -47,6 +47,8 @@ static void pb_free_build(pb_ctx* c)
     c->built = false;
     c->gm_m = 0;
     c->scratch = nullptr;
+    pb_drop_graphs(c);
+    c->gb_graph_failed = false;
     c->mv_nr = c->gb_nr = c->gb_m = c->dens_nr = 0;
     c->far_nr = 1;
     c->mxs = c->mys = c->gbV = c->gbW = c->gbZ = c->gbB = c->gbpart = c->gbsmall = nullptr;
@@ -111,7 +113,8 @@ extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
     if (cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_tree, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_tree, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         pb_destroy(c);
         return PB_ERR_CUDA;
@@ -133,6 +136,8 @@ extern "C" int pb_destroy(pb_ctx* c)
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_tree) cudaEventDestroy(c->ev_tree);
+    pb_drop_graphs(c);
+    if (c->cap_st) cudaStreamDestroy(c->cap_st);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     for (int i = 0; i < 10; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -291,18 +296,34 @@ int pb_scatter(pb_ctx* c, const double* xs, double* x)
 // y = A x in tree order for nr vectors (which: 0 = all, 1 = near field incl. mass and
 // corrections, 2 = far field). The far field runs on the context's second stream into its own
 // buffer, overlapping the near field; the corrections kernel waits for it and adds it in.
+int pb_matvec_reserve(pb_ctx* c, int nr)
+{
+    int rc;
+    if ((rc = pb_far_reserve(c, nr))) return rc;
+    if (nr > c->yfar_nr) {
+        c->yfar = (double*)pb_alloc(c, sizeof(double) * 2 * (size_t)c->nt * nr);
+        if (!c->yfar) return pb_fail(c, PB_ERR_NOMEM, "matvec: out of memory");
+        c->yfar_nr = nr;
+    }
+    return pb_near_reserve(c, nr);
+}
+
+void pb_drop_graphs(pb_ctx* c)
+{
+    for (cudaGraphExec_t g : c->gb_graphs)
+        if (g) cudaGraphExecDestroy(g);
+    c->gb_graphs.clear();
+    c->gb_graph_n.clear();
+    c->gb_graph_key = nullptr;
+}
+
 static int matvec_parts(pb_ctx* c, const double* xs, double* ys, int nr, int which)
 {
     int rc;
     const bool far = which != 1;
+    // every buffer the product touches exists before the fork (and before any capture)
+    if ((rc = pb_matvec_reserve(c, nr))) return rc;
     if (far) {
-        // every buffer the far field touches exists before the fork
-        if ((rc = pb_far_reserve(c, nr))) return rc;
-        if (nr > c->yfar_nr) {
-            c->yfar = (double*)pb_alloc(c, sizeof(double) * 2 * (size_t)c->nt * nr);
-            if (!c->yfar) return pb_fail(c, PB_ERR_NOMEM, "matvec: out of memory");
-            c->yfar_nr = nr;
-        }
         PB_CUDA(c, cudaEventRecord(c->ev_fork, c->st));
         PB_CUDA(c, cudaStreamWaitEvent(c->st2, c->ev_fork, 0));
         if ((rc = pb_far_apply(c, xs, c->yfar, nr, c->st2))) return rc;
@@ -575,6 +596,14 @@ extern "C" int pb_get_timing(pb_ctx* c, double* out)
         out[2 * s + 1] = c->tcount[s];
         c->tcount[s] = 0;
     }
+    return PB_OK;
+}
+
+extern "C" int pb_get_graph_launches(pb_ctx* c, long long* out)
+{
+    PB_ALIVE(c);
+    if (!out) return pb_fail(c, PB_ERR_ARG, "null output");
+    *out = c->graph_launches;
     return PB_OK;
 }
 

@@ -127,6 +127,14 @@ struct pb_ctx {
     int mv_nr = 0;
     double *gbV = nullptr, *gbW = nullptr, *gbZ = nullptr, *gbB = nullptr, *gbpart = nullptr, *gbsmall = nullptr;
     int gb_nr = 0, gb_m = 0;
+    // CUDA graphs of the batched Arnoldi steps (one per step index), valid for one workspace
+    std::vector<cudaGraphExec_t> gb_graphs;
+    std::vector<long long> gb_graph_n;  // kernel launches each graph holds
+    void* gb_graph_key = nullptr;
+    int gb_graph_nr = 0;
+    bool gb_graph_failed = false;
+    long long graph_launches = 0;       // replays of captured Arnoldi steps
+    cudaStream_t cap_st = nullptr;      // private stream for capturing
     double* hscal = nullptr;      // pinned host scalars
     // GMRES workspace (Krylov basis, work vectors, reduction partials, small dense state)
     int gm_m = 0;
@@ -189,6 +197,7 @@ int pb_near_setup(pb_ctx* c);                                      // nearfield.
 int pb_near_apply(pb_ctx* c, const double* xs, double* ys);        // nearfield.cu (writes ys)
 int pb_corr_apply(pb_ctx* c, const double* xs, double* ys, int nr, const double* yfar);  // nearfield.cu (adds)
 int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr);  // nearfield.cu (writes)
+int pb_near_reserve(pb_ctx* c, int nr);
 int pb_far_setup(pb_ctx* c);                                       // farfield.cu
 int pb_far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream_t st);  // farfield.cu (sets ys)
 int pb_far_reserve(pb_ctx* c, int nr);
@@ -197,6 +206,8 @@ int pb_precond_factor(pb_ctx* c);                                   // precond.c
 int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z);
 int pb_precond_apply_multi(pb_ctx* c, const double* r, long long rstr, double* z, long long zstr, int nr);
 int pb_matvec_sorted_multi(pb_ctx* c, const double* xs, double* ys, int nr);  // pb_api.cu
+int pb_matvec_reserve(pb_ctx* c, int nr);  // pb_api.cu: every buffer a product of nr vectors needs
+void pb_drop_graphs(pb_ctx* c);           // pb_api.cu
 int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double tol, int max_iter, int restart,
                           pb_solve_info* infos);  // krylov.cu
 int pb_rhs_sorted(pb_ctx* c, double* bs);                          // krylov.cu

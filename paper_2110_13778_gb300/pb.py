@@ -28,7 +28,7 @@ EXPORTS = [
     "pb_get_launch_count", "pb_solvation_energy_noalloc", "pb_solve_states",
     "pb_mlp_create", "pb_mlp_destroy", "pb_mlp_last_error", "pb_mlp_param_count", "pb_mlp_get_params",
     "pb_mlp_set_params", "pb_mlp_forward", "pb_mlp_gradient", "pb_mlp_train_step", "pb_features",
-    "pb_learned_guess", "pb_measure_alu_peaks", "pb_autotune", "pb_matvec_multi",
+    "pb_learned_guess", "pb_measure_alu_peaks", "pb_autotune", "pb_matvec_multi", "pb_get_graph_launches",
 ]
 PB_MAX_RHS = 64
 NFEAT = 18
@@ -119,6 +119,7 @@ def lib():
         L.pb_learned_guess.argtypes = [vp, vp, vp]
         L.pb_measure_alu_peaks.argtypes = [vp, dp, dp]
         L.pb_matvec_multi.argtypes = [vp, vp, vp, c_int]
+        L.pb_get_graph_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.pb_autotune.argtypes = [vp, c_double, c_int, ctypes.POINTER(pb_tune_result)]
         _lib = L
     return _lib
@@ -275,6 +276,12 @@ def pb_get_timing(ctx):
     out = (ctypes.c_double * (2 * len(TIMING_SLOTS)))()
     _check(ctx, lib().pb_get_timing(ctx, out))
     return {s: (out[2 * i], int(out[2 * i + 1])) for i, s in enumerate(TIMING_SLOTS)}
+
+
+def pb_get_graph_launches(ctx):
+    n = ctypes.c_longlong()
+    _check(ctx, lib().pb_get_graph_launches(ctx, ctypes.byref(n)))
+    return n.value
 
 
 def pb_get_launch_count(ctx):
