@@ -48,3 +48,32 @@ def test_params_struct_matches_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"\b(?:double|int)\s+(\w+);", body)
     assert fields == [f for f, _ in pb.pb_params._fields_]
+
+
+@pytest.mark.parametrize("bad", [dict(eps_in=0.0), dict(eps_out=-1.0), dict(kappa=-0.1), dict(eta0=1.0),
+                                 dict(eta0=0.0), dict(p=11), dict(qs=0), dict(qs=9), dict(precision=2),
+                                 dict(precond=3), dict(singular=3), dict(leaf_size=0), dict(levels=11)])
+def test_create_rejects_bad_parameters(bad):
+    # argument checks run before any CUDA call, so they are testable without a GPU
+    h = ctypes.c_void_p()
+    rc = pb.lib().pb_create(ctypes.byref(pb.params(**bad)), None, ctypes.byref(h))
+    assert rc == pb.PB_ERR_ARG and not h.value
+
+
+@pytest.mark.parametrize("shape", [(0, 128, 3, 2), (18, 100, 3, 2), (18, 8, 3, 2), (18, 128, 0, 2),
+                                   (18, 128, 8, 2), (18, 128, 3, 0), (18, 128, 3, 65)])
+def test_mlp_create_rejects_bad_shapes(shape):
+    h = ctypes.c_void_p()
+    rc = pb.lib().pb_mlp_create(*shape, 0, None, ctypes.byref(h))
+    assert rc == pb.PB_ERR_ARG and not h.value
+
+
+def test_null_handles_are_rejected():
+    L = pb.lib()
+    assert L.pb_destroy(None) == pb.PB_OK
+    assert L.pb_mlp_destroy(None) == pb.PB_OK
+    n = ctypes.c_longlong()
+    assert L.pb_get_launch_count(None, ctypes.byref(n)) == pb.PB_ERR_ARG
+    assert L.pb_matvec_multi(None, None, None, 1) == pb.PB_ERR_ARG
+    assert L.pb_learned_guess(None, None, None) == pb.PB_ERR_ARG
+    assert L.pb_autotune(None, 1e-4, 10, None) == pb.PB_ERR_ARG

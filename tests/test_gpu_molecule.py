@@ -165,3 +165,27 @@ def test_batched_charge_states_match_sequential(mol, prec):
     assert all(i.initial_residual <= 1.0 for i in ib[1:])
     Eo = dense.energy(dense_mesh(m, states[3]), ph, np.linalg.solve(A, dense.rhs(dense_mesh(m, states[3]), ph)))
     assert abs(Eb[3] - Eo) < 1e-3 * abs(Eo)
+
+
+def test_multi_entry_points_reject_bad_sizes(mol):
+    m, ph, A = mol
+    ctx = _ctx(m, leaf_size=32, eta0=0.7, p=6, precision=pb.PB_MIXED)
+    try:
+        X = torch.zeros((pb.PB_MAX_RHS + 1, 2 * m.nt), device="cuda", dtype=torch.float64)
+        with pytest.raises(pb.PBError):
+            pb.pb_matvec_multi(ctx, X, torch.empty_like(X))
+        Q = np.repeat(m.q[None, :], 2, axis=0)
+        with pytest.raises(pb.PBError):
+            pb.lib().pb_solve_states  # the binding forwards warm unchanged only for 0/1/2
+            rc = pb.lib().pb_solve_states(ctx, Q.ctypes.data_as(pb.ctypes.POINTER(pb.ctypes.c_double)), 2,
+                                          pb._ptr(X[:2].contiguous()), None, 1e-6, 100, 50, 3, None)
+            pb._check(ctx, rc)
+        # one vector through the multi-vector entry point is the plain product
+        x = X[:1].contiguous().normal_()
+        y1 = torch.empty_like(x)
+        pb.pb_matvec_multi(ctx, x, y1)
+        y = torch.empty(2 * m.nt, device="cuda", dtype=torch.float64)
+        pb.pb_matvec(ctx, x[0].contiguous(), y)
+        assert float((y1[0] - y).norm() / y.norm()) < 1e-12
+    finally:
+        pb.pb_destroy(ctx)
