@@ -551,8 +551,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phas
     return false;
 }
 
-// FP32: one warp per block; D and M chunks arrive by TMA bulk copy into a double buffer,
-// the next chunk's copies in flight while the current chunk is contracted.
+// FP32: one warp per block and per kernel (G0 for blockIdx.z = 0, Gk for 1); the chunk's D and
+// M blocks arrive by TMA bulk copy into shared memory (42 KB at p = 8, so five blocks share an
+// SM and hide each other's copies), completion on an mbarrier, every wait bounded.
 template <int P>
 __global__ void __launch_bounds__(32, 1) k_m2l_tma(int ncl, const int* __restrict__ soff, const float* __restrict__ D0,
                                                    const float* __restrict__ Dk, const float* __restrict__ M0,
@@ -561,73 +562,50 @@ __global__ void __launch_bounds__(32, 1) k_m2l_tma(int ncl, const int* __restric
                                                    long long lstr)
 {
     // right-hand side blockIdx.y: the same derivative tables, its own gathered moments
-    M0 += blockIdx.y * mstr;
-    Mk += blockIdx.y * mstr;
-    l0 += blockIdx.y * lstr;
-    lk += blockIdx.y * lstr;
+    const int kern = blockIdx.z;
+    const float* D = kern ? Dk : D0;
+    const float* M = (kern ? Mk : M0) + blockIdx.y * mstr;
+    float* out = (kern ? lk : l0) + blockIdx.y * lstr;
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr unsigned CH = T * 32 * sizeof(float);  // bytes of one chunk block (multiple of 16)
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ __align__(8) unsigned long long bar[2];
-    float* Ds = (float*)dsm;            // [2][T * 32]
-    float* Ms = Ds + 2 * T * 32;        // [2][T * 32]
+    __shared__ __align__(8) unsigned long long bar;
+    float* Ds = (float*)dsm;            // [T * 32]
+    float* Ms = Ds + T * 32;            // [T * 32]; with Ds, the reduction scratch [T * 33]
     const int lane = threadIdx.x;
     const int c = blockIdx.x;
     if (c >= ncl) return;
     const int sb = soff[c], nch = (soff[c + 1] - sb) >> 5;
     if (lane == 0) {
-        mbar_init(&bar[0]);
-        mbar_init(&bar[1]);
+        mbar_init(&bar);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
-    unsigned ph0 = 0u, ph1 = 0u;  // parity of the next completion of each buffer's barrier
-    bool ok = true;
-#pragma unroll 1
-    for (int kern = 0; kern < 2; ++kern) {
-        const float* D = kern ? Dk : D0;
-        const float* M = kern ? Mk : M0;
-        float* out = kern ? lk : l0;
-        float L[T];
+    unsigned ph = 0u;  // parity of the barrier's next completion
+    float L[T];
 #pragma unroll
-        for (int i = 0; i < T; ++i) L[i] = 0.f;
-        const size_t cb = (size_t)(sb >> 5);  // first chunk of this cluster
-        if (nch > 0 && lane == 0) {
-            // order the earlier shared-memory reads and writes (generic proxy) before the copies
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect(&bar[0], 2 * CH);
-            bulk_g2s(Ds, D + cb * T * 32, CH, &bar[0]);
-            bulk_g2s(Ms, M + cb * T * 32, CH, &bar[0]);
-        }
+    for (int i = 0; i < T; ++i) L[i] = 0.f;
+    const size_t cb = (size_t)(sb >> 5);  // first chunk of this cluster
 #pragma unroll 1
-        for (int k = 0; k < nch; ++k) {
-            const int buf = k & 1;
-            if (k + 1 < nch && lane == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                const int nb = buf ^ 1;
-                mbar_expect(&bar[nb], 2 * CH);
-                bulk_g2s(Ds + nb * T * 32, D + (cb + k + 1) * T * 32, CH, &bar[nb]);
-                bulk_g2s(Ms + nb * T * 32, M + (cb + k + 1) * T * 32, CH, &bar[nb]);
-            }
-            if (!mbar_wait(&bar[buf], buf ? ph1 : ph0)) {
-                ok = false;
-                break;
-            }
-            if (buf) ph1 ^= 1u;
-            else ph0 ^= 1u;
-            M2LBody<P, 0>::run(Ds + buf * T * 32 + lane, Ms + buf * T * 32 + lane, L);
-            __syncwarp();
+    for (int k = 0; k < nch; ++k) {
+        if (lane == 0) {
+            // order the earlier shared-memory reads (generic proxy) before the copies
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect(&bar, 2 * CH);
+            bulk_g2s(Ds, D + (cb + k) * T * 32, CH, &bar);
+            bulk_g2s(Ms, M + (cb + k) * T * 32, CH, &bar);
         }
-        if (!ok) break;
-        // the buffers are free again: reuse the first one as the reduction scratch
-        m2l_flush<P, float>(L, Ds, out, c, lane);
+        if (!mbar_wait(&bar, ph)) {
+            // a copy never completed: record it, give it a bounded time to land, and stop
+            if (lane == 0) atomicExch(err, 1);
+            mbar_wait(&bar, ph);
+            return;
+        }
+        ph ^= 1u;
+        M2LBody<P, 0>::run(Ds + lane, Ms + lane, L);
+        __syncwarp();
     }
-    if (!ok) {
-        // a copy never completed: record it, give any copies in flight a bounded time to land
-        if (lane == 0) atomicExch(err, 1);
-        mbar_wait(&bar[0], ph0);
-        mbar_wait(&bar[1], ph1);
-    }
+    m2l_flush<P, float>(L, Ds, out, c, lane);
 }
 
 // FP64 (and fallback): D read from global memory, the moment chunk copied to shared memory.
@@ -855,9 +833,9 @@ static int m2l_fast_launch(pb_ctx* c, PbLevel& lv, int nr, cudaStream_t st)
         T, lv.slot_src, (const R*)lv.sig0, (const R*)lv.sigk, (R*)lv.Mg0, (R*)lv.Mgk, sstr, mstr);
     PB_LAUNCH(c);
     if constexpr (sizeof(R) == sizeof(float)) {
-        size_t smem = 4 * (size_t)T * 32 * sizeof(float);
+        size_t smem = 2 * (size_t)T * 32 * sizeof(float);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_tma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_tma<P><<<dim3(lv.ncl, nr), 32, smem, st>>>(lv.ncl, lv.slot_off, (const float*)lv.D0,
+        k_m2l_tma<P><<<dim3(lv.ncl, nr, 2), 32, smem, st>>>(lv.ncl, lv.slot_off, (const float*)lv.D0,
                                                              (const float*)lv.Dk, (const float*)lv.Mg0,
                                                              (const float*)lv.Mgk, (float*)lv.lam0, (float*)lv.lamk,
                                                              c->dev_err, mstr, sstr);
