@@ -36,6 +36,8 @@
 __constant__ int c_mi[NT_MAX];          // multi-index exponents a | b << 8 | c << 16
 __constant__ double c_fact[25];         // n!
 __constant__ double c_binom[13][13];    // C(n, k)
+__constant__ float c_ifact[NT_MAX];     // 1 / (a1! a2! a3!) of multi-index a (FP32)
+__constant__ double c_ifact64[NT_MAX];  // the same in FP64
 
 __device__ __forceinline__ void mi_unpack(int v, int& a, int& b, int& c)
 {
@@ -482,7 +484,8 @@ __global__ void k_m2l_gather(int T, const int* __restrict__ ssrc, const R* __res
     for (int b = threadIdx.x; b < T; b += blockDim.x) {
         int b1, b2, b3;
         mi_unpack(c_mi[b], b1, b2, b3);
-        scs[b] = (R)(((b1 + b2 + b3) & 1 ? -1.0 : 1.0) / (c_fact[b1] * c_fact[b2] * c_fact[b3]));
+        const R f = sizeof(R) == 4 ? (R)c_ifact[b] : (R)c_ifact64[b];
+        scs[b] = (b1 + b2 + b3) & 1 ? -f : f;
     }
     __syncthreads();
     const long long chunk = blockIdx.x;
@@ -510,7 +513,7 @@ __device__ __forceinline__ void m2l_flush(R* L, R* scratch, R* __restrict__ out,
         for (int l = 0; l < 32; ++l) s += scratch[i * 33 + l];
         int a1, a2, a3;
         mi_unpack(c_mi[i], a1, a2, a3);
-        out[(size_t)c * T + i] = s * (R)(1.0 / (c_fact[a1] * c_fact[a2] * c_fact[a3]));
+        out[(size_t)c * T + i] = s * (sizeof(R) == 4 ? (R)c_ifact[i] : (R)c_ifact64[i]);
     }
     __syncwarp();
 }
@@ -768,6 +771,15 @@ static int upload_tables(pb_ctx* c)
     PB_CUDA(c, cudaMemcpyToSymbol(c_mi, mi, sizeof(mi)));
     PB_CUDA(c, cudaMemcpyToSymbol(c_fact, f, sizeof(f)));
     PB_CUDA(c, cudaMemcpyToSymbol(c_binom, bn, sizeof(bn)));
+    float iff[NT_MAX];
+    double iff64[NT_MAX];
+    for (int k = 0; k < NT_MAX; ++k) {
+        const int a1 = mi[k] & 0xff, a2 = (mi[k] >> 8) & 0xff, a3 = mi[k] >> 16;
+        iff64[k] = 1.0 / (f[a1] * f[a2] * f[a3]);
+        iff[k] = (float)iff64[k];
+    }
+    PB_CUDA(c, cudaMemcpyToSymbol(c_ifact, iff, sizeof(iff)));
+    PB_CUDA(c, cudaMemcpyToSymbol(c_ifact64, iff64, sizeof(iff64)));
     c->tables_ready = true;
     return PB_OK;
 }
