@@ -85,12 +85,30 @@ int pb_rhs_sorted(pb_ctx* c, double* bs)
 }
 
 // ---------- energy: 1/2 sum_n q_n sum_i A_i [K1(x_n, c_i) dphi_i + K2(x_n, c_i) phi_i] ----------
+// Only K1 and K2 are needed (the charge side carries no normal). FP64: every pair in double
+// precision. Mixed: pair terms in FP32 with hi + lo coordinates on both sides, each tile of
+// charges summed in FP32 and added into FP64.
+template <class R>
+__device__ __forceinline__ void energy_k12(R dx, R dy, R dz, R nx, R ny, R nz, R e, R kp, R& K1, R& K2)
+{
+    const R i4pi = R(0.07957747154594767);
+    const R r2 = dx * dx + dy * dy + dz * dz;
+    const R rinv = PbKer<R>::rsqrt_(r2);
+    const R t = kp * (r2 * rinv);
+    R E, g;
+    pb_screen<R>(t, E, g);
+    const R e1 = R(1) + g + t * E;  // e^-t (1 + t)
+    const R ri = rinv * i4pi;
+    K1 = -E * ri;
+    K2 = (nx * dx + ny * dy + nz * dz) * ri * rinv * rinv * (e * e1 - R(1));
+}
+
 template <class R>
 __global__ void k_energy(int nt, int nc, const double4_32a* __restrict__ ep, const double4_32a* __restrict__ en,
                          const double* __restrict__ qpos, const double* __restrict__ q, double eps, double kappa,
                          const double* __restrict__ xs, double* __restrict__ part)
 {
-    __shared__ double sq[KB][4];
+    __shared__ R sh[KB][3], sl[KB][3], sq[KB];
     __shared__ double red[KB];
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     double4_32a p = make_double4_32a(0, 0, 0, 0), n = p;
@@ -101,26 +119,35 @@ __global__ void k_energy(int nt, int nc, const double4_32a* __restrict__ ep, con
         ph = xs[k];
         dph = xs[nt + k];
     }
+    const R eh[3] = {(R)p.x, (R)p.y, (R)p.z};
+    const R el[3] = {(R)(p.x - (double)eh[0]), (R)(p.y - (double)eh[1]), (R)(p.z - (double)eh[2])};
+    const R nx = (R)n.x, ny = (R)n.y, nz = (R)n.z, rph = (R)ph, rdph = (R)dph;
     double acc = 0.0;
-    const R e = (R)eps, ie = (R)(1.0 / eps), kp = (R)kappa;
+    const R e = (R)eps, kp = (R)kappa;
     for (int t0 = 0; t0 < nc; t0 += KB) {
         __syncthreads();
         if (t0 + threadIdx.x < nc) {
             int t = t0 + threadIdx.x;
-            sq[threadIdx.x][0] = qpos[3 * t];
-            sq[threadIdx.x][1] = qpos[3 * t + 1];
-            sq[threadIdx.x][2] = qpos[3 * t + 2];
-            sq[threadIdx.x][3] = q[t];
+            for (int a = 0; a < 3; ++a) {
+                const double v = qpos[3 * t + a];
+                const R hv = (R)v;
+                sh[threadIdx.x][a] = hv;
+                sl[threadIdx.x][a] = (R)(v - (double)hv);
+            }
+            sq[threadIdx.x] = (R)q[t];
         }
         __syncthreads();
         int m = min(KB, nc - t0);
         if (k < nt) {
             R s = 0;
             for (int t = 0; t < m; ++t) {
-                R K[4];
-                pb_kernels<R>((R)(sq[t][0] - p.x), (R)(sq[t][1] - p.y), (R)(sq[t][2] - p.z), R(0), R(0), R(0),
-                              (R)n.x, (R)n.y, (R)n.z, e, ie, kp, K);
-                s += (R)sq[t][3] * (K[0] * (R)dph + K[1] * (R)ph);
+                // d = x_n - c_i
+                const R dx = (sh[t][0] - eh[0]) + (sl[t][0] - el[0]);
+                const R dy = (sh[t][1] - eh[1]) + (sl[t][1] - el[1]);
+                const R dz = (sh[t][2] - eh[2]) + (sl[t][2] - el[2]);
+                R K1, K2;
+                energy_k12<R>(dx, dy, dz, nx, ny, nz, e, kp, K1, K2);
+                s += sq[t] * (K1 * rdph + K2 * rph);
             }
             acc += (double)s;
         }

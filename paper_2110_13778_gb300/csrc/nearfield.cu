@@ -19,6 +19,7 @@
 // carried as FP32 hi + lo pairs so that d = (x_hi - y_hi) + (x_lo - y_lo) keeps the
 // separation of close elements to FP32 relative accuracy instead of losing digits to the
 // size of the coordinates.
+#include <algorithm>
 #include <vector>
 
 #include "kernels.cuh"
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nchunks, const i
                                                     const int* __restrict__ nidx, const float4* __restrict__ sp,
                                                     const float4* __restrict__ sn, const float4* __restrict__ sl,
                                                     const float2* __restrict__ dens, double eps_d, double kappa_d,
-                                                    double* __restrict__ ys)
+                                                    double* __restrict__ ys, int nvalid)
 {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -296,12 +297,14 @@ __global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nchunks, const i
             acc2[r] += (double)s2[r];
         }
     }
+    // densities beyond nvalid are padding of the group (finite, unused): only nvalid are written
     if (act)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            ys[2LL * nt * r + k] = acc1[r];
-            ys[2LL * nt * r + nt + k] = acc2[r];
-        }
+        for (int r = 0; r < NR; ++r)
+            if (r < nvalid) {
+                ys[2LL * nt * r + k] = acc1[r];
+                ys[2LL * nt * r + nt + k] = acc2[r];
+            }
 }
 
 // y1 = 1/2 (1 + eps) A phi - A acc1, y2 = 1/2 (1 + 1/eps) A dphi - A acc2 (FP64)
@@ -404,19 +407,20 @@ int pb_corr_apply(pb_ctx* c, const double* xs, double* ys, int nr, const double*
 }
 
 template <int NR>
-static void near_multi_launch(pb_ctx* c, const float2* dens, double* ys, double eps)
+static void near_multi_launch(pb_ctx* c, const float2* dens, double* ys, double eps, int nvalid)
 {
     const PbLevel& lv = c->lev[c->L];
     k_near32m<NR><<<(c->nchunks * 32 + 255) / 256, 256, 0, c->st>>>(c->nt, c->nchunks, c->chunk_leaf,
                                                                      c->chunk_first, lv.begin, lv.near_off,
                                                                      lv.near_idx, c->e32p, c->e32n, c->e32l, dens, eps,
-                                                                     c->prm.kappa, ys);
+                                                                     c->prm.kappa, ys, nvalid);
 }
 
 // density buffer of the multi-vector near field (build lifetime, grown on demand)
 int pb_near_reserve(pb_ctx* c, int nr)
 {
     if (c->prm.precision != PB_MIXED || nr < 2 || nr <= c->dens_nr) return PB_OK;
+    nr = (nr + 15) / 16 * 16;  // groups read whole padded widths
     c->near_dens = (float2*)pb_alloc(c, sizeof(float2) * (size_t)c->nt * nr);
     if (!c->near_dens) return pb_fail(c, PB_ERR_NOMEM, "near field: out of memory");
     c->dens_nr = nr;
@@ -440,18 +444,20 @@ int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr)
     if (rc0) return rc0;
     k_near_dens<<<dim3((nt + 255) / 256, nr), 256, 0, c->st>>>(nt, c->e32p, xs, c->near_dens);
     PB_LAUNCH(c);
+    // groups of up to 16 right-hand sides, each one launch of the smallest width that holds it
+    // (the density buffer is padded to a multiple of 16 vectors)
     for (int r0 = 0; r0 < nr;) {
-        const int left = nr - r0;
-        const int g = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        const int v = std::min(16, nr - r0);
+        const int g = v > 8 ? 16 : v > 4 ? 8 : v > 2 ? 4 : v > 1 ? 2 : 1;
         const float2* d = c->near_dens + (size_t)nt * r0;
         double* y = ys + 2LL * nt * r0;
-        if (g == 16) near_multi_launch<16>(c, d, y, eps);
-        else if (g == 8) near_multi_launch<8>(c, d, y, eps);
-        else if (g == 4) near_multi_launch<4>(c, d, y, eps);
-        else if (g == 2) near_multi_launch<2>(c, d, y, eps);
-        else near_multi_launch<1>(c, d, y, eps);
+        if (g == 16) near_multi_launch<16>(c, d, y, eps, v);
+        else if (g == 8) near_multi_launch<8>(c, d, y, eps, v);
+        else if (g == 4) near_multi_launch<4>(c, d, y, eps, v);
+        else if (g == 2) near_multi_launch<2>(c, d, y, eps, v);
+        else near_multi_launch<1>(c, d, y, eps, v);
         PB_LAUNCH(c);
-        r0 += g;
+        r0 += v;
     }
     k_near_finish<<<dim3((nt + 255) / 256, nr), 256, 0, c->st>>>(nt, c->e64p, xs, eps, ys);
     PB_LAUNCH(c);
