@@ -91,9 +91,14 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi takes a moment to start: the timed region begins after its first sample
+            t0 = time.perf_counter()
+            while not self.samples and self.proc.poll() is None and time.perf_counter() - t0 < 3.0:
+                time.sleep(0.01)
+            self.first = len(self.samples)
         except OSError:
             self.proc = None
         return self
@@ -113,6 +118,10 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        # samples taken inside the timed region; the one just before it if the region was shorter
+        # than the sampling interval
+        inside = self.samples[getattr(self, "first", 0):]
+        self.samples = inside if inside else self.samples[-1:]
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
@@ -513,14 +522,26 @@ def run_batch(a):
 
     for _ in range(a.warmup):
         step()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
+    n0 = sum(pb.pb_get_launch_count(cx) for cx in ctxs)
+    g0 = sum(pb.pb_get_graph_launches(cx) for cx in ctxs)
     barrier(world)
-    t0 = time.perf_counter()
-    units = 0
-    for _ in range(a.steps):
-        units += step()
-    torch.cuda.synchronize()
-    dt = dist_max(time.perf_counter() - t0, world)
+    units, times = 0, []
+    with ClockSampler(local) as clk:
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            units += step()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    barrier(world)
+    dt = dist_max(sum(times), world)
+    launches = sum(pb.pb_get_launch_count(cx) for cx in ctxs) - n0
+    graph_launches = sum(pb.pb_get_graph_launches(cx) for cx in ctxs) - g0
     for cx in ctxs:
         pb.pb_destroy(cx)
     if rank == 0:
@@ -529,9 +550,11 @@ def run_batch(a):
             world * units / dt / 1e6, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if a.precision == "mixed" else "f64", "data": "synthetic",
+            "clocks": clk.summary(), "gpu_launches": launches, "graph_replays": graph_launches,
             "config": {"workload": f"{a.molecules} protein-like molecules ({[int(n) for n in sizes]} atoms, "
                                    f"{[m.nt for m in mols]} triangles) x {a.states} charge states",
                        "eta0": a.eta0, "states": a.states_mode,
+                       "l2": "flushed (256 MiB write) before each step, outside the timed events",
                        "autotune": ({"leaf_size": [t["leaf_size"] for t in tuned], "p": [t["p"] for t in tuned],
                                      "rel_err": [t["rel_err"] for t in tuned], "seconds": t_tune}
                                     if tuned else {"leaf_size": a.leaf, "p": a.p})}}))
@@ -589,7 +612,10 @@ def run_learned(a):
         info = pb.pb_gmres_solve(c, x, tol=a.tol, max_iter=500, restart=50, use_x0=learned)
         return info, pb.pb_solvation_energy(c, x)
 
+    clk = ClockSampler(local)
     for it in range(a.warmup + a.steps):
+        if it == a.warmup:
+            clk.__enter__()
         for k in arms:
             flush.fill_(it & 255)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -601,6 +627,7 @@ def run_learned(a):
             if it >= a.warmup:
                 res[k]["ms"].append(e0.elapsed_time(e1))
                 res[k]["info"], res[k]["E"] = info, E
+    clk.__exit__(None, None, None)
     for c in ctxs.values():
         pb.pb_destroy(c)
     pb.pb_mlp_destroy(net)
@@ -616,7 +643,7 @@ def run_learned(a):
         "metric": "PB solve time to 1e-6 residual (build + solve + energy), learned+mixed", "value": ms["learned_mixed"],
         "unit": "ms", "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": sum(ms.values()),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64+bf16",
-        "data": "synthetic", "arms": arms_out,
+        "data": "synthetic", "clocks": clk.summary(), "arms": arms_out,
         "speedup_vs_fp64_zero": ms["zero_fp64"] / ms["learned_mixed"],
         "speedup_vs_mixed_zero": ms["zero_mixed"] / ms["learned_mixed"],
         "training": {"molecules": int(a.train_molecules), "atoms": [int(c) for c in counts], "rows": int(F.shape[0]),

@@ -554,11 +554,14 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phas
     return false;
 }
 
-// FP32: one warp per block and per kernel (G0 for blockIdx.z = 0, Gk for 1); the chunk's D and
-// M blocks arrive by TMA bulk copy into shared memory (42 KB at p = 8, so five blocks share an
-// SM and hide each other's copies), completion on an mbarrier, every wait bounded.
+// FP32: one block of two warps per cluster and per kernel (G0 for blockIdx.z = 0, Gk for 1).
+// The chunk's D and M blocks arrive by TMA bulk copy into shared memory (42 KB at p = 8, so
+// five blocks share an SM and hide each other's copies), completion on an mbarrier, every
+// wait bounded. Warp w accumulates its half of the local coefficients (M2LWarp<P, w>: equal
+// FMA counts, moments held in registers a block at a time), so each slot costs about 740
+// shared-memory loads per kernel instead of one per FMA.
 template <int P>
-__global__ void __launch_bounds__(32, 1) k_m2l_tma(int ncl, const int* __restrict__ soff, const float* __restrict__ D0,
+__global__ void __launch_bounds__(64, 1) k_m2l_tma(int ncl, const int* __restrict__ soff, const float* __restrict__ D0,
                                                    const float* __restrict__ Dk, const float* __restrict__ M0,
                                                    const float* __restrict__ Mk, float* __restrict__ l0,
                                                    float* __restrict__ lk, int* __restrict__ err, long long mstr,
@@ -571,44 +574,62 @@ __global__ void __launch_bounds__(32, 1) k_m2l_tma(int ncl, const int* __restric
     float* out = (kern ? lk : l0) + blockIdx.y * lstr;
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr unsigned CH = T * 32 * sizeof(float);  // bytes of one chunk block (multiple of 16)
+    constexpr int NL = M2LWarp<P, 0>::n > M2LWarp<P, 1>::n ? M2LWarp<P, 0>::n : M2LWarp<P, 1>::n;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) unsigned long long bar;
     float* Ds = (float*)dsm;            // [T * 32]
     float* Ms = Ds + T * 32;            // [T * 32]; with Ds, the reduction scratch [T * 33]
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int c = blockIdx.x;
     if (c >= ncl) return;
     const int sb = soff[c], nch = (soff[c + 1] - sb) >> 5;
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
         mbar_init(&bar);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncwarp();
+    __syncthreads();
     unsigned ph = 0u;  // parity of the barrier's next completion
-    float L[T];
+    float L[NL];
 #pragma unroll
-    for (int i = 0; i < T; ++i) L[i] = 0.f;
+    for (int i = 0; i < NL; ++i) L[i] = 0.f;
     const size_t cb = (size_t)(sb >> 5);  // first chunk of this cluster
 #pragma unroll 1
     for (int k = 0; k < nch; ++k) {
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             // order the earlier shared-memory reads (generic proxy) before the copies
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_expect(&bar, 2 * CH);
             bulk_g2s(Ds, D + (cb + k) * T * 32, CH, &bar);
             bulk_g2s(Ms, M + (cb + k) * T * 32, CH, &bar);
         }
-        if (!mbar_wait(&bar, ph)) {
+        // the block agrees on the outcome, so that no thread leaves while another waits
+        if (!__syncthreads_and(mbar_wait(&bar, ph))) {
             // a copy never completed: record it, give it a bounded time to land, and stop
-            if (lane == 0) atomicExch(err, 1);
+            if (threadIdx.x == 0) atomicExch(err, 1);
             mbar_wait(&bar, ph);
             return;
         }
         ph ^= 1u;
-        M2LBody<P, 0>::run(Ds + lane, Ms + lane, L);
-        __syncwarp();
+        if (wi == 0) M2LWarp<P, 0>::run(Ds + lane, Ms + lane, L);
+        else M2LWarp<P, 1>::run(Ds + lane, Ms + lane, L);
+        __syncthreads();
     }
-    m2l_flush<P, float>(L, Ds, out, c, lane);
+    // sum over the 32 slots of each lane: the warps write their coefficients to disjoint
+    // rows of the scratch, then 64 threads add the rows and scale by 1/a!
+    float* scratch = Ds;
+    if (wi == 0) {
+#pragma unroll
+        for (int i = 0; i < M2LWarp<P, 0>::n; ++i) scratch[M2LWarp<P, 0>::alpha(i) * 33 + lane] = L[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < M2LWarp<P, 1>::n; ++i) scratch[M2LWarp<P, 1>::alpha(i) * 33 + lane] = L[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T; i += 64) {
+        float s = 0.f;
+        for (int l = 0; l < 32; ++l) s += scratch[i * 33 + l];
+        out[(size_t)c * T + i] = s * c_ifact[i];
+    }
 }
 
 // FP64 (and fallback): D read from global memory, the moment chunk copied to shared memory.
@@ -847,7 +868,7 @@ static int m2l_fast_launch(pb_ctx* c, PbLevel& lv, int nr, cudaStream_t st)
     if constexpr (sizeof(R) == sizeof(float)) {
         size_t smem = 2 * (size_t)T * 32 * sizeof(float);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_tma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_tma<P><<<dim3(lv.ncl, nr, 2), 32, smem, st>>>(lv.ncl, lv.slot_off, (const float*)lv.D0,
+        k_m2l_tma<P><<<dim3(lv.ncl, nr, 2), 64, smem, st>>>(lv.ncl, lv.slot_off, (const float*)lv.D0,
                                                              (const float*)lv.Dk, (const float*)lv.Mg0,
                                                              (const float*)lv.Mgk, (float*)lv.lam0, (float*)lv.lamk,
                                                              c->dev_err, mstr, sstr);
