@@ -115,6 +115,8 @@ struct pb_ctx {
     double pc_sum_m3 = 0;         // sum of m^3 over blocks
     int* pc_begin = nullptr;      // [npcblk + 1] first sorted element of each block
     long long* blk_off = nullptr; // [npcblk + 1] offsets into minv
+    int* pc_ids = nullptr;        // [npcblk] block indices grouped by size class (order <= 64, 128, 192)
+    int pc_cls[4] = {0, 0, 0, 0}; // first position of each class in pc_ids, and the total
     void* minv = nullptr;         // inverse blocks, working precision (float in mixed mode)
     double* dinv = nullptr;       // [4 nt] inverse 2x2 blocks for PB_PRECOND_DIAG
     // work vectors in sorted order

@@ -181,13 +181,14 @@ __global__ void __launch_bounds__(GJ_T) k_blk_gj(const int* __restrict__ begin, 
 // columns from the lane holding it by a shuffle, then applies the exchange
 //   T[p][k] <- 1/a, T[p][j] <- -T[p][j]/a, T[i][k] <- T[i][k]/a, T[i][j] -= T[i][k] T[p][j]/a.
 // After m exchanges T[p_k][k'] = (A^-1)[k][p_k'], which the final store applies.
-template <int MA, int MB>
-__global__ void __launch_bounds__(256, 1) k_blk_gj_w(const int* __restrict__ begin, const long long* __restrict__ moff,
-                                                    float* __restrict__ minv, int* __restrict__ singular)
+template <int MA, int MB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_blk_gj_w(const int* __restrict__ ids, const int* __restrict__ begin,
+                                                       const long long* __restrict__ moff, float* __restrict__ minv,
+                                                       int* __restrict__ singular)
 {
     __shared__ float colb[2][32 * MA], pivv[2];
     __shared__ int pivs[2], perm[32 * MA], inv[32 * MA];
-    const int c = blockIdx.x;
+    const int c = ids[blockIdx.x];
     const int m = 2 * (begin[c + 1] - begin[c]);
     float* g = minv + moff[c];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -361,11 +362,21 @@ static int blk_build(pb_ctx* c, const long long* dmoff, long long ntot, int mcap
                                            c->prm.kappa, M);
     PB_LAUNCH(c);
     if (sizeof(R) == 4 && mcap <= 192) {
-        if (mcap <= 128)
-            k_blk_gj_w<4, 16><<<ncl, 256, 0, c->st>>>(c->pc_begin, dmoff, (float*)M, sing);
-        else
-            k_blk_gj_w<6, 24><<<ncl, 256, 0, c->st>>>(c->pc_begin, dmoff, (float*)M, sing);
-        PB_LAUNCH(c);
+        // one launch per size class, each with a register tile that just covers its blocks
+        const int* ids = c->pc_ids;
+        const int* cl = c->pc_cls;
+        if (cl[1] > cl[0]) {
+            k_blk_gj_w<2, 8, 4><<<cl[1] - cl[0], 256, 0, c->st>>>(ids + cl[0], c->pc_begin, dmoff, (float*)M, sing);
+            PB_LAUNCH(c);
+        }
+        if (cl[2] > cl[1]) {
+            k_blk_gj_w<4, 16, 2><<<cl[2] - cl[1], 256, 0, c->st>>>(ids + cl[1], c->pc_begin, dmoff, (float*)M, sing);
+            PB_LAUNCH(c);
+        }
+        if (cl[3] > cl[2]) {
+            k_blk_gj_w<6, 24, 1><<<cl[3] - cl[2], 256, 0, c->st>>>(ids + cl[2], c->pc_begin, dmoff, (float*)M, sing);
+            PB_LAUNCH(c);
+        }
         int hs = 0;
         PB_CUDA(c, cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, c->st));
         PB_CUDA(c, cudaStreamSynchronize(c->st));
@@ -426,11 +437,25 @@ int pb_precond_plan(pb_ctx* c)
         const double m = 2.0 * (pb_[k + 1] - pb_[k]);
         c->pc_sum_m3 += m * m * m;
     }
+    // size classes of the FP32 register-tile inversion: order <= 64, <= 128, larger
+    std::vector<int> ids;
+    ids.reserve(nb);
+    const int lim[3] = {64, 128, 1 << 30};
+    for (int q = 0; q < 3; ++q) {
+        c->pc_cls[q] = (int)ids.size();
+        for (int k = 0; k < nb; ++k) {
+            const int m = 2 * (pb_[k + 1] - pb_[k]);
+            if (m <= lim[q] && (q == 0 || m > lim[q - 1])) ids.push_back(k);
+        }
+    }
+    c->pc_cls[3] = (int)ids.size();
     c->pc_begin = (int*)pb_alloc(c, sizeof(int) * (nb + 1));
     c->blk_off = (long long*)pb_alloc(c, sizeof(long long) * (nb + 1));
-    if (!c->blk_off || !c->pc_begin) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
+    c->pc_ids = (int*)pb_alloc(c, sizeof(int) * (nb + 1));
+    if (!c->blk_off || !c->pc_begin || !c->pc_ids) return pb_fail(c, PB_ERR_NOMEM, "precond: out of memory");
     PB_CUDA(c, cudaMemcpyAsync(c->pc_begin, pb_.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, c->st));
     PB_CUDA(c, cudaMemcpyAsync(c->blk_off, moff.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(c->pc_ids, ids.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->st));
     c->pc_total = moff[nb];
     PB_CUDA(c, cudaStreamSynchronize(c->st));  // the host vectors go out of scope
     return PB_OK;
