@@ -353,10 +353,11 @@ int pb_near_setup(pb_ctx* c)
 {
     if (c->prm.precision != PB_MIXED) return PB_OK;
     const PbLevel& lv = c->lev[c->L];
-    std::vector<int> b(lv.ncl + 1);
-    PB_CUDA(c, cudaMemcpyAsync(b.data(), lv.begin, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost, c->st));
-    PB_CUDA(c, cudaStreamSynchronize(c->st));
-    std::vector<int> cl, cf;
+    const std::vector<int>& b = c->h_leaf_begin;  // the leaf ranges, read back by the tree build
+    std::vector<int>& cl = c->h_up_i[0];
+    std::vector<int>& cf = c->h_up_i[1];
+    cl.clear();
+    cf.clear();
     for (int k = 0; k < lv.ncl; ++k)
         for (int s = b[k]; s < b[k + 1]; s += 32) {
             cl.push_back(k);
@@ -371,7 +372,6 @@ int pb_near_setup(pb_ctx* c)
         return pb_fail(c, PB_ERR_NOMEM, "near setup: out of memory");
     PB_CUDA(c, cudaMemcpyAsync(c->chunk_leaf, cl.data(), sizeof(int) * cl.size(), cudaMemcpyHostToDevice, c->st));
     PB_CUDA(c, cudaMemcpyAsync(c->chunk_first, cf.data(), sizeof(int) * cf.size(), cudaMemcpyHostToDevice, c->st));
-    PB_CUDA(c, cudaStreamSynchronize(c->st));
     return PB_OK;
 }
 

@@ -45,6 +45,9 @@ static void pb_free_build(pb_ctx* c)
     for (void* p : c->build_allocs) cudaFreeAsync(p, c->st);
     c->build_allocs.clear();
     c->built = false;
+    c->touch_class_dev = nullptr;
+    c->canon_check = nullptr;
+    c->canon_expect = 0;
     c->gm_m = 0;
     c->scratch = nullptr;
     pb_drop_graphs(c);
@@ -245,7 +248,12 @@ extern "C" int pb_build_tree(pb_ctx* c)
     c->ys = (double*)pb_alloc(c, sizeof(double) * n2);
     c->ws = (double*)pb_alloc(c, sizeof(double) * n2);
     if (!c->xs || !c->ys || !c->ws) return pb_fail(c, PB_ERR_NOMEM, "build_tree: out of memory");
+    int ncanon = c->canon_expect;
+    if (c->canon_check) PB_CUDA(c, cudaMemcpyAsync(&ncanon, c->canon_check, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     PB_CUDA(c, cudaStreamSynchronize(c->st));
+    if (ncanon != c->canon_expect)
+        return pb_fail(c, PB_ERR_MESH, "touching pairs are not symmetric (%d unordered pairs, %d expected)", ncanon,
+                       c->canon_expect);
     c->built = true;
     return PB_OK;
 }
@@ -526,6 +534,13 @@ extern "C" int pb_get_tree_stats(pb_ctx* c, pb_tree_stats* s)
     }
     s->near_pairs = c->near_pairs;
     s->touching = c->ntouch;
+    if (c->touch_class_dev) {
+        unsigned long long h[4];
+        PB_CUDA(c, cudaMemcpyAsync(h, c->touch_class_dev, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+        PB_CUDA(c, cudaStreamSynchronize(c->st));
+        for (int q = 0; q < 4; ++q) c->touch_class[q] = (long long)h[q];
+        c->touch_class_dev = nullptr;
+    }
     for (int q = 0; q < 4; ++q) s->touch_class[q] = c->touch_class[q];
     s->max_leaf = c->max_leaf;
     if (c->prm.precond == PB_PRECOND_BLOCK) {

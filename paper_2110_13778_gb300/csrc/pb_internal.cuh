@@ -106,7 +106,17 @@ struct pb_ctx {
     double* corr = nullptr;   // [4 * ntouch] exact integral minus one-point rule (I1..I4)
     long long ntouch = 0;
     long long touch_class[4] = {0, 0, 0, 0};  // ordered pairs sharing 0..3 vertices
+    unsigned long long* touch_class_dev = nullptr;  // the same on the device, read when reported
+    const int* canon_check = nullptr;  // device count of unordered touching pairs, checked at the end of a build
+    int canon_expect = 0;
     long long near_pairs = 0;
+    // host copies made by the build: the leaf ranges (read back once by the tree build), and
+    // the sources of the build's host-to-device uploads, kept until the next build so that
+    // those copies need no synchronisation
+    std::vector<int> h_leaf_begin, h_up_i[4];
+    std::vector<long long> h_up_l;
+    std::vector<double> h_up_d;
+    std::vector<float2> h_up_f2;
     // preconditioner: per leaf a dense (2n x 2n) inverse, unknowns [phi of leaf; dphi of leaf]
     int far_nr = 1;               // right-hand sides the far-field work arrays hold
     int npcblk = 0;               // preconditioner blocks

@@ -398,8 +398,7 @@ static int blk_build(pb_ctx* c, const long long* dmoff, long long ntot, int mcap
     return PB_OK;
 }
 
-// The block partition, from the leaf ranges read back to the host (synchronises; before the
-// singular integrals are queued, so that this read-back does not wait for them).
+// The block partition, from the leaf ranges the tree build read back to the host.
 int pb_precond_plan(pb_ctx* c)
 {
     const int nt = c->nt;
@@ -407,10 +406,9 @@ int pb_precond_plan(pb_ctx* c)
     // blocks: the leaves of the tree; a leaf with more than PB_PC_BMAX elements is split into
     // nearly equal consecutive (Morton-ordered) parts of at most PB_PC_BMAX elements
     const PbLevel& lv = c->lev[c->L];
-    std::vector<int> hb(lv.ncl + 1);
-    PB_CUDA(c, cudaMemcpyAsync(hb.data(), lv.begin, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost, c->st));
-    PB_CUDA(c, cudaStreamSynchronize(c->st));
-    std::vector<int> pb_;
+    const std::vector<int>& hb = c->h_leaf_begin;
+    std::vector<int>& pb_ = c->h_up_i[2];
+    pb_.clear();
     for (int k = 0; k < lv.ncl; ++k) {
         int n = hb[k + 1] - hb[k];
         int parts = (n + PB_PC_BMAX - 1) / PB_PC_BMAX;
@@ -422,7 +420,8 @@ int pb_precond_plan(pb_ctx* c)
     }
     pb_.push_back(nt);
     const int nb = (int)pb_.size() - 1;
-    std::vector<long long> moff(nb + 1);
+    std::vector<long long>& moff = c->h_up_l;
+    moff.assign(nb + 1, 0);
     moff[0] = 0;
     int mcap = 0;
     for (int k = 0; k < nb; ++k) {
@@ -438,8 +437,8 @@ int pb_precond_plan(pb_ctx* c)
         c->pc_sum_m3 += m * m * m;
     }
     // size classes of the FP32 register-tile inversion: order <= 64, <= 128, larger
-    std::vector<int> ids;
-    ids.reserve(nb);
+    std::vector<int>& ids = c->h_up_i[3];
+    ids.clear();
     const int lim[3] = {64, 128, 1 << 30};
     for (int q = 0; q < 3; ++q) {
         c->pc_cls[q] = (int)ids.size();
@@ -457,7 +456,6 @@ int pb_precond_plan(pb_ctx* c)
     PB_CUDA(c, cudaMemcpyAsync(c->blk_off, moff.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice, c->st));
     PB_CUDA(c, cudaMemcpyAsync(c->pc_ids, ids.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->st));
     c->pc_total = moff[nb];
-    PB_CUDA(c, cudaStreamSynchronize(c->st));  // the host vectors go out of scope
     return PB_OK;
 }
 

@@ -514,14 +514,14 @@ __device__ __forceinline__ void ss_points_ff(int lane, const float2* __restrict_
 template <int PASS>
 __global__ void k_canon(int nt, const int* __restrict__ toff, const int* __restrict__ tj,
                         const int* __restrict__ order, int* __restrict__ cnt, const int* __restrict__ coff,
-                        int* __restrict__ ck, int* __restrict__ cp)
+                        int* __restrict__ ck, int* __restrict__ cp, int cap)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nt) return;
     int n = PASS ? coff[k] : 0;
     for (int t = toff[k]; t < toff[k + 1]; ++t)
         if (order[k] <= order[tj[t]]) {
-            if (PASS) {
+            if (PASS && n < cap) {  // cap: the pairs allocated (a mismatch fails the build)
                 ck[n] = k;
                 cp[n] = t;
             }
@@ -530,7 +530,8 @@ __global__ void k_canon(int nt, const int* __restrict__ toff, const int* __restr
     if (!PASS) cnt[k] = n;
 }
 
-__global__ void __launch_bounds__(256) k_singular_ff(int ncanon, const int* __restrict__ ck,
+__global__ void __launch_bounds__(256) k_singular_ff(int ncanon, const int* __restrict__ ncanon_dev,
+                                                     const int* __restrict__ ck,
                                                      const int* __restrict__ cp, const int* __restrict__ toff,
                                                      const int* __restrict__ tj, const int* __restrict__ stris,
                                                      const float2* __restrict__ erec, const float2* __restrict__ tab,
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(256) k_singular_ff(int ncanon, const int* __re
 {
     const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
-    if (w >= ncanon) return;
+    if (w >= ncanon || w >= *ncanon_dev) return;  // allocated pairs, and those the scan found
     const int k = ck[w];
     const long long pair = cp[w];
     const int j = tj[pair];
@@ -686,21 +687,22 @@ int pb_touching_and_singular(pb_ctx* c)
     k_touch<1><<<nblk(nt, 128), 128, 0, c->st>>>(nt, c->stris, voff, vlist, nullptr, c->touch_off, c->touch_j, bad);
     PB_LAUNCH(c);
     {
-        // ordered touching pairs by number of shared vertices (for the work counts of reports)
+        // ordered touching pairs by number of shared vertices (for the work counts of reports;
+        // left on the device until they are asked for)
         unsigned long long* cls = (unsigned long long*)pb_alloc(c, sizeof(unsigned long long) * 4);
         if (!cls) return pb_fail(c, PB_ERR_NOMEM, "touching: out of memory");
         k_touch_classes<<<nblk(nt, 128), 128, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->stris, cls);
         PB_LAUNCH(c);
-        unsigned long long h[4];
-        PB_CUDA(c, cudaMemcpyAsync(h, cls, sizeof(h), cudaMemcpyDeviceToHost, c->st));
-        PB_CUDA(c, cudaStreamSynchronize(c->st));
-        for (int q = 0; q < 4; ++q) c->touch_class[q] = (long long)h[q];
+        c->touch_class_dev = cls;  // read back by pb_get_tree_stats
     }
     // Gauss-Legendre rule of the 4-cube
     double gx[8] = {0}, gw[8] = {0};
     gauss01(c->prm.qs, gx, gw);
-    PB_CUDA(c, cudaMemcpyToSymbolAsync(c_gx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, c->st));
-    PB_CUDA(c, cudaMemcpyToSymbolAsync(c_gw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, c->st));
+    // (upload sources live in the context until the next build: no synchronisation needed)
+    c->h_up_d.assign(gx, gx + 8);
+    c->h_up_d.insert(c->h_up_d.end(), gw, gw + 8);
+    PB_CUDA(c, cudaMemcpyToSymbolAsync(c_gx, c->h_up_d.data(), sizeof(gx), 0, cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyToSymbolAsync(c_gw, c->h_up_d.data() + 8, sizeof(gw), 0, cudaMemcpyHostToDevice, c->st));
     double eps = c->prm.eps_out / c->prm.eps_in;
     const int mode = c->prm.singular ? c->prm.singular : (c->prm.precision == PB_MIXED ? PB_SINGULAR_FF : PB_SINGULAR_FP64);
     if (mode == PB_SINGULAR_FP64) {
@@ -714,7 +716,9 @@ int pb_touching_and_singular(pb_ctx* c)
     float2* tab = (float2*)pb_alloc(c, sizeof(float2) * T.rec.size());
     float2* erec = (float2*)pb_alloc(c, sizeof(float2) * FF_ESLOTS * (size_t)nt);
     if (!tab || !erec) return pb_fail(c, PB_ERR_NOMEM, "singular: out of memory");
-    PB_CUDA(c, cudaMemcpyAsync(tab, T.rec.data(), sizeof(float2) * T.rec.size(), cudaMemcpyHostToDevice, c->st));
+    c->h_up_f2.swap(T.rec);
+    PB_CUDA(c, cudaMemcpyAsync(tab, c->h_up_f2.data(), sizeof(float2) * c->h_up_f2.size(), cudaMemcpyHostToDevice,
+                               c->st));
     k_elem_ff<<<nblk(nt, B), B, 0, c->st>>>(nt, c->stris, c->verts, c->e64p, c->e64n, erec);
     PB_LAUNCH(c);
     // unordered pairs
@@ -722,7 +726,8 @@ int pb_touching_and_singular(pb_ctx* c)
     int* coff = (int*)pb_alloc(c, sizeof(int) * (nt + 1));
     if (!ccnt || !coff) return pb_fail(c, PB_ERR_NOMEM, "singular: out of memory");
     PB_CUDA(c, cudaMemsetAsync(ccnt + nt, 0, sizeof(int), c->st));
-    k_canon<0><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, ccnt, nullptr, nullptr, nullptr);
+    k_canon<0><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, ccnt, nullptr, nullptr, nullptr,
+                                             0);
     PB_LAUNCH(c);
     {
         size_t ctmp = 0;
@@ -733,20 +738,22 @@ int pb_touching_and_singular(pb_ctx* c)
         PB_LAUNCH(c);
         PB_CUDA(c, cudaFreeAsync(cbuf, c->st));
     }
-    int ncanon = 0;
-    PB_CUDA(c, cudaMemcpyAsync(&ncanon, coff + nt, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    // Touching is symmetric and every triangle touches itself, so the unordered pairs number
+    // (ordered pairs + nt) / 2; the kernel takes the count from the scan (coff[nt]) and the
+    // build checks the two agree when it synchronises at its end.
+    const int ncanon = (int)((htot + (long long)nt) / 2);
+    c->canon_check = coff + nt;
+    c->canon_expect = ncanon;
     int* ck = (int*)pb_alloc(c, sizeof(int) * (ncanon + 1));
     int* cp = (int*)pb_alloc(c, sizeof(int) * (ncanon + 1));
     if (!ck || !cp) return pb_fail(c, PB_ERR_NOMEM, "singular: out of memory");
-    k_canon<1><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, nullptr, coff, ck, cp);
+    k_canon<1><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, nullptr, coff, ck, cp, ncanon);
     PB_LAUNCH(c);
-    k_singular_ff<<<nblk(ncanon, 8), 256, 0, c->st>>>(ncanon, ck, cp, c->touch_off, c->touch_j, c->stris, erec, tab,
+    k_singular_ff<<<nblk(ncanon, 8), 256, 0, c->st>>>(ncanon, coff + nt, ck, cp, c->touch_off, c->touch_j, c->stris, erec, tab,
                                                     T.n, make_int3(T.off[0], T.off[1], T.off[2]),
                                                     make_int3(T.cnt[0], T.cnt[1], T.cnt[2]), ff_from(c->prm.kappa),
                                                     ff_from(eps), ff_from(1.0 / eps), c->corr);
     PB_LAUNCH(c);
-    // (the table's upload was queued before the synchronisation that read ncanon, so the host
-    // copy may go out of scope now; the singular pass itself is left running)
+    // (the singular pass is left running)
     return PB_OK;
 }

@@ -272,8 +272,8 @@ __global__ void k_sorted_elems(int nt, const int* __restrict__ order, const doub
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
-// exclusive scan of cnt[0..n) into off[0..n], off[n] = total; returns the total
-static int scan_counts(pb_ctx* c, const int* cnt, int* off, int n, long long* total)
+// exclusive scan of cnt[0..n) into off[0..n], off[n] = total (queued, no read-back)
+static int scan_only(pb_ctx* c, const int* cnt, int* off, int n)
 {
     size_t tmp = 0;
     cub::DeviceScan::ExclusiveSum(nullptr, tmp, cnt, off, n + 1, c->st);
@@ -282,10 +282,6 @@ static int scan_counts(pb_ctx* c, const int* cnt, int* off, int n, long long* to
     cub::DeviceScan::ExclusiveSum(t, tmp, cnt, off, n + 1, c->st);
     PB_LAUNCH(c);
     PB_CUDA(c, cudaFreeAsync(t, c->st));
-    int h = 0;
-    PB_CUDA(c, cudaMemcpyAsync(&h, off + n, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    PB_CUDA(c, cudaStreamSynchronize(c->st));
-    *total = h;
     return PB_OK;
 }
 
@@ -365,9 +361,12 @@ int pb_geometry_and_tree(pb_ctx* c)
     c->L = L;
 
     // clusters of each level
+    // (the cluster counts are known from the level counts, so the scans are not read back
+    // one by one: each level's total is kept on the device and all are checked at once)
     int* flag = (int*)pb_alloc(c, sizeof(int) * (nt + 1));
     int* pos = (int*)pb_alloc(c, sizeof(int) * (nt + 1));
-    if (!flag || !pos) return pb_fail(c, PB_ERR_NOMEM, "levels: out of memory");
+    int* tots = (int*)pb_alloc(c, sizeof(int) * (PB_MAXL + 1));
+    if (!flag || !pos || !tots) return pb_fail(c, PB_ERR_NOMEM, "levels: out of memory");
     for (int l = 0; l <= L; ++l) {
         PbLevel& lv = c->lev[l];
         lv.ncl = hc[l];
@@ -382,10 +381,9 @@ int pb_geometry_and_tree(pb_ctx* c)
             return pb_fail(c, PB_ERR_NOMEM, "levels: out of memory");
         k_flags<<<nblk(nt, B), B, 0, c->st>>>(nt, skeys, 3 * (PB_MAXL - l), flag);
         PB_LAUNCH(c);
-        long long tot = 0;
-        int rc = scan_counts(c, flag, pos, nt, &tot);
+        int rc = scan_only(c, flag, pos, nt);
         if (rc) return rc;
-        if (tot != lv.ncl) return pb_fail(c, PB_ERR_CUDA, "level %d: cluster count mismatch", l);
+        PB_CUDA(c, cudaMemcpyAsync(tots + l, pos + nt, sizeof(int), cudaMemcpyDeviceToDevice, c->st));
         k_compact_starts<<<nblk(nt, B), B, 0, c->st>>>(nt, flag, pos, lv.begin, lv.ncl);
         PB_LAUNCH(c);
         if (l > 0) {
@@ -430,7 +428,11 @@ int pb_geometry_and_tree(pb_ctx* c)
         PB_CUDA(c, cudaMemsetAsync(r.near_idx, 0, sizeof(int), c->st));
         r.nnear = 1;
         r.ninter = 0;
+        int ht[PB_MAXL + 1];
+        PB_CUDA(c, cudaMemcpyAsync(ht, tots, sizeof(int) * (L + 1), cudaMemcpyDeviceToHost, c->st));
         PB_CUDA(c, cudaStreamSynchronize(c->st));
+        for (int l = 0; l <= L; ++l)
+            if (ht[l] != c->lev[l].ncl) return pb_fail(c, PB_ERR_CUDA, "level %d: cluster count mismatch", l);
     }
     volatile double e2 = c->prm.eta0 * c->prm.eta0;
     for (int l = 1; l <= L; ++l) {
@@ -443,10 +445,18 @@ int pb_geometry_and_tree(pb_ctx* c)
                                                           lv.xc, lv.rho, e2, ncnt, icnt, nullptr, nullptr,
                                                           nullptr, nullptr);
         PB_LAUNCH(c);
-        int rc = scan_counts(c, ncnt, lv.near_off, lv.ncl, &lv.nnear);
+        int rc = scan_only(c, ncnt, lv.near_off, lv.ncl);
         if (rc) return rc;
-        rc = scan_counts(c, icnt, lv.int_off, lv.ncl, &lv.ninter);
+        rc = scan_only(c, icnt, lv.int_off, lv.ncl);
         if (rc) return rc;
+        // both list lengths with one read-back
+        PB_CUDA(c, cudaMemcpyAsync(tots, lv.near_off + lv.ncl, sizeof(int), cudaMemcpyDeviceToDevice, c->st));
+        PB_CUDA(c, cudaMemcpyAsync(tots + 1, lv.int_off + lv.ncl, sizeof(int), cudaMemcpyDeviceToDevice, c->st));
+        int hn[2];
+        PB_CUDA(c, cudaMemcpyAsync(hn, tots, sizeof(hn), cudaMemcpyDeviceToHost, c->st));
+        PB_CUDA(c, cudaStreamSynchronize(c->st));
+        lv.nnear = hn[0];
+        lv.ninter = hn[1];
         lv.near_idx = (int*)pb_alloc(c, sizeof(int) * (lv.nnear + 1));
         lv.int_idx = (int*)pb_alloc(c, sizeof(int) * (lv.ninter + 1));
         if (!lv.near_idx || !lv.int_idx) return pb_fail(c, PB_ERR_NOMEM, "lists: out of memory");
@@ -489,6 +499,7 @@ int pb_geometry_and_tree(pb_ctx* c)
         }
         c->max_leaf = mx;
         c->near_pairs = np;
+        c->h_leaf_begin.swap(b);
     }
     return PB_OK;
 }
