@@ -78,7 +78,7 @@ typedef struct pb_ctx pb_ctx;
 
 typedef struct pb_solve_info {
     int iterations;      /* Arnoldi steps taken (= matrix-vector products after the first) */
-    int matvecs;         /* matrix-vector products, including residual evaluations */
+    int matvecs;         /* matrix-vector products, including residual evaluations (none for a zero start) */
     double rel_residual; /* final ||b - A x|| / ||b||, recomputed with a true product */
     int status;          /* PB_OK, PB_ERR_NOT_CONVERGED or PB_ERR_NONFINITE */
     double initial_residual; /* ||b - A x0|| / ||b|| of the start (1 for a zero start) */

@@ -334,7 +334,7 @@ __global__ void k_gm_solve(int m, int k, GmState s)
 static int grid_for(long long n) { return (int)std::min<long long>((n + KB - 1) / KB, 4 * 152 * 4); }
 
 int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max_iter, int restart,
-                    pb_solve_info* info)
+                    pb_solve_info* info, bool x_zero)
 {
     const long long n = 2LL * c->nt;
     const int m = restart;
@@ -379,10 +379,15 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
     int it = 0;
     double rel = 1.0;
     bool done = false, converged = false;
+    bool first = true;
     while (!done) {
-        // r0 = b - A x ; V0 = r0 / ||r0||
-        if ((rc = pb_matvec_sorted(c, xs, w, 0))) return rc;
-        inf.matvecs++;
+        // r0 = b - A x ; V0 = r0 / ||r0||  (A x = 0 for a start the caller zeroed)
+        if (first && x_zero) {
+            PB_CUDA(c, cudaMemsetAsync(w, 0, sizeof(double) * n, c->st));
+        } else {
+            if ((rc = pb_matvec_sorted(c, xs, w, 0))) return rc;
+            inf.matvecs++;
+        }
         k_residual<<<G, KB, 0, c->st>>>(n, bs, w);
         PB_LAUNCH(c);
         k_multidot<<<dim3(DOT_BLOCKS, 1), KB, 0, c->st>>>(n, nullptr, w, part);
@@ -396,7 +401,8 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
         PB_CUDA(c, cudaMemcpyAsync(c->hscal, s.res, sizeof(double), cudaMemcpyDeviceToHost, c->st));
         PB_CUDA(c, cudaStreamSynchronize(c->st));
         rel = c->hscal[0] / bnorm;
-        if (inf.matvecs == 1) inf.initial_residual = rel;
+        if (first) inf.initial_residual = rel;
+        first = false;
         if (!isfinite(rel)) {
             inf.status = PB_ERR_NONFINITE;
             break;

@@ -435,7 +435,7 @@ extern "C" int pb_gmres_solve(pb_ctx* c, double* x, double tol, int max_iter, in
         PB_CUDA(c, cudaMemsetAsync(c->xs, 0, sizeof(double) * 2 * c->nt, c->st));
     }
     pb_solve_info loc;
-    if ((rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc)) &&
+    if ((rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc, !use_x0)) &&
         rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE && rc != PB_ERR_TIMEOUT)
         return rc;
     int rc2 = pb_scatter(c, c->xs, x);
@@ -465,7 +465,7 @@ extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, 
         if ((rc = pb_rhs_sorted(c, c->ws))) return rc;
         if (!(warm && s > 0)) PB_CUDA(c, cudaMemsetAsync(c->xs, 0, sizeof(double) * n2, c->st));
         pb_solve_info loc;
-        rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc);
+        rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc, !(warm && s > 0));
         if (rc && rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE && rc != PB_ERR_TIMEOUT) return rc;
         if (rc && worst == PB_OK) worst = rc;
         if (infos) infos[s] = loc;

@@ -225,7 +225,7 @@ int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double 
 int pb_rhs_sorted(pb_ctx* c, double* bs);                          // krylov.cu
 int pb_energy_sorted(pb_ctx* c, const double* xs, double* E);      // krylov.cu
 int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max_iter,
-                    int restart, pb_solve_info* info);              // krylov.cu
+                    int restart, pb_solve_info* info, bool x_zero);  // krylov.cu (x_zero: xs is zero)
 int pb_matvec_sorted(pb_ctx* c, const double* xs, double* ys, int which);  // pb_api.cu
 int pb_gather(pb_ctx* c, const double* x, double* xs);   // element -> sorted order
 int pb_scatter(pb_ctx* c, const double* xs, double* x);  // sorted -> element order
