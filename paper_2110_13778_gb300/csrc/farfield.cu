@@ -807,18 +807,21 @@ static int upload_tables(pb_ctx* c)
 
 static bool m2l_fast_order(int p) { return p == 4 || p == 6 || p == 8; }
 
-// interaction lists padded to multiples of 32 slots, then the derivative tensors per slot
-static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
+// interaction lists padded to multiples of 32 slots (host work and uploads; no kernels)
+static int m2l_fast_plan(pb_ctx* c, PbLevel& lv)
 {
     cudaStream_t fs = c->st2;  // the whole far-field setup runs on the second stream
     std::vector<int> off(lv.ncl + 1), idx(lv.ninter);
     PB_CUDA(c, cudaMemcpyAsync(off.data(), lv.int_off, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToHost, fs));
     PB_CUDA(c, cudaMemcpyAsync(idx.data(), lv.int_idx, sizeof(int) * lv.ninter, cudaMemcpyDeviceToHost, fs));
     PB_CUDA(c, cudaStreamSynchronize(fs));
-    std::vector<int> soff(lv.ncl + 1);
-    soff[0] = 0;
+    std::vector<int>& soff = lv.h_slot[0];
+    std::vector<int>& ssrc = lv.h_slot[1];
+    std::vector<int>& stgt = lv.h_slot[2];
+    soff.assign(lv.ncl + 1, 0);
     for (int k = 0; k < lv.ncl; ++k) soff[k + 1] = soff[k] + ((off[k + 1] - off[k] + 31) / 32) * 32;
-    std::vector<int> ssrc(soff[lv.ncl], -1), stgt(soff[lv.ncl]);
+    ssrc.assign(soff[lv.ncl], -1);
+    stgt.assign(soff[lv.ncl], 0);
     for (int k = 0; k < lv.ncl; ++k) {
         for (int t = off[k]; t < off[k + 1]; ++t) ssrc[soff[k] + (t - off[k])] = idx[t];
         for (int t = soff[k]; t < soff[k + 1]; ++t) stgt[t] = k;
@@ -828,29 +831,35 @@ static int m2l_fast_setup(pb_ctx* c, PbLevel& lv)
     size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
     lv.slot_off = (int*)pb_alloc_on(c, sizeof(int) * (lv.ncl + 1), fs);
     lv.slot_src = (int*)pb_alloc_on(c, sizeof(int) * (lv.nslots + 1), fs);
+    lv.slot_tgt = (int*)pb_alloc_on(c, sizeof(int) * (lv.nslots + 1), fs);
     lv.D0 = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
     lv.Dk = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
     lv.Mg0 = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
     lv.Mgk = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
-    if (!lv.slot_off || !lv.slot_src || !lv.D0 || !lv.Dk || !lv.Mg0 || !lv.Mgk)
+    if (!lv.slot_off || !lv.slot_src || !lv.slot_tgt || !lv.D0 || !lv.Dk || !lv.Mg0 || !lv.Mgk)
         return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
+    // (the host vectors live in the level until the next build, so no synchronisation)
     PB_CUDA(c, cudaMemcpyAsync(lv.slot_off, soff.data(), sizeof(int) * (lv.ncl + 1), cudaMemcpyHostToDevice, fs));
     PB_CUDA(c, cudaMemcpyAsync(lv.slot_src, ssrc.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, fs));
-    int* stg = (int*)pb_alloc_on(c, sizeof(int) * (lv.nslots + 1), fs);
-    if (!stg) return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
-    PB_CUDA(c, cudaMemcpyAsync(stg, stgt.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, fs));
-    // host vectors above are read by the queued copies: wait before they go out of scope
-    PB_CUDA(c, cudaStreamSynchronize(fs));
+    PB_CUDA(c, cudaMemcpyAsync(lv.slot_tgt, stgt.data(), sizeof(int) * lv.nslots, cudaMemcpyHostToDevice, fs));
+    return PB_OK;
+}
+
+// the derivative tensors per slot
+static int m2l_fast_tables(pb_ctx* c, PbLevel& lv)
+{
+    cudaStream_t fs = c->st2;
+    const int T = pb_nterms(lv.p);
     const size_t smem = sizeof(double) * 3 * (size_t)T * 8;
     const unsigned nb = (unsigned)((lv.nslots + 7) / 8);
-    if (nb == 0) {
-    } else if (c->prm.precision == PB_MIXED) {
+    if (nb == 0) return PB_OK;
+    if (c->prm.precision == PB_MIXED) {
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_setup_ff<<<nb, 256, smem, fs>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
+        k_m2l_setup_ff<<<nb, 256, smem, fs>>>(lv.nslots, lv.p, c->prm.kappa, lv.slot_tgt, lv.slot_src, lv.xc,
                                                   (float*)lv.D0, (float*)lv.Dk);
     } else {
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_setup<double><<<nb, 256, smem, fs>>>(lv.nslots, lv.p, c->prm.kappa, stg, lv.slot_src, lv.xc,
+        k_m2l_setup<double><<<nb, 256, smem, fs>>>(lv.nslots, lv.p, c->prm.kappa, lv.slot_tgt, lv.slot_src, lv.xc,
                                                        (double*)lv.D0, (double*)lv.Dk);
     }
     PB_LAUNCH(c);
@@ -909,7 +918,7 @@ int pb_far_reserve(pb_ctx* c, int nr)
 int pb_far_setup(pb_ctx* c)
 {
     c->far_nr = 1;
-    // on the second stream, after the tree (ev_tree) and concurrently with the singular pass
+    // on the second stream, after the tree (ev_tree); the host work overlaps the singular pass
     cudaStream_t fs = c->st2;
     PB_CUDA(c, cudaStreamWaitEvent(fs, c->ev_tree, 0));
     // the constant tables never change: uploaded by the first build of a context (a blocking
@@ -926,11 +935,21 @@ int pb_far_setup(pb_ctx* c)
         lv.lamk = pb_alloc_on(c, rs * n, fs);
         if (!lv.sig0 || !lv.sigk || !lv.lam0 || !lv.lamk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");
         if (lv.ninter > 0 && m2l_fast_order(lv.p)) {
-            int rc2 = m2l_fast_setup(c, lv);
+            int rc2 = m2l_fast_plan(c, lv);
             if (rc2) return rc2;
         }
     }
-    // the MtL table kernels of all levels ran on the second stream
+    // The table kernels wait for the singular pass: long-lived singular blocks would otherwise
+    // hold every SM slot while these kernels queue for them. Afterwards they run beside the
+    // preconditioner's factorisation.
+    PB_CUDA(c, cudaStreamWaitEvent(fs, c->ev_sing, 0));
+    for (int l = 1; l <= c->L; ++l) {
+        PbLevel& lv = c->lev[l];
+        if (lv.ninter > 0 && m2l_fast_order(lv.p)) {
+            int rc2 = m2l_fast_tables(c, lv);
+            if (rc2) return rc2;
+        }
+    }
     PB_CUDA(c, cudaEventRecord(c->ev_join, c->st2));
     return PB_OK;
 }

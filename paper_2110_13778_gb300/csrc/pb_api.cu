@@ -117,6 +117,7 @@ extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_tree, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_sing, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         pb_destroy(c);
@@ -139,6 +140,7 @@ extern "C" int pb_destroy(pb_ctx* c)
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_tree) cudaEventDestroy(c->ev_tree);
+    if (c->ev_sing) cudaEventDestroy(c->ev_sing);
     pb_drop_graphs(c);
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
     if (c->pool) cudaMemPoolDestroy(c->pool);
@@ -227,15 +229,17 @@ extern "C" int pb_build_tree(pb_ctx* c)
     if ((rc = pb_geometry_and_tree(c))) return rc;
     pb_toc(c, PB_T_TREE);
     // Everything that reads tree data back to the host is planned first; then the singular
-    // integrals run on the first stream while the far-field setup (host work and table
-    // kernels) proceeds on the second; the preconditioner, which needs the singular entries,
-    // is factored last and the streams are joined.
+    // integrals run on the first stream while the host prepares the far-field setup. The
+    // setup's table kernels (second stream) start when the singular pass ends and run beside
+    // the preconditioner's factorisation (first stream), whose block inversions leave most of
+    // each SM free; the streams are joined at the end.
     if ((rc = pb_near_setup(c))) return rc;
     if ((rc = pb_precond_plan(c))) return rc;
     PB_CUDA(c, cudaEventRecord(c->ev_tree, c->st));
     pb_tic(c, PB_T_SINGULAR);
     if ((rc = pb_touching_and_singular(c))) return rc;
     pb_toc(c, PB_T_SINGULAR);
+    PB_CUDA(c, cudaEventRecord(c->ev_sing, c->st));
     pb_tic_on(c, PB_T_FARSETUP, c->st2);
     if ((rc = pb_far_setup(c))) return rc;
     pb_toc_on(c, PB_T_FARSETUP, c->st2);

@@ -53,6 +53,8 @@ struct PbLevel {
     void* Dk = nullptr;      // derivatives of Gk
     void* Mg0 = nullptr;     // scaled source moments gathered into the slot layout (per product)
     void* Mgk = nullptr;
+    int* slot_tgt = nullptr; // [nslots] target cluster of each slot (table setup)
+    std::vector<int> h_slot[3];  // host sources of slot_off, slot_src, slot_tgt (kept for the async uploads)
 };
 
 struct pb_ctx {
@@ -60,6 +62,7 @@ struct pb_ctx {
     cudaStream_t st = nullptr;
     cudaStream_t st2 = nullptr;      // far field, concurrent with the near field on st
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_tree = nullptr;
+    cudaEvent_t ev_sing = nullptr;  // the singular pass has been queued up to here
     bool tables_ready = false;       // far-field constant tables uploaded
     std::string err = "no error";
     bool dead = false;

@@ -482,15 +482,15 @@ static void ss_table(int qs, SsTable& T)
         }
 }
 
-// One warp per unordered touching pair; lanes split the class's cube points. One body serves
-// all three classes (the table's zero coefficients drop the merged edge vectors, and identical
-// triangles pass zero normal projections), so the hot loop is a single copy of the code: three
+// The cube points of one pair's class (lane, lane + stride, ...). One body serves all three
+// classes (the table's zero coefficients drop the merged edge vectors, and identical triangles
+// pass zero normal projections), so the hot loop is a single copy of the code: three
 // specialised copies overflowed the instruction cache.
 __device__ __forceinline__ void ss_points_ff(int lane, const float2* __restrict__ tab, int tn, int off, int cnt,
                                              const ff (*eP)[3], const ff (*eQ)[3], const ff* proj, ff nxny, ff kap,
-                                             ff* acc)
+                                             ff* acc, int stride = 32)
 {
-    for (int i = off + lane; i < off + cnt; i += 32) {
+    for (int i = off + lane; i < off + cnt; i += stride) {
         const ff a0 = ld_ff(tab + i), a1 = ld_ff(tab + tn + i), b0 = ld_ff(tab + 2 * tn + i),
                  b1 = ld_ff(tab + 3 * tn + i), w = ld_ff(tab + 4 * tn + i);
         ff d[3];
@@ -510,36 +510,63 @@ __device__ __forceinline__ void ss_points_ff(int lane, const float2* __restrict_
 }
 
 // Unordered touching pairs: the ordered pairs (k, j) with order[k] <= order[j] (the quadrature is
-// laid out from the triangle of smaller element index), as (k, ordered-pair index).
+// laid out from the triangle of smaller element index), as (k, ordered-pair index), grouped
+// by class: shared edge first (405 cube points at q_s = 3), then identical triangles (243),
+// then a shared vertex (162), so that the 32 pairs of a warp share one trip count and the
+// longest pairs start first. cnt[g nt + k]: pairs of group g whose first triangle is k.
+__device__ __forceinline__ int canon_group(const int* __restrict__ stris, int k, int j)
+{
+    if (k == j) return 1;
+    int ns = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) ns += stris[3 * k + a] == stris[3 * j + b];
+    return ns == 2 ? 0 : 2;
+}
+
 template <int PASS>
 __global__ void k_canon(int nt, const int* __restrict__ toff, const int* __restrict__ tj,
-                        const int* __restrict__ order, int* __restrict__ cnt, const int* __restrict__ coff,
-                        int* __restrict__ ck, int* __restrict__ cp, int cap)
+                        const int* __restrict__ order, const int* __restrict__ stris, int* __restrict__ cnt,
+                        const int* __restrict__ coff, int* __restrict__ ck, int* __restrict__ cp, int cap)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nt) return;
-    int n = PASS ? coff[k] : 0;
-    for (int t = toff[k]; t < toff[k + 1]; ++t)
-        if (order[k] <= order[tj[t]]) {
-            if (PASS && n < cap) {  // cap: the pairs allocated (a mismatch fails the build)
-                ck[n] = k;
-                cp[n] = t;
+    int n[3] = {0, 0, 0};
+    if (PASS)
+        for (int g = 0; g < 3; ++g) n[g] = coff[g * nt + k];
+    for (int t = toff[k]; t < toff[k + 1]; ++t) {
+        const int j = tj[t];
+        if (order[k] <= order[j]) {
+            const int g = canon_group(stris, k, j);
+            if (PASS && n[g] < cap) {  // cap: the pairs allocated (a mismatch fails the build)
+                ck[n[g]] = k;
+                cp[n[g]] = t;
             }
-            ++n;
+            ++n[g];
         }
-    if (!PASS) cnt[k] = n;
+    }
+    if (!PASS)
+        for (int g = 0; g < 3; ++g) cnt[g * nt + k] = n[g];
 }
 
-__global__ void __launch_bounds__(256) k_singular_ff(int ncanon, const int* __restrict__ ncanon_dev,
-                                                     const int* __restrict__ ck,
-                                                     const int* __restrict__ cp, const int* __restrict__ toff,
-                                                     const int* __restrict__ tj, const int* __restrict__ stris,
-                                                     const float2* __restrict__ erec, const float2* __restrict__ tab,
-                                                     int tn, int3 toffs, int3 tcnts, ff kap, ff epsf, ff iepsf,
-                                                     double* __restrict__ corr)
+// SS_LPP threads per unordered touching pair (1: one thread per pair). Pairs are grouped by
+// class, so the pairs of a warp share one trip count and read the same (or neighbouring) table
+// entries together. With one thread per pair no per-pair work is repeated across lanes, no
+// cross-lane reduction is needed and no lane idles in a last, partial round of points (the
+// warp-per-pair form of this kernel left 10 % of its point slots idle and repeated the pair's
+// setup on 32 lanes). Both ordered entries, (k, j) and (j, k), come from the same sums and the
+// same one-point evaluation (under the exchange d -> -d, n_x <-> n_y the parts 0 and 1 are
+// unchanged and parts 2..5 map to -4, -5, -2, -3).
+#define SS_LPP 1
+__global__ void __launch_bounds__(128) k_singular_ff1(int ncanon, const int* __restrict__ ncanon_dev,
+                                                      const int* __restrict__ ck, const int* __restrict__ cp,
+                                                      const int* __restrict__ toff, const int* __restrict__ tj,
+                                                      const int* __restrict__ stris, const float2* __restrict__ erec,
+                                                      const float2* __restrict__ tab, int tn, int3 toffs, int3 tcnts,
+                                                      ff kap, ff epsf, ff iepsf, double* __restrict__ corr)
 {
-    const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    const int lane = threadIdx.x & 31;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = tid / SS_LPP, sub = tid % SS_LPP;
+    // (all SS_LPP threads of a pair leave together: the shuffles below stay within live groups)
     if (w >= ncanon || w >= *ncanon_dev) return;  // allocated pairs, and those the scan found
     const int k = ck[w];
     const long long pair = cp[w];
@@ -589,54 +616,51 @@ __global__ void __launch_bounds__(256) k_singular_ff(int ncanon, const int* __re
     }
     const int off = ns == 3 ? toffs.z : ns == 2 ? toffs.y : toffs.x;
     const int cnt = ns == 3 ? tcnts.z : ns == 2 ? tcnts.y : tcnts.x;
-    ss_points_ff(lane, tab, tn, off, cnt, eP, eQ, proj, nxny, kap, acc);
+    ss_points_ff(sub, tab, tn, off, cnt, eP, eQ, proj, nxny, kap, acc, SS_LPP);
+    // the pair's own SS_LPP lanes, all alive (a pair's lanes leave together)
+    const unsigned gmask = ((1u << SS_LPP) - 1u) << ((threadIdx.x & 31) & ~(SS_LPP - 1));
     for (int m = 0; m < 6; ++m)
-        for (int o = 16; o > 0; o >>= 1) {
-            ff v = {__shfl_xor_sync(0xffffffffu, acc[m].h, o), __shfl_xor_sync(0xffffffffu, acc[m].l, o)};
+        for (int o = 1; o < SS_LPP; o <<= 1) {
+            ff v = {__shfl_xor_sync(gmask, acc[m].h, o), __shfl_xor_sync(gmask, acc[m].l, o)};
             acc[m] = ff_add(acc[m], v);
         }
-    // Every lane now holds the sums. Even lanes assemble (k, j), odd lanes (j, k) (target t,
-    // source s); lanes 0-7 then store one entry each, so the FP64 conversions issue once.
-    const int o = lane & 1;
-    const float2* rt = o ? rj : rk;
-    const float2* rs = o ? rk : rj;
-    const ff At = ld_ff(rt + 15), As = ld_ff(rs + 15);
-    const ff jac = ff_mul_f(ff_mul(At, As), 4.0f);
+    if (sub > 1) return;
+    const ff Ak = ld_ff(rk + 15), Aj = ld_ff(rj + 15);
+    const ff AA = ff_mul(Ak, Aj);
+    const ff jac = ff_mul_f(AA, 4.0f);
     for (int m = 0; m < 6; ++m) acc[m] = ff_mul(acc[m], jac);
-    // exact integrals; for (j, k) the normals exchange roles (k_singular's assembly)
-    ff I[4];
-    I[0] = acc[0];
-    I[3] = acc[1];
-    if (!o) {
-        I[1] = ff_sub(ff_mul(epsf, acc[3]), acc[2]);
-        I[2] = ff_sub(ff_mul(acc[5], iepsf), acc[4]);
-    } else {
-        I[1] = ff_sub(acc[4], ff_mul(epsf, acc[5]));
-        I[2] = ff_sub(acc[2], ff_mul(acc[3], iepsf));
-    }
-    long long q = pair;
+    // exact integrals of (k, j) and, with the normals exchanged, of (j, k)
+    ff I[2][4];
+    I[0][0] = I[1][0] = acc[0];
+    I[0][3] = I[1][3] = acc[1];
+    I[0][1] = ff_sub(ff_mul(epsf, acc[3]), acc[2]);
+    I[0][2] = ff_sub(ff_mul(acc[5], iepsf), acc[4]);
+    I[1][1] = ff_sub(acc[4], ff_mul(epsf, acc[5]));
+    I[1][2] = ff_sub(acc[2], ff_mul(acc[3], iepsf));
+    long long qr = pair;  // position of (j, k) in j's list
     if (k != j) {
-        // one-point rule at the centroids: d = c_t - c_s, n_x = n_t, n_y = n_s
-        ff d[3], nt_[3], ns_[3];
-        for (int c = 0; c < 3; ++c) {
-            d[c] = ff_sub(ld_ff(rt + 12 + c), ld_ff(rs + 12 + c));
-            nt_[c] = ld_ff(rt + 9 + c);
-            ns_[c] = ld_ff(rs + 9 + c);
-        }
+        // one-point rule at the centroids for (k, j): d = c_k - c_j, n_x = n_k, n_y = n_j
+        ff d[3];
+        for (int c = 0; c < 3; ++c) d[c] = ff_sub(ld_ff(rk + 12 + c), ld_ff(rj + 12 + c));
         ff P[6];
-        ff_parts<6>(ff_dot3(d, d), ff_dot3(nt_, d), ff_dot3(ns_, d), ff_dot3(nt_, ns_), kap, P);
-        const ff AA = ff_mul(At, As);
-        const ff reg[4] = {P[0], ff_sub(ff_mul(epsf, P[3]), P[2]), ff_sub(ff_mul(P[5], iepsf), P[4]), P[1]};
-        for (int m = 0; m < 4; ++m) I[m] = ff_sub(I[m], ff_mul(AA, reg[m]));
-        if (o) {
-            q = toff[j];
-            while (q < toff[j + 1] && tj[q] != k) ++q;
-        }
+        ff_parts<6>(ff_dot3(d, d), ff_dot3(ni, d), ff_dot3(nj, d), nxny, kap, P);
+        const ff reg[2][4] = {{P[0], ff_sub(ff_mul(epsf, P[3]), P[2]), ff_sub(ff_mul(P[5], iepsf), P[4]), P[1]},
+                              {P[0], ff_sub(P[4], ff_mul(epsf, P[5])), ff_sub(P[2], ff_mul(P[3], iepsf)), P[1]}};
+        for (int o = 0; o < 2; ++o)
+            for (int m = 0; m < 4; ++m) I[o][m] = ff_sub(I[o][m], ff_mul(AA, reg[o][m]));
+        qr = toff[j];
+        while (qr < toff[j + 1] && tj[qr] != k) ++qr;
     }
-    const int m = (lane >> 1) & 3;
-    const ff v = m == 0 ? I[0] : m == 1 ? I[1] : m == 2 ? I[2] : I[3];
-    const bool store = lane < 8 && !(o && (k == j || q >= toff[j + 1]));
-    if (store) corr[4 * q + m] = ff_to(v);
+    if (sub == 0) {
+        double2* o0 = (double2*)(corr + 4 * pair);
+        o0[0] = make_double2(ff_to(I[0][0]), ff_to(I[0][1]));
+        o0[1] = make_double2(ff_to(I[0][2]), ff_to(I[0][3]));
+    }
+    if (sub == (SS_LPP > 1 ? 1 : 0) && k != j && qr < toff[j + 1]) {
+        double2* o1 = (double2*)(corr + 4 * qr);
+        o1[0] = make_double2(ff_to(I[1][0]), ff_to(I[1][1]));
+        o1[1] = make_double2(ff_to(I[1][2]), ff_to(I[1][3]));
+    }
 }
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
@@ -722,34 +746,35 @@ int pb_touching_and_singular(pb_ctx* c)
     k_elem_ff<<<nblk(nt, B), B, 0, c->st>>>(nt, c->stris, c->verts, c->e64p, c->e64n, erec);
     PB_LAUNCH(c);
     // unordered pairs
-    int* ccnt = (int*)pb_alloc(c, sizeof(int) * (nt + 1));
-    int* coff = (int*)pb_alloc(c, sizeof(int) * (nt + 1));
+    // (three groups of nt counts: shared edge, identical, shared vertex)
+    int* ccnt = (int*)pb_alloc(c, sizeof(int) * (3 * nt + 1));
+    int* coff = (int*)pb_alloc(c, sizeof(int) * (3 * nt + 1));
     if (!ccnt || !coff) return pb_fail(c, PB_ERR_NOMEM, "singular: out of memory");
-    PB_CUDA(c, cudaMemsetAsync(ccnt + nt, 0, sizeof(int), c->st));
-    k_canon<0><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, ccnt, nullptr, nullptr, nullptr,
-                                             0);
+    k_canon<0><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, c->stris, ccnt, nullptr, nullptr,
+                                             nullptr, 0);
     PB_LAUNCH(c);
     {
         size_t ctmp = 0;
-        cub::DeviceScan::ExclusiveSum(nullptr, ctmp, ccnt, coff, nt + 1, c->st);
+        cub::DeviceScan::ExclusiveSum(nullptr, ctmp, ccnt, coff, 3 * nt + 1, c->st);
         void* cbuf = nullptr;
         PB_CUDA(c, cudaMallocFromPoolAsync(&cbuf, ctmp, c->pool, c->st));
-        cub::DeviceScan::ExclusiveSum(cbuf, ctmp, ccnt, coff, nt + 1, c->st);
+        cub::DeviceScan::ExclusiveSum(cbuf, ctmp, ccnt, coff, 3 * nt + 1, c->st);
         PB_LAUNCH(c);
         PB_CUDA(c, cudaFreeAsync(cbuf, c->st));
     }
     // Touching is symmetric and every triangle touches itself, so the unordered pairs number
-    // (ordered pairs + nt) / 2; the kernel takes the count from the scan (coff[nt]) and the
+    // (ordered pairs + nt) / 2; the kernel takes the count from the scan (coff[3 nt]) and the
     // build checks the two agree when it synchronises at its end.
     const int ncanon = (int)((htot + (long long)nt) / 2);
-    c->canon_check = coff + nt;
+    c->canon_check = coff + 3 * nt;
     c->canon_expect = ncanon;
     int* ck = (int*)pb_alloc(c, sizeof(int) * (ncanon + 1));
     int* cp = (int*)pb_alloc(c, sizeof(int) * (ncanon + 1));
     if (!ck || !cp) return pb_fail(c, PB_ERR_NOMEM, "singular: out of memory");
-    k_canon<1><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, nullptr, coff, ck, cp, ncanon);
+    k_canon<1><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, c->stris, nullptr, coff, ck, cp,
+                                             ncanon);
     PB_LAUNCH(c);
-    k_singular_ff<<<nblk(ncanon, 8), 256, 0, c->st>>>(ncanon, coff + nt, ck, cp, c->touch_off, c->touch_j, c->stris, erec, tab,
+    k_singular_ff1<<<nblk((long long)ncanon * SS_LPP, 128), 128, 0, c->st>>>(ncanon, coff + 3 * nt, ck, cp, c->touch_off, c->touch_j, c->stris, erec, tab,
                                                     T.n, make_int3(T.off[0], T.off[1], T.off[2]),
                                                     make_int3(T.cnt[0], T.cnt[1], T.cnt[2]), ff_from(c->prm.kappa),
                                                     ff_from(eps), ff_from(1.0 / eps), c->corr);
