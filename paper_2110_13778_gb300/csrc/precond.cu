@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(GJ_T) k_blk_gj(const int* __restrict__ begin, 
 // columns from the lane holding it by a shuffle, then applies the exchange
 //   T[p][k] <- 1/a, T[p][j] <- -T[p][j]/a, T[i][k] <- T[i][k]/a, T[i][j] -= T[i][k] T[p][j]/a.
 // After m exchanges T[p_k][k'] = (A^-1)[k][p_k'], which the final store applies.
-template <int MA, int MB, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_blk_gj_w(const int* __restrict__ ids, const int* __restrict__ begin,
+template <int MA, int MB, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_blk_gj_w(const int* __restrict__ ids, const int* __restrict__ begin,
                                                        const long long* __restrict__ moff, float* __restrict__ minv,
                                                        int* __restrict__ singular)
 {
@@ -197,14 +197,14 @@ __global__ void __launch_bounds__(256, MINB) k_blk_gj_w(const int* __restrict__ 
     for (int a = 0; a < MA; ++a)
 #pragma unroll
         for (int b = 0; b < MB; ++b) {
-            const int i = lane + 32 * a, j = warp + 8 * b;
+            const int i = lane + 32 * a, j = warp + NW * b;
             v[a][b] = (i < m && j < m) ? g[(size_t)i * m + j] : 0.f;
         }
     unsigned used = 0;  // bit a: row lane + 32 a has been a pivot row
 #pragma unroll
     for (int kb = 0; kb < MB; ++kb) {
-        for (int kw = 0; kw < 8; ++kw) {
-            const int k = 8 * kb + kw;
+        for (int kw = 0; kw < NW; ++kw) {
+            const int k = NW * kb + kw;
             if (k >= m) break;
             const int s = k & 1;
             if (warp == kw) {
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(256, MINB) k_blk_gj_w(const int* __restrict__ 
     for (int a = 0; a < MA; ++a)
 #pragma unroll
         for (int b = 0; b < MB; ++b) {
-            const int i = lane + 32 * a, j = warp + 8 * b;
+            const int i = lane + 32 * a, j = warp + NW * b;
             if (i < m && j < m) g[(size_t)inv[i] * m + perm[j]] = v[a][b];
         }
 }
@@ -366,15 +366,15 @@ static int blk_build(pb_ctx* c, const long long* dmoff, long long ntot, int mcap
         const int* ids = c->pc_ids;
         const int* cl = c->pc_cls;
         if (cl[1] > cl[0]) {
-            k_blk_gj_w<2, 8, 4><<<cl[1] - cl[0], 256, 0, c->st>>>(ids + cl[0], c->pc_begin, dmoff, (float*)M, sing);
+            k_blk_gj_w<2, 8, 8, 4><<<cl[1] - cl[0], 256, 0, c->st>>>(ids + cl[0], c->pc_begin, dmoff, (float*)M, sing);
             PB_LAUNCH(c);
         }
         if (cl[2] > cl[1]) {
-            k_blk_gj_w<4, 16, 2><<<cl[2] - cl[1], 256, 0, c->st>>>(ids + cl[1], c->pc_begin, dmoff, (float*)M, sing);
+            k_blk_gj_w<4, 8, 16, 2><<<cl[2] - cl[1], 512, 0, c->st>>>(ids + cl[1], c->pc_begin, dmoff, (float*)M, sing);
             PB_LAUNCH(c);
         }
         if (cl[3] > cl[2]) {
-            k_blk_gj_w<6, 24, 1><<<cl[3] - cl[2], 256, 0, c->st>>>(ids + cl[2], c->pc_begin, dmoff, (float*)M, sing);
+            k_blk_gj_w<6, 12, 16, 1><<<cl[3] - cl[2], 512, 0, c->st>>>(ids + cl[2], c->pc_begin, dmoff, (float*)M, sing);
             PB_LAUNCH(c);
         }
         int hs = 0;
