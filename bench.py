@@ -506,7 +506,9 @@ def run_batch(a):
         cx = pb.pb_create(prm, stream)
         pb.pb_mesh_upload(cx, m.verts, m.tris, m.qpos, m.q)
         if not a.no_autotune:
-            tuned.append(pb.pb_autotune(cx, tol=1e-4, matvecs_per_solve=10 * a.states))
+            r = pb.pb_autotune(cx, tol=1e-4, matvecs_per_solve=10, nrhs=a.states)
+            r["order"] = r["order"][:pb.pb_get_tree_stats(cx)["levels"] + 1]
+            tuned.append(r)
         ctxs.append(cx)
     t_tune = time.perf_counter() - t0
     Xs = [torch.empty((a.states, 2 * m.nt), dtype=torch.float64, device="cuda") for m in mols]
@@ -556,6 +558,7 @@ def run_batch(a):
                        "eta0": a.eta0, "states": a.states_mode,
                        "l2": "flushed (256 MiB write) before each step, outside the timed events",
                        "autotune": ({"leaf_size": [t["leaf_size"] for t in tuned], "p": [t["p"] for t in tuned],
+                                     "order_per_level": [t["order"] for t in tuned],
                                      "rel_err": [t["rel_err"] for t in tuned], "seconds": t_tune}
                                     if tuned else {"leaf_size": a.leaf, "p": a.p})}}))
     return 0

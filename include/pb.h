@@ -213,7 +213,7 @@ int pb_matvec_part(pb_ctx* ctx, const double* x, double* y, int which);
 #define PB_T_PCBUILD 9    /* preconditioner assembly and inversion (setup) */
 #define PB_T_ENERGY 10    /* solvation energy */
 #define PB_T_RHS 11       /* right-hand side */
-#define PB_T_FARSETUP 12  /* MtL derivative tables and near-field chunks (setup) */
+#define PB_T_FARSETUP 12  /* MtL derivative table kernels (setup) */
 int pb_set_timing(pb_ctx* ctx, int enable);
 int pb_get_timing(pb_ctx* ctx, double* out);
 
@@ -228,23 +228,29 @@ int pb_get_graph_launches(pb_ctx* ctx, long long* out);
 
 /* Autotuner (no counterpart in the paper, which sets the leaf size and order by hand): on the
  * uploaded molecule, tries leaf sizes {32, 48, 64, 96, 128} x orders {4, 6, 8} (uniform order,
- * the context's eta0 and precision), timing pb_build_tree and pb_matvec with CUDA events and
+ * the context's eta0 and precision), timing pb_build_tree and the product with CUDA events and
  * measuring the product's relative L2 error against an order-10 product on a fixed
- * pseudo-random density. At each leaf size the orders are tried upwards until one meets tol.
- * Chooses the candidate with the least build_ms + matvecs_per_solve x matvec_ms among those
- * within tol (else the most accurate), stores its leaf size and order in the context's
- * parameters and leaves the context built with them. out: host pointer. Synchronises; takes
- * about 16 builds. */
+ * pseudo-random density. The product is timed on nrhs vectors at once (pb_matvec for 1,
+ * pb_matvec_multi above; 1 <= nrhs <= PB_MAX_RHS), as the caller will apply it, and
+ * matvecs_per_solve counts such products. At each leaf size the orders are tried upwards until
+ * one meets tol. Chooses the candidate with the least build_ms + matvecs_per_solve x matvec_ms
+ * among those within tol (else the most accurate) and stores its leaf size and order in the
+ * context's parameters. Then, from the finest level with a far field upwards, it lowers single
+ * levels' orders by 2 (not below 4) while the error stays within tol and the cost falls; these
+ * per-level orders (out->order) apply to later builds of the same depth until the next
+ * pb_autotune. Leaves the context built with the choice. out: host pointer. Synchronises;
+ * takes about 16 + L builds. */
 typedef struct pb_tune_result {
     int leaf_size;      /* chosen leaf size s */
-    int p;              /* chosen order (all levels) */
+    int p;              /* chosen uniform order (before the per-level pass) */
     double matvec_ms;   /* median product time of the choice */
     double build_ms;    /* its pb_build_tree time */
     double rel_err;     /* its product error against the order-10 reference */
     int tried;          /* candidates built */
     int met_tolerance;  /* 1 if rel_err <= tol */
+    int order[11];      /* chosen order per level 0..L (0 beyond L) */
 } pb_tune_result;
-int pb_autotune(pb_ctx* ctx, double tol, int matvecs_per_solve, pb_tune_result* out);
+int pb_autotune(pb_ctx* ctx, double tol, int matvecs_per_solve, int nrhs, pb_tune_result* out);
 
 /* Measured FMA throughput of the current device in TFLOP/s (2 flops per FMA): eight
  * independent FMA chains per thread on 8 x (SM count) blocks of 256 threads, timed with CUDA

@@ -5,7 +5,9 @@
 // candidate it builds the tree, times the matrix-vector product with CUDA events, and measures
 // its error against a reference product of order 10 on a fixed pseudo-random density; it
 // keeps the cheapest candidate (build time + expected products x product time) whose error
-// stays within the tolerance, and leaves the context built with it.
+// stays within the tolerance; then it lowers the order of single levels, finest first, while
+// the error stays within the tolerance and the cost falls, and leaves the context built with
+// the result. Products are timed on as many vectors at once as the caller will solve for.
 #include <math.h>
 
 #include <algorithm>
@@ -63,18 +65,41 @@ static int timed_build(pb_ctx* c, cudaEvent_t e0, cudaEvent_t e1, float* ms)
     return PB_OK;
 }
 
-extern "C" int pb_autotune(pb_ctx* c, double tol, int matvecs_per_solve, pb_tune_result* out)
+// one timed product of nr vectors (X, Y: nr x 2N, element order): the median of three after a
+// warm-up
+static int timed_products(pb_ctx* c, const double* X, double* Y, int nr, cudaEvent_t e0, cudaEvent_t e1,
+                          float* med)
+{
+    auto prod = [&]() { return nr == 1 ? pb_matvec(c, X, Y) : pb_matvec_multi(c, X, Y, nr); };
+    int rc = prod();
+    if (rc) return rc;
+    float t[3];
+    for (int r = 0; r < 3; ++r) {
+        PB_CUDA(c, cudaEventRecord(e0, c->st));
+        if ((rc = prod())) return rc;
+        PB_CUDA(c, cudaEventRecord(e1, c->st));
+        PB_CUDA(c, cudaEventSynchronize(e1));
+        PB_CUDA(c, cudaEventElapsedTime(&t[r], e0, e1));
+    }
+    std::sort(t, t + 3);
+    *med = t[1];
+    return PB_OK;
+}
+
+extern "C" int pb_autotune(pb_ctx* c, double tol, int matvecs_per_solve, int nrhs, pb_tune_result* out)
 {
     if (!c) return PB_ERR_ARG;
     if (c->dead) return PB_ERR_CUDA;
     if (!c->verts) return pb_fail(c, PB_ERR_STATE, "autotune before mesh_upload");
-    if (!(tol > 0) || matvecs_per_solve < 1 || !out) return pb_fail(c, PB_ERR_ARG, "autotune: bad arguments");
+    if (!(tol > 0) || matvecs_per_solve < 1 || nrhs < 1 || nrhs > PB_MAX_RHS || !out)
+        return pb_fail(c, PB_ERR_ARG, "autotune: bad arguments");
     const pb_params keep = c->prm;
+    c->p_level_L = -1;  // candidates use one order on every level
     const long long n = 2LL * c->nt;
     double *x = nullptr, *yref = nullptr, *y = nullptr, *acc = nullptr;
-    if (cudaMallocFromPoolAsync(&x, sizeof(double) * n, c->pool, c->st) != cudaSuccess ||
+    if (cudaMallocFromPoolAsync(&x, sizeof(double) * n * nrhs, c->pool, c->st) != cudaSuccess ||
         cudaMallocFromPoolAsync(&yref, sizeof(double) * n, c->pool, c->st) != cudaSuccess ||
-        cudaMallocFromPoolAsync(&y, sizeof(double) * n, c->pool, c->st) != cudaSuccess ||
+        cudaMallocFromPoolAsync(&y, sizeof(double) * n * nrhs, c->pool, c->st) != cudaSuccess ||
         cudaMallocFromPoolAsync(&acc, sizeof(double) * 2, c->pool, c->st) != cudaSuccess) {
         cudaGetLastError();
         return pb_fail(c, PB_ERR_NOMEM, "autotune: out of memory");
@@ -93,9 +118,12 @@ extern "C" int pb_autotune(pb_ctx* c, double tol, int matvecs_per_solve, pb_tune
         cudaEventDestroy(e1);
         return r;
     };
-    // x in element order; every product goes through the public entry point
-    k_tune_fill<<<G, 256, 0, c->st>>>(n, 0x5EEDULL, x);
-    PB_LAUNCH(c);
+    // nrhs pseudo-random vectors in element order; every product goes through the public entry
+    // points, and the error is measured on the first vector
+    for (int r = 0; r < nrhs; ++r) {
+        k_tune_fill<<<G, 256, 0, c->st>>>(n, 0x5EEDULL + 7919ULL * r, x + n * r);
+        PB_LAUNCH(c);
+    }
     // reference: order 10 at the caller's leaf size
     c->prm.p = 10;
     c->prm.adaptive = 0;
@@ -104,6 +132,17 @@ extern "C" int pb_autotune(pb_ctx* c, double tol, int matvecs_per_solve, pb_tune
         c->prm = keep;
         return fail(rc);
     }
+    // relative L2 error of y (first vector) against the reference
+    auto rel_err = [&](double* err) -> int {
+        PB_CUDA(c, cudaMemsetAsync(acc, 0, sizeof(double) * 2, c->st));
+        k_tune_err<<<G, 256, 0, c->st>>>(n, y, yref, acc);
+        PB_LAUNCH(c);
+        double h[2];
+        PB_CUDA(c, cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+        PB_CUDA(c, cudaStreamSynchronize(c->st));
+        *err = sqrt(h[0] / (h[1] > 0 ? h[1] : 1.0));
+        return PB_OK;
+    };
     const int leaves[5] = {32, 48, 64, 96, 128};
     const int orders[3] = {4, 6, 8};
     double best_cost = 1e300, best_err = 1e300, best_ms = 0, best_bms = 0;
@@ -114,36 +153,14 @@ extern "C" int pb_autotune(pb_ctx* c, double tol, int matvecs_per_solve, pb_tune
             c->prm.leaf_size = leaves[li];
             c->prm.levels = 0;
             c->prm.p = orders[pi];
-            float bms = 0;
-            if ((rc = timed_build(c, e0, e1, &bms))) {
+            float bms = 0, t = 0;
+            double err = 0;
+            if ((rc = timed_build(c, e0, e1, &bms)) || (rc = timed_products(c, x, y, nrhs, e0, e1, &t)) ||
+                (rc = rel_err(&err))) {
                 c->prm = keep;
                 return fail(rc);
             }
-            // one warm-up product, then the median of three
-            if ((rc = pb_matvec(c, x, y))) {
-                c->prm = keep;
-                return fail(rc);
-            }
-            float t[3];
-            for (int r = 0; r < 3; ++r) {
-                PB_CUDA(c, cudaEventRecord(e0, c->st));
-                if ((rc = pb_matvec(c, x, y))) {
-                    c->prm = keep;
-                    return fail(rc);
-                }
-                PB_CUDA(c, cudaEventRecord(e1, c->st));
-                PB_CUDA(c, cudaEventSynchronize(e1));
-                PB_CUDA(c, cudaEventElapsedTime(&t[r], e0, e1));
-            }
-            std::sort(t, t + 3);
-            PB_CUDA(c, cudaMemsetAsync(acc, 0, sizeof(double) * 2, c->st));
-            k_tune_err<<<G, 256, 0, c->st>>>(n, y, yref, acc);
-            PB_LAUNCH(c);
-            double h[2];
-            PB_CUDA(c, cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, c->st));
-            PB_CUDA(c, cudaStreamSynchronize(c->st));
-            const double err = sqrt(h[0] / (h[1] > 0 ? h[1] : 1.0));
-            const double cost = bms + (double)matvecs_per_solve * t[1];
+            const double cost = bms + (double)matvecs_per_solve * t;
             ++tried;
             const bool ok = err <= tol;
             if ((ok && (!best_ok || cost < best_cost)) || (!ok && !best_ok && err < best_err)) {
@@ -152,7 +169,7 @@ extern "C" int pb_autotune(pb_ctx* c, double tol, int matvecs_per_solve, pb_tune
                 best_err = err;
                 best_leaf = leaves[li];
                 best_p = orders[pi];
-                best_ms = t[1];
+                best_ms = t;
                 best_bms = bms;
             }
             if (ok) break;  // higher orders at this leaf size only cost more
@@ -164,6 +181,36 @@ extern "C" int pb_autotune(pb_ctx* c, double tol, int matvecs_per_solve, pb_tune
     c->prm.p = best_p;
     c->prm.adaptive = 0;
     if ((rc = timed_build(c, e0, e1, &ms))) return fail(rc);
+    // Per-level orders: from the finest level with a far field upwards, lower that level's
+    // order by 2 (not below 4) while the product stays within tol and the cost falls.
+    if (best_ok) {
+        const int L = c->L;
+        int po[PB_MAXL + 1];
+        for (int l = 0; l <= L; ++l) po[l] = c->lev[l].p;
+        for (int l = L; l >= 1; --l) {
+            if (c->lev[l].ninter == 0 || po[l] <= 4) continue;
+            for (int q = 0; q <= L; ++q) c->p_level[q] = po[q];
+            c->p_level[l] = po[l] - 2;
+            c->p_level_L = L;
+            float bms = 0, t = 0;
+            double err = 0;
+            if ((rc = timed_build(c, e0, e1, &bms)) || (rc = timed_products(c, x, y, nrhs, e0, e1, &t)) ||
+                (rc = rel_err(&err)))
+                return fail(rc);
+            ++tried;
+            const double cost = bms + (double)matvecs_per_solve * t;
+            if (c->L == L && err <= tol && cost < best_cost) {
+                po[l] -= 2;
+                best_cost = cost;
+                best_err = err;
+                best_ms = t;
+                best_bms = bms;
+            }
+        }
+        for (int q = 0; q <= L; ++q) c->p_level[q] = po[q];
+        c->p_level_L = L;
+        if ((rc = timed_build(c, e0, e1, &ms))) return fail(rc);
+    }
     out->leaf_size = best_leaf;
     out->p = best_p;
     out->matvec_ms = best_ms;
@@ -171,6 +218,7 @@ extern "C" int pb_autotune(pb_ctx* c, double tol, int matvecs_per_solve, pb_tune
     out->rel_err = best_err;
     out->tried = tried;
     out->met_tolerance = best_ok ? 1 : 0;
+    for (int l = 0; l < 11; ++l) out->order[l] = l <= c->L ? c->lev[l].p : 0;
     fail(PB_OK);
     return PB_OK;
 }

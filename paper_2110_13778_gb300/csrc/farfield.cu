@@ -943,6 +943,7 @@ int pb_far_setup(pb_ctx* c)
     // hold every SM slot while these kernels queue for them. Afterwards they run beside the
     // preconditioner's factorisation.
     PB_CUDA(c, cudaStreamWaitEvent(fs, c->ev_sing, 0));
+    pb_tic_on(c, PB_T_FARSETUP, fs);
     for (int l = 1; l <= c->L; ++l) {
         PbLevel& lv = c->lev[l];
         if (lv.ninter > 0 && m2l_fast_order(lv.p)) {
@@ -950,6 +951,7 @@ int pb_far_setup(pb_ctx* c)
             if (rc2) return rc2;
         }
     }
+    pb_toc_on(c, PB_T_FARSETUP, fs);
     PB_CUDA(c, cudaEventRecord(c->ev_join, c->st2));
     return PB_OK;
 }

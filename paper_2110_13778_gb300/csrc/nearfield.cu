@@ -26,6 +26,7 @@
 #include "pb_internal.cuh"
 
 #define NEAR_T 128
+#define NEAR_ITEM 6  // pair tiles per warp of the mixed-precision near field
 
 template <class R, class PV, bool HILO>
 __global__ void __launch_bounds__(NEAR_T) k_near(int nt, const int* __restrict__ begin,
@@ -133,26 +134,29 @@ __global__ void k_near_pack(int nt, const float4* __restrict__ e32p, const float
 // holds A_l) and one source chunk B of nb <= 32 sources. K1 and K4 are symmetric in (x, y),
 // and with d = x_i - x_j the double-layer kernels of the reversed pair follow from the same
 // radial factors: K2(j, i) = -(n_i.d) ri3 (eps e1 - 1), K3(j, i) = (n_j.d) ri3 (1 - e1/eps).
-// The warp of chunk A visits every source chunk B of the neighbour leaves c2 >= c that
-// follows A (B after A within A's own leaf). B's records are staged in shared memory; at step
+// The tiles (A, B) -- every source chunk B of the neighbour leaves c2 >= c that follows A (B
+// after A within A's own leaf) -- are cut into work items of at most NEAR_ITEM tiles of one A;
+// one warp per item, so that the warps carry nearly equal work whatever the leaf order. B's records are staged in shared memory; at step
 // s (s < nb) lane l pairs A_l with B_((l + s) mod nb), keeps the forward terms and adds the
 // reverse terms to B's shared-memory accumulators (FP32 shared atomics; lanes l and l + nb
 // meet at the same source). Forward sums of a chunk and reverse sums of a tile are FP32,
 // added into FP64 (atomics for the reverse terms and the final forward sums; ys starts at
 // zero). The tile of A with itself keeps only the forward terms and drops the identical pair.
-__global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nchunks, const int* __restrict__ chunk_leaf,
-                                                    const int* __restrict__ chunk_first,
-                                                    const int* __restrict__ begin, const int* __restrict__ noff,
-                                                    const int* __restrict__ nidx, const float4* __restrict__ sp,
-                                                    const float4* __restrict__ sn, const float4* __restrict__ sl,
-                                                    double eps_d, double kappa_d, double* __restrict__ ys)
+__global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nitems, const int4* __restrict__ items,
+                                                    const int* __restrict__ tiles, const int* __restrict__ chunk_leaf,
+                                                    const int* __restrict__ chunk_first, const int* __restrict__ begin,
+                                                    const float4* __restrict__ sp, const float4* __restrict__ sn,
+                                                    const float4* __restrict__ sl, double eps_d, double kappa_d,
+                                                    double* __restrict__ ys)
 {
     __shared__ float4 sbp[8][32], sbn[8][32], sbl[8][32];
     __shared__ float rv1[8][32], rv2[8][32];
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    if (w >= nchunks) return;
-    const int c = chunk_leaf[w], a0 = chunk_first[w];
+    if (w >= nitems) return;
+    const int4 item = items[w];
+    const int ca = item.x;
+    const int c = chunk_leaf[ca], a0 = chunk_first[ca];
     const int k = a0 + lane;
     const bool act = k < begin[c + 1];
     const int kk = act ? k : a0;
@@ -161,12 +165,11 @@ __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nchunks, const
     const float eps = (float)eps_d, inv_eps = (float)(1.0 / eps_d), kappa = (float)kappa_d;
     const float i4pi = 0.07957747154594767f;
     double acc1 = 0.0, acc2 = 0.0;
-    for (int t = noff[c]; t < noff[c + 1]; ++t) {
-        const int c2 = nidx[t];
-        if (c2 < c) continue;
-        const int sb = begin[c2], se = begin[c2 + 1];
-        for (int b0 = (c2 == c ? a0 : sb); b0 < se; b0 += 32) {
-            const bool diag = b0 == a0;
+    for (int ti = item.y; ti < item.z; ++ti) {
+        const int cb = tiles[ti];
+        const int b0 = chunk_first[cb], se = begin[chunk_leaf[cb] + 1];
+        {
+            const bool diag = cb == ca;
             const int nb = min(32, se - b0);
             const int j = b0 + lane;
             __syncwarp();
@@ -364,6 +367,40 @@ int pb_near_setup(pb_ctx* c)
             cf.push_back(s);
         }
     c->nchunks = (int)cl.size();
+    // pair tiles (A, B), B a chunk of a neighbour leaf c2 >= leaf(A) and B >= A, cut into work
+    // items of at most NEAR_ITEM tiles that share A
+    {
+        std::vector<int> first_chunk(lv.ncl + 1, 0);
+        for (int k = 0; k < lv.ncl; ++k) first_chunk[k + 1] = first_chunk[k] + (b[k + 1] - b[k] + 31) / 32;
+        std::vector<int>& tl = c->h_up_i[4];
+        std::vector<int4>& it = c->h_up_i4;
+        tl.clear();
+        it.clear();
+        const std::vector<int>& no = c->h_near_off;
+        const std::vector<int>& ni = c->h_near_idx;
+        for (int k = 0; k < lv.ncl; ++k)
+            for (int a = first_chunk[k]; a < first_chunk[k + 1]; ++a) {
+                int start = (int)tl.size();
+                for (int t = no[k]; t < no[k + 1]; ++t) {
+                    const int c2 = ni[t];
+                    if (c2 < k) continue;
+                    for (int bq = (c2 == k ? a : first_chunk[c2]); bq < first_chunk[c2 + 1]; ++bq) {
+                        tl.push_back(bq);
+                        if ((int)tl.size() - start == NEAR_ITEM) {
+                            it.push_back(make_int4(a, start, (int)tl.size(), 0));
+                            start = (int)tl.size();
+                        }
+                    }
+                }
+                if ((int)tl.size() > start) it.push_back(make_int4(a, start, (int)tl.size(), 0));
+            }
+        c->near_nitems = (int)it.size();
+        c->near_items = (int4*)pb_alloc(c, sizeof(int4) * (it.size() + 1));
+        c->near_tiles = (int*)pb_alloc(c, sizeof(int) * (tl.size() + 1));
+        if (!c->near_items || !c->near_tiles) return pb_fail(c, PB_ERR_NOMEM, "near setup: out of memory");
+        PB_CUDA(c, cudaMemcpyAsync(c->near_items, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice, c->st));
+        PB_CUDA(c, cudaMemcpyAsync(c->near_tiles, tl.data(), sizeof(int) * tl.size(), cudaMemcpyHostToDevice, c->st));
+    }
     c->chunk_leaf = (int*)pb_alloc(c, sizeof(int) * cl.size());
     c->chunk_first = (int*)pb_alloc(c, sizeof(int) * cf.size());
     c->near_sp = (float4*)pb_alloc(c, sizeof(float4) * c->nt);
@@ -384,10 +421,9 @@ int pb_near_apply(pb_ctx* c, const double* xs, double* ys)
         k_near_pack<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->e32p, c->e32n, xs, c->near_sp, c->near_sn);
         PB_LAUNCH(c);
         PB_CUDA(c, cudaMemsetAsync(ys, 0, sizeof(double) * 2 * nt, c->st));
-        k_near_tile<<<(c->nchunks * 32 + 255) / 256, 256, 0, c->st>>>(nt, c->nchunks, c->chunk_leaf,
-                                                                       c->chunk_first, lv.begin, lv.near_off,
-                                                                       lv.near_idx, c->near_sp, c->near_sn, c->e32l,
-                                                                       eps, c->prm.kappa, ys);
+        k_near_tile<<<(c->near_nitems * 32 + 255) / 256, 256, 0, c->st>>>(
+            nt, c->near_nitems, c->near_items, c->near_tiles, c->chunk_leaf, c->chunk_first, lv.begin, c->near_sp,
+            c->near_sn, c->e32l, eps, c->prm.kappa, ys);
         PB_LAUNCH(c);
         k_near_finish<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->e64p, xs, eps, ys);
     } else

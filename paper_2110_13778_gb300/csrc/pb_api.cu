@@ -240,9 +240,7 @@ extern "C" int pb_build_tree(pb_ctx* c)
     if ((rc = pb_touching_and_singular(c))) return rc;
     pb_toc(c, PB_T_SINGULAR);
     PB_CUDA(c, cudaEventRecord(c->ev_sing, c->st));
-    pb_tic_on(c, PB_T_FARSETUP, c->st2);
-    if ((rc = pb_far_setup(c))) return rc;
-    pb_toc_on(c, PB_T_FARSETUP, c->st2);
+    if ((rc = pb_far_setup(c))) return rc;  // times its table kernels as PB_T_FARSETUP
     pb_tic(c, PB_T_PCBUILD);
     if ((rc = pb_precond_factor(c))) return rc;
     pb_toc(c, PB_T_PCBUILD);

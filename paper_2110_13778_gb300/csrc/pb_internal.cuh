@@ -97,6 +97,11 @@ struct pb_ctx {
     int nchunks = 0;
     int* chunk_leaf = nullptr;
     int* chunk_first = nullptr;
+    int p_level[PB_MAXL + 1] = {};  // per-level orders chosen by the autotuner,
+    int p_level_L = -1;             // valid for builds of this depth (-1: none)
+    int near_nitems = 0;          // work items of the pair-tile near field
+    int4* near_items = nullptr;   // (target chunk, first tile, end tile, 0)
+    int* near_tiles = nullptr;    // source chunk of each tile
     float4* near_sp = nullptr;  // (x_hi, y_hi, z_hi, A phi)
     float4* near_sn = nullptr;  // (n_x, n_y, n_z, A dphi)
     float2* near_dens = nullptr; // [dens_nr][nt] (A phi, A dphi) for several right-hand sides
@@ -116,7 +121,8 @@ struct pb_ctx {
     // host copies made by the build: the leaf ranges (read back once by the tree build), and
     // the sources of the build's host-to-device uploads, kept until the next build so that
     // those copies need no synchronisation
-    std::vector<int> h_leaf_begin, h_up_i[4];
+    std::vector<int> h_leaf_begin, h_near_off, h_near_idx, h_up_i[5];
+    std::vector<int4> h_up_i4;
     std::vector<long long> h_up_l;
     std::vector<double> h_up_d;
     std::vector<float2> h_up_f2;

@@ -468,6 +468,7 @@ int pb_geometry_and_tree(pb_ctx* c)
     // Taylor orders per level
     for (int l = 0; l <= L; ++l) {
         int p = c->prm.p + (c->prm.adaptive ? (L - l) : 0);
+        if (c->p_level_L == L && c->p_level[l] > 0) p = c->p_level[l];  // the autotuner's per-level choice
         c->lev[l].p = p > PB_PMAX ? PB_PMAX : p;
     }
     // sorted element records
@@ -500,6 +501,8 @@ int pb_geometry_and_tree(pb_ctx* c)
         c->max_leaf = mx;
         c->near_pairs = np;
         c->h_leaf_begin.swap(b);
+        c->h_near_off.swap(off);
+        c->h_near_idx.swap(idxh);
     }
     return PB_OK;
 }

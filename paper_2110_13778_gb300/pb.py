@@ -58,7 +58,7 @@ class pb_solve_info(ctypes.Structure):
 class pb_tune_result(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("p", ctypes.c_int), ("matvec_ms", ctypes.c_double),
                 ("build_ms", ctypes.c_double), ("rel_err", ctypes.c_double), ("tried", ctypes.c_int),
-                ("met_tolerance", ctypes.c_int)]
+                ("met_tolerance", ctypes.c_int), ("order", ctypes.c_int * 11)]
 
 
 class pb_tree_stats(ctypes.Structure):
@@ -120,7 +120,7 @@ def lib():
         L.pb_measure_alu_peaks.argtypes = [vp, dp, dp]
         L.pb_matvec_multi.argtypes = [vp, vp, vp, c_int]
         L.pb_get_graph_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
-        L.pb_autotune.argtypes = [vp, c_double, c_int, ctypes.POINTER(pb_tune_result)]
+        L.pb_autotune.argtypes = [vp, c_double, c_int, c_int, ctypes.POINTER(pb_tune_result)]
         _lib = L
     return _lib
 
@@ -385,8 +385,11 @@ def pb_measure_alu_peaks(stream=0):
     return a.value, b.value
 
 
-def pb_autotune(ctx, tol=1e-4, matvecs_per_solve=10):
-    """Choose leaf size and order for the uploaded molecule; leaves ctx built with them."""
+def pb_autotune(ctx, tol=1e-4, matvecs_per_solve=10, nrhs=1):
+    """Choose leaf size and per-level orders for the uploaded molecule, timing products of
+    nrhs vectors; leaves ctx built with them."""
     r = pb_tune_result()
-    _check(ctx, lib().pb_autotune(ctx, tol, matvecs_per_solve, ctypes.byref(r)))
-    return {f: getattr(r, f) for f, _ in pb_tune_result._fields_}
+    _check(ctx, lib().pb_autotune(ctx, tol, matvecs_per_solve, nrhs, ctypes.byref(r)))
+    out = {f: getattr(r, f) for f, _ in pb_tune_result._fields_}
+    out["order"] = list(r.order)
+    return out

@@ -76,4 +76,4 @@ def test_null_handles_are_rejected():
     assert L.pb_get_launch_count(None, ctypes.byref(n)) == pb.PB_ERR_ARG
     assert L.pb_matvec_multi(None, None, None, 1) == pb.PB_ERR_ARG
     assert L.pb_learned_guess(None, None, None) == pb.PB_ERR_ARG
-    assert L.pb_autotune(None, 1e-4, 10, None) == pb.PB_ERR_ARG
+    assert L.pb_autotune(None, 1e-4, 10, 1, None) == pb.PB_ERR_ARG

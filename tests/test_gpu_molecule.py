@@ -88,20 +88,28 @@ def dense_mesh(m, q):
     return Mesh(m.verts, m.tris, m.qpos, q)
 
 
-@pytest.mark.parametrize("prec", [pb.PB_FP64, pb.PB_MIXED])
-def test_autotune_picks_an_accurate_configuration(mol, prec):
+@pytest.mark.parametrize("prec,nrhs", [(pb.PB_FP64, 1), (pb.PB_MIXED, 1), (pb.PB_MIXED, 4)])
+def test_autotune_picks_an_accurate_configuration(mol, prec, nrhs):
     m, ph, A = mol
     xo = np.linalg.solve(A, dense.rhs(m, ph))
     Eo = dense.energy(m, ph, xo)
     ctx = pb.pb_create(pb.params(eta0=0.7, leaf_size=64, p=8, precision=prec))
     try:
         pb.pb_mesh_upload(ctx, m.verts, m.tris, m.qpos, m.q)
-        r = pb.pb_autotune(ctx, tol=1e-4, matvecs_per_solve=10)
+        with pytest.raises(pb.PBError):
+            pb.pb_autotune(ctx, tol=1e-4, matvecs_per_solve=10, nrhs=0)
+        r = pb.pb_autotune(ctx, tol=1e-4, matvecs_per_solve=10, nrhs=nrhs)
         assert r["met_tolerance"] == 1 and r["rel_err"] <= 1e-4
         assert r["leaf_size"] in (32, 48, 64, 96, 128) and r["p"] in (4, 6, 8)
         assert r["tried"] >= 5 and r["matvec_ms"] > 0
+        # per-level orders: never above the uniform choice, never below 4, and the context's
+        # build uses them
         st = pb.pb_get_tree_stats(ctx)
-        assert all(o == r["p"] for o in st["order"][1:])
+        L = st["levels"]
+        assert list(st["order"][:L + 1]) == r["order"][:L + 1]
+        assert all(4 <= o <= r["p"] for o in r["order"][1:L + 1])
+        pb.pb_build_tree(ctx)
+        assert list(pb.pb_get_tree_stats(ctx)["order"][:L + 1]) == r["order"][:L + 1]
         # the context is left built with the choice and solves to the oracle's energy
         x = torch.zeros(2 * m.nt, device="cuda", dtype=torch.float64)
         info = pb.pb_gmres_solve(ctx, x, tol=1e-6, max_iter=300, restart=50)
