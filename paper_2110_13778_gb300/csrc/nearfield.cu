@@ -26,7 +26,8 @@
 #include "pb_internal.cuh"
 
 #define NEAR_T 128
-#define NEAR_ITEM 6  // pair tiles per warp of the mixed-precision near field
+#define NEAR_ITEM 6    // pair tiles per warp of the mixed-precision near field
+#define NEAR_ITEM_M 8  // directed tiles per warp of the several-vector near field
 
 template <class R, class PV, bool HILO>
 __global__ void __launch_bounds__(NEAR_T) k_near(int nt, const int* __restrict__ begin,
@@ -246,30 +247,34 @@ __global__ void k_near_dens(int nt, const float4* __restrict__ e32p, const doubl
     dens[(size_t)nt * blockIdx.y + k] = make_float2((float)(A * x[k]), (float)(A * x[nt + k]));
 }
 
+// Work items of at most NEAR_ITEM_M directed tiles (target chunk A, source chunk B of any
+// neighbour leaf), one warp each; the item's sums are added into ys (zeroed first) with FP64
+// atomics, so that items of one target chunk may run on different warps.
 template <int NR>
-__global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nchunks, const int* __restrict__ chunk_leaf,
+__global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nitems, const int4* __restrict__ items,
+                                                    const int* __restrict__ tiles, const int* __restrict__ chunk_leaf,
                                                     const int* __restrict__ chunk_first,
-                                                    const int* __restrict__ begin, const int* __restrict__ noff,
-                                                    const int* __restrict__ nidx, const float4* __restrict__ sp,
+                                                    const int* __restrict__ begin, const float4* __restrict__ sp,
                                                     const float4* __restrict__ sn, const float4* __restrict__ sl,
                                                     const float2* __restrict__ dens, double eps_d, double kappa_d,
                                                     double* __restrict__ ys, int nvalid)
 {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (w >= nchunks) return;
-    const int c = chunk_leaf[w];
-    const int k = chunk_first[w] + lane;
+    if (w >= nitems) return;
+    const int4 item = items[w];
+    const int c = chunk_leaf[item.x];
+    const int k = chunk_first[item.x] + lane;
     const bool act = k < begin[c + 1];
-    const int kk = act ? k : chunk_first[w];
+    const int kk = act ? k : chunk_first[item.x];
     const float4 tp = sp[kk], tn = sn[kk], tl = sl[kk];
     const float eps = (float)eps_d, inv_eps = (float)(1.0 / eps_d), kappa = (float)kappa_d;
     double acc1[NR], acc2[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc1[r] = acc2[r] = 0.0;
-    for (int t = noff[c]; t < noff[c + 1]; ++t) {
-        const int c2 = nidx[t];
-        const int sb = begin[c2], se = begin[c2 + 1];
+    for (int ti = item.y; ti < item.z; ++ti) {
+        const int cb = tiles[ti];
+        const int sb = chunk_first[cb], se = min(sb + 32, begin[chunk_leaf[cb] + 1]);
         float s1[NR], s2[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) s1[r] = s2[r] = 0.f;
@@ -300,13 +305,13 @@ __global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nchunks, const i
             acc2[r] += (double)s2[r];
         }
     }
-    // densities beyond nvalid are padding of the group (finite, unused): only nvalid are written
+    // densities beyond nvalid are padding of the group (finite, unused): only nvalid are added
     if (act)
 #pragma unroll
         for (int r = 0; r < NR; ++r)
             if (r < nvalid) {
-                ys[2LL * nt * r + k] = acc1[r];
-                ys[2LL * nt * r + nt + k] = acc2[r];
+                atomicAdd(&ys[2LL * nt * r + k], acc1[r]);
+                atomicAdd(&ys[2LL * nt * r + nt + k], acc2[r]);
             }
 }
 
@@ -395,6 +400,9 @@ int pb_near_setup(pb_ctx* c)
                 if ((int)tl.size() > start) it.push_back(make_int4(a, start, (int)tl.size(), 0));
             }
         c->near_nitems = (int)it.size();
+        c->near_mitems = 0;  // the several-vector items are made on first use (pb_near_reserve)
+        c->near_mitem = nullptr;
+        c->near_mtiles = nullptr;
         c->near_items = (int4*)pb_alloc(c, sizeof(int4) * (it.size() + 1));
         c->near_tiles = (int*)pb_alloc(c, sizeof(int) * (tl.size() + 1));
         if (!c->near_items || !c->near_tiles) return pb_fail(c, PB_ERR_NOMEM, "near setup: out of memory");
@@ -446,16 +454,56 @@ template <int NR>
 static void near_multi_launch(pb_ctx* c, const float2* dens, double* ys, double eps, int nvalid)
 {
     const PbLevel& lv = c->lev[c->L];
-    k_near32m<NR><<<(c->nchunks * 32 + 255) / 256, 256, 0, c->st>>>(c->nt, c->nchunks, c->chunk_leaf,
-                                                                     c->chunk_first, lv.begin, lv.near_off,
-                                                                     lv.near_idx, c->e32p, c->e32n, c->e32l, dens, eps,
-                                                                     c->prm.kappa, ys, nvalid);
+    k_near32m<NR><<<(c->near_mitems * 32 + 255) / 256, 256, 0, c->st>>>(
+        c->nt, c->near_mitems, c->near_mitem, c->near_mtiles, c->chunk_leaf, c->chunk_first, lv.begin, c->e32p,
+        c->e32n, c->e32l, dens, eps, c->prm.kappa, ys, nvalid);
 }
 
 // density buffer of the multi-vector near field (build lifetime, grown on demand)
+// directed tiles for the several-vector kernel: every chunk of every neighbour leaf, cut into
+// work items of at most NEAR_ITEM_M tiles of one target chunk
+static int near_multi_items(pb_ctx* c)
+{
+    const PbLevel& lv = c->lev[c->L];
+    const std::vector<int>& b = c->h_leaf_begin;
+    const std::vector<int>& no = c->h_near_off;
+    const std::vector<int>& ni = c->h_near_idx;
+    std::vector<int> first_chunk(lv.ncl + 1, 0);
+    for (int k = 0; k < lv.ncl; ++k) first_chunk[k + 1] = first_chunk[k] + (b[k + 1] - b[k] + 31) / 32;
+    std::vector<int>& tm = c->h_up_i[5];
+    std::vector<int4>& im = c->h_up_i4m;
+    tm.clear();
+    im.clear();
+    for (int k = 0; k < lv.ncl; ++k)
+        for (int a = first_chunk[k]; a < first_chunk[k + 1]; ++a) {
+            int start = (int)tm.size();
+            for (int t = no[k]; t < no[k + 1]; ++t)
+                for (int bq = first_chunk[ni[t]]; bq < first_chunk[ni[t] + 1]; ++bq) {
+                    tm.push_back(bq);
+                    if ((int)tm.size() - start == NEAR_ITEM_M) {
+                        im.push_back(make_int4(a, start, (int)tm.size(), 0));
+                        start = (int)tm.size();
+                    }
+                }
+            if ((int)tm.size() > start) im.push_back(make_int4(a, start, (int)tm.size(), 0));
+        }
+    c->near_mitems = (int)im.size();
+    c->near_mitem = (int4*)pb_alloc(c, sizeof(int4) * (im.size() + 1));
+    c->near_mtiles = (int*)pb_alloc(c, sizeof(int) * (tm.size() + 1));
+    if (!c->near_mitem || !c->near_mtiles) return pb_fail(c, PB_ERR_NOMEM, "near setup: out of memory");
+    PB_CUDA(c, cudaMemcpyAsync(c->near_mitem, im.data(), sizeof(int4) * im.size(), cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(c->near_mtiles, tm.data(), sizeof(int) * tm.size(), cudaMemcpyHostToDevice, c->st));
+    return PB_OK;
+}
+
 int pb_near_reserve(pb_ctx* c, int nr)
 {
-    if (c->prm.precision != PB_MIXED || nr < 2 || nr <= c->dens_nr) return PB_OK;
+    if (c->prm.precision != PB_MIXED || nr < 2) return PB_OK;
+    if (!c->near_mitem) {
+        int rc = near_multi_items(c);
+        if (rc) return rc;
+    }
+    if (nr <= c->dens_nr) return PB_OK;
     nr = (nr + 15) / 16 * 16;  // groups read whole padded widths
     c->near_dens = (float2*)pb_alloc(c, sizeof(float2) * (size_t)c->nt * nr);
     if (!c->near_dens) return pb_fail(c, PB_ERR_NOMEM, "near field: out of memory");
@@ -480,6 +528,7 @@ int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr)
     if (rc0) return rc0;
     k_near_dens<<<dim3((nt + 255) / 256, nr), 256, 0, c->st>>>(nt, c->e32p, xs, c->near_dens);
     PB_LAUNCH(c);
+    PB_CUDA(c, cudaMemsetAsync(ys, 0, sizeof(double) * 2 * (size_t)nt * nr, c->st));
     // groups of up to 16 right-hand sides, each one launch of the smallest width that holds it
     // (the density buffer is padded to a multiple of 16 vectors)
     for (int r0 = 0; r0 < nr;) {

@@ -102,6 +102,9 @@ struct pb_ctx {
     int near_nitems = 0;          // work items of the pair-tile near field
     int4* near_items = nullptr;   // (target chunk, first tile, end tile, 0)
     int* near_tiles = nullptr;    // source chunk of each tile
+    int near_mitems = 0;          // work items of the several-vector near field (directed tiles)
+    int4* near_mitem = nullptr;
+    int* near_mtiles = nullptr;
     float4* near_sp = nullptr;  // (x_hi, y_hi, z_hi, A phi)
     float4* near_sn = nullptr;  // (n_x, n_y, n_z, A dphi)
     float2* near_dens = nullptr; // [dens_nr][nt] (A phi, A dphi) for several right-hand sides
@@ -121,8 +124,8 @@ struct pb_ctx {
     // host copies made by the build: the leaf ranges (read back once by the tree build), and
     // the sources of the build's host-to-device uploads, kept until the next build so that
     // those copies need no synchronisation
-    std::vector<int> h_leaf_begin, h_near_off, h_near_idx, h_up_i[5];
-    std::vector<int4> h_up_i4;
+    std::vector<int> h_leaf_begin, h_near_off, h_near_idx, h_up_i[6];
+    std::vector<int4> h_up_i4, h_up_i4m;
     std::vector<long long> h_up_l;
     std::vector<double> h_up_d;
     std::vector<float2> h_up_f2;
