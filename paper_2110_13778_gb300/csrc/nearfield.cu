@@ -249,7 +249,9 @@ __global__ void k_near_dens(int nt, const float4* __restrict__ e32p, const doubl
 
 // Work items of at most NEAR_ITEM_M directed tiles (target chunk A, source chunk B of any
 // neighbour leaf), one warp each; the item's sums are added into ys (zeroed first) with FP64
-// atomics, so that items of one target chunk may run on different warps.
+// atomics, so that items of one target chunk may run on different warps. Each tile's source
+// records and its NR densities are staged in shared memory by coalesced loads (one per lane
+// and record), so the pair loop reads them as shared-memory broadcasts.
 template <int NR>
 __global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nitems, const int4* __restrict__ items,
                                                     const int* __restrict__ tiles, const int* __restrict__ chunk_leaf,
@@ -259,8 +261,16 @@ __global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nitems, const in
                                                     const float2* __restrict__ dens, double eps_d, double kappa_d,
                                                     double* __restrict__ ys, int nvalid)
 {
+    // dynamic shared memory (near32m_smem<NR>()): per warp the tile's source records, its NR
+    // densities, and the item's FP64 sums (kept here rather than in registers)
+    extern __shared__ __align__(16) unsigned char nsm[];
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    float4* s_p = (float4*)nsm + wi * 32;
+    float4* s_n = (float4*)nsm + 256 + wi * 32;
+    float4* s_l = (float4*)nsm + 512 + wi * 32;
+    float2* s_d = (float2*)((float4*)nsm + 768) + wi * NR * 32;
+    double* s_acc = (double*)((float2*)((float4*)nsm + 768) + 8 * NR * 32) + wi * 2 * NR * 32;
     if (w >= nitems) return;
     const int4 item = items[w];
     const int c = chunk_leaf[item.x];
@@ -269,18 +279,29 @@ __global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nitems, const in
     const int kk = act ? k : chunk_first[item.x];
     const float4 tp = sp[kk], tn = sn[kk], tl = sl[kk];
     const float eps = (float)eps_d, inv_eps = (float)(1.0 / eps_d), kappa = (float)kappa_d;
-    double acc1[NR], acc2[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc1[r] = acc2[r] = 0.0;
+    for (int r = 0; r < 2 * NR; ++r) s_acc[r * 32 + lane] = 0.0;
     for (int ti = item.y; ti < item.z; ++ti) {
         const int cb = tiles[ti];
         const int sb = chunk_first[cb], se = min(sb + 32, begin[chunk_leaf[cb] + 1]);
+        const int nb = se - sb;
+        __syncwarp();
+        if (lane < nb) {
+            const int j = sb + lane;
+            s_p[lane] = sp[j];
+            s_n[lane] = sn[j];
+            s_l[lane] = sl[j];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) s_d[r * 32 + lane] = dens[(size_t)nt * r + j];
+        }
+        __syncwarp();
         float s1[NR], s2[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) s1[r] = s2[r] = 0.f;
 #pragma unroll 2
-        for (int j = sb; j < se; ++j) {
-            const float4 a = sp[j], b = sn[j], l = sl[j];
+        for (int q = 0; q < nb; ++q) {
+            const int j = sb + q;
+            const float4 a = s_p[q], b = s_n[q], l = s_l[q];
             float K[4];
             float dx = (tp.x - a.x) + (tl.x - l.x);
             float dy = (tp.y - a.y) + (tl.y - l.y);
@@ -294,15 +315,15 @@ __global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nitems, const in
             K[3] *= z;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                const float2 d = dens[(size_t)nt * r + j];
+                const float2 d = s_d[r * 32 + q];
                 s1[r] = fmaf(K[0], d.y, fmaf(K[1], d.x, s1[r]));
                 s2[r] = fmaf(K[2], d.y, fmaf(K[3], d.x, s2[r]));
             }
         }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            acc1[r] += (double)s1[r];
-            acc2[r] += (double)s2[r];
+            s_acc[r * 32 + lane] += (double)s1[r];
+            s_acc[(NR + r) * 32 + lane] += (double)s2[r];
         }
     }
     // densities beyond nvalid are padding of the group (finite, unused): only nvalid are added
@@ -310,8 +331,8 @@ __global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nitems, const in
 #pragma unroll
         for (int r = 0; r < NR; ++r)
             if (r < nvalid) {
-                atomicAdd(&ys[2LL * nt * r + k], acc1[r]);
-                atomicAdd(&ys[2LL * nt * r + nt + k], acc2[r]);
+                atomicAdd(&ys[2LL * nt * r + k], s_acc[r * 32 + lane]);
+                atomicAdd(&ys[2LL * nt * r + nt + k], s_acc[(NR + r) * 32 + lane]);
             }
 }
 
@@ -451,15 +472,24 @@ int pb_corr_apply(pb_ctx* c, const double* xs, double* ys, int nr, const double*
 }
 
 template <int NR>
-static void near_multi_launch(pb_ctx* c, const float2* dens, double* ys, double eps, int nvalid)
+static constexpr size_t near32m_smem()
 {
-    const PbLevel& lv = c->lev[c->L];
-    k_near32m<NR><<<(c->near_mitems * 32 + 255) / 256, 256, 0, c->st>>>(
-        c->nt, c->near_mitems, c->near_mitem, c->near_mtiles, c->chunk_leaf, c->chunk_first, lv.begin, c->e32p,
-        c->e32n, c->e32l, dens, eps, c->prm.kappa, ys, nvalid);
+    return 768 * sizeof(float4) + 8 * NR * 32 * sizeof(float2) + 8 * 2 * NR * 32 * sizeof(double);
 }
 
-// density buffer of the multi-vector near field (build lifetime, grown on demand)
+template <int NR>
+static int near_multi_launch(pb_ctx* c, const float2* dens, double* ys, double eps, int nvalid)
+{
+    const PbLevel& lv = c->lev[c->L];
+    PB_CUDA(c, cudaFuncSetAttribute(k_near32m<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)near32m_smem<NR>()));
+    k_near32m<NR><<<(c->near_mitems * 32 + 255) / 256, 256, near32m_smem<NR>(), c->st>>>(
+        c->nt, c->near_mitems, c->near_mitem, c->near_mtiles, c->chunk_leaf, c->chunk_first, lv.begin, c->e32p,
+        c->e32n, c->e32l, dens, eps, c->prm.kappa, ys, nvalid);
+    PB_LAUNCH(c);
+    return PB_OK;
+}
+
 // directed tiles for the several-vector kernel: every chunk of every neighbour leaf, cut into
 // work items of at most NEAR_ITEM_M tiles of one target chunk
 static int near_multi_items(pb_ctx* c)
@@ -496,6 +526,8 @@ static int near_multi_items(pb_ctx* c)
     return PB_OK;
 }
 
+// density buffer of the multi-vector near field and its work items (build lifetime, grown on
+// demand)
 int pb_near_reserve(pb_ctx* c, int nr)
 {
     if (c->prm.precision != PB_MIXED || nr < 2) return PB_OK;
@@ -536,12 +568,12 @@ int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr)
         const int g = v > 8 ? 16 : v > 4 ? 8 : v > 2 ? 4 : v > 1 ? 2 : 1;
         const float2* d = c->near_dens + (size_t)nt * r0;
         double* y = ys + 2LL * nt * r0;
-        if (g == 16) near_multi_launch<16>(c, d, y, eps, v);
-        else if (g == 8) near_multi_launch<8>(c, d, y, eps, v);
-        else if (g == 4) near_multi_launch<4>(c, d, y, eps, v);
-        else if (g == 2) near_multi_launch<2>(c, d, y, eps, v);
-        else near_multi_launch<1>(c, d, y, eps, v);
-        PB_LAUNCH(c);
+        const int rc = g == 16  ? near_multi_launch<16>(c, d, y, eps, v)
+                       : g == 8 ? near_multi_launch<8>(c, d, y, eps, v)
+                       : g == 4 ? near_multi_launch<4>(c, d, y, eps, v)
+                       : g == 2 ? near_multi_launch<2>(c, d, y, eps, v)
+                                : near_multi_launch<1>(c, d, y, eps, v);
+        if (rc) return rc;
         r0 += v;
     }
     k_near_finish<<<dim3((nt + 255) / 256, nr), 256, 0, c->st>>>(nt, c->e64p, xs, eps, ys);
