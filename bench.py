@@ -257,10 +257,9 @@ FLOPS_PER_SS_POINT = 100  # FP64 formula count of one Sauter-Schwab point (maps,
 # ff_add 11, ff_mul 7, ff_sqr 7, ff_rsqrt 25, the screening series 122, the six kernel parts 350
 # (228 for the two of identical triangles), plus the point's x - y, r^2, projections and sums.
 FF_INST_PER_SS_POINT = {1: 734, 2: 662, 3: 382}
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the same kernel build, or None
-# k_near_tile: 5.35 MB read at 81920 triangles (captured on this workload); k_singular_ff: 5.25 MB
-# read at 20480 triangles, scaled by the quadrature points (x 4) to the 81920-triangle launch
-TRAFFIC_BYTES = {"near": 5.35e6, "m2l": None, "singular": 2.1e7, "pcbuild": None}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the same kernel build, or None,
+# both captured on this workload (81920 triangles): k_near_tile 5.79 MB, k_singular_ff1 20.73 MB
+TRAFFIC_BYTES = {"near": 5.79e6, "m2l": None, "singular": 2.073e7, "pcbuild": None}
 
 
 def phase_roofline(name, tv, stats, N, a, prec, pk):
