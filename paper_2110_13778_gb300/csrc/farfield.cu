@@ -119,10 +119,16 @@ __global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restr
 }
 
 // ---------- step 3: MtM, children (order pc) into parent (order pp) ----------
-// One block per parent; work items (child, parent multi-index) are spread over the threads,
-// each child's contribution lands in its own shared-memory row and the rows are added in
-// child order, so the result does not depend on thread scheduling.
+// With t = x_child - x_parent, M_parent[a] = sum_{b <= a} C(a, b) t^(a - b) M_child[b]. Divided
+// by a!, and with the child's moments divided by b!, the weights become e[a - b] = t^(a - b) /
+// (a - b)!, a product of one factor per axis, so the sum over b <= a is three one-dimensional
+// shifts: along x, then y, then z (at most p + 1 terms each instead of up to
+// (a1 + 1)(a2 + 1)(a3 + 1)). One block per parent; thread q owns the multi-indices q, q + 256;
+// children are taken one after the other in child order, so the result does not depend on
+// scheduling. All intermediate arrays use the layout of degree <= pp.
 #define M2M_T 256
+__device__ __forceinline__ double far_inv_fact(int k) { return 1.0 / c_fact[k]; }
+
 template <class R>
 __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __restrict__ cbeg,
                                                const double* __restrict__ xp, const double* __restrict__ xch,
@@ -133,61 +139,101 @@ __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __rest
     ck += blockIdx.y * cstr;
     s0 += blockIdx.y * pstr;
     sk += blockIdx.y * pstr;
-    __shared__ R tp[8][3][PB_PMAX + 1];
-    __shared__ R sbin[PB_PMAX + 1][PB_PMAX + 1];  // binomials, read with thread-dependent indices
-    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ R e[3][PB_PMAX + 1];
+    extern __shared__ __align__(16) unsigned char dsm[];
     const int Tp = pb_nterms(pp), Tc = pb_nterms(pc);
-    R* part0 = (R*)dsm;       // [8][Tp]
-    R* partk = part0 + 8 * Tp;
-    R* cm0 = partk + 8 * Tp;  // [8][Tc] the children's moments, staged once
-    R* cmk = cm0 + 8 * Tc;
-    for (int t = threadIdx.x; t < (PB_PMAX + 1) * (PB_PMAX + 1); t += blockDim.x)
-        sbin[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)] = (R)c_binom[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)];
+    R* A0 = (R*)dsm;  // [Tp] each
+    R* Ak = A0 + Tp;
+    R* B0 = Ak + Tp;
+    R* Bk = B0 + Tp;
     const int c = blockIdx.x;
     const int cb = cbeg[c], nch = min(cbeg[c + 1] - cb, 8);
-    for (int t = threadIdx.x; t < 3 * nch; t += blockDim.x) {
-        const int ch = t / 3, a = t % 3;
-        R v = 1, d = (R)(xch[3 * (cb + ch) + a] - xp[3 * c + a]);
-        for (int k = 0; k <= pp; ++k) {
-            tp[ch][a][k] = v;
-            v *= d;
-        }
+    int xi[2][3];
+    bool own[2];
+    R acc0[2] = {0, 0}, acck[2] = {0, 0};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int q = threadIdx.x + r * M2M_T;
+        own[r] = q < Tp;
+        mi_unpack(c_mi[own[r] ? q : 0], xi[r][0], xi[r][1], xi[r][2]);
     }
-    for (int t = threadIdx.x; t < nch * Tc; t += blockDim.x) {
-        cm0[t] = c0[(size_t)cb * Tc + t];
-        cmk[t] = ck[(size_t)cb * Tc + t];
-    }
-    __syncthreads();
-    for (int w = threadIdx.x; w < nch * Tp; w += M2M_T) {
-        const int ch = w / Tp, al = w - ch * Tp;
-        int a1, a2, a3;
-        mi_unpack(c_mi[al], a1, a2, a3);
-        const R* m0 = cm0 + ch * Tc;
-        const R* mk = cmk + ch * Tc;
-        R v0 = 0, vk = 0;
-        for (int b1 = 0; b1 <= a1; ++b1)
-            for (int b2 = 0; b2 <= a2; ++b2) {
-                const R w12 = sbin[a1][b1] * sbin[a2][b2] * tp[ch][0][a1 - b1] * tp[ch][1][a2 - b2];
-                const int b3max = min(a3, pc - b1 - b2);
-                for (int b3 = 0; b3 <= b3max; ++b3) {
-                    const R wgt = w12 * sbin[a3][b3] * tp[ch][2][a3 - b3];
-                    const int pos = pb_midx(b1, b2, b3);
-                    v0 += wgt * m0[pos];
-                    vk += wgt * mk[pos];
-                }
+    for (int ch = 0; ch < nch; ++ch) {
+        __syncthreads();  // the previous child's last pass has read A
+        if (threadIdx.x < 3) {
+            const int d = threadIdx.x;
+            const R t = (R)(xch[3 * (cb + ch) + d] - xp[3 * c + d]);
+            R v = 1;
+            for (int k = 0; k <= pp; ++k) {
+                e[d][k] = v * (R)far_inv_fact(k);
+                v *= t;
             }
-        part0[ch * Tp + al] = v0;
-        partk[ch * Tp + al] = vk;
-    }
-    __syncthreads();
-    for (int al = threadIdx.x; al < Tp; al += M2M_T) {
-        R v0 = 0, vk = 0;
-        for (int ch = 0; ch < nch; ++ch) {
-            v0 += part0[ch * Tp + al];
-            vk += partk[ch * Tp + al];
         }
-        s0[(size_t)c * Tp + al] = v0;
-        sk[(size_t)c * Tp + al] = vk;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int q = threadIdx.x + r * M2M_T;
+            if (!own[r]) continue;
+            // child moments exist up to degree pc (the layouts of degree <= pc and <= pp agree on
+            // their common prefix)
+            const R f = sizeof(R) == 4 ? (R)c_ifact[q] : (R)c_ifact64[q];
+            A0[q] = q < Tc ? c0[(size_t)(cb + ch) * Tc + q] * f : R(0);
+            Ak[q] = q < Tc ? ck[(size_t)(cb + ch) * Tc + q] * f : R(0);
+        }
+        __syncthreads();
+        // x: B[x1, x2, x3] = sum_{b1 <= x1} e_x[x1 - b1] A[b1, x2, x3]
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (!own[r]) continue;
+            const int x1 = xi[r][0], x2 = xi[r][1], x3 = xi[r][2];
+            R v0 = 0, vk = 0;
+            for (int b1 = 0; b1 <= x1; ++b1) {
+                const int q = pb_midx(b1, x2, x3);
+                const R w = e[0][x1 - b1];
+                v0 += w * A0[q];
+                vk += w * Ak[q];
+            }
+            B0[threadIdx.x + r * M2M_T] = v0;
+            Bk[threadIdx.x + r * M2M_T] = vk;
+        }
+        __syncthreads();
+        // y: A[x1, x2, x3] = sum_{b2 <= x2} e_y[x2 - b2] B[x1, b2, x3]
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (!own[r]) continue;
+            const int x1 = xi[r][0], x2 = xi[r][1], x3 = xi[r][2];
+            R v0 = 0, vk = 0;
+            for (int b2 = 0; b2 <= x2; ++b2) {
+                const int q = pb_midx(x1, b2, x3);
+                const R w = e[1][x2 - b2];
+                v0 += w * B0[q];
+                vk += w * Bk[q];
+            }
+            A0[threadIdx.x + r * M2M_T] = v0;
+            Ak[threadIdx.x + r * M2M_T] = vk;
+        }
+        __syncthreads();
+        // z: the parent's scaled moment gains sum_{b3 <= x3} e_z[x3 - b3] A[x1, x2, b3]
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (!own[r]) continue;
+            const int x1 = xi[r][0], x2 = xi[r][1], x3 = xi[r][2];
+            R v0 = 0, vk = 0;
+            for (int b3 = 0; b3 <= x3; ++b3) {
+                const int q = pb_midx(x1, x2, b3);
+                const R w = e[2][x3 - b3];
+                v0 += w * A0[q];
+                vk += w * Ak[q];
+            }
+            acc0[r] += v0;
+            acck[r] += vk;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int q = threadIdx.x + r * M2M_T;
+        if (!own[r]) continue;
+        const R f = (R)(c_fact[xi[r][0]] * c_fact[xi[r][1]] * c_fact[xi[r][2]]);
+        s0[(size_t)c * Tp + q] = acc0[r] * f;
+        sk[(size_t)c * Tp + q] = acck[r] * f;
     }
 }
 
@@ -671,6 +717,10 @@ __global__ void __launch_bounds__(32) k_m2l_chunks(int ncl, const int* __restric
 }
 
 // ---------- step 5: LtL, parent (order pp) into child (order pc) ----------
+// With t = x_child - x_parent, L_child[b] += sum_g C(b + g, b) t^g L_parent[b + g]. With the
+// scaled coefficients L^[a] = a! L[a] the weights become t^g / g!, one factor per axis, so the
+// sum is three one-dimensional shifts (x, then y, then z), each over the indices above b on
+// its axis. One block per child cluster; intermediate arrays in the layout of degree <= pp.
 template <class R>
 __global__ void __launch_bounds__(FAR_T) k_l2l(int pp, int pc, const int* __restrict__ parent,
                                                const double* __restrict__ xp, const double* __restrict__ xch,
@@ -681,46 +731,72 @@ __global__ void __launch_bounds__(FAR_T) k_l2l(int pp, int pc, const int* __rest
     lpk += blockIdx.y * pstr;
     lc0 += blockIdx.y * cstr;
     lck += blockIdx.y * cstr;
-    __shared__ R tp[3][PB_PMAX + 1];
-    __shared__ R sbin[PB_PMAX + 1][PB_PMAX + 1];  // binomials, read with thread-dependent indices
-    for (int t = threadIdx.x; t < (PB_PMAX + 1) * (PB_PMAX + 1); t += blockDim.x)
-        sbin[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)] = (R)c_binom[t / (PB_PMAX + 1)][t % (PB_PMAX + 1)];
+    __shared__ R e[3][PB_PMAX + 1];
+    __shared__ R A0[NT_MAX], Ak[NT_MAX], B0[NT_MAX], Bk[NT_MAX];
     const int c = blockIdx.x;
     const int P = parent[c];
     const int Tp = pb_nterms(pp), Tc = pb_nterms(pc);
     if (threadIdx.x < 3) {
-        R t = (R)(xch[3 * c + threadIdx.x] - xp[3 * P + threadIdx.x]);
+        const int d = threadIdx.x;
+        const R t = (R)(xch[3 * c + d] - xp[3 * P + d]);
         R v = 1;
         for (int k = 0; k <= pp; ++k) {
-            tp[threadIdx.x][k] = v;
+            e[d][k] = v * (R)far_inv_fact(k);
             v *= t;
         }
     }
-    __syncthreads();
-    __shared__ R pm0[NT_MAX], pmk[NT_MAX];
-    for (int t = threadIdx.x; t < Tp; t += FAR_T) {
-        pm0[t] = lp0[(size_t)P * Tp + t];
-        pmk[t] = lpk[(size_t)P * Tp + t];
+    for (int q = threadIdx.x; q < Tp; q += FAR_T) {
+        int a1, a2, a3;
+        mi_unpack(c_mi[q], a1, a2, a3);
+        const R f = (R)(c_fact[a1] * c_fact[a2] * c_fact[a3]);
+        A0[q] = lp0[(size_t)P * Tp + q] * f;
+        Ak[q] = lpk[(size_t)P * Tp + q] * f;
     }
     __syncthreads();
-    const R* m0 = pm0;
-    const R* mk = pmk;
-    for (int be = threadIdx.x; be < Tc; be += FAR_T) {
-        int b1, b2, b3;
-        mi_unpack(c_mi[be], b1, b2, b3);
-        int ng = pb_nterms(pp - (b1 + b2 + b3));
+    // x: B[b1, x2, x3] = sum_{a1 >= b1, a1 + x2 + x3 <= pp} e_x[a1 - b1] A[a1, x2, x3]
+    for (int q = threadIdx.x; q < Tp; q += FAR_T) {
+        int x1, x2, x3;
+        mi_unpack(c_mi[q], x1, x2, x3);
         R v0 = 0, vk = 0;
-        for (int g = 0; g < ng; ++g) {
-            int g1, g2, g3;
-            mi_unpack(c_mi[g], g1, g2, g3);
-            R w = sbin[b1 + g1][b1] * sbin[b2 + g2][b2] * sbin[b3 + g3][b3] * tp[0][g1] * tp[1][g2] *
-                  tp[2][g3];
-            int pos = pb_midx(b1 + g1, b2 + g2, b3 + g3);
-            v0 += w * m0[pos];
-            vk += w * mk[pos];
+        for (int a1 = x1; a1 + x2 + x3 <= pp; ++a1) {
+            const int s = pb_midx(a1, x2, x3);
+            const R w = e[0][a1 - x1];
+            v0 += w * A0[s];
+            vk += w * Ak[s];
         }
-        lc0[(size_t)c * Tc + be] += v0;
-        lck[(size_t)c * Tc + be] += vk;
+        B0[q] = v0;
+        Bk[q] = vk;
+    }
+    __syncthreads();
+    // y: A[x1, b2, x3] = sum_{a2 >= b2} e_y[a2 - b2] B[x1, a2, x3]
+    for (int q = threadIdx.x; q < Tp; q += FAR_T) {
+        int x1, x2, x3;
+        mi_unpack(c_mi[q], x1, x2, x3);
+        R v0 = 0, vk = 0;
+        for (int a2 = x2; x1 + a2 + x3 <= pp; ++a2) {
+            const int s = pb_midx(x1, a2, x3);
+            const R w = e[1][a2 - x2];
+            v0 += w * B0[s];
+            vk += w * Bk[s];
+        }
+        A0[q] = v0;
+        Ak[q] = vk;
+    }
+    __syncthreads();
+    // z, then unscale by 1/b! into the child's coefficients (degree <= pc)
+    for (int q = threadIdx.x; q < Tc; q += FAR_T) {
+        int x1, x2, x3;
+        mi_unpack(c_mi[q], x1, x2, x3);
+        R v0 = 0, vk = 0;
+        for (int a3 = x3; x1 + x2 + a3 <= pp; ++a3) {
+            const int s = pb_midx(x1, x2, a3);
+            const R w = e[2][a3 - x3];
+            v0 += w * A0[s];
+            vk += w * Ak[s];
+        }
+        const R f = sizeof(R) == 4 ? (R)c_ifact[q] : (R)c_ifact64[q];
+        lc0[(size_t)c * Tc + q] += v0 * f;
+        lck[(size_t)c * Tc + q] += vk * f;
     }
 }
 
@@ -989,7 +1065,7 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream
     for (int l = L - 1; l >= lmin; --l) {
         PbLevel& lv = c->lev[l];
         PbLevel& ch = c->lev[l + 1];
-        const size_t msm = 2 * 8 * ((size_t)pb_nterms(lv.p) + pb_nterms(ch.p)) * sizeof(R);
+        const size_t msm = 4 * (size_t)pb_nterms(lv.p) * sizeof(R);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm));
         k_m2m<R><<<dim3(lv.ncl, nr), M2M_T, msm, st>>>(lv.p, ch.p, lv.cbeg, lv.xc, ch.xc, (R*)ch.sig0,
                                                         (R*)ch.sigk, (R*)lv.sig0, (R*)lv.sigk, sstr(ch), sstr(lv));
