@@ -47,6 +47,9 @@ __device__ __forceinline__ void mi_unpack(int v, int& a, int& b, int& c)
 }
 
 // ---------- step 2: leaf moments ----------
+// Stored form of every moment array: m~[b] = (-1)^|b| m[b] / b!, the form the MtL contraction
+// uses (eqcoeff), so that MtL reads the moments as they are and MtM is a plain shift.
+// With d' = x_c - y (cluster centre minus source point), (-1)^|b| (y - x_c)^b = d'^b.
 template <class R>
 __global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restrict__ begin,
                                                const double* __restrict__ xc, const double4_32a* __restrict__ ep,
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restr
         if (threadIdx.x < ns) {
             int j = s0 + threadIdx.x;
             double4_32a P = ep[j], Nn = en[j];
-            R d[3] = {(R)(P.x - cx), (R)(P.y - cy), (R)(P.z - cz)};
+            R d[3] = {(R)(cx - P.x), (R)(cy - P.y), (R)(cz - P.z)};
             for (int a = 0; a < 3; ++a) {
                 R v = 1;
                 for (int k = 0; k <= p; ++k) {
@@ -101,9 +104,10 @@ __global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restr
                 if (a) dm += sn[q][0] * (R)a * pw[q][0][a - 1] * my * mz;
                 if (bb) dm += sn[q][1] * (R)bb * mx * pw[q][1][bb - 1] * mz;
                 if (cc) dm += sn[q][2] * (R)cc * mx * my * pw[q][2][cc - 1];
+                // with d' = -d the normal derivative of the monomial changes sign once more
                 R wphi = sw[q][0], wdphi = sw[q][1];
-                s0v += wdphi * mono - wphi * dm;
-                skv += -wdphi * mono + (R)eps * wphi * dm;
+                s0v += wdphi * mono + wphi * dm;
+                skv += -wdphi * mono - (R)eps * wphi * dm;
             }
             acc0[r] += s0v;
             acck[r] += skv;
@@ -113,16 +117,17 @@ __global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restr
     for (int r = 0; r < 4; ++r) {
         int al = threadIdx.x + r * FAR_T;
         if (al >= T) continue;
-        sig0[(size_t)c * T + al] = acc0[r];
-        sigk[(size_t)c * T + al] = acck[r];
+        const R f = sizeof(R) == 4 ? (R)c_ifact[al] : (R)c_ifact64[al];
+        sig0[(size_t)c * T + al] = acc0[r] * f;
+        sigk[(size_t)c * T + al] = acck[r] * f;
     }
 }
 
 // ---------- step 3: MtM, children (order pc) into parent (order pp) ----------
-// With t = x_child - x_parent, M_parent[a] = sum_{b <= a} C(a, b) t^(a - b) M_child[b]. Divided
-// by a!, and with the child's moments divided by b!, the weights become e[a - b] = t^(a - b) /
-// (a - b)!, a product of one factor per axis, so the sum over b <= a is three one-dimensional
-// shifts: along x, then y, then z (at most p + 1 terms each instead of up to
+// With t = x_child - x_parent, M_parent[a] = sum_{b <= a} C(a, b) t^(a - b) M_child[b]. In the
+// stored form m~ = (-1)^|b| M / b! this is m~_parent[a] = sum_{b <= a} e[a - b] m~_child[b] with
+// e[g] = (-t)^g / g!, a product of one factor per axis, so the sum over b <= a is three
+// one-dimensional shifts: along x, then y, then z (at most p + 1 terms each instead of up to
 // (a1 + 1)(a2 + 1)(a3 + 1)). One block per parent; thread q owns the multi-indices q, q + 256;
 // children are taken one after the other in child order, so the result does not depend on
 // scheduling. All intermediate arrays use the layout of degree <= pp.
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __rest
         __syncthreads();  // the previous child's last pass has read A
         if (threadIdx.x < 3) {
             const int d = threadIdx.x;
-            const R t = (R)(xch[3 * (cb + ch) + d] - xp[3 * c + d]);
+            const R t = (R)(xp[3 * c + d] - xch[3 * (cb + ch) + d]);  // -(x_child - x_parent)
             R v = 1;
             for (int k = 0; k <= pp; ++k) {
                 e[d][k] = v * (R)far_inv_fact(k);
@@ -174,9 +179,8 @@ __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __rest
             if (!own[r]) continue;
             // child moments exist up to degree pc (the layouts of degree <= pc and <= pp agree on
             // their common prefix)
-            const R f = sizeof(R) == 4 ? (R)c_ifact[q] : (R)c_ifact64[q];
-            A0[q] = q < Tc ? c0[(size_t)(cb + ch) * Tc + q] * f : R(0);
-            Ak[q] = q < Tc ? ck[(size_t)(cb + ch) * Tc + q] * f : R(0);
+            A0[q] = q < Tc ? c0[(size_t)(cb + ch) * Tc + q] : R(0);
+            Ak[q] = q < Tc ? ck[(size_t)(cb + ch) * Tc + q] : R(0);
         }
         __syncthreads();
         // x: B[x1, x2, x3] = sum_{b1 <= x1} e_x[x1 - b1] A[b1, x2, x3]
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __rest
             Ak[threadIdx.x + r * M2M_T] = vk;
         }
         __syncthreads();
-        // z: the parent's scaled moment gains sum_{b3 <= x3} e_z[x3 - b3] A[x1, x2, b3]
+        // z: the parent's moment gains sum_{b3 <= x3} e_z[x3 - b3] A[x1, x2, b3]
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             if (!own[r]) continue;
@@ -231,9 +235,8 @@ __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __rest
     for (int r = 0; r < 2; ++r) {
         const int q = threadIdx.x + r * M2M_T;
         if (!own[r]) continue;
-        const R f = (R)(c_fact[xi[r][0]] * c_fact[xi[r][1]] * c_fact[xi[r][2]]);
-        s0[(size_t)c * Tp + q] = acc0[r] * f;
-        sk[(size_t)c * Tp + q] = acck[r] * f;
+        s0[(size_t)c * Tp + q] = acc0[r];
+        sk[(size_t)c * Tp + q] = acck[r];
     }
 }
 
@@ -261,13 +264,10 @@ __global__ void __launch_bounds__(FAR_T) k_m2l(int p, double kappa, const int* _
         const R d2 = dx * dx + dy * dy + dz * dz;
         const R kap = (R)kappa;
         __syncthreads();
-        // source moments, scaled by (-1)^|b| / b!
+        // source moments (stored already scaled by (-1)^|b| / b!)
         for (int b = threadIdx.x; b < T; b += FAR_T) {
-            int b1, b2, b3;
-            mi_unpack(c_mi[b], b1, b2, b3);
-            R sc = (R)(((b1 + b2 + b3) & 1 ? -1.0 : 1.0) / (c_fact[b1] * c_fact[b2] * c_fact[b3]));
-            M0[b] = s0[(size_t)c2 * T + b] * sc;
-            Mk[b] = sk[(size_t)c2 * T + b] * sc;
+            M0[b] = s0[(size_t)c2 * T + b];
+            Mk[b] = sk[(size_t)c2 * T + b];
         }
         if (threadIdx.x == 0) {
             R r = sqrt(d2);
@@ -524,24 +524,15 @@ __global__ void k_m2l_gather(int T, const int* __restrict__ ssrc, const R* __res
     sk += blockIdx.y * sstr;
     M0 += blockIdx.y * mstr;
     Mk += blockIdx.y * mstr;
-    // one block per chunk of 32 slots; thread (b, lane) pairs walk the T x 32 block. The
-    // factors (-1)^|b| / b! are formed once per block.
-    __shared__ R scs[NT_MAX];
-    for (int b = threadIdx.x; b < T; b += blockDim.x) {
-        int b1, b2, b3;
-        mi_unpack(c_mi[b], b1, b2, b3);
-        const R f = sizeof(R) == 4 ? (R)c_ifact[b] : (R)c_ifact64[b];
-        scs[b] = (b1 + b2 + b3) & 1 ? -f : f;
-    }
-    __syncthreads();
+    // one block per chunk of 32 slots; thread (b, lane) pairs walk the T x 32 block (the
+    // moments are stored already scaled by (-1)^|b| / b!)
     const long long chunk = blockIdx.x;
     const size_t base = (size_t)chunk * T * 32;
     const int src = ssrc[chunk * 32 + (threadIdx.x & 31)];
     for (int t = threadIdx.x; t < T * 32; t += blockDim.x) {
         const int b = t >> 5;
-        const R sc = scs[b];
-        M0[base + t] = src >= 0 ? s0[(size_t)src * T + b] * sc : R(0);
-        Mk[base + t] = src >= 0 ? sk[(size_t)src * T + b] * sc : R(0);
+        M0[base + t] = src >= 0 ? s0[(size_t)src * T + b] : R(0);
+        Mk[base + t] = src >= 0 ? sk[(size_t)src * T + b] : R(0);
     }
 }
 
@@ -591,6 +582,17 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* bar, unsigned phase
         : "memory");
     return ok != 0;
 }
+// 4-byte asynchronous global -> shared copy (zero-filled when !valid: no bytes are read)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+// this thread's asynchronous copies have landed
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
 // bounded wait: gives up after PB_WAIT_LIMIT polls (each poll may itself block briefly)
 #define PB_WAIT_LIMIT (1u << 24)
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase)
@@ -601,30 +603,32 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phas
 }
 
 // FP32: one block of two warps per cluster and per kernel (G0 for blockIdx.z = 0, Gk for 1).
-// The chunk's D and M blocks arrive by TMA bulk copy into shared memory (42 KB at p = 8, so
-// five blocks share an SM and hide each other's copies), completion on an mbarrier, every
-// wait bounded. Warp w accumulates its half of the local coefficients (M2LWarp<P, w>: equal
-// FMA counts, moments held in registers a block at a time), so each slot costs about 740
-// shared-memory loads per kernel instead of one per FMA.
+// Per chunk of 32 slots, the derivative block (T x 32 floats, 21 KB at p = 8) arrives by TMA
+// bulk copy (mbarrier completion, every wait bounded) while the warps load the 32 source
+// clusters' moments straight from the level's moment array (L2-resident, stored already scaled
+// by (-1)^|b| / b!), one coalesced row per source, into shared memory rows of 33 words
+// (conflict-free in both directions): no gathered copy of the moments goes through DRAM. Warp w accumulates its half
+// of the local coefficients (M2LWarp<P, w>: equal FMA counts, moments held in registers a
+// block at a time), so each slot costs about 740 shared-memory loads per kernel.
 template <int P>
-__global__ void __launch_bounds__(64, 1) k_m2l_tma(int ncl, const int* __restrict__ soff, const float* __restrict__ D0,
-                                                   const float* __restrict__ Dk, const float* __restrict__ M0,
-                                                   const float* __restrict__ Mk, float* __restrict__ l0,
-                                                   float* __restrict__ lk, int* __restrict__ err, long long mstr,
-                                                   long long lstr)
+__global__ void __launch_bounds__(64, 1) k_m2l_tma(int ncl, const int* __restrict__ soff, const int* __restrict__ ssrc,
+                                                   const float* __restrict__ D0, const float* __restrict__ Dk,
+                                                   const float* __restrict__ s0, const float* __restrict__ sk,
+                                                   float* __restrict__ l0, float* __restrict__ lk,
+                                                   int* __restrict__ err, long long sstr)
 {
-    // right-hand side blockIdx.y: the same derivative tables, its own gathered moments
+    // right-hand side blockIdx.y: the same derivative tables, its own moments
     const int kern = blockIdx.z;
     const float* D = kern ? Dk : D0;
-    const float* M = (kern ? Mk : M0) + blockIdx.y * mstr;
-    float* out = (kern ? lk : l0) + blockIdx.y * lstr;
+    const float* sig = (kern ? sk : s0) + blockIdx.y * sstr;
+    float* out = (kern ? lk : l0) + blockIdx.y * sstr;
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
-    constexpr unsigned CH = T * 32 * sizeof(float);  // bytes of one chunk block (multiple of 16)
+    constexpr unsigned CH = T * 32 * sizeof(float);  // bytes of one derivative block (multiple of 16)
     constexpr int NL = M2LWarp<P, 0>::n > M2LWarp<P, 1>::n ? M2LWarp<P, 0>::n : M2LWarp<P, 1>::n;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) unsigned long long bar;
-    float* Ds = (float*)dsm;            // [T * 32]
-    float* Ms = Ds + T * 32;            // [T * 32]; with Ds, the reduction scratch [T * 33]
+    float* Ds = (float*)dsm;    // [T * 32]
+    float* Ms = Ds + T * 32;    // [T * 33]; with Ds, the reduction scratch [T * 33]
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int c = blockIdx.x;
     if (c >= ncl) return;
@@ -642,15 +646,23 @@ __global__ void __launch_bounds__(64, 1) k_m2l_tma(int ncl, const int* __restric
 #pragma unroll 1
     for (int k = 0; k < nch; ++k) {
         if (threadIdx.x == 0) {
-            // order the earlier shared-memory reads (generic proxy) before the copies
+            // order the earlier shared-memory reads (generic proxy) before the copy
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect(&bar, 2 * CH);
+            mbar_expect(&bar, CH);
             bulk_g2s(Ds, D + (cb + k) * T * 32, CH, &bar);
-            bulk_g2s(Ms, M + (cb + k) * T * 32, CH, &bar);
         }
+        // the moments of the chunk's sources (padding slots: zero), two rows at a time, by
+        // asynchronous copies that overlap the derivative block's copy
+        const int* src = ssrc + (cb + k) * 32;
+        for (int s = wi; s < 32; s += 2) {
+            const int j = src[s];
+            const float* row = sig + (size_t)(j < 0 ? 0 : j) * T;
+            for (int b = lane; b < T; b += 32) cp_async4(Ms + b * 33 + s, row + b, j >= 0);
+        }
+        cp_async_wait_all();
         // the block agrees on the outcome, so that no thread leaves while another waits
         if (!__syncthreads_and(mbar_wait(&bar, ph))) {
-            // a copy never completed: record it, give it a bounded time to land, and stop
+            // the copy never completed: record it, give it a bounded time to land, and stop
             if (threadIdx.x == 0) atomicExch(err, 1);
             mbar_wait(&bar, ph);
             return;
@@ -910,9 +922,11 @@ static int m2l_fast_plan(pb_ctx* c, PbLevel& lv)
     lv.slot_tgt = (int*)pb_alloc_on(c, sizeof(int) * (lv.nslots + 1), fs);
     lv.D0 = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
     lv.Dk = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
-    lv.Mg0 = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
-    lv.Mgk = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
-    if (!lv.slot_off || !lv.slot_src || !lv.slot_tgt || !lv.D0 || !lv.Dk || !lv.Mg0 || !lv.Mgk)
+    // gathered moments: the FP64 contraction only (the FP32 kernel reads the moments itself)
+    const bool gath = c->prm.precision != PB_MIXED;
+    lv.Mg0 = gath ? pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs) : nullptr;
+    lv.Mgk = gath ? pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs) : nullptr;
+    if (!lv.slot_off || !lv.slot_src || !lv.slot_tgt || !lv.D0 || !lv.Dk || (gath && (!lv.Mg0 || !lv.Mgk)))
         return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
     // (the host vectors live in the level until the next build, so no synchronisation)
     PB_CUDA(c, cudaMemcpyAsync(lv.slot_off, soff.data(), sizeof(int) * (lv.ncl + 1), cudaMemcpyHostToDevice, fs));
@@ -947,17 +961,18 @@ static int m2l_fast_launch(pb_ctx* c, PbLevel& lv, int nr, cudaStream_t st)
 {
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
     const long long sstr = (long long)lv.ncl * T, mstr = (long long)lv.nslots * T;
-    k_m2l_gather<R><<<dim3((unsigned)(lv.nslots / 32), nr), 256, 0, st>>>(
-        T, lv.slot_src, (const R*)lv.sig0, (const R*)lv.sigk, (R*)lv.Mg0, (R*)lv.Mgk, sstr, mstr);
-    PB_LAUNCH(c);
     if constexpr (sizeof(R) == sizeof(float)) {
-        size_t smem = 2 * (size_t)T * 32 * sizeof(float);
+        // the kernel reads the source moments itself: no gathered copy
+        size_t smem = (size_t)T * (32 + 33) * sizeof(float);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_tma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_tma<P><<<dim3(lv.ncl, nr, 2), 64, smem, st>>>(lv.ncl, lv.slot_off, (const float*)lv.D0,
-                                                             (const float*)lv.Dk, (const float*)lv.Mg0,
-                                                             (const float*)lv.Mgk, (float*)lv.lam0, (float*)lv.lamk,
-                                                             c->dev_err, mstr, sstr);
+        k_m2l_tma<P><<<dim3(lv.ncl, nr, 2), 64, smem, st>>>(lv.ncl, lv.slot_off, lv.slot_src, (const float*)lv.D0,
+                                                             (const float*)lv.Dk, (const float*)lv.sig0,
+                                                             (const float*)lv.sigk, (float*)lv.lam0, (float*)lv.lamk,
+                                                             c->dev_err, sstr);
     } else {
+        k_m2l_gather<R><<<dim3((unsigned)(lv.nslots / 32), nr), 256, 0, st>>>(
+            T, lv.slot_src, (const R*)lv.sig0, (const R*)lv.sigk, (R*)lv.Mg0, (R*)lv.Mgk, sstr, mstr);
+        PB_LAUNCH(c);
         size_t smem = (size_t)T * 33 * sizeof(R);
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_chunks<P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_m2l_chunks<P, R><<<dim3(lv.ncl, nr), 32, smem, st>>>(lv.ncl, lv.slot_off, (const R*)lv.D0,
@@ -968,7 +983,7 @@ static int m2l_fast_launch(pb_ctx* c, PbLevel& lv, int nr, cudaStream_t st)
     return PB_OK;
 }
 
-// moments, local coefficients and gathered moments for nr right-hand sides at once
+// moments, local coefficients (and, for FP64, gathered moments) for nr right-hand sides at once
 int pb_far_reserve(pb_ctx* c, int nr)
 {
     if (nr <= c->far_nr) return PB_OK;
@@ -981,7 +996,7 @@ int pb_far_reserve(pb_ctx* c, int nr)
         lv.lam0 = pb_alloc(c, rs * n);
         lv.lamk = pb_alloc(c, rs * n);
         if (!lv.sig0 || !lv.sigk || !lv.lam0 || !lv.lamk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");
-        if (lv.D0) {
+        if (lv.D0 && c->prm.precision != PB_MIXED) {  // gathered moments: FP64 contraction only
             lv.Mg0 = pb_alloc(c, rs * (size_t)lv.nslots * T * nr);
             lv.Mgk = pb_alloc(c, rs * (size_t)lv.nslots * T * nr);
             if (!lv.Mg0 || !lv.Mgk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");

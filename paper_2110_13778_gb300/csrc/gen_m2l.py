@@ -14,7 +14,8 @@ M2LWarp<P, W> is the register-blocked two-warp variant used by the FP32 kernel: 
 accumulates half of the local coefficients (equal FMA counts), the moments of a block of
 MBLOCK multi-indices sit in registers, and each D^gamma is loaded once per block instead of
 once per FMA, so the shared-memory loads per slot and kernel fall from 3168 to about 740
-(both warps together) at P = 8, with about 170 registers per thread and no spills.
+(both warps together) at P = 8, with about 170 registers per thread and no spills. Their
+moments are read at Ms[b * 33] (rows padded to 33 words).
 
 Run: python gen_m2l.py > m2l_unrolled.cuh  (the output is committed beside this script).
 """
@@ -29,6 +30,9 @@ GROUP = 4
 # time in registers
 NWARP = 2
 MBLOCK = {4: 35, 6: 84, 8: 84}
+# row stride of the moments in shared memory for the two-warp bodies: 33, so that the kernel
+# can write one source's moments (lanes over b) without bank conflicts
+MSTRIDE = 33
 
 
 def multi_indices(p):
@@ -108,7 +112,7 @@ def body_blocked(P, mb, aset):
             if prs:
                 work.append((g, prs))
         for k in sorted(used):
-            out.append(f"        m{k} = Ms[{blk[k] * 32}];")
+            out.append(f"        m{k} = Ms[{blk[k] * MSTRIDE}];")
         for s in range(0, len(work), GROUP):
             grp = work[s:s + GROUP]
             for k, (g, _) in enumerate(grp):
