@@ -38,6 +38,13 @@ __constant__ double c_fact[25];         // n!
 __constant__ double c_binom[13][13];    // C(n, k)
 __constant__ float c_ifact[NT_MAX];     // 1 / (a1! a2! a3!) of multi-index a (FP32)
 __constant__ double c_ifact64[NT_MAX];  // the same in FP64
+__constant__ float c_i1f[PB_PMAX + 1];  // 1 / k! (one axis), FP32
+__constant__ double c_i1d[PB_PMAX + 1]; // the same in FP64
+template <class R>
+__device__ __forceinline__ R inv_fact1(int k)
+{
+    return sizeof(R) == 4 ? (R)c_i1f[k] : (R)c_i1d[k];
+}
 
 __device__ __forceinline__ void mi_unpack(int v, int& a, int& b, int& c)
 {
@@ -50,8 +57,24 @@ __device__ __forceinline__ void mi_unpack(int v, int& a, int& b, int& c)
 // Stored form of every moment array: m~[b] = (-1)^|b| m[b] / b!, the form the MtL contraction
 // uses (eqcoeff), so that MtL reads the moments as they are and MtM is a plain shift.
 // With d' = x_c - y (cluster centre minus source point), (-1)^|b| (y - x_c)^b = d'^b.
+// With e_j[b] = d'_j^b / b! (d' = x_c - y_j, one factor per axis) the stored moments are
+//   m~0[b] = S[b] + sum_i G_i[b - e_i],   m~k[b] = -S[b] - eps sum_i G_i[b - e_i],
+//   S[b] = sum_j A_j dphi_j e_j[b],   G_i[b] = sum_j A_j phi_j n_j,i e_j[b],
+// because the normal derivative of d'^b / b! is sum_i n_i e[b - e_i] up to the sign of d'.
+// Thread q owns the multi-indices q, q + P2M_T, ...; the sources are staged P2M_S at a time
+// with their per-axis tables d'^k / k! (one row of 3 (p + 1) values per source, so that the
+// threads of a warp, which differ in k, read different banks) and their four weights (dynamic
+// shared memory, p2m_smem bytes).
+#define P2M_T 192
+#define P2M_S 96
+#define P2M_R 3  // multi-indices per thread: nterms(12) = 455 <= 3 * 192
 template <class R>
-__global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restrict__ begin,
+static size_t p2m_smem(int p)
+{
+    return sizeof(R) * ((size_t)3 * (p + 1) * P2M_S + 4 * P2M_S);
+}
+template <class R>
+__global__ void __launch_bounds__(P2M_T) k_p2m(int nt, int p, const int* __restrict__ begin,
                                                const double* __restrict__ xc, const double4_32a* __restrict__ ep,
                                                const double4_32a* __restrict__ en, const double* __restrict__ xs,
                                                double eps, R* __restrict__ sig0, R* __restrict__ sigk,
@@ -61,65 +84,86 @@ __global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restr
     xs += blockIdx.y * xstr;
     sig0 += blockIdx.y * sstr;
     sigk += blockIdx.y * sstr;
-    __shared__ R pw[FAR_T][3][PB_PMAX + 1];
-    __shared__ R sn[FAR_T][3];
-    __shared__ R sw[FAR_T][2];
+    extern __shared__ __align__(16) unsigned char p2m_sm[];
+    R* ex = (R*)p2m_sm;                   // [P2M_S][3][p + 1]: (source, axis, power)
+    R* wt = ex + 3 * (p + 1) * P2M_S;     // [4][P2M_S]: A dphi, A phi n_x, A phi n_y, A phi n_z
     const int c = blockIdx.x;
     const int T = pb_nterms(p);
+    R* Ssh = ex;                          // after the sources: S and G_x, G_y, G_z, [4][T]
+    const int rs = 3 * (p + 1);  // row of one source
+    auto EX = [&](int a, int k, int q) -> R& { return ex[q * rs + a * (p + 1) + k]; };
     const int b = begin[c], e = begin[c + 1];
     const double cx = xc[3 * c], cy = xc[3 * c + 1], cz = xc[3 * c + 2];
-    R acc0[4] = {0, 0, 0, 0}, acck[4] = {0, 0, 0, 0};  // up to 4 multi-indices per thread
-    for (int s0 = b; s0 < e; s0 += FAR_T) {
-        int ns = min(FAR_T, e - s0);
+    int xi[P2M_R][3];
+#pragma unroll
+    for (int r = 0; r < P2M_R; ++r) {
+        const int q = threadIdx.x + r * P2M_T;
+        mi_unpack(c_mi[q < T ? q : 0], xi[r][0], xi[r][1], xi[r][2]);
+    }
+    R acc[P2M_R][4] = {};
+    for (int s0 = b; s0 < e; s0 += P2M_S) {
+        const int ns = min(P2M_S, e - s0);
         __syncthreads();
         if (threadIdx.x < ns) {
-            int j = s0 + threadIdx.x;
-            double4_32a P = ep[j], Nn = en[j];
-            R d[3] = {(R)(cx - P.x), (R)(cy - P.y), (R)(cz - P.z)};
+            const int j = s0 + threadIdx.x;
+            const double4_32a P = ep[j], Nn = en[j];
+            const R d[3] = {(R)(cx - P.x), (R)(cy - P.y), (R)(cz - P.z)};
             for (int a = 0; a < 3; ++a) {
                 R v = 1;
                 for (int k = 0; k <= p; ++k) {
-                    pw[threadIdx.x][a][k] = v;
+                    EX(a, k, threadIdx.x) = v * inv_fact1<R>(k);
                     v *= d[a];
                 }
             }
-            sn[threadIdx.x][0] = (R)Nn.x;
-            sn[threadIdx.x][1] = (R)Nn.y;
-            sn[threadIdx.x][2] = (R)Nn.z;
-            sw[threadIdx.x][0] = (R)(P.w * xs[j]);       // A phi
-            sw[threadIdx.x][1] = (R)(P.w * xs[nt + j]);  // A dphi
+            const R wphi = (R)(P.w * xs[j]), wdphi = (R)(P.w * xs[nt + j]);
+            wt[threadIdx.x] = wdphi;
+            wt[P2M_S + threadIdx.x] = wphi * (R)Nn.x;
+            wt[2 * P2M_S + threadIdx.x] = wphi * (R)Nn.y;
+            wt[3 * P2M_S + threadIdx.x] = wphi * (R)Nn.z;
         }
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int al = threadIdx.x + r * FAR_T;
-            if (al >= T) continue;
-            int a, bb, cc;
-            mi_unpack(c_mi[al], a, bb, cc);
-            R s0v = 0, skv = 0;
+        for (int r = 0; r < P2M_R; ++r) {
+            if (threadIdx.x + r * P2M_T >= T) continue;
+            const R* e1 = &EX(0, xi[r][0], 0);
+            const R* e2 = &EX(1, xi[r][1], 0);
+            const R* e3 = &EX(2, xi[r][2], 0);
+            R s = 0, g0 = 0, g1 = 0, g2 = 0;
             for (int q = 0; q < ns; ++q) {
-                R mx = pw[q][0][a], my = pw[q][1][bb], mz = pw[q][2][cc];
-                R mono = mx * my * mz;
-                R dm = 0;
-                if (a) dm += sn[q][0] * (R)a * pw[q][0][a - 1] * my * mz;
-                if (bb) dm += sn[q][1] * (R)bb * mx * pw[q][1][bb - 1] * mz;
-                if (cc) dm += sn[q][2] * (R)cc * mx * my * pw[q][2][cc - 1];
-                // with d' = -d the normal derivative of the monomial changes sign once more
-                R wphi = sw[q][0], wdphi = sw[q][1];
-                s0v += wdphi * mono + wphi * dm;
-                skv += -wdphi * mono - (R)eps * wphi * dm;
+                const R m = e1[q * rs] * e2[q * rs] * e3[q * rs];
+                s += wt[q] * m;
+                g0 += wt[P2M_S + q] * m;
+                g1 += wt[2 * P2M_S + q] * m;
+                g2 += wt[3 * P2M_S + q] * m;
             }
-            acc0[r] += s0v;
-            acck[r] += skv;
+            acc[r][0] += s;
+            acc[r][1] += g0;
+            acc[r][2] += g1;
+            acc[r][3] += g2;
         }
     }
+    __syncthreads();  // the source tables are done with: S and G reuse their space
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        int al = threadIdx.x + r * FAR_T;
-        if (al >= T) continue;
-        const R f = sizeof(R) == 4 ? (R)c_ifact[al] : (R)c_ifact64[al];
-        sig0[(size_t)c * T + al] = acc0[r] * f;
-        sigk[(size_t)c * T + al] = acck[r] * f;
+    for (int r = 0; r < P2M_R; ++r) {
+        const int q = threadIdx.x + r * P2M_T;
+        if (q >= T) continue;
+        Ssh[q] = acc[r][0];
+        Ssh[T + q] = acc[r][1];
+        Ssh[2 * T + q] = acc[r][2];
+        Ssh[3 * T + q] = acc[r][3];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < P2M_R; ++r) {
+        const int q = threadIdx.x + r * P2M_T;
+        if (q >= T) continue;
+        const int a1 = xi[r][0], a2 = xi[r][1], a3 = xi[r][2];
+        R g = 0;
+        if (a1) g += Ssh[T + pb_midx(a1 - 1, a2, a3)];
+        if (a2) g += Ssh[2 * T + pb_midx(a1, a2 - 1, a3)];
+        if (a3) g += Ssh[3 * T + pb_midx(a1, a2, a3 - 1)];
+        sig0[(size_t)c * T + q] = Ssh[q] + g;
+        sigk[(size_t)c * T + q] = -Ssh[q] - (R)eps * g;
     }
 }
 
@@ -132,7 +176,6 @@ __global__ void __launch_bounds__(FAR_T) k_p2m(int nt, int p, const int* __restr
 // children are taken one after the other in child order, so the result does not depend on
 // scheduling. All intermediate arrays use the layout of degree <= pp.
 #define M2M_T 256
-__device__ __forceinline__ double far_inv_fact(int k) { return 1.0 / c_fact[k]; }
 
 template <class R>
 __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __restrict__ cbeg,
@@ -169,7 +212,7 @@ __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __rest
             const R t = (R)(xp[3 * c + d] - xch[3 * (cb + ch) + d]);  // -(x_child - x_parent)
             R v = 1;
             for (int k = 0; k <= pp; ++k) {
-                e[d][k] = v * (R)far_inv_fact(k);
+                e[d][k] = v * inv_fact1<R>(k);
                 v *= t;
             }
         }
@@ -753,7 +796,7 @@ __global__ void __launch_bounds__(FAR_T) k_l2l(int pp, int pc, const int* __rest
         const R t = (R)(xch[3 * c + d] - xp[3 * P + d]);
         R v = 1;
         for (int k = 0; k <= pp; ++k) {
-            e[d][k] = v * (R)far_inv_fact(k);
+            e[d][k] = v * inv_fact1<R>(k);
             v *= t;
         }
     }
@@ -813,6 +856,16 @@ __global__ void __launch_bounds__(FAR_T) k_l2l(int pp, int pc, const int* __rest
 }
 
 // ---------- step 6: LtP ----------
+// With the scaled coefficients L^[a] = a! L[a] and e[a] = d^a / a! (d = y - x_c), the local
+// expansion is sum_a L^[a] e[a] and its normal derivative sum_b e[b] sum_i n_i L^[b + e_i]. Per
+// cluster the three shifted arrays G_i[b] = L^[b + e_i] (potential combination of the normal
+// derivative) are formed once; each thread then evaluates one target with per-axis tables
+// (dynamic shared memory, l2p_smem bytes).
+template <class R>
+static size_t l2p_smem(int p)
+{
+    return sizeof(R) * (2 * (size_t)pb_nterms(p) + 3 * (size_t)pb_nterms(p - 1) + 3 * (size_t)(p + 1) * FAR_T);
+}
 template <class R>
 __global__ void __launch_bounds__(FAR_T) k_l2p(int nt, int p, double eps, const int* __restrict__ begin,
                                                const double* __restrict__ xc, const double4_32a* __restrict__ ep,
@@ -823,25 +876,39 @@ __global__ void __launch_bounds__(FAR_T) k_l2p(int nt, int p, double eps, const 
     l0 += blockIdx.y * lstr;
     lk += blockIdx.y * lstr;
     ys += blockIdx.y * ystr;
-    __shared__ R A1[NT_MAX], A2[NT_MAX];
-    __shared__ R pw[FAR_T][3][PB_PMAX + 1];
+    extern __shared__ __align__(16) unsigned char l2p_sm[];
     const int c = blockIdx.x;
-    const int T = pb_nterms(p);
+    const int T = pb_nterms(p), Tm = pb_nterms(p - 1);
+    R* A1 = (R*)l2p_sm;  // [T]
+    R* A2 = A1 + T;      // [T]
+    R* G = A2 + T;       // [3][Tm]
+    R* pw = G + 3 * Tm;  // [3][p + 1][FAR_T]: (axis, power, target), conflict-free by target
     for (int a = threadIdx.x; a < T; a += FAR_T) {
-        R u = l0[(size_t)c * T + a], v = lk[(size_t)c * T + a];
-        A1[a] = u + v;
-        A2[a] = u + v * (R)(1.0 / eps);
+        int a1, a2, a3;
+        mi_unpack(c_mi[a], a1, a2, a3);
+        const R f = (R)(c_fact[a1] * c_fact[a2] * c_fact[a3]);
+        const R u = l0[(size_t)c * T + a], v = lk[(size_t)c * T + a];
+        A1[a] = (u + v) * f;
+        A2[a] = (u + v * (R)(1.0 / eps)) * f;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < Tm; a += FAR_T) {
+        int a1, a2, a3;
+        mi_unpack(c_mi[a], a1, a2, a3);
+        G[a] = A2[pb_midx(a1 + 1, a2, a3)];
+        G[Tm + a] = A2[pb_midx(a1, a2 + 1, a3)];
+        G[2 * Tm + a] = A2[pb_midx(a1, a2, a3 + 1)];
     }
     const double cx = xc[3 * c], cy = xc[3 * c + 1], cz = xc[3 * c + 2];
     __syncthreads();
     for (int k = begin[c] + threadIdx.x; k < begin[c + 1]; k += FAR_T) {
         double4_32a P = ep[k], Nn = en[k];
-        R d[3] = {(R)(P.x - cx), (R)(P.y - cy), (R)(P.z - cz)};
-        R nx = (R)Nn.x, ny = (R)Nn.y, nz = (R)Nn.z;
+        const R d[3] = {(R)(P.x - cx), (R)(P.y - cy), (R)(P.z - cz)};
+        const R nx = (R)Nn.x, ny = (R)Nn.y, nz = (R)Nn.z;
         for (int a = 0; a < 3; ++a) {
             R v = 1;
             for (int q = 0; q <= p; ++q) {
-                pw[threadIdx.x][a][q] = v;
+                pw[(a * (p + 1) + q) * FAR_T + threadIdx.x] = v * inv_fact1<R>(q);
                 v *= d[a];
             }
         }
@@ -849,13 +916,10 @@ __global__ void __launch_bounds__(FAR_T) k_l2p(int nt, int p, double eps, const 
         for (int al = 0; al < T; ++al) {
             int a, b, cc;
             mi_unpack(c_mi[al], a, b, cc);
-            R mx = pw[threadIdx.x][0][a], my = pw[threadIdx.x][1][b], mz = pw[threadIdx.x][2][cc];
-            R dm = 0;
-            if (a) dm += nx * (R)a * pw[threadIdx.x][0][a - 1] * my * mz;
-            if (b) dm += ny * (R)b * mx * pw[threadIdx.x][1][b - 1] * mz;
-            if (cc) dm += nz * (R)cc * mx * my * pw[threadIdx.x][2][cc - 1];
-            s1 += A1[al] * mx * my * mz;
-            s2 += A2[al] * dm;
+            const R m = pw[a * FAR_T + threadIdx.x] * pw[((p + 1) + b) * FAR_T + threadIdx.x] *
+                        pw[(2 * (p + 1) + cc) * FAR_T + threadIdx.x];
+            s1 += A1[al] * m;
+            if (al < Tm) s2 += (nx * G[al] + ny * G[Tm + al] + nz * G[2 * Tm + al]) * m;
         }
         ys[k] = -(P.w * (double)s1);  // every element lies in one leaf: the far-field part is set here
         ys[nt + k] = -(P.w * (double)s2);
@@ -888,6 +952,14 @@ static int upload_tables(pb_ctx* c)
         iff[k] = (float)iff64[k];
     }
     PB_CUDA(c, cudaMemcpyToSymbol(c_ifact, iff, sizeof(iff)));
+    float i1f[PB_PMAX + 1];
+    double i1d[PB_PMAX + 1];
+    for (int k = 0; k <= PB_PMAX; ++k) {
+        i1d[k] = 1.0 / f[k];
+        i1f[k] = (float)i1d[k];
+    }
+    PB_CUDA(c, cudaMemcpyToSymbol(c_i1f, i1f, sizeof(i1f)));
+    PB_CUDA(c, cudaMemcpyToSymbol(c_i1d, i1d, sizeof(i1d)));
     PB_CUDA(c, cudaMemcpyToSymbol(c_ifact64, iff64, sizeof(iff64)));
     c->tables_ready = true;
     return PB_OK;
@@ -1073,7 +1145,9 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream
     pb_tic_on(c, PB_T_UP, st);
     {
         PbLevel& lv = c->lev[L];
-        k_p2m<R><<<dim3(lv.ncl, nr), FAR_T, 0, st>>>(c->nt, lv.p, lv.begin, lv.xc, c->e64p, c->e64n, xs, eps,
+        const size_t psm = p2m_smem<R>(lv.p);
+        PB_CUDA(c, cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+        k_p2m<R><<<dim3(lv.ncl, nr), P2M_T, psm, st>>>(c->nt, lv.p, lv.begin, lv.xc, c->e64p, c->e64n, xs, eps,
                                                         (R*)lv.sig0, (R*)lv.sigk, vstr, sstr(lv));
         PB_LAUNCH(c);
     }
@@ -1113,7 +1187,9 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream
     }
     {
         PbLevel& lv = c->lev[L];
-        k_l2p<R><<<dim3(lv.ncl, nr), FAR_T, 0, st>>>(c->nt, lv.p, eps, lv.begin, lv.xc, c->e64p, c->e64n,
+        const size_t lsm = l2p_smem<R>(lv.p);
+        PB_CUDA(c, cudaFuncSetAttribute(k_l2p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+        k_l2p<R><<<dim3(lv.ncl, nr), FAR_T, lsm, st>>>(c->nt, lv.p, eps, lv.begin, lv.xc, c->e64p, c->e64n,
                                                         (R*)lv.lam0, (R*)lv.lamk, ys, sstr(lv), vstr);
         PB_LAUNCH(c);
     }
