@@ -148,8 +148,10 @@ int pb_precond_apply(pb_ctx* ctx, const double* r, double* z);
 
 /* Solve A x = b for the uploaded charges with right-preconditioned restarted GMRES to
  * ||b - A x|| <= tol ||b|| (Section 2.3, last paragraph; Section 3). x: device pointer,
- * 2N doubles; read as the initial guess when use_x0 != 0 (e.g. a learned warm start),
- * otherwise zero-initialised; overwritten with the solution. restart: Krylov dimension
+ * 2N doubles; read as the initial guess when use_x0 != 0 (e.g. a learned warm start), which
+ * is first scaled by the factor a >= 0 that minimises ||b - a A x0|| (0 if none is positive);
+ * otherwise zero-initialised (the first residual is b, no product); overwritten with the
+ * solution. restart: Krylov dimension
  * m (1..200). The Arnoldi process, Givens rotations and updates run on the device in FP64;
  * the host reads one residual estimate per iteration. info may be NULL. */
 int pb_gmres_solve(pb_ctx* ctx, double* x, double tol, int max_iter, int restart, int use_x0,

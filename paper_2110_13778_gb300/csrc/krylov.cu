@@ -255,6 +255,19 @@ __global__ void k_scale(long long n, const double* __restrict__ src, const doubl
     for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) dst[i] = src[i] * f;
 }
 
+// Scale a nonzero start x (w = A x) by a = <w, b> / <w, w>, the factor that minimises
+// ||b - a A x||; a start with no positive factor becomes zero. d = {<w, b>, <w, w>}.
+__global__ void k_start_scale(long long n, const double* __restrict__ d, double* __restrict__ x,
+                              double* __restrict__ w)
+{
+    const double a = d[1] > 0.0 ? d[0] / d[1] : 0.0;
+    const double f = (a > 0.0 && isfinite(a)) ? a : 0.0;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        x[i] *= f;
+        w[i] *= f;
+    }
+}
+
 // r = b - r  (r holds A x on input)
 __global__ void k_residual(long long n, const double* __restrict__ b, double* __restrict__ r)
 {
@@ -387,6 +400,20 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
         } else {
             if ((rc = pb_matvec_sorted(c, xs, w, 0))) return rc;
             inf.matvecs++;
+            if (first) {
+                // a given start (a learned guess, say) is first rescaled by the least-squares
+                // factor along it: two dot products, no extra product
+                k_multidot<<<dim3(DOT_BLOCKS, 1), KB, 0, c->st>>>(n, bs, w, part);
+                PB_LAUNCH(c);
+                k_finish<<<1, KB, 0, c->st>>>(DOT_BLOCKS, part, s.hcol, 0);
+                PB_LAUNCH(c);
+                k_multidot<<<dim3(DOT_BLOCKS, 1), KB, 0, c->st>>>(n, nullptr, w, part);
+                PB_LAUNCH(c);
+                k_finish<<<1, KB, 0, c->st>>>(DOT_BLOCKS, part, s.hcol + 1, 0);
+                PB_LAUNCH(c);
+                k_start_scale<<<G, KB, 0, c->st>>>(n, s.hcol, xs, w);
+                PB_LAUNCH(c);
+            }
         }
         k_residual<<<G, KB, 0, c->st>>>(n, bs, w);
         PB_LAUNCH(c);

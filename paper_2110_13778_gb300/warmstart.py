@@ -1,6 +1,6 @@
 """Learned warm start for GMRES: dataset generation, training and use.
 
-The network (12 features -> 128 -> 128 -> 128 -> 2, ReLU, BF16 tensor-core kernels with
+The network (18 features -> 128 -> 128 -> 128 -> 2, ReLU, BF16 tensor-core kernels with
 FP32 accumulation) is trained on solutions the solver itself produces: every training
 molecule is solved by GMRES from a zero start, and its per-element features and scaled
 solution become rows of the training set. At use, ``pb_learned_guess`` evaluates the
@@ -29,7 +29,7 @@ def solve_params(**kw):
 
 
 def training_rows(mesh, prm, tol=1e-6, max_iter=300, restart=50):
-    """(F, T, info) for one molecule: features (nt, 12) and targets (nt, 2) as float32 CUDA
+    """(F, T, info) for one molecule: features (nt, 18) and targets (nt, 2) as float32 CUDA
     tensors from its GMRES solution."""
     import torch
 
