@@ -121,17 +121,20 @@ __global__ void k_touch(int nt, const int* __restrict__ stris, const int* __rest
 __global__ void k_touch_classes(int nt, const int* __restrict__ toff, const int* __restrict__ tj,
                                 const int* __restrict__ stris, unsigned long long* __restrict__ cls)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nt) return;
-    unsigned long long n[4] = {0, 0, 0, 0};
-    for (int t = toff[k]; t < toff[k + 1]; ++t) {
-        int j = tj[t], s = 0;
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) s += stris[3 * k + a] == stris[3 * j + b];
-        n[s > 3 ? 3 : s]++;
+    // per-warp sums first, then one atomic per warp and class (not one per thread)
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned n[4] = {0, 0, 0, 0};
+    if (k < nt)
+        for (int t = toff[k]; t < toff[k + 1]; ++t) {
+            int j = tj[t], s = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) s += stris[3 * k + a] == stris[3 * j + b];
+            n[s > 3 ? 3 : s]++;
+        }
+    for (int q = 1; q < 4; ++q) {
+        const unsigned w = __reduce_add_sync(0xffffffffu, n[q]);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&cls[q], (unsigned long long)w);
     }
-    for (int q = 1; q < 4; ++q)
-        if (n[q]) atomicAdd(&cls[q], n[q]);
 }
 
 // ---------- Sauter-Schwab sub-maps (reference triangle {0 <= e2 <= e1 <= 1}) ----------

@@ -160,15 +160,18 @@ __device__ void box_finish(const double* lo, const double* hi, double* xc, doubl
 }
 
 // leaf boxes from the vertices of the cluster's triangles; writes lo/hi for the parents
+// one warp per leaf: lanes over the leaf's elements, then a shuffle reduction (minimum and
+// maximum are exact, so the box does not depend on the order)
 __global__ void k_leaf_boxes(int ncl, const int* __restrict__ begin, const int* __restrict__ order,
                              const double* __restrict__ V, const int* __restrict__ T,
                              double* __restrict__ blo, double* __restrict__ bhi,
                              double* __restrict__ xc, double* __restrict__ rho)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (c >= ncl) return;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int s = begin[c]; s < begin[c + 1]; ++s) {
+    for (int s = begin[c] + lane; s < begin[c + 1]; s += 32) {
         int e = order[s];
         for (int a = 0; a < 3; ++a) {
             const double* p = V + 3 * T[3 * e + a];
@@ -178,11 +181,18 @@ __global__ void k_leaf_boxes(int ncl, const int* __restrict__ begin, const int* 
             }
         }
     }
-    for (int k = 0; k < 3; ++k) {
-        blo[3 * c + k] = lo[k];
-        bhi[3 * c + k] = hi[k];
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    if (lane == 0) {
+        for (int k = 0; k < 3; ++k) {
+            blo[3 * c + k] = lo[k];
+            bhi[3 * c + k] = hi[k];
+        }
+        box_finish(lo, hi, xc + 3 * c, rho + c);
     }
-    box_finish(lo, hi, xc + 3 * c, rho + c);
 }
 
 __global__ void k_parent_boxes(int ncl, const int* __restrict__ cbeg, const double* __restrict__ clo,
@@ -405,7 +415,7 @@ int pb_geometry_and_tree(pb_ctx* c)
     }
     {
         PbLevel& lv = c->lev[L];
-        k_leaf_boxes<<<nblk(lv.ncl, 128), 128, 0, c->st>>>(lv.ncl, lv.begin, c->order, c->verts, c->tris,
+        k_leaf_boxes<<<nblk((long long)lv.ncl * 32, 128), 128, 0, c->st>>>(lv.ncl, lv.begin, c->order, c->verts, c->tris,
                                                             blo[L], bhi[L], lv.xc, lv.rho);
         PB_LAUNCH(c);
     }
