@@ -223,7 +223,11 @@ __device__ __forceinline__ bool is_near(const double* xa, double ra, const doubl
     return __dmul_rn(s, s) > __dmul_rn(e2, dd);
 }
 
-// candidates of c are the children of the neighbours of its parent; pass 0 counts, pass 1 fills
+// candidates of c are the children of the neighbours of its parent; pass 0 counts, pass 1 fills.
+// One warp per cluster: lane i takes the i-th neighbour q of the parent (32 at a time) and tests
+// q's children (at most 8) into a bit mask; warp scans of the per-lane counts give each lane its
+// place, so both lists keep the sequential order (parent's neighbours in list order, children
+// in order).
 template <int PASS>
 __global__ void k_lists(int ncl, const int* __restrict__ parent, const int* __restrict__ pnear_off,
                         const int* __restrict__ pnear_idx, const int* __restrict__ pcbeg,
@@ -231,27 +235,49 @@ __global__ void k_lists(int ncl, const int* __restrict__ parent, const int* __re
                         int* __restrict__ ncnt, int* __restrict__ icnt, const int* __restrict__ noff,
                         const int* __restrict__ ioff, int* __restrict__ nidx, int* __restrict__ iidx)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (c >= ncl) return;
-    int P = parent[c];
+    const int P = parent[c];
+    int nb = PASS ? noff[c] : 0, ib = PASS ? ioff[c] : 0;  // running list ends
+    const double xa[3] = {xc[3 * c], xc[3 * c + 1], xc[3 * c + 2]};
+    const double ra = rho[c];
     int nn = 0, ni = 0;
-    int nb = PASS ? noff[c] : 0, ib = PASS ? ioff[c] : 0;
-    double xa[3] = {xc[3 * c], xc[3 * c + 1], xc[3 * c + 2]};
-    double ra = rho[c];
-    for (int t = pnear_off[P]; t < pnear_off[P + 1]; ++t) {
-        int q = pnear_idx[t];
-        for (int c2 = pcbeg[q]; c2 < pcbeg[q + 1]; ++c2) {
-            bool nr = is_near(xa, ra, xc + 3 * c2, rho[c2], e2);
-            if (nr) {
-                if (PASS) nidx[nb + nn] = c2;
-                ++nn;
-            } else {
-                if (PASS) iidx[ib + ni] = c2;
-                ++ni;
+    for (int t0 = pnear_off[P]; t0 < pnear_off[P + 1]; t0 += 32) {
+        const int t = t0 + lane;
+        int cb = 0, ce = 0;
+        unsigned mask = 0u;  // bit k: child cb + k is near
+        if (t < pnear_off[P + 1]) {
+            const int q = pnear_idx[t];
+            cb = pcbeg[q];
+            ce = pcbeg[q + 1];
+            for (int c2 = cb; c2 < ce; ++c2)
+                if (is_near(xa, ra, xc + 3 * c2, rho[c2], e2)) mask |= 1u << (c2 - cb);
+        }
+        const int kn = __popc(mask), ki = (ce - cb) - kn;
+        // inclusive warp scans of the counts
+        int sn = kn, si = ki;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(0xffffffffu, sn, o), b = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) {
+                sn += a;
+                si += b;
             }
         }
+        if (PASS) {
+            int pn = nb + sn - kn, pi = ib + si - ki;
+            for (int c2 = cb; c2 < ce; ++c2) {
+                if ((mask >> (c2 - cb)) & 1u) nidx[pn++] = c2;
+                else iidx[pi++] = c2;
+            }
+        }
+        const int tn = __shfl_sync(0xffffffffu, sn, 31), ti = __shfl_sync(0xffffffffu, si, 31);
+        nb += tn;
+        ib += ti;
+        nn += tn;
+        ni += ti;
     }
-    if (!PASS) {
+    if (!PASS && lane == 0) {
         ncnt[c] = nn;
         icnt[c] = ni;
     }
@@ -451,7 +477,7 @@ int pb_geometry_and_tree(pb_ctx* c)
         int* ncnt = (int*)pb_alloc(c, sizeof(int) * (lv.ncl + 1));
         int* icnt = (int*)pb_alloc(c, sizeof(int) * (lv.ncl + 1));
         if (!ncnt || !icnt) return pb_fail(c, PB_ERR_NOMEM, "lists: out of memory");
-        k_lists<0><<<nblk(lv.ncl, 128), 128, 0, c->st>>>(lv.ncl, lv.parent, pv.near_off, pv.near_idx, pv.cbeg,
+        k_lists<0><<<nblk((long long)lv.ncl * 32, 128), 128, 0, c->st>>>(lv.ncl, lv.parent, pv.near_off, pv.near_idx, pv.cbeg,
                                                           lv.xc, lv.rho, e2, ncnt, icnt, nullptr, nullptr,
                                                           nullptr, nullptr);
         PB_LAUNCH(c);
@@ -470,7 +496,7 @@ int pb_geometry_and_tree(pb_ctx* c)
         lv.near_idx = (int*)pb_alloc(c, sizeof(int) * (lv.nnear + 1));
         lv.int_idx = (int*)pb_alloc(c, sizeof(int) * (lv.ninter + 1));
         if (!lv.near_idx || !lv.int_idx) return pb_fail(c, PB_ERR_NOMEM, "lists: out of memory");
-        k_lists<1><<<nblk(lv.ncl, 128), 128, 0, c->st>>>(lv.ncl, lv.parent, pv.near_off, pv.near_idx, pv.cbeg,
+        k_lists<1><<<nblk((long long)lv.ncl * 32, 128), 128, 0, c->st>>>(lv.ncl, lv.parent, pv.near_off, pv.near_idx, pv.cbeg,
                                                           lv.xc, lv.rho, e2, nullptr, nullptr, lv.near_off,
                                                           lv.int_off, lv.near_idx, lv.int_idx);
         PB_LAUNCH(c);
