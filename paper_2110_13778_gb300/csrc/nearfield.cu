@@ -463,8 +463,52 @@ int pb_near_apply(pb_ctx* c, const double* xs, double* ys)
     return PB_OK;
 }
 
+// Several right-hand sides: four per thread (blockIdx.y = group of four), so each correction
+// is read once per four vectors instead of once per vector.
+__global__ void k_corrections4(int nt, int nr, const int* __restrict__ toff, const int* __restrict__ tj,
+                               const double* __restrict__ corr, const double* __restrict__ xs,
+                               double* __restrict__ ys, const double* __restrict__ yf)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    const int q0 = 4 * blockIdx.y, nq = min(4, nr - q0);
+    const long long vs = 2LL * nt;
+    double y1[4] = {0, 0, 0, 0}, y2[4] = {0, 0, 0, 0};
+    if (xs)
+        for (int t = toff[k]; t < toff[k + 1]; ++t) {
+            const int j = tj[t];
+            const double c0 = corr[4 * t], c1 = corr[4 * t + 1], c2 = corr[4 * t + 2], c3 = corr[4 * t + 3];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nq) {
+                    const double* x = xs + (q0 + q) * vs;
+                    const double ph = x[j], dph = x[nt + j];
+                    y1[q] += c0 * dph + c1 * ph;
+                    y2[q] += c2 * dph + c3 * ph;
+                }
+        }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (q < nq) {
+            const long long o = (q0 + q) * vs;
+            double a = y1[q], b = y2[q];
+            if (yf) {
+                a -= yf[o + k];
+                b -= yf[o + nt + k];
+            }
+            ys[o + k] -= a;
+            ys[o + nt + k] -= b;
+        }
+}
+
 int pb_corr_apply(pb_ctx* c, const double* xs, double* ys, int nr, const double* yfar)
 {
+    if (nr > 1) {
+        k_corrections4<<<dim3((c->nt + 255) / 256, (nr + 3) / 4), 256, 0, c->st>>>(c->nt, nr, c->touch_off, c->touch_j,
+                                                                                c->corr, xs, ys, yfar);
+        PB_LAUNCH(c);
+        return PB_OK;
+    }
     k_corrections<<<dim3((c->nt + 255) / 256, nr), 256, 0, c->st>>>(c->nt, c->touch_off, c->touch_j, c->corr, xs,
                                                                      ys, yfar);
     PB_LAUNCH(c);

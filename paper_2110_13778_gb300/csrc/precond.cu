@@ -33,14 +33,21 @@ __global__ void k_blk_fill(const int* __restrict__ begin, const long long* __res
                            const int* __restrict__ toff, const int* __restrict__ tj,
                            const double* __restrict__ corr, double eps, double kappa, R* __restrict__ minv)
 {
+    // the block's element records staged once in shared memory (n <= PB_PC_BMAX)
+    __shared__ double4_32a sp_[PB_PC_BMAX], sn_[PB_PC_BMAX];
     const int c = blockIdx.x;
     const int b = begin[c], n = begin[c + 1] - begin[c], m = 2 * n;
     R* Mc = minv + moff[c];
     const double inv_eps = 1.0 / eps;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sp_[i] = ep[b + i];
+        sn_[i] = en[b + i];
+    }
+    __syncthreads();
     for (int i = threadIdx.x / 32; i < n; i += blockDim.x / 32) {
-        const double4_32a pi = ep[b + i], ni = en[b + i];
+        const double4_32a pi = sp_[i], ni = sn_[i];
         for (int j = threadIdx.x & 31; j < n; j += 32) {
-            const double4_32a pj = ep[b + j], nj = en[b + j];
+            const double4_32a pj = sp_[j], nj = sn_[j];
             R K[4] = {0, 0, 0, 0};
             if (i != j) {
                 pb_kernels<R>((R)(pi.x - pj.x), (R)(pi.y - pj.y), (R)(pi.z - pj.z), (R)ni.x, (R)ni.y, (R)ni.z,
@@ -318,6 +325,41 @@ __global__ void k_blk_apply(int nt, const int* __restrict__ begin, const long lo
     }
 }
 
+// The same for up to 16 right-hand sides at once (q0 = 16 blockIdx.y, nq of them): each block
+// row is read once for all of them. The vectors' slices sit in shared memory as rv[j][q]; lane
+// (h, q) of a warp sums column parity h of row i for vector q (lanes of one half read the same
+// matrix entry, and the two halves hit different banks), then the halves are added.
+template <class R>
+__global__ void k_blk_apply_m(int nt, const int* __restrict__ begin, const long long* __restrict__ moff,
+                              const R* __restrict__ minv, const double* __restrict__ r, double* __restrict__ z,
+                              long long rstr, long long zstr, int nr)
+{
+    __shared__ R rv[2 * PB_PC_BMAX * 16];
+    const int q0 = 16 * blockIdx.y, nq = min(16, nr - q0);
+    const int c = blockIdx.x;
+    const int b = begin[c], n = begin[c + 1] - begin[c], m = 2 * n;
+    const R* Mc = minv + moff[c];
+    for (int t = threadIdx.x; t < m * 16; t += blockDim.x) {
+        const int j = t >> 4, q = t & 15;
+        const double* rq = r + (long long)(q0 + q) * rstr;
+        rv[t] = q < nq ? (R)(j < n ? rq[b + j] : rq[nt + b + j - n]) : R(0);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x & 31, nw = blockDim.x / 32;
+    const int h = lane >> 4, q = lane & 15;
+    for (int i = warp; i < m; i += nw) {
+        const R* row = Mc + (size_t)i * m;
+        R s = 0;
+        for (int j = h; j < m; j += 2) s += row[j] * rv[j * 16 + q];
+        s += __shfl_xor_sync(0xffffffffu, s, 16);
+        if (h == 0 && q < nq) {
+            double* zq = z + (long long)(q0 + q) * zstr;
+            if (i < n) zq[b + i] = (double)s;
+            else zq[nt + b + i - n] = (double)s;
+        }
+    }
+}
+
 // 2x2 element blocks (diagonal preconditioner): uses the (i, i) correction entry
 __global__ void k_diag_build(int nt, const double4_32a* __restrict__ ep, const int* __restrict__ toff,
                              const int* __restrict__ tj, const double* __restrict__ corr, double eps,
@@ -482,12 +524,22 @@ int pb_precond_apply_multi(pb_ctx* c, const double* r, long long rstr, double* z
     const int nt = c->nt;
     pb_tic(c, PB_T_PRECOND);
     if (c->prm.precond == PB_PRECOND_BLOCK) {
-        if (c->prm.precision == PB_MIXED)
-            k_blk_apply<float><<<dim3(c->npcblk, nr), 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off,
-                                                                       (const float*)c->minv, r, z, rstr, zstr);
-        else
-            k_blk_apply<double><<<dim3(c->npcblk, nr), 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off,
-                                                                        (const double*)c->minv, r, z, rstr, zstr);
+        const dim3 gm(c->npcblk, (nr + 15) / 16);
+        if (c->prm.precision == PB_MIXED) {
+            if (nr == 1)
+                k_blk_apply<float><<<c->npcblk, 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off, (const float*)c->minv,
+                                                                 r, z, rstr, zstr);
+            else
+                k_blk_apply_m<float><<<gm, 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off, (const float*)c->minv, r,
+                                                            z, rstr, zstr, nr);
+        } else {
+            if (nr == 1)
+                k_blk_apply<double><<<c->npcblk, 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off,
+                                                                  (const double*)c->minv, r, z, rstr, zstr);
+            else
+                k_blk_apply_m<double><<<gm, 256, 0, c->st>>>(nt, c->pc_begin, c->blk_off,
+                                                             (const double*)c->minv, r, z, rstr, zstr, nr);
+        }
     } else if (c->prm.precond == PB_PRECOND_DIAG) {
         k_diag_apply<<<dim3((nt + 255) / 256, nr), 256, 0, c->st>>>(nt, c->dinv, r, z, rstr, zstr);
     } else {
