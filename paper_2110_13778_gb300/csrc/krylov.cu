@@ -161,6 +161,153 @@ __global__ void k_energy(int nt, int nc, const double4_32a* __restrict__ ep, con
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// ---------- several charge states at once (same positions, charges Q[r nc + t]) ----------
+// The pair geometry is evaluated once for up to 16 states; each state adds its own weighted
+// sums (right-hand side: two FMAs per state; energy: the state's solution values too).
+template <class R, int NR>
+__global__ void k_rhs_m(int nt, int nc, const double4_32a* __restrict__ ep, const double4_32a* __restrict__ en,
+                        const double* __restrict__ qpos, const double* __restrict__ Q, double eps1,
+                        double* __restrict__ B, int nr)
+{
+    __shared__ R sh[KB][3], sl[KB][3], sq[NR][KB];
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double4_32a p = make_double4_32a(0, 0, 0, 0), n = p;
+    if (k < nt) {
+        p = ep[k];
+        n = en[k];
+    }
+    const R ph[3] = {(R)p.x, (R)p.y, (R)p.z};
+    const R pl[3] = {(R)(p.x - (double)ph[0]), (R)(p.y - (double)ph[1]), (R)(p.z - (double)ph[2])};
+    const R nx = (R)n.x, ny = (R)n.y, nz = (R)n.z;
+    double s1[NR], s2[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) s1[r] = s2[r] = 0.0;
+    const double i4pi = 0.07957747154594767;
+    for (int t0 = 0; t0 < nc; t0 += KB) {
+        __syncthreads();
+        if (t0 + threadIdx.x < nc) {
+            int t = t0 + threadIdx.x;
+            for (int a = 0; a < 3; ++a) {
+                double v = qpos[3 * t + a];
+                R hv = (R)v;
+                sh[threadIdx.x][a] = hv;
+                sl[threadIdx.x][a] = (R)(v - (double)hv);
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) sq[r][threadIdx.x] = r < nr ? (R)Q[(size_t)r * nc + t] : R(0);
+        }
+        __syncthreads();
+        int m = min(KB, nc - t0);
+        if (k < nt) {
+            R a1[NR], a2[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) a1[r] = a2[r] = 0;
+            for (int t = 0; t < m; ++t) {
+                R dx = (ph[0] - sh[t][0]) + (pl[0] - sl[t][0]);
+                R dy = (ph[1] - sh[t][1]) + (pl[1] - sl[t][1]);
+                R dz = (ph[2] - sh[t][2]) + (pl[2] - sl[t][2]);
+                R r2 = dx * dx + dy * dy + dz * dz;
+                R ri = PbKer<R>::rsqrt_(r2);
+                R g2 = -(nx * dx + ny * dy + nz * dz) * ri * ri * ri;  // dG0/dn_x up to 1/(4 pi)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    a1[r] += sq[r][t] * ri;
+                    a2[r] += sq[r][t] * g2;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                s1[r] += (double)a1[r];
+                s2[r] += (double)a2[r];
+            }
+        }
+    }
+    if (k < nt)
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (r < nr) {
+                B[2LL * nt * r + k] = p.w * s1[r] * i4pi / eps1;
+                B[2LL * nt * r + nt + k] = p.w * s2[r] * i4pi / eps1;
+            }
+}
+
+template <class R, int NR>
+__global__ void k_energy_m(int nt, int nc, const double4_32a* __restrict__ ep, const double4_32a* __restrict__ en,
+                           const double* __restrict__ qpos, const double* __restrict__ Q, double eps, double kappa,
+                           const double* __restrict__ X, double* __restrict__ part, int nr)
+{
+    __shared__ R sh[KB][3], sl[KB][3], sq[NR][KB];
+    __shared__ double red[KB / 32][NR];
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double4_32a p = make_double4_32a(0, 0, 0, 0), n = p;
+    R rph[NR], rdph[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) rph[r] = rdph[r] = 0;
+    if (k < nt) {
+        p = ep[k];
+        n = en[k];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (r < nr) {
+                rph[r] = (R)X[2LL * nt * r + k];
+                rdph[r] = (R)X[2LL * nt * r + nt + k];
+            }
+    }
+    const R eh[3] = {(R)p.x, (R)p.y, (R)p.z};
+    const R el[3] = {(R)(p.x - (double)eh[0]), (R)(p.y - (double)eh[1]), (R)(p.z - (double)eh[2])};
+    const R nx = (R)n.x, ny = (R)n.y, nz = (R)n.z;
+    double acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+    const R e = (R)eps, kp = (R)kappa;
+    for (int t0 = 0; t0 < nc; t0 += KB) {
+        __syncthreads();
+        if (t0 + threadIdx.x < nc) {
+            int t = t0 + threadIdx.x;
+            for (int a = 0; a < 3; ++a) {
+                const double v = qpos[3 * t + a];
+                const R hv = (R)v;
+                sh[threadIdx.x][a] = hv;
+                sl[threadIdx.x][a] = (R)(v - (double)hv);
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) sq[r][threadIdx.x] = r < nr ? (R)Q[(size_t)r * nc + t] : R(0);
+        }
+        __syncthreads();
+        int m = min(KB, nc - t0);
+        if (k < nt) {
+            R s[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) s[r] = 0;
+            for (int t = 0; t < m; ++t) {
+                const R dx = (sh[t][0] - eh[0]) + (sl[t][0] - el[0]);
+                const R dy = (sh[t][1] - eh[1]) + (sl[t][1] - el[1]);
+                const R dz = (sh[t][2] - eh[2]) + (sl[t][2] - el[2]);
+                R K1, K2;
+                energy_k12<R>(dx, dy, dz, nx, ny, nz, e, kp, K1, K2);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) s[r] += sq[r][t] * (K1 * rdph[r] + K2 * rph[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r] += (double)s[r];
+        }
+    }
+    // block sums per state: warp shuffles, then the block's warps
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        double v = acc[r] * p.w;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[w][r] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NR && threadIdx.x < nr) {
+        double v = 0.0;
+        for (int q = 0; q < KB / 32; ++q) v += red[q][threadIdx.x];
+        part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = v;
+    }
+}
+
 __global__ void k_sum(int n, const double* __restrict__ part, double* __restrict__ out, double scale)
 {
     __shared__ double red[KB];
@@ -197,6 +344,52 @@ int pb_energy_sorted(pb_ctx* c, const double* xs, double* E)
     PB_CUDA(c, cudaMemcpyAsync(c->hscal, c->scratch + nb, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     PB_CUDA(c, cudaStreamSynchronize(c->st));
     *E = c->hscal[0];
+    return PB_OK;
+}
+
+// right-hand sides of nr <= 16 charge states (device charges Q, nr x nc) into B (nr x 2N)
+int pb_rhs_states_sorted(pb_ctx* c, const double* Q, double* B, int nr)
+{
+    const int nt = c->nt;
+    pb_tic(c, PB_T_RHS);
+    if (c->prm.precision == PB_MIXED)
+        k_rhs_m<float, 16><<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, Q,
+                                                                 c->prm.eps_in, B, nr);
+    else
+        k_rhs_m<double, 16><<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, Q,
+                                                                  c->prm.eps_in, B, nr);
+    PB_LAUNCH(c);
+    pb_toc(c, PB_T_RHS);
+    return PB_OK;
+}
+
+// energies of nr <= 16 states (charges Q, solutions X, nr x 2N) into E[0..nr) (host); synchronises
+int pb_energy_states_sorted(pb_ctx* c, const double* Q, const double* X, int nr, double* E)
+{
+    const int nt = c->nt, nb = (nt + KB - 1) / KB;
+    if (!c->escratch) {
+        c->escratch = (double*)pb_alloc(c, sizeof(double) * ((size_t)nb * 16 + 16));
+        if (!c->escratch) return pb_fail(c, PB_ERR_NOMEM, "energy: out of memory");
+    }
+    double* part = c->escratch;
+    const double eps = c->prm.eps_out / c->prm.eps_in;
+    pb_tic(c, PB_T_ENERGY);
+    if (c->prm.precision == PB_MIXED)
+        k_energy_m<float, 16><<<nb, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, Q, eps, c->prm.kappa, X,
+                                                     part, nr);
+    else
+        k_energy_m<double, 16><<<nb, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, Q, eps, c->prm.kappa, X,
+                                                      part, nr);
+    PB_LAUNCH(c);
+    for (int r = 0; r < nr; ++r) {
+        k_sum<<<1, KB, 0, c->st>>>(nb, part + (size_t)r * nb, part + (size_t)nb * 16 + r, 0.5 * 4.0 * PB_PI * 332.0716);
+        PB_LAUNCH(c);
+    }
+    pb_toc(c, PB_T_ENERGY);
+    std::vector<double> h(nr);
+    PB_CUDA(c, cudaMemcpyAsync(h.data(), part + (size_t)nb * 16, sizeof(double) * nr, cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    for (int r = 0; r < nr; ++r) E[r] = h[r];
     return PB_OK;
 }
 

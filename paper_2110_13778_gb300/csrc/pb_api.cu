@@ -50,6 +50,8 @@ static void pb_free_build(pb_ctx* c)
     c->canon_expect = 0;
     c->gm_m = 0;
     c->scratch = nullptr;
+    c->escratch = nullptr;
+    c->qstates = nullptr;
     pb_drop_graphs(c);
     c->gb_graph_failed = false;
     c->mv_nr = c->gb_nr = c->gb_m = c->dens_nr = 0;
@@ -483,13 +485,20 @@ extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, 
         int rc;
         if ((rc = reserve_multi(c, nr))) return rc;
         double *Xs = c->mxs, *Bs = c->mys;
-        for (int r = 0; r < nr; ++r) {
-            if (c->nc > 0)
-                PB_CUDA(c, cudaMemcpyAsync(c->q, q + (size_t)(s0 + r) * c->nc, sizeof(double) * c->nc,
-                                           cudaMemcpyHostToDevice, c->st));
-            if ((rc = pb_rhs_sorted(c, Bs + r * n2))) return rc;
-            PB_CUDA(c, cudaMemcpyAsync(Xs + r * n2, c->xs, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->st));
+        // the batch's charges on the device, then the right-hand sides 16 states per launch
+        // (the pair geometry is shared by the states)
+        if (!c->qstates) {
+            c->qstates = (double*)pb_alloc(c, sizeof(double) * ((size_t)PB_MAX_RHS * c->nc + 1));
+            if (!c->qstates) return pb_fail(c, PB_ERR_NOMEM, "solve_states: out of memory");
         }
+        if (c->nc > 0)
+            PB_CUDA(c, cudaMemcpyAsync(c->qstates, q + (size_t)s0 * c->nc, sizeof(double) * c->nc * nr,
+                                       cudaMemcpyHostToDevice, c->st));
+        for (int g = 0; g < nr; g += 16)
+            if ((rc = pb_rhs_states_sorted(c, c->qstates + (size_t)g * c->nc, Bs + g * n2, std::min(16, nr - g))))
+                return rc;
+        for (int r = 0; r < nr; ++r)
+            PB_CUDA(c, cudaMemcpyAsync(Xs + r * n2, c->xs, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->st));
         std::vector<pb_solve_info> loc(nr);
         rc = pb_gmres_batch_sorted(c, Xs, Bs, nr, tol, max_iter, restart, loc.data());
         if (rc && rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE && rc != PB_ERR_TIMEOUT) return rc;
@@ -497,15 +506,16 @@ extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, 
         for (int r = 0; r < nr; ++r) {
             if (infos) infos[s0 + r] = loc[r];
             if ((rc = pb_scatter(c, Xs + r * n2, X + (size_t)(s0 + r) * n2))) return rc;
-            if (E) {
-                if (c->nc > 0)
-                    PB_CUDA(c, cudaMemcpyAsync(c->q, q + (size_t)(s0 + r) * c->nc, sizeof(double) * c->nc,
-                                               cudaMemcpyHostToDevice, c->st));
-                double e = 0.0;
-                if ((rc = pb_energy_sorted(c, Xs + r * n2, &e))) return rc;
-                E[s0 + r] = e;
-            }
         }
+        if (E)
+            for (int g = 0; g < nr; g += 16)
+                if ((rc = pb_energy_states_sorted(c, c->qstates + (size_t)g * c->nc, Xs + g * n2,
+                                                  std::min(16, nr - g), E + s0 + g)))
+                    return rc;
+        // the uploaded charges are left as those of the last state
+        if (c->nc > 0 && s0 + nr == nrhs)
+            PB_CUDA(c, cudaMemcpyAsync(c->q, q + (size_t)(nrhs - 1) * c->nc, sizeof(double) * c->nc,
+                                       cudaMemcpyHostToDevice, c->st));
     }
     PB_CUDA(c, cudaStreamSynchronize(c->st));
     return worst;

@@ -146,6 +146,8 @@ struct pb_ctx {
     double* ys = nullptr;
     double* ws = nullptr;
     double* scratch = nullptr;    // reduction partials
+    double* escratch = nullptr;   // per-state energy partials (several states at once)
+    double* qstates = nullptr;    // device charges of up to PB_MAX_RHS states [PB_MAX_RHS][nc]
     // several right-hand sides: tree-ordered work vectors and the batched GMRES workspace
     double *mxs = nullptr, *mys = nullptr;
     int mv_nr = 0;
@@ -236,6 +238,8 @@ int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double 
                           pb_solve_info* infos);  // krylov.cu
 int pb_rhs_sorted(pb_ctx* c, double* bs);                          // krylov.cu
 int pb_energy_sorted(pb_ctx* c, const double* xs, double* E);      // krylov.cu
+int pb_rhs_states_sorted(pb_ctx* c, const double* Q, double* B, int nr);        // krylov.cu, nr <= 16
+int pb_energy_states_sorted(pb_ctx* c, const double* Q, const double* X, int nr, double* E);  // nr <= 16
 int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max_iter,
                     int restart, pb_solve_info* info, bool x_zero);  // krylov.cu (x_zero: xs is zero)
 int pb_matvec_sorted(pb_ctx* c, const double* xs, double* ys, int which);  // pb_api.cu
