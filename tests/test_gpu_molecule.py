@@ -5,8 +5,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle import dense  # noqa: E402
-from paper_2110_13778_gb300 import molecules, pb  # noqa: E402
+from oracle import dense, fmm  # noqa: E402
+from paper_2110_13778_gb300 import inputs, molecules, pb  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -36,6 +36,51 @@ def _ctx(m, **kw):
     pb.pb_mesh_upload(ctx, m.verts, m.tris, m.qpos, m.q)
     pb.pb_build_tree(ctx)
     return ctx
+
+
+def _leaf_blocks(tr, bmax=96):
+    """Preconditioner blocks: the leaves, a leaf above bmax elements cut into nearly equal
+    consecutive (Morton-ordered) parts of at most bmax elements."""
+    out = []
+    for c in range(tr.nclusters(tr.L)):
+        e = tr.order[tr.begin[tr.L][c]:tr.end[tr.L][c]]
+        parts = (len(e) + bmax - 1) // bmax
+        base, extra = divmod(len(e), parts)
+        s0 = 0
+        for q in range(parts):
+            n = base + (1 if q < extra else 0)
+            out.append(e[s0:s0 + n])
+            s0 += n
+    return out
+
+
+@pytest.mark.parametrize("prec,leaf", [(pb.PB_MIXED, 24), (pb.PB_MIXED, 48), (pb.PB_FP64, 24)])
+def test_block_preconditioner_all_size_classes(mol, prec, leaf):
+    # block inverses of every register-tile class (order <= 64, <= 128, <= 192 under mixed
+    # precision) against FP64 solves with the oracle's diagonal blocks of the dense matrix
+    m, ph, A = mol
+    ctx = _ctx(m, leaf_size=leaf, eta0=0.8, p=4, precision=prec, precond=pb.PB_PRECOND_BLOCK)
+    try:
+        tr = fmm.Tree(m.verts, m.tris, leaf_size=leaf, eta0=0.8)
+        blocks = _leaf_blocks(tr)
+        classes = {0 if 2 * len(e) <= 64 else 1 if 2 * len(e) <= 128 else 2 for e in blocks}
+        assert classes == {0, 1, 2}  # the molecule's leaves span all three
+        st = pb.pb_get_tree_stats(ctx)
+        assert st["pc_blocks"] == len(blocks)
+        assert st["pc_max"] == 2 * max(len(e) for e in blocks)
+        r = inputs.random_density(m.nt, 29)
+        z = torch.empty(2 * m.nt, device="cuda", dtype=torch.float64)
+        pb.pb_precond_apply(ctx, torch.tensor(r, device="cuda", dtype=torch.float64), z)
+        N = m.nt
+        zo = np.zeros(2 * N)
+        for e in blocks:
+            idx = np.r_[e, N + e]
+            zo[idx] = np.linalg.solve(A[np.ix_(idx, idx)], r[idx])
+        d = float(np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo))
+        # FP32 entries and Gauss-Jordan lose a few digits against FP64
+        assert d < (1e-10 if prec == pb.PB_FP64 else 2e-4), d
+    finally:
+        pb.pb_destroy(ctx)
 
 
 @pytest.mark.parametrize("prec", [pb.PB_FP64, pb.PB_MIXED])
