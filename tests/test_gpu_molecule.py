@@ -220,6 +220,35 @@ def test_batched_charge_states_match_sequential(mol, prec):
     assert abs(Eb[3] - Eo) < 1e-3 * abs(Eo)
 
 
+def test_many_batched_states_match_single_state_calls(mol):
+    # 18 states: state 0 alone, then 17 in lockstep, whose right-hand sides and energies are
+    # formed 16 states per launch (a group of 16 and a group of 1)
+    m, ph, A = mol
+    rng = np.random.default_rng(23)
+    Q = np.repeat(m.q[None, :], 18, axis=0)
+    for s in range(1, 18):
+        flip = rng.random(m.q.size) < 0.05
+        Q[s, flip] = -Q[s, flip]
+    ctx = _ctx(m, leaf_size=32, eta0=0.7, p=8, precision=pb.PB_MIXED)
+    try:
+        X = torch.zeros((18, 2 * m.nt), device="cuda", dtype=torch.float64)
+        E, infos = pb.pb_solve_states(ctx, Q, X, tol=1e-6, max_iter=300, restart=50, warm=2)
+        assert all(i.status == pb.PB_OK and i.rel_residual <= 1.5e-6 for i in infos)
+        for s in (1, 9, 16, 17):
+            pb.pb_set_charges(ctx, Q[s])
+            # the batched energy against the single-state energy of the same solution
+            Es = pb.pb_solvation_energy(ctx, X[s].contiguous())
+            assert abs(E[s] - Es) < 1e-7 * abs(Es), (s, E[s], Es)
+            # and the batched solution against a single solve of that state
+            x = torch.zeros(2 * m.nt, device="cuda", dtype=torch.float64)
+            info = pb.pb_gmres_solve(ctx, x, tol=1e-6, max_iter=300, restart=50)
+            assert info.status == pb.PB_OK
+            d = float((X[s] - x).norm() / x.norm())
+            assert d < 1e-4, (s, d)
+    finally:
+        pb.pb_destroy(ctx)
+
+
 def test_multi_entry_points_reject_bad_sizes(mol):
     m, ph, A = mol
     ctx = _ctx(m, leaf_size=32, eta0=0.7, p=6, precision=pb.PB_MIXED)
