@@ -443,7 +443,7 @@ def run_ours(a):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        v, nrows, dt = cpu_oracle_rate(mesh, budget_s=12.0)
+        v, nrows, dt = cpu_oracle_rate(mesh, budget_s=20.0)
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{nrows} dense Galerkin rows of A x of the {N}-triangle workload ({dt:.1f} s)"}
     if rank == 0:
