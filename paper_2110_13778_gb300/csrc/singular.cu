@@ -485,12 +485,12 @@ static void ss_table(int qs, SsTable& T)
         }
 }
 
-// The cube points of one pair's class (lane, lane + stride, ...). One body serves the shared-
-// vertex and shared-edge classes (the table's zero coefficients drop the merged edge vectors).
-// IDENT: identical triangles, where x - y lies in the triangle's own plane (only a0, a1 are
+// The cube points of one pair's class (lane, lane + stride, ...), one body per class: CLS = 0,
+// a shared vertex (all four coefficients); 1, a shared edge (b0 = 0: eQ0 = eP0 is merged into
+// a0); 2, identical triangles, where x - y lies in the triangle's own plane (only a0, a1 are
 // nonzero) and both normal projections vanish, so only parts 0 and 1 of the kernel remain.
 // Pairs are grouped by class, so the warps that run each body are uniform.
-template <bool IDENT>
+template <int CLS>
 __device__ __forceinline__ void ss_points_ff(int lane, const float2* __restrict__ tab, int tn, int off, int cnt,
                                              const ff (*eP)[3], const ff (*eQ)[3], const ff* proj, ff nxny, ff kap,
                                              ff* acc, int stride)
@@ -498,7 +498,7 @@ __device__ __forceinline__ void ss_points_ff(int lane, const float2* __restrict_
     for (int i = off + lane; i < off + cnt; i += stride) {
         const ff a0 = ld_ff(tab + i), a1 = ld_ff(tab + tn + i), w = ld_ff(tab + 4 * tn + i);
         ff d[3];
-        if (IDENT) {
+        if (CLS == 2) {
             for (int c = 0; c < 3; ++c) d[c] = ff_add(ff_mul(a0, eP[0][c]), ff_mul(a1, eP[1][c]));
             const ff r2 = ff_add(ff_add(ff_sqr(d[0]), ff_sqr(d[1])), ff_sqr(d[2]));
             ff P[2];
@@ -506,15 +506,15 @@ __device__ __forceinline__ void ss_points_ff(int lane, const float2* __restrict_
             acc[0] = ff_add(acc[0], ff_mul(w, P[0]));
             acc[1] = ff_add(acc[1], ff_mul(w, P[1]));
         } else {
-            const ff b0 = ld_ff(tab + 2 * tn + i), b1 = ld_ff(tab + 3 * tn + i);
+            const ff b0 = CLS == 1 ? ff{0.f, 0.f} : ld_ff(tab + 2 * tn + i), b1 = ld_ff(tab + 3 * tn + i);
             for (int c = 0; c < 3; ++c) {
                 d[c] = ff_add(ff_mul(a0, eP[0][c]), ff_mul(a1, eP[1][c]));
-                d[c] = ff_sub(d[c], ff_add(ff_mul(b0, eQ[0][c]), ff_mul(b1, eQ[1][c])));
+                d[c] = ff_sub(d[c], CLS == 1 ? ff_mul(b1, eQ[1][c]) : ff_add(ff_mul(b0, eQ[0][c]), ff_mul(b1, eQ[1][c])));
             }
             const ff r2 = ff_add(ff_add(ff_sqr(d[0]), ff_sqr(d[1])), ff_sqr(d[2]));
             // n_x.(x - y) and n_y.(x - y): a triangle's own edges are orthogonal to its normal;
             // proj = {n_x.eQ0, n_x.eQ1, n_y.eP0, n_y.eP1}
-            const ff nxd = ff_neg(ff_add(ff_mul(b0, proj[0]), ff_mul(b1, proj[1])));
+            const ff nxd = ff_neg(CLS == 1 ? ff_mul(b1, proj[1]) : ff_add(ff_mul(b0, proj[0]), ff_mul(b1, proj[1])));
             const ff nyd = ff_add(ff_mul(a0, proj[2]), ff_mul(a1, proj[3]));
             ff P[6];
             ff_parts<6>(r2, nxd, nyd, nxny, kap, P);
@@ -630,8 +630,9 @@ __global__ void __launch_bounds__(128) k_singular_ff1(int ncanon, const int* __r
     }
     const int off = ns == 3 ? toffs.z : ns == 2 ? toffs.y : toffs.x;
     const int cnt = ns == 3 ? tcnts.z : ns == 2 ? tcnts.y : tcnts.x;
-    if (ns == 3) ss_points_ff<true>(sub, tab, tn, off, cnt, eP, eQ, proj, nxny, kap, acc, SS_LPP);
-    else ss_points_ff<false>(sub, tab, tn, off, cnt, eP, eQ, proj, nxny, kap, acc, SS_LPP);
+    if (ns == 3) ss_points_ff<2>(sub, tab, tn, off, cnt, eP, eQ, proj, nxny, kap, acc, SS_LPP);
+    else if (ns == 2) ss_points_ff<1>(sub, tab, tn, off, cnt, eP, eQ, proj, nxny, kap, acc, SS_LPP);
+    else ss_points_ff<0>(sub, tab, tn, off, cnt, eP, eQ, proj, nxny, kap, acc, SS_LPP);
     // the pair's own SS_LPP lanes, all alive (a pair's lanes leave together)
     const unsigned gmask = ((1u << SS_LPP) - 1u) << ((threadIdx.x & 31) & ~(SS_LPP - 1));
     for (int m = 0; m < 6; ++m)
