@@ -254,9 +254,10 @@ def peaks(sm_max_mhz, measured=None):
 FLOPS_PER_SS_POINT = 100  # FP64 formula count of one Sauter-Schwab point (maps, kernel parts, sums)
 # FP32 instructions of one float-float Sauter-Schwab point by class (one shared vertex, a shared
 # edge, identical), counted from csrc/singular.cu and csrc/ff.cuh: the primitives cost two-sum 6,
-# ff_add 11, ff_mul 7, ff_sqr 7, ff_rsqrt 25, the screening series 122, the six kernel parts 350
-# (228 for the two of identical triangles), plus the point's x - y, r^2, projections and sums.
-FF_INST_PER_SS_POINT = {1: 734, 2: 662, 3: 382}
+# ff_add 11, ff_mul 7, ff_sqr 7, ff_rsqrt 25, the screening series 122; the six weighted kernel
+# parts with their accumulation 409 (245 for the two of identical triangles), plus the point's
+# x - y (183 / 129 / 75 by class), r^2 (43) and normal projections (50 / 32 / 0).
+FF_INST_PER_SS_POINT = {1: 685, 2: 613, 3: 363}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the same kernel build, or None,
 # both captured on this workload (81920 triangles): k_near_tile 5.79 MB, k_singular_ff1 20.73 MB
 TRAFFIC_BYTES = {"near": 5.79e6, "m2l": None, "singular": 2.073e7, "pcbuild": None}

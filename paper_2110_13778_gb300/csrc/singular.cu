@@ -374,6 +374,38 @@ __device__ __forceinline__ void ff_parts(ff r2, ff nxd, ff nyd, ff nxny, ff kap,
     P[5] = ff_mul(P[4], e1);
 }
 
+// The parts of ff_parts, weighted by a quadrature weight w that carries the 1 / (4 pi), added
+// into acc[0 .. PARTS): w is folded into 1 / r once (w / r, w / r^3), so each part costs one
+// product fewer than forming it and then weighting it.
+template <int PARTS>
+__device__ __forceinline__ void ff_parts_w(ff w, ff r2, ff nxd, ff nyd, ff nxny, ff kap, ff* acc)
+{
+    ff rinv = ff_rsqrt(r2);
+    ff r = ff_mul(r2, rinv);
+    ff t = ff_mul(kap, r);
+    ff E, g;
+    ff_screen(t, E, g);
+    ff tE = ff_mul(t, E);
+    ff c1 = ff_neg(ff_add(g, tE));
+    ff rinv2 = ff_sqr(rinv);
+    const ff wri = ff_mul(w, rinv);       // w / (4 pi r)
+    const ff wri3 = ff_mul(wri, rinv2);   // w / (4 pi r^3)
+    acc[0] = ff_sub(acc[0], ff_mul(E, wri));
+    if (PARTS == 2) {
+        acc[1] = ff_sub(acc[1], ff_mul(wri3, ff_mul(c1, nxny)));
+        return;
+    }
+    // c3 = -3 g - t^2 - t E (3 + t)
+    ff c3 = ff_neg(ff_add(ff_add(ff_mul_f(g, 3.0f), ff_sqr(t)), ff_mul(tE, ff_add_f(t, 3.0f))));
+    acc[1] = ff_add(acc[1], ff_mul(wri3, ff_sub(ff_mul(ff_mul(c3, ff_mul(nxd, nyd)), rinv2), ff_mul(c1, nxny))));
+    ff e1 = ff_add_f(ff_neg(c1), 1.0f);
+    const ff p2 = ff_mul(nyd, wri3), p4 = ff_mul(nxd, wri3);
+    acc[2] = ff_add(acc[2], p2);
+    acc[3] = ff_add(acc[3], ff_mul(p2, e1));
+    acc[4] = ff_add(acc[4], p4);
+    acc[5] = ff_add(acc[5], ff_mul(p4, e1));
+}
+
 __device__ __forceinline__ ff ff_dot3(const ff* a, const ff* b)
 {
     return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
@@ -427,7 +459,7 @@ __device__ __forceinline__ void ff_edge(const float2* rec, int a, int b, ff* e)
 
 // Table of cube points per class (0: one shared vertex, 1: shared edge, 2: identical), each
 // record the float-float coefficients (a0, a1, b0, b1) of x - y = a0 eP0 + a1 eP1 - b0 eQ0 -
-// b1 eQ1 and the weight w (Gauss weights x Jacobian x symmetry factor). For a shared edge
+// b1 eQ1 and the weight w (Gauss weights x Jacobian x symmetry factor x 1 / (4 pi)). For a shared edge
 // eQ0 = eP0 is merged into a0; for identical triangles eQ = eP is merged into a0, a1.
 struct SsTable {
     std::vector<float2> rec;  // [5][n]: a0, a1, b0, b1, w
@@ -471,7 +503,7 @@ static void ss_table(int qs, SsTable& T)
                     co[3] = yh[1];
                 }
                 for (int m = 0; m < 4; ++m) f[m].push_back(co[m]);
-                f[4].push_back(w);
+                f[4].push_back(w * 0.07957747154594767);  // the weight carries the 1 / (4 pi)
                 ++n;
             }
         }
@@ -501,10 +533,7 @@ __device__ __forceinline__ void ss_points_ff(int lane, const float2* __restrict_
         if (CLS == 2) {
             for (int c = 0; c < 3; ++c) d[c] = ff_add(ff_mul(a0, eP[0][c]), ff_mul(a1, eP[1][c]));
             const ff r2 = ff_add(ff_add(ff_sqr(d[0]), ff_sqr(d[1])), ff_sqr(d[2]));
-            ff P[2];
-            ff_parts<2>(r2, ff{0.f, 0.f}, ff{0.f, 0.f}, nxny, kap, P);
-            acc[0] = ff_add(acc[0], ff_mul(w, P[0]));
-            acc[1] = ff_add(acc[1], ff_mul(w, P[1]));
+            ff_parts_w<2>(w, r2, ff{0.f, 0.f}, ff{0.f, 0.f}, nxny, kap, acc);
         } else {
             const ff b0 = CLS == 1 ? ff{0.f, 0.f} : ld_ff(tab + 2 * tn + i), b1 = ld_ff(tab + 3 * tn + i);
             for (int c = 0; c < 3; ++c) {
@@ -516,9 +545,7 @@ __device__ __forceinline__ void ss_points_ff(int lane, const float2* __restrict_
             // proj = {n_x.eQ0, n_x.eQ1, n_y.eP0, n_y.eP1}
             const ff nxd = ff_neg(CLS == 1 ? ff_mul(b1, proj[1]) : ff_add(ff_mul(b0, proj[0]), ff_mul(b1, proj[1])));
             const ff nyd = ff_add(ff_mul(a0, proj[2]), ff_mul(a1, proj[3]));
-            ff P[6];
-            ff_parts<6>(r2, nxd, nyd, nxny, kap, P);
-            for (int m = 0; m < 6; ++m) acc[m] = ff_add(acc[m], ff_mul(w, P[m]));
+            ff_parts_w<6>(w, r2, nxd, nyd, nxny, kap, acc);
         }
     }
 }
