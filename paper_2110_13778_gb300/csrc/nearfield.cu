@@ -201,15 +201,15 @@ __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nitems, const 
                 const float tE = tt * E;
                 const float c1 = -g - tE;
                 const float c3 = -3.f * g - tt * tt - tE * (3.f + tt);
-                const float ri = rinv * i4pi, ri3 = ri * rinv * rinv;
+                // a dropped pair (ok false) zeroes 1 / (4 pi r) and with it every term
+                const float ri = rinv * (ok ? i4pi : 0.f), ri3 = ri * rinv * rinv;
                 const float nxd = tn.x * dx + tn.y * dy + tn.z * dz;
                 const float nyd = b.x * dx + b.y * dy + b.z * dz;
                 const float nxny = tn.x * b.x + tn.y * b.y + tn.z * b.z;
                 const float e1 = 1.f - c1;
-                const float z = ok ? 1.f : 0.f;
-                const float f2 = ri3 * (eps * e1 - 1.f) * z, f3 = ri3 * (1.f - e1 * inv_eps) * z;
-                const float K1 = -E * ri * z;
-                const float K4 = ri3 * (c3 * nxd * nyd * rinv * rinv - c1 * nxny) * z;
+                const float f2 = ri3 * (eps * e1 - 1.f), f3 = ri3 * (1.f - e1 * inv_eps);
+                const float K1 = -E * ri;
+                const float K4 = ri3 * (c3 * nxd * nyd * rinv * rinv - c1 * nxny);
                 s1 += K1 * b.w + (nyd * f2) * a.w;
                 s2 += (-nxd * f3) * b.w + K4 * a.w;
                 if (!diag) {
