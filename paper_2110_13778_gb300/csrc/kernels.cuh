@@ -61,12 +61,13 @@ __device__ __forceinline__ void pb_screen<double>(double t, double& E, double& g
     g = E + t;
 }
 
-// K[0..3] = K1..K4 for d = x - y, target normal n_x, source normal n_y.
+// K[0..3] = K1..K4 for d = x - y, target normal n_x, source normal n_y, all scaled by `scale`
+// (0 drops a pair without extra products: it multiplies 1 / (4 pi r), which every term carries).
 template <class R>
 __device__ __forceinline__ void pb_kernels(R dx, R dy, R dz, R nxx, R nxy, R nxz, R nyx, R nyy, R nyz,
-                                           R eps, R inv_eps, R kappa, R* K)
+                                           R eps, R inv_eps, R kappa, R* K, R scale = R(1))
 {
-    const R i4pi = R(0.07957747154594767);  // 1 / (4 pi)
+    const R i4pi = R(0.07957747154594767) * scale;  // 1 / (4 pi), scaled
     R r2 = dx * dx + dy * dy + dz * dz;
     R rinv = PbKer<R>::rsqrt_(r2);
     R r = r2 * rinv;

@@ -307,12 +307,8 @@ __global__ void __launch_bounds__(256, 2) k_near32m(int nt, int nitems, const in
             float dy = (tp.y - a.y) + (tl.y - l.y);
             float dz = (tp.z - a.z) + (tl.z - l.z);
             if (j == k) dx = 1.0f;  // the identical pair is the correction's; keep r finite
-            pb_kernels<float>(dx, dy, dz, tn.x, tn.y, tn.z, b.x, b.y, b.z, eps, inv_eps, kappa, K);
-            const float z = (j == k) ? 0.f : 1.f;
-            K[0] *= z;
-            K[1] *= z;
-            K[2] *= z;
-            K[3] *= z;
+            pb_kernels<float>(dx, dy, dz, tn.x, tn.y, tn.z, b.x, b.y, b.z, eps, inv_eps, kappa, K,
+                              (j == k) ? 0.f : 1.f);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 const float2 d = s_d[r * 32 + q];
