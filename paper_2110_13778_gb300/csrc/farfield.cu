@@ -478,9 +478,29 @@ __device__ __forceinline__ ff ld_ffs(const float2* p)
     return {v.x, v.y};
 }
 
+// Mirror slots: the interaction lists are symmetric (c' in I(c) exactly when c in I(c')), and the
+// tensors of the two directions differ only by (-1)^|g| (G is even in x_c - x_c'). mirror[s] is
+// the slot of the reversed pair, or -1 for padding (or if none is found).
+__global__ void k_m2l_mirror(int nslots, const int* __restrict__ soff, const int* __restrict__ stgt,
+                             const int* __restrict__ ssrc, int* __restrict__ mirror)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslots) return;
+    const int q = ssrc[s], t = stgt[s];
+    int m = -1;
+    if (q >= 0)
+        for (int u = soff[q]; u < soff[q + 1]; ++u)
+            if (ssrc[u] == t) {
+                m = u;
+                break;
+            }
+    mirror[s] = m;
+}
+
 __global__ void __launch_bounds__(256) k_m2l_setup_ff(int nslots, int p, double kappa, const int* __restrict__ stgt,
                                                       const int* __restrict__ ssrc, const double* __restrict__ xc,
-                                                      float* __restrict__ D0, float* __restrict__ Dk)
+                                                      const int* __restrict__ mirror, float* __restrict__ D0,
+                                                      float* __restrict__ Dk)
 {
     extern __shared__ float2 m2lf[];
     const int T = pb_nterms(p);
@@ -499,6 +519,12 @@ __global__ void __launch_bounds__(256) k_m2l_setup_ff(int nslots, int p, double 
         }
         return;
     }
+    // a pair and its reverse are computed once, by the slot with the smaller index (only when
+    // the two slots name each other)
+    int ms = mirror[s];
+    if (ms >= 0 && mirror[ms] != s) ms = -1;
+    if (ms >= 0 && ms < s) return;
+    const size_t mbase = ms >= 0 ? ((size_t)(ms >> 5) * T) * 32 + (ms & 31) : 0;
     const ff d[3] = {ff_from(xc[3 * c] - xc[3 * c2]), ff_from(xc[3 * c + 1] - xc[3 * c2 + 1]),
                      ff_from(xc[3 * c + 2] - xc[3 * c2 + 2])};
     const ff d2 = ff_add(ff_add(ff_sqr(d[0]), ff_sqr(d[1])), ff_sqr(d[2]));
@@ -556,6 +582,11 @@ __global__ void __launch_bounds__(256) k_m2l_setup_ff(int nslots, int p, double 
         const ff a = ff_mul_f(ld_ffs(F0 + k), f), b = ff_mul_f(ld_ffs(Fk + k), f);
         D0[base + (size_t)k * 32] = a.h + a.l;
         Dk[base + (size_t)k * 32] = b.h + b.l;
+        if (ms >= 0) {  // the reversed pair: (-1)^|g|
+            const float sg = (k1 + k2 + k3) & 1 ? -1.f : 1.f;
+            D0[mbase + (size_t)k * 32] = sg * (a.h + a.l);
+            Dk[mbase + (size_t)k * 32] = sg * (b.h + b.l);
+        }
     }
 }
 
@@ -992,13 +1023,14 @@ static int m2l_fast_plan(pb_ctx* c, PbLevel& lv)
     lv.slot_off = (int*)pb_alloc_on(c, sizeof(int) * (lv.ncl + 1), fs);
     lv.slot_src = (int*)pb_alloc_on(c, sizeof(int) * (lv.nslots + 1), fs);
     lv.slot_tgt = (int*)pb_alloc_on(c, sizeof(int) * (lv.nslots + 1), fs);
+    lv.slot_mirror = (int*)pb_alloc_on(c, sizeof(int) * (lv.nslots + 1), fs);
     lv.D0 = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
     lv.Dk = pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs);
     // gathered moments: the FP64 contraction only (the FP32 kernel reads the moments itself)
     const bool gath = c->prm.precision != PB_MIXED;
     lv.Mg0 = gath ? pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs) : nullptr;
     lv.Mgk = gath ? pb_alloc_on(c, rs * (size_t)lv.nslots * T, fs) : nullptr;
-    if (!lv.slot_off || !lv.slot_src || !lv.slot_tgt || !lv.D0 || !lv.Dk || (gath && (!lv.Mg0 || !lv.Mgk)))
+    if (!lv.slot_off || !lv.slot_src || !lv.slot_tgt || !lv.slot_mirror || !lv.D0 || !lv.Dk || (gath && (!lv.Mg0 || !lv.Mgk)))
         return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
     // (the host vectors live in the level until the next build, so no synchronisation)
     PB_CUDA(c, cudaMemcpyAsync(lv.slot_off, soff.data(), sizeof(int) * (lv.ncl + 1), cudaMemcpyHostToDevice, fs));
@@ -1017,8 +1049,11 @@ static int m2l_fast_tables(pb_ctx* c, PbLevel& lv)
     if (nb == 0) return PB_OK;
     if (c->prm.precision == PB_MIXED) {
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_m2l_mirror<<<(unsigned)((lv.nslots + 255) / 256), 256, 0, fs>>>((int)lv.nslots, lv.slot_off, lv.slot_tgt,
+                                                                      lv.slot_src, lv.slot_mirror);
+        PB_LAUNCH(c);
         k_m2l_setup_ff<<<nb, 256, smem, fs>>>(lv.nslots, lv.p, c->prm.kappa, lv.slot_tgt, lv.slot_src, lv.xc,
-                                                  (float*)lv.D0, (float*)lv.Dk);
+                                                  lv.slot_mirror, (float*)lv.D0, (float*)lv.Dk);
     } else {
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_m2l_setup<double><<<nb, 256, smem, fs>>>(lv.nslots, lv.p, c->prm.kappa, lv.slot_tgt, lv.slot_src, lv.xc,

@@ -54,6 +54,7 @@ struct PbLevel {
     void* Mg0 = nullptr;     // scaled source moments gathered into the slot layout (per product)
     void* Mgk = nullptr;
     int* slot_tgt = nullptr; // [nslots] target cluster of each slot (table setup)
+    int* slot_mirror = nullptr;  // [nslots] slot of the reversed pair (table setup)
     std::vector<int> h_slot[3];  // host sources of slot_off, slot_src, slot_tgt (kept for the async uploads)
 };
 
