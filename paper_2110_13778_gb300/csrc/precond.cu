@@ -488,6 +488,10 @@ int pb_precond_plan(pb_ctx* c)
             const int m = 2 * (pb_[k + 1] - pb_[k]);
             if (m <= lim[q] && (q == 0 || m > lim[q - 1])) ids.push_back(k);
         }
+        // largest blocks first, so that the last wave of a class holds the shortest inversions
+        std::stable_sort(ids.begin() + c->pc_cls[q], ids.end(), [&](int x, int y) {
+            return pb_[x + 1] - pb_[x] > pb_[y + 1] - pb_[y];
+        });
     }
     c->pc_cls[3] = (int)ids.size();
     c->pc_begin = (int*)pb_alloc(c, sizeof(int) * (nb + 1));
