@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(M2M_T) k_m2m(int pp, int pc, const int* __rest
     s0 += blockIdx.y * pstr;
     sk += blockIdx.y * pstr;
     __shared__ R e[3][PB_PMAX + 1];
-    extern __shared__ __align__(16) unsigned char dsm[];
+    extern __shared__ __align__(128) unsigned char dsm[];
     const int Tp = pb_nterms(pp), Tc = pb_nterms(pc);
     R* A0 = (R*)dsm;  // [Tp] each
     R* Ak = A0 + Tp;
