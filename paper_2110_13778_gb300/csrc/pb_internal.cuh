@@ -125,11 +125,14 @@ struct pb_ctx {
     // host copies made by the build: the leaf ranges (read back once by the tree build), and
     // the sources of the build's host-to-device uploads, kept until the next build so that
     // those copies need no synchronisation
-    std::vector<int> h_leaf_begin, h_near_off, h_near_idx, h_up_i[6];
-    std::vector<int4> h_up_i4, h_up_i4m;
-    std::vector<long long> h_up_l;
-    std::vector<double> h_up_d;
-    std::vector<float2> h_up_f2;
+    std::vector<int> h_leaf_begin, h_near_off, h_near_idx;  // leaf ranges and leaf neighbour lists
+    // h_up_i: [0] chunk leaf, [1] chunk first element, [2] preconditioner block ranges, [3] block
+    // ids by size class, [4] near-field pair tiles, [5] several-vector directed tiles
+    std::vector<int> h_up_i[6];
+    std::vector<int4> h_up_i4, h_up_i4m;  // near-field work items: pair tiles, directed tiles
+    std::vector<long long> h_up_l;        // preconditioner block offsets
+    std::vector<double> h_up_d;           // singular quadrature: Gauss-Legendre nodes and weights
+    std::vector<float2> h_up_f2;          // singular quadrature: float-float cube-point table
     // preconditioner: per leaf a dense (2n x 2n) inverse, unknowns [phi of leaf; dphi of leaf]
     int far_nr = 1;               // right-hand sides the far-field work arrays hold
     int npcblk = 0;               // preconditioner blocks
