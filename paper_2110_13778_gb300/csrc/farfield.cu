@@ -398,7 +398,8 @@ __global__ void __launch_bounds__(FAR_T) k_m2l(int p, double kappa, const int* _
 template <class R>
 __global__ void __launch_bounds__(256) k_m2l_setup(int nslots, int p, double kappa, const int* __restrict__ stgt,
                                                    const int* __restrict__ ssrc, const double* __restrict__ xc,
-                                                   R* __restrict__ D0, R* __restrict__ Dk)
+                                                   const int* __restrict__ mirror, R* __restrict__ D0,
+                                                   R* __restrict__ Dk)
 {
     extern __shared__ double m2ls[];
     const int T = pb_nterms(p);
@@ -418,6 +419,12 @@ __global__ void __launch_bounds__(256) k_m2l_setup(int nslots, int p, double kap
         }
         return;
     }
+    // a pair and its reverse are computed once, by the slot with the smaller index (only when
+    // the two slots name each other); the reverse differs by (-1)^|g|
+    int ms = mirror[s];
+    if (ms >= 0 && mirror[ms] != s) ms = -1;
+    if (ms >= 0 && ms < s) return;
+    const size_t mbase = ms >= 0 ? ((size_t)(ms >> 5) * T) * 32 + (ms & 31) : 0;
     const double d[3] = {xc[3 * c] - xc[3 * c2], xc[3 * c + 1] - xc[3 * c2 + 1], xc[3 * c + 2] - xc[3 * c2 + 2]};
     const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (lane == 0) {
@@ -458,6 +465,11 @@ __global__ void __launch_bounds__(256) k_m2l_setup(int nslots, int p, double kap
         double f = c_fact[k1] * c_fact[k2] * c_fact[k3];
         D0[base + (size_t)k * 32] = (R)(F0[k] * f);
         Dk[base + (size_t)k * 32] = (R)(Fk[k] * f);
+        if (ms >= 0) {
+            const double sg = (k1 + k2 + k3) & 1 ? -f : f;
+            D0[mbase + (size_t)k * 32] = (R)(F0[k] * sg);
+            Dk[mbase + (size_t)k * 32] = (R)(Fk[k] * sg);
+        }
     }
 }
 
@@ -1047,17 +1059,17 @@ static int m2l_fast_tables(pb_ctx* c, PbLevel& lv)
     const size_t smem = sizeof(double) * 3 * (size_t)T * 8;
     const unsigned nb = (unsigned)((lv.nslots + 7) / 8);
     if (nb == 0) return PB_OK;
+    k_m2l_mirror<<<(unsigned)((lv.nslots + 255) / 256), 256, 0, fs>>>((int)lv.nslots, lv.slot_off, lv.slot_tgt,
+                                                                  lv.slot_src, lv.slot_mirror);
+    PB_LAUNCH(c);
     if (c->prm.precision == PB_MIXED) {
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_mirror<<<(unsigned)((lv.nslots + 255) / 256), 256, 0, fs>>>((int)lv.nslots, lv.slot_off, lv.slot_tgt,
-                                                                      lv.slot_src, lv.slot_mirror);
-        PB_LAUNCH(c);
         k_m2l_setup_ff<<<nb, 256, smem, fs>>>(lv.nslots, lv.p, c->prm.kappa, lv.slot_tgt, lv.slot_src, lv.xc,
                                                   lv.slot_mirror, (float*)lv.D0, (float*)lv.Dk);
     } else {
         PB_CUDA(c, cudaFuncSetAttribute(k_m2l_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_m2l_setup<double><<<nb, 256, smem, fs>>>(lv.nslots, lv.p, c->prm.kappa, lv.slot_tgt, lv.slot_src, lv.xc,
-                                                       (double*)lv.D0, (double*)lv.Dk);
+                                                       lv.slot_mirror, (double*)lv.D0, (double*)lv.Dk);
     }
     PB_LAUNCH(c);
     return PB_OK;
