@@ -148,3 +148,46 @@ def test_fmm_converges_to_dense(small_sphere):
     # adaptive order is at least as accurate as its finest-level order
     ea = np.linalg.norm(fmm.matvec(tr, V, T, x, ph, 2, adaptive=True, A=A) - y) / np.linalg.norm(y)
     assert ea <= errs[0]
+
+
+def _one_axis_shifts(v, idx, e, up):
+    """Three one-axis passes over the degree-<=p layout idx: x, then y, then z. For each
+    output multi-index the pass sums e[axis][|k - j|] v[... j on that axis ...] over j <= k
+    (up=False) or j >= k (up=True), staying inside the layout."""
+    pos = {a: i for i, a in enumerate(idx)}
+    p = max(sum(a) for a in idx)
+    for axis in range(3):
+        out = np.zeros_like(v)
+        for i, a in enumerate(idx):
+            s = 0.0
+            rng = range(a[axis], p - sum(a) + a[axis] + 1) if up else range(0, a[axis] + 1)
+            for j in rng:
+                b = list(a)
+                b[axis] = j
+                s += e[axis][abs(a[axis] - j)] * v[pos[tuple(b)]]
+            out[i] = s
+        v = out
+    return v
+
+
+def test_scaled_forms_make_translations_one_axis_shifts():
+    # the reading behind the GPU translations: with moments stored as (-1)^|b| m / b! (the form
+    # the MtL sum consumes), MtM is a shift by e[g] = (-t)^g / g!, one factor per axis; with
+    # local coefficients scaled by a!, LtL is the upward shift by t^g / g!
+    rng = np.random.default_rng(4)
+    p = 6
+    idx = taylor.multi_indices(p)
+    sgn = np.array([(-1.0) ** sum(a) for a in idx])
+    fac = np.array([factorial(a[0]) * factorial(a[1]) * factorial(a[2]) for a in idx], float)
+    t = np.array([0.3, -0.7, 0.45])  # x_child - x_parent
+    m_child = rng.normal(size=len(idx))
+    m_parent = fmm._shift_matrix(idx, idx, t) @ m_child  # eqMtM
+    e_m = [[(-t[d]) ** k / factorial(k) for k in range(p + 1)] for d in range(3)]
+    got = _one_axis_shifts(sgn * m_child / fac, idx, e_m, up=False)
+    assert np.allclose(got, sgn * m_parent / fac, rtol=1e-12, atol=1e-13)
+    # LtL: lam_child = S^T lam_parent with S the shift of the child centre relative to the parent
+    lam_parent = rng.normal(size=len(idx))
+    lam_child = fmm._shift_matrix(idx, idx, t).T @ lam_parent
+    e_l = [[t[d] ** k / factorial(k) for k in range(p + 1)] for d in range(3)]
+    got = _one_axis_shifts(fac * lam_parent, idx, e_l, up=True)
+    assert np.allclose(got, fac * lam_child, rtol=1e-12, atol=1e-12)
