@@ -191,3 +191,41 @@ def test_scaled_forms_make_translations_one_axis_shifts():
     e_l = [[t[d] ** k / factorial(k) for k in range(p + 1)] for d in range(3)]
     got = _one_axis_shifts(fac * lam_parent, idx, e_l, up=True)
     assert np.allclose(got, fac * lam_child, rtol=1e-12, atol=1e-12)
+
+
+def test_scaled_forms_of_leaf_moments_and_evaluation():
+    # P2M in the stored form: with e_j[b] = d'^b / b!, d' = x_c - y_j, the moments
+    # (-1)^|b| / b! (sum_j w0_j (y_j - x_c)^b - w1_j n_j . grad (y - x_c)^b) equal
+    # S[b] + sum_i G_i[b - e_i], S = sum_j w0_j e_j, G_i = sum_j w1_j n_j,i e_j; LtP: the local
+    # expansion and its normal derivative from a!-scaled coefficients and e[b] = d^b / b!
+    rng = np.random.default_rng(5)
+    p = 5
+    idx = taylor.multi_indices(p)
+    pos = {a: i for i, a in enumerate(idx)}
+    fac = np.array([factorial(a[0]) * factorial(a[1]) * factorial(a[2]) for a in idx], float)
+    sgn = np.array([(-1.0) ** sum(a) for a in idx])
+    xc = np.array([0.2, -0.1, 0.3])
+    y = xc + 0.4 * rng.normal(size=(15, 3))
+    nrm = rng.normal(size=(15, 3))
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    w0, w1 = rng.normal(size=15), rng.normal(size=15)
+    ref = w0 @ fmm._mono(y - xc, idx) - w1 @ fmm._dmono(y - xc, nrm, idx)
+    e = fmm._mono(xc - y, idx) / fac  # e_j[b]
+    S = w0 @ e
+    G = [(w1 * nrm[:, i]) @ e for i in range(3)]
+    got = np.array([S[k] + sum(G[i][pos[tuple(a[q] - (q == i) for q in range(3))]]
+                               for i in range(3) if a[i] > 0) for k, a in enumerate(idx)])
+    assert np.allclose(got, sgn * ref / fac, rtol=1e-12, atol=1e-12)
+    # LtP: value and normal derivative of sum_a lam_a (x - x_c)^a at a target with normal n
+    lam = rng.normal(size=len(idx))
+    x = xc + 0.3 * rng.normal(size=(1, 3))
+    n = np.array([[0.6, -0.48, 0.64]])
+    val = fmm._mono(x - xc, idx) @ lam
+    der = fmm._dmono(x - xc, n, idx) @ lam
+    lh = fac * lam
+    ex = (fmm._mono(x - xc, idx) / fac)[0]
+    up = [[pos.get(tuple(a[q] + (q == i) for q in range(3))) for a in idx] for i in range(3)]
+    got_v = np.dot(lh, ex)
+    got_d = sum(ex[k] * sum(n[0, i] * lh[up[i][k]] for i in range(3) if up[i][k] is not None)
+                for k in range(len(idx)))
+    assert np.isclose(got_v, val[0], rtol=1e-12) and np.isclose(got_d, der[0], rtol=1e-11)
