@@ -110,6 +110,7 @@ extern "C" int pb_autotune(pb_ctx* c, double tol, int matvecs_per_solve, int nrh
     int rc = PB_OK;
     const int G = (int)std::min<long long>((n + 255) / 256, 1024);
     auto fail = [&](int r) {
+        if (r) c->p_level_L = -1;  // a failed tuning leaves no per-level orders behind
         cudaFreeAsync(x, c->st);
         cudaFreeAsync(yref, c->st);
         cudaFreeAsync(y, c->st);
