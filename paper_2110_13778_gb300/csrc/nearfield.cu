@@ -131,6 +131,41 @@ __global__ void k_near_pack(int nt, const float4* __restrict__ e32p, const float
 }
 
 
+// One pair of the tile kernel: the forward terms of target x (position tp + tl, normal tn) from
+// source y (a + l, normal b, densities a.w = A phi, b.w = A dphi), and the reverse terms of y
+// from x (tphi = A phi, tdphi = A dphi of the target). ok false drops the pair (its 1 / (4 pi r)
+// is zeroed; dx is set so that r stays finite).
+struct NearTerms {
+    float f1, f2, r1, r2;
+};
+__device__ __forceinline__ NearTerms near_pair(float4 tp, float4 tn, float4 tl, float tphi, float tdphi, float4 a,
+                                               float4 b, float4 l, bool ok, float eps, float inv_eps, float kappa)
+{
+    const float i4pi = 0.07957747154594767f;
+    float dx = (tp.x - a.x) + (tl.x - l.x);
+    const float dy = (tp.y - a.y) + (tl.y - l.y);
+    const float dz = (tp.z - a.z) + (tl.z - l.z);
+    if (!ok) dx = 1.0f;
+    const float r2d = dx * dx + dy * dy + dz * dz;
+    const float rinv = rsqrtf(r2d);
+    const float r = r2d * rinv, tt = kappa * r;
+    float E, g;
+    pb_screen<float>(tt, E, g);
+    const float tE = tt * E;
+    const float c1 = -g - tE;
+    const float c3 = -3.f * g - tt * tt - tE * (3.f + tt);
+    const float ri = rinv * (ok ? i4pi : 0.f), ri3 = ri * rinv * rinv;
+    const float nxd = tn.x * dx + tn.y * dy + tn.z * dz;
+    const float nyd = b.x * dx + b.y * dy + b.z * dz;
+    const float nxny = tn.x * b.x + tn.y * b.y + tn.z * b.z;
+    const float e1 = 1.f - c1;
+    const float f2 = ri3 * (eps * e1 - 1.f), f3 = ri3 * (1.f - e1 * inv_eps);
+    const float K1 = -E * ri;
+    const float K4 = ri3 * (c3 * nxd * nyd * rinv * rinv - c1 * nxny);
+    return {K1 * b.w + (nyd * f2) * a.w, (-nxd * f3) * b.w + K4 * a.w, K1 * tdphi + (-nxd * f2) * tphi,
+            (nyd * f3) * tdphi + K4 * tphi};
+}
+
 // Both directions of a pair at once, by tiles of one target chunk A (up to 32 targets, lane l
 // holds A_l) and one source chunk B of nb <= 32 sources. K1 and K4 are symmetric in (x, y),
 // and with d = x_i - x_j the double-layer kernels of the reversed pair follow from the same
@@ -179,51 +214,54 @@ __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nitems, const 
                 sbn[wi][lane] = sn[j];
                 sbl[wi][lane] = sl[j];
             }
-            rv1[wi][lane] = 0.f;
-            rv2[wi][lane] = 0.f;
-            __syncwarp();
             float s1 = 0.f, s2 = 0.f;
-            int m = lane % nb;
+            if (!diag && nb == 32) {
+                // a full tile of another chunk: lane l meets source (l + s) mod 32 at step s and
+                // carries that source's reverse sums, which move one lane down after each step;
+                // after 32 steps lane l holds source l's
+                __syncwarp();
+                float q1 = 0.f, q2 = 0.f;
+                int m = lane;
 #pragma unroll 2
-            for (int s = 0; s < nb; ++s) {
-                const float4 a = sbp[wi][m], b = sbn[wi][m], l = sbl[wi][m];
-                float dx = (tp.x - a.x) + (tl.x - l.x);
-                const float dy = (tp.y - a.y) + (tl.y - l.y);
-                const float dz = (tp.z - a.z) + (tl.z - l.z);
-                // drop the identical pair (the correction's) and padding targets, keeping r finite
-                const bool ok = act && !(diag && m == lane);
-                if (!ok) dx = 1.0f;
-                const float r2d = dx * dx + dy * dy + dz * dz;
-                const float rinv = rsqrtf(r2d);
-                const float r = r2d * rinv, tt = kappa * r;
-                float E, g;
-                pb_screen<float>(tt, E, g);
-                const float tE = tt * E;
-                const float c1 = -g - tE;
-                const float c3 = -3.f * g - tt * tt - tE * (3.f + tt);
-                // a dropped pair (ok false) zeroes 1 / (4 pi r) and with it every term
-                const float ri = rinv * (ok ? i4pi : 0.f), ri3 = ri * rinv * rinv;
-                const float nxd = tn.x * dx + tn.y * dy + tn.z * dz;
-                const float nyd = b.x * dx + b.y * dy + b.z * dz;
-                const float nxny = tn.x * b.x + tn.y * b.y + tn.z * b.z;
-                const float e1 = 1.f - c1;
-                const float f2 = ri3 * (eps * e1 - 1.f), f3 = ri3 * (1.f - e1 * inv_eps);
-                const float K1 = -E * ri;
-                const float K4 = ri3 * (c3 * nxd * nyd * rinv * rinv - c1 * nxny);
-                s1 += K1 * b.w + (nyd * f2) * a.w;
-                s2 += (-nxd * f3) * b.w + K4 * a.w;
-                if (!diag) {
-                    atomicAdd(&rv1[wi][m], K1 * tdphi + (-nxd * f2) * tphi);
-                    atomicAdd(&rv2[wi][m], (nyd * f3) * tdphi + K4 * tphi);
+                for (int s = 0; s < 32; ++s) {
+                    const NearTerms t = near_pair(tp, tn, tl, tphi, tdphi, sbp[wi][m], sbn[wi][m], sbl[wi][m], act,
+                                                  eps, inv_eps, kappa);
+                    s1 += t.f1;
+                    s2 += t.f2;
+                    q1 = __shfl_sync(0xffffffffu, q1 + t.r1, (lane + 1) & 31);
+                    q2 = __shfl_sync(0xffffffffu, q2 + t.r2, (lane + 1) & 31);
+                    m = (m + 1) & 31;
                 }
-                m = m + 1 == nb ? 0 : m + 1;
-            }
-            acc1 += (double)s1;
-            acc2 += (double)s2;
-            __syncwarp();
-            if (!diag && lane < nb) {
-                atomicAdd(&ys[j], (double)rv1[wi][lane]);
-                atomicAdd(&ys[nt + j], (double)rv2[wi][lane]);
+                acc1 += (double)s1;
+                acc2 += (double)s2;
+                atomicAdd(&ys[j], (double)q1);
+                atomicAdd(&ys[nt + j], (double)q2);
+            } else {
+                rv1[wi][lane] = 0.f;
+                rv2[wi][lane] = 0.f;
+                __syncwarp();
+                int m = lane % nb;
+#pragma unroll 2
+                for (int s = 0; s < nb; ++s) {
+                    // drop the identical pair (the correction's) and padding targets
+                    const bool ok = act && !(diag && m == lane);
+                    const NearTerms t = near_pair(tp, tn, tl, tphi, tdphi, sbp[wi][m], sbn[wi][m], sbl[wi][m], ok,
+                                                  eps, inv_eps, kappa);
+                    s1 += t.f1;
+                    s2 += t.f2;
+                    if (!diag) {
+                        atomicAdd(&rv1[wi][m], t.r1);
+                        atomicAdd(&rv2[wi][m], t.r2);
+                    }
+                    m = m + 1 == nb ? 0 : m + 1;
+                }
+                acc1 += (double)s1;
+                acc2 += (double)s2;
+                __syncwarp();
+                if (!diag && lane < nb) {
+                    atomicAdd(&ys[j], (double)rv1[wi][lane]);
+                    atomicAdd(&ys[nt + j], (double)rv2[wi][lane]);
+                }
             }
         }
     }
