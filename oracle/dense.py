@@ -1,10 +1,15 @@
 """Dense Galerkin system of Section 2.3 (def:linsys, eq_linsysEntry), solved by LU.
 
-TEST INFRASTRUCTURE (see the package header). Pins, in tests/test_oracle_*.py:
-  * pair integrals -- Sauter-Schwab sub-maps integrate polynomials on tau x tau exactly;
-    coplanar identical pairs give exactly zero K2/K3 integrals; the G0 part of identical and
-    adjacent pairs matches a closed-form inner integral (uniformly charged flat triangle)
-    with high-order outer Gauss quadrature; K1/K4 blocks are symmetric.
+TEST INFRASTRUCTURE (see the package header). Pins:
+  * pair integrals (tests/test_oracle_dense.py) -- Sauter-Schwab sub-maps integrate
+    polynomials on tau x tau exactly; coplanar identical pairs give exactly zero K2/K3
+    integrals; K1/K4 blocks are symmetric; double layers of adjacent pairs against solid
+    angles, K1/K4 against refined midpoint products;
+  * singular terms (tests/test_oracle_singular_pins.py) -- the G0 part of identical,
+    edge- and vertex-adjacent pairs against the closed-form potential of a uniformly charged
+    flat triangle with a graded outer Gauss rule; K1 (all classes) and K4 (identical pairs)
+    against polar-coordinate integrals with closed-form radial parts; dG0/dn of adjacent
+    pairs against solid angles; 1e-8 at qs = 8 and 1e-11 at qs = 12.
   * solve + energy -- Kirkwood closed form (centred charge) and Kirkwood series (off-centre
     charges) within the discretisation error the paper prints in Table 1; the null case
     eps = 1, kappa = 0 gives A = mass matrix and E = 0.
@@ -84,6 +89,18 @@ def pair_integrals(verts, tris, i, j, ph: Phys):
     V, T = _f64(verts), _i32(tris)
     out = np.zeros(4)
     lib().orc_pair_integrals(_dp(V), _ip(T), int(i), int(j), ph.eps, ph.kappa, ph.qs, _dp(out))
+    return out
+
+
+def pair_terms(verts, tris, i, j, kappa, qs):
+    """Sauter-Schwab integrals over tau_a x tau_b (a = min(i, j) carries x, b = max(i, j)
+    carries y) of the eight kernel terms [G0 - Gk, d2Gk/dnx dny - d2G0/dnx dny, dG0/dny,
+    dGk/dny, dG0/dnx, dGk/dnx, G0, Gk] of a touching pair: the numbers the pair integrals are
+    made of, exposed so that each can be pinned on its own."""
+    V, T = _f64(verts), _i32(tris)
+    out = np.zeros(8)
+    if lib().orc_pair_terms(_dp(V), _ip(T), int(i), int(j), float(kappa), int(qs), _dp(out)) < 0:
+        raise ValueError("not a touching pair, or bad quadrature order")
     return out
 
 

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE. This is the oracle for the CUDA FMM path. It follows the paper's
 six-step algorithm (near field, moments, upward pass, interaction phase, downward pass,
-evaluation) with the paper's notation, in the readings the design notes list:
+evaluation) with the paper's notation, read as follows where the paper leaves a choice:
 
   * Tree (Section 2.4, cluster hierarchy): the level-0 cube is the smallest axis-parallel
     cube centred on the bounding box of the vertex array. A triangle belongs to the cube of

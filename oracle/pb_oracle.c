@@ -78,7 +78,8 @@ typedef struct {
 
 /* The six terms the kernels are made of, at x (normal nx) and y (normal ny):
  * Q[0] = G0 - Gk, Q[1] = d2Gk/dnx dny - d2G0/dnx dny, Q[2] = dG0/dny, Q[3] = dGk/dny,
- * Q[4] = dG0/dnx, Q[5] = dGk/dnx. */
+ * Q[4] = dG0/dnx, Q[5] = dGk/dnx; and, for the pins of the singular quadrature only,
+ * Q[6] = G0 and Q[7] = Gk on their own. */
 static void orc_kernel_terms(const double* x, const double* nx, const double* y, const double* ny,
                              const orc_phys* ph, double* Q)
 {
@@ -105,6 +106,8 @@ static void orc_kernel_terms(const double* x, const double* nx, const double* y,
     Q[3] = -gkp * nyd / r;
     Q[4] = g0p * nxd / r;
     Q[5] = gkp * nxd / r;
+    Q[6] = G0;
+    Q[7] = Gk;
 }
 
 /* Kout[0..3] = K1..K4 at target x (normal nx) and source y (normal ny). */
@@ -293,6 +296,52 @@ static void orc_reorder(const int32_t* T, int i, int j, int shared, int32_t* ti,
 }
 
 /* ---------- Galerkin pair integrals I_m(i,j), m = 1..4 ---------- */
+#define ORC_NTERMS 8
+
+/* Sauter-Schwab integrals over tau_first x tau_second of the eight terms of
+ * orc_kernel_terms, x on the first triangle (normal na), y on the second (normal nb).
+ * One quadrature serves both orderings of a touching pair: the rule is always laid out from
+ * the triangle with the smaller index (its shared vertices first, in its order). */
+static void orc_ss_terms(const double* V, const int32_t* T, int first, int second, int shared,
+                         const double* na, const double* nb, double Afirst, double Asecond,
+                         const orc_phys* ph, const double* gx, const double* gw, int qs,
+                         double* acc)
+{
+    int32_t ti[3], tj[3];
+    orc_reorder(T, first, second, shared, ti, tj);
+    double P[3][3], Q[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) {
+            P[a][k] = V[3 * ti[a] + k];
+            Q[a][k] = V[3 * tj[a] + k];
+        }
+    /* The reference triangle {0 <= e2 <= e1 <= 1} has corners (0,0), (1,0), (1,1); the affine
+     * map sending them to P0, P1, P2 is P0 + e1 (P1 - P0) + e2 (P2 - P1). (eqparameter prints
+     * P2 - P0 in the last term, which sends (1,1) to P1 + P2 - P0, outside the element.) */
+    for (int m = 0; m < ORC_NTERMS; ++m) acc[m] = 0.0;
+    for (int a = 0; a < qs; ++a)
+        for (int b = 0; b < qs; ++b)
+            for (int c = 0; c < qs; ++c)
+                for (int d = 0; d < qs; ++d) {
+                    double wq = gw[a] * gw[b] * gw[c] * gw[d];
+                    double xh[12], yh[12], jac[6];
+                    int ns = orc_ss_points(shared, gx[a], gx[b], gx[c], gx[d], xh, yh, jac);
+                    for (int s = 0; s < ns; ++s) {
+                        double x[3], y[3], Qt[ORC_NTERMS];
+                        for (int k = 0; k < 3; ++k) {
+                            x[k] = P[0][k] + xh[2 * s] * (P[1][k] - P[0][k]) +
+                                   xh[2 * s + 1] * (P[2][k] - P[1][k]);
+                            y[k] = Q[0][k] + yh[2 * s] * (Q[1][k] - Q[0][k]) +
+                                   yh[2 * s + 1] * (Q[2][k] - Q[1][k]);
+                        }
+                        orc_kernel_terms(x, na, y, nb, ph, Qt);
+                        for (int m = 0; m < ORC_NTERMS; ++m) acc[m] += wq * jac[s] * Qt[m];
+                    }
+                }
+    /* Jacobian of each affine element map is 2 A */
+    for (int m = 0; m < ORC_NTERMS; ++m) acc[m] *= (2.0 * Afirst) * (2.0 * Asecond);
+}
+
 static void orc_pair(const double* V, const int32_t* T, int i, int j, const orc_phys* ph,
                      const double* gx, const double* gw, int qs, double* I)
 {
@@ -312,49 +361,17 @@ static void orc_pair(const double* V, const int32_t* T, int i, int j, const orc_
         for (int m = 0; m < 4; ++m) I[m] = Ai * Aj * K[m];
         return;
     }
-    /* One quadrature serves both orderings of a touching pair: the rule is always laid out
-     * from the triangle with the smaller index (its shared vertices first, in its order),
-     * and the integrals of (j, i) follow from those of (i, j) by exchanging the roles of the
-     * two normals. */
+    /* the integrals of (j, i) follow from those of (i, j) by exchanging the roles of the two
+     * normals */
     int first = i < j ? i : j, second = i < j ? j : i;
     double na[3], nb[3];
     for (int k = 0; k < 3; ++k) {
         na[k] = (first == i) ? ni[k] : nj[k];
         nb[k] = (first == i) ? nj[k] : ni[k];
     }
-    int32_t ti[3], tj[3];
-    orc_reorder(T, first, second, shared, ti, tj);
-    double P[3][3], Q[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int k = 0; k < 3; ++k) {
-            P[a][k] = V[3 * ti[a] + k];
-            Q[a][k] = V[3 * tj[a] + k];
-        }
-    /* The reference triangle {0 <= e2 <= e1 <= 1} has corners (0,0), (1,0), (1,1); the affine
-     * map sending them to P0, P1, P2 is P0 + e1 (P1 - P0) + e2 (P2 - P1). (eqparameter prints
-     * P2 - P0 in the last term, which sends (1,1) to P1 + P2 - P0, outside the element.) */
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int a = 0; a < qs; ++a)
-        for (int b = 0; b < qs; ++b)
-            for (int c = 0; c < qs; ++c)
-                for (int d = 0; d < qs; ++d) {
-                    double wq = gw[a] * gw[b] * gw[c] * gw[d];
-                    double xh[12], yh[12], jac[6];
-                    int ns = orc_ss_points(shared, gx[a], gx[b], gx[c], gx[d], xh, yh, jac);
-                    for (int s = 0; s < ns; ++s) {
-                        double x[3], y[3], Qt[6];
-                        for (int k = 0; k < 3; ++k) {
-                            x[k] = P[0][k] + xh[2 * s] * (P[1][k] - P[0][k]) +
-                                   xh[2 * s + 1] * (P[2][k] - P[1][k]);
-                            y[k] = Q[0][k] + yh[2 * s] * (Q[1][k] - Q[0][k]) +
-                                   yh[2 * s + 1] * (Q[2][k] - Q[1][k]);
-                        }
-                        orc_kernel_terms(x, na, y, nb, ph, Qt);
-                        for (int m = 0; m < 6; ++m) acc[m] += wq * jac[s] * Qt[m];
-                    }
-                }
-    /* Jacobian of each affine element map is 2 A */
-    for (int m = 0; m < 6; ++m) acc[m] *= (2.0 * Ai) * (2.0 * Aj);
+    double acc[ORC_NTERMS];
+    orc_ss_terms(V, T, first, second, shared, na, nb, first == i ? Ai : Aj, first == i ? Aj : Ai,
+                 ph, gx, gw, qs, acc);
     double eps = ph->eps;
     I[0] = acc[0];
     I[3] = acc[1];
@@ -367,6 +384,28 @@ static void orc_pair(const double* V, const int32_t* T, int i, int j, const orc_
         I[1] = eps * acc[5] - acc[4];
         I[2] = acc[2] - acc[3] / eps;
     }
+}
+
+/* exported for the pins of the singular quadrature: the eight Sauter-Schwab term integrals
+ * (orc_kernel_terms order) of the touching pair (min(i,j), max(i,j)), x on the triangle with
+ * the smaller index. Returns the number of shared vertices, or -1 for a bad order / a pair
+ * that shares no vertex. */
+int orc_pair_terms(const double* V, const int32_t* T, int i, int j, double kappa, int qs,
+                   double* out)
+{
+    double gx[64], gw[64];
+    if (orc_gauss_legendre01(qs, gx, gw)) return -1;
+    int shared = orc_shared(T, i, j);
+    if (shared == 0) return -1;
+    orc_phys ph = {1.0, kappa};
+    int first = i < j ? i : j, second = i < j ? j : i;
+    double c[3], na[3], nb[3], Aa, Ab, u[3], v[3], w[3];
+    orc_tri(V, T, first, u, v, w);
+    orc_geom(u, v, w, c, &Aa, na);
+    orc_tri(V, T, second, u, v, w);
+    orc_geom(u, v, w, c, &Ab, nb);
+    orc_ss_terms(V, T, first, second, shared, na, nb, Aa, Ab, &ph, gx, gw, qs, out);
+    return shared;
 }
 
 /* exported: the four integrals for one ordered pair (target i, source j) */

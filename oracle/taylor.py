@@ -13,7 +13,7 @@ in h = (h1, h2, h3), composed step by step,
 
 each truncated at total degree p. The coefficient of h^gamma is D^gamma G(d)/gamma!.
 
-Pins (tests/test_oracle_taylor.py): degree-0 and degree-1 coefficients equal the closed forms
+Pins (tests/test_oracle_taylor_fmm.py): degree-0 and degree-1 coefficients equal the closed forms
 G(d) and grad G(d); second-order coefficients equal the Hessian; all coefficients to |gamma|
 = 6 agree with central finite differences of the closed form; Gk at kappa = 0 equals G0;
 G0 satisfies Laplace's equation coefficient-wise.

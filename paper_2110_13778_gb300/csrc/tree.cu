@@ -2,8 +2,10 @@
 // (Section 2.4: cluster hierarchy, shrink scheme, def:eta, interaction lists N(c), I(c)).
 //
 // Every floating-point decision that produces an integer (Morton cell, list membership) is
-// made in FP64 with explicitly rounded operations, in the order the design notes fix, so
-// that the result is reproducible bit for bit on any IEEE machine.
+// made in FP64 with explicitly rounded operations in one fixed order (Morton cell:
+// floor((c - origin) * (1024 / side)) clamped to [0, 1023]; neighbour test
+// (rho_c + rho_c')^2 > eta0^2 |x_c - x_c'|^2), so that the result is reproducible bit for
+// bit on any IEEE machine.
 #include <cub/cub.cuh>
 
 #include <algorithm>
