@@ -449,15 +449,16 @@ __global__ void k_scale(long long n, const double* __restrict__ src, const doubl
 }
 
 // Scale a nonzero start x (w = A x) by a = <w, b> / <w, w>, the factor that minimises
-// ||b - a A x||; a start with no positive factor becomes zero. d = {<w, b>, <w, w>}.
+// ||b - a A x||; a start with no positive finite factor (a useless or non-finite guess)
+// becomes exactly zero, so GMRES falls back to the zero start. d = {<w, b>, <w, w>}.
 __global__ void k_start_scale(long long n, const double* __restrict__ d, double* __restrict__ x,
                               double* __restrict__ w)
 {
     const double a = d[1] > 0.0 ? d[0] / d[1] : 0.0;
     const double f = (a > 0.0 && isfinite(a)) ? a : 0.0;
     for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
-        x[i] *= f;
-        w[i] *= f;
+        x[i] = f != 0.0 ? x[i] * f : 0.0;  // 0 * NaN would stay NaN
+        w[i] = f != 0.0 ? w[i] * f : 0.0;
     }
 }
 
@@ -577,6 +578,12 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
     PB_CUDA(c, cudaMemcpyAsync(c->hscal, s.hcol, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     PB_CUDA(c, cudaStreamSynchronize(c->st));
     const double bnorm = sqrt(c->hscal[0]);
+    if (!isfinite(bnorm)) {  // an overflowing or non-finite right-hand side
+        inf.status = PB_ERR_NONFINITE;
+        inf.rel_residual = bnorm;
+        if (info) *info = inf;
+        return PB_ERR_NONFINITE;
+    }
     if (!(bnorm > 0)) {
         PB_CUDA(c, cudaMemsetAsync(xs, 0, sizeof(double) * n, c->st));
         if (info) *info = inf;

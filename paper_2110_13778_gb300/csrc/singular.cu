@@ -21,38 +21,42 @@
 
 __constant__ double c_gx[8], c_gw[8];
 
-// Gauss-Legendre nodes on [0,1] by Newton's method on the Legendre recurrence
+// Gauss-Legendre rule on [0,1] as in Golub and Welsch (Math. Comp. 23, 1969): the nodes are
+// the eigenvalues of the symmetric tridiagonal Jacobi matrix of the Legendre polynomials
+// (zero diagonal, off-diagonal b_k = k / sqrt(4k^2 - 1)), each found here by bisection on its
+// Sturm count (the number of negative pivots of J - xI); the weights follow from the
+// Christoffel function w = 1 / sum_{k<n} q_k(x)^2 of the orthonormal polynomials q_k.
 static void gauss01(int n, double* x, double* w)
 {
-    for (int i = 0; i < n; ++i) {
-        double z = cos(PB_PI * (i + 0.75) / (n + 0.5));
-        for (int it = 0; it < 200; ++it) {
-            double p0 = 1.0, p1 = z;
-            for (int k = 2; k <= n; ++k) {
-                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = p2;
-            }
-            double pn = n == 1 ? z : p1, pm = n == 1 ? 1.0 : p0;
-            double dp = n * (z * pn - pm) / (z * z - 1.0);
-            double dz = pn / dp;
-            z -= dz;
-            if (fabs(dz) < 1e-16) {
-                p0 = 1.0;
-                p1 = z;
-                for (int k = 2; k <= n; ++k) {
-                    double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-                    p0 = p1;
-                    p1 = p2;
-                }
-                pn = n == 1 ? z : p1;
-                pm = n == 1 ? 1.0 : p0;
-                dp = n * (z * pn - pm) / (z * z - 1.0);
-                w[i] = 1.0 / ((1.0 - z * z) * dp * dp);  // 2/(..) on [-1,1], halved for [0,1]
-                x[i] = 0.5 * (1.0 - z);
-                break;
-            }
+    auto b = [](int k) { return k / sqrt(4.0 * k * k - 1.0); };
+    auto below = [&](double t) {  // eigenvalues of J smaller than t
+        int cnt = 0;
+        double d = 1.0;
+        for (int k = 0; k < n; ++k) {
+            double off = k ? b(k) : 0.0;
+            d = -t - (k ? off * off / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            cnt += d < 0.0;
         }
+        return cnt;
+    };
+    for (int i = 0; i < n; ++i) {
+        double lo = -1.0, hi = 1.0;  // all nodes lie in (-1, 1)
+        for (int it = 0; it < 200 && hi - lo > 1e-17; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (mid == lo || mid == hi) break;
+            if (below(mid) > i) hi = mid; else lo = mid;
+        }
+        double t = 0.5 * (lo + hi);
+        double qm = 0.0, q = 1.0 / sqrt(2.0), sum = q * q;
+        for (int k = 0; k + 1 < n; ++k) {
+            double qn = (t * q - (k ? b(k) : 0.0) * qm) / b(k + 1);
+            qm = q;
+            q = qn;
+            sum += q * q;
+        }
+        x[i] = 0.5 * (1.0 + t);
+        w[i] = 0.5 / sum;
     }
 }
 

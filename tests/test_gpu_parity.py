@@ -157,16 +157,23 @@ def test_fmm_p8_within_1e4_of_dense(sphere3):
             pb.pb_destroy(ctx)
 
 
-def test_mixed_matches_oracle_fmm(sphere3):
+@pytest.mark.parametrize("p,adaptive", [(4, 0), (6, 0), (8, 0), (10, 0), (5, 0), (3, 1)])
+def test_mixed_matches_oracle_fmm(sphere3, p, adaptive):
+    # p = 4, 6, 8 run the generated MtL bodies; p = 10, 5 and the adaptive orders (3..6 by
+    # level) the generic FP32 recurrence MtL
     m, ph, A = sphere3
-    ctx = _ctx(m, leaf_size=16, eta0=0.8, p=6, precision=pb.PB_MIXED)
+    ctx = _ctx(m, leaf_size=16, eta0=0.8, p=p, adaptive=adaptive, precision=pb.PB_MIXED)
     try:
         x = inputs.random_density(m.nt, 13)
         y = torch.empty(2 * m.nt, device="cuda", dtype=torch.float64)
         pb.pb_matvec(ctx, _dev(x), y)
         tr = fmm.Tree(m.verts, m.tris, leaf_size=16, eta0=0.8)
-        yo = fmm.matvec(tr, m.verts, m.tris, x, ph, 6, A=A)
+        yo = fmm.matvec(tr, m.verts, m.tris, x, ph, p, adaptive=bool(adaptive), A=A)
         assert _rel(y.cpu().numpy(), yo) < 2e-5
+        yf = torch.empty(2 * m.nt, device="cuda", dtype=torch.float64)
+        pb.pb_matvec_part(ctx, _dev(x), yf, 2)
+        f1, f2 = fmm.far_field(tr, m.verts, m.tris, x, ph, p, adaptive=bool(adaptive))
+        assert _rel(yf.cpu().numpy(), np.r_[f1, f2]) < 1e-4
     finally:
         pb.pb_destroy(ctx)
 
