@@ -139,6 +139,38 @@ def energy(mesh, ph: Phys, x):
     )
 
 
+def matvec(mesh, ph: Phys, x):
+    """The full product A x of def:linsys by rows (no matrix stored): [y1; y2]."""
+    y1, y2 = rows_matvec(mesh.verts, mesh.tris, ph, np.arange(mesh.nt), x)
+    return np.concatenate([y1, y2])
+
+
+def solve_matrix_free(mesh, ph: Phys, tol=1e-11, restart=60, maxiter=40):
+    """A x = b for meshes whose dense matrix does not fit: restarted GMRES (scipy, FP64) over
+    the row-by-row product above, right-scaled by the diagonal of mass terms
+    D = diag(1/2 (1+eps) A_i, 1/2 (1+1/eps) A_i) (the diagonal preconditioner of Section 2.6
+    without its integral part): A D^-1 z = b, x = D^-1 z, so the stopping test is on the true
+    residual. Returns (x, b, relative residual ||b - A x|| / ||b|| recomputed with one more
+    product, products used)."""
+    from scipy.sparse.linalg import LinearOperator, gmres
+
+    n = 2 * mesh.nt
+    _, area, _ = geometry(mesh.verts, mesh.tris)
+    d = np.concatenate([0.5 * (1.0 + ph.eps) * area, 0.5 * (1.0 + 1.0 / ph.eps) * area])
+    count = [0]
+
+    def mv(z):
+        count[0] += 1
+        return matvec(mesh, ph, np.asarray(z, dtype=np.float64).ravel() / d)
+
+    b = rhs(mesh, ph)
+    op = LinearOperator((n, n), matvec=mv, dtype=np.float64)
+    z, info = gmres(op, b, rtol=tol, atol=0.0, restart=restart, maxiter=maxiter)
+    x = z / d
+    res = np.linalg.norm(b - matvec(mesh, ph, x)) / np.linalg.norm(b)
+    return x, b, float(res), count[0] + 1
+
+
 def solve(mesh, ph: Phys, A=None):
     """Dense LU solve of A x = b (partial pivoting, LAPACK via numpy)."""
     if A is None:
