@@ -66,6 +66,10 @@ typedef struct pb_params {
     int precond;     /* PB_PRECOND_NONE, PB_PRECOND_DIAG or PB_PRECOND_BLOCK */
     int singular;    /* arithmetic of the Sauter-Schwab integrals: PB_SINGULAR_AUTO (0: float-float
                         under PB_MIXED, FP64 under PB_FP64), PB_SINGULAR_FP64 or PB_SINGULAR_FF */
+    int pc_block;    /* PB_PRECOND_BLOCK: most elements in one block (8..96; 0 = 96). Section 2.6
+                        takes the clusters of a designated level as blocks; here the leaves, each
+                        cut into nearly equal Morton-consecutive parts of at most pc_block
+                        elements, so smaller values stand for designated levels below the leaves */
 } pb_params;
 
 /* Float-float ("double-single", ~1e-13 relative) evaluates every step of the singular
@@ -172,10 +176,40 @@ int pb_gmres_solve(pb_ctx* ctx, double* x, double tol, int max_iter, int restart
 int pb_solve_states(pb_ctx* ctx, const double* q, int nrhs, double* X, double* E, double tol, int max_iter,
                     int restart, int warm, pb_solve_info* infos);
 
+/* Several molecules, several charge states each, in ONE CUDA-graph launch. A context holds
+ * one mesh, so the contexts ctxs[0..nmol) are the meshes of the batch; each must be built, on
+ * the current device, appear once and have per-phase timing disabled. q[k]: host pointer,
+ * nrhs x nc_k charge values of molecule k (state s at q[k] + s nc_k; positions as uploaded).
+ * X[k]: device pointer, nrhs x 2 N_k doubles, written with the solutions (state s at
+ * X[k] + 2 N_k s, element order). E: host pointer, nmol x nrhs energies in kcal/mol
+ * (molecule-major; may be NULL). infos: host pointer, nmol x nrhs records (may be NULL).
+ * The graph has one branch per molecule, run side by side: state 0 by GMRES from zero, then
+ * the other states, up to PB_MAX_RHS per batch, by one GMRES over all of them (batched
+ * products; each state keeps its own Krylov basis and stopping test) from state 0's solution
+ * scaled per state by its least-squares factor, then every state's energy. Every GMRES stops
+ * on the device (conditional graph nodes); the host reads nothing until the graph is done.
+ * tol, max_iter, restart as pb_gmres_solve; 1 <= nrhs <= 1025. Builds the graph on each call
+ * (a few hundred microseconds of host time per molecule). The uploaded charges of each context
+ * are left as they were. Synchronises. Returns the first non-OK state status (the others are
+ * in infos). No counterpart in the paper, which solves one molecule and one charge state at a
+ * time. */
+int pb_batch_solve_states(pb_ctx* const* ctxs, int nmol, const double* const* q, int nrhs, double* const* X,
+                          double* E, double tol, int max_iter, int restart, pb_solve_info* infos);
+
 /* Electrostatic solvation energy (eqsolengdis) for x = [phi; dphi/dn] in kcal/mol, using
  * the factor 4 pi 332.0716 of Section 3. x: device pointer. E_kcal: host pointer.
  * Synchronises. */
 int pb_solvation_energy(pb_ctx* ctx, const double* x, double* E_kcal);
+
+/* The same energy by the Cartesian treecode of Section 2.5 (eqMAC, eqsolengformTree): per
+ * charge, clusters from the root down; a cluster with rho_c / |x_n - x_c| <= theta (rho_c the
+ * shrink-box half diagonal, tested in FP64) contributes the Taylor series of its far-field
+ * moments at the context's per-level orders (the product's P2M and MtM, run on x up to the
+ * root), a leaf that fails is summed directly. O(N_c log N) instead of O(N_c N); the error
+ * falls with the order and with theta (about 3e-7 relative at p = 8, theta = 0.5 on a
+ * 1280-triangle sphere). x: device pointer; 0 < theta < 1; E_kcal: host pointer.
+ * Synchronises. */
+int pb_solvation_energy_treecode(pb_ctx* ctx, const double* x, double theta, double* E_kcal);
 
 /* Tree statistics after pb_build_tree. out: host pointer. Synchronises. */
 int pb_get_tree_stats(pb_ctx* ctx, pb_tree_stats* out);

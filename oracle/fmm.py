@@ -186,6 +186,118 @@ def orders(tree, p, adaptive):
     return [p + (tree.L - l) if adaptive else p for l in range(tree.L + 1)]
 
 
+def moments(tree, verts, tris, x, ph, pl, lstop=1):
+    """Moments of the two far-field expansions (eqmoment, eqmomentL) at every level from L
+    up to lstop: leaf moments by the one-point rule, then the upward pass (eqMtM). For each
+    cluster, s0 = sum_i [dphi_i m^b(psi_i) - phi_i m_nu^b(psi_i)] (for G0) and
+    sk = sum_i [-dphi_i m^b(psi_i) + eps phi_i m_nu^b(psi_i)] (for Gk), with
+    m^b(psi_i) = A_i (c_i - x_c)^b and m_nu^b(psi_i) = A_i n_i . grad (y - x_c)^b at y = c_i.
+    pl: the order of each level."""
+    V = np.asarray(verts, dtype=np.float64)
+    T = np.asarray(tris)
+    N = tree.N
+    cent, area, nrm = dense.geometry(V, T)
+    o = tree.order
+    c_s, a_s, n_s = cent[o], area[o], nrm[o]
+    phi, dphi = x[:N][o], x[N:][o]
+    eps = ph.eps
+    L = tree.L
+    idx = [taylor.multi_indices(pl[l]) for l in range(L + 1)]
+    s0 = [None] * (L + 1)
+    sk = [None] * (L + 1)
+    nL = tree.nclusters(L)
+    s0[L] = np.zeros((nL, len(idx[L])))
+    sk[L] = np.zeros((nL, len(idx[L])))
+    for c in range(nL):
+        b, e = tree.begin[L][c], tree.end[L][c]
+        dv = c_s[b:e] - tree.xc[L][c]
+        M = _mono(dv, idx[L]) * a_s[b:e, None]
+        Mn = _dmono(dv, n_s[b:e], idx[L]) * a_s[b:e, None]
+        s0[L][c] = dphi[b:e] @ M - phi[b:e] @ Mn
+        sk[L][c] = -dphi[b:e] @ M + eps * (phi[b:e] @ Mn)
+    # upward pass (MtM); child moments above the child's order are absent
+    for l in range(L - 1, lstop - 1, -1):
+        nc = tree.nclusters(l)
+        s0[l] = np.zeros((nc, len(idx[l])))
+        sk[l] = np.zeros((nc, len(idx[l])))
+        for c in range(nc):
+            for ch in range(tree.child_begin[l][c], tree.child_end[l][c]):
+                S = _shift_matrix(idx[l], idx[l + 1], tree.xc[l + 1][ch] - tree.xc[l][c])
+                s0[l][c] += S @ s0[l + 1][ch]
+                sk[l][c] += S @ sk[l + 1][ch]
+    return s0, sk
+
+
+def treecode_energy(tree, mesh, x, ph, p, theta, adaptive=False):
+    """Solvation energy (eqsolengdis) in kcal/mol by the Cartesian treecode of Section 2.5.
+
+    V_n = sum_i A_i [K1(x_n, c_i) dphi_i + K2(x_n, c_i) phi_i] (the one-point rule of the
+    direct sum) is accumulated per charge by addCluster from the root: a cluster c whose
+    radius and distance to the charge satisfy the MAC (eqMAC) r_c / R <= theta contributes
+    its Taylor series (eqsolengformTree) sum_b D^b G(x_n - x_c) (-1)^|b| / b! s[b] for both
+    expansions (G0 with s0, Gk with sk, the moments of ``moments``); otherwise its children
+    are visited, and a leaf is summed directly. r_c is read as the shrink-box half diagonal
+    rho_c, which bounds every point of the cluster, and the test is made in FP64 as
+    rho_c^2 <= theta^2 |x_n - x_c|^2. E = 1/2 * 4 pi 332.0716 * sum_n q_n V_n."""
+    V = np.asarray(mesh.verts, dtype=np.float64)
+    T = np.asarray(mesh.tris)
+    N = tree.N
+    L = tree.L
+    cent, area, nrm = dense.geometry(V, T)
+    o = tree.order
+    c_s, a_s, n_s = cent[o], area[o], nrm[o]
+    phi, dphi = x[:N][o], x[N:][o]
+    eps, kap = ph.eps, ph.kappa
+    pl = orders(tree, p, adaptive)
+    s0, sk = moments(tree, mesh.verts, mesh.tris, x, ph, pl, lstop=0)
+    idx = [taylor.multi_indices(pl[l]) for l in range(L + 1)]
+    w = [np.array([(-1.0) ** (a + b + c) / (factorial(a) * factorial(b) * factorial(c)) for a, b, c in idx[l]])
+         for l in range(L + 1)]
+    th2 = theta * theta
+    fpi = 4.0 * np.pi
+
+    def direct(xn, b, e):
+        d = xn - c_s[b:e]
+        r2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]
+        r = np.sqrt(r2)
+        ex = np.exp(-kap * r)
+        k1 = (1.0 - ex) / (fpi * r)
+        # dG/dnu_y = -g'(r) (n_y . d) / r, g0' = -1 / (4 pi r^2), gk' = -(1 + k r) e^(-k r) / (4 pi r^2)
+        nd = n_s[b:e, 0] * d[:, 0] + n_s[b:e, 1] * d[:, 1] + n_s[b:e, 2] * d[:, 2]
+        dg0 = nd / (fpi * r2 * r)
+        dgk = (1.0 + kap * r) * ex * nd / (fpi * r2 * r)
+        k2 = eps * dgk - dg0
+        return float(np.sum(a_s[b:e] * (k1 * dphi[b:e] + k2 * phi[b:e])))
+
+    E = 0.0
+    for n in range(mesh.nc):
+        xn = np.asarray(mesh.qpos[n], dtype=np.float64)
+        Vn = 0.0
+        accepted = [[] for _ in range(L + 1)]  # clusters whose series is used, by level
+        stack = [(0, 0)]
+        while stack:
+            l, c = stack.pop()
+            d = xn - tree.xc[l][c]
+            R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2]
+            if tree.rho[l][c] * tree.rho[l][c] <= th2 * R2:
+                accepted[l].append(c)
+            elif l < L:
+                for ch in range(tree.child_end[l][c] - 1, tree.child_begin[l][c] - 1, -1):
+                    stack.append((l + 1, ch))
+            else:
+                Vn += direct(xn, tree.begin[L][c], tree.end[L][c])
+        # the series of the accepted clusters, one derivative evaluation per level
+        for l in range(L + 1):
+            if accepted[l]:
+                cs = np.array(accepted[l])
+                d = xn[None, :] - tree.xc[l][cs]
+                D0 = taylor.derivatives(d, pl[l], 0.0)
+                Dk = taylor.derivatives(d, pl[l], kap)
+                Vn += float(np.sum(D0 * w[l] * s0[l][cs]) + np.sum(Dk * w[l] * sk[l][cs]))
+        E += mesh.q[n] * Vn
+    return 0.5 * E * fpi * 332.0716
+
+
 def far_field(tree, verts, tris, x, ph, p, adaptive=False):
     """Far-field part (steps 2-6) of y = A x; returns (y1, y2) in element order."""
     V = np.asarray(verts, dtype=np.float64)
@@ -203,29 +315,8 @@ def far_field(tree, verts, tris, x, ph, p, adaptive=False):
     y2 = np.zeros(N)
     if L == 0:
         return y1, y2
-    # step 2: leaf moments
-    s0 = [None] * (L + 1)
-    sk = [None] * (L + 1)
-    nL = tree.nclusters(L)
-    s0[L] = np.zeros((nL, len(idx[L])))
-    sk[L] = np.zeros((nL, len(idx[L])))
-    for c in range(nL):
-        b, e = tree.begin[L][c], tree.end[L][c]
-        dv = c_s[b:e] - tree.xc[L][c]
-        M = _mono(dv, idx[L]) * a_s[b:e, None]
-        Mn = _dmono(dv, n_s[b:e], idx[L]) * a_s[b:e, None]
-        s0[L][c] = dphi[b:e] @ M - phi[b:e] @ Mn
-        sk[L][c] = -dphi[b:e] @ M + eps * (phi[b:e] @ Mn)
-    # step 3: upward pass (MtM); child moments above the child's order are absent
-    for l in range(L - 1, 0, -1):
-        nc = tree.nclusters(l)
-        s0[l] = np.zeros((nc, len(idx[l])))
-        sk[l] = np.zeros((nc, len(idx[l])))
-        for c in range(nc):
-            for ch in range(tree.child_begin[l][c], tree.child_end[l][c]):
-                S = _shift_matrix(idx[l], idx[l + 1], tree.xc[l + 1][ch] - tree.xc[l][c])
-                s0[l][c] += S @ s0[l + 1][ch]
-                sk[l][c] += S @ sk[l + 1][ch]
+    # steps 2 and 3: leaf moments and the upward pass
+    s0, sk = moments(tree, verts, tris, x, ph, pl)
     # step 4: interaction phase (MtL), all pairs of a level at once
     lam0 = [None] * (L + 1)
     lamk = [None] * (L + 1)

@@ -1136,6 +1136,14 @@ int pb_far_setup(pb_ctx* c)
     int rc = c->tables_ready ? PB_OK : upload_tables(c);
     if (rc) return rc;
     size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
+    {
+        // the root's moments: only the treecode energy uses them
+        PbLevel& lv = c->lev[0];
+        size_t n = (size_t)lv.ncl * pb_nterms(lv.p);
+        lv.sig0 = pb_alloc_on(c, rs * n, fs);
+        lv.sigk = pb_alloc_on(c, rs * n, fs);
+        if (!lv.sig0 || !lv.sigk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");
+    }
     for (int l = 1; l <= c->L; ++l) {
         PbLevel& lv = c->lev[l];
         size_t n = (size_t)lv.ncl * pb_nterms(lv.p);
@@ -1248,4 +1256,255 @@ int pb_far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream_t s
 {
     if (c->prm.precision == PB_MIXED) return far_apply<float>(c, xs, ys, nr, st);
     return far_apply<double>(c, xs, ys, nr, st);
+}
+
+// ---------- solvation energy by the Cartesian treecode (Section 2.5) ----------
+// E = 1/2 * 4 pi 332.0716 * sum_n q_n V_n with V_n = sum_i A_i [K1(x_n, c_i) dphi_i +
+// K2(x_n, c_i) phi_i] (eqsolengdis, one-point rule). Per charge, addCluster from the root: a
+// cluster c that satisfies the MAC (eqMAC) r_c / R <= theta, tested in FP64 as
+// rho_c^2 <= theta^2 |x_n - x_c|^2 with rho_c the shrink-box half diagonal (it bounds every
+// point of the cluster), contributes its Taylor series (eqsolengformTree)
+//   sum_b D^b G0(x_n - x_c) m~0[b] + D^b Gk(x_n - x_c) m~k[b],
+// with the FMM's own moments in their stored form m~ = (-1)^|b| m / b! (the same densities as
+// the product's y1 rows, whose kernels K1 + K2 the energy uses); otherwise its children are
+// visited, and a leaf that fails is summed directly. The moments come from the same P2M and
+// MtM kernels as the product, run on the solution up to the root.
+//
+// One warp per (charge, level-1 cluster): the warp first makes the root's test (a charge far
+// from the whole surface takes the root's series once, in the warp of the first level-1
+// cluster), then runs addCluster on its subtree with a stack in shared memory. The lanes share
+// each order of the derivative recurrence (warp barriers between orders) and split the
+// contraction and the direct sums. Results per warp, summed in a fixed order afterwards.
+struct TcLevels {
+    const double* xc[PB_MAXL + 1];
+    const double* rho[PB_MAXL + 1];
+    const int* cbeg[PB_MAXL + 1];
+    const void* s0[PB_MAXL + 1];
+    const void* sk[PB_MAXL + 1];
+    int p[PB_MAXL + 1];
+    const int* leaf_begin;
+    int L, n1;
+};
+#define TC_W 4
+#define TC_STACK 96  // <= 8 children per level, 10 levels
+
+template <class R>
+__device__ double tc_series(const TcLevels& tl, int l, int c, const double* xn, double kappa, R* F0, R* Fk, R* Pk,
+                            int lane)
+{
+    const int p = tl.p[l];
+    const int T = pb_nterms(p);
+    const R dx = (R)(xn[0] - tl.xc[l][3 * c]), dy = (R)(xn[1] - tl.xc[l][3 * c + 1]),
+            dz = (R)(xn[2] - tl.xc[l][3 * c + 2]);
+    const R d2 = dx * dx + dy * dy + dz * dz;
+    const R kap = (R)kappa;
+    if (lane == 0) {
+        const R r = sqrt(d2), ex = exp(-kap * r), i4pi = (R)0.07957747154594767;
+        F0[0] = i4pi / r;
+        Fk[0] = i4pi * ex / r;
+        Pk[0] = i4pi * ex;
+    }
+    __syncwarp();
+    // Taylor coefficients F = D^k G / k! degree by degree (the MtL recurrence)
+    for (int n = 1; n <= p; ++n) {
+        const int lo = pb_nterms(n - 1), hi = pb_nterms(n);
+        for (int k = lo + lane; k < hi; k += 32) {
+            int k1, k2, k3;
+            mi_unpack(c_mi[k], k1, k2, k3);
+            const R d[3] = {dx, dy, dz};
+            const int kk[3] = {k1, k2, k3};
+            R a0 = 0, a1 = 0, ak0 = 0, ak1 = 0, ap0 = 0, ap1 = 0;
+            for (int i = 0; i < 3; ++i) {
+                if (kk[i] >= 1) {
+                    const int q = pb_midx(k1 - (i == 0), k2 - (i == 1), k3 - (i == 2));
+                    a0 += d[i] * F0[q];
+                    ak0 += d[i] * Fk[q];
+                    ap0 += d[i] * Pk[q];
+                }
+                if (kk[i] >= 2) {
+                    const int q = pb_midx(k1 - 2 * (i == 0), k2 - 2 * (i == 1), k3 - 2 * (i == 2));
+                    a1 += F0[q];
+                    ak1 += Fk[q];
+                    ap1 += Pk[q];
+                }
+            }
+            const R nn = (R)n;
+            F0[k] = (-(R)(2 * n - 1) * a0 - (nn - 1) * a1) / (d2 * nn);
+            Fk[k] = (-(R)(2 * n - 1) * ak0 - (nn - 1) * ak1 - kap * ap0 - kap * ap1) / (d2 * nn);
+            Pk[k] = -kap * (ak0 + ak1) / nn;
+        }
+        __syncwarp();
+    }
+    // sum_b D^b G m~[b] with D^b = b! F_b
+    const R* m0 = (const R*)tl.s0[l] + (size_t)c * T;
+    const R* mk = (const R*)tl.sk[l] + (size_t)c * T;
+    R acc = 0;
+    for (int k = lane; k < T; k += 32) {
+        int k1, k2, k3;
+        mi_unpack(c_mi[k], k1, k2, k3);
+        const R f = (R)(c_fact[k1] * c_fact[k2] * c_fact[k3]);
+        acc += f * (F0[k] * m0[k] + Fk[k] * mk[k]);
+    }
+    __syncwarp();  // F0, Fk, Pk are reused by the next cluster
+    return (double)acc;
+}
+
+template <class R>
+__global__ void __launch_bounds__(32 * TC_W) k_tc_energy(int nc, TcLevels tl, const double* __restrict__ qpos,
+                                                         const double* __restrict__ q,
+                                                         const double4_32a* __restrict__ ep,
+                                                         const double4_32a* __restrict__ en,
+                                                         const double* __restrict__ xs, int nt, double eps,
+                                                         double kappa, double theta2, int tmax,
+                                                         double* __restrict__ vpart)
+{
+    extern __shared__ __align__(16) unsigned char tsm[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    R* F0 = (R*)tsm + (size_t)wib * 3 * tmax;
+    R* Fk = F0 + tmax;
+    R* Pk = Fk + tmax;
+    __shared__ int stk[TC_W][TC_STACK];
+    const long long w = (long long)blockIdx.x * TC_W + wib;
+    if (w >= (long long)nc * tl.n1) return;
+    const int n = (int)(w / tl.n1), s = (int)(w % tl.n1);
+    const double xn[3] = {qpos[3 * n], qpos[3 * n + 1], qpos[3 * n + 2]};
+    auto mac = [&](int l, int c) {
+        const double dx = xn[0] - tl.xc[l][3 * c], dy = xn[1] - tl.xc[l][3 * c + 1], dz = xn[2] - tl.xc[l][3 * c + 2];
+        const double R2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        const double rh = tl.rho[l][c];
+        return __dmul_rn(rh, rh) <= __dmul_rn(theta2, R2);
+    };
+    double V = 0.0;  // lane partial
+    const R kap = (R)kappa, ep_ = (R)eps, i4pi = (R)0.07957747154594767;
+    auto leaf = [&](int c) {
+        const int b = tl.leaf_begin[c], e = tl.leaf_begin[c + 1];
+        R acc = 0;
+        for (int k = b + lane; k < e; k += 32) {
+            const double4_32a y = ep[k], nv = en[k];
+            const R dx = (R)(xn[0] - y.x), dy = (R)(xn[1] - y.y), dz = (R)(xn[2] - y.z);
+            const R r2 = dx * dx + dy * dy + dz * dz, r = sqrt(r2);
+            const R ex = exp(-kap * r);
+            const R k1 = -expm1(-kap * r) * i4pi / r;
+            const R nd = (R)nv.x * dx + (R)nv.y * dy + (R)nv.z * dz;
+            const R k2 = nd * i4pi / (r2 * r) * (ep_ * ((R)1 + kap * r) * ex - (R)1);
+            acc += (R)y.w * (k1 * (R)xs[nt + k] + k2 * (R)xs[k]);
+        }
+        return (double)acc;
+    };
+    if (mac(0, 0)) {
+        if (s == 0) V += tc_series<R>(tl, 0, 0, xn, kappa, F0, Fk, Pk, lane);
+    } else if (tl.L == 0) {
+        if (s == 0) V += leaf(0);
+    } else {
+        int sp = 0;
+        if (lane == 0) stk[wib][0] = (1 << 24) | s;
+        sp = 1;
+        __syncwarp();
+        while (sp > 0) {
+            const int e = stk[wib][sp - 1];
+            --sp;
+            const int l = e >> 24, c = e & 0xffffff;
+            if (mac(l, c)) {
+                V += tc_series<R>(tl, l, c, xn, kappa, F0, Fk, Pk, lane);
+            } else if (l < tl.L) {
+                const int cb = tl.cbeg[l][c], ce = tl.cbeg[l][c + 1];
+                __syncwarp();
+                // children in reverse, so that they are taken in order
+                for (int ch = ce - 1; ch >= cb; --ch) {
+                    if (lane == 0 && sp < TC_STACK) stk[wib][sp] = ((l + 1) << 24) | ch;
+                    ++sp;
+                }
+                if (sp > TC_STACK) sp = TC_STACK;  // cannot happen for <= 8 children and 10 levels
+                __syncwarp();
+            } else {
+                V += leaf(c);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) V += __shfl_xor_sync(0xffffffffu, V, o);
+    if (lane == 0) vpart[w] = q[n] * V;
+}
+
+__global__ void k_tc_sum(long long n, const double* __restrict__ part, double* __restrict__ out, double scale)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += 256) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] * scale;
+}
+
+template <class R>
+static int tc_energy(pb_ctx* c, const double* xs, double theta, double* E)
+{
+    const int L = c->L;
+    double eps = c->prm.eps_out / c->prm.eps_in;
+    const long long vstr = 2LL * c->nt;
+    auto sstr = [](const PbLevel& lv) { return (long long)lv.ncl * pb_nterms(lv.p); };
+    pb_tic(c, PB_T_ENERGY);
+    // moments of the solution on every level, up to the root (P2M, MtM)
+    {
+        PbLevel& lv = c->lev[L];
+        const size_t psm = p2m_smem<R>(lv.p);
+        PB_CUDA(c, cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+        k_p2m<R><<<dim3(lv.ncl, 1), P2M_T, psm, c->st>>>(c->nt, lv.p, lv.begin, lv.xc, c->e64p, c->e64n, xs, eps,
+                                                          (R*)lv.sig0, (R*)lv.sigk, vstr, sstr(lv));
+        PB_LAUNCH(c);
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        PbLevel& lv = c->lev[l];
+        PbLevel& ch = c->lev[l + 1];
+        const size_t msm = 4 * (size_t)pb_nterms(lv.p) * sizeof(R);
+        PB_CUDA(c, cudaFuncSetAttribute(k_m2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm));
+        k_m2m<R><<<dim3(lv.ncl, 1), M2M_T, msm, c->st>>>(lv.p, ch.p, lv.cbeg, lv.xc, ch.xc, (R*)ch.sig0,
+                                                          (R*)ch.sigk, (R*)lv.sig0, (R*)lv.sigk, sstr(ch), sstr(lv));
+        PB_LAUNCH(c);
+    }
+    TcLevels tl;
+    memset(&tl, 0, sizeof(tl));
+    int pmax = 0;
+    for (int l = 0; l <= L; ++l) {
+        tl.xc[l] = c->lev[l].xc;
+        tl.rho[l] = c->lev[l].rho;
+        tl.cbeg[l] = c->lev[l].cbeg;
+        tl.s0[l] = c->lev[l].sig0;
+        tl.sk[l] = c->lev[l].sigk;
+        tl.p[l] = c->lev[l].p;
+        pmax = std::max(pmax, c->lev[l].p);
+    }
+    tl.leaf_begin = c->lev[L].begin;
+    tl.L = L;
+    tl.n1 = L > 0 ? c->lev[1].ncl : 1;
+    const long long nw = (long long)c->nc * tl.n1;
+    if (nw > c->tc_nw) {
+        c->tc_part = (double*)pb_alloc(c, sizeof(double) * (size_t)(nw + 1));
+        if (!c->tc_part) return pb_fail(c, PB_ERR_NOMEM, "treecode energy: out of memory");
+        c->tc_nw = nw;
+    }
+    const int tmax = pb_nterms(pmax);
+    const size_t sm = sizeof(R) * 3 * (size_t)tmax * TC_W;
+    PB_CUDA(c, cudaFuncSetAttribute(k_tc_energy<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (nw > 0) {
+        k_tc_energy<R><<<(unsigned)((nw + TC_W - 1) / TC_W), 32 * TC_W, sm, c->st>>>(
+            c->nc, tl, c->qpos, c->q, c->e64p, c->e64n, xs, c->nt, eps, c->prm.kappa, theta * theta, tmax, c->tc_part);
+        PB_LAUNCH(c);
+    }
+    k_tc_sum<<<1, 256, 0, c->st>>>(nw, c->tc_part, c->tc_part + nw, 0.5 * 4.0 * PB_PI * 332.0716);
+    PB_LAUNCH(c);
+    pb_toc(c, PB_T_ENERGY);
+    PB_CUDA(c, cudaMemcpyAsync(c->hscal, c->tc_part + nw, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    *E = c->hscal[0];
+    return PB_OK;
+}
+
+int pb_energy_treecode_sorted(pb_ctx* c, const double* xs, double theta, double* E)
+{
+    if (c->prm.precision == PB_MIXED) return tc_energy<float>(c, xs, theta, E);
+    return tc_energy<double>(c, xs, theta, E);
 }

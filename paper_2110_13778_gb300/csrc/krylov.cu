@@ -4,7 +4,9 @@
 // the triangular solve and the update run in FP64 kernels; the host only reads one residual
 // estimate per iteration to decide whether to continue.
 #include <math.h>
+#include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "kernels.cuh"
@@ -363,14 +365,22 @@ int pb_rhs_states_sorted(pb_ctx* c, const double* Q, double* B, int nr)
     return PB_OK;
 }
 
-// energies of nr <= 16 states (charges Q, solutions X, nr x 2N) into E[0..nr) (host); synchronises
-int pb_energy_states_sorted(pb_ctx* c, const double* Q, const double* X, int nr, double* E)
+// energy scratch: nb partials for each of 16 states, then 16 results
+int pb_energy_reserve(pb_ctx* c)
 {
-    const int nt = c->nt, nb = (nt + KB - 1) / KB;
+    const int nb = (c->nt + KB - 1) / KB;
     if (!c->escratch) {
         c->escratch = (double*)pb_alloc(c, sizeof(double) * ((size_t)nb * 16 + 16));
         if (!c->escratch) return pb_fail(c, PB_ERR_NOMEM, "energy: out of memory");
     }
+    return PB_OK;
+}
+
+// energies of nr <= 16 states (charges Q, solutions X, nr x 2N) into Edev[0..nr) (device);
+// queued only (pb_energy_reserve first)
+int pb_energy_states_queue(pb_ctx* c, const double* Q, const double* X, int nr, double* Edev)
+{
+    const int nt = c->nt, nb = (nt + KB - 1) / KB;
     double* part = c->escratch;
     const double eps = c->prm.eps_out / c->prm.eps_in;
     pb_tic(c, PB_T_ENERGY);
@@ -382,12 +392,23 @@ int pb_energy_states_sorted(pb_ctx* c, const double* Q, const double* X, int nr,
                                                       part, nr);
     PB_LAUNCH(c);
     for (int r = 0; r < nr; ++r) {
-        k_sum<<<1, KB, 0, c->st>>>(nb, part + (size_t)r * nb, part + (size_t)nb * 16 + r, 0.5 * 4.0 * PB_PI * 332.0716);
+        k_sum<<<1, KB, 0, c->st>>>(nb, part + (size_t)r * nb, Edev + r, 0.5 * 4.0 * PB_PI * 332.0716);
         PB_LAUNCH(c);
     }
     pb_toc(c, PB_T_ENERGY);
+    return PB_OK;
+}
+
+// energies of nr <= 16 states (charges Q, solutions X, nr x 2N) into E[0..nr) (host); synchronises
+int pb_energy_states_sorted(pb_ctx* c, const double* Q, const double* X, int nr, double* E)
+{
+    int rc;
+    if ((rc = pb_energy_reserve(c))) return rc;
+    const int nb = (c->nt + KB - 1) / KB;
+    double* Ed = c->escratch + (size_t)nb * 16;
+    if ((rc = pb_energy_states_queue(c, Q, X, nr, Ed))) return rc;
     std::vector<double> h(nr);
-    PB_CUDA(c, cudaMemcpyAsync(h.data(), part + (size_t)nb * 16, sizeof(double) * nr, cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(h.data(), Ed, sizeof(double) * nr, cudaMemcpyDeviceToHost, c->st));
     PB_CUDA(c, cudaStreamSynchronize(c->st));
     for (int r = 0; r < nr; ++r) E[r] = h[r];
     return PB_OK;
@@ -853,6 +874,9 @@ __global__ void k_bgm_givens(int m, int j, GmState s, long long sstr)
     t.res[0] = fabs(t.g[j + 1]);
 }
 
+__global__ void k_dg_start_scale(long long n, const double* __restrict__ small, long long sstr, long long hoff,
+                                 double* __restrict__ X, double* __restrict__ W);
+
 int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double tol, int max_iter, int restart,
                           pb_solve_info* infos)
 {
@@ -986,6 +1010,20 @@ int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double 
         // r = b - A x, V_0 = r / ||r||
         if ((rc = pb_matvec_sorted_multi(c, X, W, nr))) return rc;
         for (int r = 0; r < nr; ++r) mvs[r] += active[r];
+        if (first) {
+            // each given start is first scaled by its least-squares factor (zero if none is
+            // positive): two dot products per right-hand side, no extra product
+            k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, B, n, W, part, pstr);
+            PB_LAUNCH(c);
+            k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff, S);
+            PB_LAUNCH(c);
+            k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
+            PB_LAUNCH(c);
+            k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff + 1, S);
+            PB_LAUNCH(c);
+            k_dg_start_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, small, S, hoff, X, W);
+            PB_LAUNCH(c);
+        }
         k_bresidual<<<dim3(G, nr), KB, 0, c->st>>>(n, B, W);
         PB_LAUNCH(c);
         k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
@@ -997,17 +1035,6 @@ int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double 
         k_bgm_start<<<nr, 1, 0, c->st>>>(m, st, S);
         PB_LAUNCH(c);
         if ((rc = read(roff))) return rc;
-        if (first == 1) {
-            // a start worse than zero (||b - A x0|| > ||b||) is replaced by zero, once
-            bool redo = false;
-            for (int r = 0; r < nr; ++r)
-                if (active[r] && hv[r] > bnorm[r]) {
-                    PB_CUDA(c, cudaMemsetAsync(X + r * n, 0, sizeof(double) * n, c->st));
-                    redo = true;
-                }
-            first = 2;
-            if (redo) continue;
-        }
         for (int r = 0; r < nr; ++r) {
             if (!active[r]) continue;
             rel[r] = hv[r] / bnorm[r];
@@ -1088,5 +1115,634 @@ int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double 
         if (inf.status != PB_OK && worst == PB_OK) worst = inf.status;
     }
     if (derr) pb_fail(c, PB_ERR_TIMEOUT, "a bounded wait in the MtL kernel gave up");
+    return worst;
+}
+
+// ---------- GMRES driven from the device: one CUDA graph launch per solve ----------
+// The same right-preconditioned GMRES(m) for nr right-hand sides (CGS2, Givens rotations, the
+// true residual recomputed at the end of every cycle), with every control decision taken on the
+// device instead of the host. A control block holds the step index, the shared iteration count
+// and each right-hand side's state; two conditional WHILE nodes of a CUDA graph repeat the
+// Arnoldi step (inner) and the restart cycle (outer) until every right-hand side has converged,
+// failed or run out of iterations. Kernels whose work depends on the step index read it from
+// the control block (grids sized for the largest step; blocks past the current one leave at
+// once), and the current basis vector is also kept in a fixed buffer so that the
+// preconditioner and the product read one address in every replay. The graph is built from
+// sequential stream captures on the context's private stream joined by the conditional nodes,
+// so it can be appended as one branch of a larger graph (several molecules in one launch).
+struct DgCtl {
+    int j;          // Arnoldi step within the current cycle
+    int it;         // Arnoldi steps taken (shared by the right-hand sides)
+    int cycles;     // completed restart cycles
+    int max_iter, m, nr;
+    double tol;
+    int active[PB_MAX_RHS], conv[PB_MAX_RHS], status[PB_MAX_RHS], its[PB_MAX_RHS], mvs[PB_MAX_RHS];
+    int steps[PB_MAX_RHS], cyc[PB_MAX_RHS];
+    double bnorm[PB_MAX_RHS], init[PB_MAX_RHS], rel[PB_MAX_RHS];
+};
+
+// part[r][col][blk] = partial of <V_r[col], w_r>, columns 0..j
+__global__ void k_dg_dot(long long n, const double* __restrict__ V, long long vstr, const double* __restrict__ w,
+                         double* __restrict__ part, long long pstr, const DgCtl* __restrict__ ctl)
+{
+    const int col = blockIdx.y, r = blockIdx.z;
+    if (col > ctl->j) return;
+    __shared__ double red[KB];
+    w += r * n;
+    const double* v = V + r * vstr + (size_t)col * n;
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) s += v[i] * w[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = KB / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[r * pstr + (size_t)col * DOT_BLOCKS + blockIdx.x] = red[0];
+}
+
+// out_r[col] = sum of the partials of column col, columns 0..j (at = 0), or, for at = 1, the
+// single column 0 of the partials into out_r[j + 1]
+__global__ void k_dg_finish(const double* __restrict__ part, long long pstr, double* __restrict__ out,
+                            long long ostr, const DgCtl* __restrict__ ctl, int at)
+{
+    const int col = blockIdx.x, r = blockIdx.y;
+    const int j = ctl->j;
+    if (col > (at ? 0 : j)) return;
+    __shared__ double red[KB];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < DOT_BLOCKS; i += KB) s += part[r * pstr + (size_t)col * DOT_BLOCKS + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = KB / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r * ostr + (at ? j + 1 : col)] = red[0];
+}
+
+// w_r -= V_r[:, 0..j] h_r
+__global__ void k_dg_orth(long long n, const double* __restrict__ V, long long vstr, const double* __restrict__ h,
+                          long long hstr, double* __restrict__ w, const DgCtl* __restrict__ ctl)
+{
+    const int r = blockIdx.y, ncol = ctl->j + 1;
+    V += r * vstr;
+    h += r * hstr;
+    w += r * n;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        double s = 0.0;
+        for (int c = 0; c < ncol; ++c) s += V[(size_t)c * n + i] * h[c];
+        w[i] -= s;
+    }
+}
+
+// hcol_r[i] += y_r[i], i <= j
+__global__ void k_dg_merge(double* __restrict__ small, long long sstr, long long yoff, long long hoff,
+                           const DgCtl* __restrict__ ctl)
+{
+    double* s = small + blockIdx.x * sstr;
+    const int k = ctl->j + 1;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) s[hoff + i] += s[yoff + i];
+}
+
+// V_r[c] = Vcur_r = w_r / sqrt(hcol_r[c]) with c = j + 1 (an Arnoldi step) or c = 0 (first = 1,
+// the start of a cycle)
+__global__ void k_dg_scale(long long n, const double* __restrict__ W, const double* __restrict__ small, long long sstr,
+                           long long hoff, double* __restrict__ V, long long vstr, double* __restrict__ Vcur,
+                           const DgCtl* __restrict__ ctl, int first)
+{
+    const int r = blockIdx.y;
+    const int c = first ? 0 : ctl->j + 1;
+    const double f = 1.0 / sqrt(small[r * sstr + hoff + c]);
+    const double* src = W + r * n;
+    double* dst = V + r * vstr + (size_t)c * n;
+    double* cur = Vcur + r * n;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        const double v = src[i] * f;
+        dst[i] = v;
+        cur[i] = v;
+    }
+}
+
+// step j of right-hand side r = blockIdx.x (k_bgm_givens with the step index from the device)
+__global__ void k_dg_givens(int m, GmState s, long long sstr, const DgCtl* __restrict__ ctl)
+{
+    const long long o = blockIdx.x * sstr;
+    GmState t = {s.H + o, s.cs + o, s.sn + o, s.g + o, s.y + o, s.hcol + o, s.res + o};
+    const int j = ctl->j;
+    double* Hj = t.H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) Hj[i] = t.hcol[i];
+    Hj[j + 1] = sqrt(t.hcol[j + 1]);
+    for (int i = 0; i < j; ++i) {
+        double a = Hj[i], b = Hj[i + 1];
+        Hj[i] = t.cs[i] * a + t.sn[i] * b;
+        Hj[i + 1] = -t.sn[i] * a + t.cs[i] * b;
+    }
+    double a = Hj[j], b = Hj[j + 1];
+    double rr = hypot(a, b);
+    double c = rr > 0 ? a / rr : 1.0, sn = rr > 0 ? b / rr : 0.0;
+    t.cs[j] = c;
+    t.sn[j] = sn;
+    Hj[j] = rr;
+    Hj[j + 1] = 0.0;
+    t.g[j + 1] = -sn * t.g[j];
+    t.g[j] = c * t.g[j];
+    t.res[0] = fabs(t.g[j + 1]);
+}
+
+// After an Arnoldi step: each active right-hand side counts the step and checks its residual
+// estimate; the inner loop continues while one is active, the cycle has room and the iteration
+// budget is not spent. One block of PB_MAX_RHS threads.
+__global__ void k_dg_step_ctl(DgCtl* __restrict__ ctl, const double* __restrict__ small, long long sstr,
+                              long long roff, cudaGraphConditionalHandle h)
+{
+    const int r = threadIdx.x;
+    const int j = ctl->j;
+    int act = 0;
+    if (r < ctl->nr && ctl->active[r]) {
+        ctl->its[r]++;
+        ctl->mvs[r]++;
+        ctl->steps[r] = j + 1;
+        const double rel = small[r * sstr + roff] / ctl->bnorm[r];
+        ctl->rel[r] = rel;
+        if (!isfinite(rel)) {
+            ctl->status[r] = PB_ERR_NONFINITE;
+            ctl->active[r] = 0;
+            ctl->steps[r] = 0;  // no update from a broken cycle
+        } else if (rel <= ctl->tol) {
+            ctl->conv[r] = 1;
+            ctl->active[r] = 0;
+        } else {
+            act = 1;
+        }
+    }
+    act = __syncthreads_or(act);
+    if (r == 0) {
+        const int it = ctl->it + 1;
+        ctl->it = it;
+        ctl->j = j + 1;
+        cudaGraphSetConditional(h, (act && j + 1 < ctl->m && it < ctl->max_iter) ? 1u : 0u);
+    }
+}
+
+// Start of a cycle's Arnoldi loop: enter while a right-hand side is active and iterations are left.
+__global__ void k_dg_enter(const DgCtl* __restrict__ ctl, cudaGraphConditionalHandle h)
+{
+    int act = 0;
+    for (int r = 0; r < ctl->nr; ++r) act |= ctl->active[r];
+    cudaGraphSetConditional(h, (act && ctl->j < ctl->m && ctl->it < ctl->max_iter) ? 1u : 0u);
+}
+
+// Before anything else: ||b_r|| (hcol_r[0] holds ||b_r||^2), the counters, and the host's
+// settings (tol, max_iter, m, nr stay as uploaded). start = 1: the product of the given start
+// counts for every right-hand side.
+__global__ void k_dg_init(DgCtl* __restrict__ ctl, const double* __restrict__ small, long long sstr, long long hoff,
+                          int start)
+{
+    const int r = threadIdx.x;
+    if (r == 0) {
+        ctl->j = 0;
+        ctl->it = 0;
+        ctl->cycles = 0;
+    }
+    if (r >= ctl->nr) return;
+    const double bn = sqrt(small[r * sstr + hoff]);
+    ctl->bnorm[r] = bn;
+    ctl->its[r] = 0;
+    ctl->mvs[r] = start;
+    ctl->steps[r] = 0;
+    ctl->conv[r] = 0;
+    ctl->cyc[r] = 0;
+    ctl->status[r] = PB_OK;
+    ctl->init[r] = 1.0;
+    ctl->rel[r] = 1.0;
+    ctl->active[r] = 1;
+    if (!isfinite(bn)) {  // an overflowing or non-finite right-hand side
+        ctl->status[r] = PB_ERR_NONFINITE;
+        ctl->active[r] = 0;
+        ctl->rel[r] = bn;
+    } else if (!(bn > 0)) {  // b = 0: x = 0 solves it exactly
+        ctl->active[r] = 0;
+        ctl->conv[r] = 1;
+        ctl->rel[r] = 0.0;
+        ctl->init[r] = 0.0;
+    }
+}
+
+// x_r = 0 where b_r = 0 (or is not finite)
+__global__ void k_dg_zero_x(long long n, double* __restrict__ X, const DgCtl* __restrict__ ctl)
+{
+    const int r = blockIdx.y;
+    if (ctl->bnorm[r] > 0 && isfinite(ctl->bnorm[r])) return;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) X[r * n + i] = 0.0;
+}
+
+// k_start_scale per right-hand side: d_r = hcol_r[0..1] = {<w, b>, <w, w>}
+__global__ void k_dg_start_scale(long long n, const double* __restrict__ small, long long sstr, long long hoff,
+                                 double* __restrict__ X, double* __restrict__ W)
+{
+    const int r = blockIdx.y;
+    const double* d = small + r * sstr + hoff;
+    const double a = d[1] > 0.0 ? d[0] / d[1] : 0.0;
+    const double f = (a > 0.0 && isfinite(a)) ? a : 0.0;
+    X += r * n;
+    W += r * n;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        X[i] = f != 0.0 ? X[i] * f : 0.0;
+        W[i] = f != 0.0 ? W[i] * f : 0.0;
+    }
+}
+
+// End of a cycle (first = 0) or end of the start (first = 1): the residual of the current x is
+// in res_r (true residual, from a product). Records it, retires converged or broken right-hand
+// sides, opens the next cycle for the others and decides whether the outer loop runs again.
+__global__ void k_dg_cycle_ctl(DgCtl* __restrict__ ctl, const double* __restrict__ small, long long sstr,
+                               long long roff, cudaGraphConditionalHandle h, int first)
+{
+    const int r = threadIdx.x;
+    int act = 0;
+    if (r < ctl->nr) {
+        const double bn = ctl->bnorm[r];
+        const bool live = bn > 0 && isfinite(bn);
+        const double rel = small[r * sstr + roff] / bn;
+        if (!first && ctl->cyc[r]) ctl->mvs[r]++;  // the product that closed its cycle
+        if (live) {
+            ctl->rel[r] = rel;
+            if (first) ctl->init[r] = rel;
+        }
+        if (ctl->active[r]) {
+            if (!isfinite(rel)) {
+                ctl->status[r] = PB_ERR_NONFINITE;
+                ctl->active[r] = 0;
+            } else if (rel <= ctl->tol) {
+                ctl->conv[r] = 1;
+                ctl->active[r] = 0;
+            }
+        }
+        ctl->cyc[r] = ctl->active[r];
+        ctl->steps[r] = 0;
+        act = ctl->active[r];
+    }
+    act = __syncthreads_or(act);
+    if (r == 0) {
+        ctl->j = 0;
+        if (!first) ctl->cycles++;
+        cudaGraphSetConditional(h, (act && ctl->it < ctl->max_iter) ? 1u : 0u);
+    }
+}
+
+// back substitution of right-hand side r = blockIdx.x over the steps it took in this cycle
+__global__ void k_dg_solve(int m, GmState s, long long sstr, const DgCtl* __restrict__ ctl)
+{
+    const long long o = blockIdx.x * sstr;
+    const int k = ctl->steps[blockIdx.x];
+    const double* H = s.H + o;
+    const double* g = s.g + o;
+    double* y = s.y + o;
+    for (int i = k - 1; i >= 0; --i) {
+        double v = g[i];
+        for (int q = i + 1; q < k; ++q) v -= H[(size_t)q * (m + 1) + i] * y[q];
+        const double d = H[(size_t)i * (m + 1) + i];
+        y[i] = d != 0.0 ? v / d : 0.0;
+    }
+}
+
+// u_r = V_r[:, 0..steps_r) y_r (zero for a right-hand side without steps)
+__global__ void k_dg_combine(long long n, const double* __restrict__ V, long long vstr, const double* __restrict__ small,
+                             long long sstr, long long yoff, double* __restrict__ U, const DgCtl* __restrict__ ctl)
+{
+    const int r = blockIdx.y;
+    const int k = ctl->steps[r];
+    V += r * vstr;
+    const double* y = small + r * sstr + yoff;
+    U += r * n;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        double s = 0.0;
+        for (int c = 0; c < k; ++c) s += V[(size_t)c * n + i] * y[c];
+        U[i] = s;
+    }
+}
+
+// x_r += z_r for the right-hand sides that took steps in this cycle
+__global__ void k_dg_axpy(long long n, const double* __restrict__ Z, double* __restrict__ X, const DgCtl* __restrict__ ctl)
+{
+    const int r = blockIdx.y;
+    if (ctl->steps[r] == 0) return;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB)
+        X[r * n + i] += Z[r * n + i];
+}
+
+// device workspace of the device-driven solver: the batched Krylov workspace (shared with the
+// host-driven batched solver) for nr right-hand sides, the current-vector buffer and nctl
+// control blocks
+int pb_dg_reserve(pb_ctx* c, int nr, int m, int nctl)
+{
+    const long long n = 2LL * c->nt;
+    const long long S = (long long)(m + 1) * m + 6 * (m + 2);
+    if (nr > c->gb_nr || m > c->gb_m) {
+        const int nr2 = std::max(nr, c->gb_nr), m2 = std::max(m, c->gb_m);
+        const long long S2 = (long long)(m2 + 1) * m2 + 6 * (m2 + 2);
+        c->gbV = (double*)pb_alloc(c, sizeof(double) * (size_t)((m2 + 1) * n * nr2));
+        c->gbW = (double*)pb_alloc(c, sizeof(double) * (size_t)(n * nr2));
+        c->gbZ = (double*)pb_alloc(c, sizeof(double) * (size_t)(n * nr2));
+        c->gbpart = (double*)pb_alloc(c, sizeof(double) * (size_t)(DOT_BLOCKS * (m2 + 2) * nr2));
+        c->gbsmall = (double*)pb_alloc(c, sizeof(double) * (size_t)(S2 * nr2));
+        if (!c->gbV || !c->gbW || !c->gbZ || !c->gbpart || !c->gbsmall) {
+            c->gb_nr = c->gb_m = 0;
+            return pb_fail(c, PB_ERR_NOMEM, "gmres workspace: out of memory");
+        }
+        c->gb_nr = nr2;
+        c->gb_m = m2;
+        pb_drop_graphs(c);
+    }
+    (void)S;
+    if (nr > c->dg_nr) {
+        c->dgVcur = (double*)pb_alloc(c, sizeof(double) * (size_t)(n * nr));
+        if (!c->dgVcur) return pb_fail(c, PB_ERR_NOMEM, "gmres workspace: out of memory");
+        c->dg_nr = nr;
+    }
+    if (nctl > c->dg_nctl) {
+        c->dgctl = pb_alloc(c, sizeof(DgCtl) * nctl);
+        if (!c->dgctl) return pb_fail(c, PB_ERR_NOMEM, "gmres workspace: out of memory");
+        if (c->dgctl_h) cudaFreeHost(c->dgctl_h);
+        c->dgctl_h = nullptr;
+        if (cudaMallocHost(&c->dgctl_h, sizeof(DgCtl) * nctl) != cudaSuccess) {
+            c->dgctl_h = nullptr;
+            return pb_fail(c, PB_ERR_NOMEM, "gmres workspace: out of pinned host memory");
+        }
+        memset(c->dgctl_h, 0, sizeof(DgCtl) * nctl);
+        c->dg_nctl = nctl;
+    }
+    return PB_OK;
+}
+
+// one capture segment on the context's private stream into graph g after deps
+static bool seg_begin(pb_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd)
+{
+    return cudaStreamBeginCaptureToGraph(c->st, g, nd ? deps : nullptr, nullptr, nd, cudaStreamCaptureModeThreadLocal) ==
+           cudaSuccess;
+}
+static bool seg_end(pb_ctx* c, std::vector<cudaGraphNode_t>* leaves)
+{
+    cudaStreamCaptureStatus stt;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    bool ok = cudaStreamGetCaptureInfo(c->st, &stt, nullptr, nullptr, &d, nullptr, &nd) == cudaSuccess &&
+              stt == cudaStreamCaptureStatusActive;
+    if (ok && leaves) leaves->assign(d, d + nd);
+    cudaGraph_t out = nullptr;
+    ok = (cudaStreamEndCapture(c->st, &out) == cudaSuccess) && ok;
+    return ok;
+}
+static bool add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle h,
+                      cudaGraphNode_t* node, cudaGraph_t* body)
+{
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    if (cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p) != cudaSuccess)
+        return false;
+    *body = p.conditional.phGraph_out[0];
+    return true;
+}
+
+// Append one device-driven solve of nr right-hand sides (X, B: nr x 2N in tree order, vector r
+// at + 2 N r) to graph g after deps; its last nodes go to leaves. start: 0 = from zero (X is
+// zeroed inside), 1 = from the given X, scaled per right-hand side by its least-squares
+// factor. ictl selects the control block. Must run with the context's private stream as c->st
+// and every buffer reserved. The captured launch counts go to cnt (prologue, per cycle, per
+// step).
+int pb_dg_append(pb_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, double* X, const double* B,
+                 int nr, int m, int start, int ictl, std::vector<cudaGraphNode_t>* leaves, long long cnt[3])
+{
+    const long long n = 2LL * c->nt;
+    const int G = grid_for(n);
+    const long long S = (long long)(m + 1) * m + 6 * (m + 2);
+    const long long vstr = (long long)(m + 1) * n, pstr = (long long)DOT_BLOCKS * (m + 2);
+    double *V = c->gbV, *W = c->gbW, *Z = c->gbZ, *part = c->gbpart, *small = c->gbsmall, *Vc = c->dgVcur;
+    DgCtl* ctl = (DgCtl*)c->dgctl + ictl;
+    const GmState st = gm_state(small, m);
+    const long long hoff = st.hcol - small, yoff = st.y - small, roff = st.res - small;
+    cudaGraphConditionalHandle hO, hI;
+    if (cudaGraphConditionalHandleCreate(&hO, g, 0, 0) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> lv;
+    int rc = PB_OK;
+    long long n0 = c->nlaunch;
+    // prologue: ||b||, the start, the first residual and its normalisation
+    if (!seg_begin(c, g, deps.data(), deps.size())) return -1;
+    do {
+        if (start == 0) PB_CUDA(c, cudaMemsetAsync(X, 0, sizeof(double) * n * nr, c->st));
+        k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, B, part, pstr);
+        PB_LAUNCH(c);
+        k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff, S);
+        PB_LAUNCH(c);
+        k_dg_init<<<1, PB_MAX_RHS, 0, c->st>>>(ctl, small, S, hoff, start);
+        PB_LAUNCH(c);
+        if (start == 0) {
+            PB_CUDA(c, cudaMemcpyAsync(W, B, sizeof(double) * n * nr, cudaMemcpyDeviceToDevice, c->st));
+        } else {
+            if ((rc = pb_matvec_sorted_multi(c, X, W, nr))) break;
+            k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, B, n, W, part, pstr);
+            PB_LAUNCH(c);
+            k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff, S);
+            PB_LAUNCH(c);
+            k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
+            PB_LAUNCH(c);
+            k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff + 1, S);
+            PB_LAUNCH(c);
+            k_dg_start_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, small, S, hoff, X, W);
+            PB_LAUNCH(c);
+            k_bresidual<<<dim3(G, nr), KB, 0, c->st>>>(n, B, W);
+            PB_LAUNCH(c);
+        }
+        k_dg_zero_x<<<dim3(G, nr), KB, 0, c->st>>>(n, X, ctl);
+        PB_LAUNCH(c);
+        k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
+        PB_LAUNCH(c);
+        k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff, S);
+        PB_LAUNCH(c);
+        k_dg_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, small, S, hoff, V, vstr, Vc, ctl, 1);
+        PB_LAUNCH(c);
+        k_bgm_start<<<nr, 1, 0, c->st>>>(m, st, S);
+        PB_LAUNCH(c);
+        k_dg_cycle_ctl<<<1, PB_MAX_RHS, 0, c->st>>>(ctl, small, S, roff, hO, 1);
+        PB_LAUNCH(c);
+    } while (0);
+    if (!seg_end(c, &lv) || rc) return rc ? rc : -1;
+    cnt[0] = c->nlaunch - n0;
+    // outer loop: one restart cycle per pass
+    cudaGraphNode_t wO, wI;
+    cudaGraph_t bO, bI;
+    if (!add_while(g, lv, hO, &wO, &bO)) return -1;
+    if (cudaGraphConditionalHandleCreate(&hI, bO, 0, 0) != cudaSuccess) return -1;
+    n0 = c->nlaunch;
+    if (!seg_begin(c, bO, nullptr, 0)) return -1;
+    k_dg_enter<<<1, 1, 0, c->st>>>(ctl, hI);
+    PB_LAUNCH(c);
+    if (!seg_end(c, &lv)) return -1;
+    if (!add_while(bO, lv, hI, &wI, &bI)) return -1;
+    long long n1 = c->nlaunch - n0;
+    // inner loop: one Arnoldi step per pass
+    n0 = c->nlaunch;
+    if (!seg_begin(c, bI, nullptr, 0)) return -1;
+    do {
+        if ((rc = pb_precond_apply_multi(c, Vc, n, Z, n, nr))) break;
+        if ((rc = pb_matvec_sorted_multi(c, Z, W, nr))) break;
+        for (int pass = 0; pass < 2; ++pass) {
+            k_dg_dot<<<dim3(DOT_BLOCKS, m, nr), KB, 0, c->st>>>(n, V, vstr, W, part, pstr, ctl);
+            PB_LAUNCH(c);
+            k_dg_finish<<<dim3(m, nr), KB, 0, c->st>>>(part, pstr, small + (pass ? yoff : hoff), S, ctl, 0);
+            PB_LAUNCH(c);
+            k_dg_orth<<<dim3(G, nr), KB, 0, c->st>>>(n, V, vstr, small + (pass ? yoff : hoff), S, W, ctl);
+            PB_LAUNCH(c);
+        }
+        k_dg_merge<<<nr, 64, 0, c->st>>>(small, S, yoff, hoff, ctl);
+        PB_LAUNCH(c);
+        k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
+        PB_LAUNCH(c);
+        k_dg_finish<<<dim3(1, nr), KB, 0, c->st>>>(part, pstr, small + hoff, S, ctl, 1);
+        PB_LAUNCH(c);
+        k_dg_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, small, S, hoff, V, vstr, Vc, ctl, 0);
+        PB_LAUNCH(c);
+        k_dg_givens<<<nr, 1, 0, c->st>>>(m, st, S, ctl);
+        PB_LAUNCH(c);
+        k_dg_step_ctl<<<1, PB_MAX_RHS, 0, c->st>>>(ctl, small, S, roff, hI);
+        PB_LAUNCH(c);
+    } while (0);
+    if (!seg_end(c, nullptr) || rc) return rc ? rc : -1;
+    cnt[2] = c->nlaunch - n0;
+    // end of the cycle: update, true residual, next cycle's start
+    n0 = c->nlaunch;
+    std::vector<cudaGraphNode_t> after = {wI};
+    if (!seg_begin(c, bO, after.data(), 1)) return -1;
+    do {
+        k_dg_solve<<<nr, 1, 0, c->st>>>(m, st, S, ctl);
+        PB_LAUNCH(c);
+        k_dg_combine<<<dim3(G, nr), KB, 0, c->st>>>(n, V, vstr, small, S, yoff, W, ctl);
+        PB_LAUNCH(c);
+        if ((rc = pb_precond_apply_multi(c, W, n, Z, n, nr))) break;
+        k_dg_axpy<<<dim3(G, nr), KB, 0, c->st>>>(n, Z, X, ctl);
+        PB_LAUNCH(c);
+        if ((rc = pb_matvec_sorted_multi(c, X, W, nr))) break;
+        k_bresidual<<<dim3(G, nr), KB, 0, c->st>>>(n, B, W);
+        PB_LAUNCH(c);
+        k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
+        PB_LAUNCH(c);
+        k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff, S);
+        PB_LAUNCH(c);
+        k_dg_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, small, S, hoff, V, vstr, Vc, ctl, 1);
+        PB_LAUNCH(c);
+        k_bgm_start<<<nr, 1, 0, c->st>>>(m, st, S);
+        PB_LAUNCH(c);
+        k_dg_cycle_ctl<<<1, PB_MAX_RHS, 0, c->st>>>(ctl, small, S, roff, hO, 0);
+        PB_LAUNCH(c);
+    } while (0);
+    if (!seg_end(c, nullptr) || rc) return rc ? rc : -1;
+    cnt[1] = n1 + c->nlaunch - n0;
+    if (leaves) leaves->assign(1, wO);
+    return PB_OK;
+}
+
+void pb_dg_drop(pb_ctx* c)
+{
+    if (c->dg_exec) cudaGraphExecDestroy(c->dg_exec);
+    c->dg_exec = nullptr;
+}
+
+// host side of one control block after the graph ran: solve records and launch count
+void pb_dg_results(pb_ctx* c, int ictl, int nr, const long long cnt[3], pb_solve_info* infos, int* worst)
+{
+    const DgCtl* h = (const DgCtl*)c->dgctl_h + ictl;
+    c->nlaunch += cnt[0] + (long long)h->cycles * cnt[1] + (long long)h->it * cnt[2];
+    for (int r = 0; r < nr; ++r) {
+        pb_solve_info inf = {h->its[r], h->mvs[r], h->rel[r], h->status[r], h->init[r]};
+        if (inf.status == PB_OK && !h->conv[r]) inf.status = PB_ERR_NOT_CONVERGED;
+        if (inf.status == PB_OK && !isfinite(inf.rel_residual)) inf.status = PB_ERR_NONFINITE;
+        if (infos) infos[r] = inf;
+        if (inf.status != PB_OK && *worst == PB_OK) *worst = inf.status;
+    }
+}
+
+// the host's settings of a control block (uploaded before the graph launch)
+void pb_dg_settings(pb_ctx* c, int ictl, int nr, int m, double tol, int max_iter)
+{
+    DgCtl* h = (DgCtl*)c->dgctl_h + ictl;
+    h->nr = nr;
+    h->m = m;
+    h->tol = tol;
+    h->max_iter = max_iter;
+}
+
+int pb_dg_upload(pb_ctx* c, int nctl)
+{
+    PB_CUDA(c, cudaMemcpyAsync(c->dgctl, c->dgctl_h, sizeof(DgCtl) * nctl, cudaMemcpyHostToDevice, c->st));
+    return PB_OK;
+}
+
+int pb_dg_download(pb_ctx* c, int nctl)
+{
+    PB_CUDA(c, cudaMemcpyAsync(c->dgctl_h, c->dgctl, sizeof(DgCtl) * nctl, cudaMemcpyDeviceToHost, c->st));
+    return PB_OK;
+}
+
+// Device-driven GMRES of nr right-hand sides on this context (one graph, cached while the
+// build, the workspace and the shape of the call stay the same). Returns -1 when the graph
+// cannot be built here (the caller then takes the host-driven loop).
+int pb_gmres_dev(pb_ctx* c, double* X, const double* B, int nr, double tol, int max_iter, int restart, int start,
+                 pb_solve_info* infos)
+{
+    int rc;
+    if ((rc = pb_matvec_reserve(c, nr))) return rc;
+    if ((rc = pb_dg_reserve(c, nr, restart, 1))) return rc;
+    const void* key[6] = {(void*)X, (void*)B, (void*)c->gbV, (void*)c->dgVcur, (void*)c->dgctl,
+                          (void*)(long long)c->build_gen};
+    const int ikey[3] = {nr, restart, start};
+    bool same = c->dg_exec && !memcmp(key, c->dg_key, sizeof(key)) && !memcmp(ikey, c->dg_ikey, sizeof(ikey));
+    if (!same) {
+        if (c->dg_exec) cudaGraphExecDestroy(c->dg_exec);
+        c->dg_exec = nullptr;
+        cudaGraph_t g = nullptr;
+        if (cudaGraphCreate(&g, 0) != cudaSuccess) return -1;
+        cudaStream_t keep = c->st;
+        c->st = c->cap_st;
+        const long long nl = c->nlaunch;
+        std::vector<cudaGraphNode_t> leaves;
+        rc = pb_dg_append(c, g, {}, X, B, nr, restart, start, 0, &leaves, c->dg_cnt);
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(c->st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;  // a failed segment left its capture open
+            cudaStreamEndCapture(c->st, &junk);
+            if (junk && junk != g) cudaGraphDestroy(junk);
+        }
+        c->st = keep;
+        c->nlaunch = nl;
+        if (rc == PB_OK && cudaGraphInstantiate(&c->dg_exec, g, 0) != cudaSuccess) rc = -1;
+        cudaGraphDestroy(g);
+        if (rc != PB_OK) {
+            c->dg_exec = nullptr;
+            if (rc > 0) return rc;
+            cudaGetLastError();
+            return -1;
+        }
+        memcpy(c->dg_key, key, sizeof(key));
+        memcpy(c->dg_ikey, ikey, sizeof(ikey));
+    }
+    pb_dg_settings(c, 0, nr, restart, tol, max_iter);
+    if ((rc = pb_dg_upload(c, 1))) return rc;
+    PB_CUDA(c, cudaGraphLaunch(c->dg_exec, c->st));
+    ++c->graph_launches;
+    if ((rc = pb_dg_download(c, 1))) return rc;
+    int derr = 0;
+    PB_CUDA(c, cudaMemcpyAsync(&derr, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    PB_CUDA(c, cudaStreamSynchronize(c->st));
+    int worst = PB_OK;
+    pb_dg_results(c, 0, nr, c->dg_cnt, infos, &worst);
+    if (derr) {
+        for (int r = 0; r < nr; ++r)
+            if (infos) infos[r].status = PB_ERR_TIMEOUT;
+        return pb_fail(c, PB_ERR_TIMEOUT, "a bounded wait in the MtL kernel gave up");
+    }
     return worst;
 }

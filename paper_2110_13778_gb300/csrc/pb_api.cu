@@ -52,11 +52,21 @@ static void pb_free_build(pb_ctx* c)
     c->scratch = nullptr;
     c->escratch = nullptr;
     c->qstates = nullptr;
+    c->qstates_n = 0;
     pb_drop_graphs(c);
     c->gb_graph_failed = false;
     c->mv_nr = c->gb_nr = c->gb_m = c->dens_nr = 0;
     c->far_nr = 1;
     c->mxs = c->mys = c->gbV = c->gbW = c->gbZ = c->gbB = c->gbpart = c->gbsmall = nullptr;
+    pb_dg_drop(c);
+    c->tc_part = nullptr;
+    c->tc_nw = 0;
+    c->bE = nullptr;
+    c->bE_n = 0;
+    c->dgVcur = nullptr;
+    c->dgctl = nullptr;
+    c->dg_nr = c->dg_nctl = 0;
+    ++c->build_gen;
     c->near_dens = nullptr;
     c->yfar = nullptr;
     c->yfar_nr = 0;
@@ -87,6 +97,7 @@ extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
     if (prm->precision != PB_FP64 && prm->precision != PB_MIXED) return PB_ERR_ARG;
     if (prm->singular < PB_SINGULAR_AUTO || prm->singular > PB_SINGULAR_FF) return PB_ERR_ARG;
     if (prm->precond < PB_PRECOND_NONE || prm->precond > PB_PRECOND_BLOCK) return PB_ERR_ARG;
+    if (prm->pc_block != 0 && (prm->pc_block < 8 || prm->pc_block > 96)) return PB_ERR_ARG;
     pb_ctx* c = new pb_ctx();
     c->prm = *prm;
     c->st = (cudaStream_t)stream;
@@ -144,6 +155,8 @@ extern "C" int pb_destroy(pb_ctx* c)
     if (c->ev_tree) cudaEventDestroy(c->ev_tree);
     if (c->ev_sing) cudaEventDestroy(c->ev_sing);
     pb_drop_graphs(c);
+    pb_dg_drop(c);
+    if (c->dgctl_h) cudaFreeHost(c->dgctl_h);
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     for (int i = 0; i < 10; ++i)
@@ -439,12 +452,23 @@ extern "C" int pb_gmres_solve(pb_ctx* c, double* x, double tol, int max_iter, in
         PB_CUDA(c, cudaMemsetAsync(c->xs, 0, sizeof(double) * 2 * c->nt, c->st));
     }
     pb_solve_info loc;
-    if ((rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc, !use_x0)) &&
-        rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE && rc != PB_ERR_TIMEOUT)
-        return rc;
+    // one graph launch with the stopping test on the device; with per-phase timing enabled (or
+    // where the graph cannot be built) the host-driven loop, which reads one residual per step
+    rc = -1;
+    if (!c->timing && !c->dg_failed) {
+        rc = pb_gmres_dev(c, c->xs, c->ws, 1, tol, max_iter, restart, use_x0 ? 1 : 0, &loc);
+        if (rc == -1) c->dg_failed = true;
+    }
+    if (rc == -1) rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc, !use_x0);
+    if (rc && rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE && rc != PB_ERR_TIMEOUT) return rc;
     int rc2 = pb_scatter(c, c->xs, x);
     if (info) *info = loc;
     if (rc2) return rc2;
+    if (rc == PB_ERR_NOT_CONVERGED)
+        pb_fail(c, rc, "gmres: not converged after %d iterations (relative residual %.3g)", loc.iterations,
+                loc.rel_residual);
+    else if (rc == PB_ERR_NONFINITE)
+        pb_fail(c, rc, "gmres: a residual is not finite");
     return rc;
 }
 
@@ -469,7 +493,12 @@ extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, 
         if ((rc = pb_rhs_sorted(c, c->ws))) return rc;
         if (!(warm && s > 0)) PB_CUDA(c, cudaMemsetAsync(c->xs, 0, sizeof(double) * n2, c->st));
         pb_solve_info loc;
-        rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc, !(warm && s > 0));
+        rc = -1;
+        if (!c->timing && !c->dg_failed) {
+            rc = pb_gmres_dev(c, c->xs, c->ws, 1, tol, max_iter, restart, (warm && s > 0) ? 1 : 0, &loc);
+            if (rc == -1) c->dg_failed = true;
+        }
+        if (rc == -1) rc = pb_gmres_sorted(c, c->xs, c->ws, tol, max_iter, restart, &loc, !(warm && s > 0));
         if (rc && rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE && rc != PB_ERR_TIMEOUT) return rc;
         if (rc && worst == PB_OK) worst = rc;
         if (infos) infos[s] = loc;
@@ -487,9 +516,10 @@ extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, 
         double *Xs = c->mxs, *Bs = c->mys;
         // the batch's charges on the device, then the right-hand sides 16 states per launch
         // (the pair geometry is shared by the states)
-        if (!c->qstates) {
+        if (!c->qstates || c->qstates_n < PB_MAX_RHS) {
             c->qstates = (double*)pb_alloc(c, sizeof(double) * ((size_t)PB_MAX_RHS * c->nc + 1));
             if (!c->qstates) return pb_fail(c, PB_ERR_NOMEM, "solve_states: out of memory");
+            c->qstates_n = PB_MAX_RHS;
         }
         if (c->nc > 0)
             PB_CUDA(c, cudaMemcpyAsync(c->qstates, q + (size_t)s0 * c->nc, sizeof(double) * c->nc * nr,
@@ -500,7 +530,12 @@ extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, 
         for (int r = 0; r < nr; ++r)
             PB_CUDA(c, cudaMemcpyAsync(Xs + r * n2, c->xs, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->st));
         std::vector<pb_solve_info> loc(nr);
-        rc = pb_gmres_batch_sorted(c, Xs, Bs, nr, tol, max_iter, restart, loc.data());
+        rc = -1;
+        if (!c->timing && !c->dg_failed) {
+            rc = pb_gmres_dev(c, Xs, Bs, nr, tol, max_iter, restart, 1, loc.data());
+            if (rc == -1) c->dg_failed = true;
+        }
+        if (rc == -1) rc = pb_gmres_batch_sorted(c, Xs, Bs, nr, tol, max_iter, restart, loc.data());
         if (rc && rc != PB_ERR_NOT_CONVERGED && rc != PB_ERR_NONFINITE && rc != PB_ERR_TIMEOUT) return rc;
         if (rc && worst == PB_OK) worst = rc;
         for (int r = 0; r < nr; ++r) {
@@ -529,6 +564,16 @@ extern "C" int pb_solvation_energy(pb_ctx* c, const double* x, double* E)
     int rc;
     if ((rc = pb_gather(c, x, c->xs))) return rc;
     return pb_energy_sorted(c, c->xs, E);
+}
+
+extern "C" int pb_solvation_energy_treecode(pb_ctx* c, const double* x, double theta, double* E)
+{
+    PB_ALIVE(c);
+    if (!c->built) return pb_fail(c, PB_ERR_STATE, "energy before build_tree");
+    if (!x || !E || !(theta > 0) || !(theta < 1)) return pb_fail(c, PB_ERR_ARG, "treecode energy: bad argument");
+    int rc;
+    if ((rc = pb_gather(c, x, c->xs))) return rc;
+    return pb_energy_treecode_sorted(c, c->xs, theta, E);
 }
 
 extern "C" int pb_get_tree_stats(pb_ctx* c, pb_tree_stats* s)

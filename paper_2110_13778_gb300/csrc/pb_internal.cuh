@@ -152,6 +152,7 @@ struct pb_ctx {
     double* scratch = nullptr;    // reduction partials
     double* escratch = nullptr;   // per-state energy partials (several states at once)
     double* qstates = nullptr;    // device charges of up to PB_MAX_RHS states [PB_MAX_RHS][nc]
+    int qstates_n = 0;            // states qstates holds room for (0: PB_MAX_RHS if qstates is set)
     // several right-hand sides: tree-ordered work vectors and the batched GMRES workspace
     double *mxs = nullptr, *mys = nullptr;
     int mv_nr = 0;
@@ -165,6 +166,24 @@ struct pb_ctx {
     bool gb_graph_failed = false;
     long long graph_launches = 0;       // replays of captured Arnoldi steps
     cudaStream_t cap_st = nullptr;      // private stream for capturing
+    // device-driven GMRES (one graph per solve with conditional WHILE nodes): the current basis
+    // vectors of nr right-hand sides, control blocks (device and pinned host copies), the cached
+    // executable graph of a single-context solve with its key and captured launch counts
+    double* dgVcur = nullptr;
+    int dg_nr = 0;
+    void* dgctl = nullptr;
+    void* dgctl_h = nullptr;
+    int dg_nctl = 0;
+    cudaGraphExec_t dg_exec = nullptr;
+    const void* dg_key[6] = {};
+    int dg_ikey[3] = {};
+    long long dg_cnt[3] = {};
+    bool dg_failed = false;           // graphs with conditional nodes cannot be built here
+    long long build_gen = 0;          // incremented by every pb_build_tree / pb_mesh_upload
+    double* tc_part = nullptr;        // treecode energy: one partial per (charge, level-1 cluster)
+    long long tc_nw = 0;
+    double* bE = nullptr;         // energies of the states of a batched multi-molecule solve (device)
+    int bE_n = 0;
     double* hscal = nullptr;      // pinned host scalars
     // GMRES workspace (Krylov basis, work vectors, reduction partials, small dense state)
     int gm_m = 0;
@@ -240,6 +259,22 @@ int pb_matvec_reserve(pb_ctx* c, int nr);  // pb_api.cu: every buffer a product 
 void pb_drop_graphs(pb_ctx* c);           // pb_api.cu
 int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double tol, int max_iter, int restart,
                           pb_solve_info* infos);  // krylov.cu
+// device-driven GMRES (krylov.cu): returns -1 when its graph cannot be built on this device
+// (the caller then takes the host-driven loop); start 0 = from zero, 1 = from X (scaled)
+int pb_gmres_dev(pb_ctx* c, double* X, const double* B, int nr, double tol, int max_iter, int restart, int start,
+                 pb_solve_info* infos);
+void pb_dg_drop(pb_ctx* c);
+int pb_energy_treecode_sorted(pb_ctx* c, const double* xs, double theta, double* E);  // farfield.cu
+// pieces of the device-driven solve for graphs over several contexts (krylov.cu)
+int pb_dg_reserve(pb_ctx* c, int nr, int m, int nctl);
+int pb_dg_append(pb_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, double* X, const double* B,
+                 int nr, int m, int start, int ictl, std::vector<cudaGraphNode_t>* leaves, long long cnt[3]);
+void pb_dg_settings(pb_ctx* c, int ictl, int nr, int m, double tol, int max_iter);
+int pb_dg_upload(pb_ctx* c, int nctl);
+int pb_dg_download(pb_ctx* c, int nctl);
+void pb_dg_results(pb_ctx* c, int ictl, int nr, const long long cnt[3], pb_solve_info* infos, int* worst);
+int pb_energy_reserve(pb_ctx* c);
+int pb_energy_states_queue(pb_ctx* c, const double* Q, const double* X, int nr, double* Edev);  // nr <= 16
 int pb_rhs_sorted(pb_ctx* c, double* bs);                          // krylov.cu
 int pb_energy_sorted(pb_ctx* c, const double* xs, double* E);      // krylov.cu
 int pb_rhs_states_sorted(pb_ctx* c, const double* Q, double* B, int nr);        // krylov.cu, nr <= 16

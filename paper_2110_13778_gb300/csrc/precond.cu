@@ -445,15 +445,16 @@ int pb_precond_plan(pb_ctx* c)
 {
     const int nt = c->nt;
     if (c->prm.precond != PB_PRECOND_BLOCK) return PB_OK;
-    // blocks: the leaves of the tree; a leaf with more than PB_PC_BMAX elements is split into
-    // nearly equal consecutive (Morton-ordered) parts of at most PB_PC_BMAX elements
+    // blocks: the leaves of the tree; a leaf with more than bmax elements (pc_block, at most
+    // PB_PC_BMAX) is split into nearly equal consecutive (Morton-ordered) parts of at most bmax
     const PbLevel& lv = c->lev[c->L];
     const std::vector<int>& hb = c->h_leaf_begin;
     std::vector<int>& pb_ = c->h_up_i[2];
+    const int bmax = c->prm.pc_block > 0 ? std::min(c->prm.pc_block, PB_PC_BMAX) : PB_PC_BMAX;
     pb_.clear();
     for (int k = 0; k < lv.ncl; ++k) {
         int n = hb[k + 1] - hb[k];
-        int parts = (n + PB_PC_BMAX - 1) / PB_PC_BMAX;
+        int parts = (n + bmax - 1) / bmax;
         int base = n / parts, extra = n % parts, s = hb[k];
         for (int q = 0; q < parts; ++q) {
             pb_.push_back(s);

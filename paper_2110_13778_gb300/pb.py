@@ -29,6 +29,7 @@ EXPORTS = [
     "pb_mlp_create", "pb_mlp_destroy", "pb_mlp_last_error", "pb_mlp_param_count", "pb_mlp_get_params",
     "pb_mlp_set_params", "pb_mlp_forward", "pb_mlp_gradient", "pb_mlp_train_step", "pb_features",
     "pb_learned_guess", "pb_measure_alu_peaks", "pb_autotune", "pb_matvec_multi", "pb_get_graph_launches",
+    "pb_solvation_energy_treecode", "pb_batch_solve_states",
 ]
 PB_MAX_RHS = 64
 NFEAT = 18
@@ -47,6 +48,7 @@ class pb_params(ctypes.Structure):
         ("eta0", ctypes.c_double), ("leaf_size", ctypes.c_int), ("levels", ctypes.c_int),
         ("p", ctypes.c_int), ("adaptive", ctypes.c_int), ("qs", ctypes.c_int),
         ("precision", ctypes.c_int), ("precond", ctypes.c_int), ("singular", ctypes.c_int),
+        ("pc_block", ctypes.c_int),
     ]
 
 
@@ -95,6 +97,10 @@ def lib():
         L.pb_precond_apply.argtypes = [vp, vp, vp]
         L.pb_gmres_solve.argtypes = [vp, vp, c_double, c_int, c_int, c_int, ctypes.POINTER(pb_solve_info)]
         L.pb_solvation_energy.argtypes = [vp, vp, dp]
+        L.pb_solvation_energy_treecode.argtypes = [vp, vp, c_double, dp]
+        L.pb_batch_solve_states.argtypes = [ctypes.POINTER(vp), c_int, ctypes.POINTER(dp), c_int,
+                                            ctypes.POINTER(vp), dp, c_double, c_int, c_int,
+                                            ctypes.POINTER(pb_solve_info)]
         L.pb_solve_states.argtypes = [vp, dp, c_int, vp, dp, c_double, c_int, c_int, c_int,
                                       ctypes.POINTER(pb_solve_info)]
         L.pb_get_tree_stats.argtypes = [vp, ctypes.POINTER(pb_tree_stats)]
@@ -142,8 +148,9 @@ def _check(ctx, rc):
 
 
 def params(eps_in=1.0, eps_out=80.0, kappa=0.1257, eta0=0.8, leaf_size=64, levels=0, p=8, adaptive=0, qs=3,
-           precision=PB_FP64, precond=PB_PRECOND_BLOCK, singular=0):
-    return pb_params(eps_in, eps_out, kappa, eta0, leaf_size, levels, p, adaptive, qs, precision, precond, singular)
+           precision=PB_FP64, precond=PB_PRECOND_BLOCK, singular=0, pc_block=0):
+    return pb_params(eps_in, eps_out, kappa, eta0, leaf_size, levels, p, adaptive, qs, precision, precond, singular,
+                     pc_block)
 
 
 def pb_create(prm: pb_params, stream=0):
@@ -222,9 +229,36 @@ def pb_solve_states(ctx, q_states, X, tol=1e-6, max_iter=200, restart=50, warm=T
     return E, list(infos)
 
 
+def pb_batch_solve_states(ctxs, q_states, X, tol=1e-6, max_iter=200, restart=50, raise_on_fail=True):
+    """Several molecules x several charge states in one graph launch. ctxs: built contexts;
+    q_states: per molecule an (nrhs, nc) host array (same nrhs for all); X: per molecule an
+    (nrhs, 2N) float64 CUDA tensor (overwritten). Returns (energies (nmol, nrhs), infos as a
+    list of per-molecule lists)."""
+    nmol = len(ctxs)
+    Qs = [np.ascontiguousarray(q, dtype=np.float64) for q in q_states]
+    nrhs = Qs[0].shape[0]
+    dp = ctypes.POINTER(ctypes.c_double)
+    carr = (ctypes.c_void_p * nmol)(*[c.value for c in ctxs])
+    qarr = (dp * nmol)(*[q.ctypes.data_as(dp) for q in Qs])
+    xarr = (ctypes.c_void_p * nmol)(*[_ptr(x).value for x in X])
+    E = np.zeros((nmol, nrhs))
+    infos = (pb_solve_info * (nmol * nrhs))()
+    rc = lib().pb_batch_solve_states(carr, nmol, qarr, nrhs, xarr, E.ctypes.data_as(dp), tol, max_iter, restart, infos)
+    if rc != PB_OK and (raise_on_fail or rc not in (PB_ERR_NOT_CONVERGED, PB_ERR_NONFINITE)):
+        _check(ctxs[0], rc)
+    inf = list(infos)
+    return E, [inf[k * nrhs:(k + 1) * nrhs] for k in range(nmol)]
+
+
 def pb_solvation_energy(ctx, x):
     E = ctypes.c_double()
     _check(ctx, lib().pb_solvation_energy(ctx, _ptr(x), ctypes.byref(E)))
+    return E.value
+
+
+def pb_solvation_energy_treecode(ctx, x, theta=0.5):
+    E = ctypes.c_double()
+    _check(ctx, lib().pb_solvation_energy_treecode(ctx, _ptr(x), float(theta), ctypes.byref(E)))
     return E.value
 
 

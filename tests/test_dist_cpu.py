@@ -30,7 +30,7 @@ def _rank(rank, world, port, out):
     r, w, _ = bench.dist_setup(world)
     bench.barrier(w)
     m = bench.dist_max(1.5 + r, w)
-    _, sizes = bench.batch_sizes(r, 4)
+    _, sizes = bench.batch_sizes(r, 4, 8000)
     out.put((r, w, m, [int(v) for v in sizes]))
     bench.barrier(w)
     dist.destroy_process_group()

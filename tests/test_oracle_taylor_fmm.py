@@ -229,3 +229,19 @@ def test_scaled_forms_of_leaf_moments_and_evaluation():
     got_d = sum(ex[k] * sum(n[0, i] * lh[up[i][k]] for i in range(3) if up[i][k] is not None)
                 for k in range(len(idx)))
     assert np.isclose(got_v, val[0], rtol=1e-12) and np.isclose(got_d, der[0], rtol=1e-11)
+
+
+def test_treecode_energy_pinned_by_the_direct_sum():
+    # Section 2.5's treecode approximates eqsolengdis (the oracle's direct sum): with theta
+    # so small that no cluster passes the MAC it is that sum; at theta = 0.5 its error falls
+    # geometrically with the order
+    m = inputs.kirkwood_ball(3, 20.0, 8, 16.0, seed=6)
+    ph = dense.Phys(1.0, 80.0, 0.1257, qs=3)
+    x, _, _ = dense.solve(m, ph)
+    Ed = dense.energy(m, ph, x)
+    tr = fmm.Tree(m.verts, m.tris, leaf_size=16, eta0=0.8)
+    assert abs(fmm.treecode_energy(tr, m, x, ph, 4, 1e-9) - Ed) < 1e-13 * abs(Ed)
+    errs = [abs(fmm.treecode_energy(tr, m, x, ph, p, 0.5) - Ed) / abs(Ed) for p in (2, 4, 6)]
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-5, errs
+    # a wider opening angle accepts more clusters and is less accurate
+    assert abs(fmm.treecode_energy(tr, m, x, ph, 4, 0.8) - Ed) / abs(Ed) > errs[1]
