@@ -50,13 +50,14 @@ def lib():
             L.orc_geometry.argtypes = [dp, ip, c_int, dp, dp, dp]
             L.orc_ss_points.argtypes = [c_int, c_double, c_double, c_double, c_double, dp, dp, dp]
             L.orc_ss_points.restype = c_int
-            L.orc_pair_integrals.argtypes = [dp, ip, c_int, c_int, c_double, c_double, c_int, dp]
+            L.orc_pair_integrals.argtypes = [dp, ip, c_int, c_int, c_double, c_double, c_int, c_int, dp, dp, dp, dp]
             L.orc_pair_terms.argtypes = [dp, ip, c_int, c_int, c_double, c_int, dp]
             L.orc_pair_terms.restype = c_int
-            L.orc_assemble.argtypes = [dp, ip, c_int, c_double, c_double, c_int, dp]
-            L.orc_rows_matvec.argtypes = [dp, ip, c_int, c_double, c_double, c_int, c_int, ip, dp, dp]
-            L.orc_rhs.argtypes = [dp, ip, c_int, dp, dp, c_int, c_double, dp]
-            L.orc_energy.argtypes = [dp, ip, c_int, dp, dp, c_int, c_double, c_double, dp]
+            L.orc_assemble.argtypes = [dp, ip, c_int, c_double, c_double, c_int, c_int, dp, dp, dp, dp]
+            L.orc_rows_matvec.argtypes = [dp, ip, c_int, c_double, c_double, c_int, c_int, dp, dp, dp, c_int, ip, dp,
+                                          dp]
+            L.orc_rhs.argtypes = [dp, ip, c_int, dp, dp, c_int, c_double, c_int, dp, dp, dp, dp]
+            L.orc_energy.argtypes = [dp, ip, c_int, dp, dp, c_int, c_double, c_double, c_int, dp, dp, dp, dp]
             L.orc_energy.restype = c_double
             _lib = L
     return _lib

@@ -41,16 +41,60 @@ def _i32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
 
 
+def _golub_welsch(a, b, mu0):
+    """Gauss rule of the orthogonal polynomials with monic recurrence coefficients a_k (k < n)
+    and b_k (1 <= k < n), total weight mu0: nodes are the eigenvalues of the symmetric
+    tridiagonal Jacobi matrix, weights mu0 times the squared first eigenvector components
+    (Golub and Welsch, Math. Comp. 23, 1969)."""
+    J = np.diag(np.asarray(a, dtype=np.float64))
+    if len(a) > 1:
+        off = np.sqrt(np.asarray(b, dtype=np.float64))
+        J += np.diag(off, 1) + np.diag(off, -1)
+    x, vec = np.linalg.eigh(J)
+    return x, mu0 * vec[0, :] ** 2
+
+
+def triangle_rule(q):
+    """Order-q regular rule on the reference triangle {0 <= e2 <= e1 <= 1} (q^2 points, the
+    "tensor product Gauss rule" of Section 3.1 read as a collapsed product): Gauss-Jacobi with
+    weight e1 in e1 (the Jacobian of e2 = e1 s) times Gauss-Legendre in s = e2 / e1. Exact for
+    polynomials of total degree <= 2q - 1; q = 1 is the centroid (2/3, 1/3) with weight 1/2.
+    Returns (e1, e2, w), weights summing to 1/2."""
+    k = np.arange(q)
+    kk = np.arange(1, q)
+    # weight t on [0, 1]: the Jacobi (alpha, beta) = (0, 1) recurrence on [-1, 1], shifted
+    a_t = (1.0 / ((2 * k + 1) * (2 * k + 3)) + 1.0) / 2.0
+    b_t = kk * (kk + 1) / (2.0 * kk + 1) ** 2 / 4.0
+    t, wt = _golub_welsch(a_t, b_t, 0.5)
+    # weight 1 on [0, 1]: Legendre, shifted
+    a_s = np.full(q, 0.5)
+    b_s = kk * kk / (4.0 * kk * kk - 1.0) / 4.0
+    sv, ws = _golub_welsch(a_s, b_s, 1.0)
+    e1 = np.repeat(t, q)
+    e2 = e1 * np.tile(sv, q)
+    w = np.outer(wt, ws).ravel()
+    if q == 1:  # exactly the centroid
+        e1, e2, w = np.array([2.0 / 3.0]), np.array([1.0 / 3.0]), np.array([0.5])
+    return e1, e2, w
+
+
 class Phys:
     """eps1 (inside), eps2 (outside), kappa (1/Angstrom), qs (Gauss points per cube axis of
-    the singular quadrature)."""
+    the singular quadrature), qr (order of the regular rule of non-touching pairs, the
+    right-hand side and the energy: 1 = centroid, 2-4 = Table 2's orders)."""
 
-    def __init__(self, eps1=1.0, eps2=80.0, kappa=0.1257, qs=3):
+    def __init__(self, eps1=1.0, eps2=80.0, kappa=0.1257, qs=3, qr=1):
         self.eps1, self.eps2, self.kappa, self.qs = float(eps1), float(eps2), float(kappa), int(qs)
+        self.qr = int(qr)
+        self.rule = triangle_rule(self.qr)
 
     @property
     def eps(self):
         return self.eps2 / self.eps1
+
+    def rule_args(self):
+        e1, e2, w = self.rule
+        return (len(w), _dp(e1), _dp(e2), _dp(w))
 
 
 def gauss_legendre01(n):
@@ -88,7 +132,7 @@ def ss_points(case, xi, h1, h2, h3):
 def pair_integrals(verts, tris, i, j, ph: Phys):
     V, T = _f64(verts), _i32(tris)
     out = np.zeros(4)
-    lib().orc_pair_integrals(_dp(V), _ip(T), int(i), int(j), ph.eps, ph.kappa, ph.qs, _dp(out))
+    lib().orc_pair_integrals(_dp(V), _ip(T), int(i), int(j), ph.eps, ph.kappa, ph.qs, *ph.rule_args(), _dp(out))
     return out
 
 
@@ -109,7 +153,7 @@ def assemble(verts, tris, ph: Phys):
     V, T = _f64(verts), _i32(tris)
     nt = T.shape[0]
     A = np.zeros((2 * nt, 2 * nt))
-    lib().orc_assemble(_dp(V), _ip(T), nt, ph.eps, ph.kappa, ph.qs, _dp(A))
+    lib().orc_assemble(_dp(V), _ip(T), nt, ph.eps, ph.kappa, ph.qs, *ph.rule_args(), _dp(A))
     return A
 
 
@@ -119,14 +163,16 @@ def rows_matvec(verts, tris, ph: Phys, elems, x):
     e = _i32(elems)
     xx = _f64(x)
     y = np.zeros(2 * e.shape[0])
-    lib().orc_rows_matvec(_dp(V), _ip(T), T.shape[0], ph.eps, ph.kappa, ph.qs, e.shape[0], _ip(e), _dp(xx), _dp(y))
+    lib().orc_rows_matvec(_dp(V), _ip(T), T.shape[0], ph.eps, ph.kappa, ph.qs, *ph.rule_args(), e.shape[0], _ip(e),
+                          _dp(xx), _dp(y))
     return y[0::2].copy(), y[1::2].copy()
 
 
 def rhs(mesh, ph: Phys):
     V, T = _f64(mesh.verts), _i32(mesh.tris)
     b = np.zeros(2 * T.shape[0])
-    lib().orc_rhs(_dp(V), _ip(T), T.shape[0], _dp(_f64(mesh.qpos)), _dp(_f64(mesh.q)), mesh.nc, ph.eps1, _dp(b))
+    lib().orc_rhs(_dp(V), _ip(T), T.shape[0], _dp(_f64(mesh.qpos)), _dp(_f64(mesh.q)), mesh.nc, ph.eps1,
+                  *ph.rule_args(), _dp(b))
     return b
 
 
@@ -135,7 +181,8 @@ def energy(mesh, ph: Phys, x):
     V, T = _f64(mesh.verts), _i32(mesh.tris)
     xx = _f64(x)
     return float(
-        lib().orc_energy(_dp(V), _ip(T), T.shape[0], _dp(_f64(mesh.qpos)), _dp(_f64(mesh.q)), mesh.nc, ph.eps, ph.kappa, _dp(xx))
+        lib().orc_energy(_dp(V), _ip(T), T.shape[0], _dp(_f64(mesh.qpos)), _dp(_f64(mesh.q)), mesh.nc, ph.eps, ph.kappa,
+                         *ph.rule_args(), _dp(xx))
     )
 
 

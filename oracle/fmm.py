@@ -186,6 +186,25 @@ def orders(tree, p, adaptive):
     return [p + (tree.L - l) if adaptive else p for l in range(tree.L + 1)]
 
 
+def points(tree, verts, tris, ph):
+    """The regular rule's points in tree order, element-major (the q^2 points of sorted element
+    k at k q^2 ... (k + 1) q^2 - 1): positions, weights 2 A_i w_a, unit normals. Order 1 gives
+    the centroids with weights A_i."""
+    V = np.asarray(verts, dtype=np.float64)
+    T = np.asarray(tris)
+    cent, area, nrm = dense.geometry(V, T)
+    o = tree.order
+    if ph.qr == 1:
+        return cent[o], area[o], nrm[o]
+    e1, e2, w = ph.rule
+    P = V[T[o]]  # (N, 3, 3) corners of the sorted elements
+    u, v, ww = P[:, 0, :], P[:, 1, :], P[:, 2, :]
+    pos = (u[:, None, :] + e1[None, :, None] * (v - u)[:, None, :] + e2[None, :, None] * (ww - v)[:, None, :])
+    wt = 2.0 * area[o][:, None] * w[None, :]
+    q2 = len(w)
+    return pos.reshape(-1, 3), wt.ravel(), np.repeat(nrm[o], q2, axis=0)
+
+
 def moments(tree, verts, tris, x, ph, pl, lstop=1):
     """Moments of the two far-field expansions (eqmoment, eqmomentL) at every level from L
     up to lstop: leaf moments by the one-point rule, then the upward pass (eqMtM). For each
@@ -193,13 +212,11 @@ def moments(tree, verts, tris, x, ph, pl, lstop=1):
     sk = sum_i [-dphi_i m^b(psi_i) + eps phi_i m_nu^b(psi_i)] (for Gk), with
     m^b(psi_i) = A_i (c_i - x_c)^b and m_nu^b(psi_i) = A_i n_i . grad (y - x_c)^b at y = c_i.
     pl: the order of each level."""
-    V = np.asarray(verts, dtype=np.float64)
-    T = np.asarray(tris)
     N = tree.N
-    cent, area, nrm = dense.geometry(V, T)
     o = tree.order
-    c_s, a_s, n_s = cent[o], area[o], nrm[o]
-    phi, dphi = x[:N][o], x[N:][o]
+    c_s, a_s, n_s = points(tree, verts, tris, ph)
+    q2 = len(a_s) // N
+    phi, dphi = np.repeat(x[:N][o], q2), np.repeat(x[N:][o], q2)
     eps = ph.eps
     L = tree.L
     idx = [taylor.multi_indices(pl[l]) for l in range(L + 1)]
@@ -209,7 +226,7 @@ def moments(tree, verts, tris, x, ph, pl, lstop=1):
     s0[L] = np.zeros((nL, len(idx[L])))
     sk[L] = np.zeros((nL, len(idx[L])))
     for c in range(nL):
-        b, e = tree.begin[L][c], tree.end[L][c]
+        b, e = tree.begin[L][c] * q2, tree.end[L][c] * q2
         dv = c_s[b:e] - tree.xc[L][c]
         M = _mono(dv, idx[L]) * a_s[b:e, None]
         Mn = _dmono(dv, n_s[b:e], idx[L]) * a_s[b:e, None]
@@ -232,21 +249,19 @@ def treecode_energy(tree, mesh, x, ph, p, theta, adaptive=False):
     """Solvation energy (eqsolengdis) in kcal/mol by the Cartesian treecode of Section 2.5.
 
     V_n = sum_i A_i [K1(x_n, c_i) dphi_i + K2(x_n, c_i) phi_i] (the one-point rule of the
-    direct sum) is accumulated per charge by addCluster from the root: a cluster c whose
+    direct sum; with ph.qr > 1 the regular rule's points) is accumulated per charge by addCluster from the root: a cluster c whose
     radius and distance to the charge satisfy the MAC (eqMAC) r_c / R <= theta contributes
     its Taylor series (eqsolengformTree) sum_b D^b G(x_n - x_c) (-1)^|b| / b! s[b] for both
     expansions (G0 with s0, Gk with sk, the moments of ``moments``); otherwise its children
     are visited, and a leaf is summed directly. r_c is read as the shrink-box half diagonal
     rho_c, which bounds every point of the cluster, and the test is made in FP64 as
     rho_c^2 <= theta^2 |x_n - x_c|^2. E = 1/2 * 4 pi 332.0716 * sum_n q_n V_n."""
-    V = np.asarray(mesh.verts, dtype=np.float64)
-    T = np.asarray(mesh.tris)
     N = tree.N
     L = tree.L
-    cent, area, nrm = dense.geometry(V, T)
     o = tree.order
-    c_s, a_s, n_s = cent[o], area[o], nrm[o]
-    phi, dphi = x[:N][o], x[N:][o]
+    c_s, a_s, n_s = points(tree, mesh.verts, mesh.tris, ph)
+    q2 = len(a_s) // N
+    phi, dphi = np.repeat(x[:N][o], q2), np.repeat(x[N:][o], q2)
     eps, kap = ph.eps, ph.kappa
     pl = orders(tree, p, adaptive)
     s0, sk = moments(tree, mesh.verts, mesh.tris, x, ph, pl, lstop=0)
@@ -285,7 +300,7 @@ def treecode_energy(tree, mesh, x, ph, p, theta, adaptive=False):
                 for ch in range(tree.child_end[l][c] - 1, tree.child_begin[l][c] - 1, -1):
                     stack.append((l + 1, ch))
             else:
-                Vn += direct(xn, tree.begin[L][c], tree.end[L][c])
+                Vn += direct(xn, tree.begin[L][c] * q2, tree.end[L][c] * q2)
         # the series of the accepted clusters, one derivative evaluation per level
         for l in range(L + 1):
             if accepted[l]:
@@ -300,13 +315,10 @@ def treecode_energy(tree, mesh, x, ph, p, theta, adaptive=False):
 
 def far_field(tree, verts, tris, x, ph, p, adaptive=False):
     """Far-field part (steps 2-6) of y = A x; returns (y1, y2) in element order."""
-    V = np.asarray(verts, dtype=np.float64)
-    T = np.asarray(tris)
     N = tree.N
-    cent, area, nrm = dense.geometry(V, T)
     o = tree.order
-    c_s, a_s, n_s = cent[o], area[o], nrm[o]
-    phi, dphi = x[:N][o], x[N:][o]
+    c_s, a_s, n_s = points(tree, verts, tris, ph)
+    q2 = len(a_s) // N
     eps, kap = ph.eps, ph.kappa
     L = tree.L
     pl = orders(tree, p, adaptive)
@@ -350,14 +362,15 @@ def far_field(tree, verts, tris, x, ph, p, adaptive=False):
                 S = _shift_matrix(idx[l], idx[l + 1], tree.xc[l + 1][ch] - tree.xc[l][c])
                 lam0[l + 1][ch] += S.T @ lam0[l][c]
                 lamk[l + 1][ch] += S.T @ lamk[l][c]
-    # step 6: evaluation (LtP)
+    # step 6: evaluation (LtP), integrated over each target element by the regular rule
     for c in range(tree.nclusters(L)):
         b, e = tree.begin[L][c], tree.end[L][c]
-        dv = c_s[b:e] - tree.xc[L][c]
+        pb_, pe = b * q2, e * q2
+        dv = c_s[pb_:pe] - tree.xc[L][c]
         M = _mono(dv, idx[L])
-        Mn = _dmono(dv, n_s[b:e], idx[L])
-        y1[b:e] -= a_s[b:e] * (M @ (lam0[L][c] + lamk[L][c]))
-        y2[b:e] -= a_s[b:e] * (Mn @ (lam0[L][c] + lamk[L][c] / eps))
+        Mn = _dmono(dv, n_s[pb_:pe], idx[L])
+        y1[b:e] -= (a_s[pb_:pe] * (M @ (lam0[L][c] + lamk[L][c]))).reshape(e - b, q2).sum(axis=1)
+        y2[b:e] -= (a_s[pb_:pe] * (Mn @ (lam0[L][c] + lamk[L][c] / eps))).reshape(e - b, q2).sum(axis=1)
     out1 = np.zeros(N)
     out2 = np.zeros(N)
     out1[o] = y1

@@ -19,7 +19,9 @@
  *     identical, edge-adjacent and vertex-adjacent pairs (Section 2.3, the paragraph after
  *     the right-hand side definition);
  *   - the right-hand side b1, b2 (source_terms, Section 2.2) by the centroid rule;
- *   - the per-element energy weights of eqsolengdis (Section 2.3).
+ *   - the per-element energy weights of eqsolengdis (Section 2.3);
+ *   - optionally (Section 3.1, Table 2) a regular rule of order 2-4 in place of the centroid
+ *     for regular pairs, the right-hand side and the energy (orc_rule).
  */
 #include <math.h>
 #include <stdint.h>
@@ -75,6 +77,23 @@ typedef struct {
     double eps;   /* eps = eps2/eps1 */
     double kappa; /* inverse Debye length */
 } orc_phys;
+
+/* Regular quadrature rule on the reference triangle {0 <= e2 <= e1 <= 1} (Section 3.1,
+ * Table 2: orders 1-4): n points (e1[a], e2[a]) with weights w[a] summing to 1/2; on an element
+ * with corners P0, P1, P2 the point is P0 + e1 (P1 - P0) + e2 (P2 - P1) and the weight is
+ * multiplied by the map's Jacobian 2A. n == 1 is the centroid rule (e1, e2) = (2/3, 1/3),
+ * w = 1/2, evaluated as the plain centroid with weight A. */
+typedef struct {
+    int n;
+    const double* e1;
+    const double* e2;
+    const double* w;
+} orc_rule;
+
+static void orc_rule_point(const double* u, const double* v, const double* w, double e1, double e2, double* x)
+{
+    for (int k = 0; k < 3; ++k) x[k] = u[k] + e1 * (v[k] - u[k]) + e2 * (w[k] - v[k]);
+}
 
 /* The six terms the kernels are made of, at x (normal nx) and y (normal ny):
  * Q[0] = G0 - Gk, Q[1] = d2Gk/dnx dny - d2G0/dnx dny, Q[2] = dG0/dny, Q[3] = dGk/dny,
@@ -343,7 +362,7 @@ static void orc_ss_terms(const double* V, const int32_t* T, int first, int secon
 }
 
 static void orc_pair(const double* V, const int32_t* T, int i, int j, const orc_phys* ph,
-                     const double* gx, const double* gw, int qs, double* I)
+                     const double* gx, const double* gw, int qs, const orc_rule* qr, double* I)
 {
     double ci[3], cj[3], ni[3], nj[3], Ai, Aj;
     {
@@ -354,11 +373,30 @@ static void orc_pair(const double* V, const int32_t* T, int i, int j, const orc_
         orc_geom(u, v, w, cj, &Aj, nj);
     }
     int shared = orc_shared(T, i, j);
-    if (shared == 0) {
+    if (shared == 0 && qr->n == 1) {
         /* one-point Gauss (centroid) rule for regular pairs */
         double K[4];
         orc_kernels(ci, ni, cj, nj, ph, K);
         for (int m = 0; m < 4; ++m) I[m] = Ai * Aj * K[m];
+        return;
+    }
+    if (shared == 0) {
+        /* the rule's points on both elements, every pair of them */
+        double ui[3], vi[3], wi[3], uj[3], vj[3], wj[3];
+        orc_tri(V, T, i, ui, vi, wi);
+        orc_tri(V, T, j, uj, vj, wj);
+        double acc[4] = {0, 0, 0, 0};
+        for (int a = 0; a < qr->n; ++a) {
+            double x[3];
+            orc_rule_point(ui, vi, wi, qr->e1[a], qr->e2[a], x);
+            for (int b = 0; b < qr->n; ++b) {
+                double y[3], K[4];
+                orc_rule_point(uj, vj, wj, qr->e1[b], qr->e2[b], y);
+                orc_kernels(x, ni, y, nj, ph, K);
+                for (int m = 0; m < 4; ++m) acc[m] += qr->w[a] * qr->w[b] * K[m];
+            }
+        }
+        for (int m = 0; m < 4; ++m) I[m] = (2.0 * Ai) * (2.0 * Aj) * acc[m];
         return;
     }
     /* the integrals of (j, i) follow from those of (i, j) by exchanging the roles of the two
@@ -410,22 +448,24 @@ int orc_pair_terms(const double* V, const int32_t* T, int i, int j, double kappa
 
 /* exported: the four integrals for one ordered pair (target i, source j) */
 int orc_pair_integrals(const double* V, const int32_t* T, int i, int j, double eps, double kappa,
-                       int qs, double* I)
+                       int qs, int nq, const double* qe1, const double* qe2, const double* qw, double* I)
 {
     double gx[64], gw[64];
     if (orc_gauss_legendre01(qs, gx, gw)) return -1;
     orc_phys ph = {eps, kappa};
-    orc_pair(V, T, i, j, &ph, gx, gw, qs, I);
+    orc_rule qr = {nq, qe1, qe2, qw};
+    orc_pair(V, T, i, j, &ph, gx, gw, qs, &qr, I);
     return 0;
 }
 
 /* exported: the dense 2N x 2N matrix of def:linsys, row-major, unknowns [phi ; dphi/dn] */
 int orc_assemble(const double* V, const int32_t* T, int nt, double eps, double kappa, int qs,
-                 double* A)
+                 int nq, const double* qe1, const double* qe2, const double* qw, double* A)
 {
     double gx[64], gw[64];
     if (orc_gauss_legendre01(qs, gx, gw)) return -1;
     orc_phys ph = {eps, kappa};
+    orc_rule qr = {nq, qe1, qe2, qw};
     long n2 = 2L * nt;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int i = 0; i < nt; ++i) {
@@ -437,7 +477,7 @@ int orc_assemble(const double* V, const int32_t* T, int nt, double eps, double k
         }
         for (int j = 0; j < nt; ++j) {
             double I[4];
-            orc_pair(V, T, i, j, &ph, gx, gw, qs, I);
+            orc_pair(V, T, i, j, &ph, gx, gw, qs, &qr, I);
             A[(long)i * n2 + j] = -I[1];
             A[(long)i * n2 + nt + j] = -I[0];
             A[(long)(nt + i) * n2 + j] = -I[3];
@@ -452,11 +492,13 @@ int orc_assemble(const double* V, const int32_t* T, int nt, double eps, double k
 /* exported: rows of A x for selected elements. For element e = elems[k] it writes
  * y[2k] = (A x)_e (the phi row) and y[2k+1] = (A x)_{N+e} (the dphi/dn row). */
 int orc_rows_matvec(const double* V, const int32_t* T, int nt, double eps, double kappa, int qs,
-                    int nrows, const int32_t* elems, const double* x, double* y)
+                    int nq, const double* qe1, const double* qe2, const double* qw, int nrows,
+                    const int32_t* elems, const double* x, double* y)
 {
     double gx[64], gw[64];
     if (orc_gauss_legendre01(qs, gx, gw)) return -1;
     orc_phys ph = {eps, kappa};
+    orc_rule qr = {nq, qe1, qe2, qw};
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < nrows; ++k) {
         int i = elems[k];
@@ -470,7 +512,7 @@ int orc_rows_matvec(const double* V, const int32_t* T, int nt, double eps, doubl
         double y2 = 0.5 * (1.0 + 1.0 / eps) * Ai * x[nt + i];
         for (int j = 0; j < nt; ++j) {
             double I[4];
-            orc_pair(V, T, i, j, &ph, gx, gw, qs, I);
+            orc_pair(V, T, i, j, &ph, gx, gw, qs, &qr, I);
             y1 -= I[0] * x[nt + j] + I[1] * x[j];
             y2 -= I[2] * x[nt + j] + I[3] * x[j];
         }
@@ -481,8 +523,26 @@ int orc_rows_matvec(const double* V, const int32_t* T, int nt, double eps, doubl
 }
 
 /* exported: right-hand side b = [b1; b2] (source_terms) by the centroid rule */
+/* S1 and S2 of source_terms at x (normal n), before the 1/eps1 factor */
+static void orc_sources(const double* x, const double* n, const double* qpos, const double* q, int nc,
+                        double* s1, double* s2)
+{
+    *s1 = 0.0;
+    *s2 = 0.0;
+    for (int k = 0; k < nc; ++k) {
+        double d[3] = {x[0] - qpos[3 * k], x[1] - qpos[3 * k + 1], x[2] - qpos[3 * k + 2]};
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double r = sqrt(r2);
+        double nd = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];
+        *s1 += q[k] / (4.0 * ORC_PI * r);
+        /* d G0/d nu_x = g0'(r) (n.d)/r = -(n.d)/(4 pi r^3) */
+        *s2 += q[k] * (-nd / (4.0 * ORC_PI * r2 * r));
+    }
+}
+
 void orc_rhs(const double* V, const int32_t* T, int nt, const double* qpos, const double* q,
-             int nc, double eps1, double* b)
+             int nc, double eps1, int nq, const double* qe1, const double* qe2, const double* qw,
+             double* b)
 {
     for (int i = 0; i < nt; ++i) {
         double c[3], n[3], Ai;
@@ -490,17 +550,21 @@ void orc_rhs(const double* V, const int32_t* T, int nt, const double* qpos, cons
         orc_tri(V, T, i, u, v, w);
         orc_geom(u, v, w, c, &Ai, n);
         double s1 = 0.0, s2 = 0.0;
-        for (int k = 0; k < nc; ++k) {
-            double d[3] = {c[0] - qpos[3 * k], c[1] - qpos[3 * k + 1], c[2] - qpos[3 * k + 2]};
-            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            double r = sqrt(r2);
-            double nd = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];
-            s1 += q[k] / (4.0 * ORC_PI * r);
-            /* d G0/d nu_x = g0'(r) (n.d)/r = -(n.d)/(4 pi r^3) */
-            s2 += q[k] * (-nd / (4.0 * ORC_PI * r2 * r));
+        if (nq == 1) {
+            orc_sources(c, n, qpos, q, nc, &s1, &s2);
+            s1 *= Ai;
+            s2 *= Ai;
+        } else {
+            for (int a = 0; a < nq; ++a) {
+                double x[3], t1, t2;
+                orc_rule_point(u, v, w, qe1[a], qe2[a], x);
+                orc_sources(x, n, qpos, q, nc, &t1, &t2);
+                s1 += 2.0 * Ai * qw[a] * t1;
+                s2 += 2.0 * Ai * qw[a] * t2;
+            }
         }
-        b[i] = Ai * s1 / eps1;
-        b[nt + i] = Ai * s2 / eps1;
+        b[i] = s1 / eps1;
+        b[nt + i] = s2 / eps1;
     }
 }
 
@@ -508,7 +572,8 @@ void orc_rhs(const double* V, const int32_t* T, int nt, const double* qpos, cons
  * E = 1/2 sum_n q_n sum_i A_i [K1(x_n, c_i) dphi_i + K2(x_n, c_i) phi_i], converted from
  * e_c/(4 pi Angstrom) by the factor 4 pi 332.0716 (Section 3). */
 double orc_energy(const double* V, const int32_t* T, int nt, const double* qpos, const double* q,
-                  int nc, double eps, double kappa, const double* x)
+                  int nc, double eps, double kappa, int nq, const double* qe1, const double* qe2,
+                  const double* qw, const double* x)
 {
     orc_phys ph = {eps, kappa};
     double zero[3] = {0.0, 0.0, 0.0};
@@ -520,8 +585,17 @@ double orc_energy(const double* V, const int32_t* T, int nt, const double* qpos,
             double u[3], v[3], w[3];
             orc_tri(V, T, i, u, v, w);
             orc_geom(u, v, w, c, &Ai, n);
-            orc_kernels(qpos + 3 * k, zero, c, n, &ph, K);
-            sk += Ai * (K[0] * x[nt + i] + K[1] * x[i]);
+            if (nq == 1) {
+                orc_kernels(qpos + 3 * k, zero, c, n, &ph, K);
+                sk += Ai * (K[0] * x[nt + i] + K[1] * x[i]);
+            } else {
+                for (int a = 0; a < nq; ++a) {
+                    double y[3];
+                    orc_rule_point(u, v, w, qe1[a], qe2[a], y);
+                    orc_kernels(qpos + 3 * k, zero, y, n, &ph, K);
+                    sk += 2.0 * Ai * qw[a] * (K[0] * x[nt + i] + K[1] * x[i]);
+                }
+            }
         }
         E += q[k] * sk;
     }
