@@ -70,6 +70,11 @@ typedef struct pb_params {
                         takes the clusters of a designated level as blocks; here the leaves, each
                         cut into nearly equal Morton-consecutive parts of at most pc_block
                         elements, so smaller values stand for designated levels below the leaves */
+    int qr;          /* order of the regular quadrature rule (Section 3.1, Table 2) for non-touching
+                        pairs, the right-hand side and the energy: 0 or 1 = the centroid (one
+                        point), 2..4 = q^2 points per element (collapsed Gauss product rule, exact
+                        to total degree 2q - 1). Orders above 1 support single right-hand sides
+                        (not pb_solve_states mode 2 or pb_batch_solve_states) */
 } pb_params;
 
 /* Float-float ("double-single", ~1e-13 relative) evaluates every step of the singular
@@ -355,9 +360,9 @@ int pb_learned_guess(pb_ctx* ctx, pb_mlp* net, double* x);
 /* Solvation energy for callers that cannot allocate device memory.
  *
  * The paper has no counterpart to this call; it exists for callers that must not call
- * cudaMalloc -- for example code that runs while a stream is being captured into a CUDA
- * graph, where an allocation would break the capture, or a host that gives the library a
- * fixed memory budget and forbids allocations after start-up. It computes the same energy
+ * cudaMalloc -- a host that gives the library a fixed device-memory budget and forbids
+ * allocations after start-up, or code that runs where an allocation is not allowed (an
+ * allocation may synchronise the device, or fail when memory is exhausted). It computes the same energy
  * as pb_solvation_energy, without a context, from caller-owned buffers, and allocates
  * nothing: its only scratch (one partial sum per block of 256 triangles) lives in a fixed
  * 64 KiB device array that every GPU loading this library holds until the process exits.
@@ -371,10 +376,11 @@ int pb_learned_guess(pb_ctx* ctx, pb_mlp* net, double* x);
  * PB_ERR_CUDA if the launch fails.
  *
  * The first call on a device looks up the scratch array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call before any stream
- * capture. Every call reuses the same array and leaves its partial sums there; calls that
- * may overlap on the GPU (on different streams, or from several threads) race on it and
- * must be serialised by the caller. */
+ * cudaGetSymbolAddress (with that device current) and keeps it for the life of the process;
+ * make that first call before any stream capture. Calls after cudaDeviceReset on that device
+ * are not supported (the kept address belongs to the old context). Every call reuses the same
+ * array and leaves its partial sums there; calls that may overlap on the GPU (on different
+ * streams, or from several threads) race on it and must be serialised by the caller. */
 int pb_solvation_energy_noalloc(const double* verts, const int32_t* tris, int nt, const double* qpos,
                                 const double* q, int nc, double eps_in, double eps_out, double kappa,
                                 int precision, const double* x, double* E, void* stream, char* errbuf,

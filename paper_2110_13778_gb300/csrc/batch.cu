@@ -118,6 +118,7 @@ extern "C" int pb_batch_solve_states(pb_ctx* const* ctxs, int nmol, const double
         if (c->dead) return PB_ERR_CUDA;
         if (!c->built) return pb_fail(c, PB_ERR_STATE, "batch_solve_states before build_tree");
         if (c->timing) return pb_fail(c, PB_ERR_STATE, "batch_solve_states with per-phase timing enabled");
+        if (c->q2 > 1) return pb_fail(c, PB_ERR_ARG, "batch_solve_states needs the one-point regular rule");
         for (long long i = 0; i < (long long)nrhs * c->nc; ++i)
             if (!isfinite(q[k][i])) return pb_fail(c, PB_ERR_MESH, "charge state value %lld not finite", i);
         for (int j = 0; j < k; ++j)

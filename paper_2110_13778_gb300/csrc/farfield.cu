@@ -1197,13 +1197,23 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream
         PB_CUDA(c, cudaMemsetAsync(ys, 0, sizeof(double) * 2 * c->nt * nr, st));
         return PB_OK;
     }
+    // a regular rule of order > 1 (one vector at a time): moments and evaluation on its points
+    const bool pts = c->q2 > 1;
+    const int np = c->nt * c->q2;
+    const long long pvstr = pts ? 2LL * np : vstr;
     pb_tic_on(c, PB_T_UP, st);
     {
         PbLevel& lv = c->lev[L];
         const size_t psm = p2m_smem<R>(lv.p);
+        if (pts) {
+            int rc1 = pb_to_points(c, xs, c->xq, st);
+            if (rc1) return rc1;
+        }
         PB_CUDA(c, cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-        k_p2m<R><<<dim3(lv.ncl, nr), P2M_T, psm, st>>>(c->nt, lv.p, lv.begin, lv.xc, c->e64p, c->e64n, xs, eps,
-                                                        (R*)lv.sig0, (R*)lv.sigk, vstr, sstr(lv));
+        k_p2m<R><<<dim3(lv.ncl, nr), P2M_T, psm, st>>>(np, lv.p, pts ? c->begin_q : lv.begin, lv.xc,
+                                                        pts ? c->pts_p : c->e64p, pts ? c->pts_n : c->e64n,
+                                                        pts ? c->xq : xs, eps, (R*)lv.sig0, (R*)lv.sigk, pvstr,
+                                                        sstr(lv));
         PB_LAUNCH(c);
     }
     for (int l = L - 1; l >= lmin; --l) {
@@ -1244,9 +1254,14 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream
         PbLevel& lv = c->lev[L];
         const size_t lsm = l2p_smem<R>(lv.p);
         PB_CUDA(c, cudaFuncSetAttribute(k_l2p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
-        k_l2p<R><<<dim3(lv.ncl, nr), FAR_T, lsm, st>>>(c->nt, lv.p, eps, lv.begin, lv.xc, c->e64p, c->e64n,
-                                                        (R*)lv.lam0, (R*)lv.lamk, ys, sstr(lv), vstr);
+        k_l2p<R><<<dim3(lv.ncl, nr), FAR_T, lsm, st>>>(np, lv.p, eps, pts ? c->begin_q : lv.begin, lv.xc,
+                                                        pts ? c->pts_p : c->e64p, pts ? c->pts_n : c->e64n,
+                                                        (R*)lv.lam0, (R*)lv.lamk, pts ? c->yq : ys, sstr(lv), pvstr);
         PB_LAUNCH(c);
+        if (pts) {
+            int rc1 = pb_from_points(c, c->yq, ys, 0, st);
+            if (rc1) return rc1;
+        }
     }
     pb_toc_on(c, PB_T_DOWN, st);
     return PB_OK;
@@ -1447,13 +1462,24 @@ static int tc_energy(pb_ctx* c, const double* xs, double theta, double* E)
     const long long vstr = 2LL * c->nt;
     auto sstr = [](const PbLevel& lv) { return (long long)lv.ncl * pb_nterms(lv.p); };
     pb_tic(c, PB_T_ENERGY);
+    // a regular rule of order > 1: moments and leaf sums on its points
+    const bool pts = c->q2 > 1;
+    const int np = c->nt * c->q2;
+    if (pts) {
+        int rc1 = pb_to_points(c, xs, c->xq, c->st);
+        if (rc1) return rc1;
+        xs = c->xq;
+    }
+    const long long pvstr = 2LL * np;
+    (void)vstr;
     // moments of the solution on every level, up to the root (P2M, MtM)
     {
         PbLevel& lv = c->lev[L];
         const size_t psm = p2m_smem<R>(lv.p);
         PB_CUDA(c, cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-        k_p2m<R><<<dim3(lv.ncl, 1), P2M_T, psm, c->st>>>(c->nt, lv.p, lv.begin, lv.xc, c->e64p, c->e64n, xs, eps,
-                                                          (R*)lv.sig0, (R*)lv.sigk, vstr, sstr(lv));
+        k_p2m<R><<<dim3(lv.ncl, 1), P2M_T, psm, c->st>>>(np, lv.p, pts ? c->begin_q : lv.begin, lv.xc,
+                                                          pts ? c->pts_p : c->e64p, pts ? c->pts_n : c->e64n, xs, eps,
+                                                          (R*)lv.sig0, (R*)lv.sigk, pvstr, sstr(lv));
         PB_LAUNCH(c);
     }
     for (int l = L - 1; l >= 0; --l) {
@@ -1477,7 +1503,7 @@ static int tc_energy(pb_ctx* c, const double* xs, double theta, double* E)
         tl.p[l] = c->lev[l].p;
         pmax = std::max(pmax, c->lev[l].p);
     }
-    tl.leaf_begin = c->lev[L].begin;
+    tl.leaf_begin = pts ? c->begin_q : c->lev[L].begin;
     tl.L = L;
     tl.n1 = L > 0 ? c->lev[1].ncl : 1;
     const long long nw = (long long)c->nc * tl.n1;
@@ -1491,7 +1517,8 @@ static int tc_energy(pb_ctx* c, const double* xs, double theta, double* E)
     PB_CUDA(c, cudaFuncSetAttribute(k_tc_energy<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (nw > 0) {
         k_tc_energy<R><<<(unsigned)((nw + TC_W - 1) / TC_W), 32 * TC_W, sm, c->st>>>(
-            c->nc, tl, c->qpos, c->q, c->e64p, c->e64n, xs, c->nt, eps, c->prm.kappa, theta * theta, tmax, c->tc_part);
+            c->nc, tl, c->qpos, c->q, pts ? c->pts_p : c->e64p, pts ? c->pts_n : c->e64n, xs, np, eps, c->prm.kappa,
+            theta * theta, tmax, c->tc_part);
         PB_LAUNCH(c);
     }
     k_tc_sum<<<1, 256, 0, c->st>>>(nw, c->tc_part, c->tc_part + nw, 0.5 * 4.0 * PB_PI * 332.0716);

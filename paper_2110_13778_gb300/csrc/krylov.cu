@@ -73,15 +73,21 @@ __global__ void k_rhs(int nt, int nc, const double4_32a* __restrict__ ep, const 
 
 int pb_rhs_sorted(pb_ctx* c, double* bs)
 {
-    int nt = c->nt;
+    // with a regular rule of order > 1 the kernel runs on the points, summed per element after
+    const int nt = c->nt * c->q2;
+    const double4_32a* ep = c->q2 > 1 ? c->pts_p : c->e64p;
+    const double4_32a* en = c->q2 > 1 ? c->pts_n : c->e64n;
+    double* out = c->q2 > 1 ? c->yq : bs;
     pb_tic(c, PB_T_RHS);
     if (c->prm.precision == PB_MIXED)
-        k_rhs<float><<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q, c->prm.eps_in,
-                                                           bs);
+        k_rhs<float><<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, c->prm.eps_in, out);
     else
-        k_rhs<double><<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q,
-                                                            c->prm.eps_in, bs);
+        k_rhs<double><<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, c->prm.eps_in, out);
     PB_LAUNCH(c);
+    if (c->q2 > 1) {
+        int rc = pb_from_points(c, c->yq, bs, 0, c->st);
+        if (rc) return rc;
+    }
     pb_toc(c, PB_T_RHS);
     return PB_OK;
 }
@@ -326,19 +332,25 @@ __global__ void k_sum(int n, const double* __restrict__ part, double* __restrict
 
 int pb_energy_sorted(pb_ctx* c, const double* xs, double* E)
 {
-    int nt = c->nt, nb = (nt + KB - 1) / KB;
+    // with a regular rule of order > 1 the kernel runs on the points (densities copied to them)
+    int nt = c->nt * c->q2, nb = (nt + KB - 1) / KB;
     if (!c->scratch) {
         c->scratch = (double*)pb_alloc(c, sizeof(double) * ((size_t)nb + 8));
         if (!c->scratch) return pb_fail(c, PB_ERR_NOMEM, "energy: out of memory");
     }
     double eps = c->prm.eps_out / c->prm.eps_in;
+    const double4_32a* ep = c->q2 > 1 ? c->pts_p : c->e64p;
+    const double4_32a* en = c->q2 > 1 ? c->pts_n : c->e64n;
+    if (c->q2 > 1) {
+        int rc = pb_to_points(c, xs, c->xq, c->st);
+        if (rc) return rc;
+        xs = c->xq;
+    }
     pb_tic(c, PB_T_ENERGY);
     if (c->prm.precision == PB_MIXED)
-        k_energy<float><<<nb, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q, eps, c->prm.kappa, xs,
-                                              c->scratch);
+        k_energy<float><<<nb, KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, eps, c->prm.kappa, xs, c->scratch);
     else
-        k_energy<double><<<nb, KB, 0, c->st>>>(nt, c->nc, c->e64p, c->e64n, c->qpos, c->q, eps, c->prm.kappa, xs,
-                                               c->scratch);
+        k_energy<double><<<nb, KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, eps, c->prm.kappa, xs, c->scratch);
     PB_LAUNCH(c);
     k_sum<<<1, KB, 0, c->st>>>(nb, c->scratch, c->scratch + nb, 0.5 * 4.0 * PB_PI * 332.0716);
     PB_LAUNCH(c);

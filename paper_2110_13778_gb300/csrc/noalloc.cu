@@ -1,8 +1,8 @@
 // Solvation energy without any device allocation, for callers that cannot allocate.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA stream is being captured
-// into a graph (allocation calls are not capturable and break the capture), or hosts that
-// give this library a fixed memory budget and forbid allocations after start-up. For them
+// Some callers cannot call cudaMalloc: hosts that give this library a fixed device-memory
+// budget and forbid allocations after start-up, or code that runs where an allocation is not
+// allowed (an allocation may synchronise the device, or fail when memory is exhausted). For them
 // pb_solvation_energy_noalloc evaluates the same energy as pb_solvation_energy from
 // caller-owned device buffers, and keeps its only scratch -- one partial sum per thread
 // block -- in a fixed file-scope device array instead of a context buffer.
@@ -152,6 +152,9 @@ extern "C" int pb_solvation_energy_noalloc(const double* verts, const int32_t* t
     }
     cudaStream_t st = (cudaStream_t)stream;
     double eps = eps_out / eps_in;
+    // clear a launch error left by earlier, unrelated work, so that the check below reports
+    // this call's launches only (an error that has made the context unusable stays and shows)
+    cudaGetLastError();
     if (precision == PB_MIXED)
         k_energy_noalloc<float><<<nb, NA_THREADS, 0, st>>>(nt, verts, tris, nc, qpos, q, eps, kappa, x, part);
     else

@@ -63,6 +63,10 @@ static void pb_free_build(pb_ctx* c)
     c->tc_nw = 0;
     c->bE = nullptr;
     c->bE_n = 0;
+    c->q2 = 1;
+    c->pts_p = c->pts_n = nullptr;
+    c->begin_q = nullptr;
+    c->xq = c->yq = nullptr;
     c->dgVcur = nullptr;
     c->dgctl = nullptr;
     c->dg_nr = c->dg_nctl = 0;
@@ -98,6 +102,7 @@ extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
     if (prm->singular < PB_SINGULAR_AUTO || prm->singular > PB_SINGULAR_FF) return PB_ERR_ARG;
     if (prm->precond < PB_PRECOND_NONE || prm->precond > PB_PRECOND_BLOCK) return PB_ERR_ARG;
     if (prm->pc_block != 0 && (prm->pc_block < 8 || prm->pc_block > 96)) return PB_ERR_ARG;
+    if (prm->qr < 0 || prm->qr > 4) return PB_ERR_ARG;
     pb_ctx* c = new pb_ctx();
     c->prm = *prm;
     c->st = (cudaStream_t)stream;
@@ -242,6 +247,7 @@ extern "C" int pb_build_tree(pb_ctx* c)
     if (!c->dev_err) return pb_fail(c, PB_ERR_NOMEM, "build_tree: out of memory");
     pb_tic(c, PB_T_TREE);
     if ((rc = pb_geometry_and_tree(c))) return rc;
+    if ((rc = pb_regular_setup(c))) return rc;
     pb_toc(c, PB_T_TREE);
     // Everything that reads tree data back to the host is planned first; then the singular
     // integrals run on the first stream while the host prepares the far-field setup. The
@@ -253,6 +259,7 @@ extern "C" int pb_build_tree(pb_ctx* c)
     PB_CUDA(c, cudaEventRecord(c->ev_tree, c->st));
     pb_tic(c, PB_T_SINGULAR);
     if ((rc = pb_touching_and_singular(c))) return rc;
+    if ((rc = pb_regular_corrections(c))) return rc;
     pb_toc(c, PB_T_SINGULAR);
     PB_CUDA(c, cudaEventRecord(c->ev_sing, c->st));
     if ((rc = pb_far_setup(c))) return rc;  // times its table kernels as PB_T_FARSETUP
@@ -345,6 +352,11 @@ void pb_drop_graphs(pb_ctx* c)
 static int matvec_parts(pb_ctx* c, const double* xs, double* ys, int nr, int which)
 {
     int rc;
+    if (c->q2 > 1 && nr > 1) {  // the regular rule of order > 1 works one vector at a time
+        for (int r = 0; r < nr; ++r)
+            if ((rc = matvec_parts(c, xs + 2LL * c->nt * r, ys + 2LL * c->nt * r, 1, which))) return rc;
+        return PB_OK;
+    }
     const bool far = which != 1;
     // every buffer the product touches exists before the fork (and before any capture)
     if ((rc = pb_matvec_reserve(c, nr))) return rc;
@@ -360,7 +372,9 @@ static int matvec_parts(pb_ctx* c, const double* xs, double* ys, int nr, int whi
         return pb_corr_apply(c, nullptr, ys, nr, c->yfar);
     }
     pb_tic(c, PB_T_NEAR);
-    if ((rc = nr == 1 ? pb_near_apply(c, xs, ys) : pb_near_apply_multi(c, xs, ys, nr))) return rc;
+    if ((rc = c->q2 > 1 ? pb_near_q_apply(c, xs, ys)
+                        : nr == 1 ? pb_near_apply(c, xs, ys) : pb_near_apply_multi(c, xs, ys, nr)))
+        return rc;
     pb_toc(c, PB_T_NEAR);
     if (far) PB_CUDA(c, cudaStreamWaitEvent(c->st, c->ev_join, 0));
     pb_tic(c, PB_T_CORR);
@@ -481,6 +495,8 @@ extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, 
         return pb_fail(c, PB_ERR_ARG, "solve_states: bad arguments");
     for (long long k = 0; k < (long long)nrhs * c->nc; ++k)
         if (!isfinite(q[k])) return pb_fail(c, PB_ERR_MESH, "charge state value %lld not finite", k);
+    if (warm == 2 && c->q2 > 1)
+        return pb_fail(c, PB_ERR_ARG, "solve_states: batched states need the one-point regular rule");
     const size_t n2 = 2 * (size_t)c->nt;
     int worst = PB_OK;
     // batched: state 0 alone from zero, then the others in lockstep from its solution

@@ -182,6 +182,14 @@ struct pb_ctx {
     long long build_gen = 0;          // incremented by every pb_build_tree / pb_mesh_upload
     double* tc_part = nullptr;        // treecode energy: one partial per (charge, level-1 cluster)
     long long tc_nw = 0;
+    // regular rule of order q > 1: q2 = q^2 points per element, their records (tree order,
+    // element-major), the leaf ranges in points and point work vectors (2 x N q2 each)
+    int q2 = 1;
+    double4_32a* pts_p = nullptr;
+    double4_32a* pts_n = nullptr;
+    int* begin_q = nullptr;
+    double* xq = nullptr;
+    double* yq = nullptr;
     double* bE = nullptr;         // energies of the states of a batched multi-molecule solve (device)
     int bE_n = 0;
     double* hscal = nullptr;      // pinned host scalars
@@ -274,6 +282,12 @@ int pb_dg_upload(pb_ctx* c, int nctl);
 int pb_dg_download(pb_ctx* c, int nctl);
 void pb_dg_results(pb_ctx* c, int ictl, int nr, const long long cnt[3], pb_solve_info* infos, int* worst);
 int pb_energy_reserve(pb_ctx* c);
+// regular rule of order > 1 (regular.cu)
+int pb_regular_setup(pb_ctx* c);        // points (after the tree)
+int pb_regular_corrections(pb_ctx* c);  // corrections: exact - order-q rule (after the singular pass)
+int pb_near_q_apply(pb_ctx* c, const double* xs, double* ys);
+int pb_to_points(pb_ctx* c, const double* xs, double* xq, cudaStream_t st);
+int pb_from_points(pb_ctx* c, const double* yq, double* ys, int add, cudaStream_t st);
 int pb_energy_states_queue(pb_ctx* c, const double* Q, const double* X, int nr, double* Edev);  // nr <= 16
 int pb_rhs_sorted(pb_ctx* c, double* bs);                          // krylov.cu
 int pb_energy_sorted(pb_ctx* c, const double* xs, double* E);      // krylov.cu

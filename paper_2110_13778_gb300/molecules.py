@@ -11,7 +11,9 @@ side through the same arrays.
   on a grid of spacing h, triangulated by marching tetrahedra (six tetrahedra per grid cube
   along the main diagonal, so neighbouring cubes agree on shared faces): a closed, conforming
   (welded), outward-oriented surface.
-* ``molecule(n, seed, h)`` -- both together as an ``inputs.Mesh``.
+* ``clean_mesh(V, T, lmin)`` -- collapses edges shorter than lmin where the surface stays a
+  closed manifold (the slivers that linear cuts next to grid points leave).
+* ``molecule(n, seed, h, clean)`` -- both together as an ``inputs.Mesh``.
 """
 from __future__ import annotations
 
@@ -187,7 +189,103 @@ def _gkey(ijk):
     return (ijk[:, 0].astype(np.int64) * 1024 + ijk[:, 1]) * 1024 + ijk[:, 2]
 
 
-def molecule(n_atoms: int, seed: int, h: float = 0.5):
+def clean_mesh(V, T, lmin):
+    """Collapse every edge shorter than lmin, shortest first, into its midpoint, where the
+    collapse keeps the surface a closed 2-manifold (link condition: the two end vertices share
+    exactly the two opposite vertices of the edge's triangles) and turns no neighbouring
+    triangle over or to zero area; the edge's two triangles disappear. Linear cuts next to grid
+    points leave triangles with areas down to 1e-11 of the mean; these are removed (the
+    standard mesh-quality step of isosurface extraction). Returns (V, T, collapses)."""
+    nv = len(V)
+    E = np.concatenate([T[:, [0, 1]], T[:, [1, 2]], T[:, [2, 0]]]).astype(np.int64)
+    E.sort(axis=1)
+    L = np.linalg.norm(V[E[:, 0]] - V[E[:, 1]], axis=1)
+    sel = np.flatnonzero(L < lmin)
+    if sel.size == 0:
+        return V, T, 0
+    key, first = np.unique(E[sel, 0] * nv + E[sel, 1], return_index=True)
+    sel = sel[first]
+    sel = sel[np.argsort(L[sel], kind="stable")]
+    cand = E[sel].tolist()
+    order = np.argsort(T.reshape(-1), kind="stable")
+    tri_of = (order // 3).tolist()
+    ptr = np.searchsorted(T.reshape(-1)[order], np.arange(nv + 1)).tolist()
+    Vl = V.tolist()
+    Tl = T.tolist()
+    alive = [True] * len(Tl)
+    inc = {}
+    dead = set()
+    lmin2 = lmin * lmin
+
+    def tris_of(v):
+        s_ = inc.get(v)
+        if s_ is None:
+            s_ = set(tri_of[ptr[v]:ptr[v + 1]])
+            inc[v] = s_
+        return s_
+
+    def normal(a, b, c):
+        ux, uy, uz = b[0] - a[0], b[1] - a[1], b[2] - a[2]
+        vx, vy, vz = c[0] - a[0], c[1] - a[1], c[2] - a[2]
+        return (uy * vz - uz * vy, uz * vx - ux * vz, ux * vy - uy * vx)
+
+    ncol = 0
+    for u, v in cand:
+        if u in dead or v in dead:
+            continue
+        pu, pv = Vl[u], Vl[v]
+        if (pu[0] - pv[0]) ** 2 + (pu[1] - pv[1]) ** 2 + (pu[2] - pv[2]) ** 2 >= lmin2:
+            continue  # an end moved in an earlier collapse
+        tu, tv = tris_of(u), tris_of(v)
+        shared = tu & tv
+        if len(shared) != 2:
+            continue
+        opp = set()
+        for t in shared:
+            opp.update(Tl[t])
+        opp.discard(u)
+        opp.discard(v)
+        nu, nvv = set(), set()
+        for t in tu:
+            nu.update(Tl[t])
+        for t in tv:
+            nvv.update(Tl[t])
+        nu.discard(u)
+        nvv.discard(v)
+        if len(opp) != 2 or (nu & nvv) != opp:
+            continue
+        m = [0.5 * (pu[0] + pv[0]), 0.5 * (pu[1] + pv[1]), 0.5 * (pu[2] + pv[2])]
+        ok = True
+        for t in (tu | tv) - shared:
+            n0 = normal(*[Vl[w] for w in Tl[t]])
+            n1 = normal(*[m if w == u or w == v else Vl[w] for w in Tl[t]])
+            if n0[0] * n1[0] + n0[1] * n1[1] + n0[2] * n1[2] <= 0.0 or n1[0] ** 2 + n1[1] ** 2 + n1[2] ** 2 <= 1e-24:
+                ok = False
+                break
+        if not ok:
+            continue
+        Vl[u] = m
+        for t in tv - shared:
+            Tl[t] = [u if w == v else w for w in Tl[t]]
+        for t in shared:
+            alive[t] = False
+            for w in Tl[t]:
+                if w != u and w != v:
+                    tris_of(w).discard(t)
+        inc[u] = (tu | tv) - shared
+        dead.add(v)
+        inc.pop(v, None)
+        ncol += 1
+    Tn = np.array([t for t, a in zip(Tl, alive) if a], dtype=np.int64)
+    used, remap = np.unique(Tn.reshape(-1), return_inverse=True)
+    return np.array(Vl)[used], remap.reshape(-1, 3).astype(np.int32), ncol
+
+
+def molecule(n_atoms: int, seed: int, h: float = 0.5, clean: bool = False):
+    """The molecule and its surface; clean=True collapses the edges shorter than h / 10
+    (clean_mesh)."""
     pos, rad, q = saw_atoms(n_atoms, seed)
     V, T = gaussian_surface(pos, rad, h)
+    if clean:
+        V, T, _ = clean_mesh(V, T, 0.1 * h)
     return Mesh(V, T, pos, q), rad

@@ -48,15 +48,16 @@ def training_rows(mesh, prm, tol=1e-6, max_iter=300, restart=50):
         pb.pb_destroy(ctx)
 
 
-def make_dataset(atom_counts, seed=0, grid=1.0, prm=None):
-    """Features and targets of freshly generated molecules (atom counts as given, seeded),
-    concatenated and shuffled once by a seeded row permutation."""
+def make_dataset(atom_counts, seed=0, grid=1.0, prm=None, clean=False):
+    """Features and targets of freshly generated molecules (atom counts as given, seeded;
+    clean: collapse the short edges of their surfaces), concatenated and shuffled once by a
+    seeded row permutation."""
     import torch
 
     prm = prm or solve_params()
     Fs, Ts = [], []
     for i, n in enumerate(atom_counts):
-        mesh, _ = molecules.molecule(int(n), seed + 1009 * i, grid)
+        mesh, _ = molecules.molecule(int(n), seed + 1009 * i, grid, clean=clean)
         F, T, _ = training_rows(mesh, prm)
         Fs.append(F)
         Ts.append(T)

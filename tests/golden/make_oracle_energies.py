@@ -60,7 +60,7 @@ def run(name):
     else:
         x, _, res, nmv = dense.solve_matrix_free(m, ph)
         rec["energy_kcal"] = dense.energy(m, ph, x)
-        rec["method"] = "matrix-free GMRES, no preconditioner"
+        rec["method"] = "matrix-free GMRES right-scaled by the diagonal mass terms"
         rec["residual"], rec["products"] = res, nmv
         rec["seconds"] = time.time() - t0
     return rec

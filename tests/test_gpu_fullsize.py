@@ -90,3 +90,47 @@ def test_molecule_2000_atoms_sampled_rows():
         assert _sampled_rows(m, ctx, 128, 63) < 1e-4
     finally:
         pb.pb_destroy(ctx)
+
+
+@pytest.fixture(scope="module")
+def molecule20k():
+    # the default benchmark workload: a 20000-atom walk on a 0.9 A grid, short edges collapsed
+    # (~1.8M triangles)
+    return molecules.molecule(20000, 23000, 0.9, clean=True)[0]
+
+
+def test_molecule_20000_atoms_sampled_rows(molecule20k):
+    m = molecule20k
+    assert m.nt > 1_500_000
+    ctx = _bench_ctx(m, pb.PB_MIXED)
+    try:
+        assert _sampled_rows(m, ctx, 48, 64) < 1e-4
+    finally:
+        pb.pb_destroy(ctx)
+
+
+def test_molecule_20000_atoms_solve_and_treecode(molecule20k):
+    # the benchmark's solve converges on the full molecule; its solution satisfies sampled rows
+    # of the dense Galerkin system to the FMM's accuracy; the treecode energy matches the
+    # direct sum
+    m = molecule20k
+    ctx = _bench_ctx(m, pb.PB_MIXED)
+    try:
+        x = torch.zeros(2 * m.nt, device="cuda", dtype=torch.float64)
+        info = pb.pb_gmres_solve(ctx, x, tol=1e-6, max_iter=500, restart=50)
+        assert info.status == pb.PB_OK
+        xs = x.cpu().numpy()
+        rows = np.sort(np.random.default_rng(65).choice(m.nt, 32, replace=False))
+        y1, y2 = dense.rows_matvec(m.verts, m.tris, PH, rows, xs)
+        # each right-hand-side row depends on its own element only: the oracle's rows from the
+        # sub-mesh of the sampled elements
+        sub = inputs.Mesh(m.verts, m.tris[rows], m.qpos, m.q)
+        bs = dense.rhs(sub, PH)
+        r = np.concatenate([bs[:len(rows)] - y1, bs[len(rows):] - y2])
+        bb = bs
+        assert np.linalg.norm(r) / np.linalg.norm(bb) < 1e-3
+        E = pb.pb_solvation_energy(ctx, x)
+        Et = pb.pb_solvation_energy_treecode(ctx, x, 0.5)
+        assert abs(Et - E) < 1e-5 * abs(E)
+    finally:
+        pb.pb_destroy(ctx)

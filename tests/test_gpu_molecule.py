@@ -205,8 +205,9 @@ def test_batched_charge_states_match_sequential(mol, prec):
             assert all(i.status == pb.PB_OK for i in infos)
             assert all(i.rel_residual <= 1.5e-6 for i in infos)
             res[mode] = (E, X.cpu().numpy(), infos)
-            # the lockstep steps of the batched mode replay captured CUDA graphs
-            assert (pb.pb_get_graph_launches(ctx) > 0) == (mode == 2)
+            # every solve is one CUDA-graph launch: one per state sequentially (mode 1), state 0
+            # and then one launch for the other five (mode 2)
+            assert pb.pb_get_graph_launches(ctx) == (len(states) if mode == 1 else 2)
         finally:
             pb.pb_destroy(ctx)
     Es, Xs, _ = res[1]

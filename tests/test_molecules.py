@@ -41,3 +41,30 @@ def test_surface_closed_manifold_outward(n, seed, h):
                + np.einsum("ij,ij->i", R[:, 0], R[:, 2]) * r[:, 1] + np.einsum("ij,ij->i", R[:, 1], R[:, 2]) * r[:, 0])
         wind = (2 * np.arctan2(num, den)).sum() / (4 * np.pi)
         assert abs(wind - 1.0) < 1e-6
+
+
+def test_clean_mesh_keeps_a_closed_oriented_surface():
+    from oracle import dense
+
+    raw = molecules.molecule(60, 3060, 0.9)[0]
+    m = molecules.molecule(60, 3060, 0.9, clean=True)[0]
+    assert m.nt < raw.nt
+    T = m.tris.astype(np.int64)
+    nv = len(m.verts)
+    E = np.concatenate([T[:, [0, 1]], T[:, [1, 2]], T[:, [2, 0]]])
+    d = E[:, 0] * nv + E[:, 1]
+    r = E[:, 1] * nv + E[:, 0]
+    # closed and consistently oriented: every directed edge once, its reverse once
+    assert len(np.unique(d)) == len(d) and np.array_equal(np.sort(d), np.sort(r))
+    # Euler characteristic unchanged (edge collapses keep the topology)
+    def chi(mm):
+        TT = mm.tris.astype(np.int64)
+        EE = np.unique(np.sort(np.concatenate([TT[:, [0, 1]], TT[:, [1, 2]], TT[:, [2, 0]]]), axis=1), axis=0)
+        return len(np.unique(TT)) - len(EE) + len(TT)
+    assert chi(m) == chi(raw)
+    # the tiny triangles are gone; the enclosed volume barely moves
+    _, a_raw, _ = dense.geometry(raw.verts, raw.tris)
+    c, a, n = dense.geometry(m.verts, m.tris)
+    assert (a / a.mean() < 1e-4).sum() < 0.1 * (a_raw / a_raw.mean() < 1e-4).sum()
+    vol = lambda mm: np.sum(np.einsum("ij,ij->i", dense.geometry(mm.verts, mm.tris)[0], dense.geometry(mm.verts, mm.tris)[2]) * dense.geometry(mm.verts, mm.tris)[1]) / 3
+    assert abs(vol(m) - vol(raw)) < 2e-3 * vol(raw)

@@ -1,9 +1,10 @@
 """The allocation-free energy entry point against the regular one. Needs a GPU.
 
-pb_solvation_energy_noalloc serves callers that cannot call cudaMalloc (for example while a
-stream is being captured into a CUDA graph, or under a fixed device-memory budget): it keeps
-its scratch in a fixed device array instead of allocating. This file is named so that pytest
-collects it last; it must pass alone in a fresh process and after the other tests.
+pb_solvation_energy_noalloc serves callers that cannot call cudaMalloc (a host with a fixed
+device-memory budget that forbids allocations after start-up, or code where an allocation is
+not allowed): it keeps its scratch in a fixed device array instead of allocating. This file
+is named so that pytest collects it last; it must pass alone in a fresh process and after the
+other tests.
 """
 import ctypes
 
@@ -62,3 +63,18 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                               ctypes.c_void_p(0), err, 256)
     assert rc == pb.PB_ERR_ARG
     assert b"scratch limit" in err.value
+
+
+def test_noalloc_without_charges_gives_zero():
+    m = inputs.kirkwood_ball(2, 2.0, 3, 1.5, seed=22)
+    dv = torch.tensor(m.verts, device="cuda", dtype=torch.float64)
+    dt = torch.tensor(m.tris, device="cuda", dtype=torch.int32)
+    x = torch.tensor(inputs.random_density(m.nt, 3), device="cuda", dtype=torch.float64)
+    E = torch.full((1,), 7.0, device="cuda", dtype=torch.float64)
+    err = ctypes.create_string_buffer(256)
+    rc = pb.lib().pb_solvation_energy_noalloc(ctypes.c_void_p(dv.data_ptr()), ctypes.c_void_p(dt.data_ptr()), m.nt,
+                                              None, None, 0, 1.0, 80.0, 0.1257, pb.PB_FP64,
+                                              ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(E.data_ptr()),
+                                              ctypes.c_void_p(0), err, 256)
+    torch.cuda.synchronize()
+    assert rc == pb.PB_OK and float(E.item()) == 0.0
