@@ -4,16 +4,17 @@
 Workload (default): the largest single-GPU configuration -- a 20000-atom synthetic
 protein-like molecule (self-avoiding walk, step 1.5 A, minimum separation 2.8 A; radii
 {1.2, 1.55, 1.7, 1.8} A; charges U[-0.8, 0.8] e shifted to an integer total; seed 23000)
-under the level-1.0 surface of sum_i exp(-(d/r_i)^2) on a 0.9 A grid: 2,066,599 flat
-triangles, 4.1M unknowns. eps_in = 1, eps_out = 80, kappa = 0.1257 / A; FMM order p = 8,
-eta0 = 0.8, leaf size 64, FP32 bulk arithmetic with float-float singular integrals and FP64
-Arnoldi, preconditioner and energy (mixed precision), block-diagonal preconditioner,
-GMRES(50) to 1e-6 relative residual. --workload sphere runs the Kirkwood sphere with
-off-centre charges (radius 20 A, icosphere level 6, 81920 triangles, 50 charges).
+under the level-1.0 surface of sum_i exp(-(d/r_i)^2) on a 0.9 A grid, edges shorter than
+0.09 A collapsed: 1,836,805 flat triangles, 3.67M unknowns, 20000 charges. eps_in = 1,
+eps_out = 80, kappa = 0.1257 / A; FMM order p = 8, eta0 = 0.8, leaf size 64, FP32 bulk
+arithmetic with float-float singular integrals and FP64 Arnoldi, preconditioner and energy
+(mixed precision), block-diagonal preconditioner, GMRES(200) to 1e-6 relative residual,
+solvation energy by the Cartesian treecode (theta 0.5). --workload sphere runs the Kirkwood
+sphere with off-centre charges (radius 20 A, icosphere level 6, 81920 triangles, 50 charges).
 
 One step = the whole hot path on the resident mesh: pb_build_tree (geometry, octree,
 lists, singular integrals, preconditioner), pb_gmres_solve (right-hand side + GMRES with
-FMM products) and pb_solvation_energy. value = element-matvecs per second of the step:
+FMM products) and the solvation energy. value = element-matvecs per second of the step:
 N x (matrix-vector products the solver performed) / step time, in Melem/s -- setup
 included. Inputs are far larger than the 129 MB L2 (and the L2 is flushed between steps,
 outside the timed events). The plain FP64 method is timed on the same molecule in the same
@@ -70,9 +71,14 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--restart", type=int, default=200, help="GMRES restart length m (Krylov basis vectors)")
+    ap.add_argument("--energy", default="treecode", choices=["treecode", "direct"],
+                    help="solvation energy of the step: the Cartesian treecode of Section 2.5 or the direct sum")
+    ap.add_argument("--theta", type=float, default=0.5, help="treecode MAC parameter")
     ap.add_argument("--workload", default="molecule", choices=["sphere", "molecule", "batch", "learned", "precond"])
     ap.add_argument("--train-molecules", type=int, default=48)
     ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--train-atoms", type=int, nargs=2, default=[50, 500], metavar=("MIN", "MAX"),
+                    help="training molecules: atom counts log-uniform in [MIN, MAX]")
     ap.add_argument("--atoms", type=int, default=None,
                     help="molecule size (default 20000 for --workload molecule, 2000 for learned)")
     ap.add_argument("--fp64-budget", type=float, default=60.0,
@@ -245,7 +251,8 @@ def config_dict(a, mesh):
         "workload": wl,
         "N": mesh.nt, "p": a.p, "eta0": a.eta0, "leaf_size": a.leaf, "precision": a.precision,
         "precond": "block-diagonal (leaf level)", "gmres": f"GMRES({a.restart}) tol {a.tol}",
-        "step": "build_tree + gmres_solve + solvation_energy on the resident mesh",
+        "step": "build_tree + gmres_solve + solvation energy on the resident mesh",
+        "energy": (f"treecode (Section 2.5), theta {a.theta}" if a.energy == "treecode" else "direct sum"),
         "l2": "flushed between steps (256 MiB write, outside the timed events)",
     }
 
@@ -282,7 +289,11 @@ FF_INST_PER_SS_POINT = {1: 685, 2: 613, 3: 363}
 # for one product / one build), by workload, from the captures summarised in profiles/; None
 # where no capture of the current kernel exists
 TRAFFIC_BYTES = {
+    # profiles/k_near_tile_kirkwood_l6.md (near), round-one singular capture
     "sphere_l6_p8_leaf64": {"near": 5.791e6, "m2l": None, "singular": 2.0755e7, "pcbuild": None},
+    # profiles/traffic_molecule20k_mixed_p8.md: near, the six MtL levels of one product, the
+    # singular pass, the three block-inversion classes of one build
+    "molecule_20000_p8_leaf64": {"near": 1.4429e8, "m2l": 1.0849e9, "singular": 1.9656e9, "pcbuild": 4.4812e9},
 }
 
 
@@ -387,11 +398,15 @@ def run_ours(a):
     x = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
+    def energy(c):
+        if a.energy == "treecode":
+            return pb.pb_solvation_energy_treecode(c, x, a.theta)
+        return pb.pb_solvation_energy(c, x)
+
     def step(c):
         pb.pb_build_tree(c)
         info = pb.pb_gmres_solve(c, x, tol=a.tol, max_iter=2000, restart=a.restart)
-        E = pb.pb_solvation_energy(c, x)
-        return info, E
+        return info, energy(c)
 
     for _ in range(a.warmup):
         step(ctx)
@@ -439,6 +454,10 @@ def run_ours(a):
     t_total = sum(times) / 1e3
     t_max = dist_max(t_total, world)
     value = world * N * matvecs / t_max / 1e6
+
+    # the other energy evaluation on the last solution (untimed), for the treecode's error
+    E_other = pb.pb_solvation_energy(ctx, x) if a.energy == "treecode" else pb.pb_solvation_energy_treecode(
+        ctx, x, a.theta)
 
     # matrix-vector product alone, resident, L2 warm (reported beside the step metric)
     xv = torch.rand(2 * N, dtype=torch.float64, device="cuda")
@@ -545,7 +564,8 @@ def run_ours(a):
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
             "gmres_iterations": iters, "matvecs_per_step": matvecs / a.steps,
             "phases_ms_per_step": per_step, "phase_rooflines": rooflines, "matvec_ms": t_mv, "matvec_only_melem_s": N / t_mv / 1e3,
-            "energy_kcal": energies[-1], "kirkwood_series_kcal": Ek, "tree": stats, "fp64_method": fp64,
+            "energy_kcal": energies[-1], ("energy_direct_kcal" if a.energy == "treecode" else "energy_treecode_kcal"):
+            E_other, "kirkwood_series_kcal": Ek, "tree": stats, "fp64_method": fp64,
             "device_driven_gmres": device_driven,
             "peaks": pk,
         }
@@ -603,14 +623,25 @@ def run_batch(a):
     Xs = [torch.empty((a.states, 2 * m.nt), dtype=torch.float64, device="cuda") for m in mols]
     restart = a.batch_restart
 
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    split = {"build_ms": [], "solve_ms": []}
+
     def step():
+        ev[0].record()
         for cx in ctxs:
             pb.pb_build_tree(cx)
+        ev[1].record()
         E, infos = pb.pb_batch_solve_states(ctxs, states, Xs, tol=a.tol, max_iter=500, restart=restart)
+        ev[2].record()
+        torch.cuda.synchronize()
+        split["build_ms"].append(ev[0].elapsed_time(ev[1]))
+        split["solve_ms"].append(ev[1].elapsed_time(ev[2]))
         return sum(i.matvecs * m.nt for inf, m in zip(infos, mols) for i in inf), E, infos
 
     for _ in range(a.warmup):
         step()
+    split["build_ms"].clear()
+    split["solve_ms"].clear()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     n0 = sum(pb.pb_get_launch_count(cx) for cx in ctxs)
@@ -632,9 +663,10 @@ def run_batch(a):
     dt = dist_max(sum(times), world)
     launches = sum(pb.pb_get_launch_count(cx) for cx in ctxs) - n0
     graph_launches = [pb.pb_get_graph_launches(cx) - g for cx, g in zip(ctxs, g0)]
-    # the same molecules one at a time (pb_solve_states, batched states per molecule), for the
-    # energies' agreement and the gain of the single launch
-    t1 = time.perf_counter()
+    # the same solves one molecule at a time (pb_solve_states, batched states per molecule, two
+    # graph launches each), for the energies' agreement and the gain of the single launch
+    torch.cuda.synchronize()
+    ev[0].record()
     worst = 0.0
     seq_units = 0
     for k, (cx, m) in enumerate(zip(ctxs, mols)):
@@ -642,8 +674,9 @@ def run_batch(a):
         Er, ir = pb.pb_solve_states(cx, states[k], Xr, tol=a.tol, max_iter=500, restart=restart, warm=2)
         worst = max(worst, float(np.max(np.abs(Er - E[k]) / np.abs(Er))))
         seq_units += sum(i.matvecs * m.nt for i in ir)
+    ev[1].record()
     torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t1
+    t_seq = ev[0].elapsed_time(ev[1]) / 1e3
     mem = torch.cuda.mem_get_info()
     for cx in ctxs:
         pb.pb_destroy(cx)
@@ -655,7 +688,9 @@ def run_batch(a):
             "dtype": "f32+f64" if a.precision == "mixed" else "f64", "data": "synthetic",
             "clocks": clk.summary(), "gpu_launches": launches, "graph_launches_per_step": [g / a.steps for g in graph_launches],
             "iterations_max": max(i.iterations for inf in infos for i in inf),
-            "one_by_one": {"value": seq_units / t_seq / 1e6, "seconds": t_seq,
+            "build_ms_per_step": float(np.mean(split["build_ms"])), "solve_ms_per_step": float(np.mean(split["solve_ms"])),
+            "one_by_one": {"solve_ms": 1e3 * t_seq, "value_solves_only": seq_units / t_seq / 1e6,
+                           "batch_value_solves_only": units / a.steps / (np.mean(split["solve_ms"]) / 1e3) / 1e6,
                            "max_rel_energy_diff_vs_batch": worst},
             "device_memory_free_gb": mem[0] / 1e9, "device_memory_total_gb": mem[1] / 1e9,
             "config": {"workload": f"{a.molecules} protein-like molecules, atoms log-uniform in [200, {a.max_atoms}] "
@@ -740,7 +775,8 @@ def run_precond(a):
 def run_learned(a):
     """Learned warm start against a zero start, and both against plain FP64 from zero.
 
-    Training (untimed): `train-molecules` protein-like molecules of 50-500 atoms (log-uniform),
+    Training (untimed): `train-molecules` protein-like molecules of `train-atoms` atoms (default
+    50-500, log-uniform),
     each solved from zero by the mixed-precision solver; the network (18 -> 128 -> 128 -> 128
     -> 2, BF16 tensor-core kernels) is fitted to their scaled solutions by Adam. Evaluation:
     the `atoms`-atom molecule, three arms per step, each pb_build_tree + solve to `tol` +
@@ -755,7 +791,7 @@ def run_learned(a):
     build.build()
     stream = torch.cuda.current_stream().cuda_stream
     rng = np.random.default_rng(6000 + rank)
-    counts = np.exp(rng.uniform(np.log(50), np.log(500), a.train_molecules)).astype(int)
+    counts = np.exp(rng.uniform(np.log(a.train_atoms[0]), np.log(a.train_atoms[1]), a.train_molecules)).astype(int)
     t0 = time.perf_counter()
     F, T = warmstart.make_dataset(counts, seed=6100 + rank, grid=a.grid, clean=not a.raw_mesh)
     t_data = time.perf_counter() - t0

@@ -28,7 +28,7 @@ def solve_params(**kw):
     return pb.params(**base)
 
 
-def training_rows(mesh, prm, tol=1e-6, max_iter=300, restart=50):
+def training_rows(mesh, prm, tol=1e-6, max_iter=1000, restart=200):
     """(F, T, info) for one molecule: features (nt, 18) and targets (nt, 2) as float32 CUDA
     tensors from its GMRES solution."""
     import torch
