@@ -150,15 +150,7 @@ __device__ __forceinline__ NearTerms near_pair(float4 tp, float4 tn, float4 tl, 
     const float rinv = rsqrtf(r2d);
     const float r = r2d * rinv, tt = kappa * r;
     float E, g;
-    // the series of pb_screen is needed only below kappa r = 0.125; a wave of 32 pairs without
-    // such a pair (most of them) takes the exponential branch it would select anyway. Every
-    // caller runs this with the whole warp.
-    if (__any_sync(0xffffffffu, tt < 0.125f)) {
-        pb_screen<float>(tt, E, g);
-    } else {
-        E = __expf(-tt) - 1.0f;
-        g = E + tt;
-    }
+    pb_screen<float>(tt, E, g);
     const float tE = tt * E;
     const float c1 = -g - tE;
     const float c3 = -3.f * g - tt * tt - tE * (3.f + tt);

@@ -249,6 +249,10 @@ void* pb_alloc_on(pb_ctx* c, size_t bytes, cudaStream_t s, bool build_lifetime =
 
 // translation-unit entry points
 int pb_geometry_and_tree(pb_ctx* c);          // tree.cu
+// radix.cu: out[0..n] = exclusive prefix sums of in[0..n) (out[n] the total); stable sort of
+// (key, value) pairs by the low `bits` key bits. Both queued on c->st, no read-back.
+int pb_scan_exclusive(pb_ctx* c, const int* in, int* out, int n);
+int pb_radix_sort_pairs(pb_ctx* c, const unsigned* kin, const int* vin, unsigned* kout, int* vout, int n, int bits);
 int pb_touching_and_singular(pb_ctx* c);      // singular.cu
 int pb_near_setup(pb_ctx* c);                                      // nearfield.cu
 int pb_near_apply(pb_ctx* c, const double* xs, double* ys);        // nearfield.cu (writes ys)

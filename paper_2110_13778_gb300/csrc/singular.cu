@@ -7,7 +7,6 @@
 // the exact (FP64, qs^4-point) integral minus the one-point rule that the near-field kernel
 // applies to every non-identical pair. Adding corr to the near-field product therefore gives
 // the Galerkin entries of eq_linsysEntry for touching pairs.
-#include <cub/cub.cuh>
 
 #include <math.h>
 
@@ -726,26 +725,12 @@ int pb_touching_and_singular(pb_ctx* c)
         return pb_fail(c, PB_ERR_NOMEM, "touching: out of memory");
     k_vcount<<<nblk(nt, B), B, 0, c->st>>>(nt, c->stris, vcnt);
     PB_LAUNCH(c);
-    size_t tmp = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, tmp, vcnt, voff, nv + 1, c->st);
-    void* t = nullptr;
-    PB_CUDA(c, cudaMallocFromPoolAsync(&t, tmp, c->pool, c->st));
-    cub::DeviceScan::ExclusiveSum(t, tmp, vcnt, voff, nv + 1, c->st);
-    PB_LAUNCH(c);
+    if (int rc = pb_scan_exclusive(c, vcnt, voff, nv)) return rc;
     k_vfill<<<nblk(nt, B), B, 0, c->st>>>(nt, c->stris, voff, vfill, vlist);
     PB_LAUNCH(c);
     k_touch<0><<<nblk(nt, 128), 128, 0, c->st>>>(nt, c->stris, voff, vlist, tcnt, nullptr, nullptr, bad);
     PB_LAUNCH(c);
-    size_t tmp2 = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, tmp2, tcnt, c->touch_off, nt + 1, c->st);
-    if (tmp2 > tmp) {
-        PB_CUDA(c, cudaFreeAsync(t, c->st));
-        PB_CUDA(c, cudaMallocFromPoolAsync(&t, tmp2, c->pool, c->st));
-        tmp = tmp2;
-    }
-    cub::DeviceScan::ExclusiveSum(t, tmp, tcnt, c->touch_off, nt + 1, c->st);
-    PB_LAUNCH(c);
-    PB_CUDA(c, cudaFreeAsync(t, c->st));
+    if (int rc = pb_scan_exclusive(c, tcnt, c->touch_off, nt)) return rc;
     int hb = 0, htot = 0;
     PB_CUDA(c, cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     PB_CUDA(c, cudaMemcpyAsync(&htot, c->touch_off + nt, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -800,15 +785,7 @@ int pb_touching_and_singular(pb_ctx* c)
     k_canon<0><<<nblk(nt, B), B, 0, c->st>>>(nt, c->touch_off, c->touch_j, c->order, c->stris, ccnt, nullptr, nullptr,
                                              nullptr, 0);
     PB_LAUNCH(c);
-    {
-        size_t ctmp = 0;
-        cub::DeviceScan::ExclusiveSum(nullptr, ctmp, ccnt, coff, 3 * nt + 1, c->st);
-        void* cbuf = nullptr;
-        PB_CUDA(c, cudaMallocFromPoolAsync(&cbuf, ctmp, c->pool, c->st));
-        cub::DeviceScan::ExclusiveSum(cbuf, ctmp, ccnt, coff, 3 * nt + 1, c->st);
-        PB_LAUNCH(c);
-        PB_CUDA(c, cudaFreeAsync(cbuf, c->st));
-    }
+    if (int rc = pb_scan_exclusive(c, ccnt, coff, 3 * nt)) return rc;
     // Touching is symmetric and every triangle touches itself, so the unordered pairs number
     // (ordered pairs + nt) / 2; the kernel takes the count from the scan (coff[3 nt]) and the
     // build checks the two agree when it synchronises at its end.

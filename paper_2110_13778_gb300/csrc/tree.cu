@@ -6,7 +6,6 @@
 // floor((c - origin) * (1024 / side)) clamped to [0, 1023]; neighbour test
 // (rho_c + rho_c')^2 > eta0^2 |x_c - x_c'|^2), so that the result is reproducible bit for
 // bit on any IEEE machine.
-#include <cub/cub.cuh>
 
 #include <algorithm>
 #include <vector>
@@ -311,17 +310,7 @@ __global__ void k_sorted_elems(int nt, const int* __restrict__ order, const doub
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
 // exclusive scan of cnt[0..n) into off[0..n], off[n] = total (queued, no read-back)
-static int scan_only(pb_ctx* c, const int* cnt, int* off, int n)
-{
-    size_t tmp = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, tmp, cnt, off, n + 1, c->st);
-    void* t = nullptr;
-    PB_CUDA(c, cudaMallocFromPoolAsync(&t, tmp, c->pool, c->st));
-    cub::DeviceScan::ExclusiveSum(t, tmp, cnt, off, n + 1, c->st);
-    PB_LAUNCH(c);
-    PB_CUDA(c, cudaFreeAsync(t, c->st));
-    return PB_OK;
-}
+static int scan_only(pb_ctx* c, const int* cnt, int* off, int n) { return pb_scan_exclusive(c, cnt, off, n); }
 
 int pb_geometry_and_tree(pb_ctx* c)
 {
@@ -371,15 +360,7 @@ int pb_geometry_and_tree(pb_ctx* c)
     if (!keys || !skeys || !idx || !c->order || !c->rank) return pb_fail(c, PB_ERR_NOMEM, "morton: out of memory");
     k_morton<<<nblk(nt, B), B, 0, c->st>>>(nt, c->cent, origin[0], origin[1], origin[2], scale, keys, idx);
     PB_LAUNCH(c);
-    {
-        size_t tmp = 0;
-        cub::DeviceRadixSort::SortPairs(nullptr, tmp, keys, skeys, idx, c->order, nt, 0, 3 * PB_MAXL, c->st);
-        void* t = nullptr;
-        PB_CUDA(c, cudaMallocFromPoolAsync(&t, tmp, c->pool, c->st));
-        cub::DeviceRadixSort::SortPairs(t, tmp, keys, skeys, idx, c->order, nt, 0, 3 * PB_MAXL, c->st);
-        PB_LAUNCH(c);
-        PB_CUDA(c, cudaFreeAsync(t, c->st));
-    }
+    if (int rc = pb_radix_sort_pairs(c, keys, idx, skeys, c->order, nt, 3 * PB_MAXL)) return rc;
 
     // depth: deepest level whose mean cluster size is >= leaf_size (or the given depth)
     int* cnt = (int*)pb_alloc(c, sizeof(int) * (PB_MAXL + 1));

@@ -79,6 +79,27 @@ def test_tree_bit_exact(sphere3, leaf, eta0):
         pb.pb_destroy(ctx)
 
 
+def test_morton_order_large_and_tied():
+    """The stable radix sort of the Morton keys (Section 2.4) on 81920 triangles (320 sort tiles,
+    a ragged last scan tile) and on two copies of that surface 2e-4 apart, where most keys tie
+    with the key of the element 81920 places later (another sort tile): the order must be the
+    keys' order with ties by element index, bit for bit."""
+    m = inputs.kirkwood_ball(6, 2.0, 3, 1.5, seed=6)
+    V2 = np.vstack([m.verts, m.verts + 2e-4])
+    T2 = np.vstack([m.tris, m.tris + len(m.verts)])
+    for V, T in ((m.verts, m.tris), (V2, T2)):
+        ctx = _ctx(inputs.Mesh(V, T, m.qpos, m.q), leaf_size=64, eta0=0.8, precision=pb.PB_FP64)
+        try:
+            st, order, *_ = pb.pb_get_tree(ctx, len(T))
+        finally:
+            pb.pb_destroy(ctx)
+        key, _, _ = fmm.morton_keys(fmm.centroids(V, T), V)
+        ref = np.lexsort((np.arange(len(T)), key))
+        assert np.array_equal(order, ref)
+        if len(T) > len(m.tris):
+            assert np.count_nonzero(np.diff(key[ref]) == 0) > len(m.tris) // 2  # many ties
+
+
 def test_all_near_fp64_equals_dense(sphere3):
     m, ph, A = sphere3
     ctx = _ctx(m, leaf_size=16, eta0=1e-6, p=2, precision=pb.PB_FP64)
