@@ -10,6 +10,7 @@ Modules:
   kirkwood  -- closed-form and series Kirkwood energies of a dielectric sphere
   taylor    -- Taylor coefficients of G0 / Gk by truncated power-series arithmetic
   fmm       -- the six-step Cartesian FMM of Section 2.4 in plain numpy
+  linear    -- the piecewise-linear (continuous hat function) Galerkin system of Section 2.3
 
 Parity status of each function is stated in its module header.
 """
@@ -59,5 +60,15 @@ def lib():
             L.orc_rhs.argtypes = [dp, ip, c_int, dp, dp, c_int, c_double, c_int, dp, dp, dp, dp]
             L.orc_energy.argtypes = [dp, ip, c_int, dp, dp, c_int, c_double, c_double, c_int, dp, dp, dp, dp]
             L.orc_energy.restype = c_double
+            L.orc_p1_pair_integrals.argtypes = [dp, ip, c_int, c_int, c_double, c_double, c_int, c_int, dp, dp, dp,
+                                                dp]
+            L.orc_p1_pair_terms.argtypes = [dp, ip, c_int, c_int, c_double, c_int, dp]
+            L.orc_p1_pair_terms.restype = c_int
+            L.orc_p1_matvec.argtypes = [dp, ip, c_int, c_int, c_double, c_double, c_int, c_int, dp, dp, dp, dp, dp]
+            L.orc_p1_assemble.argtypes = [dp, ip, c_int, c_int, c_double, c_double, c_int, c_int, dp, dp, dp, dp]
+            L.orc_p1_rhs.argtypes = [dp, ip, c_int, c_int, dp, dp, c_int, c_double, c_int, dp, dp, dp, dp]
+            L.orc_p1_energy.argtypes = [dp, ip, c_int, c_int, dp, dp, c_int, c_double, c_double, c_int, dp, dp, dp,
+                                        dp]
+            L.orc_p1_energy.restype = c_double
             _lib = L
     return _lib

@@ -601,3 +601,353 @@ double orc_energy(const double* V, const int32_t* T, int nt, const double* qpos,
     }
     return 0.5 * E * 4.0 * ORC_PI * 332.0716;
 }
+
+/* ---------- piecewise-linear Galerkin: continuous hat functions (S^1_h, Section 2.3) ----------
+ * The unknowns live at the vertices: x = [phi_1..phi_nv ; dphi_1..dphi_nv]. On an element with
+ * corners P0, P1, P2 the point P0 + e1 (P1 - P0) + e2 (P2 - P1) carries the three linear
+ * functions of eqlinearfcn, 1 - e1, e1 - e2 and e2, which are the barycentric weights of P0,
+ * P1 and P2; the hat function of vertex v (eqglinearcfcn) is, on every element containing v,
+ * the one of them that is 1 at v. The entries become
+ *    I_m(a, b) = sum over elements tau containing a, sigma containing b of
+ *                int_tau int_sigma psi_a(x) K_m(x, y) psi_b(y) dS_y dS_x,
+ * and the identity term of the variational form the mass matrix
+ *    M(a, b) = int psi_a psi_b = sum_tau A_tau (1 + [a == b]) / 12 over tau containing both. */
+static void orc_lambda(double e1, double e2, double* lam)
+{
+    lam[0] = 1.0 - e1;
+    lam[1] = e1 - e2;
+    lam[2] = e2;
+}
+
+/* position of vertex id v in triangle i (uploaded order) */
+static int orc_corner(const int32_t* T, int i, int32_t v)
+{
+    for (int a = 0; a < 3; ++a)
+        if (T[3 * i + a] == v) return a;
+    return -1;
+}
+
+/* Sauter-Schwab integrals of the eight kernel terms weighted by the linear functions of both
+ * triangles: acc[m][a][b], a a corner of `first` and b a corner of `second`, both in the
+ * reordered (shared corners first) layout whose vertex ids come back in ti, tj. */
+static void orc_p1_ss_terms(const double* V, const int32_t* T, int first, int second, int shared,
+                            const double* na, const double* nb, double Afirst, double Asecond,
+                            const orc_phys* ph, const double* gx, const double* gw, int qs,
+                            double acc[ORC_NTERMS][3][3], int32_t* ti, int32_t* tj)
+{
+    orc_reorder(T, first, second, shared, ti, tj);
+    double P[3][3], Q[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) {
+            P[a][k] = V[3 * ti[a] + k];
+            Q[a][k] = V[3 * tj[a] + k];
+        }
+    memset(acc, 0, sizeof(double) * ORC_NTERMS * 9);
+    for (int a = 0; a < qs; ++a)
+        for (int b = 0; b < qs; ++b)
+            for (int c = 0; c < qs; ++c)
+                for (int d = 0; d < qs; ++d) {
+                    double wq = gw[a] * gw[b] * gw[c] * gw[d];
+                    double xh[12], yh[12], jac[6];
+                    int ns = orc_ss_points(shared, gx[a], gx[b], gx[c], gx[d], xh, yh, jac);
+                    for (int s = 0; s < ns; ++s) {
+                        double x[3], y[3], Qt[ORC_NTERMS], lx[3], ly[3];
+                        for (int k = 0; k < 3; ++k) {
+                            x[k] = P[0][k] + xh[2 * s] * (P[1][k] - P[0][k]) +
+                                   xh[2 * s + 1] * (P[2][k] - P[1][k]);
+                            y[k] = Q[0][k] + yh[2 * s] * (Q[1][k] - Q[0][k]) +
+                                   yh[2 * s + 1] * (Q[2][k] - Q[1][k]);
+                        }
+                        orc_lambda(xh[2 * s], xh[2 * s + 1], lx);
+                        orc_lambda(yh[2 * s], yh[2 * s + 1], ly);
+                        orc_kernel_terms(x, na, y, nb, ph, Qt);
+                        for (int m = 0; m < ORC_NTERMS; ++m)
+                            for (int p = 0; p < 3; ++p)
+                                for (int r = 0; r < 3; ++r)
+                                    acc[m][p][r] += wq * jac[s] * lx[p] * ly[r] * Qt[m];
+                    }
+                }
+    for (int m = 0; m < ORC_NTERMS; ++m)
+        for (int p = 0; p < 3; ++p)
+            for (int r = 0; r < 3; ++r) acc[m][p][r] *= (2.0 * Afirst) * (2.0 * Asecond);
+}
+
+/* I[m][a][b] = int_{tau_i} int_{tau_j} lambda_a(x) K_m(x, y) lambda_b(y), m = 1..4, a and b the
+ * corners of i and j in uploaded order. Regular pairs by the rule qr (the centroid rule, where
+ * every linear function is 1/3, for qr->n == 1); touching pairs by Sauter-Schwab. */
+static void orc_p1_pair(const double* V, const int32_t* T, int i, int j, const orc_phys* ph,
+                        const double* gx, const double* gw, int qs, const orc_rule* qr, double I[4][3][3])
+{
+    double ci[3], cj[3], ni[3], nj[3], Ai, Aj;
+    double ui[3], vi[3], wi[3], uj[3], vj[3], wj[3];
+    orc_tri(V, T, i, ui, vi, wi);
+    orc_geom(ui, vi, wi, ci, &Ai, ni);
+    orc_tri(V, T, j, uj, vj, wj);
+    orc_geom(uj, vj, wj, cj, &Aj, nj);
+    int shared = orc_shared(T, i, j);
+    if (shared == 0) {
+        memset(I, 0, sizeof(double) * 36);
+        if (qr->n == 1) {
+            double K[4];
+            orc_kernels(ci, ni, cj, nj, ph, K);
+            for (int m = 0; m < 4; ++m)
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) I[m][a][b] = Ai * Aj * K[m] / 9.0;
+            return;
+        }
+        for (int p = 0; p < qr->n; ++p) {
+            double x[3], lx[3];
+            orc_rule_point(ui, vi, wi, qr->e1[p], qr->e2[p], x);
+            orc_lambda(qr->e1[p], qr->e2[p], lx);
+            for (int r = 0; r < qr->n; ++r) {
+                double y[3], ly[3], K[4];
+                orc_rule_point(uj, vj, wj, qr->e1[r], qr->e2[r], y);
+                orc_lambda(qr->e1[r], qr->e2[r], ly);
+                orc_kernels(x, ni, y, nj, ph, K);
+                double wgt = (2.0 * Ai) * (2.0 * Aj) * qr->w[p] * qr->w[r];
+                for (int m = 0; m < 4; ++m)
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) I[m][a][b] += wgt * lx[a] * ly[b] * K[m];
+            }
+        }
+        return;
+    }
+    int first = i < j ? i : j, second = i < j ? j : i;
+    double na[3], nb[3];
+    for (int k = 0; k < 3; ++k) {
+        na[k] = (first == i) ? ni[k] : nj[k];
+        nb[k] = (first == i) ? nj[k] : ni[k];
+    }
+    double acc[ORC_NTERMS][3][3];
+    int32_t ta[3], tb[3];
+    orc_p1_ss_terms(V, T, first, second, shared, na, nb, first == i ? Ai : Aj, first == i ? Aj : Ai,
+                    ph, gx, gw, qs, acc, ta, tb);
+    double eps = ph->eps;
+    /* acc is laid out [first corner][second corner]; the result [target corner][source corner] */
+    for (int p = 0; p < 3; ++p)
+        for (int r = 0; r < 3; ++r) {
+            int a, b;
+            double t[ORC_NTERMS];
+            if (first == i) {
+                a = orc_corner(T, i, ta[p]);
+                b = orc_corner(T, j, tb[r]);
+            } else {
+                a = orc_corner(T, i, tb[r]);
+                b = orc_corner(T, j, ta[p]);
+            }
+            for (int m = 0; m < ORC_NTERMS; ++m) t[m] = acc[m][p][r];
+            I[0][a][b] = t[0];
+            I[3][a][b] = t[1];
+            if (first == i) {
+                I[1][a][b] = eps * t[3] - t[2];
+                I[2][a][b] = t[4] - t[5] / eps;
+            } else {
+                I[1][a][b] = eps * t[5] - t[4];
+                I[2][a][b] = t[2] - t[3] / eps;
+            }
+        }
+}
+
+/* exported: the 4 x 3 x 3 weighted integrals of the ordered pair (target i, source j), corners
+ * in uploaded order */
+int orc_p1_pair_integrals(const double* V, const int32_t* T, int i, int j, double eps, double kappa,
+                          int qs, int nq, const double* qe1, const double* qe2, const double* qw,
+                          double* out)
+{
+    double gx[64], gw[64];
+    if (orc_gauss_legendre01(qs, gx, gw)) return -1;
+    orc_phys ph = {eps, kappa};
+    orc_rule qr = {nq, qe1, qe2, qw};
+    double I[4][3][3];
+    orc_p1_pair(V, T, i, j, &ph, gx, gw, qs, &qr, I);
+    memcpy(out, I, sizeof(I));
+    return 0;
+}
+
+/* exported, for the pins: the eight Sauter-Schwab term integrals of a touching pair weighted by
+ * the linear functions, out[m][a][b] with a a corner of min(i, j) and b a corner of max(i, j),
+ * both in uploaded order. Returns the number of shared vertices (-1: no touching pair). */
+int orc_p1_pair_terms(const double* V, const int32_t* T, int i, int j, double kappa, int qs, double* out)
+{
+    double gx[64], gw[64];
+    if (orc_gauss_legendre01(qs, gx, gw)) return -1;
+    int shared = orc_shared(T, i, j);
+    if (shared == 0) return -1;
+    orc_phys ph = {1.0, kappa};
+    int first = i < j ? i : j, second = i < j ? j : i;
+    double c[3], na[3], nb[3], Aa, Ab, u[3], v[3], w[3];
+    orc_tri(V, T, first, u, v, w);
+    orc_geom(u, v, w, c, &Aa, na);
+    orc_tri(V, T, second, u, v, w);
+    orc_geom(u, v, w, c, &Ab, nb);
+    double acc[ORC_NTERMS][3][3];
+    int32_t ta[3], tb[3];
+    orc_p1_ss_terms(V, T, first, second, shared, na, nb, Aa, Ab, &ph, gx, gw, qs, acc, ta, tb);
+    for (int p = 0; p < 3; ++p)
+        for (int r = 0; r < 3; ++r) {
+            int a = orc_corner(T, first, ta[p]), b = orc_corner(T, second, tb[r]);
+            for (int m = 0; m < ORC_NTERMS; ++m) out[(m * 3 + a) * 3 + b] = acc[m][p][r];
+        }
+    return shared;
+}
+
+/* exported: y = A x for the piecewise-linear system, x and y of length 2 nv,
+ *    y1_a = 1/2 (1 + eps) sum_b M(a,b) phi_b - sum_b [I1(a,b) dphi_b + I2(a,b) phi_b]
+ *    y2_a = 1/2 (1 + 1/eps) sum_b M(a,b) dphi_b - sum_b [I3(a,b) dphi_b + I4(a,b) phi_b].
+ * Every element's three test rows are summed first (in parallel over elements), then added to
+ * their vertices in element order. */
+int orc_p1_matvec(const double* V, const int32_t* T, int nt, int nv, double eps, double kappa, int qs,
+                  int nq, const double* qe1, const double* qe2, const double* qw, const double* x,
+                  double* y)
+{
+    double gx[64], gw[64];
+    if (orc_gauss_legendre01(qs, gx, gw)) return -1;
+    orc_phys ph = {eps, kappa};
+    orc_rule qr = {nq, qe1, qe2, qw};
+    double* yl = (double*)calloc((size_t)6 * nt, sizeof(double));
+    if (!yl) return -2;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < nt; ++i) {
+        double c[3], n[3], Ai, u[3], v[3], w[3];
+        orc_tri(V, T, i, u, v, w);
+        orc_geom(u, v, w, c, &Ai, n);
+        double y1[3] = {0, 0, 0}, y2[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double M = Ai * (a == b ? 2.0 : 1.0) / 12.0;
+                y1[a] += 0.5 * (1.0 + eps) * M * x[T[3 * i + b]];
+                y2[a] += 0.5 * (1.0 + 1.0 / eps) * M * x[nv + T[3 * i + b]];
+            }
+        for (int j = 0; j < nt; ++j) {
+            double I[4][3][3];
+            orc_p1_pair(V, T, i, j, &ph, gx, gw, qs, &qr, I);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double ph_b = x[T[3 * j + b]], dph_b = x[nv + T[3 * j + b]];
+                    y1[a] -= I[0][a][b] * dph_b + I[1][a][b] * ph_b;
+                    y2[a] -= I[2][a][b] * dph_b + I[3][a][b] * ph_b;
+                }
+        }
+        for (int a = 0; a < 3; ++a) {
+            yl[6 * i + a] = y1[a];
+            yl[6 * i + 3 + a] = y2[a];
+        }
+    }
+    for (int k = 0; k < 2 * nv; ++k) y[k] = 0.0;
+    for (int i = 0; i < nt; ++i)
+        for (int a = 0; a < 3; ++a) {
+            y[T[3 * i + a]] += yl[6 * i + a];
+            y[nv + T[3 * i + a]] += yl[6 * i + 3 + a];
+        }
+    free(yl);
+    return 0;
+}
+
+/* exported: the dense 2 nv x 2 nv piecewise-linear matrix (row-major), same layout as the
+ * product above. Serial: small meshes only. */
+int orc_p1_assemble(const double* V, const int32_t* T, int nt, int nv, double eps, double kappa, int qs,
+                    int nq, const double* qe1, const double* qe2, const double* qw, double* A)
+{
+    double gx[64], gw[64];
+    if (orc_gauss_legendre01(qs, gx, gw)) return -1;
+    orc_phys ph = {eps, kappa};
+    orc_rule qr = {nq, qe1, qe2, qw};
+    long n2 = 2L * nv;
+    memset(A, 0, sizeof(double) * n2 * n2);
+    for (int i = 0; i < nt; ++i) {
+        double c[3], n[3], Ai, u[3], v[3], w[3];
+        orc_tri(V, T, i, u, v, w);
+        orc_geom(u, v, w, c, &Ai, n);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                long ra = T[3 * i + a], cb = T[3 * i + b];
+                double M = Ai * (a == b ? 2.0 : 1.0) / 12.0;
+                A[ra * n2 + cb] += 0.5 * (1.0 + eps) * M;
+                A[(nv + ra) * n2 + nv + cb] += 0.5 * (1.0 + 1.0 / eps) * M;
+            }
+        for (int j = 0; j < nt; ++j) {
+            double I[4][3][3];
+            orc_p1_pair(V, T, i, j, &ph, gx, gw, qs, &qr, I);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    long ra = T[3 * i + a], cb = T[3 * j + b];
+                    A[ra * n2 + cb] -= I[1][a][b];
+                    A[ra * n2 + nv + cb] -= I[0][a][b];
+                    A[(nv + ra) * n2 + cb] -= I[3][a][b];
+                    A[(nv + ra) * n2 + nv + cb] -= I[2][a][b];
+                }
+        }
+    }
+    return 0;
+}
+
+/* exported: piecewise-linear right-hand side, b_a = int psi_a S(x) / eps1 for both source terms
+ * of source_terms, by the rule (the centroid rule weighs every corner by 1/3) */
+void orc_p1_rhs(const double* V, const int32_t* T, int nt, int nv, const double* qpos, const double* q,
+                int nc, double eps1, int nq, const double* qe1, const double* qe2, const double* qw,
+                double* b)
+{
+    for (int k = 0; k < 2 * nv; ++k) b[k] = 0.0;
+    for (int i = 0; i < nt; ++i) {
+        double c[3], n[3], Ai, u[3], v[3], w[3];
+        orc_tri(V, T, i, u, v, w);
+        orc_geom(u, v, w, c, &Ai, n);
+        for (int p = 0; p < nq; ++p) {
+            double x[3], lam[3], t1, t2, wgt;
+            if (nq == 1) {
+                for (int k = 0; k < 3; ++k) x[k] = c[k];
+                lam[0] = lam[1] = lam[2] = 1.0 / 3.0;
+                wgt = Ai;
+            } else {
+                orc_rule_point(u, v, w, qe1[p], qe2[p], x);
+                orc_lambda(qe1[p], qe2[p], lam);
+                wgt = 2.0 * Ai * qw[p];
+            }
+            orc_sources(x, n, qpos, q, nc, &t1, &t2);
+            for (int a = 0; a < 3; ++a) {
+                b[T[3 * i + a]] += wgt * lam[a] * t1 / eps1;
+                b[nv + T[3 * i + a]] += wgt * lam[a] * t2 / eps1;
+            }
+        }
+    }
+}
+
+/* exported: the energy of eqsolengdis for a piecewise-linear solution (the densities at each
+ * rule point interpolated from the element's corners), kcal/mol as orc_energy */
+double orc_p1_energy(const double* V, const int32_t* T, int nt, int nv, const double* qpos, const double* q,
+                     int nc, double eps, double kappa, int nq, const double* qe1, const double* qe2,
+                     const double* qw, const double* x)
+{
+    orc_phys ph = {eps, kappa};
+    double zero[3] = {0.0, 0.0, 0.0};
+    double E = 0.0;
+    for (int k = 0; k < nc; ++k) {
+        double sk = 0.0;
+        for (int i = 0; i < nt; ++i) {
+            double c[3], n[3], Ai, u[3], v[3], w[3];
+            orc_tri(V, T, i, u, v, w);
+            orc_geom(u, v, w, c, &Ai, n);
+            for (int p = 0; p < nq; ++p) {
+                double y[3], lam[3], K[4], wgt;
+                if (nq == 1) {
+                    for (int d = 0; d < 3; ++d) y[d] = c[d];
+                    lam[0] = lam[1] = lam[2] = 1.0 / 3.0;
+                    wgt = Ai;
+                } else {
+                    orc_rule_point(u, v, w, qe1[p], qe2[p], y);
+                    orc_lambda(qe1[p], qe2[p], lam);
+                    wgt = 2.0 * Ai * qw[p];
+                }
+                double phv = 0.0, dphv = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    phv += lam[a] * x[T[3 * i + a]];
+                    dphv += lam[a] * x[nv + T[3 * i + a]];
+                }
+                orc_kernels(qpos + 3 * k, zero, y, n, &ph, K);
+                sk += wgt * (K[0] * dphv + K[1] * phv);
+            }
+        }
+        E += q[k] * sk;
+    }
+    return 0.5 * E * 4.0 * ORC_PI * 332.0716;
+}
