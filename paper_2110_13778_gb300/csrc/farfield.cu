@@ -688,16 +688,21 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phas
     return false;
 }
 
-// FP32: one block of two warps per cluster and per kernel (G0 for blockIdx.z = 0, Gk for 1).
-// Per chunk of 32 slots, the derivative block (T x 32 floats, 21 KB at p = 8) arrives by TMA
-// bulk copy (mbarrier completion, every wait bounded) while the warps load the 32 source
-// clusters' moments straight from the level's moment array (L2-resident, stored already scaled
-// by (-1)^|b| / b!), one coalesced row per source, into shared memory rows of 33 words
-// (conflict-free in both directions): no gathered copy of the moments goes through DRAM. Warp w accumulates its half
-// of the local coefficients (M2LWarp<P, w>: equal FMA counts, moments held in registers a
-// block at a time), so each slot costs about 740 shared-memory loads per kernel.
+// FP32: one block of two warps per chunk of 32 slots and per kernel (G0 for blockIdx.z = 0, Gk
+// for 1). Under mixed precision the slots of a level are packed without padding (the
+// interaction lists of consecutive targets follow one another; only the level's end is padded
+// to 32), so a chunk's lanes may belong to several targets. The chunk's derivative block (T x 32
+// floats, 21 KB at p = 8) arrives by TMA bulk copy (mbarrier completion, every wait bounded)
+// while the warps load the 32 source clusters' moments straight from the level's moment array
+// (L2-resident, stored already scaled by (-1)^|b| / b!; the source indices come from one
+// coalesced load and a shuffle per row), one coalesced row per source, into shared memory rows
+// of 33 words (conflict-free in both directions). Warp w accumulates its half of the local
+// coefficients (M2LWarp<P, w>: equal FMA counts, moments held in registers a block at a time).
+// After the chunk, the lanes' coefficients are summed per target run (consecutive lanes with
+// the same target), scaled by 1/a! and added into the local coefficients, which the caller
+// zeroes first (FP32 atomics: the order of the additions varies from run to run).
 template <int P>
-__global__ void __launch_bounds__(64, 1) k_m2l_tma(int ncl, const int* __restrict__ soff, const int* __restrict__ ssrc,
+__global__ void __launch_bounds__(64, 1) k_m2l_seg(int nch, const int* __restrict__ ssrc, const int* __restrict__ stgt,
                                                    const float* __restrict__ D0, const float* __restrict__ Dk,
                                                    const float* __restrict__ s0, const float* __restrict__ sk,
                                                    float* __restrict__ l0, float* __restrict__ lk,
@@ -713,53 +718,44 @@ __global__ void __launch_bounds__(64, 1) k_m2l_tma(int ncl, const int* __restric
     constexpr int NL = M2LWarp<P, 0>::n > M2LWarp<P, 1>::n ? M2LWarp<P, 0>::n : M2LWarp<P, 1>::n;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) unsigned long long bar;
+    __shared__ int tg[32];      // target of each lane's slot (-1: padding)
     float* Ds = (float*)dsm;    // [T * 32]
     float* Ms = Ds + T * 32;    // [T * 33]; with Ds, the reduction scratch [T * 33]
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const int c = blockIdx.x;
-    if (c >= ncl) return;
-    const int sb = soff[c], nch = (soff[c + 1] - sb) >> 5;
+    const int k = blockIdx.x;
+    if (k >= nch) return;
+    const int jl = ssrc[(size_t)k * 32 + lane];
+    if (wi == 0) tg[lane] = jl >= 0 ? stgt[(size_t)k * 32 + lane] : -1;
     if (threadIdx.x == 0) {
         mbar_init(&bar);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect(&bar, CH);
+        bulk_g2s(Ds, D + (size_t)k * T * 32, CH, &bar);
     }
-    __syncthreads();
-    unsigned ph = 0u;  // parity of the barrier's next completion
+    // the moments of the chunk's sources (padding slots: zero), two rows at a time, by
+    // asynchronous copies that overlap the derivative block's copy
+#pragma unroll 4
+    for (int s = wi; s < 32; s += 2) {
+        const int j = __shfl_sync(0xffffffffu, jl, s);
+        const float* row = sig + (size_t)(j < 0 ? 0 : j) * T;
+        for (int b = lane; b < T; b += 32) cp_async4(Ms + b * 33 + s, row + b, j >= 0);
+    }
+    cp_async_wait_all();
+    // the block agrees on the outcome, so that no thread leaves while another waits
+    if (!__syncthreads_and(mbar_wait(&bar, 0u))) {
+        // the copy never completed: record it, give it a bounded time to land, and stop
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        mbar_wait(&bar, 0u);
+        return;
+    }
     float L[NL];
 #pragma unroll
     for (int i = 0; i < NL; ++i) L[i] = 0.f;
-    const size_t cb = (size_t)(sb >> 5);  // first chunk of this cluster
-#pragma unroll 1
-    for (int k = 0; k < nch; ++k) {
-        if (threadIdx.x == 0) {
-            // order the earlier shared-memory reads (generic proxy) before the copy
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect(&bar, CH);
-            bulk_g2s(Ds, D + (cb + k) * T * 32, CH, &bar);
-        }
-        // the moments of the chunk's sources (padding slots: zero), two rows at a time, by
-        // asynchronous copies that overlap the derivative block's copy
-        const int* src = ssrc + (cb + k) * 32;
-        for (int s = wi; s < 32; s += 2) {
-            const int j = src[s];
-            const float* row = sig + (size_t)(j < 0 ? 0 : j) * T;
-            for (int b = lane; b < T; b += 32) cp_async4(Ms + b * 33 + s, row + b, j >= 0);
-        }
-        cp_async_wait_all();
-        // the block agrees on the outcome, so that no thread leaves while another waits
-        if (!__syncthreads_and(mbar_wait(&bar, ph))) {
-            // the copy never completed: record it, give it a bounded time to land, and stop
-            if (threadIdx.x == 0) atomicExch(err, 1);
-            mbar_wait(&bar, ph);
-            return;
-        }
-        ph ^= 1u;
-        if (wi == 0) M2LWarp<P, 0>::run(Ds + lane, Ms + lane, L);
-        else M2LWarp<P, 1>::run(Ds + lane, Ms + lane, L);
-        __syncthreads();
-    }
-    // sum over the 32 slots of each lane: the warps write their coefficients to disjoint
-    // rows of the scratch, then 64 threads add the rows and scale by 1/a!
+    if (wi == 0) M2LWarp<P, 0>::run(Ds + lane, Ms + lane, L);
+    else M2LWarp<P, 1>::run(Ds + lane, Ms + lane, L);
+    __syncthreads();
+    // per-lane coefficients into disjoint rows of the scratch, then sums over runs of lanes
+    // with the same target
     float* scratch = Ds;
     if (wi == 0) {
 #pragma unroll
@@ -770,9 +766,19 @@ __global__ void __launch_bounds__(64, 1) k_m2l_tma(int ncl, const int* __restric
     }
     __syncthreads();
     for (int i = threadIdx.x; i < T; i += 64) {
-        float s = 0.f;
-        for (int l = 0; l < 32; ++l) s += scratch[i * 33 + l];
-        out[(size_t)c * T + i] = s * c_ifact[i];
+        const float sc = c_ifact[i];
+        float acc = 0.f;
+        int cur = tg[0];
+        for (int l = 0; l < 32; ++l) {
+            const int t = tg[l];
+            if (t != cur) {
+                if (cur >= 0) atomicAdd(&out[(size_t)cur * T + i], acc * sc);
+                acc = 0.f;
+                cur = t;
+            }
+            acc += scratch[i * 33 + l];
+        }
+        if (cur >= 0) atomicAdd(&out[(size_t)cur * T + i], acc * sc);
     }
 }
 
@@ -1010,7 +1016,9 @@ static int upload_tables(pb_ctx* c)
 
 static bool m2l_fast_order(int p) { return p == 4 || p == 6 || p == 8; }
 
-// interaction lists padded to multiples of 32 slots (host work and uploads; no kernels)
+// interaction lists as slots (host work and uploads; no kernels): each target's list padded to
+// a multiple of 32 slots for the FP64 contraction (one block per target), packed one after the
+// other under mixed precision (the chunk kernel sums per target run), the level's end padded
 static int m2l_fast_plan(pb_ctx* c, PbLevel& lv)
 {
     cudaStream_t fs = c->st2;  // the whole far-field setup runs on the second stream
@@ -1021,15 +1029,20 @@ static int m2l_fast_plan(pb_ctx* c, PbLevel& lv)
     std::vector<int>& soff = lv.h_slot[0];
     std::vector<int>& ssrc = lv.h_slot[1];
     std::vector<int>& stgt = lv.h_slot[2];
+    const bool packed = c->prm.precision == PB_MIXED;
     soff.assign(lv.ncl + 1, 0);
-    for (int k = 0; k < lv.ncl; ++k) soff[k + 1] = soff[k] + ((off[k + 1] - off[k] + 31) / 32) * 32;
-    ssrc.assign(soff[lv.ncl], -1);
-    stgt.assign(soff[lv.ncl], 0);
+    for (int k = 0; k < lv.ncl; ++k) {
+        const int n = off[k + 1] - off[k];
+        soff[k + 1] = soff[k] + (packed ? n : ((n + 31) / 32) * 32);
+    }
+    const int ns = ((soff[lv.ncl] + 31) / 32) * 32;
+    ssrc.assign(ns, -1);
+    stgt.assign(ns, -1);
     for (int k = 0; k < lv.ncl; ++k) {
         for (int t = off[k]; t < off[k + 1]; ++t) ssrc[soff[k] + (t - off[k])] = idx[t];
         for (int t = soff[k]; t < soff[k + 1]; ++t) stgt[t] = k;
     }
-    lv.nslots = soff[lv.ncl];
+    lv.nslots = ns;
     const int T = pb_nterms(lv.p);
     size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
     lv.slot_off = (int*)pb_alloc_on(c, sizeof(int) * (lv.ncl + 1), fs);
@@ -1081,13 +1094,18 @@ static int m2l_fast_launch(pb_ctx* c, PbLevel& lv, int nr, cudaStream_t st)
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
     const long long sstr = (long long)lv.ncl * T, mstr = (long long)lv.nslots * T;
     if constexpr (sizeof(R) == sizeof(float)) {
-        // the kernel reads the source moments itself: no gathered copy
+        // the kernel reads the source moments itself (no gathered copy) and adds into zeroed
+        // local coefficients
+        PB_CUDA(c, cudaMemsetAsync(lv.lam0, 0, sizeof(float) * (size_t)sstr * nr, st));
+        PB_CUDA(c, cudaMemsetAsync(lv.lamk, 0, sizeof(float) * (size_t)sstr * nr, st));
+        const int nch = (int)(lv.nslots / 32);
+        if (nch == 0) return PB_OK;
         size_t smem = (size_t)T * (32 + 33) * sizeof(float);
-        PB_CUDA(c, cudaFuncSetAttribute(k_m2l_tma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_tma<P><<<dim3(lv.ncl, nr, 2), 64, smem, st>>>(lv.ncl, lv.slot_off, lv.slot_src, (const float*)lv.D0,
-                                                             (const float*)lv.Dk, (const float*)lv.sig0,
-                                                             (const float*)lv.sigk, (float*)lv.lam0, (float*)lv.lamk,
-                                                             c->dev_err, sstr);
+        PB_CUDA(c, cudaFuncSetAttribute(k_m2l_seg<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_m2l_seg<P><<<dim3(nch, nr, 2), 64, smem, st>>>(nch, lv.slot_src, lv.slot_tgt, (const float*)lv.D0,
+                                                          (const float*)lv.Dk, (const float*)lv.sig0,
+                                                          (const float*)lv.sigk, (float*)lv.lam0, (float*)lv.lamk,
+                                                          c->dev_err, sstr);
     } else {
         k_m2l_gather<R><<<dim3((unsigned)(lv.nslots / 32), nr), 256, 0, st>>>(
             T, lv.slot_src, (const R*)lv.sig0, (const R*)lv.sigk, (R*)lv.Mg0, (R*)lv.Mgk, sstr, mstr);
