@@ -74,13 +74,14 @@ def args_parse():
     ap.add_argument("--energy", default="treecode", choices=["treecode", "direct"],
                     help="solvation energy of the step: the Cartesian treecode of Section 2.5 or the direct sum")
     ap.add_argument("--theta", type=float, default=0.5, help="treecode MAC parameter")
-    ap.add_argument("--workload", default="molecule", choices=["sphere", "molecule", "batch", "learned", "precond"])
+    ap.add_argument("--workload", default="molecule",
+                    choices=["sphere", "molecule", "batch", "learned", "precond", "linear"])
     ap.add_argument("--train-molecules", type=int, default=48)
     ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--train-atoms", type=int, nargs=2, default=[50, 500], metavar=("MIN", "MAX"),
                     help="training molecules: atom counts log-uniform in [MIN, MAX]")
     ap.add_argument("--atoms", type=int, default=None,
-                    help="molecule size (default 20000 for --workload molecule, 2000 for learned)")
+                    help="molecule size (default 20000 for --workload molecule, 2000 for learned and linear)")
     ap.add_argument("--fp64-budget", type=float, default=60.0,
                     help="seconds of timed FP64-method steps (at most --steps of them, at least one)")
     ap.add_argument("--grid", type=float, default=0.9)
@@ -95,7 +96,7 @@ def args_parse():
                     help="sphere / molecule: choose leaf size and per-level orders with pb_autotune first (untimed)")
     a = ap.parse_args()
     if a.atoms is None:
-        a.atoms = 2000 if a.workload == "learned" else 20000
+        a.atoms = 2000 if a.workload in ("learned", "linear") else 20000
     return a
 
 
@@ -772,6 +773,106 @@ def run_precond(a):
     return 0
 
 
+def run_linear(a):
+    """The piecewise-linear basis (continuous hat functions, Section 2.3) on a protein-like
+    molecule: one step = pb_build_tree + pb_gmres_solve + the solvation energy, vertex unknowns,
+    order-2 regular rule (4 points per element), p = 8, mixed precision, the 2 x 2 vertex-block
+    preconditioner; value = N_elements x products / step time (the default metric's unit). The
+    piecewise-constant step on the same molecule and rule is timed beside it. Roofline: the
+    near field k_near_p1, 16 point pairs per near element pair x 75 flops."""
+    rank, world, local = dist_setup(a.gpus)
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_2110_13778_gb300 import build, pb
+
+    build.build()
+    mesh = workload(kind="molecule", atoms=a.atoms, h=a.grid, clean=not a.raw_mesh)
+    N, nv = mesh.nt, mesh.verts.shape[0]
+    prec = pb.PB_MIXED if a.precision == "mixed" else pb.PB_FP64
+    stream = torch.cuda.current_stream().cuda_stream
+    qr = 2
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def arm(basis):
+        prm = pb.params(eps_in=1.0, eps_out=80.0, kappa=0.1257, eta0=a.eta0, leaf_size=a.leaf, p=a.p, qs=3,
+                        precision=prec, precond=pb.PB_PRECOND_BLOCK, qr=qr, basis=basis)
+        cx = pb.pb_create(prm, stream)
+        pb.pb_mesh_upload(cx, mesh.verts, mesh.tris, mesh.qpos, mesh.q)
+        n = 2 * (nv if basis == pb.PB_BASIS_LINEAR else N)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+
+        def step():
+            pb.pb_build_tree(cx)
+            info = pb.pb_gmres_solve(cx, x, tol=a.tol, max_iter=2000, restart=a.restart)
+            return info, pb.pb_solvation_energy(cx, x)
+
+        for _ in range(a.warmup):
+            step()
+        torch.cuda.synchronize()
+        pb.pb_set_timing(cx, 1)
+        n0 = pb.pb_get_launch_count(cx)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times, mv, its = [], 0, []
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0.record()
+            info, E = step()
+            ev1.record()
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+            mv += info.matvecs
+            its.append(info.iterations)
+        phases = pb.pb_get_timing(cx)
+        launches = pb.pb_get_launch_count(cx) - n0
+        pb.pb_set_timing(cx, 0)
+        stats = pb.pb_get_tree_stats(cx)
+        pb.pb_destroy(cx)
+        return {"times": times, "matvecs": mv, "iterations": its, "energy": E, "phases": phases, "launches": launches,
+                "stats": stats}
+
+    with ClockSampler(local) as clk:
+        lin = arm(pb.PB_BASIS_LINEAR)
+    const = arm(pb.PB_BASIS_CONSTANT)
+    t_max = dist_max(sum(lin["times"]) / 1e3, world)
+    value = world * N * lin["matvecs"] / t_max / 1e6
+    pk = peaks(clk.summary().get("sm_max_mhz"), pb.pb_measure_alu_peaks(stream))
+    near_ms, near_n = lin["phases"]["near"]
+    avg = near_ms / max(near_n, 1)
+    pairs = lin["stats"]["near_pairs"] - N  # the identical pair is stored whole with the touching blocks
+    flops = pairs * (qr * qr) ** 2 * FLOPS_PER_NEAR_PAIR
+    peak = pk["fp32_tflops"] if prec == pb.PB_MIXED else pk["fp64_tflops"]
+    ach = flops / (avg * 1e-3) / 1e12
+    if rank != 0:
+        return 0
+    print(json.dumps({
+        "metric": "piecewise-linear FMM matvec Melem/s (whole solve: setup + GMRES to 1e-6 + energy)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": float(np.mean(lin["times"])), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == pb.PB_MIXED else "f64", "data": "synthetic", "clocks": clk.summary(),
+        "gpu_launches": lin["launches"], "gmres_iterations": lin["iterations"],
+        "matvecs_per_step": lin["matvecs"] / a.steps, "energy_kcal": lin["energy"],
+        "phases_ms_per_step": {k: v[0] / a.steps for k, v in lin["phases"].items() if v[1]},
+        "roofline": {"kernel": "k_near_p1", "avg_launch_ms": avg, "bound": "alu", "achieved": ach, "peak": peak,
+                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                     "work_per_launch": f"{pairs} element pairs x {(qr * qr) ** 2} point pairs x "
+                                        f"{FLOPS_PER_NEAR_PAIR} flops",
+                     "peak_source": pk["alu_source"]},
+        "piecewise_constant": {"ms_per_step": float(np.mean(const["times"])), "gmres_iterations": const["iterations"],
+                               "energy_kcal": const["energy"],
+                               "value": world * N * const["matvecs"] / dist_max(sum(const["times"]) / 1e3, world)
+                               / 1e6},
+        "config": {"workload": f"protein-like molecule: {a.atoms}-atom self-avoiding walk, Gaussian isosurface at 1.0 "
+                               f"on a {a.grid} A grid, {N} triangles, {nv} vertices, {mesh.nc} charges",
+                   "basis": "continuous piecewise-linear (hat functions at the vertices)", "qr": qr, "p": a.p,
+                   "eta0": a.eta0, "leaf_size": a.leaf, "precision": a.precision,
+                   "precond": "2 x 2 vertex blocks of the exact diagonal",
+                   "gmres": f"GMRES({a.restart}) tol {a.tol}",
+                   "l2": "flushed between steps (256 MiB write, outside the timed events)"}}))
+    return 0
+
+
 def run_learned(a):
     """Learned warm start against a zero start, and both against plain FP64 from zero.
 
@@ -878,6 +979,8 @@ def main():
         return run_learned(a)
     if a.workload == "precond":
         return run_precond(a)
+    if a.workload == "linear":
+        return run_linear(a)
     return run_ours(a)
 
 

@@ -75,7 +75,19 @@ typedef struct pb_params {
                         point), 2..4 = q^2 points per element (collapsed Gauss product rule, exact
                         to total degree 2q - 1). Orders above 1 support single right-hand sides
                         (not pb_solve_states mode 2 or pb_batch_solve_states) */
+    int basis;       /* PB_BASIS_CONSTANT (0, piecewise constant, one pair of unknowns per element)
+                        or PB_BASIS_LINEAR (continuous piecewise-linear hat functions S^1_h of
+                        Section 2.3, eqlinearfcn / eqglinearcfcn: one pair per vertex; needs
+                        qr 2..4). Under PB_BASIS_LINEAR the vectors of pb_matvec, pb_rhs,
+                        pb_precond_apply, pb_gmres_solve and pb_solvation_energy have 2 nv
+                        entries [phi at the vertices; dphi/dn at the vertices] in the uploaded
+                        vertex order, the preconditioner is the 2 x 2 block diagonal of the vertex
+                        system (exact entries), and the several-vector, batched, treecode and
+                        learned-start calls are rejected with PB_ERR_ARG */
 } pb_params;
+
+#define PB_BASIS_CONSTANT 0
+#define PB_BASIS_LINEAR 1
 
 /* Float-float ("double-single", ~1e-13 relative) evaluates every step of the singular
  * quadrature on the FP32 pipe, whose rate on this GPU is 64 times the FP64 rate. */

@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "libpb.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["pb_api.cu", "tree.cu", "singular.cu", "nearfield.cu", "farfield.cu", "precond.cu", "krylov.cu",
-           "noalloc.cu", "mlp.cu", "probe.cu", "autotune.cu", "batch.cu", "regular.cu", "radix.cu"]
+           "noalloc.cu", "mlp.cu", "probe.cu", "autotune.cu", "batch.cu", "regular.cu", "radix.cu", "linear.cu"]
 
 
 def nvcc():

@@ -93,6 +93,7 @@ extern "C" int pb_autotune(pb_ctx* c, double tol, int matvecs_per_solve, int nrh
     if (!c->verts) return pb_fail(c, PB_ERR_STATE, "autotune before mesh_upload");
     if (!(tol > 0) || matvecs_per_solve < 1 || nrhs < 1 || nrhs > PB_MAX_RHS || !out)
         return pb_fail(c, PB_ERR_ARG, "autotune: bad arguments");
+    if (c->prm.basis != PB_BASIS_CONSTANT) return pb_fail(c, PB_ERR_ARG, "autotune: piecewise-constant basis only");
     const pb_params keep = c->prm;
     c->p_level_L = -1;  // candidates use one order on every level
     const long long n = 2LL * c->nt;

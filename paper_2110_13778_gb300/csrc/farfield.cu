@@ -698,22 +698,27 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phas
 // coalesced load and a shuffle per row), one coalesced row per source, into shared memory rows
 // of 33 words (conflict-free in both directions). Warp w accumulates its half of the local
 // coefficients (M2LWarp<P, w>: equal FMA counts, moments held in registers a block at a time).
-// After the chunk, the lanes' coefficients are summed per target run (consecutive lanes with
-// the same target), scaled by 1/a! and added into the local coefficients, which the caller
-// zeroes first (FP32 atomics: the order of the additions varies from run to run).
+// After the chunk, the lanes' coefficients are summed per run of lanes with the same target and
+// scaled by 1/a!: a target whose list lies inside the chunk is written directly; the run that
+// opens the chunk and the run that closes it, when their target's list crosses the chunk's
+// edge, go to the staging rows part[2 k] and part[2 k + 1], which k_m2l_runs adds up per
+// target in chunk order. No atomics: the result does not depend on scheduling.
 template <int P>
-__global__ void __launch_bounds__(64, 1) k_m2l_seg(int nch, const int* __restrict__ ssrc, const int* __restrict__ stgt,
+__global__ void __launch_bounds__(64, 1) k_m2l_seg(int nch, const int* __restrict__ soff,
+                                                   const int* __restrict__ ssrc, const int* __restrict__ stgt,
                                                    const float* __restrict__ D0, const float* __restrict__ Dk,
                                                    const float* __restrict__ s0, const float* __restrict__ sk,
                                                    float* __restrict__ l0, float* __restrict__ lk,
+                                                   float* __restrict__ p0, float* __restrict__ pk,
                                                    int* __restrict__ err, long long sstr)
 {
     // right-hand side blockIdx.y: the same derivative tables, its own moments
     const int kern = blockIdx.z;
     const float* D = kern ? Dk : D0;
+    constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
     const float* sig = (kern ? sk : s0) + blockIdx.y * sstr;
     float* out = (kern ? lk : l0) + blockIdx.y * sstr;
-    constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
+    float* part = (kern ? pk : p0) + (size_t)blockIdx.y * nch * 2 * T;
     constexpr unsigned CH = T * 32 * sizeof(float);  // bytes of one derivative block (multiple of 16)
     constexpr int NL = M2LWarp<P, 0>::n > M2LWarp<P, 1>::n ? M2LWarp<P, 0>::n : M2LWarp<P, 1>::n;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -765,21 +770,51 @@ __global__ void __launch_bounds__(64, 1) k_m2l_seg(int nch, const int* __restric
         for (int i = 0; i < M2LWarp<P, 1>::n; ++i) scratch[M2LWarp<P, 1>::alpha(i) * 33 + lane] = L[i];
     }
     __syncthreads();
+    const long long s0k = 32LL * k;  // first slot of the chunk
     for (int i = threadIdx.x; i < T; i += 64) {
         const float sc = c_ifact[i];
         float acc = 0.f;
-        int cur = tg[0];
+        int l0r = 0;
         for (int l = 0; l < 32; ++l) {
-            const int t = tg[l];
-            if (t != cur) {
-                if (cur >= 0) atomicAdd(&out[(size_t)cur * T + i], acc * sc);
-                acc = 0.f;
-                cur = t;
-            }
             acc += scratch[i * 33 + l];
+            const int t = tg[l];
+            if (l == 31 || tg[l + 1] != t) {  // the run [l0r, l] of target t ends here
+                if (t >= 0) {
+                    const bool opens = l0r == 0 && soff[t] < s0k;        // began in an earlier chunk
+                    const bool closes = l == 31 && soff[t + 1] > s0k + 32;  // goes on in a later one
+                    if (opens) part[(2LL * k) * T + i] = acc * sc;
+                    if (closes) part[(2LL * k + 1) * T + i] = acc * sc;
+                    if (!opens && !closes) out[(size_t)t * T + i] = acc * sc;
+                }
+                acc = 0.f;
+                l0r = l + 1;
+            }
         }
-        if (cur >= 0) atomicAdd(&out[(size_t)cur * T + i], acc * sc);
     }
+}
+
+// the local coefficients of the targets whose lists cross a chunk edge (the closing run of the
+// first chunk, the opening run of every later one, in chunk order), and zeros for the targets
+// without an interaction
+__global__ void k_m2l_runs(int ncl, int T, int nch, const int* __restrict__ soff, const float* __restrict__ p0,
+                           const float* __restrict__ pk, float* __restrict__ l0, float* __restrict__ lk,
+                           long long sstr)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)ncl * T) return;
+    const int c = (int)(e / T), i = (int)(e % T);
+    const float* part = (blockIdx.z ? pk : p0) + (size_t)blockIdx.y * nch * 2 * T;
+    float* out = (blockIdx.z ? lk : l0) + blockIdx.y * sstr;
+    const int b = soff[c], en = soff[c + 1];
+    if (b == en) {
+        out[e] = 0.f;
+        return;
+    }
+    const int k0 = b >> 5, k1 = (en - 1) >> 5;
+    if (k0 == k1) return;  // written by the chunk kernel
+    float s = part[(2LL * k0 + 1) * T + i];
+    for (int k = k0 + 1; k <= k1; ++k) s += part[(2LL * k) * T + i];
+    out[e] = s;
 }
 
 // FP64 (and fallback): D read from global memory, the moment chunk copied to shared memory.
@@ -1043,6 +1078,11 @@ static int m2l_fast_plan(pb_ctx* c, PbLevel& lv)
         for (int t = soff[k]; t < soff[k + 1]; ++t) stgt[t] = k;
     }
     lv.nslots = ns;
+    if (packed) {  // the chunk kernel's staging rows, one vector (pb_far_reserve grows them)
+        lv.Mp0 = pb_alloc_on(c, sizeof(float) * (size_t)(ns / 32) * 2 * pb_nterms(lv.p), fs);
+        lv.Mpk = pb_alloc_on(c, sizeof(float) * (size_t)(ns / 32) * 2 * pb_nterms(lv.p), fs);
+        if (!lv.Mp0 || !lv.Mpk) return pb_fail(c, PB_ERR_NOMEM, "m2l setup: out of memory");
+    }
     const int T = pb_nterms(lv.p);
     size_t rs = c->prm.precision == PB_MIXED ? sizeof(float) : sizeof(double);
     lv.slot_off = (int*)pb_alloc_on(c, sizeof(int) * (lv.ncl + 1), fs);
@@ -1094,18 +1134,23 @@ static int m2l_fast_launch(pb_ctx* c, PbLevel& lv, int nr, cudaStream_t st)
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
     const long long sstr = (long long)lv.ncl * T, mstr = (long long)lv.nslots * T;
     if constexpr (sizeof(R) == sizeof(float)) {
-        // the kernel reads the source moments itself (no gathered copy) and adds into zeroed
-        // local coefficients
-        PB_CUDA(c, cudaMemsetAsync(lv.lam0, 0, sizeof(float) * (size_t)sstr * nr, st));
-        PB_CUDA(c, cudaMemsetAsync(lv.lamk, 0, sizeof(float) * (size_t)sstr * nr, st));
+        // the kernel reads the source moments itself (no gathered copy); the targets whose
+        // lists cross a chunk edge are summed by a second pass
         const int nch = (int)(lv.nslots / 32);
-        if (nch == 0) return PB_OK;
         size_t smem = (size_t)T * (32 + 33) * sizeof(float);
-        PB_CUDA(c, cudaFuncSetAttribute(k_m2l_seg<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_m2l_seg<P><<<dim3(nch, nr, 2), 64, smem, st>>>(nch, lv.slot_src, lv.slot_tgt, (const float*)lv.D0,
-                                                          (const float*)lv.Dk, (const float*)lv.sig0,
-                                                          (const float*)lv.sigk, (float*)lv.lam0, (float*)lv.lamk,
-                                                          c->dev_err, sstr);
+        if (nch > 0) {
+            PB_CUDA(c, cudaFuncSetAttribute(k_m2l_seg<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_m2l_seg<P><<<dim3(nch, nr, 2), 64, smem, st>>>(nch, lv.slot_off, lv.slot_src, lv.slot_tgt,
+                                                              (const float*)lv.D0, (const float*)lv.Dk,
+                                                              (const float*)lv.sig0, (const float*)lv.sigk,
+                                                              (float*)lv.lam0, (float*)lv.lamk, (float*)lv.Mp0,
+                                                              (float*)lv.Mpk, c->dev_err, sstr);
+            PB_LAUNCH(c);
+        }
+        const long long ne = (long long)lv.ncl * T;
+        k_m2l_runs<<<dim3((unsigned)((ne + 255) / 256), nr, 2), 256, 0, st>>>(
+            lv.ncl, T, nch, lv.slot_off, (const float*)lv.Mp0, (const float*)lv.Mpk, (float*)lv.lam0,
+            (float*)lv.lamk, sstr);
     } else {
         k_m2l_gather<R><<<dim3((unsigned)(lv.nslots / 32), nr), 256, 0, st>>>(
             T, lv.slot_src, (const R*)lv.sig0, (const R*)lv.sigk, (R*)lv.Mg0, (R*)lv.Mgk, sstr, mstr);
@@ -1137,6 +1182,11 @@ int pb_far_reserve(pb_ctx* c, int nr)
             lv.Mg0 = pb_alloc(c, rs * (size_t)lv.nslots * T * nr);
             lv.Mgk = pb_alloc(c, rs * (size_t)lv.nslots * T * nr);
             if (!lv.Mg0 || !lv.Mgk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");
+        }
+        if (lv.D0 && c->prm.precision == PB_MIXED) {  // staging rows of the chunk kernel
+            lv.Mp0 = pb_alloc(c, sizeof(float) * (size_t)(lv.nslots / 32) * 2 * T * nr);
+            lv.Mpk = pb_alloc(c, sizeof(float) * (size_t)(lv.nslots / 32) * 2 * T * nr);
+            if (!lv.Mp0 || !lv.Mpk) return pb_fail(c, PB_ERR_NOMEM, "far field: out of memory");
         }
     }
     c->far_nr = nr;
@@ -1223,7 +1273,7 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream
     {
         PbLevel& lv = c->lev[L];
         const size_t psm = p2m_smem<R>(lv.p);
-        if (pts) {
+        if (pts && xs) {  // (xs == nullptr: the caller has filled the point densities)
             int rc1 = pb_to_points(c, xs, c->xq, st);
             if (rc1) return rc1;
         }

@@ -576,7 +576,7 @@ static int grid_for(long long n) { return (int)std::min<long long>((n + KB - 1) 
 int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max_iter, int restart,
                     pb_solve_info* info, bool x_zero)
 {
-    const long long n = 2LL * c->nt;
+    const long long n = 2LL * c->nu;
     const int m = restart;
     const int G = grid_for(n);
     int rc;
@@ -892,7 +892,7 @@ __global__ void k_dg_start_scale(long long n, const double* __restrict__ small, 
 int pb_gmres_batch_sorted(pb_ctx* c, double* X, const double* B, int nr, double tol, int max_iter, int restart,
                           pb_solve_info* infos)
 {
-    const long long n = 2LL * c->nt;
+    const long long n = 2LL * c->nu;
     const int m = restart;
     const int G = grid_for(n);
     const long long S = (long long)(m + 1) * m + 6 * (m + 2);  // small state per right-hand side
@@ -1449,7 +1449,7 @@ __global__ void k_dg_axpy(long long n, const double* __restrict__ Z, double* __r
 // control blocks
 int pb_dg_reserve(pb_ctx* c, int nr, int m, int nctl)
 {
-    const long long n = 2LL * c->nt;
+    const long long n = 2LL * c->nu;
     const long long S = (long long)(m + 1) * m + 6 * (m + 2);
     if (nr > c->gb_nr || m > c->gb_m) {
         const int nr2 = std::max(nr, c->gb_nr), m2 = std::max(m, c->gb_m);
@@ -1529,7 +1529,7 @@ static bool add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, c
 int pb_dg_append(pb_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, double* X, const double* B,
                  int nr, int m, int start, int ictl, std::vector<cudaGraphNode_t>* leaves, long long cnt[3])
 {
-    const long long n = 2LL * c->nt;
+    const long long n = 2LL * c->nu;
     const int G = grid_for(n);
     const long long S = (long long)(m + 1) * m + 6 * (m + 2);
     const long long vstr = (long long)(m + 1) * n, pstr = (long long)DOT_BLOCKS * (m + 2);

@@ -828,6 +828,7 @@ extern "C" int pb_features(pb_ctx* c, float* F, const double* x, float* T, doubl
     if (!c) return PB_ERR_ARG;
     if (c->dead) return PB_ERR_CUDA;
     if (!c->built) return pb_fail(c, PB_ERR_STATE, "features before build_tree");
+    if (c->prm.basis != PB_BASIS_CONSTANT) return pb_fail(c, PB_ERR_ARG, "features: piecewise-constant basis only");
     if (!F || (!x) != (!T)) return pb_fail(c, PB_ERR_ARG, "features: F is required, x and T go together");
     PoolTmp stats(c, sizeof(double) * NSTAT);
     if (!stats.p) return pb_fail(c, PB_ERR_NOMEM, "features: out of memory");
@@ -855,6 +856,7 @@ extern "C" int pb_learned_guess(pb_ctx* c, pb_mlp* m, double* x)
     if (!c || !m || !x) return PB_ERR_ARG;
     if (c->dead) return PB_ERR_CUDA;
     if (!c->built) return pb_fail(c, PB_ERR_STATE, "learned guess before build_tree");
+    if (c->prm.basis != PB_BASIS_CONSTANT) return pb_fail(c, PB_ERR_ARG, "learned guess: piecewise-constant basis only");
     if (m->nin != NFEAT || m->nout != 2) return pb_fail(c, PB_ERR_ARG, "learned guess: network must map 18 -> 2");
     const int nt = c->nt;
     PoolTmp F(c, sizeof(float) * (size_t)nt * NFEAT), Y(c, sizeof(float) * (size_t)nt * 2),

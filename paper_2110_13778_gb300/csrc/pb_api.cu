@@ -67,6 +67,8 @@ static void pb_free_build(pb_ctx* c)
     c->pts_p = c->pts_n = nullptr;
     c->begin_q = nullptr;
     c->xq = c->yq = nullptr;
+    c->p1_voff = c->p1_vlist = nullptr;
+    c->p1_corr = c->p1_diag = c->p1_pinv = c->p1_yqn = c->p1_yl = nullptr;
     c->dgVcur = nullptr;
     c->dgctl = nullptr;
     c->dg_nr = c->dg_nctl = 0;
@@ -103,6 +105,8 @@ extern "C" int pb_create(const pb_params* prm, void* stream, pb_ctx** out)
     if (prm->precond < PB_PRECOND_NONE || prm->precond > PB_PRECOND_BLOCK) return PB_ERR_ARG;
     if (prm->pc_block != 0 && (prm->pc_block < 8 || prm->pc_block > 96)) return PB_ERR_ARG;
     if (prm->qr < 0 || prm->qr > 4) return PB_ERR_ARG;
+    if (prm->basis != PB_BASIS_CONSTANT && prm->basis != PB_BASIS_LINEAR) return PB_ERR_ARG;
+    if (prm->basis == PB_BASIS_LINEAR && prm->qr < 2) return PB_ERR_ARG;  // the points carry the linear functions
     pb_ctx* c = new pb_ctx();
     c->prm = *prm;
     c->st = (cudaStream_t)stream;
@@ -247,6 +251,7 @@ extern "C" int pb_build_tree(pb_ctx* c)
     if (!c->dev_err) return pb_fail(c, PB_ERR_NOMEM, "build_tree: out of memory");
     pb_tic(c, PB_T_TREE);
     if ((rc = pb_geometry_and_tree(c))) return rc;
+    c->nu = c->prm.basis == PB_BASIS_LINEAR ? c->nv : c->nt;
     if ((rc = pb_regular_setup(c))) return rc;
     pb_toc(c, PB_T_TREE);
     // Everything that reads tree data back to the host is planned first; then the singular
@@ -255,19 +260,20 @@ extern "C" int pb_build_tree(pb_ctx* c)
     // the preconditioner's factorisation (first stream), whose block inversions leave most of
     // each SM free; the streams are joined at the end.
     if ((rc = pb_near_setup(c))) return rc;
-    if ((rc = pb_precond_plan(c))) return rc;
+    const bool linear = c->prm.basis == PB_BASIS_LINEAR;
+    if (!linear && (rc = pb_precond_plan(c))) return rc;
     PB_CUDA(c, cudaEventRecord(c->ev_tree, c->st));
     pb_tic(c, PB_T_SINGULAR);
     if ((rc = pb_touching_and_singular(c))) return rc;
-    if ((rc = pb_regular_corrections(c))) return rc;
+    if ((rc = linear ? pb_p1_setup(c) : pb_regular_corrections(c))) return rc;
     pb_toc(c, PB_T_SINGULAR);
     PB_CUDA(c, cudaEventRecord(c->ev_sing, c->st));
     if ((rc = pb_far_setup(c))) return rc;  // times its table kernels as PB_T_FARSETUP
     pb_tic(c, PB_T_PCBUILD);
-    if ((rc = pb_precond_factor(c))) return rc;
+    if (!linear && (rc = pb_precond_factor(c))) return rc;
     pb_toc(c, PB_T_PCBUILD);
     PB_CUDA(c, cudaStreamWaitEvent(c->st, c->ev_join, 0));
-    size_t n2 = 2 * (size_t)c->nt;
+    size_t n2 = 2 * (size_t)std::max(c->nt, c->nv);  // element or vertex unknowns
     c->xs = (double*)pb_alloc(c, sizeof(double) * n2);
     c->ys = (double*)pb_alloc(c, sizeof(double) * n2);
     c->ws = (double*)pb_alloc(c, sizeof(double) * n2);
@@ -311,6 +317,10 @@ __global__ void k_scatter(int n, const int* __restrict__ order, const double* __
 
 int pb_gather(pb_ctx* c, const double* x, double* xs)
 {
+    if (c->prm.basis == PB_BASIS_LINEAR) {  // vertex vectors keep the uploaded order
+        PB_CUDA(c, cudaMemcpyAsync(xs, x, sizeof(double) * 2 * (size_t)c->nv, cudaMemcpyDeviceToDevice, c->st));
+        return PB_OK;
+    }
     int n = c->nt;
     k_gather<<<(n + 255) / 256, 256, 0, c->st>>>(n, c->order, x, xs);
     PB_LAUNCH(c);
@@ -319,6 +329,10 @@ int pb_gather(pb_ctx* c, const double* x, double* xs)
 
 int pb_scatter(pb_ctx* c, const double* xs, double* x)
 {
+    if (c->prm.basis == PB_BASIS_LINEAR) {
+        PB_CUDA(c, cudaMemcpyAsync(x, xs, sizeof(double) * 2 * (size_t)c->nv, cudaMemcpyDeviceToDevice, c->st));
+        return PB_OK;
+    }
     int n = c->nt;
     k_scatter<<<(n + 255) / 256, 256, 0, c->st>>>(n, c->order, xs, x);
     PB_LAUNCH(c);
@@ -333,7 +347,7 @@ int pb_matvec_reserve(pb_ctx* c, int nr)
     int rc;
     if ((rc = pb_far_reserve(c, nr))) return rc;
     if (nr > c->yfar_nr) {
-        c->yfar = (double*)pb_alloc(c, sizeof(double) * 2 * (size_t)c->nt * nr);
+        c->yfar = (double*)pb_alloc(c, sizeof(double) * 2 * (size_t)std::max(c->nt, c->nv) * nr);
         if (!c->yfar) return pb_fail(c, PB_ERR_NOMEM, "matvec: out of memory");
         c->yfar_nr = nr;
     }
@@ -383,10 +397,21 @@ static int matvec_parts(pb_ctx* c, const double* xs, double* ys, int nr, int whi
     return PB_OK;
 }
 
-int pb_matvec_sorted(pb_ctx* c, const double* xs, double* ys, int which) { return matvec_parts(c, xs, ys, 1, which); }
+int pb_matvec_sorted(pb_ctx* c, const double* xs, double* ys, int which)
+{
+    if (c->prm.basis == PB_BASIS_LINEAR) return pb_p1_matvec(c, xs, ys);
+    return matvec_parts(c, xs, ys, 1, which);
+}
 
 // nr products at once: xs and ys hold nr vectors of 2 nt in tree order
-int pb_matvec_sorted_multi(pb_ctx* c, const double* xs, double* ys, int nr) { return matvec_parts(c, xs, ys, nr, 0); }
+int pb_matvec_sorted_multi(pb_ctx* c, const double* xs, double* ys, int nr)
+{
+    if (c->prm.basis == PB_BASIS_LINEAR) {
+        if (nr != 1) return pb_fail(c, PB_ERR_ARG, "piecewise-linear basis: one vector at a time");
+        return pb_p1_matvec(c, xs, ys);
+    }
+    return matvec_parts(c, xs, ys, nr, 0);
+}
 
 // tree-ordered work vectors for nr right-hand sides (build lifetime, grown on demand)
 static int reserve_multi(pb_ctx* c, int nr)
@@ -405,6 +430,7 @@ extern "C" int pb_matvec_multi(pb_ctx* c, const double* X, double* Y, int nr)
     PB_ALIVE(c);
     if (!c->built) return pb_fail(c, PB_ERR_STATE, "matvec before build_tree");
     if (!X || !Y || X == Y || nr < 1 || nr > PB_MAX_RHS) return pb_fail(c, PB_ERR_ARG, "matvec_multi: bad arguments");
+    if (c->prm.basis != PB_BASIS_CONSTANT) return pb_fail(c, PB_ERR_ARG, "matvec_multi: piecewise-constant basis only");
     int rc;
     if ((rc = reserve_multi(c, nr))) return rc;
     const int n = c->nt;
@@ -421,6 +447,8 @@ extern "C" int pb_matvec_part(pb_ctx* c, const double* x, double* y, int which)
     PB_ALIVE(c);
     if (!c->built) return pb_fail(c, PB_ERR_STATE, "matvec before build_tree");
     if (!x || !y || x == y || which < 0 || which > 2) return pb_fail(c, PB_ERR_ARG, "matvec: bad arguments");
+    if (which != 0 && c->prm.basis != PB_BASIS_CONSTANT)
+        return pb_fail(c, PB_ERR_ARG, "matvec_part: piecewise-constant basis only");
     int rc;
     if ((rc = pb_gather(c, x, c->xs))) return rc;
     if ((rc = pb_matvec_sorted(c, c->xs, c->ys, which))) return rc;
@@ -463,7 +491,7 @@ extern "C" int pb_gmres_solve(pb_ctx* c, double* x, double tol, int max_iter, in
     if (use_x0) {
         if ((rc = pb_gather(c, x, c->xs))) return rc;
     } else {
-        PB_CUDA(c, cudaMemsetAsync(c->xs, 0, sizeof(double) * 2 * c->nt, c->st));
+        PB_CUDA(c, cudaMemsetAsync(c->xs, 0, sizeof(double) * 2 * (size_t)c->nu, c->st));
     }
     pb_solve_info loc;
     // one graph launch with the stopping test on the device; with per-phase timing enabled (or
@@ -493,6 +521,7 @@ extern "C" int pb_solve_states(pb_ctx* c, const double* q, int nrhs, double* X, 
     if (!c->built) return pb_fail(c, PB_ERR_STATE, "solve_states before build_tree");
     if (!q || !X || nrhs < 1 || !(tol > 0) || max_iter < 1 || restart < 1 || restart > 200 || warm < 0 || warm > 2)
         return pb_fail(c, PB_ERR_ARG, "solve_states: bad arguments");
+    if (c->prm.basis != PB_BASIS_CONSTANT) return pb_fail(c, PB_ERR_ARG, "solve_states: piecewise-constant basis only");
     for (long long k = 0; k < (long long)nrhs * c->nc; ++k)
         if (!isfinite(q[k])) return pb_fail(c, PB_ERR_MESH, "charge state value %lld not finite", k);
     if (warm == 2 && c->q2 > 1)
@@ -586,6 +615,7 @@ extern "C" int pb_solvation_energy_treecode(pb_ctx* c, const double* x, double t
 {
     PB_ALIVE(c);
     if (!c->built) return pb_fail(c, PB_ERR_STATE, "energy before build_tree");
+    if (c->prm.basis != PB_BASIS_CONSTANT) return pb_fail(c, PB_ERR_ARG, "treecode energy: piecewise-constant basis only");
     if (!x || !E || !(theta > 0) || !(theta < 1)) return pb_fail(c, PB_ERR_ARG, "treecode energy: bad argument");
     int rc;
     if ((rc = pb_gather(c, x, c->xs))) return rc;

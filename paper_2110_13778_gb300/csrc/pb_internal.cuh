@@ -53,6 +53,8 @@ struct PbLevel {
     void* Dk = nullptr;      // derivatives of Gk
     void* Mg0 = nullptr;     // scaled source moments gathered into the slot layout (per product)
     void* Mgk = nullptr;
+    void* Mp0 = nullptr;     // mixed MtL: the sums of the runs that cross a chunk edge, [nr][chunk][2][T]
+    void* Mpk = nullptr;
     int* slot_tgt = nullptr; // [nslots] target cluster of each slot (table setup)
     int* slot_mirror = nullptr;  // [nslots] slot of the reversed pair (table setup)
     std::vector<int> h_slot[3];  // host sources of slot_off, slot_src, slot_tgt (kept for the async uploads)
@@ -190,6 +192,18 @@ struct pb_ctx {
     int* begin_q = nullptr;
     double* xq = nullptr;
     double* yq = nullptr;
+    // piecewise-linear basis: unknowns per half (nt, or nv under PB_BASIS_LINEAR); the vertex
+    // lists (for each vertex its element corners 3 k + a, sorted), per touching pair the 4 x 3 x
+    // 3 blocks exact minus the order-q rule, the exact vertex diagonal (4 per vertex), the 2 x 2
+    // inverses of the preconditioner and the near field's work arrays
+    int nu = 0;
+    int* p1_voff = nullptr;
+    int* p1_vlist = nullptr;
+    double* p1_corr = nullptr;
+    double* p1_diag = nullptr;
+    double* p1_pinv = nullptr;
+    double* p1_yqn = nullptr;
+    double* p1_yl = nullptr;
     double* bE = nullptr;         // energies of the states of a batched multi-molecule solve (device)
     int bE_n = 0;
     double* hscal = nullptr;      // pinned host scalars
@@ -291,6 +305,13 @@ int pb_regular_setup(pb_ctx* c);        // points (after the tree)
 int pb_regular_corrections(pb_ctx* c);  // corrections: exact - order-q rule (after the singular pass)
 int pb_near_q_apply(pb_ctx* c, const double* xs, double* ys);
 int pb_to_points(pb_ctx* c, const double* xs, double* xq, cudaStream_t st);
+// linear.cu: the piecewise-linear basis (set-up after the singular pass; product, preconditioner)
+int pb_p1_setup(pb_ctx* c);
+void pb_triangle_rule(int q, double* e1, double* e2, double* w);  // regular.cu
+int pb_p1_matvec(pb_ctx* c, const double* x, double* y);
+int pb_p1_precond(pb_ctx* c, const double* r, double* z);
+int pb_p1_to_points(pb_ctx* c, const double* x, double* xq, cudaStream_t st);
+int pb_p1_from_points(pb_ctx* c, const double* yq, double* y, int add, cudaStream_t st);
 int pb_from_points(pb_ctx* c, const double* yq, double* ys, int add, cudaStream_t st);
 int pb_energy_states_queue(pb_ctx* c, const double* Q, const double* X, int nr, double* Edev);  // nr <= 16
 int pb_rhs_sorted(pb_ctx* c, double* bs);                          // krylov.cu

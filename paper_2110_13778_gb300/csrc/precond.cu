@@ -526,6 +526,13 @@ int pb_precond_factor(pb_ctx* c)
 // z_q = M^-1 r_q for nr vectors r_q = r + q rstr, z_q = z + q zstr
 int pb_precond_apply_multi(pb_ctx* c, const double* r, long long rstr, double* z, long long zstr, int nr)
 {
+    if (c->prm.basis == PB_BASIS_LINEAR) {
+        for (int q = 0; q < nr; ++q) {
+            int rc = pb_p1_precond(c, r + q * rstr, z + q * zstr);
+            if (rc) return rc;
+        }
+        return PB_OK;
+    }
     const int nt = c->nt;
     pb_tic(c, PB_T_PRECOND);
     if (c->prm.precond == PB_PRECOND_BLOCK) {
@@ -559,4 +566,8 @@ int pb_precond_apply_multi(pb_ctx* c, const double* r, long long rstr, double* z
     return PB_OK;
 }
 
-int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z) { return pb_precond_apply_multi(c, r, 0, z, 0, 1); }
+int pb_precond_apply_sorted(pb_ctx* c, const double* r, double* z)
+{
+    if (c->prm.basis == PB_BASIS_LINEAR) return pb_p1_precond(c, r, z);
+    return pb_precond_apply_multi(c, r, 0, z, 0, 1);
+}

@@ -277,6 +277,7 @@ int pb_near_q_apply(pb_ctx* c, const double* xs, double* ys)
 
 int pb_to_points(pb_ctx* c, const double* xs, double* xq, cudaStream_t st)
 {
+    if (c->prm.basis == PB_BASIS_LINEAR) return pb_p1_to_points(c, xs, xq, st);
     const long long np = (long long)c->nt * c->q2;
     k_to_points<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(c->nt, c->q2, xs, xq);
     PB_LAUNCH(c);
@@ -285,6 +286,7 @@ int pb_to_points(pb_ctx* c, const double* xs, double* xq, cudaStream_t st)
 
 int pb_from_points(pb_ctx* c, const double* yq, double* ys, int add, cudaStream_t st)
 {
+    if (c->prm.basis == PB_BASIS_LINEAR) return pb_p1_from_points(c, yq, ys, add, st);
     k_from_points<<<(c->nt + 255) / 256, 256, 0, st>>>(c->nt, c->q2, yq, ys, add);
     PB_LAUNCH(c);
     return PB_OK;

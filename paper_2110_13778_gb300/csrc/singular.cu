@@ -305,6 +305,133 @@ __global__ void __launch_bounds__(256) k_singular(long long npairs, int nt, cons
     }
 }
 
+// ---------- piecewise-linear basis (continuous hat functions, Section 2.3) ----------
+// The same Sauter-Schwab quadrature weighted by the linear functions of both triangles: at the
+// reference point (e1, e2) of a triangle laid out as P0 + e1 (P1 - P0) + e2 (P2 - P1) they are
+// 1 - e1, e1 - e2 and e2 (eqlinearfcn), the weights of P0, P1 and P2. One warp per unordered
+// touching pair, laid out from the triangle with the smaller element index as above; all six
+// kernel parts and all sub-maps (the identical pair's x <-> y pairing of sub-maps does not
+// carry over to the weighted integrand). The warp writes the 3 x 3 blocks of (k, j) and
+// (j, k), corner indices in uploaded corner order: corr1[36 t + 9 m + 3 a + b] for kernel K_m,
+// target corner a, source corner b; and adds every entry whose two corners are the same vertex
+// into diag[4 v + m] (FP64 atomics: the exact diagonal of the vertex system).
+__global__ void __launch_bounds__(256) k_singular_p1(long long npairs, int nt, const int* __restrict__ toff,
+                                                     const int* __restrict__ tj, const int* __restrict__ stris,
+                                                     const int* __restrict__ order, const double* __restrict__ V,
+                                                     const double4_32a* __restrict__ ep,
+                                                     const double4_32a* __restrict__ en, int qs, double eps,
+                                                     double kappa, double* __restrict__ corr1,
+                                                     double* __restrict__ diag)
+{
+    long long pair = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x & 31;
+    if (pair >= npairs) return;
+    int lo = 0, hi = nt;
+    while (hi - lo > 1) {
+        int m = (lo + hi) / 2;
+        if (toff[m] <= pair) lo = m;
+        else hi = m;
+    }
+    int k = lo, j = tj[pair];
+    if (order[k] > order[j]) return;
+    int ti[3] = {stris[3 * k], stris[3 * k + 1], stris[3 * k + 2]};
+    int tjv[3] = {stris[3 * j], stris[3 * j + 1], stris[3 * j + 2]};
+    // shared vertices first (in k's corner order), then the others; ci / cj: the corner index
+    // of each laid-out position
+    int ci[3], cj[3], ns = 0;
+    if (k == j) {
+        ns = 3;
+        for (int a = 0; a < 3; ++a) ci[a] = cj[a] = a;
+    } else {
+        int usedi[3] = {0, 0, 0}, usedj[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (ti[a] == tjv[b]) {
+                    ci[ns] = a;
+                    cj[ns] = b;
+                    usedi[a] = usedj[b] = 1;
+                    ++ns;
+                }
+        int p = ns, q = ns;
+        for (int a = 0; a < 3; ++a)
+            if (!usedi[a]) ci[p++] = a;
+        for (int b = 0; b < 3; ++b)
+            if (!usedj[b]) cj[q++] = b;
+    }
+    double P[3][3], Q[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int d = 0; d < 3; ++d) {
+            P[a][d] = V[3 * ti[ci[a]] + d];
+            Q[a][d] = V[3 * tjv[cj[a]] + d];
+        }
+    const double4_32a pi = ep[k], pj = ep[j], ni = en[k], nj = en[j];
+    const int nsub = ns == 3 ? 6 : (ns == 2 ? 5 : 2);
+    double acc[6][9];
+    for (int m = 0; m < 6; ++m)
+        for (int e = 0; e < 9; ++e) acc[m][e] = 0.0;
+    const int npts = qs * qs * qs * qs;
+    double eP[2][3], eQ[2][3], d0[3];
+    for (int e = 0; e < 3; ++e) {
+        eP[0][e] = P[1][e] - P[0][e];
+        eP[1][e] = P[2][e] - P[1][e];
+        eQ[0][e] = Q[1][e] - Q[0][e];
+        eQ[1][e] = Q[2][e] - Q[1][e];
+        d0[e] = P[0][e] - Q[0][e];
+    }
+    for (int t = lane; t < npts; t += 32) {
+        int a = t % qs, b = (t / qs) % qs, cc = (t / (qs * qs)) % qs, d = t / (qs * qs * qs);
+        double xi = c_gx[a], h1 = c_gx[b], h2 = c_gx[cc], h3 = c_gx[d];
+        double wq = c_gw[a] * c_gw[b] * c_gw[cc] * c_gw[d];
+        for (int sm = 0; sm < nsub; ++sm) {
+            double xh[2], yh[2];
+            ss_map(ns, sm, xi, h1, h2, h3, xh, yh);
+            const double w = wq * ss_weight(ns, sm, xi, h1, h2);
+            double dv[3];
+            for (int e = 0; e < 3; ++e)
+                dv[e] = d0[e] + xh[0] * eP[0][e] + xh[1] * eP[1][e] - yh[0] * eQ[0][e] - yh[1] * eQ[1][e];
+            double Pt[6];
+            pb_kernel_parts<double>(dv[0], dv[1], dv[2], ni.x, ni.y, ni.z, nj.x, nj.y, nj.z, kappa, Pt);
+            const double lx[3] = {1.0 - xh[0], xh[0] - xh[1], xh[1]};
+            const double ly[3] = {1.0 - yh[0], yh[0] - yh[1], yh[1]};
+            for (int p = 0; p < 3; ++p)
+                for (int r = 0; r < 3; ++r) {
+                    const double wl = w * lx[p] * ly[r];
+                    for (int m = 0; m < 6; ++m) acc[m][3 * p + r] += wl * Pt[m];
+                }
+        }
+    }
+    for (int m = 0; m < 6; ++m)
+        for (int e = 0; e < 9; ++e)
+            for (int o = 16; o > 0; o >>= 1) acc[m][e] += __shfl_xor_sync(0xffffffffu, acc[m][e], o);
+    // lanes 0..8: one laid-out position pair (p, r) each
+    if (lane < 9) {
+        const int p = lane / 3, r = lane % 3;
+        const double jac = (2.0 * pi.w) * (2.0 * pj.w);
+        double A6[6];
+        for (int m = 0; m < 6; ++m) A6[m] = acc[m][lane] * jac;
+        const double inv_eps = 1.0 / eps;
+        const int a = ci[p], b = cj[r];
+        const bool same = ti[a] == tjv[b];
+        // (k, j): target k (corner a), source j (corner b)
+        const double Ikj[4] = {A6[0], eps * A6[3] - A6[2], -A6[4] + A6[5] * inv_eps, A6[1]};
+        for (int m = 0; m < 4; ++m) {
+            corr1[36 * pair + 9 * m + 3 * a + b] = Ikj[m];
+            if (same) atomicAdd(&diag[4LL * ti[a] + m], Ikj[m]);
+        }
+        if (k != j) {
+            // (j, k): target j (corner b), source k (corner a), the normals' roles exchanged
+            const double Ijk[4] = {A6[0], A6[4] - eps * A6[5], A6[2] - A6[3] * inv_eps, A6[1]};
+            int q = toff[j];
+            while (q < toff[j + 1] && tj[q] != k) ++q;
+            if (q < toff[j + 1])
+                for (int m = 0; m < 4; ++m) {
+                    corr1[36LL * q + 9 * m + 3 * b + a] = Ijk[m];
+                    if (same) atomicAdd(&diag[4LL * ti[a] + m], Ijk[m]);
+                }
+        }
+    }
+}
+
 // ---------- the same integrals in float-float arithmetic (mixed precision) ----------
 // Every step of k_singular, carried out in float-float (ff.cuh) on the FP32 pipe: ~1e-13
 // relative instead of FP64's ~1e-16, at a fraction of the FP64 pipe's time. The cube points
@@ -760,6 +887,17 @@ int pb_touching_and_singular(pb_ctx* c)
     PB_CUDA(c, cudaMemcpyToSymbolAsync(c_gx, c->h_up_d.data(), sizeof(gx), 0, cudaMemcpyHostToDevice, c->st));
     PB_CUDA(c, cudaMemcpyToSymbolAsync(c_gw, c->h_up_d.data() + 8, sizeof(gw), 0, cudaMemcpyHostToDevice, c->st));
     double eps = c->prm.eps_out / c->prm.eps_in;
+    if (c->prm.basis == PB_BASIS_LINEAR) {
+        // the vertex system's blocks (FP64); the order-q rule part is taken off afterwards
+        c->p1_corr = (double*)pb_alloc(c, sizeof(double) * 36 * (size_t)(htot + 1));
+        c->p1_diag = (double*)pb_alloc(c, sizeof(double) * 4 * (size_t)(c->nv + 1));
+        if (!c->p1_corr || !c->p1_diag) return pb_fail(c, PB_ERR_NOMEM, "singular: out of memory");
+        k_singular_p1<<<nblk(htot, 8), 256, 0, c->st>>>(htot, nt, c->touch_off, c->touch_j, c->stris, c->order,
+                                                        c->verts, c->e64p, c->e64n, c->prm.qs, eps, c->prm.kappa,
+                                                        c->p1_corr, c->p1_diag);
+        PB_LAUNCH(c);
+        return PB_OK;
+    }
     const int mode = c->prm.singular ? c->prm.singular : (c->prm.precision == PB_MIXED ? PB_SINGULAR_FF : PB_SINGULAR_FP64);
     if (mode == PB_SINGULAR_FP64) {
         k_singular<<<nblk(htot, 8), 256, 0, c->st>>>(htot, nt, c->touch_off, c->touch_j, c->stris, c->order, c->verts,

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libpb.so")
 PB_FP64, PB_MIXED = 0, 1
 PB_PRECOND_NONE, PB_PRECOND_DIAG, PB_PRECOND_BLOCK = 0, 1, 2
 PB_SINGULAR_AUTO, PB_SINGULAR_FP64, PB_SINGULAR_FF = 0, 1, 2
+PB_BASIS_CONSTANT, PB_BASIS_LINEAR = 0, 1
 
 EXPORTS = [
     "pb_create", "pb_destroy", "pb_last_error", "pb_mesh_upload", "pb_set_charges", "pb_build_tree",
@@ -48,7 +49,7 @@ class pb_params(ctypes.Structure):
         ("eta0", ctypes.c_double), ("leaf_size", ctypes.c_int), ("levels", ctypes.c_int),
         ("p", ctypes.c_int), ("adaptive", ctypes.c_int), ("qs", ctypes.c_int),
         ("precision", ctypes.c_int), ("precond", ctypes.c_int), ("singular", ctypes.c_int),
-        ("pc_block", ctypes.c_int), ("qr", ctypes.c_int),
+        ("pc_block", ctypes.c_int), ("qr", ctypes.c_int), ("basis", ctypes.c_int),
     ]
 
 
@@ -148,9 +149,9 @@ def _check(ctx, rc):
 
 
 def params(eps_in=1.0, eps_out=80.0, kappa=0.1257, eta0=0.8, leaf_size=64, levels=0, p=8, adaptive=0, qs=3,
-           precision=PB_FP64, precond=PB_PRECOND_BLOCK, singular=0, pc_block=0, qr=0):
+           precision=PB_FP64, precond=PB_PRECOND_BLOCK, singular=0, pc_block=0, qr=0, basis=0):
     return pb_params(eps_in, eps_out, kappa, eta0, leaf_size, levels, p, adaptive, qs, precision, precond, singular,
-                     pc_block, qr)
+                     pc_block, qr, basis)
 
 
 def pb_create(prm: pb_params, stream=0):
