@@ -294,7 +294,7 @@ TRAFFIC_BYTES = {
     "sphere_l6_p8_leaf64": {"near": 5.791e6, "m2l": None, "singular": 2.0755e7, "pcbuild": None},
     # profiles/traffic_molecule20k_mixed_p8.md: near, the six MtL levels of one product, the
     # singular pass, the three block-inversion classes of one build
-    "molecule_20000_p8_leaf64": {"near": 1.4429e8, "m2l": None, "singular": 1.9656e9, "pcbuild": 4.4812e9},
+    "molecule_20000_p8_leaf64": {"near": 1.4429e8, "m2l": 7.098e8, "singular": 1.9656e9, "pcbuild": 4.4812e9},
 }
 
 

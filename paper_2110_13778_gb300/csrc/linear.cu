@@ -152,9 +152,10 @@ __global__ void k_p1_precond(int nv, const double* __restrict__ pinv, const doub
 // ---------- near field ----------
 // One block per leaf, one warp per target element k, the lanes over the source elements of the
 // leaf's neighbour list (k itself excluded: its block is stored whole with the touching pairs).
-// For every target point a: -W_a sum_j sum_b W_b [K1 dphi_b + K2 phi_b] (first half) and
+// For every target point a: sum_j sum_b W_b [K1 dphi_b + K2 phi_b] (first half) and
 // [K3 dphi_b + K4 phi_b] (second), the kernels in precision R, each source element's sum over
-// its points in R and added in FP64.
+// its points in R and added in FP64. (Under mixed precision with 4 or 16 points per element the
+// pair-tile kernel of the near field computes the same sums instead.)
 template <class R, int Q2>
 __global__ void __launch_bounds__(128) k_near_p1(int nt, const int* __restrict__ begin, const int* __restrict__ noff,
                                                  const int* __restrict__ nidx, const double4_32a* __restrict__ pp,
@@ -202,17 +203,17 @@ __global__ void __launch_bounds__(128) k_near_p1(int nt, const int* __restrict__
         if (lane == 0) {
 #pragma unroll
             for (int a = 0; a < Q2; ++a) {
-                const double wa = pp[(long long)k * Q2 + a].w;
-                yqn[(long long)k * Q2 + a] = -wa * y1[a];
-                yqn[np + (long long)k * Q2 + a] = -wa * y2[a];
+                yqn[(long long)k * Q2 + a] = y1[a];
+                yqn[np + (long long)k * Q2 + a] = y2[a];
             }
         }
     }
 }
 
-// per element corner (k, i), both halves: the near field's points weighed by the corner's
-// linear function, the mass terms and the touching pairs' stored blocks
-__global__ void k_p1_local(int nt, int q2, const double* __restrict__ yqn, const double4_32a* __restrict__ ep,
+// per element corner (k, i), both halves: the near field's point sums weighed by -W_a and the
+// corner's linear function, the mass terms and the touching pairs' stored blocks
+__global__ void k_p1_local(int nt, int q2, const double* __restrict__ yqn, const double4_32a* __restrict__ pp,
+                           const double4_32a* __restrict__ ep,
                            const int* __restrict__ stris, const double* __restrict__ x, int nv,
                            const int* __restrict__ toff, const int* __restrict__ tj,
                            const double* __restrict__ corr1, double eps, double* __restrict__ yl)
@@ -222,7 +223,8 @@ __global__ void k_p1_local(int nt, int q2, const double* __restrict__ yqn, const
     const long long np = (long long)nt * q2;
     double y1[3] = {0, 0, 0}, y2[3] = {0, 0, 0};
     for (int a = 0; a < q2; ++a) {
-        const double u1 = yqn[(long long)k * q2 + a], u2 = yqn[np + (long long)k * q2 + a];
+        const double W = pp[(long long)k * q2 + a].w;
+        const double u1 = -W * yqn[(long long)k * q2 + a], u2 = -W * yqn[np + (long long)k * q2 + a];
         for (int i = 0; i < 3; ++i) {
             y1[i] += c_lam[3 * a + i] * u1;
             y2[i] += c_lam[3 * a + i] * u2;
@@ -357,16 +359,19 @@ int pb_p1_matvec(pb_ctx* c, const double* x, double* y)
     PB_CUDA(c, cudaEventRecord(c->ev_join, c->st2));
     pb_tic(c, PB_T_NEAR);
     const bool mixed = c->prm.precision == PB_MIXED;
-    switch (c->q2) {
+    if (pb_near_points_ok(c)) {
+        if ((rc = pb_near_points_apply(c, nullptr, c->xq, c->p1_yqn))) return rc;
+    } else switch (c->q2) {
         case 4: mixed ? near_p1_launch<float, 4>(c, c->xq, eps) : near_p1_launch<double, 4>(c, c->xq, eps); break;
         case 9: mixed ? near_p1_launch<float, 9>(c, c->xq, eps) : near_p1_launch<double, 9>(c, c->xq, eps); break;
         case 16: mixed ? near_p1_launch<float, 16>(c, c->xq, eps) : near_p1_launch<double, 16>(c, c->xq, eps); break;
         default: return pb_fail(c, PB_ERR_ARG, "piecewise-linear basis: rule of %d points", c->q2);
     }
-    PB_LAUNCH(c);
+    if (!pb_near_points_ok(c)) PB_LAUNCH(c);
     pb_toc(c, PB_T_NEAR);
     pb_tic(c, PB_T_CORR);
-    k_p1_local<<<nblk(c->nt, 128), 128, 0, c->st>>>(c->nt, c->q2, c->p1_yqn, c->e64p, c->stris, x, c->nv, c->touch_off,
+    k_p1_local<<<nblk(c->nt, 128), 128, 0, c->st>>>(c->nt, c->q2, c->p1_yqn, c->pts_p, c->e64p, c->stris, x, c->nv,
+                                                    c->touch_off,
                                                     c->touch_j, c->p1_corr, eps, c->p1_yl);
     PB_LAUNCH(c);
     PB_CUDA(c, cudaStreamWaitEvent(c->st, c->ev_join, 0));

@@ -178,6 +178,10 @@ __device__ __forceinline__ NearTerms near_pair(float4 tp, float4 tn, float4 tl, 
 // meet at the same source). Forward sums of a chunk and reverse sums of a tile are FP32,
 // added into FP64 (atomics for the reverse terms and the final forward sums; ys starts at
 // zero). The tile of A with itself keeps only the forward terms and drops the identical pair.
+// Q2 > 1: the records are the points of a regular rule (Q2 per element, consecutive; Q2 divides
+// 32 and every leaf starts at an element, so no chunk splits an element): the pairs of points of
+// one element are dropped, which can only happen in the tile of a chunk with itself.
+template <int Q2>
 __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nitems, const int4* __restrict__ items,
                                                     const int* __restrict__ tiles, const int* __restrict__ chunk_leaf,
                                                     const int* __restrict__ chunk_first, const int* __restrict__ begin,
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nitems, const 
 #pragma unroll 2
                 for (int s = 0; s < nb; ++s) {
                     // drop the identical pair (the correction's) and padding targets
-                    const bool ok = act && !(diag && m == lane);
+                    const bool ok = act && !(diag && (Q2 == 1 ? m == lane : m / Q2 == lane / Q2));
                     const NearTerms t = near_pair(tp, tn, tl, tphi, tdphi, sbp[wi][m], sbn[wi][m], sbl[wi][m], ok,
                                                   eps, inv_eps, kappa);
                     s1 += t.f1;
@@ -484,7 +488,7 @@ int pb_near_apply(pb_ctx* c, const double* xs, double* ys)
         k_near_pack<<<(nt + 255) / 256, 256, 0, c->st>>>(nt, c->e32p, c->e32n, xs, c->near_sp, c->near_sn);
         PB_LAUNCH(c);
         PB_CUDA(c, cudaMemsetAsync(ys, 0, sizeof(double) * 2 * nt, c->st));
-        k_near_tile<<<(c->near_nitems * 32 + 255) / 256, 256, 0, c->st>>>(
+        k_near_tile<1><<<(c->near_nitems * 32 + 255) / 256, 256, 0, c->st>>>(
             nt, c->near_nitems, c->near_items, c->near_tiles, c->chunk_leaf, c->chunk_first, lv.begin, c->near_sp,
             c->near_sn, c->e32l, eps, c->prm.kappa, ys);
         PB_LAUNCH(c);
@@ -655,6 +659,172 @@ int pb_near_apply_multi(pb_ctx* c, const double* xs, double* ys, int nr)
         r0 += v;
     }
     k_near_finish<<<dim3((nt + 255) / 256, nr), 256, 0, c->st>>>(nt, c->e64p, xs, eps, ys);
+    PB_LAUNCH(c);
+    return PB_OK;
+}
+
+// ---------- the near field on the points of a regular rule (mixed precision) ----------
+// The same pair-tile kernel over the q2 points of every element (q2 = 4 or 16), so the order-q
+// rule's near field (both bases) runs at the element kernel's rate: point chunks of 32 within
+// each leaf's point range, the tiles of the element plan's neighbour lists, FP32 hi/lo point
+// records built once per build.
+__global__ void k_pts32(long long np, const double4_32a* __restrict__ pp, const double4_32a* __restrict__ pn,
+                        float4* __restrict__ p32, float4* __restrict__ l32, float4* __restrict__ n32)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double4_32a x = pp[p], n = pn[p];
+    const float hx = (float)x.x, hy = (float)x.y, hz = (float)x.z;
+    p32[p] = make_float4(hx, hy, hz, (float)x.w);
+    l32[p] = make_float4((float)(x.x - (double)hx), (float)(x.y - (double)hy), (float)(x.z - (double)hz), 0.f);
+    n32[p] = make_float4((float)n.x, (float)n.y, (float)n.z, 0.f);
+}
+
+// point records with densities: W_p times the point's values, from the element values xs
+// (piecewise constant: every point of element p / q2) or from per-point values xq
+__global__ void k_pts_pack(long long np, int q2, int nt, const float4* __restrict__ p32, const float4* __restrict__ n32,
+                           const double4_32a* __restrict__ pp, const double* __restrict__ xs,
+                           const double* __restrict__ xq, float4* __restrict__ sp, float4* __restrict__ sn)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double W = pp[p].w;
+    double u1, u2;
+    if (xq) {
+        u1 = xq[p];
+        u2 = xq[np + p];
+    } else {
+        const int k = (int)(p / q2);
+        u1 = xs[k];
+        u2 = xs[nt + k];
+    }
+    const float4 a = p32[p], b = n32[p];
+    sp[p] = make_float4(a.x, a.y, a.z, (float)(W * u1));
+    sn[p] = make_float4(b.x, b.y, b.z, (float)(W * u2));
+}
+
+// ys[k] = mass - sum over element k's points of W_a y_a (both halves), y the point sums
+__global__ void k_pts_finish_elem(int nt, int q2, const double4_32a* __restrict__ ep,
+                                  const double4_32a* __restrict__ pp, const double* __restrict__ xs,
+                                  const double* __restrict__ ypt, double eps, double* __restrict__ ys)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    const long long np = (long long)nt * q2;
+    double s1 = 0.0, s2 = 0.0;
+    for (int a = 0; a < q2; ++a) {
+        const long long p = (long long)k * q2 + a;
+        const double W = pp[p].w;
+        s1 += W * ypt[p];
+        s2 += W * ypt[np + p];
+    }
+    const double A = ep[k].w;
+    ys[k] = 0.5 * (1.0 + eps) * A * xs[k] - s1;
+    ys[nt + k] = 0.5 * (1.0 + 1.0 / eps) * A * xs[nt + k] - s2;
+}
+
+bool pb_near_points_ok(const pb_ctx* c) { return c->prm.precision == PB_MIXED && (c->q2 == 4 || c->q2 == 16); }
+
+int pb_near_points_setup(pb_ctx* c)
+{
+    if (!pb_near_points_ok(c)) return PB_OK;
+    const PbLevel& lv = c->lev[c->L];
+    const int q2 = c->q2;
+    const long long np = (long long)c->nt * q2;
+    const std::vector<int>& b = c->h_leaf_begin;
+    std::vector<int> cl, cf, tl;
+    std::vector<int4> it;
+    std::vector<int> first_chunk(lv.ncl + 1, 0);
+    for (int k = 0; k < lv.ncl; ++k) {
+        const long long s0 = (long long)b[k] * q2, s1 = (long long)b[k + 1] * q2;
+        for (long long s = s0; s < s1; s += 32) {
+            cl.push_back(k);
+            cf.push_back((int)s);
+        }
+        first_chunk[k + 1] = (int)cl.size();
+    }
+    const std::vector<int>& no = c->h_near_off;
+    const std::vector<int>& ni = c->h_near_idx;
+    for (int k = 0; k < lv.ncl; ++k)
+        for (int a = first_chunk[k]; a < first_chunk[k + 1]; ++a) {
+            int start = (int)tl.size();
+            for (int t = no[k]; t < no[k + 1]; ++t) {
+                const int c2 = ni[t];
+                if (c2 < k) continue;
+                for (int bq = (c2 == k ? a : first_chunk[c2]); bq < first_chunk[c2 + 1]; ++bq) {
+                    tl.push_back(bq);
+                    if ((int)tl.size() - start == NEAR_ITEM) {
+                        it.push_back(make_int4(a, start, (int)tl.size(), 0));
+                        start = (int)tl.size();
+                    }
+                }
+            }
+            if ((int)tl.size() > start) it.push_back(make_int4(a, start, (int)tl.size(), 0));
+        }
+    c->pn_nitems = (int)it.size();
+    c->h_pn_i[0].swap(cl);
+    c->h_pn_i[1].swap(cf);
+    c->h_pn_i[2].swap(tl);
+    c->h_pn_i4.swap(it);
+    c->pn_items = (int4*)pb_alloc(c, sizeof(int4) * (c->h_pn_i4.size() + 1));
+    c->pn_tiles = (int*)pb_alloc(c, sizeof(int) * (c->h_pn_i[2].size() + 1));
+    c->pn_chunk_leaf = (int*)pb_alloc(c, sizeof(int) * (c->h_pn_i[0].size() + 1));
+    c->pn_chunk_first = (int*)pb_alloc(c, sizeof(int) * (c->h_pn_i[1].size() + 1));
+    c->pn_begin = (int*)pb_alloc(c, sizeof(int) * (lv.ncl + 1));
+    c->pn_p32 = (float4*)pb_alloc(c, sizeof(float4) * np);
+    c->pn_l32 = (float4*)pb_alloc(c, sizeof(float4) * np);
+    c->pn_n32 = (float4*)pb_alloc(c, sizeof(float4) * np);
+    c->pn_sp = (float4*)pb_alloc(c, sizeof(float4) * np);
+    c->pn_sn = (float4*)pb_alloc(c, sizeof(float4) * np);
+    c->pn_y = (double*)pb_alloc(c, sizeof(double) * 2 * np);
+    if (!c->pn_items || !c->pn_tiles || !c->pn_chunk_leaf || !c->pn_chunk_first || !c->pn_begin || !c->pn_p32 ||
+        !c->pn_l32 || !c->pn_n32 || !c->pn_sp || !c->pn_sn || !c->pn_y)
+        return pb_fail(c, PB_ERR_NOMEM, "point near field: out of memory");
+    // (the host vectors live in the context until the next build: no synchronisation needed)
+    PB_CUDA(c, cudaMemcpyAsync(c->pn_items, c->h_pn_i4.data(), sizeof(int4) * c->h_pn_i4.size(),
+                               cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(c->pn_tiles, c->h_pn_i[2].data(), sizeof(int) * c->h_pn_i[2].size(),
+                               cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(c->pn_chunk_leaf, c->h_pn_i[0].data(), sizeof(int) * c->h_pn_i[0].size(),
+                               cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(c->pn_chunk_first, c->h_pn_i[1].data(), sizeof(int) * c->h_pn_i[1].size(),
+                               cudaMemcpyHostToDevice, c->st));
+    PB_CUDA(c, cudaMemcpyAsync(c->pn_begin, c->begin_q, sizeof(int) * (lv.ncl + 1), cudaMemcpyDeviceToDevice, c->st));
+    k_pts32<<<(unsigned)((np + 255) / 256), 256, 0, c->st>>>(np, c->pts_p, c->pts_n, c->pn_p32, c->pn_l32, c->pn_n32);
+    PB_LAUNCH(c);
+    return PB_OK;
+}
+
+// ypt (2 np) = per point sum over the near points of other elements of K (W u), in FP64; the
+// densities from element values xs or point values xq (one of them null)
+int pb_near_points_apply(pb_ctx* c, const double* xs, const double* xq, double* ypt)
+{
+    const long long np = (long long)c->nt * c->q2;
+    const double eps = c->prm.eps_out / c->prm.eps_in;
+    k_pts_pack<<<(unsigned)((np + 255) / 256), 256, 0, c->st>>>(np, c->q2, c->nt, c->pn_p32, c->pn_n32, c->pts_p, xs,
+                                                                 xq, c->pn_sp, c->pn_sn);
+    PB_LAUNCH(c);
+    PB_CUDA(c, cudaMemsetAsync(ypt, 0, sizeof(double) * 2 * np, c->st));
+    const unsigned nb = (unsigned)(((long long)c->pn_nitems * 32 + 255) / 256);
+    if (c->q2 == 4)
+        k_near_tile<4><<<nb, 256, 0, c->st>>>((int)np, c->pn_nitems, c->pn_items, c->pn_tiles, c->pn_chunk_leaf,
+                                               c->pn_chunk_first, c->pn_begin, c->pn_sp, c->pn_sn, c->pn_l32, eps,
+                                               c->prm.kappa, ypt);
+    else
+        k_near_tile<16><<<nb, 256, 0, c->st>>>((int)np, c->pn_nitems, c->pn_items, c->pn_tiles, c->pn_chunk_leaf,
+                                                c->pn_chunk_first, c->pn_begin, c->pn_sp, c->pn_sn, c->pn_l32, eps,
+                                                c->prm.kappa, ypt);
+    PB_LAUNCH(c);
+    return PB_OK;
+}
+
+// the piecewise-constant order-q near field with the mass terms from the point tiles
+int pb_near_points_elem(pb_ctx* c, const double* xs, double* ys)
+{
+    int rc;
+    if ((rc = pb_near_points_apply(c, xs, nullptr, c->pn_y))) return rc;
+    const double eps = c->prm.eps_out / c->prm.eps_in;
+    k_pts_finish_elem<<<(c->nt + 255) / 256, 256, 0, c->st>>>(c->nt, c->q2, c->e64p, c->pts_p, xs, c->pn_y, eps, ys);
     PB_LAUNCH(c);
     return PB_OK;
 }

@@ -69,6 +69,11 @@ static void pb_free_build(pb_ctx* c)
     c->xq = c->yq = nullptr;
     c->p1_voff = c->p1_vlist = nullptr;
     c->p1_corr = c->p1_diag = c->p1_pinv = c->p1_yqn = c->p1_yl = nullptr;
+    c->pn_nitems = 0;
+    c->pn_items = nullptr;
+    c->pn_tiles = c->pn_chunk_leaf = c->pn_chunk_first = c->pn_begin = nullptr;
+    c->pn_p32 = c->pn_l32 = c->pn_n32 = c->pn_sp = c->pn_sn = nullptr;
+    c->pn_y = nullptr;
     c->dgVcur = nullptr;
     c->dgctl = nullptr;
     c->dg_nr = c->dg_nctl = 0;
@@ -260,6 +265,7 @@ extern "C" int pb_build_tree(pb_ctx* c)
     // the preconditioner's factorisation (first stream), whose block inversions leave most of
     // each SM free; the streams are joined at the end.
     if ((rc = pb_near_setup(c))) return rc;
+    if ((rc = pb_near_points_setup(c))) return rc;
     const bool linear = c->prm.basis == PB_BASIS_LINEAR;
     if (!linear && (rc = pb_precond_plan(c))) return rc;
     PB_CUDA(c, cudaEventRecord(c->ev_tree, c->st));

@@ -108,6 +108,14 @@ struct pb_ctx {
     int near_mitems = 0;          // work items of the several-vector near field (directed tiles)
     int4* near_mitem = nullptr;
     int* near_mtiles = nullptr;
+    // the same near field on the points of a regular rule (mixed precision, q2 = 4 or 16)
+    int pn_nitems = 0;
+    int4* pn_items = nullptr;
+    int *pn_tiles = nullptr, *pn_chunk_leaf = nullptr, *pn_chunk_first = nullptr, *pn_begin = nullptr;
+    float4 *pn_p32 = nullptr, *pn_l32 = nullptr, *pn_n32 = nullptr, *pn_sp = nullptr, *pn_sn = nullptr;
+    double* pn_y = nullptr;
+    std::vector<int> h_pn_i[3];
+    std::vector<int4> h_pn_i4;
     float4* near_sp = nullptr;  // (x_hi, y_hi, z_hi, A phi)
     float4* near_sn = nullptr;  // (n_x, n_y, n_z, A dphi)
     float2* near_dens = nullptr; // [dens_nr][nt] (A phi, A dphi) for several right-hand sides
@@ -307,6 +315,12 @@ int pb_near_q_apply(pb_ctx* c, const double* xs, double* ys);
 int pb_to_points(pb_ctx* c, const double* xs, double* xq, cudaStream_t st);
 // linear.cu: the piecewise-linear basis (set-up after the singular pass; product, preconditioner)
 int pb_p1_setup(pb_ctx* c);
+// nearfield.cu: the pair-tile near field on the points of the regular rule (mixed precision,
+// q2 = 4 or 16): set-up after the points, per-point sums, and the piecewise-constant rows
+bool pb_near_points_ok(const pb_ctx* c);
+int pb_near_points_setup(pb_ctx* c);
+int pb_near_points_apply(pb_ctx* c, const double* xs, const double* xq, double* ypt);
+int pb_near_points_elem(pb_ctx* c, const double* xs, double* ys);
 void pb_triangle_rule(int q, double* e1, double* e2, double* w);  // regular.cu
 int pb_p1_matvec(pb_ctx* c, const double* x, double* y);
 int pb_p1_precond(pb_ctx* c, const double* r, double* z);

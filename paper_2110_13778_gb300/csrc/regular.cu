@@ -263,6 +263,7 @@ int pb_regular_corrections(pb_ctx* c)
 
 int pb_near_q_apply(pb_ctx* c, const double* xs, double* ys)
 {
+    if (pb_near_points_ok(c)) return pb_near_points_elem(c, xs, ys);
     const PbLevel& lv = c->lev[c->L];
     const double eps = c->prm.eps_out / c->prm.eps_in;
     if (c->prm.precision == PB_MIXED)
