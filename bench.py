@@ -844,6 +844,19 @@ def run_linear(a):
     flops = pairs * (qr * qr) ** 2 * FLOPS_PER_NEAR_PAIR
     peak = pk["fp32_tflops"] if prec == pb.PB_MIXED else pk["fp64_tflops"]
     ach = flops / (avg * 1e-3) / 1e12
+    # the weighted Sauter-Schwab pass (FP64, once per build): per cube point and sub-map the
+    # point's kernel parts (FLOPS_PER_SS_POINT) plus 9 weight products and 54 weighted FMAs;
+    # 2 / 5 / 6 sub-maps for unordered pairs sharing a vertex / an edge / identical
+    tc = lin["stats"]["touch_class"]
+    sub = tc[1] // 2 * 2 + tc[2] // 2 * 5 + N * 6
+    sflops = 3 ** 4 * sub * (FLOPS_PER_SS_POINT + 9 + 2 * 54)
+    s_ms, s_n = lin["phases"]["singular"]
+    s_avg = s_ms / max(s_n, 1)
+    s_ach = sflops / (s_avg * 1e-3) / 1e12
+    sing = {"kernel": "k_singular_p1", "avg_launch_ms": s_avg, "bound": "alu", "achieved": s_ach,
+            "peak": pk["fp64_tflops"], "unit": "TFLOP/s", "frac": s_ach / pk["fp64_tflops"], "traffic": None,
+            "work_per_launch": f"81 cube points x {sub} sub-map evaluations x {FLOPS_PER_SS_POINT + 9 + 2 * 54} FP64 flops",
+            "peak_source": "FP64 " + pk["alu_source"]}
     if rank != 0:
         return 0
     print(json.dumps({
@@ -854,11 +867,13 @@ def run_linear(a):
         "gpu_launches": lin["launches"], "gmres_iterations": lin["iterations"],
         "matvecs_per_step": lin["matvecs"] / a.steps, "energy_kcal": lin["energy"],
         "phases_ms_per_step": {k: v[0] / a.steps for k, v in lin["phases"].items() if v[1]},
-        "roofline": {"kernel": "k_near_p1", "avg_launch_ms": avg, "bound": "alu", "achieved": ach, "peak": peak,
+        "roofline": {"kernel": "near (k_near_tile<4> on the rule's points)" if prec == pb.PB_MIXED else "near (k_near_p1)",
+                     "avg_launch_ms": avg, "bound": "alu", "achieved": ach, "peak": peak,
                      "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                      "work_per_launch": f"{pairs} element pairs x {(qr * qr) ** 2} point pairs x "
                                         f"{FLOPS_PER_NEAR_PAIR} flops",
                      "peak_source": pk["alu_source"]},
+        "phase_rooflines": {"singular_p1": sing},
         "piecewise_constant": {"ms_per_step": float(np.mean(const["times"])), "gmres_iterations": const["iterations"],
                                "energy_kcal": const["energy"],
                                "value": world * N * const["matvecs"] / dist_max(sum(const["times"]) / 1e3, world)

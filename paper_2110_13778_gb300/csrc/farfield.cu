@@ -734,6 +734,9 @@ __global__ void __launch_bounds__(64, 1) k_m2l_seg(int nch, const int* __restric
     if (threadIdx.x == 0) {
         mbar_init(&bar);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();  // the barrier is initialised before any thread waits on it
+    if (threadIdx.x == 0) {
         mbar_expect(&bar, CH);
         bulk_g2s(Ds, D + (size_t)k * T * 32, CH, &bar);
     }

@@ -172,17 +172,20 @@ __device__ __forceinline__ NearTerms near_pair(float4 tp, float4 tn, float4 tl, 
 // radial factors: K2(j, i) = -(n_i.d) ri3 (eps e1 - 1), K3(j, i) = (n_j.d) ri3 (1 - e1/eps).
 // The tiles (A, B) -- every source chunk B of the neighbour leaves c2 >= c that follows A (B
 // after A within A's own leaf) -- are cut into work items of at most NEAR_ITEM tiles of one A;
-// one warp per item, so that the warps carry nearly equal work whatever the leaf order. B's records are staged in shared memory; at step
-// s (s < nb) lane l pairs A_l with B_((l + s) mod nb), keeps the forward terms and adds the
-// reverse terms to B's shared-memory accumulators (FP32 shared atomics; lanes l and l + nb
-// meet at the same source). Forward sums of a chunk and reverse sums of a tile are FP32,
-// added into FP64 (atomics for the reverse terms and the final forward sums; ys starts at
-// zero). The tile of A with itself keeps only the forward terms and drops the identical pair.
+// one warp per item, so that the warps carry nearly equal work whatever the leaf order. B's
+// records are staged in shared memory; at step s (s < nb) lane l pairs A_l with
+// B_((l + s) mod nb) and keeps the forward terms. The reverse terms of a full tile of another
+// chunk (nb = 32) ride in registers that move one lane down after every step (a shuffle), so
+// that after 32 steps lane l holds source l's sums; partial tiles add them to B's
+// shared-memory accumulators instead (FP32 shared atomics; lanes l and l + nb meet at the same
+// source). Forward sums of a chunk and reverse sums of a tile are FP32, added into FP64
+// (atomics for the reverse terms and the final forward sums; ys starts at zero). The tile of A
+// with itself keeps only the forward terms and drops the identical pair.
 // Q2 > 1: the records are the points of a regular rule (Q2 per element, consecutive; Q2 divides
 // 32 and every leaf starts at an element, so no chunk splits an element): the pairs of points of
 // one element are dropped, which can only happen in the tile of a chunk with itself.
 template <int Q2>
-__global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nitems, const int4* __restrict__ items,
+__global__ void __launch_bounds__(256, 4) k_near_tile(int nt, int nitems, const int4* __restrict__ items,
                                                     const int* __restrict__ tiles, const int* __restrict__ chunk_leaf,
                                                     const int* __restrict__ chunk_first, const int* __restrict__ begin,
                                                     const float4* __restrict__ sp, const float4* __restrict__ sn,
@@ -203,7 +206,6 @@ __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nitems, const 
     const float4 tp = sp[kk], tn = sn[kk], tl = sl[kk];
     const float tphi = act ? tp.w : 0.f, tdphi = act ? tn.w : 0.f;  // A phi_i, A dphi_i of the target
     const float eps = (float)eps_d, inv_eps = (float)(1.0 / eps_d), kappa = (float)kappa_d;
-    const float i4pi = 0.07957747154594767f;
     double acc1 = 0.0, acc2 = 0.0;
     for (int ti = item.y; ti < item.z; ++ti) {
         const int cb = tiles[ti];
