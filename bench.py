@@ -474,6 +474,16 @@ def run_ours(a):
     torch.cuda.synchronize()
     t_mv = ev0.elapsed_time(ev1) / nmv
 
+    # the far field alone (nothing beside it on the GPU), per-phase events: the MtL's rate on its
+    # own, reported beside its rate inside the step (where it shares the SMs with the near field)
+    pb.pb_set_timing(ctx, 1)
+    pb.pb_get_timing(ctx)
+    for _ in range(10):
+        pb.pb_matvec_part(ctx, xv, yv, 2)
+    torch.cuda.synchronize()
+    far_alone = pb.pb_get_timing(ctx)
+    pb.pb_set_timing(ctx, 0)
+
     # end to end through the public API with host buffers
     pin = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).pin_memory().numpy()
     hv, ht, hqp, hq = pin(mesh.verts), pin(mesh.tris), pin(mesh.qpos), pin(mesh.q)
@@ -541,6 +551,11 @@ def run_ours(a):
         for r in rooflines.values():
             if r:
                 r["traffic"] = None
+    if far_alone.get("m2l", (0, 0))[1] > 0:
+        iso = phase_roofline("m2l", far_alone["m2l"], stats, N, a, prec, pk, wl_key)
+        if iso:
+            iso["note"] = "far field alone (pb_matvec_part, which = 2): no near field beside it"
+            rooflines["m2l_alone"] = iso
     roof = rooflines.get("near")
 
     cpu = None

@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(_compile, SOURCES))
     if force or not os.path.exists(OUT) or any(os.path.getmtime(o) > os.path.getmtime(OUT) for o in objs):
         tmp = OUT + f".tmp{os.getpid()}"
-        cmd = [nvcc(), ARCH, "-shared", "-o", tmp] + objs + ["-lcudart"]
+        cmd = [nvcc(), ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -305,7 +305,7 @@ __global__ void k_blk_apply(int nt, const int* __restrict__ begin, const long lo
                             const R* __restrict__ minv, const double* __restrict__ r, double* __restrict__ z,
                             long long rstr, long long zstr)
 {
-    __shared__ R rv[2 * PB_PC_BMAX];
+    __shared__ __align__(16) R rv[2 * PB_PC_BMAX];
     r += blockIdx.y * rstr;  // right-hand side blockIdx.y
     z += blockIdx.y * zstr;
     const int c = blockIdx.x;
@@ -316,7 +316,18 @@ __global__ void k_blk_apply(int nt, const int* __restrict__ begin, const long lo
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31, nw = blockDim.x / 32;
     for (int i = warp; i < m; i += nw) {
         R s = 0;
-        for (int j = lane; j < m; j += 32) s += Mc[(size_t)i * m + j] * rv[j];
+        if constexpr (sizeof(R) == sizeof(float)) {
+            // m is even and every block starts at a multiple of 4 entries (the orders m^2 of the
+            // blocks before it are multiples of 4): rows and the staged slice read in pairs
+            const float2* row = reinterpret_cast<const float2*>(Mc + (size_t)i * m);
+            const float2* rv2 = reinterpret_cast<const float2*>(rv);
+            for (int j = lane; j < m / 2; j += 32) {
+                const float2 a = row[j], b = rv2[j];
+                s += a.x * b.x + a.y * b.y;
+            }
+        } else {
+            for (int j = lane; j < m; j += 32) s += Mc[(size_t)i * m + j] * rv[j];
+        }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
             if (i < n) z[b + i] = (double)s;
