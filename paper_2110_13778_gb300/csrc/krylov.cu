@@ -19,55 +19,79 @@
 // (separations keep FP32 relative accuracy), each tile of charges summed in FP32 and added
 // into FP64 accumulators.
 template <class R>
-__global__ void k_rhs(int nt, int nc, const double4_32a* __restrict__ ep, const double4_32a* __restrict__ en,
-                      const double* __restrict__ qpos, const double* __restrict__ q, double eps1,
-                      double* __restrict__ b)
+struct RhsCharge {
+    R x, y, z, q;
+};
+
+// Each thread takes two target elements (k and k + blockDim.x of the block's pair of slices),
+// so that every staged charge (its hi and lo coordinates and charge: two broadcast
+// shared-memory reads) serves two pair evaluations.
+template <class R>
+__global__ void __launch_bounds__(KB) k_rhs(int nt, int nc, const double4_32a* __restrict__ ep,
+                                            const double4_32a* __restrict__ en, const double* __restrict__ qpos,
+                                            const double* __restrict__ q, double eps1, double* __restrict__ b)
 {
-    __shared__ R sh[KB][3], sl[KB][3], sq[KB];
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    double4_32a p = make_double4_32a(0, 0, 0, 0), n = p;
-    if (k < nt) {
-        p = ep[k];
-        n = en[k];
+    __shared__ RhsCharge<R> shq[KB], slo[KB];
+    const int k0 = blockIdx.x * 2 * KB + threadIdx.x;
+    R ph[2][3], pl[2][3], nr[2][3];
+    double w[2];
+    bool act[2];
+    for (int u = 0; u < 2; ++u) {
+        const int k = k0 + u * KB;
+        act[u] = k < nt;
+        double4_32a p = make_double4_32a(0, 0, 0, 0), n = p;
+        if (act[u]) {
+            p = ep[k];
+            n = en[k];
+        }
+        const double pc[3] = {p.x, p.y, p.z}, nc3[3] = {n.x, n.y, n.z};
+        for (int a = 0; a < 3; ++a) {
+            ph[u][a] = (R)pc[a];
+            pl[u][a] = (R)(pc[a] - (double)ph[u][a]);
+            nr[u][a] = (R)nc3[a];
+        }
+        w[u] = p.w;
     }
-    const R ph[3] = {(R)p.x, (R)p.y, (R)p.z};
-    const R pl[3] = {(R)(p.x - (double)ph[0]), (R)(p.y - (double)ph[1]), (R)(p.z - (double)ph[2])};
-    const R nx = (R)n.x, ny = (R)n.y, nz = (R)n.z;
-    double s1 = 0.0, s2 = 0.0;
+    double s1[2] = {0.0, 0.0}, s2[2] = {0.0, 0.0};
     const double i4pi = 0.07957747154594767;
     for (int t0 = 0; t0 < nc; t0 += KB) {
         __syncthreads();
         if (t0 + threadIdx.x < nc) {
-            int t = t0 + threadIdx.x;
-            for (int a = 0; a < 3; ++a) {
-                double v = qpos[3 * t + a];
-                R hv = (R)v;
-                sh[threadIdx.x][a] = hv;
-                sl[threadIdx.x][a] = (R)(v - (double)hv);
-            }
-            sq[threadIdx.x] = (R)q[t];
+            const int t = t0 + threadIdx.x;
+            const double v[3] = {qpos[3 * t], qpos[3 * t + 1], qpos[3 * t + 2]};
+            const R h[3] = {(R)v[0], (R)v[1], (R)v[2]};
+            shq[threadIdx.x] = {h[0], h[1], h[2], (R)q[t]};
+            slo[threadIdx.x] = {(R)(v[0] - (double)h[0]), (R)(v[1] - (double)h[1]), (R)(v[2] - (double)h[2]), R(0)};
         }
         __syncthreads();
-        int m = min(KB, nc - t0);
-        if (k < nt) {
-            R a1 = 0, a2 = 0;
-            for (int t = 0; t < m; ++t) {
-                R dx = (ph[0] - sh[t][0]) + (pl[0] - sl[t][0]);
-                R dy = (ph[1] - sh[t][1]) + (pl[1] - sl[t][1]);
-                R dz = (ph[2] - sh[t][2]) + (pl[2] - sl[t][2]);
-                R r2 = dx * dx + dy * dy + dz * dz;
-                R ri = PbKer<R>::rsqrt_(r2);
-                R nd = nx * dx + ny * dy + nz * dz;
-                a1 += sq[t] * ri;
-                a2 -= sq[t] * nd * ri * ri * ri;  // dG0/dn_x = -(n.d)/(4 pi r^3)
+        const int m = min(KB, nc - t0);
+        R a1[2] = {0, 0}, a2[2] = {0, 0};
+        for (int t = 0; t < m; ++t) {
+            const RhsCharge<R> ch = shq[t], cl = slo[t];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const R dx = (ph[u][0] - ch.x) + (pl[u][0] - cl.x);
+                const R dy = (ph[u][1] - ch.y) + (pl[u][1] - cl.y);
+                const R dz = (ph[u][2] - ch.z) + (pl[u][2] - cl.z);
+                const R r2 = dx * dx + dy * dy + dz * dz;
+                const R ri = PbKer<R>::rsqrt_(r2);
+                const R nd = nr[u][0] * dx + nr[u][1] * dy + nr[u][2] * dz;
+                const R qr = ch.q * ri;
+                a1[u] += qr;
+                a2[u] -= qr * nd * ri * ri;  // dG0/dn_x = -(n.d)/(4 pi r^3)
             }
-            s1 += (double)a1;
-            s2 += (double)a2;
+        }
+        for (int u = 0; u < 2; ++u) {
+            s1[u] += (double)a1[u];
+            s2[u] += (double)a2[u];
         }
     }
-    if (k < nt) {
-        b[k] = p.w * s1 * i4pi / eps1;
-        b[nt + k] = p.w * s2 * i4pi / eps1;
+    for (int u = 0; u < 2; ++u) {
+        const int k = k0 + u * KB;
+        if (act[u]) {
+            b[k] = w[u] * s1[u] * i4pi / eps1;
+            b[nt + k] = w[u] * s2[u] * i4pi / eps1;
+        }
     }
 }
 
@@ -80,9 +104,11 @@ int pb_rhs_sorted(pb_ctx* c, double* bs)
     double* out = c->q2 > 1 ? c->yq : bs;
     pb_tic(c, PB_T_RHS);
     if (c->prm.precision == PB_MIXED)
-        k_rhs<float><<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, c->prm.eps_in, out);
+        k_rhs<float><<<(nt + 2 * KB - 1) / (2 * KB), KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, c->prm.eps_in,
+                                                                     out);
     else
-        k_rhs<double><<<(nt + KB - 1) / KB, KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, c->prm.eps_in, out);
+        k_rhs<double><<<(nt + 2 * KB - 1) / (2 * KB), KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, c->prm.eps_in,
+                                                                      out);
     PB_LAUNCH(c);
     if (c->q2 > 1) {
         int rc = pb_from_points(c, c->yq, bs, 0, c->st);

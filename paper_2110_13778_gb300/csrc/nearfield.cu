@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256, 4) k_near_tile(int nt, int nitems, const 
                 __syncwarp();
                 float q1 = 0.f, q2 = 0.f;
                 int m = lane;
-#pragma unroll 2
+#pragma unroll 4
                 for (int s = 0; s < 32; ++s) {
                     const NearTerms t = near_pair(tp, tn, tl, tphi, tdphi, sbp[wi][m], sbn[wi][m], sbl[wi][m], act,
                                                   eps, inv_eps, kappa);
