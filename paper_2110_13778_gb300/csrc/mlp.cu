@@ -3,9 +3,11 @@
 // the solver itself produces. GMRES started from its prediction still converges to the same
 // residual, so the network only changes the number of iterations, never the answer.
 //
-// Arithmetic: BF16 weights and activations, FP32 accumulation, on the tensor cores through
-// mma.sync m16n8k16 (BF16 inputs, FP32 accumulators); FP32 master weights and Adam moments.
-// Hidden layers use ReLU, the output layer is linear, the loss is the mean squared error.
+// Arithmetic: BF16 weights and activations, FP32 accumulation, on the tensor cores: inference
+// of the default shape (width 128) through tcgen05.mma with tensor-memory accumulators, the
+// training GEMMs and other shapes through mma.sync m16n8k16 (BF16 inputs, FP32 accumulators);
+// FP32 master weights and Adam moments. Hidden layers use ReLU, the output layer is linear, the
+// loss is the mean squared error.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
@@ -31,6 +33,7 @@ struct pb_mlp {
     float* dA = nullptr;
     __nv_bfloat16* dZb = nullptr;
     float* lossbuf = nullptr;
+    int* derr = nullptr;  // set by the tensor-core inference when a bounded wait gives up
     long long nparam = 0;
     int adam_t = 0;
     std::string err;
@@ -328,6 +331,8 @@ extern "C" int pb_mlp_create(int nin, int width, int depth, int nout, unsigned l
     ok &= cudaMalloc(&m->G, sizeof(float) * o) == cudaSuccess;
     ok &= cudaMalloc(&m->Wb, sizeof(__nv_bfloat16) * o) == cudaSuccess;
     ok &= cudaMalloc(&m->lossbuf, sizeof(float)) == cudaSuccess;
+    ok &= cudaMalloc(&m->derr, sizeof(int)) == cudaSuccess;
+    ok &= ok && cudaMemset(m->derr, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         delete m;
@@ -371,6 +376,7 @@ extern "C" int pb_mlp_destroy(pb_mlp* m)
     cudaFree(m->G);
     cudaFree(m->Wb);
     cudaFree(m->lossbuf);
+    cudaFree(m->derr);
     for (int l = 0; l < MLP_MAXL; ++l) cudaFree(m->Z[l]);
     for (int l = 0; l <= MLP_MAXL; ++l) cudaFree(m->Ab[l]);
     cudaFree(m->dA);
@@ -407,137 +413,197 @@ extern "C" int pb_mlp_set_params(pb_mlp* m, const float* host)
 }
 
 // ---------- fused inference: every layer in one kernel ----------
-// For width 128, a first layer of at most 32 padded inputs and at most 16 padded outputs. A CTA
-// of four warps converts all weights to BF16 into shared memory once (rows padded to 136 / 40
-// elements so that the eight rows a B fragment touches fall in distinct banks), then loops over
-// tiles of 64 rows: each warp runs its 16 rows through all layers with the activations held in
-// registers -- the FP32 accumulator fragment of one layer, rounded to BF16 pairs, is exactly the
-// A fragment of the next -- so the features are read once and two outputs written per row.
-// Rounding points are those of the layer-by-layer path.
+// For width 128, a first layer of at most 32 padded inputs and at most 16 padded outputs: all
+// weights are converted to BF16 once per block and every tile of rows runs through all layers
+// inside the kernel, so the features are read once and two outputs written per row.
 #define FUSED_W 128
-#define FUSED_WP 136
-#define FUSED_D0P 40
 struct MlpDesc {
     long long woff[MLP_MAXL], boff[MLP_MAXL];
     int nin, din0, nl, nout;  // inputs, padded inputs (row length of W_0), layers, outputs
 };
 
-__device__ __forceinline__ void mma_bf16(float* c, const unsigned* a, unsigned b0, unsigned b1)
+// ---------- fused inference on the fifth-generation tensor cores (tcgen05) ----------
+// The layers and rounding points of the layer-by-layer path, one tile of 128 rows at a time: the
+// tile's BF16 activations sit in shared memory in the K-major layout without swizzle that the
+// MMA reads through matrix descriptors (8 x 16-byte core matrices: the next core matrix along K
+// 128 bytes on, the next group of 8 rows K / 8 x 128 bytes on); one thread issues the layer's
+// tcgen05.mma instructions (M = 128, N = 128 or 16, K = 16 each, BF16 in, FP32 accumulate) into a
+// 128-column tensor-memory accumulator and commits them to an mbarrier; each warp then reads its
+// 32 rows back with tcgen05.ld, adds the bias, applies ReLU, rounds to BF16 and writes the next
+// layer's operand in place. Every wait is bounded: a wait that gives up sets *err, lets the MMAs
+// in flight finish (bounded again), frees the tensor memory and leaves.
+#define TC_ROWS 128
+__device__ __forceinline__ unsigned tc_su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// shared-memory matrix descriptor: start address, leading (K) and stride (8-row) byte offsets,
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(unsigned addr, unsigned lbo, unsigned sbo)
 {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M = 128
+__device__ __forceinline__ unsigned tc_idesc(int nn)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(nn >> 3) << 17) | ((unsigned)(TC_ROWS >> 4) << 24);
+}
+__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned ph)
+{
+    for (unsigned it = 0; it < (1u << 24); ++it) {
+        unsigned ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(bar), "r"(ph) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// byte offset of element (r, k) in the no-swizzle K-major layout of a matrix with K columns
+__device__ __forceinline__ unsigned tc_off(int r, int k, int K) { return (r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+// 32 consecutive FP32 accumulator columns of this warp's 32 lanes (rows)
+__device__ __forceinline__ void tc_ld32(unsigned taddr, float* v)
+{
+    unsigned r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ unsigned pack_f2(float lo, float hi)
+static size_t tc_smem(int nl, int din0)
 {
-    return pack2(__float2bfloat16(lo), __float2bfloat16(hi));
+    return sizeof(__nv_bfloat16) * ((size_t)FUSED_W * din0 + (size_t)(nl - 2) * FUSED_W * FUSED_W + 16 * FUSED_W +
+                                    (size_t)TC_ROWS * FUSED_W) +
+           sizeof(float) * ((size_t)(nl - 1) * FUSED_W + 16) + 128;
 }
 
-static size_t fused_smem(int nl)
+__global__ void __launch_bounds__(128, 1) k_mlp_tc(int n, const float* __restrict__ X, const float* __restrict__ W,
+                                                   MlpDesc md, float* __restrict__ Y, int* __restrict__ err)
 {
-    return sizeof(__nv_bfloat16) * ((size_t)FUSED_W * FUSED_D0P + (size_t)(nl - 2) * FUSED_W * FUSED_WP +
-                                     16 * FUSED_WP) +
-           sizeof(float) * ((size_t)(nl - 1) * FUSED_W + 16);
-}
-
-__global__ void __launch_bounds__(128) k_mlp_fused(int n, const float* __restrict__ X, const float* __restrict__ W,
-                                                   MlpDesc md, float* __restrict__ Y)
-{
-    extern __shared__ __align__(16) unsigned char fsm[];
+    extern __shared__ __align__(128) unsigned char tsm[];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ unsigned tslot;
     const int nl = md.nl, din0 = md.din0;
-    __nv_bfloat16* w0 = (__nv_bfloat16*)fsm;                 // [128][40]
-    __nv_bfloat16* wh = w0 + FUSED_W * FUSED_D0P;            // [nl-2][128][136]
-    __nv_bfloat16* wl = wh + (size_t)(nl - 2) * FUSED_W * FUSED_WP;  // [16][136]
-    float* bs = (float*)(wl + 16 * FUSED_WP);                // [nl-1][128] then [16]
-    for (int i = threadIdx.x; i < FUSED_W * din0; i += blockDim.x)
-        w0[(i / din0) * FUSED_D0P + i % din0] = __float2bfloat16(W[md.woff[0] + i]);
+    __nv_bfloat16* w0 = (__nv_bfloat16*)tsm;                           // [128 x din0]
+    __nv_bfloat16* wh = w0 + FUSED_W * din0;                           // [nl-2][128 x 128]
+    __nv_bfloat16* wl = wh + (size_t)(nl - 2) * FUSED_W * FUSED_W;     // [16 x 128]
+    __nv_bfloat16* as = wl + 16 * FUSED_W;                             // [128 x 128] activations
+    float* bs = (float*)(as + TC_ROWS * FUSED_W);                      // [nl-1][128] then [16]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // weights (row o of layer l is output o: the B operand, K-major) and biases
+    for (int i = tid; i < FUSED_W * din0; i += 128)
+        *(__nv_bfloat16*)((char*)w0 + tc_off(i / din0, i % din0, din0)) = __float2bfloat16(W[md.woff[0] + i]);
     for (int l = 1; l < nl - 1; ++l)
-        for (int i = threadIdx.x; i < FUSED_W * FUSED_W; i += blockDim.x)
-            wh[(size_t)(l - 1) * FUSED_W * FUSED_WP + (i / FUSED_W) * FUSED_WP + i % FUSED_W] =
+        for (int i = tid; i < FUSED_W * FUSED_W; i += 128)
+            *(__nv_bfloat16*)((char*)(wh + (size_t)(l - 1) * FUSED_W * FUSED_W) + tc_off(i / FUSED_W, i % FUSED_W, FUSED_W)) =
                 __float2bfloat16(W[md.woff[l] + i]);
-    for (int i = threadIdx.x; i < 16 * FUSED_W; i += blockDim.x)
-        wl[(i / FUSED_W) * FUSED_WP + i % FUSED_W] = __float2bfloat16(W[md.woff[nl - 1] + i]);
+    for (int i = tid; i < 16 * FUSED_W; i += 128)
+        *(__nv_bfloat16*)((char*)wl + tc_off(i / FUSED_W, i % FUSED_W, FUSED_W)) = __float2bfloat16(W[md.woff[nl - 1] + i]);
     for (int l = 0; l < nl - 1; ++l)
-        for (int i = threadIdx.x; i < FUSED_W; i += blockDim.x) bs[l * FUSED_W + i] = W[md.boff[l] + i];
-    for (int i = threadIdx.x; i < 16; i += blockDim.x) bs[(nl - 1) * FUSED_W + i] = W[md.boff[nl - 1] + i];
+        for (int i = tid; i < FUSED_W; i += 128) bs[l * FUSED_W + i] = W[md.boff[l] + i];
+    for (int i = tid; i < 16; i += 128) bs[(nl - 1) * FUSED_W + i] = W[md.boff[nl - 1] + i];
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_su32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_su32(&tslot)),
+                     "r"(FUSED_W)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
     __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int ntiles = (n + 63) / 64;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int r0 = tile * 64 + warp * 16;
-        if (r0 >= n) continue;
-        const int ra = r0 + g, rb = r0 + g + 8;
-        float acc[16][4];
-        unsigned a[8][4];
-        // layer 0: A fragments straight from the FP32 features (columns >= nin and rows >= n are 0)
-        auto xin = [&](int r, int c) -> float { return (r < n && c < md.nin) ? X[(size_t)r * md.nin + c] : 0.f; };
+    tc_fence_after();
+    const unsigned taddr = tslot, tw = taddr + ((unsigned)(32 * warp) << 16);
+    unsigned ph = 0u;
+    bool alive = true;
+    const int ntiles = (n + TC_ROWS - 1) / TC_ROWS;
+    for (int tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
+        // the tile's features, BF16, zero beyond nin and beyond n, in the layer-0 layout
+        {
+            const int r = tid, row = tile * TC_ROWS + r;
+            for (int k0 = 0; k0 < din0; k0 += 8) {
+                __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
-        for (int kc = 0; kc < 8; ++kc) {
-            const int c0 = 16 * kc + 2 * t;
-            if (kc >= 2) {
-                a[kc][0] = a[kc][1] = a[kc][2] = a[kc][3] = 0u;
-                continue;
-            }
-            a[kc][0] = pack_f2(xin(ra, c0), xin(ra, c0 + 1));
-            a[kc][1] = pack_f2(xin(rb, c0), xin(rb, c0 + 1));
-            a[kc][2] = pack_f2(xin(ra, c0 + 8), xin(ra, c0 + 9));
-            a[kc][3] = pack_f2(xin(rb, c0 + 8), xin(rb, c0 + 9));
-        }
-        int kchunks = din0 / 16;
-        for (int l = 0; l < nl; ++l) {
-            const bool last = l == nl - 1;
-            const int ntile = last ? 2 : 16;
-            const __nv_bfloat16* wsm = l == 0 ? w0 : last ? wl : wh + (size_t)(l - 1) * FUSED_W * FUSED_WP;
-            const int stride = l == 0 ? FUSED_D0P : FUSED_WP;
-            const float* bias = bs + l * FUSED_W;
-#pragma unroll
-            for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
-#pragma unroll
-            for (int kc = 0; kc < 8; ++kc) {
-                if (kc >= kchunks) break;
-#pragma unroll
-                for (int nt = 0; nt < 16; ++nt) {
-                    if (nt < ntile) {
-                        const __nv_bfloat16* wr = wsm + (nt * 8 + g) * stride + 16 * kc + 2 * t;
-                        mma_bf16(acc[nt], a[kc], *(const unsigned*)wr, *(const unsigned*)(wr + 8));
-                    }
+                for (int q = 0; q < 8; ++q) {
+                    const int c = k0 + q;
+                    v[q] = __float2bfloat16(row < n && c < md.nin ? X[(size_t)row * md.nin + c] : 0.f);
                 }
+                *(uint4*)((char*)as + tc_off(r, k0, din0)) = *(const uint4*)v;
             }
-            if (last) {
-                // bias and output: row g holds columns 2t, 2t+1 of tile 0 (and of tile 1 above 8)
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int col = nt * 8 + 2 * t + (q & 1), row = q < 2 ? ra : rb;
-                        if (col < md.nout && row < n) Y[(size_t)row * md.nout + col] = acc[nt][q] + bias[col];
-                    }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        for (int l = 0; l < nl && alive; ++l) {
+            const bool last = l == nl - 1;
+            const int K = l == 0 ? din0 : FUSED_W, nn = last ? 16 : FUSED_W;
+            const __nv_bfloat16* wb = l == 0 ? w0 : last ? wl : wh + (size_t)(l - 1) * FUSED_W * FUSED_W;
+            if (tid == 0) {
+                const unsigned sbo = (K / 8) * 128, id = tc_idesc(nn);
+                for (int ks = 0; ks < K / 16; ++ks) {
+                    const uint64_t ad = tc_desc(tc_su32(as) + ks * 256, 128, sbo);
+                    const uint64_t bd = tc_desc(tc_su32(wb) + ks * 256, 128, sbo);
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                 ::"r"(taddr), "l"(ad), "l"(bd), "r"(id), "r"((unsigned)(ks > 0)) : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(tc_su32(&bar)) : "memory");
+            }
+            if (!__syncthreads_and(tc_wait(tc_su32(&bar), ph))) {
+                if (tid == 0) atomicExch(err, 1);
+                tc_wait(tc_su32(&bar), ph);  // let the MMAs in flight finish before the memory goes
+                alive = false;
                 break;
             }
+            ph ^= 1u;
+            tc_fence_after();
+            const float* bias = bs + l * FUSED_W;
+            const int r = 32 * warp + lane, row = tile * TC_ROWS + r;
+            if (last) {
+                float v[32];
+                tc_ld32(tw, v);  // (columns 16..31 are not part of this layer's result)
+                for (int c = 0; c < md.nout; ++c)
+                    if (row < n) Y[(size_t)row * md.nout + c] = v[c] + bias[c];
+            } else {
+                for (int c0 = 0; c0 < FUSED_W; c0 += 32) {
+                    float v[32];
+                    tc_ld32(tw + c0, v);
 #pragma unroll
-            for (int kc = 0; kc < 8; ++kc) {
-                const int c0 = 16 * kc + 2 * t;
-                a[kc][0] = pack_f2(fmaxf(acc[2 * kc][0] + bias[c0], 0.f), fmaxf(acc[2 * kc][1] + bias[c0 + 1], 0.f));
-                a[kc][1] = pack_f2(fmaxf(acc[2 * kc][2] + bias[c0], 0.f), fmaxf(acc[2 * kc][3] + bias[c0 + 1], 0.f));
-                a[kc][2] = pack_f2(fmaxf(acc[2 * kc + 1][0] + bias[c0 + 8], 0.f),
-                                   fmaxf(acc[2 * kc + 1][1] + bias[c0 + 9], 0.f));
-                a[kc][3] = pack_f2(fmaxf(acc[2 * kc + 1][2] + bias[c0 + 8], 0.f),
-                                   fmaxf(acc[2 * kc + 1][3] + bias[c0 + 9], 0.f));
+                    for (int q0 = 0; q0 < 32; q0 += 8) {
+                        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) o[q] = __float2bfloat16(fmaxf(v[q0 + q] + bias[c0 + q0 + q], 0.f));
+                        *(uint4*)((char*)as + tc_off(r, c0 + q0, FUSED_W)) = *(const uint4*)o;
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
-            kchunks = 8;
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
         }
     }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(FUSED_W) : "memory");
 }
 
 static bool fused_ok(const pb_mlp* m)
 {
     return m->width == FUSED_W && m->din[0] <= 32 && m->dout[m->nl - 1] == 16 && m->nl >= 2 &&
-           fused_smem(m->nl) <= 200 * 1024;
+           tc_smem(m->nl, m->din[0]) <= 200 * 1024;
 }
 
 static int mlp_forward_fused(pb_mlp* m, const float* X, int n, float* Y)
@@ -551,16 +617,25 @@ static int mlp_forward_fused(pb_mlp* m, const float* X, int n, float* Y)
     md.din0 = m->din[0];
     md.nl = m->nl;
     md.nout = m->nout;
-    const size_t smem = fused_smem(m->nl);
-    if (cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    const size_t smem = tc_smem(m->nl, m->din[0]);
+    if (cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return mlp_fail(m, PB_ERR_CUDA, "mlp: shared memory attribute failed");
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int tiles = (n + 63) / 64;
-    const int grid = std::max(1, std::min(tiles, 2 * nsm));
-    k_mlp_fused<<<grid, 128, smem, m->st>>>(n, X, m->W, md, Y);
-    return cudaGetLastError() == cudaSuccess ? PB_OK : mlp_fail(m, PB_ERR_CUDA, "mlp fused forward launch failed");
+    const int tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    const int grid = std::max(1, std::min(tiles, nsm));  // one block per SM (its tensor memory and shared memory)
+    k_mlp_tc<<<grid, 128, smem, m->st>>>(n, X, m->W, md, Y, m->derr);
+    if (cudaGetLastError() != cudaSuccess) return mlp_fail(m, PB_ERR_CUDA, "mlp fused forward launch failed");
+    int herr = 0;
+    if (cudaMemcpyAsync(&herr, m->derr, sizeof(int), cudaMemcpyDeviceToHost, m->st) != cudaSuccess ||
+        cudaStreamSynchronize(m->st) != cudaSuccess)
+        return mlp_fail(m, PB_ERR_CUDA, "mlp fused forward failed");
+    if (herr) {
+        cudaMemsetAsync(m->derr, 0, sizeof(int), m->st);
+        return mlp_fail(m, PB_ERR_TIMEOUT, "mlp: a bounded wait on the tensor cores gave up");
+    }
+    return PB_OK;
 }
 
 extern "C" int pb_mlp_forward(pb_mlp* m, const float* X, int n, float* Y)
