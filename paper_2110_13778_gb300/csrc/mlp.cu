@@ -3,11 +3,11 @@
 // the solver itself produces. GMRES started from its prediction still converges to the same
 // residual, so the network only changes the number of iterations, never the answer.
 //
-// Arithmetic: BF16 weights and activations, FP32 accumulation, on the tensor cores: inference
-// of the default shape (width 128) through tcgen05.mma with tensor-memory accumulators, the
-// training GEMMs and other shapes through mma.sync m16n8k16 (BF16 inputs, FP32 accumulators);
-// FP32 master weights and Adam moments. Hidden layers use ReLU, the output layer is linear, the
-// loss is the mean squared error.
+// Arithmetic: BF16 weights and activations, FP32 accumulation, on the fifth-generation tensor
+// cores (tcgen05.mma with tensor-memory accumulators): the fused inference of the default shape
+// (width 128) and a generic tiled GEMM for the training passes and other shapes; FP32 master
+// weights and Adam moments. Hidden layers use ReLU, the output layer is linear, the loss is the
+// mean squared error.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
@@ -44,77 +44,160 @@ static int mlp_fail(pb_mlp* m, int code, const char* msg)
     if (m) m->err = msg;
     return code;
 }
+static int mlp_check_err(pb_mlp* m);
 
-// ---------- generic BF16 GEMM on the tensor cores ----------
-// C[M x N] (FP32, ldc) = sum_k A(i, k) B(k, j) with A(i, k) = A[i * sAi + k * sAk] and
-// B(k, j) = B[k * sBk + j * sBj] (BF16, any strides); one warp per 16 x 64 tile, K split over
-// gridDim.z slices that accumulate with atomicAdd when ksplit > 1.
-__device__ __forceinline__ unsigned pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
+// ---------- tcgen05 helpers ----------
+#define TC_ROWS 128
+__device__ __forceinline__ unsigned tc_su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// shared-memory matrix descriptor: start address, leading (K) and stride (8-row) byte offsets,
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(unsigned addr, unsigned lbo, unsigned sbo)
 {
-    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M = 128
+__device__ __forceinline__ unsigned tc_idesc(int nn)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(nn >> 3) << 17) | ((unsigned)(TC_ROWS >> 4) << 24);
+}
+__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned ph)
+{
+    for (unsigned it = 0; it < (1u << 24); ++it) {
+        unsigned ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(bar), "r"(ph) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// byte offset of element (r, k) in the no-swizzle K-major layout of a matrix with K columns
+__device__ __forceinline__ unsigned tc_off(int r, int k, int K) { return (r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+// 32 consecutive FP32 accumulator columns of this warp's 32 lanes (rows)
+__device__ __forceinline__ void tc_ld32(unsigned taddr, float* v)
+{
+    unsigned r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
-                                                   long long sAi, long long sAk, const __nv_bfloat16* __restrict__ B,
-                                                   long long sBk, long long sBj, float* __restrict__ C, long long ldc,
-                                                   int accumulate)
+
+// ---------- generic BF16 GEMM on the fifth-generation tensor cores ----------
+// C[M x N] (FP32, ldc) = sum_k A(i, k) B(k, j) with A(i, k) = A[i * sAi + k * sAk] and
+// B(k, j) = B[k * sBk + j * sBj] (BF16, any strides; the training passes read transposed
+// operands). One block of four warps per 128 x 128 tile of C and per slice of K (gridDim.z
+// slices that add into C with atomicAdd when ksplit > 1): chunks of 64 along K are staged by
+// plain loads into shared memory in the no-swizzle K-major layout (zero outside A, B and the
+// slice), four tcgen05.mma (M = N = 128, K = 16) per chunk accumulate into 128 columns of tensor
+// memory, committed to an mbarrier; each warp then reads its 32 rows back with tcgen05.ld.
+// Every wait is bounded (a wait that gives up sets *err, waits once more and stops).
+#define GT_K 64
+__device__ __forceinline__ unsigned gt_off(int r, int k) { return (r >> 3) * (GT_K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+__device__ __forceinline__ unsigned gt_su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
+                                                    long long sAi, long long sAk, const __nv_bfloat16* __restrict__ B,
+                                                    long long sBk, long long sBj, float* __restrict__ C, long long ldc,
+                                                    int accumulate, int* __restrict__ err)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int i0 = (blockIdx.x * 4 + warp) * 16;
-    const int j0 = blockIdx.y * 64;
-    if (i0 >= M) return;
+    __shared__ __align__(128) __nv_bfloat16 As[128 * GT_K], Bs[128 * GT_K];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ unsigned tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.x * 128, j0 = blockIdx.y * 128;
     const int kslice = (K + gridDim.z - 1) / gridDim.z;
     const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(gt_su32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gt_su32(&tslot)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned taddr = tslot;
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    const unsigned sbo = (GT_K / 8) * 128;
     const __nv_bfloat16 z = __float2bfloat16(0.f);
-    float acc[8][4];
-#pragma unroll
-    for (int n = 0; n < 8; ++n)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[n][q] = 0.f;
-    auto ld_a = [&](int i, int k) -> __nv_bfloat16 {
-        return (i < M && k < ke) ? A[(long long)i * sAi + (long long)k * sAk] : z;
-    };
-    auto ld_b = [&](int k, int j) -> __nv_bfloat16 {
-        return (j < N && k < ke) ? B[(long long)k * sBk + (long long)j * sBj] : z;
-    };
-    for (int k0 = kb; k0 < ke; k0 += 16) {
-        unsigned a[4];
-        a[0] = pack2(ld_a(i0 + g, k0 + 2 * t), ld_a(i0 + g, k0 + 2 * t + 1));
-        a[1] = pack2(ld_a(i0 + g + 8, k0 + 2 * t), ld_a(i0 + g + 8, k0 + 2 * t + 1));
-        a[2] = pack2(ld_a(i0 + g, k0 + 2 * t + 8), ld_a(i0 + g, k0 + 2 * t + 9));
-        a[3] = pack2(ld_a(i0 + g + 8, k0 + 2 * t + 8), ld_a(i0 + g + 8, k0 + 2 * t + 9));
-#pragma unroll
-        for (int n = 0; n < 8; ++n) {
-            const int j = j0 + n * 8 + g;
-            unsigned b0 = pack2(ld_b(k0 + 2 * t, j), ld_b(k0 + 2 * t + 1, j));
-            unsigned b1 = pack2(ld_b(k0 + 2 * t + 8, j), ld_b(k0 + 2 * t + 9, j));
-            asm volatile(
-                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                "{%0,%1,%2,%3};\n"
-                : "+f"(acc[n][0]), "+f"(acc[n][1]), "+f"(acc[n][2]), "+f"(acc[n][3])
-                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    unsigned ph = 0u;
+    bool alive = true, any = false;
+    for (int k0 = kb; k0 < ke && alive; k0 += GT_K) {
+        for (int e = tid; e < 128 * GT_K; e += 128) {
+            const int r = e / GT_K, kk = e % GT_K, k = k0 + kk;
+            const int i = i0 + r, j = j0 + r;
+            const bool kin = k < ke;
+            *(__nv_bfloat16*)((char*)As + gt_off(r, kk)) = (kin && i < M) ? A[(long long)i * sAi + (long long)k * sAk] : z;
+            *(__nv_bfloat16*)((char*)Bs + gt_off(r, kk)) = (kin && j < N) ? B[(long long)k * sBk + (long long)j * sBj] : z;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            for (int ks = 0; ks < GT_K / 16; ++ks) {
+                const uint64_t ad = tc_desc(gt_su32(As) + ks * 256, 128, sbo);
+                const uint64_t bd = tc_desc(gt_su32(Bs) + ks * 256, 128, sbo);
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"((unsigned)(any || ks > 0)) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(gt_su32(&bar)) : "memory");
+        }
+        any = true;
+        if (!__syncthreads_and(tc_wait(gt_su32(&bar), ph))) {
+            if (tid == 0) atomicExch(err, 1);
+            tc_wait(gt_su32(&bar), ph);
+            alive = false;
+            break;
+        }
+        ph ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (alive && (any || !accumulate)) {
+        const int i = i0 + 32 * warp + lane;
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+            float v[32];
+            if (any) tc_ld32(taddr + ((unsigned)(32 * warp) << 16) + c0, v);
+            else
+                for (int q = 0; q < 32; ++q) v[q] = 0.f;
+            if (i < M)
+                for (int q = 0; q < 32; ++q) {
+                    const int j = j0 + c0 + q;
+                    if (j < N) {
+                        float* c = C + (long long)i * ldc + j;
+                        if (accumulate) atomicAdd(c, v[q]);
+                        else *c = v[q];
+                    }
+                }
         }
     }
-#pragma unroll
-    for (int n = 0; n < 8; ++n)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + g + (q >= 2 ? 8 : 0);
-            const int j = j0 + n * 8 + 2 * t + (q & 1);
-            if (i < M && j < N) {
-                float* c = C + (long long)i * ldc + j;
-                if (accumulate) atomicAdd(c, acc[n][q]);
-                else *c = acc[n][q];
-            }
-        }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(128) : "memory");
 }
 
 static void gemm(cudaStream_t st, int M, int N, int K, const __nv_bfloat16* A, long long sAi, long long sAk,
-                 const __nv_bfloat16* B, long long sBk, long long sBj, float* C, long long ldc, int ksplit)
+                 const __nv_bfloat16* B, long long sBk, long long sBj, float* C, long long ldc, int ksplit, int* err)
 {
-    dim3 grid((M + 63) / 64, (N + 63) / 64, ksplit);
-    k_gemm_bf16<<<grid, 128, 0, st>>>(M, N, K, A, sAi, sAk, B, sBk, sBj, C, ldc, ksplit > 1);
+    dim3 grid((M + 127) / 128, (N + 127) / 128, ksplit);
+    k_gemm_tc<<<grid, 128, 0, st>>>(M, N, K, A, sAi, sAk, B, sBk, sBj, C, ldc, ksplit > 1, err);
 }
 
 // ---------- elementwise pieces ----------
@@ -267,7 +350,7 @@ static int mlp_forward(pb_mlp* m, const float* X, int n)
     for (int l = 0; l < m->nl; ++l) {
         const int k = m->din[l], d = m->dout[l];
         // Z = A W^T: B(kk, j) = W[j][kk]
-        gemm(m->st, n, d, k, m->Ab[l], k, 1, m->Wb + m->woff[l], 1, k, m->Z[l], d, 1);
+        gemm(m->st, n, d, k, m->Ab[l], k, 1, m->Wb + m->woff[l], 1, k, m->Z[l], d, 1, m->derr);
         k_bias_act<<<grid1((long long)n * d), 256, 0, m->st>>>(n, d, m->W + m->boff[l], m->Z[l], m->Ab[l + 1],
                                                                l + 1 < m->nl);
     }
@@ -287,11 +370,11 @@ static int mlp_backward(pb_mlp* m, const float* T, int n)
         const int k = m->din[l], d = m->dout[l];
         // dW = dZ^T A: A-operand (i = out unit, kk = row) = dZ[kk][i]; B(kk = row, j = in) = A[kk][j]
         const int ks = std::max(1, std::min(64, n / 2048));
-        gemm(m->st, d, k, n, m->dZb, 1, d, m->Ab[l], k, 1, m->G + m->woff[l], k, ks);
+        gemm(m->st, d, k, n, m->dZb, 1, d, m->Ab[l], k, 1, m->G + m->woff[l], k, ks, m->derr);
         k_colsum<<<d, 256, 0, m->st>>>(n, d, m->dZb, m->G + m->boff[l]);
         if (l > 0) {
             // dA_prev = dZ W: A(i = row, kk = out) = dZ[i][kk]; B(kk = out, j = in) = W[kk][j]
-            gemm(m->st, n, k, d, m->dZb, d, 1, m->Wb + m->woff[l], k, 1, m->dA, k, 1);
+            gemm(m->st, n, k, d, m->dZb, d, 1, m->Wb + m->woff[l], k, 1, m->dA, k, 1, m->derr);
             k_relu_back<<<grid1((long long)n * k), 256, 0, m->st>>>((long long)n * k, m->Z[l - 1], m->dA, m->dZb);
         }
     }
@@ -432,51 +515,6 @@ struct MlpDesc {
 // 32 rows back with tcgen05.ld, adds the bias, applies ReLU, rounds to BF16 and writes the next
 // layer's operand in place. Every wait is bounded: a wait that gives up sets *err, lets the MMAs
 // in flight finish (bounded again), frees the tensor memory and leaves.
-#define TC_ROWS 128
-__device__ __forceinline__ unsigned tc_su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-// shared-memory matrix descriptor: start address, leading (K) and stride (8-row) byte offsets,
-// descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t tc_desc(unsigned addr, unsigned lbo, unsigned sbo)
-{
-    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-           (1ull << 46);
-}
-// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M = 128
-__device__ __forceinline__ unsigned tc_idesc(int nn)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(nn >> 3) << 17) | ((unsigned)(TC_ROWS >> 4) << 24);
-}
-__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned ph)
-{
-    for (unsigned it = 0; it < (1u << 24); ++it) {
-        unsigned ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok) : "r"(bar), "r"(ph) : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// byte offset of element (r, k) in the no-swizzle K-major layout of a matrix with K columns
-__device__ __forceinline__ unsigned tc_off(int r, int k, int K) { return (r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
-// 32 consecutive FP32 accumulator columns of this warp's 32 lanes (rows)
-__device__ __forceinline__ void tc_ld32(unsigned taddr, float* v)
-{
-    unsigned r[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 static size_t tc_smem(int nl, int din0)
 {
     return sizeof(__nv_bfloat16) * ((size_t)FUSED_W * din0 + (size_t)(nl - 2) * FUSED_W * FUSED_W + 16 * FUSED_W +
@@ -627,15 +665,7 @@ static int mlp_forward_fused(pb_mlp* m, const float* X, int n, float* Y)
     const int grid = std::max(1, std::min(tiles, nsm));  // one block per SM (its tensor memory and shared memory)
     k_mlp_tc<<<grid, 128, smem, m->st>>>(n, X, m->W, md, Y, m->derr);
     if (cudaGetLastError() != cudaSuccess) return mlp_fail(m, PB_ERR_CUDA, "mlp fused forward launch failed");
-    int herr = 0;
-    if (cudaMemcpyAsync(&herr, m->derr, sizeof(int), cudaMemcpyDeviceToHost, m->st) != cudaSuccess ||
-        cudaStreamSynchronize(m->st) != cudaSuccess)
-        return mlp_fail(m, PB_ERR_CUDA, "mlp fused forward failed");
-    if (herr) {
-        cudaMemsetAsync(m->derr, 0, sizeof(int), m->st);
-        return mlp_fail(m, PB_ERR_TIMEOUT, "mlp: a bounded wait on the tensor cores gave up");
-    }
-    return PB_OK;
+    return mlp_check_err(m);
 }
 
 extern "C" int pb_mlp_forward(pb_mlp* m, const float* X, int n, float* Y)
@@ -652,6 +682,18 @@ extern "C" int pb_mlp_forward(pb_mlp* m, const float* X, int n, float* Y)
     return PB_OK;
 }
 
+// PB_ERR_TIMEOUT (and the flag cleared) if a bounded wait of a tensor-core kernel gave up
+static int mlp_check_err(pb_mlp* m)
+{
+    int herr = 0;
+    if (cudaMemcpyAsync(&herr, m->derr, sizeof(int), cudaMemcpyDeviceToHost, m->st) != cudaSuccess ||
+        cudaStreamSynchronize(m->st) != cudaSuccess)
+        return mlp_fail(m, PB_ERR_CUDA, "mlp: sync failed");
+    if (!herr) return PB_OK;
+    cudaMemsetAsync(m->derr, 0, sizeof(int), m->st);
+    return mlp_fail(m, PB_ERR_TIMEOUT, "mlp: a bounded wait on the tensor cores gave up");
+}
+
 extern "C" int pb_mlp_gradient(pb_mlp* m, const float* X, const float* T, int n, float* loss, float* grad_host)
 {
     if (!m || !X || !T || n < 1) return PB_ERR_ARG;
@@ -664,7 +706,7 @@ extern "C" int pb_mlp_gradient(pb_mlp* m, const float* X, const float* T, int n,
         cudaMemcpyAsync(grad_host, m->G, sizeof(float) * m->nparam, cudaMemcpyDeviceToHost, m->st) != cudaSuccess)
         return mlp_fail(m, PB_ERR_CUDA, "mlp: copy failed");
     if (cudaStreamSynchronize(m->st) != cudaSuccess) return mlp_fail(m, PB_ERR_CUDA, "mlp: sync failed");
-    return PB_OK;
+    return mlp_check_err(m);
 }
 
 extern "C" int pb_mlp_train_step(pb_mlp* m, const float* X, const float* T, int n, float lr, float* loss)
