@@ -290,8 +290,9 @@ FF_INST_PER_SS_POINT = {1: 685, 2: 613, 3: 363}
 # for one product / one build), by workload, from the captures summarised in profiles/; None
 # where no capture of the current kernel exists
 TRAFFIC_BYTES = {
-    # profiles/k_near_tile_kirkwood_l6.md (near), round-one singular capture
-    "sphere_l6_p8_leaf64": {"near": 5.791e6, "m2l": None, "singular": 2.0755e7, "pcbuild": None},
+    # profiles/k_singular_ff1_kirkwood_l6.md (singular); the near-field kernel has changed since
+    # its sphere capture
+    "sphere_l6_p8_leaf64": {"near": None, "m2l": None, "singular": 2.0755e7, "pcbuild": None},
     # profiles/traffic_molecule20k_mixed_p8.md: near, the six MtL levels of one product, the
     # singular pass, the three block-inversion classes of one build
     "molecule_20000_p8_leaf64": {"near": 1.4529e8, "m2l": 7.101e8, "singular": 1.9617e9, "pcbuild": 4.4800e9},

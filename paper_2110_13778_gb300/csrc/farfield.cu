@@ -710,15 +710,18 @@ __global__ void __launch_bounds__(64, 1) k_m2l_seg(int nch, const int* __restric
                                                    const float* __restrict__ s0, const float* __restrict__ sk,
                                                    float* __restrict__ l0, float* __restrict__ lk,
                                                    float* __restrict__ p0, float* __restrict__ pk,
-                                                   int* __restrict__ err, long long sstr)
+                                                   int* __restrict__ err, long long sstr, int nr)
 {
-    // right-hand side blockIdx.y: the same derivative tables, its own moments
+    // block x = chunk * nr + right-hand side r: the nr blocks of a chunk are adjacent in launch
+    // order, so its derivative block comes from HBM once and from L2 for the other vectors
     const int kern = blockIdx.z;
+    const int r = (int)(blockIdx.x % (unsigned)nr);
+    const int k = (int)(blockIdx.x / (unsigned)nr);
     const float* D = kern ? Dk : D0;
     constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6;
-    const float* sig = (kern ? sk : s0) + blockIdx.y * sstr;
-    float* out = (kern ? lk : l0) + blockIdx.y * sstr;
-    float* part = (kern ? pk : p0) + (size_t)blockIdx.y * nch * 2 * T;
+    const float* sig = (kern ? sk : s0) + r * sstr;
+    float* out = (kern ? lk : l0) + r * sstr;
+    float* part = (kern ? pk : p0) + (size_t)r * nch * 2 * T;
     constexpr unsigned CH = T * 32 * sizeof(float);  // bytes of one derivative block (multiple of 16)
     constexpr int NL = M2LWarp<P, 0>::n > M2LWarp<P, 1>::n ? M2LWarp<P, 0>::n : M2LWarp<P, 1>::n;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -727,7 +730,6 @@ __global__ void __launch_bounds__(64, 1) k_m2l_seg(int nch, const int* __restric
     float* Ds = (float*)dsm;    // [T * 32]
     float* Ms = Ds + T * 32;    // [T * 33]; with Ds, the reduction scratch [T * 33]
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const int k = blockIdx.x;
     if (k >= nch) return;
     const int jl = ssrc[(size_t)k * 32 + lane];
     if (wi == 0) tg[lane] = jl >= 0 ? stgt[(size_t)k * 32 + lane] : -1;
@@ -1142,12 +1144,12 @@ static int m2l_fast_launch(pb_ctx* c, PbLevel& lv, int nr, cudaStream_t st)
         const int nch = (int)(lv.nslots / 32);
         size_t smem = (size_t)T * (32 + 33) * sizeof(float);
         if (nch > 0) {
+            if ((long long)nch * nr > 0x7fffffffLL) return pb_fail(c, PB_ERR_ARG, "far field: too many chunks x vectors");
             PB_CUDA(c, cudaFuncSetAttribute(k_m2l_seg<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_m2l_seg<P><<<dim3(nch, nr, 2), 64, smem, st>>>(nch, lv.slot_off, lv.slot_src, lv.slot_tgt,
-                                                              (const float*)lv.D0, (const float*)lv.Dk,
-                                                              (const float*)lv.sig0, (const float*)lv.sigk,
-                                                              (float*)lv.lam0, (float*)lv.lamk, (float*)lv.Mp0,
-                                                              (float*)lv.Mpk, c->dev_err, sstr);
+            k_m2l_seg<P><<<dim3((unsigned)(nch * nr), 1, 2), 64, smem, st>>>(
+                nch, lv.slot_off, lv.slot_src, lv.slot_tgt, (const float*)lv.D0, (const float*)lv.Dk,
+                (const float*)lv.sig0, (const float*)lv.sigk, (float*)lv.lam0, (float*)lv.lamk, (float*)lv.Mp0,
+                (float*)lv.Mpk, c->dev_err, sstr, nr);
             PB_LAUNCH(c);
         }
         const long long ne = (long long)lv.ncl * T;
