@@ -22,8 +22,10 @@
 #include <algorithm>
 #include <vector>
 
+#include "f32x2.cuh"
 #include "kernels.cuh"
 #include "pb_internal.cuh"
+
 
 #define NEAR_T 128
 #define NEAR_ITEM 6    // pair tiles per warp of the mixed-precision near field
@@ -131,41 +133,7 @@ __global__ void k_near_pack(int nt, const float4* __restrict__ e32p, const float
 }
 
 
-// One pair of the tile kernel: the forward terms of target x (position tp + tl, normal tn) from
-// source y (a + l, normal b, densities a.w = A phi, b.w = A dphi), and the reverse terms of y
-// from x (tphi = A phi, tdphi = A dphi of the target). ok false drops the pair (its 1 / (4 pi r)
-// is zeroed; dx is set so that r stays finite).
-struct NearTerms {
-    float f1, f2, r1, r2;
-};
-__device__ __forceinline__ NearTerms near_pair(float4 tp, float4 tn, float4 tl, float tphi, float tdphi, float4 a,
-                                               float4 b, float4 l, bool ok, float eps, float inv_eps, float kappa)
-{
-    const float i4pi = 0.07957747154594767f;
-    float dx = (tp.x - a.x) + (tl.x - l.x);
-    const float dy = (tp.y - a.y) + (tl.y - l.y);
-    const float dz = (tp.z - a.z) + (tl.z - l.z);
-    if (!ok) dx = 1.0f;
-    const float r2d = dx * dx + dy * dy + dz * dz;
-    const float rinv = rsqrtf(r2d);
-    const float r = r2d * rinv, tt = kappa * r;
-    float E, g;
-    pb_screen<float>(tt, E, g);
-    const float tE = tt * E;
-    const float c1 = -g - tE;
-    const float c3 = -3.f * g - tt * tt - tE * (3.f + tt);
-    const float ri = rinv * (ok ? i4pi : 0.f), ri3 = ri * rinv * rinv;
-    const float nxd = tn.x * dx + tn.y * dy + tn.z * dz;
-    const float nyd = b.x * dx + b.y * dy + b.z * dz;
-    const float nxny = tn.x * b.x + tn.y * b.y + tn.z * b.z;
-    const float e1 = 1.f - c1;
-    const float f2 = ri3 * (eps * e1 - 1.f), f3 = ri3 * (1.f - e1 * inv_eps);
-    const float K1 = -E * ri;
-    const float K4 = ri3 * (c3 * nxd * nyd * rinv * rinv - c1 * nxny);
-    return {K1 * b.w + (nyd * f2) * a.w, (-nxd * f3) * b.w + K4 * a.w, K1 * tdphi + (-nxd * f2) * tphi,
-            (nyd * f3) * tdphi + K4 * tphi};
-}
-
+// ---------- the tile kernel (mixed precision) ----------
 // Both directions of a pair at once, by tiles of one target chunk A (up to 32 targets, lane l
 // holds A_l) and one source chunk B of nb <= 32 sources. K1 and K4 are symmetric in (x, y),
 // and with d = x_i - x_j the double-layer kernels of the reversed pair follow from the same
@@ -173,27 +141,112 @@ __device__ __forceinline__ NearTerms near_pair(float4 tp, float4 tn, float4 tl, 
 // The tiles (A, B) -- every source chunk B of the neighbour leaves c2 >= c that follows A (B
 // after A within A's own leaf) -- are cut into work items of at most NEAR_ITEM tiles of one A;
 // one warp per item, so that the warps carry nearly equal work whatever the leaf order. B's
-// records are staged in shared memory; at step s (s < nb) lane l pairs A_l with
-// B_((l + s) mod nb) and keeps the forward terms. The reverse terms of a full tile of another
-// chunk (nb = 32) ride in registers that move one lane down after every step (a shuffle), so
-// that after 32 steps lane l holds source l's sums; partial tiles add them to B's
-// shared-memory accumulators instead (FP32 shared atomics; lanes l and l + nb meet at the same
-// source). Forward sums of a chunk and reverse sums of a tile are FP32, added into FP64
-// (atomics for the reverse terms and the final forward sums; ys starts at zero). The tile of A
-// with itself keeps only the forward terms and drops the identical pair.
+// records are staged in shared memory as packed pairs (below); at step s (s < ceil(nb / 2)) lane
+// l pairs A_l with B_((l + s) mod nb) and B_((l + s + h) mod nb), h = ceil(nb / 2), and keeps
+// the forward terms. The reverse terms of a full tile of another chunk (nb = 32) ride in
+// registers that move one lane down after every step (shuffles), so that after 16 steps lane l
+// holds the sums of sources (l + 16) mod 32 and l; partial tiles add them to B's shared-memory
+// accumulators instead (FP32 shared atomics). Forward sums of a chunk and reverse sums of a
+// tile are FP32, added into FP64 (atomics for the reverse terms and the final forward sums; ys
+// starts at zero). The tile of A with itself keeps only the forward terms and drops the
+// identical pair.
 // Q2 > 1: the records are the points of a regular rule (Q2 per element, consecutive; Q2 divides
 // 32 and every leaf starts at an element, so no chunk splits an element): the pairs of points of
 // one element are dropped, which can only happen in the tile of a chunk with itself.
+//
+// Packed pairs: entry m of a staged tile holds source m in the low halves and source
+// (m + h) mod nb in the high halves, as F0 = (x, y), F1 = (z, A phi), F2 = (n_x, n_y),
+// F3 = (n_z, -A dphi) of the high coordinate parts and F4 = (x, y), F5 = (z, 0) of the low
+// parts. Every FP32 operation of the two pairs of a step is one f32x2 instruction; only the
+// reciprocal square root, the exponential and the branch of the screening function run per
+// half. (The packed instructions do not raise the FP32 rate; they halve the issue slots that
+// bound this loop.)
+struct NearTgt2 {
+    f2x px, py, pz, lx, ly, lz, nx, ny, nz, phi, dphi;
+};
+
+// s1, s2 += forward terms; q1n -= first reverse term, q2 += second reverse term (per half).
+// bump is added to r^2 of dropped pairs (so that r stays finite), scale = 1 / (4 pi) or 0.
+template <bool BUMP>
+__device__ __forceinline__ void near_pair_x2(const NearTgt2& T, const float4* __restrict__ e, f2x bump, f2x scale,
+                                             f2x eps2, f2x nieps2, f2x kappa2, f2x& s1, f2x& s2, f2x& q1n, f2x& q2)
+{
+    const float4 g0 = e[0], g1 = e[32], g2 = e[64], g3 = e[96], g4 = e[128], g5 = e[160];
+    const f2x ax = x2_pack(g0.x, g0.y), ay = x2_pack(g0.z, g0.w), az = x2_pack(g1.x, g1.y);
+    const f2x aphi = x2_pack(g1.z, g1.w);
+    const f2x bx = x2_pack(g2.x, g2.y), by = x2_pack(g2.z, g2.w), bz = x2_pack(g3.x, g3.y);
+    const f2x nadphi = x2_pack(g3.z, g3.w);
+    const f2x lx = x2_pack(g4.x, g4.y), ly = x2_pack(g4.z, g4.w), lz = x2_pack(g5.x, g5.y);
+    const f2x one = x2_dup(1.f), mone = x2_dup(-1.f), three = x2_dup(3.f);
+    const f2x dx = x2_add(x2_sub(T.px, ax), x2_sub(T.lx, lx));
+    const f2x dy = x2_add(x2_sub(T.py, ay), x2_sub(T.ly, ly));
+    const f2x dz = x2_add(x2_sub(T.pz, az), x2_sub(T.lz, lz));
+    f2x r2 = x2_fma(dz, dz, x2_fma(dy, dy, x2_mul(dx, dx)));
+    if (BUMP) r2 = x2_add(r2, bump);
+    float ra, rb;
+    x2_unpack(r2, ra, rb);
+    const f2x rinv = x2_pack(rsqrtf(ra), rsqrtf(rb));
+    const f2x tt = x2_mul(kappa2, x2_mul(r2, rinv));
+    // g / t^2 = 1/2 - t/6 + t^2/24 - ... (the Taylor series of e^-t - 1 + t), for small t
+    f2x sg = x2_fma(x2_dup(1.f / 40320.f), tt, x2_dup(-1.f / 5040.f));
+    sg = x2_fma(sg, tt, x2_dup(1.f / 720.f));
+    sg = x2_fma(sg, tt, x2_dup(-1.f / 120.f));
+    sg = x2_fma(sg, tt, x2_dup(1.f / 24.f));
+    sg = x2_fma(sg, tt, x2_dup(-1.f / 6.f));
+    sg = x2_fma(sg, tt, x2_dup(0.5f));
+    const f2x gs = x2_mul(x2_mul(sg, tt), tt);
+    float ta, tb;
+    x2_unpack(tt, ta, tb);
+    const f2x ed = x2_add(x2_pack(__expf(-ta), __expf(-tb)), mone);
+    const f2x ga = x2_add(ed, tt), eb = x2_sub(gs, tt);
+    float gsa, gsb, gaa, gab, eba, ebb, eda, edb;
+    x2_unpack(gs, gsa, gsb);
+    x2_unpack(ga, gaa, gab);
+    x2_unpack(eb, eba, ebb);
+    x2_unpack(ed, eda, edb);
+    const bool sa = ta < 0.125f, sb = tb < 0.125f;
+    const f2x g = x2_pack(sa ? gsa : gaa, sb ? gsb : gab);
+    const f2x E = x2_pack(sa ? eba : eda, sb ? ebb : edb);
+    const f2x tE = x2_mul(tt, E);
+    const f2x c1n = x2_add(g, tE);                                            // -c1
+    const f2x c3n = x2_fma(tE, x2_add(three, tt), x2_fma(tt, tt, x2_mul(three, g)));  // -c3
+    const f2x ri = x2_mul(rinv, scale);
+    const f2x ri3 = x2_mul(x2_mul(ri, rinv), rinv);
+    const f2x nxd = x2_fma(T.nz, dz, x2_fma(T.ny, dy, x2_mul(T.nx, dx)));
+    const f2x nyd = x2_fma(bz, dz, x2_fma(by, dy, x2_mul(bx, dx)));
+    const f2x nxny = x2_fma(T.nz, bz, x2_fma(T.ny, by, x2_mul(T.nx, bx)));
+    const f2x e1 = x2_add(one, c1n);
+    const f2x f2 = x2_mul(ri3, x2_fma(eps2, e1, mone));   // ri3 (eps e1 - 1)
+    const f2x f3 = x2_mul(ri3, x2_fma(nieps2, e1, one));  // ri3 (1 - e1 / eps)
+    const f2x k1n = x2_mul(E, ri);                       // -K1
+    const f2x u = x2_mul(x2_mul(nxd, nyd), x2_mul(rinv, rinv));
+    const f2x k4 = x2_mul(ri3, x2_sub(x2_mul(c1n, nxny), x2_mul(c3n, u)));
+    s1 = x2_fma(k1n, nadphi, x2_fma(x2_mul(nyd, f2), aphi, s1));
+    s2 = x2_fma(k4, aphi, x2_fma(x2_mul(nxd, f3), nadphi, s2));
+    q1n = x2_fma(k1n, T.dphi, x2_fma(x2_mul(nxd, f2), T.phi, q1n));
+    q2 = x2_fma(k4, T.phi, x2_fma(x2_mul(nyd, f3), T.dphi, q2));
+}
+
+__device__ __forceinline__ f2x x2_shfl_down1(f2x v, int lane)
+{
+    float a, b;
+    x2_unpack(v, a, b);
+    a = __shfl_sync(0xffffffffu, a, (lane + 1) & 31);
+    b = __shfl_sync(0xffffffffu, b, (lane + 1) & 31);
+    return x2_pack(a, b);
+}
+
 template <int Q2>
-__global__ void __launch_bounds__(256, 4) k_near_tile(int nt, int nitems, const int4* __restrict__ items,
+__global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nitems, const int4* __restrict__ items,
                                                     const int* __restrict__ tiles, const int* __restrict__ chunk_leaf,
                                                     const int* __restrict__ chunk_first, const int* __restrict__ begin,
                                                     const float4* __restrict__ sp, const float4* __restrict__ sn,
                                                     const float4* __restrict__ sl, double eps_d, double kappa_d,
                                                     double* __restrict__ ys)
 {
-    __shared__ float4 sbp[8][32], sbn[8][32], sbl[8][32];
+    __shared__ float4 fq[8][6 * 32];
     __shared__ float rv1[8][32], rv2[8][32];
+    const float i4pi = 0.07957747154594767f;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     if (w >= nitems) return;
@@ -203,73 +256,118 @@ __global__ void __launch_bounds__(256, 4) k_near_tile(int nt, int nitems, const 
     const int k = a0 + lane;
     const bool act = k < begin[c + 1];
     const int kk = act ? k : a0;
-    const float4 tp = sp[kk], tn = sn[kk], tl = sl[kk];
-    const float tphi = act ? tp.w : 0.f, tdphi = act ? tn.w : 0.f;  // A phi_i, A dphi_i of the target
-    const float eps = (float)eps_d, inv_eps = (float)(1.0 / eps_d), kappa = (float)kappa_d;
+    NearTgt2 T;
+    {
+        const float4 tp = sp[kk], tn = sn[kk], tl = sl[kk];
+        T.px = x2_dup(tp.x);
+        T.py = x2_dup(tp.y);
+        T.pz = x2_dup(tp.z);
+        T.lx = x2_dup(tl.x);
+        T.ly = x2_dup(tl.y);
+        T.lz = x2_dup(tl.z);
+        T.nx = x2_dup(tn.x);
+        T.ny = x2_dup(tn.y);
+        T.nz = x2_dup(tn.z);
+        T.phi = x2_dup(act ? tp.w : 0.f);
+        T.dphi = x2_dup(act ? tn.w : 0.f);
+    }
+    const f2x eps2 = x2_dup((float)eps_d), nieps2 = x2_dup((float)(-1.0 / eps_d)), kappa2 = x2_dup((float)kappa_d);
+    const f2x zero = x2_dup(0.f);
     double acc1 = 0.0, acc2 = 0.0;
+    float4* F = fq[wi];
     for (int ti = item.y; ti < item.z; ++ti) {
         const int cb = tiles[ti];
         const int b0 = chunk_first[cb], se = begin[chunk_leaf[cb] + 1];
+        const bool diag = cb == ca;
+        const int nb = min(32, se - b0);
+        if (nb <= 0) continue;  // no chunk is empty; the test keeps the indexing below in range
+        const int h = (nb + 1) >> 1;
+        // stage the tile: lane l < nb writes entry l = (source l, source (l + h) mod nb)
         {
-            const bool diag = cb == ca;
-            const int nb = min(32, se - b0);
-            const int j = b0 + lane;
+            const int j = b0 + min(lane, nb - 1);
+            const float4 p = sp[j], n = sn[j], lo = sl[j];
+            int src = lane + h;
+            if (src >= nb) src -= nb;
+            if (lane >= nb) src = lane;
+            const float Px = __shfl_sync(0xffffffffu, p.x, src), Py = __shfl_sync(0xffffffffu, p.y, src);
+            const float Pz = __shfl_sync(0xffffffffu, p.z, src), Pw = __shfl_sync(0xffffffffu, p.w, src);
+            const float Nx = __shfl_sync(0xffffffffu, n.x, src), Ny = __shfl_sync(0xffffffffu, n.y, src);
+            const float Nz = __shfl_sync(0xffffffffu, n.z, src), Nw = __shfl_sync(0xffffffffu, n.w, src);
+            const float Lx = __shfl_sync(0xffffffffu, lo.x, src), Ly = __shfl_sync(0xffffffffu, lo.y, src);
+            const float Lz = __shfl_sync(0xffffffffu, lo.z, src);
             __syncwarp();
             if (lane < nb) {
-                sbp[wi][lane] = sp[j];
-                sbn[wi][lane] = sn[j];
-                sbl[wi][lane] = sl[j];
+                F[lane] = make_float4(p.x, Px, p.y, Py);
+                F[32 + lane] = make_float4(p.z, Pz, p.w, Pw);
+                F[64 + lane] = make_float4(n.x, Nx, n.y, Ny);
+                F[96 + lane] = make_float4(n.z, Nz, -n.w, -Nw);
+                F[128 + lane] = make_float4(lo.x, Lx, lo.y, Ly);
+                F[160 + lane] = make_float4(lo.z, Lz, 0.f, 0.f);
             }
-            float s1 = 0.f, s2 = 0.f;
-            if (!diag && nb == 32) {
-                // a full tile of another chunk: lane l meets source (l + s) mod 32 at step s and
-                // carries that source's reverse sums, which move one lane down after each step;
-                // after 32 steps lane l holds source l's
-                __syncwarp();
-                float q1 = 0.f, q2 = 0.f;
-                int m = lane;
-#pragma unroll 4
-                for (int s = 0; s < 32; ++s) {
-                    const NearTerms t = near_pair(tp, tn, tl, tphi, tdphi, sbp[wi][m], sbn[wi][m], sbl[wi][m], act,
-                                                  eps, inv_eps, kappa);
-                    s1 += t.f1;
-                    s2 += t.f2;
-                    q1 = __shfl_sync(0xffffffffu, q1 + t.r1, (lane + 1) & 31);
-                    q2 = __shfl_sync(0xffffffffu, q2 + t.r2, (lane + 1) & 31);
-                    m = (m + 1) & 31;
-                }
-                acc1 += (double)s1;
-                acc2 += (double)s2;
-                atomicAdd(&ys[j], (double)q1);
-                atomicAdd(&ys[nt + j], (double)q2);
-            } else {
-                rv1[wi][lane] = 0.f;
-                rv2[wi][lane] = 0.f;
-                __syncwarp();
-                int m = lane % nb;
+            __syncwarp();
+        }
+        f2x s1 = zero, s2 = zero;
+        if (!diag && nb == 32) {
+            // full tile of another chunk: lane l meets sources (l + s) mod 32 and (l + s + 16)
+            // mod 32 at step s; the reverse sums move one lane down after every step
+            const f2x sc = x2_dup(act ? i4pi : 0.f);
+            f2x q1n = zero, q2 = zero;
+            int m = lane;
 #pragma unroll 2
-                for (int s = 0; s < nb; ++s) {
-                    // drop the identical pair (the correction's) and padding targets
-                    const bool ok = act && !(diag && (Q2 == 1 ? m == lane : m / Q2 == lane / Q2));
-                    const NearTerms t = near_pair(tp, tn, tl, tphi, tdphi, sbp[wi][m], sbn[wi][m], sbl[wi][m], ok,
-                                                  eps, inv_eps, kappa);
-                    s1 += t.f1;
-                    s2 += t.f2;
-                    if (!diag) {
-                        atomicAdd(&rv1[wi][m], t.r1);
-                        atomicAdd(&rv2[wi][m], t.r2);
-                    }
-                    m = m + 1 == nb ? 0 : m + 1;
+            for (int s = 0; s < 16; ++s) {
+                near_pair_x2<false>(T, F + m, zero, sc, eps2, nieps2, kappa2, s1, s2, q1n, q2);
+                q1n = x2_shfl_down1(q1n, lane);
+                q2 = x2_shfl_down1(q2, lane);
+                m = (m + 1) & 31;
+            }
+            // lane l: the low halves belong to source (l + 16) mod 32, the high halves to l
+            float a1, b1, a2, b2;
+            x2_unpack(q1n, a1, b1);
+            x2_unpack(q2, a2, b2);
+            const float t1 = b1 + __shfl_sync(0xffffffffu, a1, (lane + 16) & 31);
+            const float t2 = b2 + __shfl_sync(0xffffffffu, a2, (lane + 16) & 31);
+            atomicAdd(&ys[b0 + lane], -(double)t1);
+            atomicAdd(&ys[nt + b0 + lane], (double)t2);
+        } else {
+            rv1[wi][lane] = 0.f;
+            rv2[wi][lane] = 0.f;
+            __syncwarp();
+            int m = lane % nb;
+            int m2 = m + h;
+            if (m2 >= nb) m2 -= nb;
+            const bool odd = nb & 1;
+            for (int s = 0; s < h; ++s) {
+                // drop the identical pair (the correction's), padding targets and, for odd nb,
+                // the repeated source of the last step
+                const bool okl = act && !(diag && (Q2 == 1 ? m == lane : m / Q2 == lane / Q2));
+                const bool okh = act && !(odd && s == h - 1) && !(diag && (Q2 == 1 ? m2 == lane : m2 / Q2 == lane / Q2));
+                const f2x bump = x2_pack(okl ? 0.f : 1.f, okh ? 0.f : 1.f);
+                const f2x sc = x2_pack(okl ? i4pi : 0.f, okh ? i4pi : 0.f);
+                f2x q1n = zero, q2 = zero;
+                near_pair_x2<true>(T, F + m, bump, sc, eps2, nieps2, kappa2, s1, s2, q1n, q2);
+                if (!diag) {
+                    float a1, b1, a2, b2;
+                    x2_unpack(q1n, a1, b1);
+                    x2_unpack(q2, a2, b2);
+                    atomicAdd(&rv1[wi][m], -a1);
+                    atomicAdd(&rv1[wi][m2], -b1);
+                    atomicAdd(&rv2[wi][m], a2);
+                    atomicAdd(&rv2[wi][m2], b2);
                 }
-                acc1 += (double)s1;
-                acc2 += (double)s2;
-                __syncwarp();
-                if (!diag && lane < nb) {
-                    atomicAdd(&ys[j], (double)rv1[wi][lane]);
-                    atomicAdd(&ys[nt + j], (double)rv2[wi][lane]);
-                }
+                m = m + 1 == nb ? 0 : m + 1;
+                m2 = m2 + 1 == nb ? 0 : m2 + 1;
+            }
+            __syncwarp();
+            if (!diag && lane < nb) {
+                atomicAdd(&ys[b0 + lane], (double)rv1[wi][lane]);
+                atomicAdd(&ys[nt + b0 + lane], (double)rv2[wi][lane]);
             }
         }
+        float a, b;
+        x2_unpack(s1, a, b);
+        acc1 += (double)(a + b);
+        x2_unpack(s2, a, b);
+        acc2 += (double)(a + b);
     }
     if (act) {
         atomicAdd(&ys[k], acc1);
