@@ -4,6 +4,7 @@
 // the triangular solve and the update run in FP64 kernels; the host only reads one residual
 // estimate per iteration to decide whether to continue.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <algorithm>
@@ -599,6 +600,175 @@ __global__ void k_gm_solve(int m, int k, GmState s)
 
 static int grid_for(long long n) { return (int)std::min<long long>((n + KB - 1) / KB, 4 * 152 * 4); }
 
+// ---------- float-float Krylov basis (mixed precision) ----------
+// On this GPU FP64 arithmetic runs at 1/64 of the FP32 rate, and CGS2 over a basis of FP64
+// vectors (one FP64 FMA per element and column, four passes per Arnoldi step) is bound by it,
+// not by HBM. In mixed precision the basis and the vector being orthogonalised are kept as
+// float-float pairs (hi, lo) instead, 8 bytes per element as before, and every dot product
+// and update runs on the FP32 pipe (about 15 FP32 instructions per element and column, a
+// 48-bit significand), which leaves the passes bound by the HBM reads of the basis. The
+// Hessenberg entries, norms and Givens rotations stay FP64; the product and the
+// preconditioner still see FP64 vectors (a copy of v_j written beside its float-float form).
+// The kernels serve the host-driven loop (explicit column counts) and the device-driven graph
+// (jdev = the device's step index; right-hand side r = the last grid dimension).
+#define FFK_CG 4         // basis vectors per block of the float-float dot products
+#define FFK_MAXCOL 201   // restart length <= 200
+
+// s += a b in float-float, renormalised once
+__device__ __forceinline__ void ffk_acc(float& sh, float& sl, float ah, float al, float bh, float bl)
+{
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float t = sh + p;
+    const float bb = t - sh;
+    sl += ((sh - (t - bb)) + (p - bb)) + e;
+    sh = t + sl;
+    sl -= sh - t;
+}
+
+__device__ __forceinline__ double ffk_to(float h, float l) { return (double)h + (double)l; }
+__device__ __forceinline__ float2 ffk_from(double x)
+{
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+
+// part_r[col * gridDim.x + blk] = partial of <V_r[col], w_r> over the block's elements for the
+// FFK_CG columns blockIdx.y * FFK_CG + q < ncol (ncol = *jdev + 1 when jdev is given); with
+// V == nullptr, <w_r, w_r> into column 0
+__global__ void __launch_bounds__(KB) k_ffdot(long long n, int ncol, const int* __restrict__ jdev,
+                                              const float2* __restrict__ V, long long vstr,
+                                              const float2* __restrict__ w, double* __restrict__ part, long long pstr)
+{
+    __shared__ double red[FFK_CG][KB / 32];
+    const int r = blockIdx.z;
+    if (jdev) ncol = *jdev + 1;
+    const int c0 = blockIdx.y * FFK_CG;
+    const int nc = V ? min(FFK_CG, ncol - c0) : (blockIdx.y == 0 ? 1 : 0);
+    if (nc <= 0) return;
+    w += r * n;
+    part += r * pstr;
+    const float2* v = V ? V + r * vstr + (size_t)c0 * n : w;
+    float sh[FFK_CG] = {}, sl[FFK_CG] = {};
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        const float2 b = w[i];
+#pragma unroll
+        for (int q = 0; q < FFK_CG; ++q)
+            if (q < nc) {
+                const float2 a = v[(size_t)q * n + i];
+                ffk_acc(sh[q], sl[q], a.x, a.y, b.x, b.y);
+            }
+    }
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < FFK_CG; ++q) {
+        double s = ffk_to(sh[q], sl[q]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[q][wi] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        double s = 0.0;
+        for (int k = 0; k < KB / 32; ++k) s += red[threadIdx.x][k];
+        part[(size_t)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// wf_r (float-float) = w_r (FP64), the vectors the product wrote
+__global__ void k_to_ff(long long n, const double* __restrict__ w, float2* __restrict__ wf)
+{
+    const long long o = blockIdx.y * n;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB)
+        wf[o + i] = ffk_from(w[o + i]);
+}
+
+// w_r -= V_r[:, 0..ncol) h_r in float-float (h FP64, split once per block; ncol = *jdev + 1 when
+// jdev is given)
+__global__ void __launch_bounds__(KB) k_fforth(long long n, int ncol, const int* __restrict__ jdev,
+                                               const float2* __restrict__ V, long long vstr,
+                                               const double* __restrict__ h, long long hstr, float2* __restrict__ w)
+{
+    __shared__ float2 hs[FFK_MAXCOL];
+    const int r = blockIdx.y;
+    if (jdev) ncol = *jdev + 1;
+    V += r * vstr;
+    h += r * hstr;
+    w += r * n;
+    for (int q = threadIdx.x; q < ncol; q += KB) hs[q] = ffk_from(h[q]);
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        float sh = 0.f, sl = 0.f;
+        int q = 0;
+        for (; q + 4 <= ncol; q += 4) {
+            const float2 a0 = V[(size_t)q * n + i], a1 = V[(size_t)(q + 1) * n + i];
+            const float2 a2 = V[(size_t)(q + 2) * n + i], a3 = V[(size_t)(q + 3) * n + i];
+            ffk_acc(sh, sl, a0.x, a0.y, hs[q].x, hs[q].y);
+            ffk_acc(sh, sl, a1.x, a1.y, hs[q + 1].x, hs[q + 1].y);
+            ffk_acc(sh, sl, a2.x, a2.y, hs[q + 2].x, hs[q + 2].y);
+            ffk_acc(sh, sl, a3.x, a3.y, hs[q + 3].x, hs[q + 3].y);
+        }
+        for (; q < ncol; ++q) {
+            const float2 a = V[(size_t)q * n + i];
+            ffk_acc(sh, sl, a.x, a.y, hs[q].x, hs[q].y);
+        }
+        // w - s: two-sum of the high parts, then the low parts, renormalised
+        const float2 b = w[i];
+        const float t = b.x - sh;
+        const float bb = t - b.x;
+        float e = ((b.x - (t - bb)) + (-sh - bb)) + (b.y - sl);
+        const float s = t + e;
+        e -= s - t;
+        w[i] = make_float2(s, e);
+    }
+}
+
+// V_r[:, c] = w_r / sqrt(small_r[hoff + c]) in float-float, and vd_r = the same in FP64 (the next
+// product's input), c = 0 for the start of a cycle (first), else (the step index) + 1 with the
+// step from *jdev or jhost. The source is w64_r (FP64) when given, else wf_r.
+__global__ void k_ffscale(long long n, const float2* __restrict__ wf, const double* __restrict__ w64,
+                          const double* __restrict__ small, long long sstr, long long hoff, const int* __restrict__ jdev,
+                          int jhost, int first, float2* __restrict__ V, long long vstr, double* __restrict__ vd)
+{
+    const int r = blockIdx.y;
+    const int c = first ? 0 : (jdev ? *jdev : jhost) + 1;
+    const double f = 1.0 / sqrt(small[r * sstr + hoff + c]);
+    const float fh = (float)f, fl = (float)(f - (double)fh);
+    float2* dst = V + r * vstr + (size_t)c * n;
+    vd += r * n;
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        const float2 a = w64 ? ffk_from(w64[r * n + i]) : wf[r * n + i];
+        float sh = 0.f, sl = 0.f;
+        ffk_acc(sh, sl, a.x, a.y, fh, fl);
+        dst[i] = make_float2(sh, sl);
+        vd[i] = ffk_to(sh, sl);
+    }
+}
+
+// u_r = V_r[:, 0..k) y_r (FP64 out), k = ksteps[r] when given, else khost
+__global__ void __launch_bounds__(KB) k_ffcombine(long long n, int khost, const int* __restrict__ ksteps,
+                                                  const float2* __restrict__ V, long long vstr,
+                                                  const double* __restrict__ y, long long ystr, double* __restrict__ u)
+{
+    __shared__ float2 ys[FFK_MAXCOL];
+    const int r = blockIdx.y;
+    const int k = ksteps ? ksteps[r] : khost;
+    V += r * vstr;
+    y += r * ystr;
+    u += r * n;
+    for (int q = threadIdx.x; q < k; q += KB) ys[q] = ffk_from(y[q]);
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
+        float sh = 0.f, sl = 0.f;
+        for (int q = 0; q < k; ++q) {
+            const float2 a = V[(size_t)q * n + i];
+            ffk_acc(sh, sl, a.x, a.y, ys[q].x, ys[q].y);
+        }
+        u[i] = ffk_to(sh, sl);
+    }
+}
+
 int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max_iter, int restart,
                     pb_solve_info* info, bool x_zero)
 {
@@ -613,6 +783,11 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
         c->gmz = (double*)pb_alloc(c, sizeof(double) * n);
         c->gmpart = (double*)pb_alloc(c, sizeof(double) * DOT_BLOCKS * (m + 2));
         c->gmsmall = (double*)pb_alloc(c, sizeof(double) * ((m + 1) * m + 6 * (m + 2)));
+        if (c->prm.precision == PB_MIXED) {  // float-float work vector, FP64 copy of v_j
+            c->gmwf = (float2*)pb_alloc(c, sizeof(float2) * n);
+            c->gmvd = (double*)pb_alloc(c, sizeof(double) * n);
+            if (!c->gmwf || !c->gmvd) c->gmV = nullptr;
+        }
         if (!c->gmV || !c->gmw || !c->gmz || !c->gmpart || !c->gmsmall) {
             c->gm_m = 0;
             return pb_fail(c, PB_ERR_NOMEM, "gmres: out of memory");
@@ -620,6 +795,10 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
         c->gm_m = m;
     }
     double *V = c->gmV, *w = c->gmw, *z = c->gmz, *part = c->gmpart, *small = c->gmsmall;
+    // mixed precision: the basis as float-float pairs in the same storage
+    const bool ffb = c->prm.precision == PB_MIXED;
+    float2 *Vf = (float2*)c->gmV, *wf = c->gmwf;
+    double* vd = c->gmvd;
     GmState s;
     s.H = small;
     s.cs = s.H + (size_t)(m + 1) * m;
@@ -680,7 +859,10 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
         PB_LAUNCH(c);
         k_finish<<<1, KB, 0, c->st>>>(DOT_BLOCKS, part, s.hcol, 0);
         PB_LAUNCH(c);
-        k_scale<<<G, KB, 0, c->st>>>(n, w, s.hcol, V);
+        if (ffb)
+            k_ffscale<<<dim3(G, 1), KB, 0, c->st>>>(n, nullptr, w, s.hcol, 0, 0, nullptr, 0, 1, Vf, 0, vd);
+        else
+            k_scale<<<G, KB, 0, c->st>>>(n, w, s.hcol, V);
         PB_LAUNCH(c);
         k_gm_start<<<1, 1, 0, c->st>>>(m, s);
         PB_LAUNCH(c);
@@ -699,13 +881,35 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
         }
         int k = 0;
         for (int j = 0; j < m && it < max_iter; ++j) {
-            double* vj = V + (size_t)j * n;
+            double* vj = ffb ? vd : V + (size_t)j * n;
             if ((rc = pb_precond_apply_sorted(c, vj, z))) return rc;
             if ((rc = pb_matvec_sorted(c, z, w, 0))) return rc;
             inf.matvecs++;
             pb_tic(c, PB_T_ARNOLDI);
             // CGS2
-            for (int pass = 0; pass < 2; ++pass) {
+            if (ffb) {
+                k_to_ff<<<dim3(G, 1), KB, 0, c->st>>>(n, w, wf);
+                PB_LAUNCH(c);
+                const unsigned ng = (unsigned)((j + 1 + FFK_CG - 1) / FFK_CG);
+                for (int pass = 0; pass < 2; ++pass) {
+                    double* h = pass ? s.y : s.hcol;
+                    k_ffdot<<<dim3(DOT_BLOCKS, ng, 1), KB, 0, c->st>>>(n, j + 1, nullptr, Vf, 0, wf, part, 0);
+                    PB_LAUNCH(c);
+                    k_finish<<<j + 1, KB, 0, c->st>>>(DOT_BLOCKS, part, h, 0);
+                    PB_LAUNCH(c);
+                    k_fforth<<<dim3(G, 1), KB, 0, c->st>>>(n, j + 1, nullptr, Vf, 0, h, 0, wf);
+                    PB_LAUNCH(c);
+                }
+                k_axpy1<<<1, KB, 0, c->st>>>(j + 1, s.y, s.hcol);
+                PB_LAUNCH(c);
+                k_ffdot<<<dim3(DOT_BLOCKS, 1, 1), KB, 0, c->st>>>(n, 1, nullptr, nullptr, 0, wf, part, 0);
+                PB_LAUNCH(c);
+                k_finish<<<1, KB, 0, c->st>>>(DOT_BLOCKS, part, s.hcol + j + 1, 0);
+                PB_LAUNCH(c);
+                k_ffscale<<<dim3(G, 1), KB, 0, c->st>>>(n, wf, nullptr, s.hcol, 0, 0, nullptr, j, 0, Vf, 0, vd);
+                PB_LAUNCH(c);
+            }
+            for (int pass = 0; pass < 2 && !ffb; ++pass) {
                 k_multidot<<<dim3(DOT_BLOCKS, j + 1), KB, 0, c->st>>>(n, V, w, part);
                 PB_LAUNCH(c);
                 k_finish<<<j + 1, KB, 0, c->st>>>(DOT_BLOCKS, part, pass ? s.y : s.hcol, 0);
@@ -713,15 +917,17 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
                 k_orth_update<<<G, KB, 0, c->st>>>(n, j + 1, V, pass ? s.y : s.hcol, w);
                 PB_LAUNCH(c);
             }
-            // merge the two passes: hcol[i] += y[i]
-            k_axpy1<<<1, KB, 0, c->st>>>(j + 1, s.y, s.hcol);
-            PB_LAUNCH(c);
-            k_multidot<<<dim3(DOT_BLOCKS, 1), KB, 0, c->st>>>(n, nullptr, w, part);
-            PB_LAUNCH(c);
-            k_finish<<<1, KB, 0, c->st>>>(DOT_BLOCKS, part, s.hcol + j + 1, 0);
-            PB_LAUNCH(c);
-            k_scale<<<G, KB, 0, c->st>>>(n, w, s.hcol + j + 1, V + (size_t)(j + 1) * n);
-            PB_LAUNCH(c);
+            if (!ffb) {
+                // merge the two passes: hcol[i] += y[i]
+                k_axpy1<<<1, KB, 0, c->st>>>(j + 1, s.y, s.hcol);
+                PB_LAUNCH(c);
+                k_multidot<<<dim3(DOT_BLOCKS, 1), KB, 0, c->st>>>(n, nullptr, w, part);
+                PB_LAUNCH(c);
+                k_finish<<<1, KB, 0, c->st>>>(DOT_BLOCKS, part, s.hcol + j + 1, 0);
+                PB_LAUNCH(c);
+                k_scale<<<G, KB, 0, c->st>>>(n, w, s.hcol + j + 1, V + (size_t)(j + 1) * n);
+                PB_LAUNCH(c);
+            }
             k_gm_givens<<<1, 1, 0, c->st>>>(m, j, s);
             PB_LAUNCH(c);
             pb_toc(c, PB_T_ARNOLDI);
@@ -744,7 +950,10 @@ int pb_gmres_sorted(pb_ctx* c, double* xs, const double* bs, double tol, int max
             // x += M^-1 V y
             k_gm_solve<<<1, 1, 0, c->st>>>(m, k, s);
             PB_LAUNCH(c);
-            k_combine<<<G, KB, 0, c->st>>>(n, k, V, s.y, w);
+            if (ffb)
+                k_ffcombine<<<dim3(G, 1), KB, 0, c->st>>>(n, k, nullptr, Vf, 0, s.y, 0, w);
+            else
+                k_combine<<<G, KB, 0, c->st>>>(n, k, V, s.y, w);
             PB_LAUNCH(c);
             if ((rc = pb_precond_apply_sorted(c, w, z))) return rc;
             k_axpy1<<<G, KB, 0, c->st>>>(n, z, xs);
@@ -1496,7 +1705,9 @@ int pb_dg_reserve(pb_ctx* c, int nr, int m, int nctl)
     (void)S;
     if (nr > c->dg_nr) {
         c->dgVcur = (double*)pb_alloc(c, sizeof(double) * (size_t)(n * nr));
-        if (!c->dgVcur) return pb_fail(c, PB_ERR_NOMEM, "gmres workspace: out of memory");
+        c->dgWf = c->prm.precision == PB_MIXED ? (float2*)pb_alloc(c, sizeof(float2) * (size_t)(n * nr)) : nullptr;
+        if (!c->dgVcur || (c->prm.precision == PB_MIXED && !c->dgWf))
+            return pb_fail(c, PB_ERR_NOMEM, "gmres workspace: out of memory");
         c->dg_nr = nr;
     }
     if (nctl > c->dg_nctl) {
@@ -1561,6 +1772,12 @@ int pb_dg_append(pb_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>& d
     const long long vstr = (long long)(m + 1) * n, pstr = (long long)DOT_BLOCKS * (m + 2);
     double *V = c->gbV, *W = c->gbW, *Z = c->gbZ, *part = c->gbpart, *small = c->gbsmall, *Vc = c->dgVcur;
     DgCtl* ctl = (DgCtl*)c->dgctl + ictl;
+    // mixed precision: float-float basis in the same storage (the step index and the per-vector
+    // step counts read by the kernels from the control block)
+    const bool ffb = c->prm.precision == PB_MIXED;
+    float2 *Vf = (float2*)c->gbV, *Wf = c->dgWf;
+    const int* jdev = (const int*)((const char*)ctl + offsetof(DgCtl, j));
+    const int* ksteps = (const int*)((const char*)ctl + offsetof(DgCtl, steps));
     const GmState st = gm_state(small, m);
     const long long hoff = st.hcol - small, yoff = st.y - small, roff = st.res - small;
     cudaGraphConditionalHandle hO, hI;
@@ -1601,7 +1818,10 @@ int pb_dg_append(pb_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>& d
         PB_LAUNCH(c);
         k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff, S);
         PB_LAUNCH(c);
-        k_dg_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, small, S, hoff, V, vstr, Vc, ctl, 1);
+        if (ffb)
+            k_ffscale<<<dim3(G, nr), KB, 0, c->st>>>(n, nullptr, W, small, S, hoff, nullptr, 0, 1, Vf, vstr, Vc);
+        else
+            k_dg_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, small, S, hoff, V, vstr, Vc, ctl, 1);
         PB_LAUNCH(c);
         k_bgm_start<<<nr, 1, 0, c->st>>>(m, st, S);
         PB_LAUNCH(c);
@@ -1628,21 +1848,39 @@ int pb_dg_append(pb_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>& d
     do {
         if ((rc = pb_precond_apply_multi(c, Vc, n, Z, n, nr))) break;
         if ((rc = pb_matvec_sorted_multi(c, Z, W, nr))) break;
+        if (ffb) {
+            k_to_ff<<<dim3(G, nr), KB, 0, c->st>>>(n, W, Wf);
+            PB_LAUNCH(c);
+        }
         for (int pass = 0; pass < 2; ++pass) {
-            k_dg_dot<<<dim3(DOT_BLOCKS, m, nr), KB, 0, c->st>>>(n, V, vstr, W, part, pstr, ctl);
+            double* h = small + (pass ? yoff : hoff);
+            if (ffb)
+                k_ffdot<<<dim3(DOT_BLOCKS, (m + FFK_CG - 1) / FFK_CG, nr), KB, 0, c->st>>>(n, 0, jdev, Vf, vstr, Wf,
+                                                                                           part, pstr);
+            else
+                k_dg_dot<<<dim3(DOT_BLOCKS, m, nr), KB, 0, c->st>>>(n, V, vstr, W, part, pstr, ctl);
             PB_LAUNCH(c);
-            k_dg_finish<<<dim3(m, nr), KB, 0, c->st>>>(part, pstr, small + (pass ? yoff : hoff), S, ctl, 0);
+            k_dg_finish<<<dim3(m, nr), KB, 0, c->st>>>(part, pstr, h, S, ctl, 0);
             PB_LAUNCH(c);
-            k_dg_orth<<<dim3(G, nr), KB, 0, c->st>>>(n, V, vstr, small + (pass ? yoff : hoff), S, W, ctl);
+            if (ffb)
+                k_fforth<<<dim3(G, nr), KB, 0, c->st>>>(n, 0, jdev, Vf, vstr, h, S, Wf);
+            else
+                k_dg_orth<<<dim3(G, nr), KB, 0, c->st>>>(n, V, vstr, h, S, W, ctl);
             PB_LAUNCH(c);
         }
         k_dg_merge<<<nr, 64, 0, c->st>>>(small, S, yoff, hoff, ctl);
         PB_LAUNCH(c);
-        k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
+        if (ffb)
+            k_ffdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, 1, nullptr, nullptr, 0, Wf, part, pstr);
+        else
+            k_bdot<<<dim3(DOT_BLOCKS, 1, nr), KB, 0, c->st>>>(n, nullptr, 0, W, part, pstr);
         PB_LAUNCH(c);
         k_dg_finish<<<dim3(1, nr), KB, 0, c->st>>>(part, pstr, small + hoff, S, ctl, 1);
         PB_LAUNCH(c);
-        k_dg_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, small, S, hoff, V, vstr, Vc, ctl, 0);
+        if (ffb)
+            k_ffscale<<<dim3(G, nr), KB, 0, c->st>>>(n, Wf, nullptr, small, S, hoff, jdev, 0, 0, Vf, vstr, Vc);
+        else
+            k_dg_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, small, S, hoff, V, vstr, Vc, ctl, 0);
         PB_LAUNCH(c);
         k_dg_givens<<<nr, 1, 0, c->st>>>(m, st, S, ctl);
         PB_LAUNCH(c);
@@ -1658,7 +1896,10 @@ int pb_dg_append(pb_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>& d
     do {
         k_dg_solve<<<nr, 1, 0, c->st>>>(m, st, S, ctl);
         PB_LAUNCH(c);
-        k_dg_combine<<<dim3(G, nr), KB, 0, c->st>>>(n, V, vstr, small, S, yoff, W, ctl);
+        if (ffb)
+            k_ffcombine<<<dim3(G, nr), KB, 0, c->st>>>(n, 0, ksteps, Vf, vstr, small + yoff, S, W);
+        else
+            k_dg_combine<<<dim3(G, nr), KB, 0, c->st>>>(n, V, vstr, small, S, yoff, W, ctl);
         PB_LAUNCH(c);
         if ((rc = pb_precond_apply_multi(c, W, n, Z, n, nr))) break;
         k_dg_axpy<<<dim3(G, nr), KB, 0, c->st>>>(n, Z, X, ctl);
@@ -1670,7 +1911,10 @@ int pb_dg_append(pb_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>& d
         PB_LAUNCH(c);
         k_bfinish<<<dim3(1, nr), KB, 0, c->st>>>(DOT_BLOCKS, part, pstr, small + hoff, S);
         PB_LAUNCH(c);
-        k_dg_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, small, S, hoff, V, vstr, Vc, ctl, 1);
+        if (ffb)
+            k_ffscale<<<dim3(G, nr), KB, 0, c->st>>>(n, nullptr, W, small, S, hoff, nullptr, 0, 1, Vf, vstr, Vc);
+        else
+            k_dg_scale<<<dim3(G, nr), KB, 0, c->st>>>(n, W, small, S, hoff, V, vstr, Vc, ctl, 1);
         PB_LAUNCH(c);
         k_bgm_start<<<nr, 1, 0, c->st>>>(m, st, S);
         PB_LAUNCH(c);

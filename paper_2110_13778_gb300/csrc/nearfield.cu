@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(256, 3) k_near_tile(int nt, int nitems, const 
             const f2x sc = x2_dup(act ? i4pi : 0.f);
             f2x q1n = zero, q2 = zero;
             int m = lane;
-#pragma unroll 2
+#pragma unroll 4
             for (int s = 0; s < 16; ++s) {
                 near_pair_x2<false>(T, F + m, zero, sc, eps2, nieps2, kappa2, s1, s2, q1n, q2);
                 q1n = x2_shfl_down1(q1n, lane);

@@ -49,6 +49,8 @@ static void pb_free_build(pb_ctx* c)
     c->canon_check = nullptr;
     c->canon_expect = 0;
     c->gm_m = 0;
+    c->gmwf = nullptr;
+    c->gmvd = nullptr;
     c->scratch = nullptr;
     c->escratch = nullptr;
     c->qstates = nullptr;
@@ -75,6 +77,7 @@ static void pb_free_build(pb_ctx* c)
     c->pn_p32 = c->pn_l32 = c->pn_n32 = c->pn_sp = c->pn_sn = nullptr;
     c->pn_y = nullptr;
     c->dgVcur = nullptr;
+    c->dgWf = nullptr;
     c->dgctl = nullptr;
     c->dg_nr = c->dg_nctl = 0;
     ++c->build_gen;

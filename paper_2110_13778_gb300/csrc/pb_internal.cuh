@@ -180,6 +180,7 @@ struct pb_ctx {
     // vectors of nr right-hand sides, control blocks (device and pinned host copies), the cached
     // executable graph of a single-context solve with its key and captured launch counts
     double* dgVcur = nullptr;
+    float2* dgWf = nullptr;  // mixed precision: float-float work vectors of the device-driven Arnoldi step
     int dg_nr = 0;
     void* dgctl = nullptr;
     void* dgctl_h = nullptr;
@@ -218,6 +219,8 @@ struct pb_ctx {
     // GMRES workspace (Krylov basis, work vectors, reduction partials, small dense state)
     int gm_m = 0;
     double *gmV = nullptr, *gmw = nullptr, *gmz = nullptr, *gmpart = nullptr, *gmsmall = nullptr;
+    float2* gmwf = nullptr;  // mixed precision: float-float work vector of the Arnoldi step
+    double* gmvd = nullptr;  // mixed precision: FP64 copy of the current basis vector
     // timing: per slot a ring of (start, stop) event pairs, read back by pb_get_timing
     bool timing = false;
     cudaEvent_t ev[10] = {};
