@@ -564,18 +564,19 @@ __global__ void k_gm_start(int m, GmState s)
     s.res[0] = s.g[0];
 }
 
-// step j: H[:, j] = (hcol[0..j], sqrt(hcol[j+1])); apply rotations; new rotation; residual
-__global__ void k_gm_givens(int m, int j, GmState s)
+// step j: H[:, j] = (hcol[0..j], sqrt(hcol[j+1])); apply rotations; new rotation; residual.
+// The entry that rotation i - 1 left for rotation i stays in a register (a round trip through
+// global memory per rotation made this serial loop latency-bound).
+__device__ __forceinline__ void gm_givens_step(int m, int j, GmState s)
 {
     double* Hj = s.H + (size_t)j * (m + 1);
-    for (int i = 0; i <= j; ++i) Hj[i] = s.hcol[i];
-    Hj[j + 1] = sqrt(s.hcol[j + 1]);
+    double a = s.hcol[0];
     for (int i = 0; i < j; ++i) {
-        double a = Hj[i], b = Hj[i + 1];
+        const double b = s.hcol[i + 1];
         Hj[i] = s.cs[i] * a + s.sn[i] * b;
-        Hj[i + 1] = -s.sn[i] * a + s.cs[i] * b;
+        a = -s.sn[i] * a + s.cs[i] * b;
     }
-    double a = Hj[j], b = Hj[j + 1];
+    const double b = sqrt(s.hcol[j + 1]);
     double r = hypot(a, b);
     double c = r > 0 ? a / r : 1.0, sn = r > 0 ? b / r : 0.0;
     s.cs[j] = c;
@@ -586,6 +587,8 @@ __global__ void k_gm_givens(int m, int j, GmState s)
     s.g[j] = c * s.g[j];
     s.res[0] = fabs(s.g[j + 1]);
 }
+
+__global__ void k_gm_givens(int m, int j, GmState s) { gm_givens_step(m, j, s); }
 
 // back substitution: H[0..k, 0..k) y = g
 __global__ void k_gm_solve(int m, int k, GmState s)
@@ -611,7 +614,7 @@ static int grid_for(long long n) { return (int)std::min<long long>((n + KB - 1) 
 // preconditioner still see FP64 vectors (a copy of v_j written beside its float-float form).
 // The kernels serve the host-driven loop (explicit column counts) and the device-driven graph
 // (jdev = the device's step index; right-hand side r = the last grid dimension).
-#define FFK_CG 4         // basis vectors per block of the float-float dot products
+#define FFK_CG 2         // basis vectors per block of the float-float dot products
 #define FFK_MAXCOL 201   // restart length <= 200
 
 // s += a b in float-float, renormalised once
@@ -637,7 +640,9 @@ __device__ __forceinline__ float2 ffk_from(double x)
 
 // part_r[col * gridDim.x + blk] = partial of <V_r[col], w_r> over the block's elements for the
 // FFK_CG columns blockIdx.y * FFK_CG + q < ncol (ncol = *jdev + 1 when jdev is given); with
-// V == nullptr, <w_r, w_r> into column 0
+// V == nullptr, <w_r, w_r> into column 0. Each thread takes two elements a stride apart per
+// iteration, their loads issued before the sums (two columns x two elements measured 6.2 TB/s
+// on 70 basis vectors of 3.67 M elements; four columns x one element 5.5 TB/s).
 __global__ void __launch_bounds__(KB) k_ffdot(long long n, int ncol, const int* __restrict__ jdev,
                                               const float2* __restrict__ V, long long vstr,
                                               const float2* __restrict__ w, double* __restrict__ part, long long pstr)
@@ -652,14 +657,23 @@ __global__ void __launch_bounds__(KB) k_ffdot(long long n, int ncol, const int* 
     part += r * pstr;
     const float2* v = V ? V + r * vstr + (size_t)c0 * n : w;
     float sh[FFK_CG] = {}, sl[FFK_CG] = {};
-    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
-        const float2 b = w[i];
+    const long long stride = (long long)gridDim.x * KB;
+    const float2 zero = make_float2(0.f, 0.f);
+    for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += 2 * stride) {
+        const long long i2 = i + stride;
+        const bool two = i2 < n;
+        const float2 b0 = w[i], b1 = two ? w[i2] : zero;
+        float2 a0[FFK_CG], a1[FFK_CG];
 #pragma unroll
-        for (int q = 0; q < FFK_CG; ++q)
-            if (q < nc) {
-                const float2 a = v[(size_t)q * n + i];
-                ffk_acc(sh[q], sl[q], a.x, a.y, b.x, b.y);
-            }
+        for (int q = 0; q < FFK_CG; ++q) {
+            a0[q] = q < nc ? v[(size_t)q * n + i] : zero;
+            a1[q] = (q < nc && two) ? v[(size_t)q * n + i2] : zero;
+        }
+#pragma unroll
+        for (int q = 0; q < FFK_CG; ++q) {
+            ffk_acc(sh[q], sl[q], a0[q].x, a0[q].y, b0.x, b0.y);
+            ffk_acc(sh[q], sl[q], a1[q].x, a1[q].y, b1.x, b1.y);
+        }
     }
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
 #pragma unroll
@@ -1101,24 +1115,7 @@ __global__ void k_bgm_givens(int m, int j, GmState s, long long sstr)
 {
     const long long o = blockIdx.x * sstr;
     GmState t = {s.H + o, s.cs + o, s.sn + o, s.g + o, s.y + o, s.hcol + o, s.res + o};
-    double* Hj = t.H + (size_t)j * (m + 1);
-    for (int i = 0; i <= j; ++i) Hj[i] = t.hcol[i];
-    Hj[j + 1] = sqrt(t.hcol[j + 1]);
-    for (int i = 0; i < j; ++i) {
-        double a = Hj[i], b = Hj[i + 1];
-        Hj[i] = t.cs[i] * a + t.sn[i] * b;
-        Hj[i + 1] = -t.sn[i] * a + t.cs[i] * b;
-    }
-    double a = Hj[j], b = Hj[j + 1];
-    double rr = hypot(a, b);
-    double c = rr > 0 ? a / rr : 1.0, sn = rr > 0 ? b / rr : 0.0;
-    t.cs[j] = c;
-    t.sn[j] = sn;
-    Hj[j] = rr;
-    Hj[j + 1] = 0.0;
-    t.g[j + 1] = -sn * t.g[j];
-    t.g[j] = c * t.g[j];
-    t.res[0] = fabs(t.g[j + 1]);
+    gm_givens_step(m, j, t);
 }
 
 __global__ void k_dg_start_scale(long long n, const double* __restrict__ small, long long sstr, long long hoff,
@@ -1476,25 +1473,7 @@ __global__ void k_dg_givens(int m, GmState s, long long sstr, const DgCtl* __res
 {
     const long long o = blockIdx.x * sstr;
     GmState t = {s.H + o, s.cs + o, s.sn + o, s.g + o, s.y + o, s.hcol + o, s.res + o};
-    const int j = ctl->j;
-    double* Hj = t.H + (size_t)j * (m + 1);
-    for (int i = 0; i <= j; ++i) Hj[i] = t.hcol[i];
-    Hj[j + 1] = sqrt(t.hcol[j + 1]);
-    for (int i = 0; i < j; ++i) {
-        double a = Hj[i], b = Hj[i + 1];
-        Hj[i] = t.cs[i] * a + t.sn[i] * b;
-        Hj[i + 1] = -t.sn[i] * a + t.cs[i] * b;
-    }
-    double a = Hj[j], b = Hj[j + 1];
-    double rr = hypot(a, b);
-    double c = rr > 0 ? a / rr : 1.0, sn = rr > 0 ? b / rr : 0.0;
-    t.cs[j] = c;
-    t.sn[j] = sn;
-    Hj[j] = rr;
-    Hj[j + 1] = 0.0;
-    t.g[j + 1] = -sn * t.g[j];
-    t.g[j] = c * t.g[j];
-    t.res[0] = fabs(t.g[j + 1]);
+    gm_givens_step(m, ctl->j, t);
 }
 
 // After an Arnoldi step: each active right-hand side counts the step and checks its residual

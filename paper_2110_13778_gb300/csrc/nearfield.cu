@@ -500,11 +500,14 @@ __global__ void k_corrections(int nt, const int* __restrict__ toff, const int* _
     double y1 = 0.0, y2 = 0.0;
     if (xs) {
         xs += o;
+        // the four values of a pair as two 16-byte loads
+        const double2* c2 = reinterpret_cast<const double2*>(corr);
         for (int t = toff[k]; t < toff[k + 1]; ++t) {
             int j = tj[t];
             double ph = xs[j], dph = xs[nt + j];
-            y1 += corr[4 * t] * dph + corr[4 * t + 1] * ph;
-            y2 += corr[4 * t + 2] * dph + corr[4 * t + 3] * ph;
+            const double2 a = c2[2 * t], b = c2[2 * t + 1];
+            y1 += a.x * dph + a.y * ph;
+            y2 += b.x * dph + b.y * ph;
         }
     }
     if (yf) {
@@ -615,7 +618,9 @@ __global__ void k_corrections4(int nt, int nr, const int* __restrict__ toff, con
     if (xs)
         for (int t = toff[k]; t < toff[k + 1]; ++t) {
             const int j = tj[t];
-            const double c0 = corr[4 * t], c1 = corr[4 * t + 1], c2 = corr[4 * t + 2], c3 = corr[4 * t + 3];
+            const double2 a = reinterpret_cast<const double2*>(corr)[2 * t];
+            const double2 b = reinterpret_cast<const double2*>(corr)[2 * t + 1];
+            const double c0 = a.x, c1 = a.y, c2 = b.x, c3 = b.y;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (q < nq) {
