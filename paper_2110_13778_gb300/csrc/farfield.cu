@@ -65,6 +65,10 @@ __device__ __forceinline__ void mi_unpack(int v, int& a, int& b, int& c)
 // with their per-axis tables d'^k / k! (one row of 3 (p + 1) values per source, so that the
 // threads of a warp, which differ in k, read different banks) and their four weights (dynamic
 // shared memory, p2m_smem bytes).
+template <class R>
+struct __align__(4 * sizeof(R)) P2mW {
+    R a, b, c, d;
+};
 #define P2M_T 192
 #define P2M_S 96
 #define P2M_R 3  // multi-indices per thread: nterms(12) = 455 <= 3 * 192
@@ -84,9 +88,10 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nt, int p, const int* __restr
     xs += blockIdx.y * xstr;
     sig0 += blockIdx.y * sstr;
     sigk += blockIdx.y * sstr;
-    extern __shared__ __align__(16) unsigned char p2m_sm[];
+    extern __shared__ __align__(32) unsigned char p2m_sm[];
     R* ex = (R*)p2m_sm;                   // [P2M_S][3][p + 1]: (source, axis, power)
-    R* wt = ex + 3 * (p + 1) * P2M_S;     // [4][P2M_S]: A dphi, A phi n_x, A phi n_y, A phi n_z
+    // [P2M_S] records (A dphi, A phi n_x, A phi n_y, A phi n_z): one broadcast load per source
+    P2mW<R>* wt = (P2mW<R>*)(ex + 3 * (p + 1) * P2M_S);
     const int c = blockIdx.x;
     const int T = pb_nterms(p);
     R* Ssh = ex;                          // after the sources: S and G_x, G_y, G_z, [4][T]
@@ -116,10 +121,7 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nt, int p, const int* __restr
                 }
             }
             const R wphi = (R)(P.w * xs[j]), wdphi = (R)(P.w * xs[nt + j]);
-            wt[threadIdx.x] = wdphi;
-            wt[P2M_S + threadIdx.x] = wphi * (R)Nn.x;
-            wt[2 * P2M_S + threadIdx.x] = wphi * (R)Nn.y;
-            wt[3 * P2M_S + threadIdx.x] = wphi * (R)Nn.z;
+            wt[threadIdx.x] = {wdphi, wphi * (R)Nn.x, wphi * (R)Nn.y, wphi * (R)Nn.z};
         }
         __syncthreads();
 #pragma unroll
@@ -131,10 +133,11 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nt, int p, const int* __restr
             R s = 0, g0 = 0, g1 = 0, g2 = 0;
             for (int q = 0; q < ns; ++q) {
                 const R m = e1[q * rs] * e2[q * rs] * e3[q * rs];
-                s += wt[q] * m;
-                g0 += wt[P2M_S + q] * m;
-                g1 += wt[2 * P2M_S + q] * m;
-                g2 += wt[3 * P2M_S + q] * m;
+                const P2mW<R> w = wt[q];
+                s += w.a * m;
+                g0 += w.b * m;
+                g1 += w.c * m;
+                g2 += w.d * m;
             }
             acc[r][0] += s;
             acc[r][1] += g0;
@@ -1015,6 +1018,121 @@ __global__ void __launch_bounds__(FAR_T) k_l2p(int nt, int p, double eps, const 
     }
 }
 
+// LtP in FP32 for a compile-time order P (the mixed-precision path): per leaf the coefficients
+// are staged once as (L^[a], G_1[a], G_2[a], G_3[a]) records, one 16-byte shared-memory
+// broadcast per term; per target the per-axis tables d^q / q! live in registers and the loops
+// over the multi-indices are unrolled in layout order, so a term costs one product, one load
+// and four FMAs instead of an index unpack and three table loads.
+template <int P>
+__global__ void __launch_bounds__(FAR_T) k_l2p_f(int nt, double eps, const int* __restrict__ begin,
+                                                 const double* __restrict__ xc, const double4_32a* __restrict__ ep,
+                                                 const double4_32a* __restrict__ en, const float* __restrict__ l0,
+                                                 const float* __restrict__ lk, double* __restrict__ ys, long long lstr,
+                                                 long long ystr)
+{
+    constexpr int T = (P + 1) * (P + 2) * (P + 3) / 6, Tm = P * (P + 1) * (P + 2) / 6;
+    __shared__ float A2[T];
+    __shared__ float4 cf[T];
+    l0 += blockIdx.y * lstr;
+    lk += blockIdx.y * lstr;
+    ys += blockIdx.y * ystr;
+    const int c = blockIdx.x;
+    const float ieps = (float)(1.0 / eps);
+    for (int a = threadIdx.x; a < T; a += FAR_T) {
+        int a1, a2, a3;
+        mi_unpack(c_mi[a], a1, a2, a3);
+        const float f = (float)(c_fact[a1] * c_fact[a2] * c_fact[a3]);
+        const float u = l0[(size_t)c * T + a], v = lk[(size_t)c * T + a];
+        cf[a].x = (u + v) * f;
+        A2[a] = (u + v * ieps) * f;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < T; a += FAR_T) {
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        if (a < Tm) {
+            int a1, a2, a3;
+            mi_unpack(c_mi[a], a1, a2, a3);
+            g0 = A2[pb_midx(a1 + 1, a2, a3)];
+            g1 = A2[pb_midx(a1, a2 + 1, a3)];
+            g2 = A2[pb_midx(a1, a2, a3 + 1)];
+        }
+        cf[a].y = g0;
+        cf[a].z = g1;
+        cf[a].w = g2;
+    }
+    const double cx = xc[3 * c], cy = xc[3 * c + 1], cz = xc[3 * c + 2];
+    __syncthreads();
+    for (int k = begin[c] + threadIdx.x; k < begin[c + 1]; k += FAR_T) {
+        const double4_32a Pp = ep[k], Nn = en[k];
+        const float dx = (float)(Pp.x - cx), dy = (float)(Pp.y - cy), dz = (float)(Pp.z - cz);
+        float ex[P + 1], ey[P + 1], ez[P + 1];
+        {
+            float vx = 1.f, vy = 1.f, vz = 1.f;
+#pragma unroll
+            for (int q = 0; q <= P; ++q) {
+                const float f = c_i1f[q];
+                ex[q] = vx * f;
+                ey[q] = vy * f;
+                ez[q] = vz * f;
+                vx *= dx;
+                vy *= dy;
+                vz *= dz;
+            }
+        }
+        float s1 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f;
+        // an offset the compiler cannot see through, so that the coefficient loads stay in the
+        // target loop (hoisted out of it they would need 4 T registers)
+        int z;
+        asm volatile("mov.u32 %0, 0;" : "=r"(z));
+        const float4* cfz = cf + z;
+        int al = 0;
+#pragma unroll
+        for (int n = 0; n <= P; ++n)
+#pragma unroll
+            for (int a = n; a >= 0; --a)
+#pragma unroll
+                for (int b = n - a; b >= 0; --b) {
+                    const float m = ex[a] * (ey[b] * ez[n - a - b]);
+                    const float4 k4 = cfz[al];
+                    s1 = fmaf(k4.x, m, s1);
+                    if (n < P) {
+                        t0 = fmaf(k4.y, m, t0);
+                        t1 = fmaf(k4.z, m, t1);
+                        t2 = fmaf(k4.w, m, t2);
+                    }
+                    ++al;
+                }
+        const float s2 = (float)Nn.x * t0 + (float)Nn.y * t1 + (float)Nn.z * t2;
+        ys[k] = -(Pp.w * (double)s1);  // every element lies in one leaf: the far-field part is set here
+        ys[nt + k] = -(Pp.w * (double)s2);
+    }
+}
+
+template <int P>
+static void l2p_f_launch(dim3 g, cudaStream_t st, int nt, double eps, const int* begin, const double* xc,
+                         const double4_32a* ep, const double4_32a* en, const float* l0, const float* lk, double* ys,
+                         long long lstr, long long ystr)
+{
+    k_l2p_f<P><<<g, FAR_T, 0, st>>>(nt, eps, begin, xc, ep, en, l0, lk, ys, lstr, ystr);
+}
+
+// the fixed-order FP32 LtP for orders 1..12; false for other orders (the generic kernel then)
+static bool l2p_f(int p, dim3 g, cudaStream_t st, int nt, double eps, const int* begin, const double* xc,
+                  const double4_32a* ep, const double4_32a* en, const float* l0, const float* lk, double* ys,
+                  long long lstr, long long ystr)
+{
+#define PB_L2P_F(P)                                                                     \
+    case P:                                                                             \
+        l2p_f_launch<P>(g, st, nt, eps, begin, xc, ep, en, l0, lk, ys, lstr, ystr); \
+        return true;
+    switch (p) {
+        PB_L2P_F(1) PB_L2P_F(2) PB_L2P_F(3) PB_L2P_F(4) PB_L2P_F(5) PB_L2P_F(6)
+        PB_L2P_F(7) PB_L2P_F(8) PB_L2P_F(9) PB_L2P_F(10) PB_L2P_F(11) PB_L2P_F(12)
+    }
+#undef PB_L2P_F
+    return false;
+}
+
 
 static int upload_tables(pb_ctx* c)
 {
@@ -1325,11 +1443,19 @@ static int far_apply(pb_ctx* c, const double* xs, double* ys, int nr, cudaStream
     }
     {
         PbLevel& lv = c->lev[L];
-        const size_t lsm = l2p_smem<R>(lv.p);
-        PB_CUDA(c, cudaFuncSetAttribute(k_l2p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
-        k_l2p<R><<<dim3(lv.ncl, nr), FAR_T, lsm, st>>>(np, lv.p, eps, pts ? c->begin_q : lv.begin, lv.xc,
-                                                        pts ? c->pts_p : c->e64p, pts ? c->pts_n : c->e64n,
-                                                        (R*)lv.lam0, (R*)lv.lamk, pts ? c->yq : ys, sstr(lv), pvstr);
+        const int* tb = pts ? c->begin_q : lv.begin;
+        const double4_32a *tp = pts ? c->pts_p : c->e64p, *tn = pts ? c->pts_n : c->e64n;
+        double* ty = pts ? c->yq : ys;
+        bool done = false;
+        if constexpr (sizeof(R) == sizeof(float))
+            done = l2p_f(lv.p, dim3(lv.ncl, nr), st, np, eps, tb, lv.xc, tp, tn, (const float*)lv.lam0,
+                         (const float*)lv.lamk, ty, sstr(lv), pvstr);
+        if (!done) {
+            const size_t lsm = l2p_smem<R>(lv.p);
+            PB_CUDA(c, cudaFuncSetAttribute(k_l2p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+            k_l2p<R><<<dim3(lv.ncl, nr), FAR_T, lsm, st>>>(np, lv.p, eps, tb, lv.xc, tp, tn, (R*)lv.lam0, (R*)lv.lamk,
+                                                            ty, sstr(lv), pvstr);
+        }
         PB_LAUNCH(c);
         if (pts) {
             int rc1 = pb_from_points(c, c->yq, ys, 0, st);
