@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "f32x2.cuh"
 #include "kernels.cuh"
 #include "pb_internal.cuh"
 
@@ -96,6 +97,91 @@ __global__ void __launch_bounds__(KB) k_rhs(int nt, int nc, const double4_32a* _
     }
 }
 
+// The mixed-precision form on packed FP32 pairs: the two target elements of a thread are the
+// two halves of every f32x2 operation, and each staged charge is stored duplicated in both
+// halves (x, x, y, y), (z, z, q, q) and (x_lo, x_lo, y_lo, y_lo), (z_lo, z_lo, 0, 0), so one
+// instruction does the work of both pair evaluations; only the reciprocal square root runs per
+// half.
+__global__ void __launch_bounds__(KB, 4) k_rhs_x2(int nt, int nc, const double4_32a* __restrict__ ep,
+                                               const double4_32a* __restrict__ en, const double* __restrict__ qpos,
+                                               const double* __restrict__ q, double eps1, double* __restrict__ b)
+{
+    __shared__ float4 sq[4][KB];
+    const int k0 = blockIdx.x * 2 * KB + threadIdx.x;
+    float ph[2][3], pl[2][3], nr[2][3];
+    double w[2];
+    bool act[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int k = k0 + u * KB;
+        act[u] = k < nt;
+        double4_32a p = make_double4_32a(0, 0, 0, 0), n = p;
+        if (act[u]) {
+            p = ep[k];
+            n = en[k];
+        }
+        const double pc[3] = {p.x, p.y, p.z}, nc3[3] = {n.x, n.y, n.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            ph[u][a] = (float)pc[a];
+            pl[u][a] = (float)(pc[a] - (double)ph[u][a]);
+            nr[u][a] = (float)nc3[a];
+        }
+        w[u] = p.w;
+    }
+    const f2x px = x2_pack(ph[0][0], ph[1][0]), py = x2_pack(ph[0][1], ph[1][1]), pz = x2_pack(ph[0][2], ph[1][2]);
+    const f2x lx = x2_pack(pl[0][0], pl[1][0]), ly = x2_pack(pl[0][1], pl[1][1]), lz = x2_pack(pl[0][2], pl[1][2]);
+    const f2x nx = x2_pack(nr[0][0], nr[1][0]), ny = x2_pack(nr[0][1], nr[1][1]), nz = x2_pack(nr[0][2], nr[1][2]);
+    double s1[2] = {0.0, 0.0}, s2[2] = {0.0, 0.0};
+    const double i4pi = 0.07957747154594767;
+    for (int t0 = 0; t0 < nc; t0 += KB) {
+        __syncthreads();
+        if (t0 + threadIdx.x < nc) {
+            const int t = t0 + threadIdx.x;
+            const double v[3] = {qpos[3 * t], qpos[3 * t + 1], qpos[3 * t + 2]};
+            const float h[3] = {(float)v[0], (float)v[1], (float)v[2]};
+            const float l[3] = {(float)(v[0] - (double)h[0]), (float)(v[1] - (double)h[1]), (float)(v[2] - (double)h[2])};
+            const float qq = (float)q[t];
+            sq[0][threadIdx.x] = make_float4(h[0], h[0], h[1], h[1]);
+            sq[1][threadIdx.x] = make_float4(h[2], h[2], qq, qq);
+            sq[2][threadIdx.x] = make_float4(l[0], l[0], l[1], l[1]);
+            sq[3][threadIdx.x] = make_float4(l[2], l[2], 0.f, 0.f);
+        }
+        __syncthreads();
+        const int m = min(KB, nc - t0);
+        f2x a1 = x2_dup(0.f), a2 = x2_dup(0.f);
+        for (int t = 0; t < m; ++t) {
+            const float4 g0 = sq[0][t], g1 = sq[1][t], g2 = sq[2][t], g3 = sq[3][t];
+            const f2x dx = x2_add(x2_sub(px, x2_pack(g0.x, g0.y)), x2_sub(lx, x2_pack(g2.x, g2.y)));
+            const f2x dy = x2_add(x2_sub(py, x2_pack(g0.z, g0.w)), x2_sub(ly, x2_pack(g2.z, g2.w)));
+            const f2x dz = x2_add(x2_sub(pz, x2_pack(g1.x, g1.y)), x2_sub(lz, x2_pack(g3.x, g3.y)));
+            const f2x r2 = x2_fma(dz, dz, x2_fma(dy, dy, x2_mul(dx, dx)));
+            float ra, rb;
+            x2_unpack(r2, ra, rb);
+            const f2x ri = x2_pack(rsqrtf(ra), rsqrtf(rb));
+            const f2x nd = x2_fma(nz, dz, x2_fma(ny, dy, x2_mul(nx, dx)));
+            const f2x qr = x2_mul(x2_pack(g1.z, g1.w), ri);
+            a1 = x2_add(a1, qr);
+            a2 = x2_sub(a2, x2_mul(x2_mul(qr, nd), x2_mul(ri, ri)));  // dG0/dn_x = -(n.d)/(4 pi r^3)
+        }
+        float u0, u1;
+        x2_unpack(a1, u0, u1);
+        s1[0] += (double)u0;
+        s1[1] += (double)u1;
+        x2_unpack(a2, u0, u1);
+        s2[0] += (double)u0;
+        s2[1] += (double)u1;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int k = k0 + u * KB;
+        if (act[u]) {
+            b[k] = w[u] * s1[u] * i4pi / eps1;
+            b[nt + k] = w[u] * s2[u] * i4pi / eps1;
+        }
+    }
+}
+
 int pb_rhs_sorted(pb_ctx* c, double* bs)
 {
     // with a regular rule of order > 1 the kernel runs on the points, summed per element after
@@ -105,8 +191,7 @@ int pb_rhs_sorted(pb_ctx* c, double* bs)
     double* out = c->q2 > 1 ? c->yq : bs;
     pb_tic(c, PB_T_RHS);
     if (c->prm.precision == PB_MIXED)
-        k_rhs<float><<<(nt + 2 * KB - 1) / (2 * KB), KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, c->prm.eps_in,
-                                                                     out);
+        k_rhs_x2<<<(nt + 2 * KB - 1) / (2 * KB), KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, c->prm.eps_in, out);
     else
         k_rhs<double><<<(nt + 2 * KB - 1) / (2 * KB), KB, 0, c->st>>>(nt, c->nc, ep, en, c->qpos, c->q, c->prm.eps_in,
                                                                       out);

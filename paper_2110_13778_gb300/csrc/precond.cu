@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_blk_gj_w(const int* __restric
 }
 
 // z = M^-1 r per leaf: the block's slice of r staged once in shared memory (in the working
-// precision), then one warp per row with lanes striding the columns
+// precision), then one warp per row (FP32: two rows) with lanes striding the columns
 template <class R>
 __global__ void k_blk_apply(int nt, const int* __restrict__ begin, const long long* __restrict__ moff,
                             const R* __restrict__ minv, const double* __restrict__ r, double* __restrict__ z,
@@ -314,20 +314,40 @@ __global__ void k_blk_apply(int nt, const int* __restrict__ begin, const long lo
     for (int j = threadIdx.x; j < m; j += blockDim.x) rv[j] = (R)(j < n ? r[b + j] : r[nt + b + j - n]);
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31, nw = blockDim.x / 32;
+    if constexpr (sizeof(R) == sizeof(float)) {
+        // m is even and every block starts at a multiple of 4 entries (the orders m^2 of the
+        // blocks before it are multiples of 4): rows and the staged slice read in pairs; two rows
+        // per warp at a time, so that twice the loads are in flight
+        const float2* rv2 = reinterpret_cast<const float2*>(rv);
+        for (int i = warp; i < m; i += 2 * nw) {
+            const int i2 = i + nw;
+            const bool two = i2 < m;
+            const float2* row = reinterpret_cast<const float2*>(Mc + (size_t)i * m);
+            const float2* row2 = reinterpret_cast<const float2*>(Mc + (size_t)(two ? i2 : i) * m);
+            float s = 0.f, s2 = 0.f;
+            for (int j = lane; j < m / 2; j += 32) {
+                const float2 a = row[j], a2 = row2[j], v = rv2[j];
+                s += a.x * v.x + a.y * v.y;
+                s2 += a2.x * v.x + a2.y * v.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                s += __shfl_xor_sync(0xffffffffu, s, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            }
+            if (lane == 0) {
+                if (i < n) z[b + i] = (double)s;
+                else z[nt + b + i - n] = (double)s;
+                if (two) {
+                    if (i2 < n) z[b + i2] = (double)s2;
+                    else z[nt + b + i2 - n] = (double)s2;
+                }
+            }
+        }
+        return;
+    }
     for (int i = warp; i < m; i += nw) {
         R s = 0;
-        if constexpr (sizeof(R) == sizeof(float)) {
-            // m is even and every block starts at a multiple of 4 entries (the orders m^2 of the
-            // blocks before it are multiples of 4): rows and the staged slice read in pairs
-            const float2* row = reinterpret_cast<const float2*>(Mc + (size_t)i * m);
-            const float2* rv2 = reinterpret_cast<const float2*>(rv);
-            for (int j = lane; j < m / 2; j += 32) {
-                const float2 a = row[j], b = rv2[j];
-                s += a.x * b.x + a.y * b.y;
-            }
-        } else {
-            for (int j = lane; j < m; j += 32) s += Mc[(size_t)i * m + j] * rv[j];
-        }
+        for (int j = lane; j < m; j += 32) s += Mc[(size_t)i * m + j] * rv[j];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
             if (i < n) z[b + i] = (double)s;
