@@ -178,10 +178,10 @@ def test_fmm_p8_within_1e4_of_dense(sphere3):
             pb.pb_destroy(ctx)
 
 
-@pytest.mark.parametrize("p,adaptive", [(4, 0), (6, 0), (8, 0), (10, 0), (5, 0), (3, 1)])
+@pytest.mark.parametrize("p,adaptive", [(4, 0), (6, 0), (8, 0), (10, 0), (5, 0), (3, 1), (2, 0), (7, 0), (9, 0)])
 def test_mixed_matches_oracle_fmm(sphere3, p, adaptive):
-    # p = 4, 6, 8 run the generated MtL bodies; p = 10, 5 and the adaptive orders (3..6 by
-    # level) the generic FP32 recurrence MtL
+    # p = 4, 6, 8 run the generated MtL bodies; p = 10, 5, 2, 7, 9 and the adaptive orders
+    # (3..6 by level) the generic FP32 recurrence MtL; every order runs its own fixed-order LtP
     m, ph, A = sphere3
     ctx = _ctx(m, leaf_size=16, eta0=0.8, p=p, adaptive=adaptive, precision=pb.PB_MIXED)
     try:
