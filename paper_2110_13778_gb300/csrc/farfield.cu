@@ -707,7 +707,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phas
 // edge, go to the staging rows part[2 k] and part[2 k + 1], which k_m2l_runs adds up per
 // target in chunk order. No atomics: the result does not depend on scheduling.
 template <int P>
-__global__ void __launch_bounds__(64, 1) k_m2l_seg(int nch, const int* __restrict__ soff,
+__global__ void __launch_bounds__(64, 5) k_m2l_seg(int nch, const int* __restrict__ soff,
                                                    const int* __restrict__ ssrc, const int* __restrict__ stgt,
                                                    const float* __restrict__ D0, const float* __restrict__ Dk,
                                                    const float* __restrict__ s0, const float* __restrict__ sk,
@@ -729,13 +729,40 @@ __global__ void __launch_bounds__(64, 1) k_m2l_seg(int nch, const int* __restric
     constexpr int NL = M2LWarp<P, 0>::n > M2LWarp<P, 1>::n ? M2LWarp<P, 0>::n : M2LWarp<P, 1>::n;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) unsigned long long bar;
-    __shared__ int tg[32];      // target of each lane's slot (-1: padding)
+    // the chunk's runs of slots with the same target (targets are sorted, so each is one run):
+    // first lane, target (-1: padding) and whether it began in an earlier chunk (1) or goes on
+    // in a later one (2)
+    __shared__ int rs[33], rt[32], rf[32];
+    __shared__ int nrun;
     float* Ds = (float*)dsm;    // [T * 32]
     float* Ms = Ds + T * 32;    // [T * 33]; with Ds, the reduction scratch [T * 33]
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     if (k >= nch) return;
     const int jl = ssrc[(size_t)k * 32 + lane];
-    if (wi == 0) tg[lane] = jl >= 0 ? stgt[(size_t)k * 32 + lane] : -1;
+    if (wi == 0) {
+        const int t = jl >= 0 ? stgt[(size_t)k * 32 + lane] : -1;
+        const int tp = __shfl_up_sync(0xffffffffu, t, 1);
+        const bool st = lane == 0 || tp != t;
+        const unsigned m = __ballot_sync(0xffffffffu, st);
+        if (st) {
+            const int q = __popc(m & ((1u << lane) - 1));
+            const unsigned later = lane == 31 ? 0u : (m >> (lane + 1)) << (lane + 1);
+            const int end = later ? __ffs(later) - 1 : 32;
+            const long long s0k = 32LL * k;  // first slot of the chunk
+            int f = 0;
+            if (t >= 0) {
+                if (lane == 0 && soff[t] < s0k) f |= 1;
+                if (end == 32 && soff[t + 1] > s0k + 32) f |= 2;
+            }
+            rs[q] = lane;
+            rt[q] = t;
+            rf[q] = f;
+        }
+        if (lane == 0) {
+            nrun = __popc(m);
+            rs[__popc(m)] = 32;
+        }
+    }
     if (threadIdx.x == 0) {
         mbar_init(&bar);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -778,24 +805,24 @@ __global__ void __launch_bounds__(64, 1) k_m2l_seg(int nch, const int* __restric
         for (int i = 0; i < M2LWarp<P, 1>::n; ++i) scratch[M2LWarp<P, 1>::alpha(i) * 33 + lane] = L[i];
     }
     __syncthreads();
-    const long long s0k = 32LL * k;  // first slot of the chunk
+    // per coefficient, the sum of each run in lane order: a run inside the chunk is the
+    // target's coefficient; one that crosses an edge is staged for k_m2l_runs
+    const int nrn = nrun;
     for (int i = threadIdx.x; i < T; i += 64) {
         const float sc = c_ifact[i];
-        float acc = 0.f;
-        int l0r = 0;
-        for (int l = 0; l < 32; ++l) {
-            acc += scratch[i * 33 + l];
-            const int t = tg[l];
-            if (l == 31 || tg[l + 1] != t) {  // the run [l0r, l] of target t ends here
-                if (t >= 0) {
-                    const bool opens = l0r == 0 && soff[t] < s0k;        // began in an earlier chunk
-                    const bool closes = l == 31 && soff[t + 1] > s0k + 32;  // goes on in a later one
-                    if (opens) part[(2LL * k) * T + i] = acc * sc;
-                    if (closes) part[(2LL * k + 1) * T + i] = acc * sc;
-                    if (!opens && !closes) out[(size_t)t * T + i] = acc * sc;
-                }
-                acc = 0.f;
-                l0r = l + 1;
+        const float* row = scratch + i * 33;
+        for (int q = 0; q < nrn; ++q) {
+            const int l1 = rs[q + 1];
+            int l = rs[q];
+            float acc = 0.f;
+            for (; l + 4 <= l1; l += 4) acc = (((acc + row[l]) + row[l + 1]) + row[l + 2]) + row[l + 3];
+            for (; l < l1; ++l) acc += row[l];
+            const int t = rt[q];
+            if (t >= 0) {
+                const int f = rf[q];
+                if (f & 1) part[(2LL * k) * T + i] = acc * sc;
+                if (f & 2) part[(2LL * k + 1) * T + i] = acc * sc;
+                if (!f) out[(size_t)t * T + i] = acc * sc;
             }
         }
     }
